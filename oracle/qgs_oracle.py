@@ -1,0 +1,605 @@
+"""FP64 CPU oracle for the quadric Gaussian splatting rasterizer.
+
+TEST INFRASTRUCTURE ONLY. Nothing on the product path may import or call this
+module: only the tests, the smoke check in ``__graft_entry__`` and the CPU-baseline
+leg of ``bench.py`` use it. It shares no code with the CUDA path.
+
+What it computes, step by step, and where each step is defined in the paper
+(arXiv 2411.16392, "Quadratic Gaussian Splatting"):
+
+  * Frame (Sec. 3.2, congruent transform Q = T^-T D T^-1 with T = [R c; 0 1]):
+    local coordinates x_hat = R^T (x - mu); the camera centre and the pixel ray
+    are taken into that frame.
+  * Surface (Sec. 3.2, explicit paraboloid equation): z_hat = a*x_hat^2 + b*y_hat^2,
+    with a = sign(s1)*s3/s1^2 and b = sign(s2)*s3/s2^2 (the lambda_1, lambda_2 of the
+    curvature paragraph).
+  * Ray-splat intersection (supplementary, "Details of Ray-splat Intersection"): the
+    quadratic A t^2 + B t + C = 0 and its two roots t_n <= t_f.
+  * Hit selection (Sec. 3.2.1): the near root if its geodesic distance is within
+    3 sigma(theta), else the far root under the same test, else no hit.
+  * Geodesic Gaussian (Sec. 3.2, polar form z = a(theta) rho^2, arc-length Eq.,
+    sigma(theta) Eq., G Eq.): l(a(theta), rho) in closed form, G = exp(-l^2/(2 sigma^2)).
+  * Normal (Sec. 3.2, normal Eq.): gradient of the implicit function at the hit,
+    rotated to camera space and turned to face the camera.
+  * Colour (Sec. 3.1): degree-3 real spherical harmonics, as in 3DGS.
+  * Alpha blending (Sec. 3.1 blending Eq., Eq. of the normal/curvature maps and the
+    supplementary's X_hat = sum alpha_i T_i X_i): front to back, in sorted order.
+  * Tile binning (supplementary, per-tile sorting): 16x16 tiles, one 64-bit key
+    (tile << 32 | float bits of the view depth) per (tile, primitive) pair, stable sort.
+
+Readings where the paper is silent (each one is listed with its reason in the
+design notes of the repository):
+  * alpha = min(0.99, o*G); pairs with alpha < 1/255 are skipped; a pixel stops
+    before blending the first pair that would take T below 1e-4 (the 3DGS constants
+    of the framework the paper builds on, Sec. 4.1 "Rasterizer").
+  * Roots are accepted only in front of the near plane (t > near, near = 0.2);
+    primitives whose centre is not in front of the near plane are culled.
+  * t is the camera-space z depth of the hit; the depth map is sum w_i t_i
+    (unnormalised), the normal map sum w_i n_i (unnormalised), in camera space.
+  * The roots are the exact roots of the quadratic (evaluated without cancellation);
+    the paper's |A| < 1e-6 tangent-plane fallback t = -C/B is the A -> 0 limit of
+    the near root and is not used as a separate approximation.
+  * Screen bound: the 8 corners of the local box |x| <= 3 s_u, |y| <= 3 s_v,
+    z_lo <= z <= z_hi, clipped to the near plane, projected, and their pixel AABB
+    taken (the "loose" box of the supplementary's bounding-box section, with a
+    provable z clamp). It is evaluated in FP32 with correctly rounded operations in
+    a fixed order so that tile lists and keys can be compared bit for bit.
+
+Gradients are exact derivatives of this FP64 forward, taken by PyTorch autograd.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+F64 = torch.float64
+TILE = 16
+ALPHA_MAX = 0.99
+ALPHA_MIN = 1.0 / 255.0
+T_MIN = 1e-4
+CUTOFF = 3.0          # support radius in sigma(theta) units
+TAYLOR_U = 1e-3       # |u| below which l is evaluated from its Taylor series
+
+
+# =========================================================================== FP32 binning
+@dataclass
+class Binning:
+    visible: np.ndarray     # bool [N]
+    zbits: np.ndarray       # uint32 [N] float32 bits of the view depth of the centre
+    rect: np.ndarray        # int32 [N, 4] (tx0, tx1, ty0, ty1), inclusive
+    count: np.ndarray       # int64 [N] tiles covered
+    keys: np.ndarray        # uint64 [I] sorted
+    vals: np.ndarray        # uint32 [I] primitive index per sorted key
+    ranges: np.ndarray      # int64 [n_tiles, 2] [start, end) into keys
+    tiles_x: int
+    tiles_y: int
+    pix_bbox: np.ndarray    # float32 [N, 4] (xmin, xmax, ymin, ymax) in pixels
+
+
+def bin_fp32(scene, cam) -> Binning:
+    """Conservative screen bound, tile rectangle and sort key of every primitive.
+
+    FP32, correctly rounded + - * / sqrt only, each operation rounded separately in
+    the order written below (no fused multiply-add). Loose bounding box of the
+    supplementary ("Details of Bounding Box Calculation"): the local box is
+    |x| <= 3 s_u, |y| <= 3 s_v and z between
+      z_lo = max(9 (min(0,a) s_u^2 + min(0,b) s_v^2), -3 max(s_u, s_v))
+      z_hi = min(9 (max(0,a) s_u^2 + max(0,b) s_v^2),  3 max(s_u, s_v)).
+    Any point of the support has l <= 3 sigma(theta); since l >= rho this gives
+    x^2/s_u^2 + y^2/s_v^2 <= 9, and since l >= |a(theta)| rho^2 = |z| it gives
+    |z| <= 3 max(s_u, s_v).
+    """
+    f = np.float32
+    N = scene.n
+    with np.errstate(all="ignore"):
+        mx, my, mz = (scene.mean[:, k].astype(f) for k in range(3))
+        Rc = cam.R_cw.astype(f)
+        tc = cam.t_cw.astype(f)
+        near = f(cam.near)
+
+        def cam_row(i):
+            return ((Rc[i, 0] * mx + Rc[i, 1] * my) + Rc[i, 2] * mz) + tc[i]
+
+        muc = [cam_row(0), cam_row(1), cam_row(2)]
+        qw, qx, qy, qz = (scene.quat[:, k].astype(f) for k in range(4))
+        n2 = ((qw * qw + qx * qx) + qy * qy) + qz * qz
+        r = np.sqrt(n2)
+        w, x, y, z = qw / r, qx / r, qy / r, qz / r
+        one, two = f(1.0), f(2.0)
+        R = [[one - two * (y * y + z * z), two * (x * y - w * z), two * (x * z + w * y)],
+             [two * (x * y + w * z), one - two * (x * x + z * z), two * (y * z - w * x)],
+             [two * (x * z - w * y), two * (y * z + w * x), one - two * (x * x + y * y)]]
+        Wm = [[(Rc[i, 0] * R[0][j] + Rc[i, 1] * R[1][j]) + Rc[i, 2] * R[2][j] for j in range(3)]
+              for i in range(3)]
+        su = scene.scale[:, 0].astype(f)
+        sv = scene.scale[:, 1].astype(f)
+        a = scene.curv[:, 0].astype(f)
+        b = scene.curv[:, 1].astype(f)
+        three, nine, zero = f(3.0), f(9.0), f(0.0)
+        X = three * su
+        Y = three * sv
+        zc = three * np.maximum(su, sv)
+        su2 = su * su
+        sv2 = sv * sv
+        apos = np.where(a > zero, a, zero)
+        bpos = np.where(b > zero, b, zero)
+        aneg = np.where(a < zero, a, zero)
+        bneg = np.where(b < zero, b, zero)
+        zhi = nine * (apos * su2 + bpos * sv2)
+        zlo = nine * (aneg * su2 + bneg * sv2)
+        zmax = np.minimum(zhi, zc)
+        zmin = np.maximum(zlo, -zc)
+
+        corners = []
+        for k in range(8):
+            sx = X if (k & 1) else -X
+            sy = Y if (k & 2) else -Y
+            sz = zmax if (k & 4) else zmin
+            corners.append([((muc[i] + Wm[i][0] * sx) + Wm[i][1] * sy) + Wm[i][2] * sz
+                            for i in range(3)])
+        fx, fy, cx, cy = f(cam.fx), f(cam.fy), f(cam.cx), f(cam.cy)
+        inf = f(np.inf)
+        xmin = np.full(N, inf, f)
+        xmax = np.full(N, -inf, f)
+        ymin = np.full(N, inf, f)
+        ymax = np.full(N, -inf, f)
+        anyp = np.zeros(N, bool)
+
+        def add_point(mask, px, py, pz):
+            u = fx * (px / pz) + cx
+            v = fy * (py / pz) + cy
+            xmin[mask] = np.minimum(xmin[mask], u[mask])
+            xmax[mask] = np.maximum(xmax[mask], u[mask])
+            ymin[mask] = np.minimum(ymin[mask], v[mask])
+            ymax[mask] = np.maximum(ymax[mask], v[mask])
+            anyp[mask] = True
+
+        inside = [c[2] >= near for c in corners]
+        for k in range(8):
+            add_point(inside[k], *corners[k])
+        for k0 in range(8):
+            for bit in (1, 2, 4):
+                if k0 & bit:
+                    continue
+                k1 = k0 | bit
+                P0, P1 = corners[k0], corners[k1]
+                cross = inside[k0] != inside[k1]
+                lam = (near - P0[2]) / (P1[2] - P0[2])
+                ex = P0[0] + lam * (P1[0] - P0[0])
+                ey = P0[1] + lam * (P1[1] - P0[1])
+                add_point(cross, ex, ey, np.full(N, near, f))
+
+        TX = (cam.W + TILE - 1) // TILE
+        TY = (cam.H + TILE - 1) // TILE
+        finite_in = (np.isfinite(scene.mean).all(1) & np.isfinite(scene.quat).all(1)
+                     & np.isfinite(scene.scale).all(1) & np.isfinite(scene.curv).all(1)
+                     & np.isfinite(scene.opacity))
+        vis = (finite_in & (n2 > zero) & (su > zero) & (sv > zero) & (muc[2] > near) & anyp
+               & np.isfinite(xmin) & np.isfinite(xmax) & np.isfinite(ymin) & np.isfinite(ymax))
+        vis &= ~((xmax < zero) | (ymax < zero) | (xmin >= f(cam.W)) | (ymin >= f(cam.H)))
+        sixteenth = f(1.0 / TILE)
+        tx0 = np.maximum(np.floor(xmin * sixteenth), zero)
+        tx1 = np.minimum(np.floor(xmax * sixteenth), f(TX - 1))
+        ty0 = np.maximum(np.floor(ymin * sixteenth), zero)
+        ty1 = np.minimum(np.floor(ymax * sixteenth), f(TY - 1))
+        rect = np.zeros((N, 4), np.int32)
+        rect[vis, 0] = tx0[vis].astype(np.int32)
+        rect[vis, 1] = tx1[vis].astype(np.int32)
+        rect[vis, 2] = ty0[vis].astype(np.int32)
+        rect[vis, 3] = ty1[vis].astype(np.int32)
+        count = np.where(vis, (rect[:, 1] - rect[:, 0] + 1).astype(np.int64)
+                         * (rect[:, 3] - rect[:, 2] + 1), 0)
+        zbits = muc[2].astype(f).view(np.uint32).copy()
+
+    # instances in primitive order, tiles row-major inside each rectangle
+    I = int(count.sum())
+    keys = np.empty(I, np.uint64)
+    vals = np.empty(I, np.uint32)
+    pos = 0
+    for i in np.nonzero(count)[0]:
+        x0, x1, y0, y1 = rect[i]
+        ty, tx = np.meshgrid(np.arange(y0, y1 + 1), np.arange(x0, x1 + 1), indexing="ij")
+        tiles = (ty * TX + tx).reshape(-1).astype(np.uint64)
+        c = tiles.size
+        keys[pos:pos + c] = (tiles << np.uint64(32)) | np.uint64(zbits[i])
+        vals[pos:pos + c] = i
+        pos += c
+    order = np.argsort(keys, kind="stable")
+    keys = keys[order]
+    vals = vals[order]
+    tiles_sorted = (keys >> np.uint64(32)).astype(np.int64)
+    ntiles = TX * TY
+    starts = np.searchsorted(tiles_sorted, np.arange(ntiles), side="left")
+    ends = np.searchsorted(tiles_sorted, np.arange(ntiles), side="right")
+    ranges = np.stack([starts, ends], 1).astype(np.int64)
+    pix_bbox = np.stack([xmin, xmax, ymin, ymax], 1).astype(np.float32)
+    return Binning(vis, zbits, rect, count, keys, vals, ranges, TX, TY, pix_bbox)
+
+
+# =========================================================================== FP64 geometry
+def quat_to_rot(q: torch.Tensor) -> torch.Tensor:
+    """Rotation matrix (local -> world) of the normalised quaternion (w, x, y, z)."""
+    q = q / torch.linalg.vector_norm(q, dim=-1, keepdim=True)
+    w, x, y, z = q.unbind(-1)
+    return torch.stack([
+        torch.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], -1),
+        torch.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], -1),
+        torch.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1),
+    ], -2)
+
+
+def arc_length(a_theta: torch.Tensor, rho: torch.Tensor) -> torch.Tensor:
+    """Arc length of the radial section z = a rho^2 from the vertex to rho (Sec. 3.2,
+    geodesic Eq.): l = [ln(sqrt(u^2+1) + u) + u sqrt(u^2+1)] / (4a), u = 2 a rho.
+    For |u| < 1e-3 the series rho (1 + u^2/6 - u^4/40) is used (it also covers a = 0,
+    where l = rho, the planar limit stated in Sec. 3.2)."""
+    u = 2.0 * a_theta * rho
+    small = u.abs() < TAYLOR_U
+    u_s = torch.where(small, torch.full_like(u, 1.0), u)
+    a_s = torch.where(small, torch.full_like(u, 1.0), a_theta)
+    r = torch.sqrt(u_s * u_s + 1.0)
+    closed = (torch.log(r + u_s) + u_s * r) / (4.0 * a_s)
+    u2 = u * u
+    series = rho * (1.0 + u2 / 6.0 - u2 * u2 / 40.0)
+    return torch.where(small, series, closed)
+
+
+def sigma_theta(theta: torch.Tensor, s1: torch.Tensor, s2: torch.Tensor) -> torch.Tensor:
+    """Directional standard deviation of the in-surface Gaussian (Sec. 3.2, sigma Eq.)."""
+    return s1 * s2 / torch.sqrt((s2 * torch.cos(theta)) ** 2 + (s1 * torch.sin(theta)) ** 2)
+
+
+def geodesic_gaussian(x, y, a, b, s1, s2):
+    """Geodesic Gaussian at a surface point with local (x, y) (Sec. 3.2).
+    Returns (G, l, sigma). theta is the cylindrical angle of (x, y);
+    a(theta) = a cos^2 theta + b sin^2 theta (polar form of the paraboloid)."""
+    rho2 = x * x + y * y
+    zero = rho2 == 0
+    xs = torch.where(zero, torch.ones_like(x), x)
+    ys = torch.where(zero, torch.zeros_like(y), y)
+    theta = torch.atan2(ys, xs)
+    rho = torch.sqrt(torch.where(zero, torch.ones_like(rho2), rho2))
+    rho = torch.where(zero, torch.zeros_like(rho), rho)
+    a_th = a * torch.cos(theta) ** 2 + b * torch.sin(theta) ** 2
+    l = arc_length(a_th, rho)
+    sig = sigma_theta(theta, s1, s2)
+    G = torch.exp(-(l * l) / (2.0 * sig * sig))
+    return G, l, sig
+
+
+def quadratic_roots(A, B, C):
+    """Both real roots (t1 <= t2) of A t^2 + B t + C = 0 and whether they exist.
+    q = -(B + sgn(B) sqrt(D)) / 2 with sgn(0) = +1; the roots are C/q and q/A, each
+    missing when its denominator is zero (A = 0 leaves the single root -C/B)."""
+    D = B * B - 4.0 * A * C
+    real = D >= 0
+    Ds = torch.where(real, D, torch.zeros_like(D))
+    sgn = torch.where(B >= 0, torch.ones_like(B), -torch.ones_like(B))
+    q = -0.5 * (B + sgn * torch.sqrt(Ds))
+    ok1 = real & (q != 0)
+    ok2 = real & (A != 0)
+    q_s = torch.where(q != 0, q, torch.ones_like(q))
+    A_s = torch.where(A != 0, A, torch.ones_like(A))
+    r1 = C / q_s
+    r2 = q / A_s
+    ok1 = ok1 & torch.isfinite(r1)
+    ok2 = ok2 & torch.isfinite(r2)
+    # order: put the smaller existing root first
+    swap = ok1 & ok2 & (r2 < r1)
+    t1 = torch.where(swap, r2, r1)
+    t2 = torch.where(swap, r1, r2)
+    e1 = torch.where(swap, ok2, ok1)
+    e2 = torch.where(swap, ok1, ok2)
+    # a single existing root is the "near" one
+    only2 = ~e1 & e2
+    t1, t2 = torch.where(only2, t2, t1), torch.where(only2, t1, t2)
+    e1, e2 = e1 | e2, e1 & e2
+    margin_D = (D.abs() / (B * B + 4.0 * (A * C).abs()).clamp_min(1e-300)).detach()
+    return t1, t2, e1, e2, margin_D
+
+
+# =========================================================================== colour
+SH_C0 = 0.5 * math.sqrt(1.0 / math.pi)
+SH_C1 = math.sqrt(3.0 / (4.0 * math.pi))
+SH_C2 = (0.5 * math.sqrt(15.0 / math.pi), -0.5 * math.sqrt(15.0 / math.pi),
+         0.25 * math.sqrt(5.0 / math.pi), -0.5 * math.sqrt(15.0 / math.pi),
+         0.25 * math.sqrt(15.0 / math.pi))
+SH_C3 = (-0.25 * math.sqrt(35.0 / (2 * math.pi)), 0.5 * math.sqrt(105.0 / math.pi),
+         -0.25 * math.sqrt(21.0 / (2 * math.pi)), 0.25 * math.sqrt(7.0 / math.pi),
+         -0.25 * math.sqrt(21.0 / (2 * math.pi)), 0.25 * math.sqrt(105.0 / math.pi),
+         -0.25 * math.sqrt(35.0 / (2 * math.pi)))
+
+
+def sh_basis(d: torch.Tensor) -> torch.Tensor:
+    """The 16 real spherical-harmonic basis functions of degree <= 3 at unit directions
+    d [..., 3], in the order and sign convention of 3DGS (Sec. 3.1 uses its colour model)."""
+    x, y, z = d.unbind(-1)
+    xx, yy, zz = x * x, y * y, z * z
+    one = torch.ones_like(x)
+    return torch.stack([
+        SH_C0 * one,
+        -SH_C1 * y, SH_C1 * z, -SH_C1 * x,
+        SH_C2[0] * x * y, SH_C2[1] * y * z, SH_C2[2] * (2 * zz - xx - yy),
+        SH_C2[3] * x * z, SH_C2[4] * (xx - yy),
+        SH_C3[0] * y * (3 * xx - yy), SH_C3[1] * x * y * z,
+        SH_C3[2] * y * (4 * zz - xx - yy), SH_C3[3] * z * (2 * zz - 3 * xx - 3 * yy),
+        SH_C3[4] * x * (4 * zz - xx - yy), SH_C3[5] * z * (xx - yy),
+        SH_C3[6] * x * (xx - 3 * yy),
+    ], -1)
+
+
+# =========================================================================== params
+class Params:
+    """FP64 leaf tensors of a scene (SH decoded from its bfloat16 storage)."""
+
+    def __init__(self, scene, requires_grad=False):
+        from paper_2411_16392_gb300.scenes import bf16_bits_to_f32
+
+        def t(x):
+            return torch.tensor(np.asarray(x, np.float64), dtype=F64, requires_grad=requires_grad)
+
+        self.mean = t(scene.mean)
+        self.quat = t(scene.quat)
+        self.scale = t(scene.scale)
+        self.curv = t(scene.curv)
+        self.opacity = t(scene.opacity)
+        self.sh = t(bf16_bits_to_f32(scene.sh).reshape(-1, 16, 3))
+
+    def leaves(self):
+        return dict(mean=self.mean, quat=self.quat, scale=self.scale, curv=self.curv,
+                    opacity=self.opacity, sh=self.sh)
+
+
+class CamF64:
+    def __init__(self, cam):
+        self.W, self.H = cam.W, cam.H
+        self.fx, self.fy = float(np.float32(cam.fx)), float(np.float32(cam.fy))
+        self.cx, self.cy = float(np.float32(cam.cx)), float(np.float32(cam.cy))
+        self.R = torch.tensor(cam.R_cw.astype(np.float64), dtype=F64)
+        self.t = torch.tensor(cam.t_cw.astype(np.float64), dtype=F64)
+        self.near = float(np.float32(cam.near))
+        self.c_w = -(self.R.T @ self.t)      # camera centre in world coordinates
+
+
+# =========================================================================== per-pair evaluation
+def _eval_pairs(prm: Params, cam: CamF64, idx: torch.Tensor, px: torch.Tensor, py: torch.Tensor):
+    """Evaluate every (pixel, primitive) pair of a pixel set [P] and a primitive list [L].
+    Returns per-pair tensors [P, L]: alpha (0 where no contribution), validity, depth t,
+    colour [P, L, 3] (broadcast), camera-space unit normal [P, L, 3] and decision margins."""
+    mu = prm.mean[idx]
+    R = quat_to_rot(prm.quat[idx])                  # [L,3,3] columns = local axes (world)
+    su, sv = prm.scale[idx].unbind(-1)
+    a, b = prm.curv[idx].unbind(-1)
+    o = prm.opacity[idx]
+
+    # Local camera centre and pixel rays (congruent transform, Sec. 3.2).
+    o_hat = torch.einsum("lji,lj->li", R, cam.c_w[None, :] - mu)         # R^T (c - mu)
+    d_cam = torch.stack([(px + 0.5 - cam.cx) / cam.fx, (py + 0.5 - cam.cy) / cam.fy,
+                         torch.ones_like(px)], -1)                         # [P,3], z = 1
+    d_w = d_cam @ cam.R                                                    # R_cw^T d_cam
+    d_hat = torch.einsum("lji,pj->pli", R, d_w)                            # [P,L,3]
+    ox, oy, oz = (o_hat[:, k][None, :] for k in range(3))
+    dx, dy, dz = d_hat.unbind(-1)
+    A_ = a * dx * dx + b * dy * dy
+    B_ = 2.0 * (a * ox * dx + b * oy * dy) - dz
+    C_ = (a * ox * ox + b * oy * oy - oz).expand_as(A_)
+    t1, t2, e1, e2, _ = quadratic_roots(A_, B_, C_)
+    # Margin of the decision D >= 0, measured in a translation-invariant way: D is the
+    # same for the ray re-parametrised as s = t - t0 around the depth t0 of the centre,
+    # where B and C are of the size of the primitive instead of the camera distance.
+    with torch.no_grad():
+        t0 = (mu @ cam.R[2] + cam.t[2])[None, :]
+        D_ = B_ * B_ - 4.0 * A_ * C_
+        B0 = B_ + 2.0 * A_ * t0
+        C0 = (A_ * t0 + B_) * t0 + C_
+        m_D = D_.abs() / (B0 * B0 + 4.0 * (A_ * C0).abs()).clamp_min(1e-300)
+        # The decision only matters where the double root t* = -B/(2A) lies on the
+        # support (x^2/s_u^2 + y^2/s_v^2 <= 9, with slack); elsewhere both outcomes
+        # contribute nothing.
+        As = torch.where(A_ != 0, A_, torch.ones_like(A_))
+        tv = -B_ / (2.0 * As)
+        ev = ((ox + tv * dx) / su) ** 2 + ((oy + tv * dy) / sv) ** 2
+        m_D = torch.where((A_ != 0) & (ev <= 10.0), m_D, torch.full_like(m_D, np.inf))
+
+    near = cam.near
+    f1 = e1 & (t1 > near)
+    f2 = e2 & (t2 > near)
+    m_near = torch.minimum(torch.where(e1, (t1 - near).abs() / near, torch.full_like(t1, np.inf)),
+                           torch.where(e2, (t2 - near).abs() / near, torch.full_like(t2, np.inf))).detach()
+
+    def at(t, ok):
+        ts = torch.where(ok, t, torch.zeros_like(t))
+        x = ox + ts * dx
+        y = oy + ts * dy
+        G, l, sig = geodesic_gaussian(x, y, a, b, su, sv)
+        inside = ok & (l <= CUTOFF * sig)
+        margin = torch.where(ok, (l - CUTOFF * sig).abs() / (CUTOFF * sig), torch.full_like(l, np.inf))
+        return ts, x, y, G, inside, margin.detach()
+
+    # candidates in increasing t: the near root first, then the far one (Sec. 3.2.1)
+    tn, xn, yn, Gn, in_n, m_n = at(t1, f1)
+    tf, xf, yf, Gf, in_f, m_f = at(t2, f2)
+    pick_n = in_n
+    pick_f = ~in_n & in_f
+    hit = pick_n | pick_f
+    t = torch.where(pick_n, tn, tf)
+    x = torch.where(pick_n, xn, xf)
+    y = torch.where(pick_n, yn, yf)
+    G = torch.where(pick_n, Gn, torch.where(pick_f, Gf, torch.zeros_like(Gf)))
+    m_sig = torch.minimum(m_n, torch.where(in_n, torch.full_like(m_f, np.inf), m_f))
+
+    oG = o * G
+    alpha = torch.clamp(oG, max=ALPHA_MAX)
+    valid = hit & (alpha >= ALPHA_MIN)
+    alpha = torch.where(valid, alpha, torch.zeros_like(alpha))
+    m_amin = torch.where(hit, (oG - ALPHA_MIN).abs() / ALPHA_MIN, torch.full_like(oG, np.inf)).detach()
+    m_amax = torch.where(valid, (oG - ALPHA_MAX).abs() / ALPHA_MAX, torch.full_like(oG, np.inf)).detach()
+
+    # Normal: gradient of a x^2 + b y^2 - z at the hit (Sec. 3.2 normal Eq.), camera space,
+    # facing the camera.
+    n_l = torch.stack([2.0 * a * x, 2.0 * b * y, -torch.ones_like(x)], -1)   # [P,L,3]
+    n_w = torch.einsum("lij,plj->pli", R, n_l)
+    n_c = n_w @ cam.R.T
+    n_c = n_c / torch.linalg.vector_norm(n_c, dim=-1, keepdim=True)
+    facing = (n_c * d_cam[:, None, :]).sum(-1) > 0
+    n_c = torch.where(facing[..., None], -n_c, n_c)
+
+    # View-dependent colour (degree-3 SH, Sec. 3.1) at dir = normalise(mu - c).
+    dv = mu - cam.c_w[None, :]
+    dv = dv / torch.linalg.vector_norm(dv, dim=-1, keepdim=True)
+    rgb = torch.clamp((sh_basis(dv)[:, :, None] * prm.sh[idx]).sum(1) + 0.5, min=0.0)   # [L,3]
+
+    margin = torch.minimum(torch.minimum(m_D, m_near),
+                           torch.minimum(m_sig, torch.minimum(m_amin, m_amax)))
+    return dict(alpha=alpha, valid=valid, hit=hit, t=t, rgb=rgb, normal=n_c, margin=margin)
+
+
+def _composite(prm, cam, idx, px, py, chunk=4096):
+    """Front-to-back alpha blending of a pixel set over one sorted primitive list
+    (blending Eq. of Sec. 3.1 and X_hat = sum alpha_i T_i X_i of the supplementary)."""
+    P = px.shape[0]
+    dev = dict(dtype=F64)
+    T = torch.ones(P, **dev)
+    alive = torch.ones(P, dtype=torch.bool)
+    rgb = torch.zeros(P, 3, **dev)
+    depth = torch.zeros(P, **dev)
+    normal = torch.zeros(P, 3, **dev)
+    n_eval = torch.zeros(P, dtype=torch.int64)
+    n_contrib = torch.zeros(P, dtype=torch.int64)
+    margin = torch.full((P,), np.inf, **dev)
+    L = idx.shape[0]
+    for c0 in range(0, L, chunk):
+        sl = idx[c0:c0 + chunk]
+        Lc = sl.shape[0]
+        pe = _eval_pairs(prm, cam, sl, px, py)
+        al, v = pe["alpha"], pe["valid"]
+        onem = 1.0 - al
+        cp = torch.cumprod(onem, dim=1)
+        Tex = T[:, None] * torch.cat([torch.ones(P, 1, **dev), cp[:, :-1]], 1)
+        m_T = torch.where(v, (Tex * onem - T_MIN).abs().detach() / T_MIN,
+                          torch.full_like(Tex, np.inf))
+        term = v & ((Tex * onem) < T_MIN) & alive[:, None]
+        has = term.any(1)
+        k = torch.where(has, torch.argmax(term.to(torch.int8), 1), torch.full((P,), Lc))
+        ar = torch.arange(Lc)[None, :]
+        seen = (ar <= k[:, None]) & alive[:, None]
+        keep = v & (ar < k[:, None]) & alive[:, None]
+        w = torch.where(keep, al * Tex, torch.zeros_like(al))
+        rgb = rgb + (w[..., None] * pe["rgb"][None, :, :]).sum(1)
+        depth = depth + (w * pe["t"]).sum(1)
+        normal = normal + (w[..., None] * pe["normal"]).sum(1)
+        T = T * torch.where(keep, onem, torch.ones_like(onem)).prod(1)
+        mm = torch.minimum(pe["margin"], m_T)
+        margin = torch.minimum(margin, torch.where(seen, mm, torch.full_like(mm, np.inf)).min(1).values)
+        n_eval = n_eval + torch.where(alive, torch.where(has, k + 1, torch.full_like(k, Lc)),
+                                      torch.zeros_like(k))
+        last = torch.where(keep, ar.expand(P, Lc) + c0 + 1, torch.zeros_like(keep, dtype=torch.int64))
+        n_contrib = torch.maximum(n_contrib, last.max(1).values)
+        alive = alive & ~has
+        if not bool(alive.any()):
+            break
+    return dict(rgb=rgb, alpha=1.0 - T, depth=depth, normal=normal, T_final=T,
+                n_eval=n_eval, n_contrib=n_contrib, margin=margin)
+
+
+# =========================================================================== images
+OUT_KEYS = ("rgb", "alpha", "depth", "normal")
+
+
+def _tile_pixels(cam, tile, TX):
+    ty, tx = divmod(int(tile), TX)
+    ys, xs = np.meshgrid(np.arange(ty * TILE, min(ty * TILE + TILE, cam.H)),
+                         np.arange(tx * TILE, min(tx * TILE + TILE, cam.W)), indexing="ij")
+    return xs.reshape(-1), ys.reshape(-1)
+
+
+def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=None):
+    """Render the full image (or the listed tiles). Returns a dict of numpy arrays:
+    rgb [3,H,W], alpha [H,W], depth [H,W], normal [3,H,W], margin [H,W], n_eval [H,W],
+    n_contrib [H,W], T_final [H,W]. With `grad_images` (a dict of upstream gradients
+    with the same shapes as the outputs), also returns `grads`: the exact FP64 gradient
+    of sum(grad * output) with respect to every scene parameter."""
+    if binning is None:
+        binning = bin_fp32(scene, cam)
+    want_grad = grad_images is not None
+    prm = Params(scene, requires_grad=want_grad)
+    c64 = CamF64(cam)
+    H, W = cam.H, cam.W
+    out = dict(rgb=np.zeros((3, H, W)), alpha=np.zeros((H, W)), depth=np.zeros((H, W)),
+               normal=np.zeros((3, H, W)), margin=np.full((H, W), np.inf),
+               n_eval=np.zeros((H, W), np.int64), n_contrib=np.zeros((H, W), np.int64),
+               T_final=np.ones((H, W)))
+    TX = binning.tiles_x
+    if tiles is None:
+        tiles = range(binning.tiles_x * binning.tiles_y)
+    g = None
+    if want_grad:
+        g = {k: torch.tensor(np.asarray(v, np.float64)) for k, v in grad_images.items()}
+    for tile in tiles:
+        s, e = binning.ranges[tile]
+        xs, ys = _tile_pixels(cam, tile, TX)
+        if e <= s:
+            continue
+        idx = torch.from_numpy(binning.vals[s:e].astype(np.int64))
+        px = torch.tensor(xs, dtype=F64)
+        py = torch.tensor(ys, dtype=F64)
+        with torch.set_grad_enabled(want_grad):
+            r = _composite(prm, c64, idx, px, py)
+            if want_grad:
+                loss = ((g["rgb"][:, ys, xs].T * r["rgb"]).sum() + (g["alpha"][ys, xs] * r["alpha"]).sum()
+                        + (g["depth"][ys, xs] * r["depth"]).sum()
+                        + (g["normal"][:, ys, xs].T * r["normal"]).sum())
+                if loss.requires_grad:
+                    loss.backward()
+        out["rgb"][:, ys, xs] = r["rgb"].detach().numpy().T
+        out["alpha"][ys, xs] = r["alpha"].detach().numpy()
+        out["depth"][ys, xs] = r["depth"].detach().numpy()
+        out["normal"][:, ys, xs] = r["normal"].detach().numpy().T
+        out["margin"][ys, xs] = r["margin"].numpy()
+        out["n_eval"][ys, xs] = r["n_eval"].numpy()
+        out["n_contrib"][ys, xs] = r["n_contrib"].numpy()
+        out["T_final"][ys, xs] = r["T_final"].detach().numpy()
+    if want_grad:
+        grads = {}
+        for k, v in prm.leaves().items():
+            gr = v.grad if v.grad is not None else torch.zeros_like(v)
+            grads[k] = gr.numpy().copy()
+        grads["sh"] = grads["sh"].reshape(-1, 48)
+        out["grads"] = grads
+    out["binning"] = binning
+    return out
+
+
+def render_pixels(scene, cam, pixels, binning: Binning | None = None):
+    """Render individual pixels [(x, y), ...] one at a time (same lists and order as
+    the full image). Returns dict of arrays indexed like `pixels`."""
+    if binning is None:
+        binning = bin_fp32(scene, cam)
+    prm = Params(scene)
+    c64 = CamF64(cam)
+    TX = binning.tiles_x
+    res = {k: [] for k in ("rgb", "alpha", "depth", "normal", "margin", "n_eval", "n_contrib")}
+    for (x, y) in pixels:
+        tile = (y // TILE) * TX + (x // TILE)
+        s, e = binning.ranges[tile]
+        idx = torch.from_numpy(binning.vals[s:e].astype(np.int64))
+        with torch.no_grad():
+            r = _composite(prm, c64, idx, torch.tensor([float(x)], dtype=F64),
+                           torch.tensor([float(y)], dtype=F64))
+        for k in res:
+            res[k].append(r[k][0].numpy())
+    return {k: np.array(v) for k, v in res.items()}
+
+
+def pair_count(binning: Binning, cam) -> int:
+    """Number of (pixel, listed primitive) pairs before any early termination."""
+    TX = binning.tiles_x
+    tot = 0
+    for tile in range(binning.tiles_x * binning.tiles_y):
+        s, e = binning.ranges[tile]
+        xs, _ = _tile_pixels(cam, tile, TX)
+        tot += int(e - s) * xs.size
+    return tot
