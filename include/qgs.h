@@ -1,0 +1,198 @@
+/*
+ * qgs.h - C ABI of the GB300 (sm_103a) quadric Gaussian splatting rasterizer.
+ *
+ * The library renders and differentiates the paraboloid Gaussian primitives of
+ * "Quadratic Gaussian Splatting" (arXiv 2411.16392):
+ *   - primitive parameters: Sec. 3.2 (position c, rotation R, scales, signed curvature);
+ *     here mean, quaternion (w, x, y, z), in-surface scales (s_u, s_v) = (|s1|, |s2|),
+ *     curvatures (a, b) = (sign(s1) s3 / s1^2, sign(s2) s3 / s2^2) of the local surface
+ *     z = a x^2 + b y^2 (the lambda_1, lambda_2 of the curvature paragraph), opacity and
+ *     degree-3 SH colour (Sec. 3.1);
+ *   - geodesic Gaussian G = exp(-l^2 / (2 sigma(theta)^2)) with the closed-form arc
+ *     length l (Sec. 3.2, geodesic Eq.);
+ *   - ray-splat intersection and near/far hit selection within 3 sigma (Sec. 3.2.1 and
+ *     the supplementary's intersection section);
+ *   - front-to-back alpha blending of colour, alpha, depth and normal (Sec. 3.1 blending
+ *     Eq., Sec. 3.2 normal/curvature-map Eq.);
+ *   - 16x16 tiles ordered by 64-bit (tile << 32 | depth bits) keys (supplementary,
+ *     per-tile sorting);
+ *   - the reverse-order backward of the supplementary's dX/d(alpha) formula.
+ *
+ * Conventions for every entry point:
+ *   - Every function returns a qgs_status; nothing aborts or exits. On failure the
+ *     context keeps a message readable with qgs_last_error().
+ *   - Pointers inside qgs_scene, qgs_image and qgs_scene_grad are DEVICE pointers on
+ *     the context's device, owned by the caller, and must stay valid until the work
+ *     enqueued on `stream` has finished. Inputs are never modified.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     All device work is enqueued on it. render_forward synchronises the stream once
+ *     (to size the tile-instance buffers from the instance count); render_backward
+ *     does not synchronise.
+ *   - A context is not thread-safe; use one per host thread. The serving object
+ *     (qgs_server) is thread-safe.
+ *   - Images are planar float32: rgb[c*H*W + y*W + x], alpha[y*W + x], ...
+ */
+#ifndef QGS_H_
+#define QGS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QGS_OK = 0,
+  QGS_EINVAL = 1,      /* bad argument (null pointer, size, non-finite camera, ...) */
+  QGS_ENOMEM = 2,      /* device or host allocation failed */
+  QGS_ECAPACITY = 3,   /* a fixed-capacity buffer (serving) is too small for a frame */
+  QGS_ECUDA = 4,       /* a CUDA runtime call or kernel launch failed */
+  QGS_ETIMEDOUT = 5,   /* a bounded wait ran out */
+  QGS_EBUSY = 6,       /* the serving queue is full */
+  QGS_ENOTFOUND = 7,   /* unknown scene id or ticket */
+  QGS_ESTATE = 8       /* call out of order (backward without a matching forward) */
+} qgs_status;
+
+typedef void* qgs_stream; /* cudaStream_t */
+
+/* Pinhole camera. x_cam = R_cw * x_world + t_cw (R_cw row-major). The ray through
+ * pixel (px, py) goes through its centre: d_cam = ((px+0.5-cx)/fx, (py+0.5-cy)/fy, 1),
+ * so the ray parameter t is the camera-space z depth. Hits with t <= near_plane are
+ * ignored and primitives whose centre has z <= near_plane are culled. */
+typedef struct {
+  int32_t W, H;
+  float fx, fy, cx, cy;
+  float R_cw[9];
+  float t_cw[3];
+  float near_plane;
+} qgs_camera;
+
+/* Scene: n primitives, device pointers (float32 unless stated). */
+typedef struct {
+  int64_t n;
+  const float* mean;      /* [n*3] world-space centre */
+  const float* quat;      /* [n*4] (w, x, y, z), any nonzero norm */
+  const float* scale;     /* [n*2] (s_u, s_v) > 0 */
+  const float* curv;      /* [n*2] (a, b) */
+  const float* opacity;   /* [n]   in (0, 1) */
+  const uint16_t* sh;     /* [n*48] bfloat16 bits, index k*3 + c (SH coefficient k, channel c) */
+} qgs_scene;
+
+/* Image planes (device pointers). Output of render_forward (fully overwritten) or the
+ * upstream gradient given to render_backward (read only). */
+typedef struct {
+  float* rgb;      /* [3*H*W] */
+  float* alpha;    /* [H*W]   1 - final transmittance */
+  float* depth;    /* [H*W]   sum_i w_i t_i (unnormalised expected z depth) */
+  float* normal;   /* [3*H*W] sum_i w_i n_i, camera space, each n_i facing the camera */
+} qgs_image;
+
+/* Gradients of a scalar loss with respect to the scene parameters (device pointers,
+ * float32, same layouts as qgs_scene; sh is float32 [n*48]). render_backward ADDS into
+ * them; the caller zeroes them when needed. */
+typedef struct {
+  float* mean;
+  float* quat;
+  float* scale;
+  float* curv;
+  float* opacity;
+  float* sh;
+} qgs_scene_grad;
+
+/* Blending constants and pipeline options. qgs_config_default() gives the values the
+ * oracle and the tests use: alpha_max 0.99, alpha_min 1/255, T_min 1e-4,
+ * grazing_eps 1e-5 (roots whose discriminant D satisfies |D| <= grazing_eps * B^2 are
+ * re-solved in FP64), sort_mode 0. */
+typedef struct {
+  float alpha_max;
+  float alpha_min;
+  float T_min;
+  float grazing_eps;
+  int32_t sort_mode;   /* 0: per-primitive depth sort, then a stable sort of the
+                          (tile, primitive) instances by tile: the same order as sorting
+                          the 64-bit keys, with fewer passes over the instances.
+                          1: one radix sort of the full 64-bit tile|depth keys. */
+  int32_t reserved;
+} qgs_config;
+
+/* Counters of the last render_forward / render_backward. Pair counters classify the
+ * (pixel, listed primitive) pairs visited before each pixel stopped. Stage times are
+ * CUDA-event times on the caller's stream, filled only while profiling is enabled
+ * (qgs_set_profiling), else -1. */
+typedef struct {
+  int64_t n_primitives;
+  int64_t n_visible;        /* primitives with a nonempty tile rectangle */
+  int64_t n_instances;      /* (tile, primitive) pairs = sort length */
+  int64_t n_tiles;
+  int64_t pair_evals;       /* forward: pairs visited (the pair that stopped a pixel included) */
+  int64_t pair_isect;       /* forward: pairs inside the primitive's pixel box (quadratic solved) */
+  int64_t pair_hits;        /* forward: pairs with a root within 3 sigma */
+  int64_t pair_blended;     /* forward: pairs blended */
+  int64_t grazing_resolves; /* forward: pairs whose roots were re-solved in FP64 */
+  int64_t bwd_pairs;        /* backward: pairs recomputed */
+  int64_t bwd_contrib;      /* backward: pairs that produced a gradient */
+  int64_t launches_fwd;     /* kernels launched by the last render_forward */
+  int64_t launches_bwd;     /* kernels launched by the last render_backward */
+  float ms_preprocess, ms_depth_sort, ms_emit, ms_tile_sort, ms_raster_fwd;
+  float ms_raster_bwd, ms_preprocess_bwd;
+} qgs_frame_stats;
+
+typedef struct qgs_ctx qgs_ctx;
+
+/* Default constants (see qgs_config). Never fails. */
+void qgs_config_default(qgs_config* cfg);
+
+/* Create a rendering context on CUDA device `device`. The context owns its work
+ * buffers (projected primitives, keys, tile ranges, per-pixel residue), grown on
+ * demand. cfg may be NULL for the defaults. Errors: EINVAL, ECUDA, ENOMEM. */
+qgs_status qgs_create(qgs_ctx** out, const qgs_config* cfg, int32_t device);
+
+/* Free a context and its device buffers (waits for its work). NULL is ignored. */
+void qgs_destroy(qgs_ctx* ctx);
+
+/* Message of the last failure on this context ("" if none). Valid until the next call. */
+const char* qgs_last_error(const qgs_ctx* ctx);
+
+/* Forward render (Sec. 3.1-3.2, supplementary): preprocessing, tile binning, radix sort,
+ * per-tile compositing. Writes all four planes of `out` (W*H from `cam`). Keeps the
+ * per-pixel residue (final transmittance and the count of listed primitives up to the
+ * last blended one) and the sorted lists in the context for render_backward.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera* cam,
+                          const qgs_image* out, qgs_stream stream);
+
+/* Backward of the last render_forward on this context (same scene pointers, same camera):
+ * reverse-order traversal per pixel with transmittance recomputed from the residue
+ * (supplementary, dX/d(alpha) back-to-front form), then the chain rule to every primitive
+ * parameter. grad_out holds dL/d(rgb, alpha, depth, normal); a NULL plane means zero.
+ * Results are ADDED into `grad`. Errors: EINVAL, ESTATE, ENOMEM, ECUDA. */
+qgs_status render_backward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera* cam,
+                           const qgs_image* grad_out, const qgs_scene_grad* grad,
+                           qgs_stream stream);
+
+/* Counters (and, when profiling, stage times) of the last forward and backward.
+ * Synchronises the context's last stream. Errors: EINVAL, ESTATE, ECUDA. */
+qgs_status qgs_get_frame_stats(qgs_ctx* ctx, qgs_frame_stats* stats);
+
+/* Enable (1) or disable (0) CUDA-event timing of each pipeline stage on the caller's
+ * stream. Off by default; costs a few event records per call. Errors: EINVAL, ECUDA. */
+qgs_status qgs_set_profiling(qgs_ctx* ctx, int32_t enable);
+
+/* Copy the last forward's tile binning to HOST memory, for inspection and tests:
+ * keys[i] = (tile << 32) | float bits of the primitive's view depth, vals[i] = primitive
+ * index, in sorted order (cap entries at most); ranges[2*t], ranges[2*t+1] = [start, end)
+ * of tile t; rects[4*i] = (tx0, tx1, ty0, ty1) of primitive i (-1s when culled).
+ * Any pointer may be NULL. *n_instances receives the instance count.
+ * Errors: EINVAL, ESTATE, ECAPACITY (cap too small), ECUDA. */
+qgs_status qgs_copy_binning(qgs_ctx* ctx, uint64_t* keys, uint32_t* vals, int64_t cap,
+                            uint32_t* ranges, int32_t* rects, int64_t* n_instances);
+
+/* Copy the last forward's per-pixel residue to HOST memory: final transmittance and
+ * n_contrib (index + 1, within the pixel's tile list, of its last blended primitive). */
+qgs_status qgs_copy_residue(qgs_ctx* ctx, float* T_final, uint32_t* n_contrib);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QGS_H_ */

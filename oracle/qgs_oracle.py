@@ -79,7 +79,7 @@ class Binning:
     pix_bbox: np.ndarray    # float32 [N, 4] (xmin, xmax, ymin, ymax) in pixels
 
 
-def bin_fp32(scene, cam) -> Binning:
+def bin_fp32(scene, cam, emit: bool = True) -> Binning:
     """Conservative screen bound, tile rectangle and sort key of every primitive.
 
     FP32, correctly rounded + - * / sqrt only, each operation rounded separately in
@@ -194,6 +194,9 @@ def bin_fp32(scene, cam) -> Binning:
                          * (rect[:, 3] - rect[:, 2] + 1), 0)
         zbits = muc[2].astype(f).view(np.uint32).copy()
 
+    pix_bbox = np.stack([xmin, xmax, ymin, ymax], 1).astype(np.float32)
+    if not emit:
+        return Binning(vis, zbits, rect, count, None, None, None, TX, TY, pix_bbox)
     # instances in primitive order, tiles row-major inside each rectangle
     I = int(count.sum())
     keys = np.empty(I, np.uint64)
@@ -215,8 +218,17 @@ def bin_fp32(scene, cam) -> Binning:
     starts = np.searchsorted(tiles_sorted, np.arange(ntiles), side="left")
     ends = np.searchsorted(tiles_sorted, np.arange(ntiles), side="right")
     ranges = np.stack([starts, ends], 1).astype(np.int64)
-    pix_bbox = np.stack([xmin, xmax, ymin, ymax], 1).astype(np.float32)
     return Binning(vis, zbits, rect, count, keys, vals, ranges, TX, TY, pix_bbox)
+
+
+def tile_list(binning: Binning, tile: int) -> np.ndarray:
+    """Sorted primitive list of one tile, from the rectangles and depth keys alone
+    (the same order as the sorted 64-bit keys: depth bits, then primitive index)."""
+    ty, tx = divmod(int(tile), binning.tiles_x)
+    r = binning.rect
+    sel = np.nonzero((binning.count > 0) & (r[:, 0] <= tx) & (tx <= r[:, 1]) & (r[:, 2] <= ty) & (ty <= r[:, 3]))[0]
+    order = np.lexsort((sel, binning.zbits[sel]))
+    return sel[order].astype(np.uint32)
 
 
 # =========================================================================== FP64 geometry
@@ -396,6 +408,10 @@ def _eval_pairs(prm: Params, cam: CamF64, idx: torch.Tensor, px: torch.Tensor, p
         B0 = B_ + 2.0 * A_ * t0
         C0 = (A_ * t0 + B_) * t0 + C_
         m_D = D_.abs() / (B0 * B0 + 4.0 * (A_ * C0).abs()).clamp_min(1e-300)
+        # Conditioning of a hit's derivative: at a root, d f / d t = +-sqrt(D), so the
+        # derivative of the root (and everything downstream of it) scales like 1/sqrt(D);
+        # relative input perturbations e move it by about e * B^2 / D.
+        m_cond = m_D.clone()
         # The decision only matters where the double root t* = -B/(2A) lies on the
         # support (x^2/s_u^2 + y^2/s_v^2 <= 9, with slack); elsewhere both outcomes
         # contribute nothing.
@@ -454,7 +470,8 @@ def _eval_pairs(prm: Params, cam: CamF64, idx: torch.Tensor, px: torch.Tensor, p
 
     margin = torch.minimum(torch.minimum(m_D, m_near),
                            torch.minimum(m_sig, torch.minimum(m_amin, m_amax)))
-    return dict(alpha=alpha, valid=valid, hit=hit, t=t, rgb=rgb, normal=n_c, margin=margin)
+    cond = torch.where(valid, m_cond, torch.full_like(m_cond, np.inf))
+    return dict(alpha=alpha, valid=valid, hit=hit, t=t, rgb=rgb, normal=n_c, margin=margin, cond=cond)
 
 
 def _composite(prm, cam, idx, px, py, chunk=4096):
@@ -470,6 +487,8 @@ def _composite(prm, cam, idx, px, py, chunk=4096):
     n_eval = torch.zeros(P, dtype=torch.int64)
     n_contrib = torch.zeros(P, dtype=torch.int64)
     margin = torch.full((P,), np.inf, **dev)
+    cond = torch.full((P,), np.inf, **dev)
+    list_cond = None
     L = idx.shape[0]
     for c0 in range(0, L, chunk):
         sl = idx[c0:c0 + chunk]
@@ -494,6 +513,9 @@ def _composite(prm, cam, idx, px, py, chunk=4096):
         T = T * torch.where(keep, onem, torch.ones_like(onem)).prod(1)
         mm = torch.minimum(pe["margin"], m_T)
         margin = torch.minimum(margin, torch.where(seen, mm, torch.full_like(mm, np.inf)).min(1).values)
+        cond = torch.minimum(cond, torch.where(keep, pe["cond"], torch.full_like(mm, np.inf)).min(1).values)
+        lc = torch.where(keep, pe["cond"], torch.full_like(mm, np.inf)).min(0).values
+        list_cond = lc if list_cond is None else torch.cat([list_cond, lc])
         n_eval = n_eval + torch.where(alive, torch.where(has, k + 1, torch.full_like(k, Lc)),
                                       torch.zeros_like(k))
         last = torch.where(keep, ar.expand(P, Lc) + c0 + 1, torch.zeros_like(keep, dtype=torch.int64))
@@ -501,8 +523,11 @@ def _composite(prm, cam, idx, px, py, chunk=4096):
         alive = alive & ~has
         if not bool(alive.any()):
             break
+    if list_cond is None or list_cond.shape[0] < L:
+        pad = torch.full((L - (0 if list_cond is None else list_cond.shape[0]),), np.inf, **dev)
+        list_cond = pad if list_cond is None else torch.cat([list_cond, pad])
     return dict(rgb=rgb, alpha=1.0 - T, depth=depth, normal=normal, T_final=T,
-                n_eval=n_eval, n_contrib=n_contrib, margin=margin)
+                n_eval=n_eval, n_contrib=n_contrib, margin=margin, cond=cond, list_cond=list_cond)
 
 
 # =========================================================================== images
@@ -529,9 +554,9 @@ def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=N
     c64 = CamF64(cam)
     H, W = cam.H, cam.W
     out = dict(rgb=np.zeros((3, H, W)), alpha=np.zeros((H, W)), depth=np.zeros((H, W)),
-               normal=np.zeros((3, H, W)), margin=np.full((H, W), np.inf),
+               normal=np.zeros((3, H, W)), margin=np.full((H, W), np.inf), cond=np.full((H, W), np.inf),
                n_eval=np.zeros((H, W), np.int64), n_contrib=np.zeros((H, W), np.int64),
-               T_final=np.ones((H, W)))
+               T_final=np.ones((H, W)), prim_cond=np.full(scene.n, np.inf))
     TX = binning.tiles_x
     if tiles is None:
         tiles = range(binning.tiles_x * binning.tiles_y)
@@ -539,11 +564,15 @@ def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=N
     if want_grad:
         g = {k: torch.tensor(np.asarray(v, np.float64)) for k, v in grad_images.items()}
     for tile in tiles:
-        s, e = binning.ranges[tile]
+        if binning.ranges is not None:
+            s, e = binning.ranges[tile]
+            lst = binning.vals[s:e]
+        else:
+            lst = tile_list(binning, tile)
         xs, ys = _tile_pixels(cam, tile, TX)
-        if e <= s:
+        if lst.size == 0:
             continue
-        idx = torch.from_numpy(binning.vals[s:e].astype(np.int64))
+        idx = torch.from_numpy(lst.astype(np.int64))
         px = torch.tensor(xs, dtype=F64)
         py = torch.tensor(ys, dtype=F64)
         with torch.set_grad_enabled(want_grad):
@@ -559,6 +588,8 @@ def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=N
         out["depth"][ys, xs] = r["depth"].detach().numpy()
         out["normal"][:, ys, xs] = r["normal"].detach().numpy().T
         out["margin"][ys, xs] = r["margin"].numpy()
+        out["cond"][ys, xs] = r["cond"].numpy()
+        np.minimum.at(out["prim_cond"], idx.numpy(), r["list_cond"].numpy())
         out["n_eval"][ys, xs] = r["n_eval"].numpy()
         out["n_contrib"][ys, xs] = r["n_contrib"].numpy()
         out["T_final"][ys, xs] = r["T_final"].detach().numpy()
@@ -581,11 +612,18 @@ def render_pixels(scene, cam, pixels, binning: Binning | None = None):
     prm = Params(scene)
     c64 = CamF64(cam)
     TX = binning.tiles_x
-    res = {k: [] for k in ("rgb", "alpha", "depth", "normal", "margin", "n_eval", "n_contrib")}
+    res = {k: [] for k in ("rgb", "alpha", "depth", "normal", "margin", "cond", "n_eval", "n_contrib")}
+    lists = {}
     for (x, y) in pixels:
         tile = (y // TILE) * TX + (x // TILE)
-        s, e = binning.ranges[tile]
-        idx = torch.from_numpy(binning.vals[s:e].astype(np.int64))
+        if binning.ranges is not None:
+            s, e = binning.ranges[tile]
+            lst = binning.vals[s:e]
+        else:
+            if tile not in lists:
+                lists[tile] = tile_list(binning, tile)
+            lst = lists[tile]
+        idx = torch.from_numpy(lst.astype(np.int64))
         with torch.no_grad():
             r = _composite(prm, c64, idx, torch.tensor([float(x)], dtype=F64),
                            torch.tensor([float(y)], dtype=F64))

@@ -1,0 +1,615 @@
+// C ABI of libqgs: rendering context, tile binning and the forward/backward pipelines.
+//
+// Forward pipeline on the caller's stream (supplementary, per-tile sorting; Sec. 3.1-3.2):
+//   k_preprocess            per primitive: projected state, tile rectangle, depth key
+//   depth sort              radix sort of the visible primitives by depth (u32 keys)
+//   count gather + scan     instance offsets in depth order
+//   (one host read of the instance total, to size the instance buffers)
+//   k_emit_sorted           (tile << 32 | primitive) per covered tile, in depth order
+//   tile sort               stable radix sort of the instances on the tile bits only
+//   k_tile_ranges           [start, end) of every tile's list
+//   k_raster_fwd            per-tile compositing
+// Because the instances are emitted in depth order and the tile sort is stable, the
+// final order equals the order of the 64-bit keys (tile << 32 | depth bits) with ties
+// broken by primitive index. sort_mode 1 instead emits the 64-bit keys in primitive
+// order and radix-sorts all of their significant bits.
+#include <cstdio>
+#include <cstring>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "qgs_internal.cuh"
+
+using namespace qgs;
+
+namespace {
+
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t cap = 0;
+  cudaError_t reserve(size_t n) {
+    if (n <= cap) return cudaSuccess;
+    size_t want = n + n / 4 + 64;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc((void**)&p, want * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    cap = want;
+    return cudaSuccess;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+__global__ void k_gather_u32(int64_t n, const uint32_t* __restrict__ idx, const uint32_t* __restrict__ src,
+                             uint32_t* __restrict__ dst) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[idx[i]];
+}
+
+// Write the tile instances of 32 consecutive primitives per warp (coalesced).
+// sidx == nullptr: primitive order (full-key mode, keys carry the depth bits, values the
+// primitive); otherwise depth order (keys carry the primitive in their low half).
+__global__ void k_emit(int64_t n, const uint32_t* __restrict__ sidx, const uint32_t* __restrict__ count,
+                       const short4* __restrict__ rect, const uint32_t* __restrict__ offs,
+                       const uint32_t* __restrict__ zkey, int tiles_x, uint64_t* __restrict__ keys,
+                       uint32_t* __restrict__ vals) {
+  const int lane = threadIdx.x & 31;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t pid = 0, c = 0, off = 0, lowv = 0;
+  short4 r = make_short4(0, 0, 0, 0);
+  if (j < n) {
+    pid = sidx ? sidx[j] : (uint32_t)j;
+    c = count[pid];
+    if (c) {
+      off = offs[j];
+      r = rect[pid];
+      lowv = sidx ? pid : zkey[pid];
+    }
+  }
+  for (int k = 0; k < 32; ++k) {
+    const uint32_t cc = __shfl_sync(0xffffffffu, c, k);
+    if (!cc) continue;
+    const uint32_t pp = __shfl_sync(0xffffffffu, pid, k);
+    const uint32_t oo = __shfl_sync(0xffffffffu, off, k);
+    const uint32_t lv = __shfl_sync(0xffffffffu, lowv, k);
+    const int rx0 = __shfl_sync(0xffffffffu, (int)r.x, k);
+    const int rx1 = __shfl_sync(0xffffffffu, (int)r.y, k);
+    const int ry0 = __shfl_sync(0xffffffffu, (int)r.z, k);
+    const uint32_t w = (uint32_t)(rx1 - rx0 + 1);
+    for (uint32_t e = lane; e < cc; e += 32) {
+      const uint32_t dy = e / w, dx = e - dy * w;
+      const uint32_t tile = (uint32_t)(ry0 + (int)dy) * (uint32_t)tiles_x + (uint32_t)(rx0 + (int)dx);
+      keys[(size_t)oo + e] = ((uint64_t)tile << 32) | lv;
+      if (vals) vals[(size_t)oo + e] = pp;
+    }
+  }
+}
+
+__global__ void k_tile_ranges(int64_t n, const uint64_t* __restrict__ keys, uint2* __restrict__ ranges) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t t = (uint32_t)(keys[i] >> 32);
+  if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[t].x = (uint32_t)i;
+  if (i == n - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[t].y = (uint32_t)(i + 1);
+}
+
+__global__ void k_debug_keys(int64_t n, const uint64_t* __restrict__ inst, const PrimState* __restrict__ state,
+                             uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t v = inst[i];
+  const uint32_t pid = (uint32_t)v;
+  keys[i] = (v & 0xFFFFFFFF00000000ull) | __float_as_uint(state[pid].f[2].w);
+  vals[i] = pid;
+}
+
+inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+struct qgs_ctx {
+  int device = 0;
+  qgs_config cfg{};
+  std::string err;
+  // per-primitive
+  DevBuf<PrimState> state;
+  DevBuf<uint32_t> count, zkey, idx, zkey2, idx2, cnt_sorted, offs;
+  DevBuf<short4> rect;
+  // per-instance
+  DevBuf<uint64_t> inst, inst2;
+  DevBuf<uint32_t> vals, vals2;
+  // per-tile / per-pixel
+  DevBuf<uint2> ranges;
+  DevBuf<float> T_final;
+  DevBuf<uint32_t> n_contrib;
+  // backward
+  DevBuf<float> pgrad;
+  // scratch
+  DevBuf<uint32_t> hist, scan_tmp;
+  DevBuf<RasterStats> stats;
+  DevBuf<uint32_t> dcount;      // [0] visible primitives of the current frame
+  uint32_t* h_total = nullptr;  // pinned: instance total, visible count
+  int64_t n_visible = 0;
+  const uint32_t* vis_list = nullptr;
+  // last frame
+  bool have_frame = false;
+  int64_t n = 0, n_inst = 0;
+  int W = 0, H = 0, tiles_x = 0, tiles_y = 0;
+  const float* scene_mean = nullptr;
+  const uint32_t* ids = nullptr;  // sorted primitive ids of the last frame
+  int id_stride = 1;
+  const uint64_t* sorted_keys = nullptr;
+  cudaStream_t last_stream = nullptr;
+  bool bwd_attr_set = false;
+  // profiling: events at stage boundaries (forward 0..6, backward 7..9)
+  bool profiling = false;
+  bool have_fwd_times = false, have_bwd_times = false;
+  cudaEvent_t ev[10] = {};
+  int64_t launches_fwd = 0, launches_bwd = 0;
+  CamParams cp{};
+  RasterParams rp{};
+};
+
+namespace {
+
+qgs_status fail(qgs_ctx* c, qgs_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+qgs_status cuda_fail(qgs_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, e == cudaErrorMemoryAllocation ? QGS_ENOMEM : QGS_ECUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define QGS_CU(call, where)                          \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+  } while (0)
+
+bool finite_cam(const qgs_camera* c) {
+  bool ok = std::isfinite(c->fx) && std::isfinite(c->fy) && std::isfinite(c->cx) && std::isfinite(c->cy) &&
+            std::isfinite(c->near_plane) && c->fx > 0 && c->fy > 0 && c->near_plane > 0;
+  for (int i = 0; i < 9; ++i) ok = ok && std::isfinite(c->R_cw[i]);
+  for (int i = 0; i < 3; ++i) ok = ok && std::isfinite(c->t_cw[i]);
+  return ok;
+}
+
+qgs_status check_scene(qgs_ctx* ctx, const qgs_scene* s) {
+  if (!s) return fail(ctx, QGS_EINVAL, "scene is NULL");
+  if (s->n < 0 || s->n > (int64_t)0x7FFFFFFF) return fail(ctx, QGS_EINVAL, "scene n out of range [0, 2^31)");
+  if (s->n > 0 && (!s->mean || !s->quat || !s->scale || !s->curv || !s->opacity || !s->sh))
+    return fail(ctx, QGS_EINVAL, "scene has a NULL parameter pointer");
+  if (s->n > 0 && ((((uintptr_t)s->quat) & 15) || (((uintptr_t)s->sh) & 15) || (((uintptr_t)s->scale) & 7) ||
+                   (((uintptr_t)s->curv) & 7)))
+    return fail(ctx, QGS_EINVAL, "quat/sh must be 16-byte aligned, scale/curv 8-byte aligned");
+  return QGS_OK;
+}
+
+void make_params(const qgs_ctx* ctx, const qgs_camera* cam, CamParams& cp, RasterParams& rp) {
+  for (int i = 0; i < 9; ++i) cp.Rc[i] = cam->R_cw[i];
+  for (int i = 0; i < 3; ++i) cp.tc[i] = cam->t_cw[i];
+  for (int i = 0; i < 3; ++i) {
+    double s = 0;
+    for (int k = 0; k < 3; ++k) s -= (double)cam->R_cw[3 * k + i] * cam->t_cw[k];
+    cp.cw[i] = (float)s;
+  }
+  cp.fx = cam->fx; cp.fy = cam->fy; cp.cx = cam->cx; cp.cy = cam->cy; cp.near = cam->near_plane;
+  cp.W = cam->W; cp.H = cam->H;
+  cp.tiles_x = (cam->W + TILE - 1) / TILE;
+  cp.tiles_y = (cam->H + TILE - 1) / TILE;
+  rp.W = cam->W; rp.H = cam->H; rp.tiles_x = cp.tiles_x; rp.tiles_y = cp.tiles_y;
+  rp.cx = cam->cx; rp.cy = cam->cy;
+  rp.inv_fx = 1.f / cam->fx; rp.inv_fy = 1.f / cam->fy;
+  rp.near_plane = cam->near_plane;
+  rp.alpha_max = ctx->cfg.alpha_max; rp.alpha_min = ctx->cfg.alpha_min;
+  rp.T_min = ctx->cfg.T_min; rp.grazing_eps = ctx->cfg.grazing_eps;
+}
+
+inline void mark(qgs_ctx* c, int i, cudaStream_t st) {
+  if (c->profiling) cudaEventRecord(c->ev[i], st);
+}
+
+int bits_for(int64_t v) {
+  int b = 1;
+  while (b < 62 && ((int64_t)1 << b) < v) ++b;
+  return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+void qgs_config_default(qgs_config* cfg) {
+  if (!cfg) return;
+  cfg->alpha_max = 0.99f;
+  cfg->alpha_min = 1.0f / 255.0f;
+  cfg->T_min = 1e-4f;
+  cfg->grazing_eps = 1e-5f;
+  cfg->sort_mode = 0;
+  cfg->reserved = 0;
+}
+
+qgs_status qgs_create(qgs_ctx** out, const qgs_config* cfg, int32_t device) {
+  if (!out) return QGS_EINVAL;
+  *out = nullptr;
+  qgs_ctx* c = new (std::nothrow) qgs_ctx();
+  if (!c) return QGS_ENOMEM;
+  qgs_config_default(&c->cfg);
+  if (cfg) {
+    if (!(cfg->alpha_max > 0 && cfg->alpha_max < 1 && cfg->alpha_min >= 0 && cfg->alpha_min < cfg->alpha_max &&
+          cfg->T_min > 0 && cfg->T_min < 1 && cfg->grazing_eps >= 0 && (cfg->sort_mode == 0 || cfg->sort_mode == 1))) {
+      delete c;
+      return QGS_EINVAL;
+    }
+    c->cfg = *cfg;
+  }
+  c->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete c;
+    return QGS_ECUDA;
+  }
+  if (cudaHostAlloc((void**)&c->h_total, 16, cudaHostAllocDefault) != cudaSuccess) {
+    delete c;
+    return QGS_ENOMEM;
+  }
+  if (c->stats.reserve(1) != cudaSuccess || c->dcount.reserve(4) != cudaSuccess) {
+    cudaFreeHost(c->h_total);
+    delete c;
+    return QGS_ENOMEM;
+  }
+  *out = c;
+  return QGS_OK;
+}
+
+void qgs_destroy(qgs_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  c->state.release(); c->count.release(); c->zkey.release(); c->idx.release(); c->zkey2.release();
+  c->idx2.release(); c->cnt_sorted.release(); c->offs.release(); c->rect.release(); c->inst.release();
+  c->inst2.release(); c->vals.release(); c->vals2.release(); c->ranges.release(); c->T_final.release();
+  c->n_contrib.release(); c->pgrad.release(); c->hist.release(); c->scan_tmp.release(); c->stats.release();
+  c->dcount.release();
+  if (c->h_total) cudaFreeHost(c->h_total);
+  for (int i = 0; i < 10; ++i)
+    if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  delete c;
+}
+
+const char* qgs_last_error(const qgs_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera* cam, const qgs_image* out,
+                          qgs_stream stream) {
+  if (!ctx) return QGS_EINVAL;
+  ctx->err.clear();
+  qgs_status s = check_scene(ctx, scene);
+  if (s != QGS_OK) return s;
+  if (!cam || !out) return fail(ctx, QGS_EINVAL, "camera/output is NULL");
+  if (cam->W <= 0 || cam->H <= 0 || cam->W > 32768 || cam->H > 32768)
+    return fail(ctx, QGS_EINVAL, "image size must be in [1, 32768]");
+  if (!finite_cam(cam)) return fail(ctx, QGS_EINVAL, "camera has non-finite or non-positive intrinsics");
+  if (!out->rgb || !out->alpha || !out->depth || !out->normal) return fail(ctx, QGS_EINVAL, "output plane is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  QGS_CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+  ctx->have_frame = false;
+  const int64_t N = scene->n;
+  CamParams cp;
+  RasterParams rp;
+  make_params(ctx, cam, cp, rp);
+  const int64_t ntiles = (int64_t)cp.tiles_x * cp.tiles_y;
+  const int64_t P = (int64_t)cam->W * cam->H;
+  const int sm = ctx->cfg.sort_mode;
+
+  const size_t n1 = (size_t)(N > 0 ? N : 1);
+  QGS_CU(ctx->state.reserve(n1), "alloc state");
+  QGS_CU(ctx->count.reserve(n1), "alloc count");
+  QGS_CU(ctx->zkey.reserve(n1), "alloc zkey");
+  QGS_CU(ctx->idx.reserve(n1), "alloc idx");
+  QGS_CU(ctx->zkey2.reserve(n1), "alloc zkey2");
+  QGS_CU(ctx->idx2.reserve(n1), "alloc idx2");
+  QGS_CU(ctx->cnt_sorted.reserve(n1), "alloc cnt");
+  QGS_CU(ctx->offs.reserve(n1 + 1), "alloc offs");
+  QGS_CU(ctx->rect.reserve(n1), "alloc rect");
+  QGS_CU(ctx->ranges.reserve((size_t)ntiles), "alloc ranges");
+  QGS_CU(ctx->T_final.reserve((size_t)P), "alloc T_final");
+  QGS_CU(ctx->n_contrib.reserve((size_t)P), "alloc n_contrib");
+  QGS_CU(ctx->hist.reserve(radix_hist_elems((int64_t)n1)), "alloc hist");
+  QGS_CU(ctx->scan_tmp.reserve(scan_tmp_elems((int64_t)radix_hist_elems((int64_t)n1) + (int64_t)n1)), "alloc scan");
+  SortTemp tmp;
+  tmp.hist = ctx->hist.p;
+  tmp.hist_cap = ctx->hist.cap;
+  tmp.scan_tmp = ctx->scan_tmp.p;
+  tmp.scan_cap = ctx->scan_tmp.cap;
+
+  const int64_t launches0 = launch_counter();
+  ctx->have_fwd_times = false;
+  QGS_CU(cudaMemsetAsync(ctx->dcount.p, 0, sizeof(uint32_t) * 4, st), "memset counters");
+  mark(ctx, 0, st);
+  SceneView sv{scene->mean, scene->quat, scene->scale, scene->curv, scene->opacity, scene->sh};
+  if (N > 0) {
+    k_preprocess<<<nblk(N), 256, 0, st>>>(N, sv, cp, ctx->state.p, ctx->count.p, ctx->zkey.p, ctx->idx.p,
+                                          ctx->rect.p, ctx->dcount.p);
+    ++launch_counter();
+    QGS_CU(cudaGetLastError(), "k_preprocess");
+  }
+  mark(ctx, 1, st);
+  const uint32_t* sidx = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (sm == 0) {
+    const bool fl = radix_sort_u32_pairs(ctx->zkey.p, ctx->idx.p, ctx->zkey2.p, ctx->idx2.p, N, 0, 32, tmp, st, &e);
+    QGS_CU(e, "depth sort");
+    sidx = fl ? ctx->idx2.p : ctx->idx.p;
+    if (N > 0) {
+      k_gather_u32<<<nblk(N), 256, 0, st>>>(N, sidx, ctx->count.p, ctx->cnt_sorted.p);
+      ++launch_counter();
+      QGS_CU(cudaGetLastError(), "gather");
+    }
+    QGS_CU(scan_exclusive_u32(ctx->cnt_sorted.p, ctx->offs.p, N, ctx->scan_tmp.p, ctx->scan_tmp.cap, st), "scan");
+  } else {
+    QGS_CU(scan_exclusive_u32(ctx->count.p, ctx->offs.p, N, ctx->scan_tmp.p, ctx->scan_tmp.cap, st), "scan");
+  }
+  mark(ctx, 2, st);
+  QGS_CU(cudaMemcpyAsync(ctx->h_total, ctx->offs.p + N, sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "total");
+  QGS_CU(cudaMemcpyAsync(ctx->h_total + 1, ctx->dcount.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "visible");
+  QGS_CU(cudaStreamSynchronize(st), "sync");
+  const int64_t I = (int64_t)ctx->h_total[0];
+  ctx->n_visible = (int64_t)ctx->h_total[1];
+  ctx->vis_list = sm == 0 ? sidx : nullptr;  // depth order puts the visible primitives first
+
+  const size_t i1 = (size_t)(I > 0 ? I : 1);
+  QGS_CU(ctx->inst.reserve(i1), "alloc inst");
+  QGS_CU(ctx->inst2.reserve(i1), "alloc inst2");
+  if (sm == 1) {
+    QGS_CU(ctx->vals.reserve(i1), "alloc vals");
+    QGS_CU(ctx->vals2.reserve(i1), "alloc vals2");
+  }
+  QGS_CU(ctx->hist.reserve(radix_hist_elems((int64_t)i1)), "alloc hist");
+  QGS_CU(ctx->scan_tmp.reserve(scan_tmp_elems((int64_t)radix_hist_elems((int64_t)i1))), "alloc scan");
+  tmp.hist = ctx->hist.p;
+  tmp.hist_cap = ctx->hist.cap;
+  tmp.scan_tmp = ctx->scan_tmp.p;
+  tmp.scan_cap = ctx->scan_tmp.cap;
+
+  const int tb = bits_for(ntiles);
+  const uint64_t* sorted = nullptr;
+  mark(ctx, 3, st);
+  if (N > 0 && I > 0) {
+    if (sm == 0) {
+      k_emit<<<nblk(N), 256, 0, st>>>(N, sidx, ctx->count.p, ctx->rect.p, ctx->offs.p, nullptr, cp.tiles_x,
+                                      ctx->inst.p, nullptr);
+      ++launch_counter();
+      QGS_CU(cudaGetLastError(), "emit");
+      mark(ctx, 4, st);
+      const bool fl = radix_sort_u64_keys(ctx->inst.p, ctx->inst2.p, I, 32, 32 + tb, tmp, st, &e);
+      QGS_CU(e, "tile sort");
+      sorted = fl ? ctx->inst2.p : ctx->inst.p;
+      ctx->ids = reinterpret_cast<const uint32_t*>(sorted);
+      ctx->id_stride = 2;
+    } else {
+      k_emit<<<nblk(N), 256, 0, st>>>(N, nullptr, ctx->count.p, ctx->rect.p, ctx->offs.p, ctx->zkey.p, cp.tiles_x,
+                                      ctx->inst.p, ctx->vals.p);
+      ++launch_counter();
+      QGS_CU(cudaGetLastError(), "emit");
+      mark(ctx, 4, st);
+      const bool fl =
+          radix_sort_u64_pairs(ctx->inst.p, ctx->vals.p, ctx->inst2.p, ctx->vals2.p, I, 0, 32 + tb, tmp, st, &e);
+      QGS_CU(e, "key sort");
+      sorted = fl ? ctx->inst2.p : ctx->inst.p;
+      ctx->ids = fl ? ctx->vals2.p : ctx->vals.p;
+      ctx->id_stride = 1;
+    }
+  } else {
+    ctx->ids = reinterpret_cast<const uint32_t*>(ctx->inst.p);
+    ctx->id_stride = sm == 0 ? 2 : 1;
+    if (sm == 1) ctx->ids = ctx->vals.p;
+    mark(ctx, 4, st);
+  }
+  ctx->sorted_keys = sorted;
+  QGS_CU(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(uint2) * (size_t)ntiles, st), "memset ranges");
+  if (I > 0) {
+    k_tile_ranges<<<nblk(I), 256, 0, st>>>(I, sorted, ctx->ranges.p);
+    ++launch_counter();
+    QGS_CU(cudaGetLastError(), "ranges");
+  }
+  QGS_CU(cudaMemsetAsync(ctx->stats.p, 0, sizeof(RasterStats), st), "memset stats");
+  mark(ctx, 5, st);
+  k_raster_fwd<<<(unsigned)ntiles, BLOCK, 0, st>>>(ctx->ranges.p, ctx->ids, ctx->id_stride, ctx->state.p, rp,
+                                                   out->rgb, out->alpha, out->depth, out->normal, ctx->T_final.p,
+                                                   ctx->n_contrib.p, ctx->stats.p);
+  ++launch_counter();
+  QGS_CU(cudaGetLastError(), "k_raster_fwd");
+  mark(ctx, 6, st);
+  ctx->have_fwd_times = ctx->profiling;
+  ctx->have_bwd_times = false;
+  ctx->launches_fwd = launch_counter() - launches0;
+  ctx->launches_bwd = 0;
+  ctx->have_frame = true;
+  ctx->n = N;
+  ctx->n_inst = I;
+  ctx->W = cam->W;
+  ctx->H = cam->H;
+  ctx->tiles_x = cp.tiles_x;
+  ctx->tiles_y = cp.tiles_y;
+  ctx->scene_mean = scene->mean;
+  ctx->last_stream = st;
+  ctx->cp = cp;
+  ctx->rp = rp;
+  return QGS_OK;
+}
+
+qgs_status render_backward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera* cam, const qgs_image* grad_out,
+                           const qgs_scene_grad* grad, qgs_stream stream) {
+  if (!ctx) return QGS_EINVAL;
+  ctx->err.clear();
+  qgs_status s = check_scene(ctx, scene);
+  if (s != QGS_OK) return s;
+  if (!cam || !grad_out || !grad) return fail(ctx, QGS_EINVAL, "camera/grad_out/grad is NULL");
+  if (!ctx->have_frame) return fail(ctx, QGS_ESTATE, "render_backward without a preceding render_forward");
+  if (scene->n != ctx->n || scene->mean != ctx->scene_mean || cam->W != ctx->W || cam->H != ctx->H)
+    return fail(ctx, QGS_ESTATE, "render_backward scene/camera differ from the last render_forward");
+  if (scene->n > 0 && (!grad->mean || !grad->quat || !grad->scale || !grad->curv || !grad->opacity || !grad->sh))
+    return fail(ctx, QGS_EINVAL, "gradient buffer is NULL");
+  if (scene->n > 0 && ((((uintptr_t)grad->quat) & 15) || (((uintptr_t)grad->sh) & 15) ||
+                       (((uintptr_t)grad->scale) & 7) || (((uintptr_t)grad->curv) & 7)))
+    return fail(ctx, QGS_EINVAL, "grad quat/sh must be 16-byte aligned, scale/curv 8-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  QGS_CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+  const int64_t N = scene->n;
+  if (N == 0) return QGS_OK;
+  CamParams cp;
+  RasterParams rp;
+  make_params(ctx, cam, cp, rp);
+  QGS_CU(ctx->pgrad.reserve((size_t)N * NGRAD_PAD), "alloc pgrad");
+  QGS_CU(cudaMemsetAsync(ctx->pgrad.p, 0, sizeof(float) * (size_t)N * NGRAD_PAD, st), "memset pgrad");
+  const int64_t ntiles = (int64_t)cp.tiles_x * cp.tiles_y;
+  const int64_t launches0 = launch_counter();
+  if (!ctx->bwd_attr_set) {
+    QGS_CU(cudaFuncSetAttribute(k_raster_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RASTER_BWD_SMEM),
+           "smem attribute");
+    ctx->bwd_attr_set = true;
+  }
+  mark(ctx, 7, st);
+  k_raster_bwd<<<(unsigned)ntiles, BLOCK, RASTER_BWD_SMEM, st>>>(ctx->ranges.p, ctx->ids, ctx->id_stride,
+                                                                 ctx->state.p, rp, grad_out->rgb, grad_out->alpha,
+                                                                 grad_out->depth, grad_out->normal, ctx->T_final.p,
+                                                                 ctx->n_contrib.p, ctx->pgrad.p, ctx->stats.p);
+  ++launch_counter();
+  QGS_CU(cudaGetLastError(), "k_raster_bwd");
+  mark(ctx, 8, st);
+  SceneView sv{scene->mean, scene->quat, scene->scale, scene->curv, scene->opacity, scene->sh};
+  GradView gv{grad->mean, grad->quat, grad->scale, grad->curv, grad->opacity, grad->sh};
+  const int64_t nb = ctx->vis_list ? ctx->n_visible : N;
+  if (nb > 0) k_preprocess_bwd<<<nblk(nb), 256, 0, st>>>(nb, ctx->vis_list, sv, cp, ctx->count.p, ctx->pgrad.p, gv);
+  ++launch_counter();
+  QGS_CU(cudaGetLastError(), "k_preprocess_bwd");
+  mark(ctx, 9, st);
+  ctx->have_bwd_times = ctx->profiling;
+  ctx->launches_bwd = launch_counter() - launches0;
+  ctx->last_stream = st;
+  return QGS_OK;
+}
+
+qgs_status qgs_get_frame_stats(qgs_ctx* ctx, qgs_frame_stats* out) {
+  if (!ctx || !out) return QGS_EINVAL;
+  if (!ctx->have_frame) return fail(ctx, QGS_ESTATE, "no frame rendered yet");
+  QGS_CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+  QGS_CU(cudaStreamSynchronize(ctx->last_stream), "sync");
+  RasterStats rs;
+  QGS_CU(cudaMemcpy(&rs, ctx->stats.p, sizeof(rs), cudaMemcpyDeviceToHost), "stats");
+  int64_t vis = 0;
+  if (ctx->n > 0) {
+    std::vector<uint32_t> cnt((size_t)ctx->n);
+    QGS_CU(cudaMemcpy(cnt.data(), ctx->count.p, sizeof(uint32_t) * (size_t)ctx->n, cudaMemcpyDeviceToHost), "count");
+    for (uint32_t c : cnt) vis += c > 0;
+  }
+  out->n_primitives = ctx->n;
+  out->n_visible = vis;
+  out->n_instances = ctx->n_inst;
+  out->n_tiles = (int64_t)ctx->tiles_x * ctx->tiles_y;
+  out->pair_evals = (int64_t)rs.pair_evals;
+  out->pair_isect = (int64_t)rs.pair_isect;
+  out->pair_hits = (int64_t)rs.pair_hits;
+  out->pair_blended = (int64_t)rs.pair_blended;
+  out->grazing_resolves = (int64_t)rs.grazing;
+  out->bwd_pairs = (int64_t)rs.bwd_pairs;
+  out->bwd_contrib = (int64_t)rs.bwd_contrib;
+  out->launches_fwd = ctx->launches_fwd;
+  out->launches_bwd = ctx->launches_bwd;
+  auto el = [&](int a, int b) {
+    float ms = -1.f;
+    if (cudaEventElapsedTime(&ms, ctx->ev[a], ctx->ev[b]) != cudaSuccess) ms = -1.f;
+    return ms;
+  };
+  out->ms_preprocess = ctx->have_fwd_times ? el(0, 1) : -1.f;
+  out->ms_depth_sort = ctx->have_fwd_times ? el(1, 2) : -1.f;
+  out->ms_emit = ctx->have_fwd_times ? el(3, 4) : -1.f;
+  out->ms_tile_sort = ctx->have_fwd_times ? el(4, 5) : -1.f;
+  out->ms_raster_fwd = ctx->have_fwd_times ? el(5, 6) : -1.f;
+  out->ms_raster_bwd = ctx->have_bwd_times ? el(7, 8) : -1.f;
+  out->ms_preprocess_bwd = ctx->have_bwd_times ? el(8, 9) : -1.f;
+  return QGS_OK;
+}
+
+qgs_status qgs_set_profiling(qgs_ctx* ctx, int32_t enable) {
+  if (!ctx) return QGS_EINVAL;
+  QGS_CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (enable && !ctx->ev[0]) {
+    for (int i = 0; i < 10; ++i) QGS_CU(cudaEventCreate(&ctx->ev[i]), "cudaEventCreate");
+  }
+  ctx->profiling = enable != 0;
+  return QGS_OK;
+}
+
+qgs_status qgs_copy_binning(qgs_ctx* ctx, uint64_t* keys, uint32_t* vals, int64_t cap, uint32_t* ranges,
+                            int32_t* rects, int64_t* n_instances) {
+  if (!ctx) return QGS_EINVAL;
+  if (!ctx->have_frame) return fail(ctx, QGS_ESTATE, "no frame rendered yet");
+  QGS_CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+  QGS_CU(cudaStreamSynchronize(ctx->last_stream), "sync");
+  const int64_t I = ctx->n_inst;
+  if (n_instances) *n_instances = I;
+  if ((keys || vals) && cap < I) return fail(ctx, QGS_ECAPACITY, "key/value capacity smaller than the instance count");
+  if ((keys || vals) && I > 0) {
+    DevBuf<uint64_t> dk;
+    DevBuf<uint32_t> dv;
+    QGS_CU(dk.reserve((size_t)I), "alloc");
+    if (dv.reserve((size_t)I) != cudaSuccess) {
+      dk.release();
+      return fail(ctx, QGS_ENOMEM, "alloc");
+    }
+    if (ctx->cfg.sort_mode == 0) {
+      k_debug_keys<<<nblk(I), 256>>>(I, ctx->sorted_keys, ctx->state.p, dk.p, dv.p);
+    } else {
+      cudaMemcpy(dk.p, ctx->sorted_keys, sizeof(uint64_t) * (size_t)I, cudaMemcpyDeviceToDevice);
+      cudaMemcpy(dv.p, ctx->ids, sizeof(uint32_t) * (size_t)I, cudaMemcpyDeviceToDevice);
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && keys) e = cudaMemcpy(keys, dk.p, sizeof(uint64_t) * (size_t)I, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && vals) e = cudaMemcpy(vals, dv.p, sizeof(uint32_t) * (size_t)I, cudaMemcpyDeviceToHost);
+    dk.release();
+    dv.release();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy keys");
+  }
+  if (ranges) {
+    QGS_CU(cudaMemcpy(ranges, ctx->ranges.p, sizeof(uint2) * (size_t)ctx->tiles_x * ctx->tiles_y,
+                      cudaMemcpyDeviceToHost),
+           "copy ranges");
+  }
+  if (rects && ctx->n > 0) {
+    std::vector<short4> r((size_t)ctx->n);
+    QGS_CU(cudaMemcpy(r.data(), ctx->rect.p, sizeof(short4) * (size_t)ctx->n, cudaMemcpyDeviceToHost), "copy rects");
+    for (int64_t i = 0; i < ctx->n; ++i) {
+      rects[4 * i] = r[i].x;
+      rects[4 * i + 1] = r[i].y;
+      rects[4 * i + 2] = r[i].z;
+      rects[4 * i + 3] = r[i].w;
+    }
+  }
+  return QGS_OK;
+}
+
+qgs_status qgs_copy_residue(qgs_ctx* ctx, float* T_final, uint32_t* n_contrib) {
+  if (!ctx) return QGS_EINVAL;
+  if (!ctx->have_frame) return fail(ctx, QGS_ESTATE, "no frame rendered yet");
+  QGS_CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+  QGS_CU(cudaStreamSynchronize(ctx->last_stream), "sync");
+  const size_t P = (size_t)ctx->W * ctx->H;
+  if (T_final) QGS_CU(cudaMemcpy(T_final, ctx->T_final.p, sizeof(float) * P, cudaMemcpyDeviceToHost), "copy T");
+  if (n_contrib)
+    QGS_CU(cudaMemcpy(n_contrib, ctx->n_contrib.p, sizeof(uint32_t) * P, cudaMemcpyDeviceToHost), "copy n");
+  return QGS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,403 @@
+// Per-primitive preprocessing (forward and backward) of the quadric rasterizer.
+//
+// Forward (one thread per primitive):
+//   - camera-space centre, rotation R from the normalised quaternion and the
+//     camera-from-local rotation W = R_cw R (the congruent transform of Sec. 3.2);
+//   - the conservative screen bound of the curved patch and its 16x16 tile rectangle
+//     (supplementary, "Details of Bounding Box Calculation": the loose box, with a
+//     provable z clamp, clipped to the near plane), and the 32-bit depth key
+//     (supplementary, per-tile sorting);
+//   - degree-3 SH colour (Sec. 3.1) from bfloat16 coefficients, evaluated in FP32;
+//   - the 128-byte projected-state record read by the compositing kernels.
+// The centre depth, the box and the tile rectangle are computed with correctly
+// rounded FP32 operations only (__fmul_rn, __fadd_rn, __fdiv_rn, __fsqrt_rn), each in
+// a fixed order, so that the tile lists and keys are reproducible bit for bit by an
+// independent implementation of the same recipe.
+//
+// Backward (one thread per primitive): chain rule from the per-primitive gradient
+// record accumulated by the compositing backward to mean, quaternion, scales,
+// curvatures, opacity and SH coefficients.
+#include "qgs_internal.cuh"
+
+namespace qgs {
+
+namespace {
+
+__device__ __forceinline__ float bf16_to_f32(uint16_t b) {
+  return __uint_as_float(((uint32_t)b) << 16);
+}
+
+// Real SH normalisation constants (degree <= 3) in the 3DGS sign convention.
+__device__ __constant__ float kSH0 = 0.28209479177387814f;
+__device__ __constant__ float kSH1 = 0.4886025119029199f;
+__device__ __constant__ float kSH2[5] = {1.0925484305920792f, -1.0925484305920792f, 0.31539156525252005f,
+                                        -1.0925484305920792f, 0.5462742152960396f};
+__device__ __constant__ float kSH3[7] = {-0.5900435899266435f, 2.890611442640554f, -0.4570457994644658f,
+                                        0.3731763325901154f, -0.4570457994644658f, 1.445305721320277f,
+                                        -0.5900435899266435f};
+
+__device__ __forceinline__ void sh_basis16(float x, float y, float z, float Y[16]) {
+  float xx = x * x, yy = y * y, zz = z * z;
+  Y[0] = kSH0;
+  Y[1] = -kSH1 * y;
+  Y[2] = kSH1 * z;
+  Y[3] = -kSH1 * x;
+  Y[4] = kSH2[0] * x * y;
+  Y[5] = kSH2[1] * y * z;
+  Y[6] = kSH2[2] * (2.f * zz - xx - yy);
+  Y[7] = kSH2[3] * x * z;
+  Y[8] = kSH2[4] * (xx - yy);
+  Y[9] = kSH3[0] * y * (3.f * xx - yy);
+  Y[10] = kSH3[1] * x * y * z;
+  Y[11] = kSH3[2] * y * (4.f * zz - xx - yy);
+  Y[12] = kSH3[3] * z * (2.f * zz - 3.f * xx - 3.f * yy);
+  Y[13] = kSH3[4] * x * (4.f * zz - xx - yy);
+  Y[14] = kSH3[5] * z * (xx - yy);
+  Y[15] = kSH3[6] * x * (xx - 3.f * yy);
+}
+
+// Gradient of each basis function with respect to the (unnormalised-use) direction
+// components, written out from the polynomials above.
+__device__ __forceinline__ void sh_basis16_grad(float x, float y, float z, float gx[16], float gy[16],
+                                                float gz[16]) {
+  float xx = x * x, yy = y * y, zz = z * z;
+  gx[0] = gy[0] = gz[0] = 0.f;
+  gx[1] = 0.f; gy[1] = -kSH1; gz[1] = 0.f;
+  gx[2] = 0.f; gy[2] = 0.f; gz[2] = kSH1;
+  gx[3] = -kSH1; gy[3] = 0.f; gz[3] = 0.f;
+  gx[4] = kSH2[0] * y; gy[4] = kSH2[0] * x; gz[4] = 0.f;
+  gx[5] = 0.f; gy[5] = kSH2[1] * z; gz[5] = kSH2[1] * y;
+  gx[6] = -2.f * kSH2[2] * x; gy[6] = -2.f * kSH2[2] * y; gz[6] = 4.f * kSH2[2] * z;
+  gx[7] = kSH2[3] * z; gy[7] = 0.f; gz[7] = kSH2[3] * x;
+  gx[8] = 2.f * kSH2[4] * x; gy[8] = -2.f * kSH2[4] * y; gz[8] = 0.f;
+  gx[9] = 6.f * kSH3[0] * x * y; gy[9] = kSH3[0] * (3.f * xx - 3.f * yy); gz[9] = 0.f;
+  gx[10] = kSH3[1] * y * z; gy[10] = kSH3[1] * x * z; gz[10] = kSH3[1] * x * y;
+  gx[11] = -2.f * kSH3[2] * x * y; gy[11] = kSH3[2] * (4.f * zz - xx - 3.f * yy); gz[11] = 8.f * kSH3[2] * y * z;
+  gx[12] = -6.f * kSH3[3] * x * z; gy[12] = -6.f * kSH3[3] * y * z; gz[12] = kSH3[3] * (6.f * zz - 3.f * xx - 3.f * yy);
+  gx[13] = kSH3[4] * (4.f * zz - 3.f * xx - yy); gy[13] = -2.f * kSH3[4] * x * y; gz[13] = 8.f * kSH3[4] * x * z;
+  gx[14] = 2.f * kSH3[5] * x * z; gy[14] = -2.f * kSH3[5] * y * z; gz[14] = kSH3[5] * (xx - yy);
+  gx[15] = kSH3[6] * (3.f * xx - 3.f * yy); gy[15] = -6.f * kSH3[6] * x * y; gz[15] = 0.f;
+}
+
+// Rotation matrix (local -> world, row-major R[3*i + j]) of the normalised quaternion,
+// correctly rounded FP32 in a fixed order (the bit-exact recipe).
+__device__ __forceinline__ bool quat_rot_exact(float qw, float qx, float qy, float qz, float R[9]) {
+  float n2 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(qw, qw), __fmul_rn(qx, qx)), __fmul_rn(qy, qy)),
+                       __fmul_rn(qz, qz));
+  if (!(n2 > 0.f)) return false;
+  float r = __fsqrt_rn(n2);
+  float w = __fdiv_rn(qw, r), x = __fdiv_rn(qx, r), y = __fdiv_rn(qy, r), z = __fdiv_rn(qz, r);
+  R[0] = __fsub_rn(1.f, __fmul_rn(2.f, __fadd_rn(__fmul_rn(y, y), __fmul_rn(z, z))));
+  R[1] = __fmul_rn(2.f, __fsub_rn(__fmul_rn(x, y), __fmul_rn(w, z)));
+  R[2] = __fmul_rn(2.f, __fadd_rn(__fmul_rn(x, z), __fmul_rn(w, y)));
+  R[3] = __fmul_rn(2.f, __fadd_rn(__fmul_rn(x, y), __fmul_rn(w, z)));
+  R[4] = __fsub_rn(1.f, __fmul_rn(2.f, __fadd_rn(__fmul_rn(x, x), __fmul_rn(z, z))));
+  R[5] = __fmul_rn(2.f, __fsub_rn(__fmul_rn(y, z), __fmul_rn(w, x)));
+  R[6] = __fmul_rn(2.f, __fsub_rn(__fmul_rn(x, z), __fmul_rn(w, y)));
+  R[7] = __fmul_rn(2.f, __fadd_rn(__fmul_rn(y, z), __fmul_rn(w, x)));
+  R[8] = __fsub_rn(1.f, __fmul_rn(2.f, __fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y))));
+  return true;
+}
+
+struct Box2 {
+  float xmin, xmax, ymin, ymax;
+  bool any;
+};
+
+__device__ __forceinline__ void box_add(Box2& b, const CamParams& cp, float px, float py, float pz) {
+  float u = __fadd_rn(__fmul_rn(cp.fx, __fdiv_rn(px, pz)), cp.cx);
+  float v = __fadd_rn(__fmul_rn(cp.fy, __fdiv_rn(py, pz)), cp.cy);
+  b.xmin = fminf(b.xmin, u);
+  b.xmax = fmaxf(b.xmax, u);
+  b.ymin = fminf(b.ymin, v);
+  b.ymax = fmaxf(b.ymax, v);
+  b.any = true;
+}
+
+}  // namespace
+
+__device__ __forceinline__ bool preprocess_one(int64_t i, const SceneView& sc, const CamParams& cp,
+                                               PrimState* __restrict__ state, uint32_t* __restrict__ count,
+                                               uint32_t* __restrict__ zkey, uint32_t* __restrict__ idx,
+                                               short4* __restrict__ rect);
+
+__global__ void __launch_bounds__(256) k_preprocess(int64_t n, SceneView sc, CamParams cp, PrimState* __restrict__ state,
+                                                    uint32_t* __restrict__ count, uint32_t* __restrict__ zkey,
+                                                    uint32_t* __restrict__ idx, short4* __restrict__ rect,
+                                                    uint32_t* __restrict__ n_visible) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  {
+    // visible-primitive count: one atomic per warp
+    const bool active = i < n;
+    uint32_t vis = 0;
+    if (active) vis = preprocess_one(i, sc, cp, state, count, zkey, idx, rect) ? 1u : 0u;
+    vis = __reduce_add_sync(0xffffffffu, vis);
+    if ((threadIdx.x & 31) == 0 && vis) atomicAdd(n_visible, vis);
+  }
+}
+
+__device__ __forceinline__ bool preprocess_one(int64_t i, const SceneView& sc, const CamParams& cp,
+                                               PrimState* __restrict__ state, uint32_t* __restrict__ count,
+                                               uint32_t* __restrict__ zkey, uint32_t* __restrict__ idx,
+                                               short4* __restrict__ rect) {
+  idx[i] = (uint32_t)i;
+  const float mx = sc.mean[3 * i], my = sc.mean[3 * i + 1], mz = sc.mean[3 * i + 2];
+  const float4 q = reinterpret_cast<const float4*>(sc.quat)[i];
+  const float2 s = reinterpret_cast<const float2*>(sc.scale)[i];
+  const float2 ab = reinterpret_cast<const float2*>(sc.curv)[i];
+  const float op = sc.opacity[i];
+
+  uint32_t cnt = 0;
+  short4 rc = make_short4(-1, -1, -1, -1);
+  uint32_t key = 0xFFFFFFFFu;
+
+  // --- bit-exact part: centre depth, box, tile rectangle -------------------------
+  float muc[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+    muc[r] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(cp.Rc[3 * r], mx), __fmul_rn(cp.Rc[3 * r + 1], my)),
+                                 __fmul_rn(cp.Rc[3 * r + 2], mz)),
+                       cp.tc[r]);
+  float R[9], W[9];
+  bool finite_in = isfinite(mx) && isfinite(my) && isfinite(mz) && isfinite(q.x) && isfinite(q.y) && isfinite(q.z) &&
+                   isfinite(q.w) && isfinite(s.x) && isfinite(s.y) && isfinite(ab.x) && isfinite(ab.y) && isfinite(op);
+  bool ok = finite_in && quat_rot_exact(q.x, q.y, q.z, q.w, R) && s.x > 0.f && s.y > 0.f && muc[2] > cp.near;
+  Box2 bx{INFINITY, -INFINITY, INFINITY, -INFINITY, false};
+  if (ok) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        W[3 * r + c] = __fadd_rn(__fadd_rn(__fmul_rn(cp.Rc[3 * r], R[c]), __fmul_rn(cp.Rc[3 * r + 1], R[3 + c])),
+                                 __fmul_rn(cp.Rc[3 * r + 2], R[6 + c]));
+    const float su = s.x, sv = s.y, a = ab.x, b = ab.y;
+    const float X = __fmul_rn(3.f, su), Y = __fmul_rn(3.f, sv);
+    const float zc = __fmul_rn(3.f, fmaxf(su, sv));
+    const float su2 = __fmul_rn(su, su), sv2 = __fmul_rn(sv, sv);
+    const float apos = a > 0.f ? a : 0.f, bpos = b > 0.f ? b : 0.f;
+    const float aneg = a < 0.f ? a : 0.f, bneg = b < 0.f ? b : 0.f;
+    const float zhi = __fmul_rn(9.f, __fadd_rn(__fmul_rn(apos, su2), __fmul_rn(bpos, sv2)));
+    const float zlo = __fmul_rn(9.f, __fadd_rn(__fmul_rn(aneg, su2), __fmul_rn(bneg, sv2)));
+    const float zmax = fminf(zhi, zc), zmin = fmaxf(zlo, -zc);
+    float P[8][3];
+    bool in[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float sx = (k & 1) ? X : -X, sy = (k & 2) ? Y : -Y, sz = (k & 4) ? zmax : zmin;
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+        P[k][r] = __fadd_rn(__fadd_rn(__fadd_rn(muc[r], __fmul_rn(W[3 * r], sx)), __fmul_rn(W[3 * r + 1], sy)),
+                            __fmul_rn(W[3 * r + 2], sz));
+      in[k] = P[k][2] >= cp.near;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (in[k]) box_add(bx, cp, P[k][0], P[k][1], P[k][2]);
+#pragma unroll
+    for (int k0 = 0; k0 < 8; ++k0) {
+#pragma unroll
+      for (int bit = 1; bit <= 4; bit <<= 1) {
+        if (k0 & bit) continue;
+        const int k1 = k0 | bit;
+        if (in[k0] != in[k1]) {
+          const float lam = __fdiv_rn(__fsub_rn(cp.near, P[k0][2]), __fsub_rn(P[k1][2], P[k0][2]));
+          const float ex = __fadd_rn(P[k0][0], __fmul_rn(lam, __fsub_rn(P[k1][0], P[k0][0])));
+          const float ey = __fadd_rn(P[k0][1], __fmul_rn(lam, __fsub_rn(P[k1][1], P[k0][1])));
+          box_add(bx, cp, ex, ey, cp.near);
+        }
+      }
+    }
+    ok = bx.any && isfinite(bx.xmin) && isfinite(bx.xmax) && isfinite(bx.ymin) && isfinite(bx.ymax) &&
+         !(bx.xmax < 0.f || bx.ymax < 0.f || bx.xmin >= (float)cp.W || bx.ymin >= (float)cp.H);
+    if (ok) {
+      const float tx0 = fmaxf(floorf(__fmul_rn(bx.xmin, 0.0625f)), 0.f);
+      const float tx1 = fminf(floorf(__fmul_rn(bx.xmax, 0.0625f)), (float)(cp.tiles_x - 1));
+      const float ty0 = fmaxf(floorf(__fmul_rn(bx.ymin, 0.0625f)), 0.f);
+      const float ty1 = fminf(floorf(__fmul_rn(bx.ymax, 0.0625f)), (float)(cp.tiles_y - 1));
+      rc = make_short4((short)tx0, (short)tx1, (short)ty0, (short)ty1);
+      cnt = (uint32_t)((rc.y - rc.x + 1) * (rc.w - rc.z + 1));
+      key = __float_as_uint(muc[2]);
+    }
+  }
+  count[i] = cnt;
+  zkey[i] = key;
+  rect[i] = rc;
+  if (!cnt) return false;
+
+  // --- projected state (ordinary FP32/FP64 arithmetic) ---------------------------
+  const float zmu = muc[2];
+  const double iz = 1.0 / (double)zmu;
+  const double pcx = (double)cp.fx * ((double)muc[0] * iz) + (double)cp.cx;
+  const double pcy = (double)cp.fy * ((double)muc[1] * iz) + (double)cp.cy;
+  const float pcx_hi = (float)pcx, pcy_hi = (float)pcy;
+  const float pcx_lo = (float)(pcx - (double)pcx_hi), pcy_lo = (float)(pcy - (double)pcy_hi);
+  float g[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    g[c] = (float)(((double)W[c] * muc[0] + (double)W[3 + c] * muc[1] + (double)W[6 + c] * muc[2]) * iz);
+  const float padx0 = 1e-3f + 1e-6f * fabsf(bx.xmin), padx1 = 1e-3f + 1e-6f * fabsf(bx.xmax);
+  const float pady0 = 1e-3f + 1e-6f * fabsf(bx.ymin), pady1 = 1e-3f + 1e-6f * fabsf(bx.ymax);
+
+  // colour: degree-3 SH at the direction from the camera centre to the primitive
+  float dx = mx - cp.cw[0], dy = my - cp.cw[1], dz = mz - cp.cw[2];
+  const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+  dx *= inv; dy *= inv; dz *= inv;
+  float Yb[16];
+  sh_basis16(dx, dy, dz, Yb);
+  float col[3] = {0.5f, 0.5f, 0.5f};
+  const uint4* shp = reinterpret_cast<const uint4*>(sc.sh + 48 * i);
+#pragma unroll
+  for (int v = 0; v < 6; ++v) {
+    const uint4 w4 = shp[v];
+    const uint32_t wd[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+      const int e = 8 * v + h;  // element index k*3 + c
+      const float cval = bf16_to_f32((uint16_t)((h & 1) ? (wd[h >> 1] >> 16) : (wd[h >> 1] & 0xFFFFu)));
+      col[e % 3] = fmaf(Yb[e / 3], cval, col[e % 3]);
+    }
+  }
+  PrimState ps;
+  ps.f[0] = make_float4(bx.xmin - padx0, bx.xmax + padx1, bx.ymin - pady0, bx.ymax + pady1);
+  ps.f[1] = make_float4(pcx_hi, pcx_lo, pcy_hi, pcy_lo);
+  ps.f[2] = make_float4(zmu / cp.fx, zmu / cp.fy, (float)iz, zmu);
+  ps.f[3] = make_float4(W[0], W[3], W[1], W[4]);
+  ps.f[4] = make_float4(W[2], W[5], g[0], g[1]);
+  ps.f[5] = make_float4(g[2], ab.x, ab.y, op);
+  ps.f[6] = make_float4(1.f / (s.x * s.x), 1.f / (s.y * s.y), W[6], W[7]);
+  ps.f[7] = make_float4(W[8], fmaxf(col[0], 0.f), fmaxf(col[1], 0.f), fmaxf(col[2], 0.f));
+  state[i] = ps;
+  return true;
+}
+
+__global__ void __launch_bounds__(256) k_preprocess_bwd(int64_t n, const uint32_t* __restrict__ list, SceneView sc,
+                                                        CamParams cp, const uint32_t* __restrict__ count,
+                                                        const float* __restrict__ pgrad, GradView gd) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int64_t i = list ? (int64_t)list[j] : j;
+  if (count[i] == 0) return;
+  const float* pg = pgrad + (size_t)NGRAD_PAD * i;
+  float P[9], Hh[3];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) P[k] = pg[k];
+  Hh[0] = pg[9]; Hh[1] = pg[10]; Hh[2] = pg[11];
+  const float d_a = pg[12], d_b = pg[13], d_iu = pg[14], d_iv = pg[15], d_o = pg[16];
+  const float d_col[3] = {pg[17], pg[18], pg[19]};
+
+  const float mx = sc.mean[3 * i], my = sc.mean[3 * i + 1], mz = sc.mean[3 * i + 2];
+  const float4 q = reinterpret_cast<const float4*>(sc.quat)[i];
+  const float2 s = reinterpret_cast<const float2*>(sc.scale)[i];
+  const float qn = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+  const float w = q.x / qn, x = q.y / qn, y = q.z / qn, z = q.w / qn;
+  float R[9];
+  R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z); R[2] = 2.f * (x * z + w * y);
+  R[3] = 2.f * (x * y + w * z); R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+  R[6] = 2.f * (x * z - w * y); R[7] = 2.f * (y * z + w * x); R[8] = 1.f - 2.f * (x * x + y * y);
+  float W[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      W[3 * r + c] = cp.Rc[3 * r] * R[c] + cp.Rc[3 * r + 1] * R[3 + c] + cp.Rc[3 * r + 2] * R[6 + c];
+  // dL/dW = W P ; dL/dmu_cam = -W H
+  float dW[9], dmuc[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dW[3 * r + c] = W[3 * r] * P[c] + W[3 * r + 1] * P[3 + c] + W[3 * r + 2] * P[6 + c];
+    dmuc[r] = -(W[3 * r] * Hh[0] + W[3 * r + 1] * Hh[1] + W[3 * r + 2] * Hh[2]);
+  }
+  // to world: dR = R_cw^T dW, dmu = R_cw^T dmu_cam
+  float dR[9], dmu[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dR[3 * r + c] = cp.Rc[r] * dW[c] + cp.Rc[3 + r] * dW[3 + c] + cp.Rc[6 + r] * dW[6 + c];
+    dmu[r] = cp.Rc[r] * dmuc[0] + cp.Rc[3 + r] * dmuc[1] + cp.Rc[6 + r] * dmuc[2];
+  }
+  // rotation matrix -> normalised quaternion
+  const float gw = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+  const float gx = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] + w * dR[7] -
+                          2.f * x * dR[8]);
+  const float gy = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] + z * dR[7] -
+                          2.f * y * dR[8]);
+  const float gz = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] + y * dR[5] +
+                          x * dR[6] + y * dR[7]);
+  // normalisation q_hat = q / |q|
+  const float dotq = w * gw + x * gx + y * gy + z * gz;
+  const float iqn = 1.f / qn;
+
+  // colour: SH backward through the clamp at 0 and the view direction
+  float ddx = mx - cp.cw[0], ddy = my - cp.cw[1], ddz = mz - cp.cw[2];
+  const float dn = sqrtf(ddx * ddx + ddy * ddy + ddz * ddz);
+  const float idn = 1.f / dn;
+  const float vx = ddx * idn, vy = ddy * idn, vz = ddz * idn;
+  float Yb[16];
+  sh_basis16(vx, vy, vz, Yb);
+  float shv[48];
+  const uint4* shp = reinterpret_cast<const uint4*>(sc.sh + 48 * i);
+#pragma unroll
+  for (int v = 0; v < 6; ++v) {
+    const uint4 w4 = shp[v];
+    const uint32_t wd[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+    for (int h = 0; h < 8; ++h)
+      shv[8 * v + h] = bf16_to_f32((uint16_t)((h & 1) ? (wd[h >> 1] >> 16) : (wd[h >> 1] & 0xFFFFu)));
+  }
+  float dc[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float v = 0.5f;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v = fmaf(Yb[k], shv[3 * k + c], v);
+    dc[c] = v < 0.f ? 0.f : d_col[c];
+  }
+  float4* gsh = reinterpret_cast<float4*>(gd.sh + 48 * i);
+#pragma unroll
+  for (int v = 0; v < 12; ++v) {
+    float4 g4 = gsh[v];
+    float* gg = reinterpret_cast<float*>(&g4);
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const int e = 4 * v + h;
+      gg[h] += Yb[e / 3] * dc[e % 3];
+    }
+    gsh[v] = g4;
+  }
+  float Gx[16], Gy[16], Gz[16];
+  sh_basis16_grad(vx, vy, vz, Gx, Gy, Gz);
+  float gvx = 0.f, gvy = 0.f, gvz = 0.f;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const float t = dc[0] * shv[3 * k] + dc[1] * shv[3 * k + 1] + dc[2] * shv[3 * k + 2];
+    gvx = fmaf(t, Gx[k], gvx);
+    gvy = fmaf(t, Gy[k], gvy);
+    gvz = fmaf(t, Gz[k], gvz);
+  }
+  const float vd = vx * gvx + vy * gvy + vz * gvz;
+  dmu[0] += (gvx - vx * vd) * idn;
+  dmu[1] += (gvy - vy * vd) * idn;
+  dmu[2] += (gvz - vz * vd) * idn;
+
+  gd.mean[3 * i] += dmu[0];
+  gd.mean[3 * i + 1] += dmu[1];
+  gd.mean[3 * i + 2] += dmu[2];
+  float4 gq = reinterpret_cast<float4*>(gd.quat)[i];
+  gq.x += (gw - w * dotq) * iqn;
+  gq.y += (gx - x * dotq) * iqn;
+  gq.z += (gy - y * dotq) * iqn;
+  gq.w += (gz - z * dotq) * iqn;
+  reinterpret_cast<float4*>(gd.quat)[i] = gq;
+  float2 gs = reinterpret_cast<float2*>(gd.scale)[i];
+  gs.x += d_iu * (-2.f / (s.x * s.x * s.x));
+  gs.y += d_iv * (-2.f / (s.y * s.y * s.y));
+  reinterpret_cast<float2*>(gd.scale)[i] = gs;
+  float2 gc = reinterpret_cast<float2*>(gd.curv)[i];
+  gc.x += d_a;
+  gc.y += d_b;
+  reinterpret_cast<float2*>(gd.curv)[i] = gc;
+  gd.opacity[i] += d_o;
+}
+
+}  // namespace qgs

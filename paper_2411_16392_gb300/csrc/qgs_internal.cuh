@@ -1,0 +1,88 @@
+// Internal declarations shared by the translation units of libqgs (not part of the ABI).
+#pragma once
+
+#include "qgs_common.cuh"
+
+namespace qgs {
+
+struct SceneView {
+  const float* mean;
+  const float* quat;
+  const float* scale;
+  const float* curv;
+  const float* opacity;
+  const uint16_t* sh;
+};
+
+struct GradView {
+  float* mean;
+  float* quat;
+  float* scale;
+  float* curv;
+  float* opacity;
+  float* sh;
+};
+
+struct CamParams {
+  float Rc[9];   // world -> camera rotation, row-major
+  float tc[3];
+  float cw[3];   // camera centre in world coordinates
+  float fx, fy, cx, cy, near;
+  int W, H, tiles_x, tiles_y;
+};
+
+// ---------------------------------------------------------------- preprocessing
+__global__ void k_preprocess(int64_t n, SceneView sc, CamParams cp, PrimState* state, uint32_t* count,
+                             uint32_t* zkey, uint32_t* idx, short4* rect, uint32_t* n_visible);
+// list == nullptr: threads 0..n-1 are primitives 0..n-1; else primitive list[j].
+__global__ void k_preprocess_bwd(int64_t n, const uint32_t* list, SceneView sc, CamParams cp, const uint32_t* count,
+                                 const float* pgrad, GradView gd);
+
+// ---------------------------------------------------------------- sorting / scan
+// Temporary storage of the device-wide scan and radix sort.
+struct SortTemp {
+  uint32_t* hist = nullptr;   // [256 * max_blocks]
+  uint32_t* scan_tmp = nullptr;
+  size_t hist_cap = 0, scan_cap = 0;
+};
+
+// Exclusive prefix sum of n u32 values; out[n] receives the total (out has n + 1 slots).
+cudaError_t scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, size_t tmp_cap,
+                               cudaStream_t st);
+size_t scan_tmp_elems(int64_t n);
+
+// Stable LSD radix sort of u32 keys with u32 values over bits [begin_bit, end_bit).
+// Ping-pongs between (k0, v0) and (k1, v1); returns true if the result ends in (k1, v1).
+bool radix_sort_u32_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t n, int begin_bit,
+                          int end_bit, SortTemp& tmp, cudaStream_t st, cudaError_t* err);
+// Stable LSD radix sort of u64 keys (no values) over bits [begin_bit, end_bit).
+bool radix_sort_u64_keys(uint64_t* k0, uint64_t* k1, int64_t n, int begin_bit, int end_bit, SortTemp& tmp,
+                         cudaStream_t st, cudaError_t* err);
+// Stable LSD radix sort of u64 keys with u32 values over bits [begin_bit, end_bit).
+bool radix_sort_u64_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n, int begin_bit,
+                          int end_bit, SortTemp& tmp, cudaStream_t st, cudaError_t* err);
+size_t radix_hist_elems(int64_t n);
+
+// ---------------------------------------------------------------- compositing
+struct RasterStats {
+  unsigned long long pair_evals, pair_isect, pair_hits, pair_blended, grazing;
+  unsigned long long bwd_pairs, bwd_contrib;
+};
+
+// Kernel launches issued by the calling host thread (the library's launch sites
+// increment it; the API reports per-call differences).
+inline int64_t& launch_counter() {
+  static thread_local int64_t n = 0;
+  return n;
+}
+
+__global__ void k_raster_fwd(const uint2* ranges, const uint32_t* ids, int id_stride, const PrimState* state,
+                             RasterParams rp, float* out_rgb, float* out_alpha, float* out_depth,
+                             float* out_normal, float* T_final, uint32_t* n_contrib, RasterStats* stats);
+constexpr size_t RASTER_BWD_SMEM = sizeof(PrimState) * BLOCK + sizeof(float) * BLOCK * NGRAD + sizeof(int) * BLOCK;
+__global__ void k_raster_bwd(const uint2* ranges, const uint32_t* ids, int id_stride, const PrimState* state,
+                             RasterParams rp, const float* g_rgb, const float* g_alpha, const float* g_depth,
+                             const float* g_normal, const float* T_final, const uint32_t* n_contrib,
+                             float* pgrad, RasterStats* stats);
+
+}  // namespace qgs

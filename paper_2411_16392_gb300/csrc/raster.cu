@@ -1,0 +1,468 @@
+// Per-tile compositing of quadric Gaussian primitives: forward and backward.
+//
+// One CTA per 16x16 tile, one thread per pixel (warps cover 8x4 pixel blocks). The
+// tile's sorted primitive list is walked in batches of 256 projected-state records
+// staged in shared memory (one 128-byte line per primitive, gathered by 8 threads per
+// record). Per (pixel, primitive) pair:
+//   - the pixel ray is expressed in the primitive's local frame relative to the point
+//     where it crosses the depth of the primitive's centre (a translation of the ray
+//     parameter t = z_mu + s); the pixel offset from the projected centre is formed in
+//     double-float, so the local ray origin and the quadratic's coefficients stay of the
+//     size of the primitive instead of the camera distance;
+//   - ray-quadric intersection with z = a x^2 + b y^2 (supplementary, intersection Eq.),
+//     roots from the cancellation-free form q = -(B' + sgn(B') sqrt(D')), s = C/q, q/A
+//     (B' = B/2, D' = D/4), and an FP64 re-solve when |D| <= grazing_eps * B^2;
+//   - near-then-far selection within 3 sigma(theta) (Sec. 3.2.1) via the trig-free form
+//     l^2 / sigma(theta)^2 = F(u)^2 E, E = x^2/s_u^2 + y^2/s_v^2, u = 2 a(theta) rho,
+//     F(u) = l / rho = (asinh(u)/u + sqrt(1 + u^2)) / 2 (geodesic Eq. and sigma Eq. of
+//     Sec. 3.2); F >= 1, so E > 9 rejects a candidate before F is evaluated; F uses its
+//     Taylor series 1 + u^2/6 - u^4/40 for |u| < 1e-3;
+//   - G = exp(-F^2 E / 2), alpha = min(alpha_max, o G), skip below alpha_min, stop before
+//     the transmittance would fall below T_min (Sec. 3.1 blending Eq.);
+//   - normal = gradient of the implicit function (Sec. 3.2 normal Eq.) in camera space,
+//     facing the camera.
+// The backward walks each pixel's list in reverse from its last blended primitive,
+// recomputing T_i = T_{i+1} / (1 - alpha_i) (supplementary, back-to-front dX/d(alpha)),
+// and differentiates through the implicit root, the geodesic weight and the normal.
+// Per-primitive gradients are reduced across each warp with a transpose reduction,
+// accumulated per batch in shared memory, and added to global memory once per
+// (tile, primitive).
+//
+// Every operation that decides whether a pair contributes is written with explicitly
+// rounded intrinsics, so the forward and the backward (which recomputes the pairs)
+// take identical decisions.
+#include "qgs_internal.cuh"
+
+namespace qgs {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+struct Hit {
+  float s;            // root offset: t = z_mu + s
+  float x, y, zs;     // local hit point (zs = a x^2 + b y^2)
+  float dx, dy, dz;   // local ray direction (camera-space ray with z component 1)
+  float rho2, u, F, E, G;
+};
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// F(u) = l(a, rho) / rho with u = 2 a rho (the arc-length closed form of Sec. 3.2,
+// divided by rho); Taylor series for |u| < 1e-3.
+__device__ __forceinline__ float arc_ratio(float u) {
+  const float au = fabsf(u);
+  if (au < 1e-3f) {
+    const float u2 = __fmul_rn(u, u);
+    return __fmaf_rn(u2, __fmaf_rn(u2, -0.025f, 0.16666667f), 1.f);
+  }
+  return __fmul_rn(0.5f, __fadd_rn(__fdividef(asinhf(au), au), __fsqrt_rn(__fmaf_rn(au, au, 1.f))));
+}
+
+// dF/du. Series u (1/3 - u^2/10 + 3u^4/56 - 5u^6/144 + 35u^8/1408 - 63u^10/3328) for
+// |u| < 0.25; otherwise from (u F)' = sqrt(1 + u^2), i.e. F' = (sqrt(1 + u^2) - F) / u.
+__device__ __forceinline__ float arc_ratio_prime(float u, float F) {
+  if (fabsf(u) < 0.25f) {
+    const float u2 = u * u;
+    float p = -63.f / 3328.f;
+    p = fmaf(p, u2, 35.f / 1408.f);
+    p = fmaf(p, u2, -5.f / 144.f);
+    p = fmaf(p, u2, 3.f / 56.f);
+    p = fmaf(p, u2, -0.1f);
+    p = fmaf(p, u2, 1.f / 3.f);
+    return u * p;
+  }
+  return (sqrtf(fmaf(u, u, 1.f)) - F) / u;
+}
+
+// Evaluate one (pixel, primitive) pair. Returns true when a root in front of the near
+// plane lies within 3 sigma(theta) (the selected hit is in h, G included).
+__device__ __forceinline__ bool eval_pair(const PrimState& P, float X, float Y, const RasterParams& rp, Hit& h,
+                                          bool& grazed, uint32_t& isect) {
+  const float4 f0 = P.f[0];
+  if (X < f0.x || X > f0.y || Y < f0.z || Y > f0.w) return false;
+  ++isect;
+  const float4 f1 = P.f[1], f2 = P.f[2], f3 = P.f[3], f4 = P.f[4], f5 = P.f[5], f6 = P.f[6];
+  // camera-plane offset at the centre's depth, then the local frame (W^T e, e_z = 0)
+  const float ex = __fmul_rn(__fsub_rn(__fsub_rn(X, f1.x), f1.y), f2.x);
+  const float ey = __fmul_rn(__fsub_rn(__fsub_rn(Y, f1.z), f1.w), f2.y);
+  const float bx = __fmaf_rn(f3.x, ex, __fmul_rn(f3.y, ey));
+  const float by = __fmaf_rn(f3.z, ex, __fmul_rn(f3.w, ey));
+  const float bz = __fmaf_rn(f4.x, ex, __fmul_rn(f4.y, ey));
+  const float dx = __fmaf_rn(bx, f2.z, f4.z);
+  const float dy = __fmaf_rn(by, f2.z, f4.w);
+  const float dz = __fmaf_rn(bz, f2.z, f5.x);
+  const float a = f5.y, b = f5.z;
+  const float adx = __fmul_rn(a, dx), bdy = __fmul_rn(b, dy);
+  const float A = __fmaf_rn(adx, dx, __fmul_rn(bdy, dy));
+  const float Bh = __fmaf_rn(adx, bx, __fmaf_rn(bdy, by, __fmul_rn(-0.5f, dz)));
+  const float C = __fmaf_rn(__fmul_rn(a, bx), bx, __fmaf_rn(__fmul_rn(b, by), by, -bz));
+  const float Dq = __fmaf_rn(Bh, Bh, -__fmul_rn(A, C));
+  float s1, s2;
+  if (fabsf(Dq) <= __fmul_rn(rp.grazing_eps, __fmul_rn(Bh, Bh))) {
+    // grazing ray: re-solve in FP64 from the FP32 local ray
+    grazed = true;
+    const double ad = a, bd = b, dxd = dx, dyd = dy, bxd = bx, byd = by;
+    const double Ad = ad * dxd * dxd + bd * dyd * dyd;
+    const double Bd = ad * bxd * dxd + bd * byd * dyd - 0.5 * (double)dz;
+    const double Cd = ad * bxd * bxd + bd * byd * byd - (double)bz;
+    const double Dd = Bd * Bd - Ad * Cd;
+    if (Dd < 0.0) return false;
+    const double sq = sqrt(Dd);
+    const double qd = -(Bd + (Bd >= 0.0 ? sq : -sq));
+    s1 = qd != 0.0 ? (float)(Cd / qd) : __int_as_float(0x7fc00000);
+    s2 = Ad != 0.0 ? (float)(qd / Ad) : __int_as_float(0x7fc00000);
+  } else {
+    if (Dq < 0.f) return false;
+    const float sq = sqrt_approx(Dq);
+    const float q = -__fadd_rn(Bh, Bh >= 0.f ? sq : -sq);
+    s1 = __fdividef(C, q);
+    s2 = __fdividef(q, A);
+  }
+  const bool e1 = isfinite(s1), e2 = isfinite(s2);
+  float sn, sf;
+  bool hasf;
+  if (e1 && e2) {
+    sn = fminf(s1, s2);
+    sf = fmaxf(s1, s2);
+    hasf = true;
+  } else if (e1 || e2) {
+    sn = e1 ? s1 : s2;
+    sf = sn;
+    hasf = false;
+  } else {
+    return false;
+  }
+  const float smin = __fsub_rn(rp.near_plane, f2.w);  // t > near  <=>  s > near - z_mu
+  const float iu = f6.x, iv = f6.y;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const float s = c ? sf : sn;
+    if (c && !hasf) break;
+    if (!(s > smin)) continue;
+    const float x = __fmaf_rn(s, dx, bx), y = __fmaf_rn(s, dy, by);
+    const float x2 = __fmul_rn(x, x), y2 = __fmul_rn(y, y);
+    const float E = __fmaf_rn(iu, x2, __fmul_rn(iv, y2));
+    if (!(E <= 9.f)) continue;  // F >= 1: outside the 3-sigma ellipse already
+    const float rho2 = __fadd_rn(x2, y2);
+    const float zs = __fmaf_rn(a, x2, __fmul_rn(b, y2));
+    const float u = rho2 > 0.f ? __fmul_rn(__fmul_rn(2.f, zs), rsqrtf(rho2)) : 0.f;
+    const float F = arc_ratio(u);
+    const float Q = __fmul_rn(__fmul_rn(F, F), E);
+    if (!(Q <= 9.f)) continue;
+    h.s = s; h.x = x; h.y = y; h.zs = zs;
+    h.dx = dx; h.dy = dy; h.dz = dz;
+    h.rho2 = rho2; h.u = u; h.F = F; h.E = E;
+    h.G = __expf(__fmul_rn(-0.5f, Q));
+    return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void pixel_of(int tile, int tiles_x, int& px, int& py) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  px = (tile % tiles_x) * TILE + (warp & 1) * 8 + (lane & 7);
+  py = (tile / tiles_x) * TILE + (warp >> 1) * 4 + (lane >> 3);
+}
+
+__device__ __forceinline__ void stage_batch(PrimState* sm, const uint32_t* ids, int id_stride, const PrimState* state,
+                                            uint32_t first, int cnt) {
+  for (int e = threadIdx.x; e < cnt * 8; e += BLOCK) {
+    const int r = e >> 3, c = e & 7;
+    const uint32_t pid = __ldg(ids + (size_t)(first + r) * id_stride);
+    reinterpret_cast<float4*>(sm)[r * 8 + c] = __ldg(reinterpret_cast<const float4*>(state + pid) + c);
+  }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(BLOCK, 3)
+    k_raster_fwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids, int id_stride,
+                 const PrimState* __restrict__ state, RasterParams rp, float* __restrict__ out_rgb,
+                 float* __restrict__ out_alpha, float* __restrict__ out_depth, float* __restrict__ out_normal,
+                 float* __restrict__ T_final, uint32_t* __restrict__ n_contrib, RasterStats* __restrict__ stats) {
+  __shared__ PrimState sm[BLOCK];
+  const int tile = blockIdx.x;
+  int px, py;
+  pixel_of(tile, rp.tiles_x, px, py);
+  const bool inside = px < rp.W && py < rp.H;
+  const uint2 rg = ranges[tile];
+  const int n = (int)(rg.y - rg.x);
+  const float X = (float)px + 0.5f, Y = (float)py + 0.5f;
+  const float xn = (X - rp.cx) * rp.inv_fx, yn = (Y - rp.cy) * rp.inv_fy;
+  float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, dep = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
+  uint32_t last = 0, evals = 0, grazes = 0, isect = 0, hits = 0, blended = 0;
+  bool done = !inside;
+  for (int b0 = 0; b0 < n; b0 += BLOCK) {
+    if (__syncthreads_count(done) == BLOCK) break;
+    const int cnt = min(BLOCK, n - b0);
+    stage_batch(sm, ids, id_stride, state, rg.x + b0, cnt);
+    __syncthreads();
+    if (!done) {
+      for (int j = 0; j < cnt; ++j) {
+        ++evals;
+        Hit h;
+        bool gz = false;
+        const bool hit = eval_pair(sm[j], X, Y, rp, h, gz, isect);
+        grazes += gz;
+        if (!hit) continue;
+        ++hits;
+        const float4 f5 = sm[j].f[5];
+        const float al = fminf(rp.alpha_max, __fmul_rn(f5.w, h.G));
+        if (al < rp.alpha_min) continue;
+        const float Tn = __fmul_rn(T, __fsub_rn(1.f, al));
+        if (Tn < rp.T_min) {
+          done = true;
+          break;
+        }
+        const float w = al * T;
+        const float4 f2 = sm[j].f[2], f3 = sm[j].f[3], f4 = sm[j].f[4], f6 = sm[j].f[6], f7 = sm[j].f[7];
+        cr = fmaf(w, f7.y, cr);
+        cg = fmaf(w, f7.z, cg);
+        cb = fmaf(w, f7.w, cb);
+        dep = fmaf(w, f2.w + h.s, dep);
+        const float nlx = 2.f * f5.y * h.x, nly = 2.f * f5.z * h.y;
+        const float ncx = fmaf(f3.x, nlx, fmaf(f3.z, nly, -f4.x));
+        const float ncy = fmaf(f3.y, nlx, fmaf(f3.w, nly, -f4.y));
+        const float ncz = fmaf(f6.z, nlx, fmaf(f6.w, nly, -f7.x));
+        float inn = rsqrtf(fmaf(ncx, ncx, fmaf(ncy, ncy, ncz * ncz)));
+        if (fmaf(ncx, xn, fmaf(ncy, yn, ncz)) > 0.f) inn = -inn;
+        const float wn = w * inn;
+        nx = fmaf(wn, ncx, nx);
+        ny = fmaf(wn, ncy, ny);
+        nz = fmaf(wn, ncz, nz);
+        T = Tn;
+        ++blended;
+        last = (uint32_t)(b0 + j + 1);
+      }
+    }
+  }
+  if (inside) {
+    const size_t P = (size_t)rp.W * rp.H, pix = (size_t)py * rp.W + px;
+    out_rgb[pix] = cr;
+    out_rgb[P + pix] = cg;
+    out_rgb[2 * P + pix] = cb;
+    out_alpha[pix] = 1.f - T;
+    out_depth[pix] = dep;
+    out_normal[pix] = nx;
+    out_normal[P + pix] = ny;
+    out_normal[2 * P + pix] = nz;
+    T_final[pix] = T;
+    n_contrib[pix] = last;
+  }
+  // counters: one atomic per warp and counter
+  if (stats) {
+    const unsigned ev = __reduce_add_sync(FULL, evals), is = __reduce_add_sync(FULL, isect);
+    const unsigned hi = __reduce_add_sync(FULL, hits), bl = __reduce_add_sync(FULL, blended);
+    const unsigned gzz = __reduce_add_sync(FULL, grazes);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&stats->pair_evals, (unsigned long long)ev);
+      atomicAdd(&stats->pair_isect, (unsigned long long)is);
+      atomicAdd(&stats->pair_hits, (unsigned long long)hi);
+      atomicAdd(&stats->pair_blended, (unsigned long long)bl);
+      if (gzz) atomicAdd(&stats->grazing, (unsigned long long)gzz);
+    }
+  }
+}
+
+namespace {
+
+// Butterfly reduce-scatter of 32 per-lane values across the warp: afterwards lane l
+// holds the warp-wide sum of component l.
+__device__ __forceinline__ float warp_transpose_sum(float v[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int k = 0; k < off; ++k) {
+      const float send = up ? v[k] : v[k + off];
+      const float keep = up ? v[k + off] : v[k];
+      v[k] = keep + __shfl_xor_sync(FULL, send, off);
+    }
+  }
+  return v[0];
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(BLOCK, 2)
+    k_raster_bwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids, int id_stride,
+                 const PrimState* __restrict__ state, RasterParams rp, const float* __restrict__ g_rgb,
+                 const float* __restrict__ g_alpha, const float* __restrict__ g_depth,
+                 const float* __restrict__ g_normal, const float* __restrict__ T_final,
+                 const uint32_t* __restrict__ n_contrib, float* __restrict__ pgrad,
+                 RasterStats* __restrict__ stats) {
+  // dynamic shared memory: BLOCK records, then BLOCK x NGRAD accumulators, then flags
+  extern __shared__ float4 dyn_smem[];
+  PrimState* sm = reinterpret_cast<PrimState*>(dyn_smem);
+  float(*sg)[NGRAD] = reinterpret_cast<float(*)[NGRAD]>(sm + BLOCK);
+  int* sflag = reinterpret_cast<int*>(&sg[BLOCK][0]);
+  __shared__ int smax;
+  const int tile = blockIdx.x;
+  int px, py;
+  pixel_of(tile, rp.tiles_x, px, py);
+  const bool inside = px < rp.W && py < rp.H;
+  const uint2 rg = ranges[tile];
+  const float X = (float)px + 0.5f, Y = (float)py + 0.5f;
+  const float xn = (X - rp.cx) * rp.inv_fx, yn = (Y - rp.cy) * rp.inv_fy;
+  const size_t P = (size_t)rp.W * rp.H, pix = inside ? (size_t)py * rp.W + px : 0;
+  float T = inside ? T_final[pix] : 1.f;
+  const float Tfin = T;
+  const uint32_t last = inside ? n_contrib[pix] : 0u;
+  float gR = 0.f, gG = 0.f, gB = 0.f, gA = 0.f, gD = 0.f, gNx = 0.f, gNy = 0.f, gNz = 0.f;
+  if (inside) {
+    if (g_rgb) { gR = g_rgb[pix]; gG = g_rgb[P + pix]; gB = g_rgb[2 * P + pix]; }
+    if (g_alpha) gA = g_alpha[pix];
+    if (g_depth) gD = g_depth[pix];
+    if (g_normal) { gNx = g_normal[pix]; gNy = g_normal[P + pix]; gNz = g_normal[2 * P + pix]; }
+  }
+  if (threadIdx.x == 0) smax = 0;
+  __syncthreads();
+  {
+    unsigned m = __reduce_max_sync(FULL, last);
+    if ((threadIdx.x & 31) == 0) atomicMax(&smax, (int)m);
+  }
+  __syncthreads();
+  const int maxlast = smax;
+  float Sdot = 0.f;  // sum over later pairs j of w_j * (g . X_j)
+  uint32_t n_pairs = 0, n_contrib_pairs = 0, isect = 0;
+  for (int b0 = ((maxlast - 1) / BLOCK) * BLOCK; maxlast > 0 && b0 >= 0; b0 -= BLOCK) {
+    const int cnt = min(BLOCK, maxlast - b0);
+    __syncthreads();
+    stage_batch(sm, ids, id_stride, state, rg.x + b0, cnt);
+    for (int e = threadIdx.x; e < BLOCK * NGRAD; e += BLOCK) (&sg[0][0])[e] = 0.f;
+    sflag[threadIdx.x] = 0;
+    __syncthreads();
+    for (int j = cnt - 1; j >= 0; --j) {
+      float v[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) v[k] = 0.f;
+      bool contrib = false;
+      if ((uint32_t)(b0 + j) < last) {
+        Hit h;
+        bool gz = false;
+        ++n_pairs;
+        if (eval_pair(sm[j], X, Y, rp, h, gz, isect)) {
+          const float4 f2 = sm[j].f[2], f3 = sm[j].f[3], f4 = sm[j].f[4], f5 = sm[j].f[5], f6 = sm[j].f[6],
+                       f7 = sm[j].f[7];
+          const float a = f5.y, b = f5.z, o = f5.w;
+          const float oG = __fmul_rn(o, h.G);
+          const float al = fminf(rp.alpha_max, oG);
+          if (al >= rp.alpha_min) {
+            contrib = true;
+            ++n_contrib_pairs;
+            const float onem = 1.f - al;
+            T = T / onem;  // T_i from T_{i+1}
+            const float w = al * T;
+            const float W00 = f3.x, W10 = f3.y, W01 = f3.z, W11 = f3.w, W02 = f4.x, W12 = f4.y, W20 = f6.z,
+                        W21 = f6.w, W22 = f7.x;
+            const float x = h.x, y = h.y;
+            const float nlx = 2.f * a * x, nly = 2.f * b * y;
+            const float ncx = fmaf(W00, nlx, fmaf(W01, nly, -W02));
+            const float ncy = fmaf(W10, nlx, fmaf(W11, nly, -W12));
+            const float ncz = fmaf(W20, nlx, fmaf(W21, nly, -W22));
+            const float inn = rsqrtf(fmaf(ncx, ncx, fmaf(ncy, ncy, ncz * ncz)));
+            const float sg_ = fmaf(ncx, xn, fmaf(ncy, yn, ncz)) > 0.f ? -1.f : 1.f;
+            const float hx = ncx * inn, hy = ncy * inn, hz = ncz * inn;  // unsigned unit normal
+            const float nox = sg_ * hx, noy = sg_ * hy, noz = sg_ * hz;
+            const float t = f2.w + h.s;
+            const float gX = gR * f7.y + gG * f7.z + gB * f7.w + gD * t + gNx * nox + gNy * noy + gNz * noz;
+            const float dal = T * gX - (Sdot - gA * Tfin) / onem;
+            Sdot = fmaf(w, gX, Sdot);
+            v[17] = w * gR;
+            v[18] = w * gG;
+            v[19] = w * gB;
+            const float d_t = w * gD;
+            // alpha = min(alpha_max, o G)
+            float dG = 0.f;
+            if (oG < rp.alpha_max) {
+              v[16] = dal * h.G;
+              dG = dal * o;
+            }
+            const float dQ = -0.5f * h.G * dG;
+            const float dF = dQ * 2.f * h.F * h.E;
+            const float dE = dQ * h.F * h.F;
+            v[14] = dE * x * x;
+            v[15] = dE * y * y;
+            float gx = dE * 2.f * f6.x * x, gy = dE * 2.f * f6.y * y;
+            float da = 0.f, db = 0.f;
+            if (h.rho2 > 0.f) {
+              const float irho = rsqrtf(h.rho2);
+              const float du = dF * arc_ratio_prime(h.u, h.F);
+              const float ur = h.u * irho * irho;
+              gx += du * (4.f * a * x * irho - ur * x);
+              gy += du * (4.f * b * y * irho - ur * y);
+              da += du * 2.f * x * x * irho;
+              db += du * 2.f * y * y * irho;
+            }
+            // normal: n_out = sg * n_c / |n_c|, n_c = W n_l
+            const float dnx = w * gNx, dny = w * gNy, dnz = w * gNz;
+            const float dd = hx * dnx + hy * dny + hz * dnz;
+            const float sc_ = sg_ * inn;
+            const float dcx = sc_ * (dnx - hx * dd), dcy = sc_ * (dny - hy * dd), dcz = sc_ * (dnz - hz * dd);
+            const float gmx = W00 * dcx + W10 * dcy + W20 * dcz;
+            const float gmy = W01 * dcx + W11 * dcy + W21 * dcz;
+            const float gmz = W02 * dcx + W12 * dcy + W22 * dcz;
+            gx += 2.f * a * gmx;
+            gy += 2.f * b * gmy;
+            da += 2.f * x * gmx;
+            db += 2.f * y * gmy;
+            // the root moves with the parameters: t(theta) from f(p_hat(t)) = 0
+            const float den = nlx * h.dx + nly * h.dy - h.dz;
+            const float kk = den != 0.f ? (gx * h.dx + gy * h.dy + d_t) / den : 0.f;
+            const float hhx = gx - kk * nlx, hhy = gy - kk * nly, hhz = kk;
+            da -= kk * x * x;
+            db -= kk * y * y;
+            v[12] = da;
+            v[13] = db;
+            v[9] = hhx;
+            v[10] = hhy;
+            v[11] = hhz;
+            // P = p_hat h^T + gamma n_l^T, p_hat = (x, y, zs), n_l = (nlx, nly, -1)
+            const float pz = h.zs;
+            v[0] = x * hhx + gmx * nlx;
+            v[1] = x * hhy + gmx * nly;
+            v[2] = x * hhz - gmx;
+            v[3] = y * hhx + gmy * nlx;
+            v[4] = y * hhy + gmy * nly;
+            v[5] = y * hhz - gmy;
+            v[6] = pz * hhx + gmz * nlx;
+            v[7] = pz * hhy + gmz * nly;
+            v[8] = pz * hhz - gmz;
+          }
+        }
+      }
+      if (__any_sync(FULL, contrib)) {
+        const float r = warp_transpose_sum(v);
+        const int lane = threadIdx.x & 31;
+        if (lane < NGRAD && r != 0.f) atomicAdd(&sg[j][lane], r);
+        if (lane == 0) sflag[j] = 1;
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt * NGRAD; e += BLOCK) {
+      const int r = e / NGRAD, c = e - r * NGRAD;
+      if (sflag[r]) {
+        const float val = sg[r][c];
+        if (val != 0.f) {
+          const uint32_t pid = __ldg(ids + (size_t)(rg.x + b0 + r) * id_stride);
+          atomicAdd(pgrad + (size_t)pid * NGRAD_PAD + c, val);
+        }
+      }
+    }
+  }
+  if (stats) {
+    const unsigned np = __reduce_add_sync(FULL, n_pairs), nc = __reduce_add_sync(FULL, n_contrib_pairs);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&stats->bwd_pairs, (unsigned long long)np);
+      atomicAdd(&stats->bwd_contrib, (unsigned long long)nc);
+    }
+  }
+}
+
+}  // namespace qgs

@@ -1,0 +1,314 @@
+// Device-wide exclusive scan and stable LSD radix sort (hand-written, no library).
+//
+// Radix sort: per pass of at most 8 bits,
+//   1. upsweep  - each CTA histograms the digits of its 4096-key chunk into a
+//                 digit-major count matrix hist[d * nblocks + b];
+//   2. scan     - one exclusive scan of that matrix gives, for every (digit, chunk), the
+//                 global position of the chunk's first key with that digit;
+//   3. downsweep - each warp ranks its 512 keys in order with __match_any_sync
+//                 (peers with the same digit), warp-level digit counters are scanned
+//                 across the CTA's warps, and every key is written to
+//                 base(d, chunk) + (keys with digit d in earlier warps) + rank in warp.
+// Keys keep their relative order within a digit (stable), so successive passes from
+// the least significant digit up sort by the whole bit range.
+#include "qgs_internal.cuh"
+
+namespace qgs {
+
+namespace {
+
+constexpr int SCAN_ITEMS = 16;
+constexpr int SCAN_CHUNK = BLOCK * SCAN_ITEMS;  // 4096 values per CTA
+constexpr int RS_WARPS = 8;
+constexpr int RS_ITEMS = 16;                    // keys per lane
+constexpr int RS_CHUNK = RS_WARPS * 32 * RS_ITEMS;  // 4096 keys per CTA
+constexpr unsigned FULL = 0xffffffffu;
+
+// Exclusive scan of the CTA's values in shared memory (SCAN_CHUNK of them); returns the
+// CTA total. Thread t scans items [t*16, t*16+16) sequentially, then the thread totals
+// are scanned with warp shuffles and one pass over the warp totals.
+__device__ uint32_t block_exclusive_scan(uint32_t* s) {
+  __shared__ uint32_t warp_tot[BLOCK / 32];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  uint32_t run = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    const uint32_t v = s[t * SCAN_ITEMS + k];
+    s[t * SCAN_ITEMS + k] = run;
+    run += v;
+  }
+  uint32_t inc = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t n = __shfl_up_sync(FULL, inc, o);
+    if (lane >= o) inc += n;
+  }
+  if (lane == 31) warp_tot[warp] = inc;
+  __syncthreads();
+  uint32_t wbase = 0, total = 0;
+#pragma unroll
+  for (int w = 0; w < BLOCK / 32; ++w) {
+    const uint32_t v = warp_tot[w];
+    if (w < warp) wbase += v;
+    total += v;
+  }
+  const uint32_t base = wbase + inc - run;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) s[t * SCAN_ITEMS + k] += base;
+  __syncthreads();
+  return total;
+}
+
+__global__ void __launch_bounds__(BLOCK) k_scan_reduce(const uint32_t* __restrict__ in, int64_t n,
+                                                       uint32_t* __restrict__ sums) {
+  __shared__ uint32_t red[BLOCK / 32];
+  const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK;
+  uint32_t acc = 0;
+  for (int k = threadIdx.x; k < SCAN_CHUNK; k += BLOCK) {
+    const int64_t i = base + k;
+    if (i < n) acc += in[i];
+  }
+  acc = __reduce_add_sync(FULL, acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < BLOCK / 32; ++w) t += red[w];
+    sums[blockIdx.x] = t;
+  }
+}
+
+// Scan of each chunk plus its chunk offset; the last CTA also writes the total to out[n].
+__global__ void __launch_bounds__(BLOCK) k_scan_down(const uint32_t* __restrict__ in, int64_t n,
+                                                     const uint32_t* __restrict__ offs, uint32_t* __restrict__ out) {
+  __shared__ uint32_t s[SCAN_CHUNK];
+  const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK;
+  for (int k = threadIdx.x; k < SCAN_CHUNK; k += BLOCK) {
+    const int64_t i = base + k;
+    s[k] = i < n ? in[i] : 0u;
+  }
+  __syncthreads();
+  const uint32_t total = block_exclusive_scan(s);
+  const uint32_t off = offs ? offs[blockIdx.x] : 0u;
+  for (int k = threadIdx.x; k < SCAN_CHUNK; k += BLOCK) {
+    const int64_t i = base + k;
+    if (i < n) out[i] = s[k] + off;
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = off + total;
+}
+
+template <typename K>
+__device__ __forceinline__ uint32_t digit_of(K key, int shift, uint32_t mask) {
+  return (uint32_t)(key >> shift) & mask;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(BLOCK) k_radix_upsweep(const K* __restrict__ keys, int64_t n, int shift,
+                                                         uint32_t mask, uint32_t* __restrict__ hist, int nblocks) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * RS_CHUNK;
+  for (int k = threadIdx.x; k < RS_CHUNK; k += BLOCK) {
+    const int64_t i = base + k;
+    if (i < n) atomicAdd(&h[digit_of(keys[i], shift, mask)], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x <= mask) hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+template <typename K, bool HAS_VAL>
+constexpr size_t downsweep_smem() {
+  return sizeof(K) * RS_CHUNK + (HAS_VAL ? sizeof(uint32_t) * RS_CHUNK : 0);
+}
+
+// Stable scatter of one 4096-key chunk. Keys are ranked per warp (match_any peers), the
+// per-warp digit counts are scanned across warps and digits, the chunk is reordered by
+// digit in shared memory, and then written out so that consecutive threads store
+// consecutive keys of a digit run (coalesced).
+template <typename K, bool HAS_VAL>
+__global__ void __launch_bounds__(BLOCK) k_radix_downsweep(const K* __restrict__ kin, K* __restrict__ kout,
+                                                           const uint32_t* __restrict__ vin,
+                                                           uint32_t* __restrict__ vout, int64_t n, int shift,
+                                                           uint32_t mask, const uint32_t* __restrict__ offs,
+                                                           int nblocks) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  K* skeys = reinterpret_cast<K*>(dsm);
+  uint32_t* svals = reinterpret_cast<uint32_t*>(skeys + RS_CHUNK);
+  __shared__ uint32_t wh[RS_WARPS][256];
+  __shared__ uint32_t boff[256];
+  __shared__ uint32_t lstart[256];
+  __shared__ uint32_t wsum[RS_WARPS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int e = threadIdx.x; e < RS_WARPS * 256; e += BLOCK) (&wh[0][0])[e] = 0;
+  if (threadIdx.x <= mask) boff[threadIdx.x] = offs[(size_t)threadIdx.x * nblocks + blockIdx.x];
+  __syncthreads();
+  const int64_t cbase = (int64_t)blockIdx.x * RS_CHUNK;
+  const int64_t wbase = cbase + (int64_t)warp * 32 * RS_ITEMS;
+  const uint32_t lt = (1u << lane) - 1u;
+  K kk[RS_ITEMS];
+  uint32_t vv[RS_ITEMS];
+  uint32_t rk[RS_ITEMS];
+#pragma unroll
+  for (int it = 0; it < RS_ITEMS; ++it) {
+    const int64_t i = wbase + it * 32 + lane;
+    const bool valid = i < n;
+    const K key = valid ? kin[i] : (K)0;
+    if (HAS_VAL) vv[it] = valid ? vin[i] : 0u;
+    const uint32_t d = valid ? digit_of(key, shift, mask) : 0x100u + (uint32_t)lane;
+    const uint32_t peers = __match_any_sync(FULL, d);
+    const uint32_t before = valid ? wh[warp][d] : 0u;
+    __syncwarp();
+    if (valid && (peers & lt) == 0) wh[warp][d] = before + __popc(peers);
+    __syncwarp();
+    kk[it] = key;
+    rk[it] = valid ? before + __popc(peers & lt) : 0xFFFFFFFFu;
+  }
+  __syncthreads();
+  // per digit: exclusive scan across warps; digit totals -> exclusive scan across digits
+  uint32_t tot = 0;
+  {
+    const int d = threadIdx.x;
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w) {
+      const uint32_t c = wh[w][d];
+      wh[w][d] = tot;
+      tot += c;
+    }
+    uint32_t inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(FULL, inc, o);
+      if (lane >= o) inc += v;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    uint32_t base = 0;
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w)
+      if (w < warp) base += wsum[w];
+    lstart[d] = base + inc - tot;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < RS_ITEMS; ++it) {
+    if (rk[it] == 0xFFFFFFFFu) continue;
+    const uint32_t d = digit_of(kk[it], shift, mask);
+    const uint32_t lp = lstart[d] + wh[warp][d] + rk[it];
+    skeys[lp] = kk[it];
+    if (HAS_VAL) svals[lp] = vv[it];
+  }
+  __syncthreads();
+  const int cnt = (int)min((int64_t)RS_CHUNK, n - cbase);
+  for (int i = threadIdx.x; i < cnt; i += BLOCK) {
+    const K key = skeys[i];
+    const uint32_t d = digit_of(key, shift, mask);
+    const uint32_t pos = boff[d] + (uint32_t)i - lstart[d];
+    kout[pos] = key;
+    if (HAS_VAL) vout[pos] = svals[i];
+  }
+}
+
+int scan_blocks(int64_t n) { return (int)((n + SCAN_CHUNK - 1) / SCAN_CHUNK); }
+
+template <typename K, bool HAS_VAL>
+bool radix_sort_impl(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, int begin_bit, int end_bit,
+                     SortTemp& tmp, cudaStream_t st, cudaError_t* err) {
+  *err = cudaSuccess;
+  bool flipped = false;
+  if (n <= 1 || end_bit <= begin_bit) return false;
+  const int bits = end_bit - begin_bit;
+  const int passes = (bits + 7) / 8;
+  const int nblocks = (int)((n + RS_CHUNK - 1) / RS_CHUNK);
+  constexpr size_t smem = downsweep_smem<K, HAS_VAL>();
+  static bool attr_set[64] = {};  // per instantiation and device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+    *err = cudaFuncSetAttribute(k_radix_downsweep<K, HAS_VAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+    if (*err != cudaSuccess) return false;
+    if (dev >= 0 && dev < 64) attr_set[dev] = true;
+  }
+  int shift = begin_bit;
+  for (int p = 0; p < passes; ++p) {
+    const int pb = (bits - (shift - begin_bit) + (passes - p) - 1) / (passes - p);  // spread bits evenly
+    const uint32_t mask = (1u << pb) - 1u;
+    const int64_t m = (int64_t)(mask + 1) * nblocks;
+    K* kin = flipped ? k1 : k0;
+    K* kout = flipped ? k0 : k1;
+    uint32_t* vin = flipped ? v1 : v0;
+    uint32_t* vout = flipped ? v0 : v1;
+    k_radix_upsweep<K><<<nblocks, BLOCK, 0, st>>>(kin, n, shift, mask, tmp.hist, nblocks);
+    ++launch_counter();
+    *err = scan_exclusive_u32(tmp.hist, tmp.hist, m, tmp.scan_tmp, tmp.scan_cap, st);
+    if (*err != cudaSuccess) return flipped;
+    k_radix_downsweep<K, HAS_VAL><<<nblocks, BLOCK, smem, st>>>(kin, kout, vin, vout, n, shift, mask, tmp.hist,
+                                                                nblocks);
+    ++launch_counter();
+    *err = cudaGetLastError();
+    if (*err != cudaSuccess) return flipped;
+    flipped = !flipped;
+    shift += pb;
+  }
+  return flipped;
+}
+
+}  // namespace
+
+size_t scan_tmp_elems(int64_t n) {
+  // block sums of each level plus their scans, with room for the totals
+  size_t tot = 0;
+  int64_t m = n;
+  while (m > SCAN_CHUNK) {
+    const int64_t b = scan_blocks(m);
+    tot += 2 * (size_t)b + 2;
+    m = b;
+  }
+  return tot + 16;
+}
+
+size_t radix_hist_elems(int64_t n) {
+  const int64_t nblocks = (n + RS_CHUNK - 1) / RS_CHUNK;
+  return (size_t)256 * (size_t)(nblocks > 0 ? nblocks : 1) + 1;
+}
+
+cudaError_t scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, size_t tmp_cap,
+                               cudaStream_t st) {
+  if (n <= 0) {
+    return cudaMemsetAsync(out, 0, sizeof(uint32_t), st);
+  }
+  const int nb = scan_blocks(n);
+  if (nb == 1) {
+    k_scan_down<<<1, BLOCK, 0, st>>>(in, n, nullptr, out);
+    ++launch_counter();
+    return cudaGetLastError();
+  }
+  if ((size_t)(2 * nb + 2) > tmp_cap) return cudaErrorInvalidValue;
+  uint32_t* sums = tmp;
+  uint32_t* sums_scan = tmp + nb;  // nb + 1 slots
+  k_scan_reduce<<<nb, BLOCK, 0, st>>>(in, n, sums);
+  ++launch_counter();
+  cudaError_t e = scan_exclusive_u32(sums, sums_scan, nb, tmp + 2 * nb + 2, tmp_cap - (2 * nb + 2), st);
+  if (e != cudaSuccess) return e;
+  k_scan_down<<<nb, BLOCK, 0, st>>>(in, n, sums_scan, out);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+bool radix_sort_u32_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t n, int begin_bit,
+                          int end_bit, SortTemp& tmp, cudaStream_t st, cudaError_t* err) {
+  return radix_sort_impl<uint32_t, true>(k0, v0, k1, v1, n, begin_bit, end_bit, tmp, st, err);
+}
+
+bool radix_sort_u64_keys(uint64_t* k0, uint64_t* k1, int64_t n, int begin_bit, int end_bit, SortTemp& tmp,
+                         cudaStream_t st, cudaError_t* err) {
+  return radix_sort_impl<uint64_t, false>(k0, nullptr, k1, nullptr, n, begin_bit, end_bit, tmp, st, err);
+}
+
+bool radix_sort_u64_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int64_t n, int begin_bit,
+                          int end_bit, SortTemp& tmp, cudaStream_t st, cudaError_t* err) {
+  return radix_sort_impl<uint64_t, true>(k0, v0, k1, v1, n, begin_bit, end_bit, tmp, st, err);
+}
+
+}  // namespace qgs

@@ -1,0 +1,341 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Sizes: the 1,000-primitive 128x128 scene in full; the 300k-primitive 1600x1200 object
+scene in full on the GPU against oracle crops; the 3M-primitive 1297x840 scene in full on
+the GPU against bit-exact tile rectangles for every primitive, bit-exact lists of sampled
+tiles, sampled pixels and a gradient crop. Plus edge cases.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle.qgs_oracle as O
+from paper_2411_16392_gb300.scenes import (Camera, Scene, f32_to_bf16_bits, scene_object, scene_small,
+                                           scene_unbounded)
+from tests.parity_util import (MARGIN, assert_grads_close, assert_images_close, grad_mask,
+                               oracle_grads_with_spread)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2411_16392_gb300 import _lib as L
+    L.load()
+    return torch.device("cuda", 0)
+
+
+def _ras(dev, **kw):
+    from paper_2411_16392_gb300.render import Rasterizer
+    return Rasterizer(dev, **kw)
+
+
+def _ds(sc, dev):
+    from paper_2411_16392_gb300.render import DeviceScene
+    return DeviceScene.from_host(sc, dev)
+
+
+def _np(out):
+    return {k: v.detach().cpu().numpy() for k, v in out.items()}
+
+
+def _grad_images(H, W, seed, mask=None):
+    rng = np.random.default_rng(seed)
+    g = dict(rgb=rng.normal(size=(3, H, W)), alpha=rng.normal(size=(H, W)), depth=rng.normal(size=(H, W)),
+             normal=rng.normal(size=(3, H, W)))
+    if mask is not None:
+        for k in g:
+            g[k] = g[k] * mask
+    return {k: v.astype(np.float32).astype(np.float64) for k, v in g.items()}
+
+
+def _to_dev(g, dev):
+    return {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).to(dev) for k, v in g.items()}
+
+
+def _check_binning(ras, ref_bin, label):
+    keys, vals, ranges, rects = ras.binning()
+    vis = ref_bin.count > 0
+    want_rect = np.where(vis[:, None], ref_bin.rect, -1)
+    assert np.array_equal(rects, want_rect), label + ": tile rectangles differ"
+    if ref_bin.keys is not None:
+        assert keys.shape == ref_bin.keys.shape, label
+        assert np.array_equal(keys, ref_bin.keys), label + ": keys differ"
+        assert np.array_equal(vals, ref_bin.vals), label + ": values differ"
+        r = ranges.astype(np.int64)
+        empty = ref_bin.ranges[:, 1] == ref_bin.ranges[:, 0]
+        assert np.array_equal(r[~empty], ref_bin.ranges[~empty]), label + ": tile ranges differ"
+        assert np.all(r[empty, 1] == r[empty, 0]), label + ": empty tiles must have empty ranges"
+    return keys, vals, ranges, rects
+
+
+# ----------------------------------------------------------------------------- small scene
+@pytest.mark.parametrize("sort_mode", [0, 1])
+def test_small_scene_forward(dev, sort_mode):
+    sc, cam = scene_small(0, 1000)
+    ras = _ras(dev, sort_mode=sort_mode)
+    out = _np(ras.forward(_ds(sc, dev), cam))
+    ref = O.render(sc, cam)
+    _check_binning(ras, ref["binning"], f"small/mode{sort_mode}")
+    assert_images_close(out, ref, label=f"small/mode{sort_mode}")
+    T, nc = ras.residue()
+    ok = ref["margin"] > MARGIN
+    assert np.array_equal(nc[ok], ref["n_contrib"][ok])
+    assert np.abs(T - ref["T_final"])[ok].max() <= 1e-4
+    st = ras.stats()
+    print("stats", st, "oracle pair evals", int(ref["n_eval"].sum()))
+    amb_evals = int(np.abs(ref["n_eval"][~ok]).sum())
+    assert abs(st["pair_evals"] - int(ref["n_eval"].sum())) <= amb_evals + 256 * (~ok).sum()
+    assert st["n_instances"] == len(ref["binning"].keys)
+
+
+def test_sort_modes_bit_identical(dev):
+    sc, cam = scene_small(1, 1000)
+    outs = []
+    bins = []
+    for m in (0, 1):
+        ras = _ras(dev, sort_mode=m)
+        outs.append(_np(ras.forward(_ds(sc, dev), cam)))
+        bins.append(ras.binning())
+    for k in outs[0]:
+        assert np.array_equal(outs[0][k], outs[1][k]), k
+    for a, b in zip(bins[0], bins[1]):
+        assert np.array_equal(a, b)
+
+
+def test_small_scene_backward(dev):
+    sc, cam = scene_small(0, 1000)
+    ref0 = O.render(sc, cam)
+    mask, frac = grad_mask(ref0)
+    print("small/bwd excluded pixel fraction", frac)
+    assert frac < 0.01
+    g = _grad_images(cam.H, cam.W, 7, mask)
+    ref, spread = oracle_grads_with_spread(O, sc, cam, g)
+    ras = _ras(dev)
+    ds = _ds(sc, dev)
+    ras.forward(ds, cam)
+    gg = ras.backward(ds, cam, _to_dev(g, dev))
+    gg = {k: v.cpu().numpy() for k, v in gg.items()}
+    e = assert_grads_close(gg, ref["grads"], label="small/bwd", spread=spread,
+                           prim_cond=ref["prim_cond"])
+    for k, v in e.items():
+        assert v["widened"] < 0.01, (k, v)
+
+
+def test_autograd_function_matches_raw_backward(dev):
+    from paper_2411_16392_gb300.render import render
+    sc, cam = scene_small(2, 500)
+    ds = _ds(sc, dev)
+    ras = _ras(dev)
+    leaves = [t.clone().requires_grad_(True) for t in (ds.mean, ds.quat, ds.scale, ds.curv, ds.opacity)]
+    sh = ds.sh.view(torch.bfloat16).clone().requires_grad_(True)
+    rgb, alpha, depth, normal = render(ras, cam, *leaves, sh)
+    g = _to_dev(_grad_images(cam.H, cam.W, 3), dev)
+    loss = (rgb * g["rgb"]).sum() + (alpha * g["alpha"]).sum() + (depth * g["depth"]).sum() + \
+        (normal * g["normal"]).sum()
+    loss.backward()
+    raw = ras.backward(ds, cam, g) if ras.forward(ds, cam) is not None else None
+    for leaf, k in zip(leaves, ("mean", "quat", "scale", "curv", "opacity")):
+        assert torch.allclose(leaf.grad, raw[k], rtol=1e-5, atol=1e-7), k
+    assert torch.allclose(sh.grad.float(), raw["sh"].to(torch.bfloat16).float())
+
+
+# ----------------------------------------------------------------------------- edge cases
+def test_empty_and_culled_scenes(dev):
+    ras = _ras(dev)
+    cam = Camera(37, 23, 30.0, 30.0, 18.5, 11.5)
+    sc, _ = scene_small(0, 50)
+    empty = sc.subset(np.arange(0))
+    out = _np(ras.forward(_ds(empty, dev), cam))
+    assert all(np.all(v == 0) for v in out.values())
+    behind = sc.copy()
+    behind.mean[:, 2] = -behind.mean[:, 2]
+    out = _np(ras.forward(_ds(behind, dev), cam))
+    assert all(np.all(v == 0) for v in out.values())
+    assert ras.stats()["n_instances"] == 0
+
+
+def test_invalid_parameters_are_culled(dev):
+    sc, cam = scene_small(3, 300)
+    bad = sc.copy()
+    bad.mean[0, 0] = np.nan
+    bad.quat[1] = 0
+    bad.scale[2, 0] = 0
+    bad.opacity[3] = np.inf
+    ras = _ras(dev)
+    out = _np(ras.forward(_ds(bad, dev), cam))
+    ref = O.render(bad, cam)
+    _check_binning(ras, ref["binning"], "invalid")
+    assert not ref["binning"].visible[:4].any()
+    assert_images_close(out, ref, label="invalid")
+
+
+@pytest.mark.parametrize("W,H", [(1, 1), (17, 33), (129, 70)])
+def test_ragged_image_sizes(dev, W, H):
+    sc, _ = scene_small(4, 400)
+    cam = Camera(W, H, 128.0, 128.0, W / 2, H / 2)
+    ras = _ras(dev)
+    out = _np(ras.forward(_ds(sc, dev), cam))
+    ref = O.render(sc, cam)
+    _check_binning(ras, ref["binning"], f"ragged{W}x{H}")
+    assert_images_close(out, ref, max_amb=0.01, label=f"ragged{W}x{H}")
+
+
+def test_camera_inside_the_cloud_near_plane_clipping(dev):
+    sc, cam = scene_small(5, 1000)
+    sc.mean[:, 2] -= 3.6
+    sc.scale *= 4
+    cam = Camera(96, 80, 70.0, 70.0, 48.0, 40.0)
+    ras = _ras(dev)
+    ds = _ds(sc, dev)
+    out = _np(ras.forward(ds, cam))
+    ref = O.render(sc, cam)
+    _check_binning(ras, ref["binning"], "inside")
+    assert_images_close(out, ref, max_amb=0.01, label="inside")
+    mask, frac = grad_mask(ref)
+    print("inside/bwd excluded pixel fraction", frac)
+    assert frac < 0.02
+    g = _grad_images(cam.H, cam.W, 11, mask)
+    refg, spread = oracle_grads_with_spread(O, sc, cam, g)
+    gg = {k: v.cpu().numpy() for k, v in ras.backward(ds, cam, _to_dev(g, dev)).items()}
+    assert_grads_close(gg, refg["grads"], label="inside/bwd", spread=spread,
+                      prim_cond=refg["prim_cond"])
+
+
+def test_planar_primitives(dev):
+    """Zero and near-zero curvature (the 2DGS limit, and the near-planar share of the
+    unbounded scene)."""
+    sc, cam = scene_small(6, 800)
+    sc.curv[:400] = 0
+    sc.curv[400:] = (np.random.default_rng(0).uniform(-1e-6, 1e-6, (400, 2)) / sc.scale[400:]).astype(np.float32)
+    ras = _ras(dev)
+    ds = _ds(sc, dev)
+    out = _np(ras.forward(ds, cam))
+    ref = O.render(sc, cam)
+    assert_images_close(out, ref, label="planar")
+    mask, frac = grad_mask(ref)
+    assert frac < 0.01
+    g = _grad_images(cam.H, cam.W, 12, mask)
+    refg, spread = oracle_grads_with_spread(O, sc, cam, g)
+    gg = {k: v.cpu().numpy() for k, v in ras.backward(ds, cam, _to_dev(g, dev)).items()}
+    assert_grads_close(gg, refg["grads"], label="planar/bwd", spread=spread,
+                      prim_cond=refg["prim_cond"])
+
+
+# ----------------------------------------------------------------------------- 300k object scene
+@pytest.fixture(scope="module")
+def object_scene():
+    return scene_object(0)
+
+
+def test_object_scene_crop_forward_backward(dev, object_scene):
+    """Full 1600x1200 render and backward on the GPU; the oracle renders a tile-aligned
+    64x64 crop (lists from the full camera) with upstream gradients only there."""
+    sc, cam = object_scene
+    x0, y0, w = 768, 560, 64
+    binning = O.bin_fp32(sc, cam, emit=False)
+    TX = binning.tiles_x
+    tiles = [(y0 // 16 + j) * TX + (x0 // 16 + i) for j in range(w // 16) for i in range(w // 16)]
+    ras = _ras(dev)
+    ds = _ds(sc, dev)
+    out = _np(ras.forward(ds, cam))
+    keys, vals, ranges, rects = _check_binning(ras, binning, "object")
+    for t in tiles:
+        s, e = ranges[t]
+        assert np.array_equal(vals[s:e], O.tile_list(binning, t)), t
+    ref = O.render(sc, cam, binning, tiles=tiles)
+    crop = np.zeros((cam.H, cam.W), bool)
+    crop[y0:y0 + w, x0:x0 + w] = True
+    # strongly curved patches (|kappa| up to 20) make grazing silhouettes common
+    assert_images_close(out, ref, mask=crop, max_amb=0.03, label="object/crop")
+    mask, frac = grad_mask(ref, crop)
+    print("object/crop bwd excluded pixel fraction", frac)
+    assert frac < 0.03
+    g = _grad_images(cam.H, cam.W, 21, mask)
+    refg, spread = oracle_grads_with_spread(O, sc, cam, g, binning, tiles)
+    gg = {k: v.cpu().numpy() for k, v in ras.backward(ds, cam, _to_dev(g, dev)).items()}
+    touched = np.unique(np.concatenate([O.tile_list(binning, t) for t in tiles])).astype(np.int64)
+    assert_grads_close(gg, refg["grads"], idx=touched, label="object/crop bwd", spread=spread,
+                      prim_cond=refg["prim_cond"])
+    for k, v in gg.items():
+        assert np.isfinite(v).all(), k
+
+
+# ----------------------------------------------------------------------------- 3M unbounded scene
+@pytest.fixture(scope="module")
+def unbounded():
+    sc, cam = scene_unbounded(0)
+    return sc, cam, O.bin_fp32(sc, cam, emit=False)
+
+
+def test_unbounded_scene_full_size(dev, unbounded):
+    """3M primitives at 1297x840 (the benchmark workload): bit-exact tile rectangles for
+    all primitives, bit-exact sorted lists and keys of sampled tiles, sampled pixels
+    against the oracle one by one, and output invariants everywhere."""
+    sc, cam, binning = unbounded
+    ras = _ras(dev)
+    ds = _ds(sc, dev)
+    out = _np(ras.forward(ds, cam))
+    keys, vals, ranges, rects = _check_binning(ras, binning, "unbounded")
+    st = ras.stats()
+    assert st["n_instances"] == int(binning.count.sum())
+    rng = np.random.default_rng(0)
+    TX = binning.tiles_x
+    ntiles = TX * binning.tiles_y
+    sample_tiles = np.unique(np.concatenate([[0, ntiles - 1, ntiles // 2], rng.integers(0, ntiles, 12)]))
+    for t in sample_tiles:
+        s, e = ranges[t]
+        lst = O.tile_list(binning, t)
+        assert np.array_equal(vals[s:e], lst), t
+        want = (np.uint64(t) << np.uint64(32)) | binning.zbits[lst].astype(np.uint64)
+        assert np.array_equal(keys[s:e], want), t
+    pix = [(int(x), int(y)) for x, y in zip(rng.integers(0, cam.W, 40), rng.integers(0, cam.H, 40))]
+    pix += [(0, 0), (cam.W - 1, cam.H - 1), (cam.W // 2, cam.H // 2)]
+    ref = O.render_pixels(sc, cam, pix, binning)
+    xs = np.array([p[0] for p in pix])
+    ys = np.array([p[1] for p in pix])
+    got = dict(rgb=out["rgb"][:, ys, xs].T, alpha=out["alpha"][ys, xs], depth=out["depth"][ys, xs],
+               normal=out["normal"][:, ys, xs].T)
+    ok = ref["margin"] > MARGIN
+    print("unbounded sampled ambiguous", (~ok).sum(), "of", len(pix))
+    assert ok.mean() >= 0.9
+    assert np.abs(got["rgb"] - ref["rgb"])[ok].max() <= 1e-4
+    assert np.abs(got["alpha"] - ref["alpha"])[ok].max() <= 1e-4
+    assert np.abs(got["normal"] - ref["normal"])[ok].max() <= 1e-4
+    assert (np.abs(got["depth"] - ref["depth"]) / np.maximum(np.abs(ref["depth"]), 1e-6))[ok].max() <= 1e-4
+    T, nc = ras.residue()
+    assert np.array_equal(nc[ys, xs][ok], ref["n_contrib"][ok])
+    assert np.all((out["alpha"] >= 0) & (out["alpha"] <= 1))
+    assert np.allclose(T, 1 - out["alpha"], atol=1e-6)
+    assert all(np.isfinite(v).all() for v in out.values())
+
+
+def test_unbounded_scene_gradient_crop(dev, unbounded):
+    """Full-size backward at 3M primitives with upstream gradients on a 32x32 crop,
+    against the oracle's gradient of the same crop."""
+    sc, cam, binning = unbounded
+    x0, y0, w = 640, 416, 32
+    TX = binning.tiles_x
+    tiles = [(y0 // 16 + j) * TX + (x0 // 16 + i) for j in range(w // 16) for i in range(w // 16)]
+    ref0 = O.render(sc, cam, binning, tiles=tiles)
+    crop = np.zeros((cam.H, cam.W), bool)
+    crop[y0:y0 + w, x0:x0 + w] = True
+    mask, frac = grad_mask(ref0, crop)
+    print("unbounded/crop bwd excluded pixel fraction", frac)
+    assert frac < 0.02
+    g = _grad_images(cam.H, cam.W, 31, mask)
+    refg, spread = oracle_grads_with_spread(O, sc, cam, g, binning, tiles)
+    ras = _ras(dev)
+    ds = _ds(sc, dev)
+    out = _np(ras.forward(ds, cam))
+    assert_images_close(out, ref0, mask=crop, max_amb=0.02, label="unbounded/crop")
+    gg = {k: v.cpu().numpy() for k, v in ras.backward(ds, cam, _to_dev(g, dev)).items()}
+    touched = np.unique(np.concatenate([O.tile_list(binning, t) for t in tiles])).astype(np.int64)
+    assert_grads_close(gg, refg["grads"], idx=touched, label="unbounded/crop bwd", spread=spread,
+                      prim_cond=refg["prim_cond"])
+    untouched = np.setdiff1d(np.arange(sc.n), touched)[:100000]
+    for k, v in gg.items():
+        assert np.isfinite(v).all(), k
+        assert np.all(v[untouched] == 0), k
