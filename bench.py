@@ -173,7 +173,7 @@ def run_gpu(args):
     from paper_2411_16392_gb300.render import DeviceScene, Rasterizer
     from paper_2411_16392_gb300.scenes import scene_unbounded
 
-    sc, cam = scene_unbounded(0)
+    sc, cam = scene_unbounded(0, args.prims)
     ds = DeviceScene.from_host(sc, dev)
     ras = Rasterizer(dev)
     H, W = cam.H, cam.W
@@ -232,6 +232,20 @@ def run_gpu(args):
     value = world * P / (ms_max * 1e-3) / 1e6
 
     # ---- end to end through the public API with host buffers
+    if args.no_e2e:
+        e2e_value, h2d, d2h = None, 0, 0
+    else:
+        e2e_value, h2d, d2h = _e2e(args, ras, ds, cam, gout, grads, out, dev, world, P)
+    return _report(args, rank, world, sc, cam, st, stage, clk, ms_max, value, e2e_value, h2d, d2h)
+
+
+def _e2e(args, ras, ds, cam, gout, grads, out, dev, world, P):
+    import torch
+    import torch.distributed as dist
+    H, W = cam.H, cam.W
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
     host_g = {k: v.cpu().pin_memory() for k, v in gout.items()}
     host_rgb = torch.empty(3, H, W, pin_memory=True)
     dev_g = {k: torch.empty_like(v) for k, v in gout.items()}
@@ -261,7 +275,12 @@ def run_gpu(args):
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     e2e_value = world * P / (float(t.item()) * 1e-3) / 1e6
+    return e2e_value, h2d, d2h
 
+
+def _report(args, rank, world, sc, cam, st, stage, clk, ms_max, value, e2e_value, h2d, d2h):
+    import torch.distributed as dist
+    H, W = cam.H, cam.W
     # ---- roofline of the dominant kernel (FP32 ALU bound)
     peaks, peak_kind = _peaks()
     mean = {k: (sum(v) / len(v) if v and min(v) >= 0 else None) for k, v in stage.items()}
@@ -286,7 +305,8 @@ def run_gpu(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "primitives": sc.n, "width": W, "height": H,
+            "config": {"workload": WORKLOAD if sc.n == 3_000_000 else f"unbounded_{sc.n}_1297x840",
+                       "primitives": sc.n, "width": W, "height": H,
                        "visible": st["n_visible"], "instances": st["n_instances"],
                        "l2": "inputs larger than L2 (scene 432 MB, instances ~1 GB per frame)",
                        "parallelism": f"replicas x{world}"},
@@ -317,6 +337,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-tiles", type=int, default=2)
+    ap.add_argument("--prims", type=int, default=3_000_000,
+                    help="primitive count (the benchmark workload is 3,000,000; smaller counts are for profiling)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
