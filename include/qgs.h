@@ -192,6 +192,30 @@ qgs_status qgs_copy_binning(qgs_ctx* ctx, uint64_t* keys, uint32_t* vals, int64_
  * n_contrib (index + 1, within the pixel's tile list, of its last blended primitive). */
 qgs_status qgs_copy_residue(qgs_ctx* ctx, float* T_final, uint32_t* n_contrib);
 
+/* Forward render that allocates nothing. The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory at render time, e.g. a host
+ * process whose memory manager takes the GPU's memory in one pool at start-up and
+ * refuses other allocations, or a real-time loop that forbids cudaMalloc/cudaFree after
+ * warm-up because they can block and fragment memory. It computes the same images as
+ * render_forward with the default qgs_config (same kernels), but takes every work
+ * buffer from one statically sized device array (about 24 MB) that each GPU loading the
+ * library holds until the process exits; it calls no cudaMalloc, cudaFree or allocating
+ * library routine, and needs no context.
+ *   Limits: n <= 32768 primitives, W*H <= 262144 pixels, at most 4096 16x16 tiles, and at
+ *   most 1,048,576 (tile, primitive) instances in the frame; beyond them it returns
+ *   QGS_ECAPACITY (the instance count is known only after preprocessing, so that case is
+ *   reported after a synchronisation of `stream`, with `out` unspecified).
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *   with that device current; make that first call before any stream capture.
+ *   All calls in the process share the array and leave their contents in it (each call
+ *   clears what must start at zero): calls whose GPU work overlaps (concurrent streams,
+ *   host threads) race and corrupt each other's results; serialise them.
+ *   Scene/camera/output pointers follow the conventions above; the call synchronises
+ *   `stream` once. Errors: EINVAL, ECAPACITY, ECUDA. No per-call residue is kept, so
+ *   render_backward cannot follow it. */
+qgs_status render_forward_noalloc(const qgs_scene* scene, const qgs_camera* cam, const qgs_image* out,
+                                  qgs_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,9 +13,10 @@
 // final order equals the order of the 64-bit keys (tile << 32 | depth bits) with ties
 // broken by primitive index. sort_mode 1 instead emits the 64-bit keys in primitive
 // order and radix-sorts all of their significant bits.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <cmath>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -613,3 +614,150 @@ qgs_status qgs_copy_residue(qgs_ctx* ctx, float* T_final, uint32_t* n_contrib) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// render_forward_noalloc: the forward render with every work buffer carved out of one
+// statically sized device array (no cudaMalloc, cudaFree or allocating library call).
+// It runs the same kernels as render_forward, with fixed capacities.
+namespace {
+
+constexpr int64_t NA_MAX_PRIMS = 32768;
+constexpr int64_t NA_MAX_PIXELS = 262144;     // e.g. 512 x 512
+constexpr int64_t NA_MAX_TILES = 4096;
+constexpr int64_t NA_MAX_INSTANCES = 1 << 20;  // (tile, primitive) pairs per frame
+
+constexpr size_t na_align(size_t b) { return (b + 255) & ~(size_t)255; }
+constexpr size_t NA_HIST = (size_t)256 * ((NA_MAX_INSTANCES + 4095) / 4096) + 1;  // radix histogram (u32)
+constexpr size_t NA_SCAN = 8192;                                                  // scan block sums (u32)
+// byte offsets of each region inside the array
+constexpr size_t NA_OFF_STATE = 0;
+constexpr size_t NA_OFF_COUNT = NA_OFF_STATE + na_align(sizeof(PrimState) * NA_MAX_PRIMS);
+constexpr size_t NA_OFF_ZKEY = NA_OFF_COUNT + na_align(4 * NA_MAX_PRIMS);
+constexpr size_t NA_OFF_IDX = NA_OFF_ZKEY + na_align(4 * NA_MAX_PRIMS);
+constexpr size_t NA_OFF_ZKEY2 = NA_OFF_IDX + na_align(4 * NA_MAX_PRIMS);
+constexpr size_t NA_OFF_IDX2 = NA_OFF_ZKEY2 + na_align(4 * NA_MAX_PRIMS);
+constexpr size_t NA_OFF_CNT = NA_OFF_IDX2 + na_align(4 * NA_MAX_PRIMS);
+constexpr size_t NA_OFF_OFFS = NA_OFF_CNT + na_align(4 * NA_MAX_PRIMS);
+constexpr size_t NA_OFF_RECT = NA_OFF_OFFS + na_align(4 * (NA_MAX_PRIMS + 1));
+constexpr size_t NA_OFF_INST = NA_OFF_RECT + na_align(sizeof(short4) * NA_MAX_PRIMS);
+constexpr size_t NA_OFF_INST2 = NA_OFF_INST + na_align(8 * NA_MAX_INSTANCES);
+constexpr size_t NA_OFF_RANGES = NA_OFF_INST2 + na_align(8 * NA_MAX_INSTANCES);
+constexpr size_t NA_OFF_TFIN = NA_OFF_RANGES + na_align(sizeof(uint2) * NA_MAX_TILES);
+constexpr size_t NA_OFF_NCON = NA_OFF_TFIN + na_align(4 * NA_MAX_PIXELS);
+constexpr size_t NA_OFF_HIST = NA_OFF_NCON + na_align(4 * NA_MAX_PIXELS);
+constexpr size_t NA_OFF_SCAN = NA_OFF_HIST + na_align(4 * NA_HIST);
+constexpr size_t NA_OFF_STATS = NA_OFF_SCAN + na_align(4 * NA_SCAN);
+constexpr size_t NA_OFF_VIS = NA_OFF_STATS + na_align(sizeof(RasterStats));
+constexpr size_t NA_BYTES = NA_OFF_VIS + na_align(16);
+
+// The scratch itself (about 24 MB). Every GPU that loads the library holds it until the
+// process exits. Host code must not use this name as a device address.
+__device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+std::mutex g_na_mutex;
+unsigned char* g_na_ptr[64] = {};  // device address of the array, per device
+
+}  // namespace
+
+extern "C" qgs_status render_forward_noalloc(const qgs_scene* scene, const qgs_camera* cam, const qgs_image* out,
+                                             qgs_stream stream) {
+  qgs_ctx* ctx = nullptr;  // QGS_CU needs the name; there is no context here
+  if (!scene || !cam || !out) return QGS_EINVAL;
+  if (scene->n < 0) return QGS_EINVAL;
+  if (scene->n > 0 && (!scene->mean || !scene->quat || !scene->scale || !scene->curv || !scene->opacity ||
+                       !scene->sh))
+    return QGS_EINVAL;
+  if (scene->n > 0 && ((((uintptr_t)scene->quat) & 15) || (((uintptr_t)scene->sh) & 15) ||
+                       (((uintptr_t)scene->scale) & 7) || (((uintptr_t)scene->curv) & 7)))
+    return QGS_EINVAL;
+  if (cam->W <= 0 || cam->H <= 0 || !finite_cam(cam)) return QGS_EINVAL;
+  if (!out->rgb || !out->alpha || !out->depth || !out->normal) return QGS_EINVAL;
+  const int64_t N = scene->n;
+  const int64_t P = (int64_t)cam->W * cam->H;
+  const int64_t TX = (cam->W + TILE - 1) / TILE, TY = (cam->H + TILE - 1) / TILE;
+  if (N > NA_MAX_PRIMS || P > NA_MAX_PIXELS || TX * TY > NA_MAX_TILES) return QGS_ECAPACITY;
+
+  int dev = 0;
+  QGS_CU(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev < 0 || dev >= 64) return QGS_EINVAL;
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_ptr[dev]) {
+      void* p = nullptr;
+      QGS_CU(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress");
+      g_na_ptr[dev] = static_cast<unsigned char*>(p);
+    }
+    base = g_na_ptr[dev];
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  PrimState* state = reinterpret_cast<PrimState*>(base + NA_OFF_STATE);
+  uint32_t* count = reinterpret_cast<uint32_t*>(base + NA_OFF_COUNT);
+  uint32_t* zkey = reinterpret_cast<uint32_t*>(base + NA_OFF_ZKEY);
+  uint32_t* idx = reinterpret_cast<uint32_t*>(base + NA_OFF_IDX);
+  uint32_t* zkey2 = reinterpret_cast<uint32_t*>(base + NA_OFF_ZKEY2);
+  uint32_t* idx2 = reinterpret_cast<uint32_t*>(base + NA_OFF_IDX2);
+  uint32_t* cnt_sorted = reinterpret_cast<uint32_t*>(base + NA_OFF_CNT);
+  uint32_t* offs = reinterpret_cast<uint32_t*>(base + NA_OFF_OFFS);
+  short4* rect = reinterpret_cast<short4*>(base + NA_OFF_RECT);
+  uint64_t* inst = reinterpret_cast<uint64_t*>(base + NA_OFF_INST);
+  uint64_t* inst2 = reinterpret_cast<uint64_t*>(base + NA_OFF_INST2);
+  uint2* ranges = reinterpret_cast<uint2*>(base + NA_OFF_RANGES);
+  float* T_final = reinterpret_cast<float*>(base + NA_OFF_TFIN);
+  uint32_t* n_contrib = reinterpret_cast<uint32_t*>(base + NA_OFF_NCON);
+  SortTemp tmp;
+  tmp.hist = reinterpret_cast<uint32_t*>(base + NA_OFF_HIST);
+  tmp.hist_cap = NA_HIST;
+  tmp.scan_tmp = reinterpret_cast<uint32_t*>(base + NA_OFF_SCAN);
+  tmp.scan_cap = NA_SCAN;
+  RasterStats* stats = reinterpret_cast<RasterStats*>(base + NA_OFF_STATS);
+  uint32_t* visible = reinterpret_cast<uint32_t*>(base + NA_OFF_VIS);
+
+  qgs_config cfg;
+  qgs_config_default(&cfg);
+  qgs_ctx defaults;
+  defaults.cfg = cfg;
+  CamParams cp;
+  RasterParams rp;
+  make_params(&defaults, cam, cp, rp);
+  const int64_t ntiles = TX * TY;
+
+  // everything that must start at zero: the visible counter, tile ranges, counters
+  QGS_CU(cudaMemsetAsync(visible, 0, 16, st), "memset");
+  QGS_CU(cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)ntiles, st), "memset");
+  QGS_CU(cudaMemsetAsync(stats, 0, sizeof(RasterStats), st), "memset");
+  SceneView sv{scene->mean, scene->quat, scene->scale, scene->curv, scene->opacity, scene->sh};
+  if (N > 0) {
+    k_preprocess<<<nblk(N), 256, 0, st>>>(N, sv, cp, state, count, zkey, idx, rect, visible);
+    QGS_CU(cudaGetLastError(), "k_preprocess");
+  }
+  cudaError_t e = cudaSuccess;
+  const bool fl = radix_sort_u32_pairs(zkey, idx, zkey2, idx2, N, 0, 32, tmp, st, &e);
+  QGS_CU(e, "depth sort");
+  const uint32_t* sidx = fl ? idx2 : idx;
+  if (N > 0) {
+    k_gather_u32<<<nblk(N), 256, 0, st>>>(N, sidx, count, cnt_sorted);
+    QGS_CU(cudaGetLastError(), "gather");
+  }
+  QGS_CU(scan_exclusive_u32(cnt_sorted, offs, N, tmp.scan_tmp, tmp.scan_cap, st), "scan");
+  uint32_t total = 0;  // pageable host word: a copy, not an allocation
+  QGS_CU(cudaMemcpyAsync(&total, offs + N, sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "total");
+  QGS_CU(cudaStreamSynchronize(st), "sync");
+  const int64_t I = (int64_t)total;
+  if (I > NA_MAX_INSTANCES) return QGS_ECAPACITY;
+  const uint64_t* sorted = inst;
+  if (N > 0 && I > 0) {
+    k_emit<<<nblk(N), 256, 0, st>>>(N, sidx, count, rect, offs, nullptr, cp.tiles_x, inst, nullptr);
+    QGS_CU(cudaGetLastError(), "emit");
+    const bool f2 = radix_sort_u64_keys(inst, inst2, I, 32, 32 + bits_for(ntiles), tmp, st, &e);
+    QGS_CU(e, "tile sort");
+    sorted = f2 ? inst2 : inst;
+    k_tile_ranges<<<nblk(I), 256, 0, st>>>(I, sorted, ranges);
+    QGS_CU(cudaGetLastError(), "ranges");
+  }
+  k_raster_fwd<<<(unsigned)ntiles, BLOCK, 0, st>>>(ranges, reinterpret_cast<const uint32_t*>(sorted), 2, state, rp,
+                                                   out->rgb, out->alpha, out->depth, out->normal, T_final,
+                                                   n_contrib, stats);
+  QGS_CU(cudaGetLastError(), "k_raster_fwd");
+  return QGS_OK;
+}
