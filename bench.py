@@ -158,6 +158,56 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- GPU
+def serve_measure(dev_index, ds, n_req, lam, slots, seed=0, budget=64 << 30):
+    """Open-loop serving run: Poisson arrivals at `lam` requests/s, cameras on a radius-2
+    orbit with resolutions drawn from {256^2, 512x384, 1024x768, 1920x1080}; returns the
+    server's latency statistics (submit -> result ready on the device)."""
+    import threading
+    import numpy as np
+    from paper_2411_16392_gb300.scenes import orbit_camera
+    from paper_2411_16392_gb300.serve import Server
+    rng = np.random.default_rng(seed)
+    cams = [orbit_camera(rng) for _ in range(n_req)]
+    gaps = rng.exponential(1.0 / lam, n_req)
+    srv = Server(dev_index, budget_bytes=budget, slots=slots, queue=max(64, n_req))
+    sid = srv.load_scene(ds)
+    for cam in cams[:4]:                        # warm-up (buffers, kernels)
+        srv.wait(srv.submit(sid, cam))
+    srv.reset_stats()
+    tickets = []
+    lock = threading.Lock()
+    done = threading.Event()
+
+    def waiter():
+        k = 0
+        while k < n_req:
+            with lock:
+                have = len(tickets)
+            if k < have:
+                srv.wait(tickets[k])
+                k += 1
+            else:
+                time.sleep(0.0002)
+        done.set()
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    t0 = time.perf_counter()
+    t_next = t0
+    for cam, gap in zip(cams, gaps):
+        t_next += gap
+        dt = t_next - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        t = srv.submit(sid, cam)
+        with lock:
+            tickets.append(t)
+    th.join()
+    st = srv.stats()
+    srv.close()
+    return {k: st[k] for k in ("p50_ms", "p99_ms", "mean_ms", "frames_per_s", "completed", "max_in_flight")}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -318,6 +368,8 @@ def _report(args, rank, world, sc, cam, st, stage, clk, ms_max, value, e2e_value
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int((st["launches_fwd"] + st["launches_bwd"]) * args.steps),
             "clocks": clk}
+    if rank == 0 and world == 1 and args.serve_requests > 0:
+        line["serving"] = _serving_leg(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(sc, cam, args.cpu_tiles)
         line["cpu_baseline"].pop("frame_s_extrapolated", None)
@@ -327,6 +379,23 @@ def _report(args, rank, world, sc, cam, st, stage, clk, ms_max, value, e2e_value
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def _serving_leg(args):
+    """Served p50/p99 latency and frames/s of the 1M-quadric serving workload: plain
+    one-at-a-time (1 slot) against continuous batching (args.serve_slots slots), same
+    arrival process."""
+    import torch
+    from paper_2411_16392_gb300.render import DeviceScene
+    from paper_2411_16392_gb300.scenes import serving_scene
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ds = DeviceScene.from_host(serving_scene(0, 1_000_000), dev)
+    res = {"workload": "serving_1m_mixed_res", "arrival_rate_per_s": args.serve_rate,
+           "requests": args.serve_requests}
+    for name, slots in (("one_at_a_time", 1), ("batched", args.serve_slots)):
+        res[name] = serve_measure(dev.index, ds, args.serve_requests, args.serve_rate, slots)
+    del ds
+    return res
 
 
 def main():
@@ -340,6 +409,9 @@ def main():
     ap.add_argument("--prims", type=int, default=3_000_000,
                     help="primitive count (the benchmark workload is 3,000,000; smaller counts are for profiling)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--serve-requests", type=int, default=600, help="requests per serving run (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, requests/s")
+    ap.add_argument("--serve-slots", type=int, default=4)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

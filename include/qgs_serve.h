@@ -1,0 +1,79 @@
+/*
+ * qgs_serve.h - serving loop of the quadric Gaussian splatting rasterizer.
+ *
+ * The paper renders one view at a time during training (Sec. 4.1); serving novel views
+ * of resident scenes is this library's own layer around the same forward render
+ * (include/qgs.h: render_forward, Sec. 3.1-3.2 and the supplementary). It implements
+ * continuous batching:
+ *   - scenes are copied once into server-owned device memory (serve_load_scene);
+ *   - serve_submit enqueues a view request and returns at once (bounded FIFO queue);
+ *   - worker slots, each with its own rendering context and CUDA stream, take requests
+ *     from the head of the queue as soon as a slot is free AND the request's estimated
+ *     memory (projected primitives, tile keys and their sort buffers, residue, result
+ *     planes) fits in the remaining HBM budget; requests that arrive while others run
+ *     are admitted as slots and memory free up, and their kernels overlap on the GPU;
+ *   - serve_wait returns a finished result (host or device destination) with a bounded
+ *     wait; serve_stats reports p50/p99 latency (submit to result ready) and frames/s.
+ * All functions are thread-safe. Status codes as in qgs.h; nothing aborts.
+ */
+#ifndef QGS_SERVE_H_
+#define QGS_SERVE_H_
+
+#include "qgs.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qgs_server qgs_server;
+
+typedef struct {
+  int64_t submitted;       /* accepted by serve_submit */
+  int64_t completed;       /* finished (ok or failed) */
+  int64_t failed;          /* finished with an error status */
+  int64_t rejected;        /* refused by serve_submit (queue full: QGS_EBUSY) */
+  int64_t max_in_flight;   /* most requests running at once */
+  double p50_ms, p99_ms, mean_ms;  /* latency submit -> result ready, completed requests */
+  double frames_per_s;     /* completed / (last completion - first submission) */
+  int64_t bytes_budget;    /* HBM budget given to serve_create */
+  int64_t bytes_reserved_peak; /* most estimated bytes admitted at once */
+} qgs_serve_stats;
+
+/* Create a server on CUDA device `device` with `max_slots` worker slots (1 = plain
+ * one-request-at-a-time), a queue of `queue_capacity` requests and an HBM budget for
+ * in-flight requests. device = -1 creates a host-only server whose workers do not
+ * touch a GPU and take `fake_us_per_mpix` microseconds per million pixels per request
+ * (for testing the queue, admission and accounting without a GPU; results are zero).
+ * Errors: EINVAL, ECUDA, ENOMEM. */
+qgs_status serve_create(qgs_server** out, int32_t device, int64_t hbm_budget_bytes, int32_t max_slots,
+                        int32_t queue_capacity, double fake_us_per_mpix);
+
+/* Stop the workers after the running requests finish, drop queued requests, free
+ * everything. NULL is ignored. */
+void serve_destroy(qgs_server* srv);
+
+/* Copy a scene (device pointers, layouts of qgs_scene) into server-owned device memory;
+ * *scene_id receives its id. Not counted in the per-request budget. Errors: EINVAL,
+ * ENOMEM, ECUDA. */
+qgs_status serve_load_scene(qgs_server* srv, const qgs_scene* scene, int32_t* scene_id);
+
+/* Enqueue a forward render of scene `scene_id` from `cam`; returns immediately with a
+ * ticket. Errors: EINVAL (bad camera or size), ENOTFOUND (scene), EBUSY (queue full),
+ * ECAPACITY (the request alone exceeds the budget). */
+qgs_status serve_submit(qgs_server* srv, int32_t scene_id, const qgs_camera* cam, uint64_t* ticket);
+
+/* Wait up to timeout_ms (< 0: no limit) for a ticket to finish, then copy its planes
+ * into `out` (rgb 3HW, alpha HW, depth HW, normal 3HW floats; any plane may be NULL;
+ * host or device pointers) and release the ticket. Errors: ENOTFOUND (unknown or
+ * already released ticket), ETIMEDOUT (still running; the ticket stays valid), the
+ * request's own error status, ECUDA. */
+qgs_status serve_wait(qgs_server* srv, uint64_t ticket, int32_t timeout_ms, const qgs_image* out);
+
+/* Statistics since creation or the last serve_reset_stats. */
+qgs_status serve_stats(qgs_server* srv, qgs_serve_stats* stats);
+qgs_status serve_reset_stats(qgs_server* srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QGS_SERVE_H_ */

@@ -230,6 +230,10 @@ int bits_for(int64_t v) {
 
 }  // namespace
 
+namespace qgs {
+int64_t last_instance_count(const qgs_ctx* ctx) { return ctx ? ctx->n_inst : 0; }
+}  // namespace qgs
+
 extern "C" {
 
 void qgs_config_default(qgs_config* cfg) {

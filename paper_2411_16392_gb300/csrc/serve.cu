@@ -1,0 +1,398 @@
+// Serving loop: resident scenes, bounded FIFO queue, memory-budget admission, worker
+// slots with their own rendering context and stream (continuous batching: requests are
+// admitted as slots and budget free up, and the kernels of in-flight requests overlap).
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/qgs_serve.h"
+#include "qgs_internal.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct SceneDev {
+  int64_t n = 0;
+  float *mean = nullptr, *quat = nullptr, *scale = nullptr, *curv = nullptr, *opacity = nullptr;
+  uint16_t* sh = nullptr;
+  double inst_per_pixel = 64.0;  // running estimate of tile instances per pixel
+};
+
+struct Request {
+  uint64_t ticket = 0;
+  int32_t scene = 0;
+  SceneDev scn;  // copy of the scene's pointers taken at submission
+  qgs_camera cam{};
+  Clock::time_point t_submit, t_done;
+  int state = 0;  // 0 queued, 1 running, 2 done
+  qgs_status status = QGS_OK;
+  int64_t est_bytes = 0;
+  float* result = nullptr;       // 8 planes of W*H floats (device, or host in fake mode)
+  bool result_on_host = false;
+};
+
+struct Slot {
+  qgs_ctx* ctx = nullptr;
+  cudaStream_t stream = nullptr;
+  std::thread th;
+};
+
+int64_t request_bytes(const SceneDev& s, const qgs_camera& c) {
+  const double P = (double)c.W * c.H;
+  const double inst = s.inst_per_pixel * P;
+  // projected state + per-primitive keys/indices/offsets, instance ping-pong buffers,
+  // radix histogram, residue, and the 8 result planes
+  return (int64_t)(s.n * 168.0 + inst * 16.0 + inst / 16.0 + P * 8.0 + P * 32.0) + (1 << 20);
+}
+
+}  // namespace
+
+namespace qgs {
+// defined in api.cu: instance count of the context's last forward
+int64_t last_instance_count(const qgs_ctx* ctx);
+}  // namespace qgs
+
+struct qgs_server {
+  int device = 0;
+  bool fake = false;
+  double fake_us_per_mpix = 0;
+  int64_t budget = 0;
+  int queue_cap = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request*> queue;
+  std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
+  std::deque<SceneDev> scenes;  // references stay valid as scenes are added
+  std::vector<Slot> slots;
+  cudaStream_t copy_stream = nullptr;
+  uint64_t next_ticket = 1;
+  int64_t reserved = 0;
+  int running = 0;
+  bool stop = false;
+  // statistics
+  std::vector<double> lat_ms;
+  int64_t submitted = 0, completed = 0, failed = 0, rejected = 0, max_in_flight = 0, reserved_peak = 0;
+  bool have_first = false;
+  Clock::time_point t_first, t_last;
+
+  void worker(int slot_index);
+  void run_one(Slot& s, Request* r);
+};
+
+void qgs_server::run_one(Slot& s, Request* r) {
+  const int64_t P = (int64_t)r->cam.W * r->cam.H;
+  if (fake) {
+    r->result = static_cast<float*>(calloc((size_t)P * 8, sizeof(float)));
+    r->result_on_host = true;
+    if (!r->result) {
+      r->status = QGS_ENOMEM;
+      return;
+    }
+    const double us = fake_us_per_mpix * (double)P / 1e6;
+    std::this_thread::sleep_for(std::chrono::microseconds((int64_t)us));
+    r->status = QGS_OK;
+    return;
+  }
+  cudaSetDevice(device);
+  const SceneDev& sc = r->scn;
+  void* buf = nullptr;
+  cudaError_t e = cudaMallocAsync(&buf, sizeof(float) * 8 * (size_t)P, s.stream);
+  if (e != cudaSuccess) {
+    r->status = e == cudaErrorMemoryAllocation ? QGS_ENOMEM : QGS_ECUDA;
+    return;
+  }
+  r->result = static_cast<float*>(buf);
+  qgs_scene scn{sc.n, sc.mean, sc.quat, sc.scale, sc.curv, sc.opacity, sc.sh};
+  qgs_image img{r->result, r->result + 3 * P, r->result + 4 * P, r->result + 5 * P};
+  r->status = render_forward(s.ctx, &scn, &r->cam, &img, s.stream);
+  if (r->status == QGS_OK && cudaStreamSynchronize(s.stream) != cudaSuccess) r->status = QGS_ECUDA;
+  if (r->status == QGS_OK) {
+    const int64_t inst = qgs::last_instance_count(s.ctx);
+    std::lock_guard<std::mutex> lk(mu);
+    SceneDev& sd = scenes[r->scene];
+    sd.inst_per_pixel = 0.7 * sd.inst_per_pixel + 0.3 * ((double)inst / (double)std::max<int64_t>(P, 1));
+  }
+}
+
+void qgs_server::worker(int si) {
+  Slot& s = slots[si];
+  if (!fake) cudaSetDevice(device);
+  for (;;) {
+    Request* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      cv_work.wait(lk, [&] {
+        if (stop) return true;
+        if (queue.empty()) return false;
+        // FIFO head is admitted when it fits in the remaining budget (or nothing runs)
+        return running == 0 || reserved + queue.front()->est_bytes <= budget;
+      });
+      if (stop) return;
+      r = queue.front();
+      queue.pop_front();
+      r->state = 1;
+      reserved += r->est_bytes;
+      ++running;
+      max_in_flight = std::max<int64_t>(max_in_flight, running);
+      reserved_peak = std::max(reserved_peak, reserved);
+    }
+    run_one(s, r);
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      r->t_done = Clock::now();
+      r->state = 2;
+      reserved -= r->est_bytes;
+      --running;
+      ++completed;
+      if (r->status != QGS_OK) ++failed;
+      lat_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+      t_last = r->t_done;
+    }
+    cv_done.notify_all();
+    cv_work.notify_all();
+  }
+}
+
+extern "C" {
+
+qgs_status serve_create(qgs_server** out, int32_t device, int64_t hbm_budget_bytes, int32_t max_slots,
+                        int32_t queue_capacity, double fake_us_per_mpix) {
+  if (!out || max_slots < 1 || max_slots > 64 || queue_capacity < 1 || hbm_budget_bytes <= 0) return QGS_EINVAL;
+  *out = nullptr;
+  std::unique_ptr<qgs_server> s(new (std::nothrow) qgs_server());
+  if (!s) return QGS_ENOMEM;
+  s->device = device;
+  s->fake = device < 0;
+  s->fake_us_per_mpix = fake_us_per_mpix;
+  s->budget = hbm_budget_bytes;
+  s->queue_cap = queue_capacity;
+  s->slots.resize(max_slots);
+  if (!s->fake) {
+    if (cudaSetDevice(device) != cudaSuccess) return QGS_ECUDA;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;  // keep freed result buffers cached in the pool
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    if (cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) != cudaSuccess) return QGS_ECUDA;
+    for (auto& sl : s->slots) {
+      qgs_status st = qgs_create(&sl.ctx, nullptr, device);
+      if (st != QGS_OK) {
+        for (auto& t : s->slots) {
+          if (t.ctx) qgs_destroy(t.ctx);
+          if (t.stream) cudaStreamDestroy(t.stream);
+        }
+        cudaStreamDestroy(s->copy_stream);
+        return st;
+      }
+      if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess) return QGS_ECUDA;
+    }
+  }
+  qgs_server* raw = s.release();
+  for (int i = 0; i < max_slots; ++i) raw->slots[i].th = std::thread(&qgs_server::worker, raw, i);
+  *out = raw;
+  return QGS_OK;
+}
+
+void serve_destroy(qgs_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  for (auto& sl : s->slots)
+    if (sl.th.joinable()) sl.th.join();
+  if (!s->fake) cudaSetDevice(s->device);
+  for (auto& kv : s->reqs) {
+    Request* r = kv.second.get();
+    if (r->result) {
+      if (r->result_on_host)
+        free(r->result);
+      else
+        cudaFree(r->result);
+    }
+  }
+  for (auto& sl : s->slots) {
+    if (sl.ctx) qgs_destroy(sl.ctx);
+    if (sl.stream) cudaStreamDestroy(sl.stream);
+  }
+  if (!s->fake) {
+    for (auto& sc : s->scenes) {
+      cudaFree(sc.mean); cudaFree(sc.quat); cudaFree(sc.scale); cudaFree(sc.curv); cudaFree(sc.opacity);
+      cudaFree(sc.sh);
+    }
+  }
+  if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+  delete s;
+}
+
+qgs_status serve_load_scene(qgs_server* s, const qgs_scene* sc, int32_t* scene_id) {
+  if (!s || !sc || !scene_id || sc->n < 0 || sc->n > (int64_t)0x7FFFFFFF) return QGS_EINVAL;
+  SceneDev d;
+  d.n = sc->n;
+  if (!s->fake && sc->n > 0) {
+    if (!sc->mean || !sc->quat || !sc->scale || !sc->curv || !sc->opacity || !sc->sh) return QGS_EINVAL;
+    cudaSetDevice(s->device);
+    const size_t n = (size_t)sc->n;
+    struct Item {
+      void** dst;
+      const void* src;
+      size_t bytes;
+    } items[] = {{(void**)&d.mean, sc->mean, 12 * n},  {(void**)&d.quat, sc->quat, 16 * n},
+                 {(void**)&d.scale, sc->scale, 8 * n}, {(void**)&d.curv, sc->curv, 8 * n},
+                 {(void**)&d.opacity, sc->opacity, 4 * n}, {(void**)&d.sh, sc->sh, 96 * n}};
+    for (auto& it : items) {
+      if (cudaMalloc(it.dst, it.bytes) != cudaSuccess) {
+        for (auto& jt : items)
+          if (*jt.dst) cudaFree(*jt.dst);
+        return QGS_ENOMEM;
+      }
+      if (cudaMemcpy(*it.dst, it.src, it.bytes, cudaMemcpyDefault) != cudaSuccess) {
+        for (auto& jt : items)
+          if (*jt.dst) cudaFree(*jt.dst);
+        return QGS_ECUDA;
+      }
+    }
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->scenes.push_back(d);
+  *scene_id = (int32_t)s->scenes.size() - 1;
+  return QGS_OK;
+}
+
+qgs_status serve_submit(qgs_server* s, int32_t scene_id, const qgs_camera* cam, uint64_t* ticket) {
+  if (!s || !cam || !ticket) return QGS_EINVAL;
+  if (cam->W <= 0 || cam->H <= 0 || cam->W > 32768 || cam->H > 32768 || !(cam->fx > 0) || !(cam->fy > 0) ||
+      !(cam->near_plane > 0))
+    return QGS_EINVAL;
+  std::unique_ptr<Request> r(new (std::nothrow) Request());
+  if (!r) return QGS_ENOMEM;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (scene_id < 0 || scene_id >= (int32_t)s->scenes.size()) return QGS_ENOTFOUND;
+    if ((int)s->queue.size() >= s->queue_cap) {
+      ++s->rejected;
+      return QGS_EBUSY;
+    }
+    r->scn = s->scenes[scene_id];
+    r->est_bytes = request_bytes(r->scn, *cam);
+    if (r->est_bytes > s->budget) {
+      ++s->rejected;
+      return QGS_ECAPACITY;
+    }
+    r->ticket = s->next_ticket++;
+    r->scene = scene_id;
+    r->cam = *cam;
+    r->t_submit = Clock::now();
+    if (!s->have_first) {
+      s->have_first = true;
+      s->t_first = r->t_submit;
+    }
+    ++s->submitted;
+    *ticket = r->ticket;
+    s->queue.push_back(r.get());
+    s->reqs.emplace(r->ticket, std::move(r));
+  }
+  s->cv_work.notify_one();
+  return QGS_OK;
+}
+
+qgs_status serve_wait(qgs_server* s, uint64_t ticket, int32_t timeout_ms, const qgs_image* out) {
+  if (!s) return QGS_EINVAL;
+  Request* r = nullptr;
+  {
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return QGS_ENOTFOUND;
+    r = it->second.get();
+    auto done = [&] { return r->state == 2; };
+    if (timeout_ms < 0) {
+      s->cv_done.wait(lk, done);
+    } else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done)) {
+      return QGS_ETIMEDOUT;
+    }
+  }
+  qgs_status st = r->status;
+  const size_t P = (size_t)r->cam.W * r->cam.H;
+  if (st == QGS_OK && out && r->result) {
+    float* planes[4] = {out->rgb, out->alpha, out->depth, out->normal};
+    const size_t off[4] = {0, 3 * P, 4 * P, 5 * P};
+    const size_t cnt[4] = {3 * P, P, P, 3 * P};
+    if (r->result_on_host) {
+      for (int k = 0; k < 4; ++k)
+        if (planes[k]) {
+          if (s->fake)
+            memcpy(planes[k], r->result + off[k], sizeof(float) * cnt[k]);
+        }
+    } else {
+      cudaSetDevice(s->device);
+      for (int k = 0; k < 4 && st == QGS_OK; ++k)
+        if (planes[k] &&
+            cudaMemcpyAsync(planes[k], r->result + off[k], sizeof(float) * cnt[k], cudaMemcpyDefault,
+                            s->copy_stream) != cudaSuccess)
+          st = QGS_ECUDA;
+      if (cudaStreamSynchronize(s->copy_stream) != cudaSuccess) st = QGS_ECUDA;
+    }
+  }
+  if (r->result) {
+    if (r->result_on_host) {
+      free(r->result);
+    } else {
+      cudaSetDevice(s->device);
+      cudaFreeAsync(r->result, s->copy_stream);
+    }
+    r->result = nullptr;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->reqs.erase(ticket);
+  return st;
+}
+
+qgs_status serve_stats(qgs_server* s, qgs_serve_stats* out) {
+  if (!s || !out) return QGS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  memset(out, 0, sizeof(*out));
+  out->submitted = s->submitted;
+  out->completed = s->completed;
+  out->failed = s->failed;
+  out->rejected = s->rejected;
+  out->max_in_flight = s->max_in_flight;
+  out->bytes_budget = s->budget;
+  out->bytes_reserved_peak = s->reserved_peak;
+  if (!s->lat_ms.empty()) {
+    std::vector<double> v = s->lat_ms;
+    std::sort(v.begin(), v.end());
+    auto q = [&](double f) { return v[std::min(v.size() - 1, (size_t)(f * (double)(v.size() - 1) + 0.5))]; };
+    out->p50_ms = q(0.50);
+    out->p99_ms = q(0.99);
+    double sum = 0;
+    for (double x : v) sum += x;
+    out->mean_ms = sum / (double)v.size();
+    const double span = std::chrono::duration<double>(s->t_last - s->t_first).count();
+    out->frames_per_s = span > 0 ? (double)s->completed / span : 0.0;
+  }
+  return QGS_OK;
+}
+
+qgs_status serve_reset_stats(qgs_server* s) {
+  if (!s) return QGS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->lat_ms.clear();
+  s->submitted = s->completed = s->failed = s->rejected = 0;
+  s->max_in_flight = s->running;
+  s->reserved_peak = s->reserved;
+  s->have_first = false;
+  return QGS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,49 @@
+"""Serving on the GPU: each result is the same alone (render_forward) and in the mix
+(several requests of mixed resolutions in flight on a 4-slot server)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2411_16392_gb300.scenes import orbit_camera, serving_scene
+from tests.parity_util import TOL_ABS
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2411_16392_gb300 import _lib as L
+    L.load()
+    return torch.device("cuda", 0)
+
+
+def test_results_alone_equal_results_in_the_mix(dev):
+    from paper_2411_16392_gb300.render import DeviceScene, Rasterizer
+    from paper_2411_16392_gb300.serve import Server
+    sc = serving_scene(0, 200_000)
+    ds = DeviceScene.from_host(sc, dev)
+    rng = np.random.default_rng(0)
+    cams = [orbit_camera(rng) for _ in range(12)]
+    ras = Rasterizer(dev)
+    alone = []
+    for cam in cams:
+        o = ras.forward(ds, cam)
+        alone.append({k: v.clone() for k, v in o.items()})
+    srv = Server(dev.index or 0, budget_bytes=16 << 30, slots=4)
+    sid = srv.load_scene(ds)
+    del ds
+    tickets = [srv.submit(sid, cam) for cam in cams]      # all in flight together
+    for t, cam, ref in zip(tickets, cams, alone):
+        out = {k: torch.full_like(v, 9.0) for k, v in ref.items()}
+        srv.wait(t, out=out, timeout_ms=60_000)
+        torch.cuda.synchronize()
+        for k in ref:
+            err = (out[k] - ref[k]).abs().max().item()
+            assert err <= TOL_ABS, (k, err)
+    st = srv.stats()
+    print("serve stats", st)
+    assert st["completed"] == len(cams) and st["failed"] == 0
+    assert st["max_in_flight"] >= 2
+    srv.close()
