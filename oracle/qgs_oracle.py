@@ -39,11 +39,11 @@ design notes of the repository):
   * The roots are the exact roots of the quadratic (evaluated without cancellation);
     the paper's |A| < 1e-6 tangent-plane fallback t = -C/B is the A -> 0 limit of
     the near root and is not used as a separate approximation.
-  * Screen bound: the 8 corners of the local box |x| <= 3 s_u, |y| <= 3 s_v,
-    z_lo <= z <= z_hi, clipped to the near plane, projected, and their pixel AABB
-    taken (the "loose" box of the supplementary's bounding-box section, with a
-    provable z clamp). It is evaluated in FP32 with correctly rounded operations in
-    a fixed order so that tile lists and keys can be compared bit for bit.
+  * Screen bound: the 8 corners of a local box that contains the support, clipped to
+    the near plane, projected, and their pixel AABB taken (the supplementary's
+    bounding-box section). The box comes from "arc length >= chord" (see bin_fp32);
+    it is evaluated in FP32 with correctly rounded operations in a fixed order so
+    that tile lists and keys can be compared bit for bit.
 
 Gradients are exact derivatives of this FP64 forward, taken by PyTorch autograd.
 """
@@ -83,14 +83,20 @@ def bin_fp32(scene, cam, emit: bool = True) -> Binning:
     """Conservative screen bound, tile rectangle and sort key of every primitive.
 
     FP32, correctly rounded + - * / sqrt only, each operation rounded separately in
-    the order written below (no fused multiply-add). Loose bounding box of the
-    supplementary ("Details of Bounding Box Calculation"): the local box is
-    |x| <= 3 s_u, |y| <= 3 s_v and z between
-      z_lo = max(9 (min(0,a) s_u^2 + min(0,b) s_v^2), -3 max(s_u, s_v))
-      z_hi = min(9 (max(0,a) s_u^2 + max(0,b) s_v^2),  3 max(s_u, s_v)).
-    Any point of the support has l <= 3 sigma(theta); since l >= rho this gives
-    x^2/s_u^2 + y^2/s_v^2 <= 9, and since l >= |a(theta)| rho^2 = |z| it gives
-    |z| <= 3 max(s_u, s_v).
+    the order written below (no fused multiply-add). Bounding box of the support in the
+    local frame, projected (the supplementary's "Details of Bounding Box Calculation":
+    project the 8 vertices of a 3-D box of the patch and take their 2-D AABB).
+    The box: a point (x, y, z) of the support has l <= 3 sigma(theta), and the arc is no
+    shorter than its chord, so x^2 + y^2 + z^2 <= 9 sigma(theta)^2; dividing by
+    sigma(theta)^2 (with (x^2+y^2)/sigma^2 = x^2/s_u^2 + y^2/s_v^2 =: E and
+    sigma <= m = max(s_u, s_v)) gives   E + z^2/m^2 <= 9.                          (*)
+      z: with X = x^2, Y = y^2 >= 0 and X/s_u^2 + Y/s_v^2 <= 9 - z^2/m^2, z = aX + bY is
+         at most (9 - z^2/m^2) c+ with c+ = max(0, a s_u^2, b s_v^2), so z <= z+, the
+         positive root of (c+/m^2) z^2 + z - 9 c+ = 0, i.e. 18 c+ / (1 + sqrt(1 + 36 c+^2/m^2));
+         likewise z >= -z- with c- = max(0, -a s_u^2, -b s_v^2).
+      x: if a and b do not have opposite signs, (a X + b Y)^2 >= (a X)^2, so (*) gives
+         X/s_u^2 + a^2 X^2/m^2 <= 9, X <= 18 / (1/s_u^2 + sqrt(1/s_u^4 + 36 a^2/m^2));
+         otherwise X <= 9 s_u^2 (E <= 9). Same for y with b, s_v.
     """
     f = np.float32
     N = scene.n
@@ -118,20 +124,30 @@ def bin_fp32(scene, cam, emit: bool = True) -> Binning:
         sv = scene.scale[:, 1].astype(f)
         a = scene.curv[:, 0].astype(f)
         b = scene.curv[:, 1].astype(f)
-        three, nine, zero = f(3.0), f(9.0), f(0.0)
-        X = three * su
-        Y = three * sv
-        zc = three * np.maximum(su, sv)
+        nine, zero = f(9.0), f(0.0)
+        c18, c36 = f(18.0), f(36.0)
+        m = np.maximum(su, sv)
         su2 = su * su
         sv2 = sv * sv
-        apos = np.where(a > zero, a, zero)
-        bpos = np.where(b > zero, b, zero)
-        aneg = np.where(a < zero, a, zero)
-        bneg = np.where(b < zero, b, zero)
-        zhi = nine * (apos * su2 + bpos * sv2)
-        zlo = nine * (aneg * su2 + bneg * sv2)
-        zmax = np.minimum(zhi, zc)
-        zmin = np.maximum(zlo, -zc)
+        ap = a * su2
+        bp = b * sv2
+        cpos = np.maximum(np.maximum(ap, bp), zero)
+        cneg = np.maximum(np.maximum(-ap, -bp), zero)
+
+        def root(num, c):
+            # num / (1 + sqrt(1 + 36 (c/m)^2)): the positive roots above, written with
+            # the dimensionless c/m so that nothing overflows
+            t = c / m
+            t = c36 * (t * t)
+            return num / (one + np.sqrt(one + t))
+
+        zmax = root(c18 * cpos, cpos)
+        zmin = -root(c18 * cneg, cneg)
+        same = ~(((a > zero) & (b < zero)) | ((a < zero) & (b > zero)))
+        Xs = np.where(same, root(c18 * su2, ap), nine * su2)
+        Ys = np.where(same, root(c18 * sv2, bp), nine * sv2)
+        X = np.sqrt(Xs)
+        Y = np.sqrt(Ys)
 
         corners = []
         for k in range(8):
@@ -177,7 +193,8 @@ def bin_fp32(scene, cam, emit: bool = True) -> Binning:
         finite_in = (np.isfinite(scene.mean).all(1) & np.isfinite(scene.quat).all(1)
                      & np.isfinite(scene.scale).all(1) & np.isfinite(scene.curv).all(1)
                      & np.isfinite(scene.opacity))
-        vis = (finite_in & (n2 > zero) & (su > zero) & (sv > zero) & (muc[2] > near) & anyp
+        vis = (finite_in & (n2 > zero) & (su > zero) & (sv > zero) & (su2 > zero) & (sv2 > zero)
+               & (muc[2] > near) & anyp
                & np.isfinite(xmin) & np.isfinite(xmax) & np.isfinite(ymin) & np.isfinite(ymax))
         vis &= ~((xmax < zero) | (ymax < zero) | (xmin >= f(cam.W)) | (ymin >= f(cam.H)))
         sixteenth = f(1.0 / TILE)

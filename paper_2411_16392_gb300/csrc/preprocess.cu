@@ -99,9 +99,13 @@ __device__ __forceinline__ bool quat_rot_exact(float qw, float qx, float qy, flo
   return true;
 }
 
+// Projected points of the support box: their pixel AABB (bit-exact part) and their
+// spans along the two directions of a screen-space parallelogram (ordinary FP32).
 struct Box2 {
   float xmin, xmax, ymin, ymax;
   bool any;
+  float n1x, n1y, n2x, n2y, pcx, pcy;   // parallelogram directions, projected centre
+  float s1min, s1max, s2min, s2max;
 };
 
 __device__ __forceinline__ void box_add(Box2& b, const CamParams& cp, float px, float py, float pz) {
@@ -112,6 +116,38 @@ __device__ __forceinline__ void box_add(Box2& b, const CamParams& cp, float px, 
   b.ymin = fminf(b.ymin, v);
   b.ymax = fmaxf(b.ymax, v);
   b.any = true;
+  const float du = u - b.pcx, dv = v - b.pcy;
+  const float t1 = b.n1x * du + b.n1y * dv, t2 = b.n2x * du + b.n2y * dv;
+  b.s1min = fminf(b.s1min, t1);
+  b.s1max = fmaxf(b.s1max, t1);
+  b.s2min = fminf(b.s2min, t2);
+  b.s2max = fmaxf(b.s2max, t2);
+}
+
+// Unit normal (in pixels) of the projection of the camera-space direction r at the
+// centre mu: the screen direction of a local axis, turned by 90 degrees.
+__device__ __forceinline__ void screen_normal(const CamParams& cp, const float* muc, float rx, float ry, float rz,
+                                              float& nx, float& ny) {
+  const float z = muc[2];
+  const float du = cp.fx * (rx * z - muc[0] * rz), dv = cp.fy * (ry * z - muc[1] * rz);
+  const float l2 = du * du + dv * dv;
+  if (l2 > 0.f && isfinite(l2)) {
+    const float il = rsqrtf(l2);
+    nx = -dv * il;
+    ny = du * il;
+  } else {
+    nx = 1.f;
+    ny = 0.f;
+  }
+}
+
+// Scaled slab of the parallelogram: (p_x, p_y, p_c) with |p_x dx + p_y dy - p_c| <= 1
+// for every pixel offset (dx, dy) from the projected centre inside the span.
+__device__ __forceinline__ float3 slab_of(float nx, float ny, float smin, float smax) {
+  const float c = 0.5f * (smin + smax);
+  const float w = 0.5f * (smax - smin) * (1.f + 1e-5f) + 2e-3f + 1e-6f * fabsf(c);
+  const float iw = 1.f / w;
+  return make_float3(nx * iw, ny * iw, c * iw);
 }
 
 }  // namespace
@@ -161,8 +197,12 @@ __device__ __forceinline__ bool preprocess_one(int64_t i, const SceneView& sc, c
   float R[9], W[9];
   bool finite_in = isfinite(mx) && isfinite(my) && isfinite(mz) && isfinite(q.x) && isfinite(q.y) && isfinite(q.z) &&
                    isfinite(q.w) && isfinite(s.x) && isfinite(s.y) && isfinite(ab.x) && isfinite(ab.y) && isfinite(op);
-  bool ok = finite_in && quat_rot_exact(q.x, q.y, q.z, q.w, R) && s.x > 0.f && s.y > 0.f && muc[2] > cp.near;
-  Box2 bx{INFINITY, -INFINITY, INFINITY, -INFINITY, false};
+  const float su2 = __fmul_rn(s.x, s.x), sv2 = __fmul_rn(s.y, s.y);
+  bool ok = finite_in && quat_rot_exact(q.x, q.y, q.z, q.w, R) && s.x > 0.f && s.y > 0.f && su2 > 0.f &&
+            sv2 > 0.f && muc[2] > cp.near;
+  Box2 bx;
+  bx.xmin = INFINITY; bx.xmax = -INFINITY; bx.ymin = INFINITY; bx.ymax = -INFINITY; bx.any = false;
+  bx.s1min = INFINITY; bx.s1max = -INFINITY; bx.s2min = INFINITY; bx.s2max = -INFINITY;
   if (ok) {
 #pragma unroll
     for (int r = 0; r < 3; ++r)
@@ -170,15 +210,27 @@ __device__ __forceinline__ bool preprocess_one(int64_t i, const SceneView& sc, c
       for (int c = 0; c < 3; ++c)
         W[3 * r + c] = __fadd_rn(__fadd_rn(__fmul_rn(cp.Rc[3 * r], R[c]), __fmul_rn(cp.Rc[3 * r + 1], R[3 + c])),
                                  __fmul_rn(cp.Rc[3 * r + 2], R[6 + c]));
+    // box of the support from "arc >= chord": E + z^2/m^2 <= 9 (derivation in the oracle)
     const float su = s.x, sv = s.y, a = ab.x, b = ab.y;
-    const float X = __fmul_rn(3.f, su), Y = __fmul_rn(3.f, sv);
-    const float zc = __fmul_rn(3.f, fmaxf(su, sv));
-    const float su2 = __fmul_rn(su, su), sv2 = __fmul_rn(sv, sv);
-    const float apos = a > 0.f ? a : 0.f, bpos = b > 0.f ? b : 0.f;
-    const float aneg = a < 0.f ? a : 0.f, bneg = b < 0.f ? b : 0.f;
-    const float zhi = __fmul_rn(9.f, __fadd_rn(__fmul_rn(apos, su2), __fmul_rn(bpos, sv2)));
-    const float zlo = __fmul_rn(9.f, __fadd_rn(__fmul_rn(aneg, su2), __fmul_rn(bneg, sv2)));
-    const float zmax = fminf(zhi, zc), zmin = fmaxf(zlo, -zc);
+    const float m = fmaxf(su, sv);
+    const float ap = __fmul_rn(a, su2), bp = __fmul_rn(b, sv2);
+    const float cpos = fmaxf(fmaxf(ap, bp), 0.f), cneg = fmaxf(fmaxf(-ap, -bp), 0.f);
+    auto root = [&](float num, float c) {
+      float t = __fdiv_rn(c, m);
+      t = __fmul_rn(36.f, __fmul_rn(t, t));
+      return __fdiv_rn(num, __fadd_rn(1.f, __fsqrt_rn(__fadd_rn(1.f, t))));
+    };
+    const float zmax = root(__fmul_rn(18.f, cpos), cpos);
+    const float zmin = -root(__fmul_rn(18.f, cneg), cneg);
+    const bool same = !((a > 0.f && b < 0.f) || (a < 0.f && b > 0.f));
+    const float Xs = same ? root(__fmul_rn(18.f, su2), ap) : __fmul_rn(9.f, su2);
+    const float Ys = same ? root(__fmul_rn(18.f, sv2), bp) : __fmul_rn(9.f, sv2);
+    const float X = __fsqrt_rn(Xs), Y = __fsqrt_rn(Ys);
+    // parallelogram directions: normals of the projected local x and y axes
+    screen_normal(cp, muc, W[0], W[3], W[6], bx.n1x, bx.n1y);
+    screen_normal(cp, muc, W[1], W[4], W[7], bx.n2x, bx.n2y);
+    bx.pcx = (float)((double)cp.fx * ((double)muc[0] / (double)muc[2]) + (double)cp.cx);
+    bx.pcy = (float)((double)cp.fy * ((double)muc[1] / (double)muc[2]) + (double)cp.cy);
     float P[8][3];
     bool in[8];
 #pragma unroll
@@ -235,8 +287,8 @@ __device__ __forceinline__ bool preprocess_one(int64_t i, const SceneView& sc, c
 #pragma unroll
   for (int c = 0; c < 3; ++c)
     g[c] = (float)(((double)W[c] * muc[0] + (double)W[3 + c] * muc[1] + (double)W[6 + c] * muc[2]) * iz);
-  const float padx0 = 1e-3f + 1e-6f * fabsf(bx.xmin), padx1 = 1e-3f + 1e-6f * fabsf(bx.xmax);
-  const float pady0 = 1e-3f + 1e-6f * fabsf(bx.ymin), pady1 = 1e-3f + 1e-6f * fabsf(bx.ymax);
+  const float3 p1 = slab_of(bx.n1x, bx.n1y, bx.s1min, bx.s1max);
+  const float3 p2 = slab_of(bx.n2x, bx.n2y, bx.s2min, bx.s2max);
 
   // colour: degree-3 SH at the direction from the camera centre to the primitive
   float dx = mx - cp.cw[0], dy = my - cp.cw[1], dz = mz - cp.cw[2];
@@ -258,9 +310,9 @@ __device__ __forceinline__ bool preprocess_one(int64_t i, const SceneView& sc, c
     }
   }
   PrimState ps;
-  ps.f[0] = make_float4(bx.xmin - padx0, bx.xmax + padx1, bx.ymin - pady0, bx.ymax + pady1);
+  ps.f[0] = make_float4(p1.x, p1.y, p1.z, p2.x);
   ps.f[1] = make_float4(pcx_hi, pcx_lo, pcy_hi, pcy_lo);
-  ps.f[2] = make_float4(zmu / cp.fx, zmu / cp.fy, (float)iz, zmu);
+  ps.f[2] = make_float4(p2.y, p2.z, (float)iz, zmu);
   ps.f[3] = make_float4(W[0], W[3], W[1], W[4]);
   ps.f[4] = make_float4(W[2], W[5], g[0], g[1]);
   ps.f[5] = make_float4(g[2], ab.x, ab.y, op);

@@ -16,9 +16,11 @@ constexpr int NGRAD_PAD = 20;       // 80 B: 16-byte aligned records
 // Per-primitive projected state: one 128-byte record (8 x float4), written by the
 // preprocessing kernel for the visible primitives and gathered by the compositing
 // kernels in sorted order (one cache line per primitive).
-//   f[0] = pixel-centre AABB (xmin, xmax, ymin, ymax), slightly padded
+//   f[0] = (p1x, p1y, p1c, p2x)   screen-space parallelogram containing the projected
+//   f[2].xy = (p2y, p2c)            support box: |p_x dx + p_y dy - p_c| <= 1 for the
+//                                   pixel offset (dx, dy) from the projected centre
 //   f[1] = projected centre as double-float (pcx_hi, pcx_lo, pcy_hi, pcy_lo)
-//   f[2] = (kx, ky, inv_z, z_mu): kx = z_mu/fx, ky = z_mu/fy, inv_z = 1/z_mu
+//   f[2].zw = (inv_z, z_mu)
 //   f[3] = (W00, W10, W01, W11)   W = R_cw * R: camera-from-local rotation
 //   f[4] = (W02, W12, g_x, g_y)   g = W^T mu_cam / z_mu: local direction of the centre ray
 //   f[5] = (g_z, a, b, opacity)

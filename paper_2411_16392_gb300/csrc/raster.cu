@@ -83,13 +83,18 @@ __device__ __forceinline__ float arc_ratio_prime(float u, float F) {
 // plane lies within 3 sigma(theta) (the selected hit is in h, G included).
 __device__ __forceinline__ bool eval_pair(const PrimState& P, float X, float Y, const RasterParams& rp, Hit& h,
                                           bool& grazed, uint32_t& isect) {
-  const float4 f0 = P.f[0];
-  if (X < f0.x || X > f0.y || Y < f0.z || Y > f0.w) return false;
+  const float4 f0 = P.f[0], f1 = P.f[1], f2 = P.f[2];
+  // pixel offset from the projected centre (double-float centre), parallelogram test
+  const float dxp = __fsub_rn(__fsub_rn(X, f1.x), f1.y);
+  const float dyp = __fsub_rn(__fsub_rn(Y, f1.z), f1.w);
+  const float t1 = __fmaf_rn(f0.x, dxp, __fmaf_rn(f0.y, dyp, -f0.z));
+  const float t2 = __fmaf_rn(f0.w, dxp, __fmaf_rn(f2.x, dyp, -f2.y));
+  if (!(fabsf(t1) <= 1.f && fabsf(t2) <= 1.f)) return false;
   ++isect;
-  const float4 f1 = P.f[1], f2 = P.f[2], f3 = P.f[3], f4 = P.f[4], f5 = P.f[5], f6 = P.f[6];
+  const float4 f3 = P.f[3], f4 = P.f[4], f5 = P.f[5], f6 = P.f[6];
   // camera-plane offset at the centre's depth, then the local frame (W^T e, e_z = 0)
-  const float ex = __fmul_rn(__fsub_rn(__fsub_rn(X, f1.x), f1.y), f2.x);
-  const float ey = __fmul_rn(__fsub_rn(__fsub_rn(Y, f1.z), f1.w), f2.y);
+  const float ex = __fmul_rn(__fmul_rn(dxp, f2.w), rp.inv_fx);
+  const float ey = __fmul_rn(__fmul_rn(dyp, f2.w), rp.inv_fy);
   const float bx = __fmaf_rn(f3.x, ex, __fmul_rn(f3.y, ey));
   const float by = __fmaf_rn(f3.z, ex, __fmul_rn(f3.w, ey));
   const float bz = __fmaf_rn(f4.x, ex, __fmul_rn(f4.y, ey));
