@@ -104,6 +104,17 @@ __global__ void k_tile_ranges(int64_t n, const uint64_t* __restrict__ keys, uint
   if (i == n - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[t].y = (uint32_t)(i + 1);
 }
 
+// Tile schedule key: heaviest tiles (most listed instances) first, bucketed by
+// floor(log2(count + 1)) so that one 5-bit radix pass orders them.
+__global__ void k_tile_sched_keys(int64_t ntiles, const uint2* __restrict__ ranges, uint32_t* __restrict__ key,
+                                  uint32_t* __restrict__ val) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntiles) return;
+  const uint32_t c = ranges[t].y - ranges[t].x;
+  key[t] = 31u - (31u - (uint32_t)__clz(c + 1u));  // 31 - floor(log2(c + 1)), in [0, 31]
+  val[t] = (uint32_t)t;
+}
+
 __global__ void k_debug_keys(int64_t n, const uint64_t* __restrict__ inst, const PrimState* __restrict__ state,
                              uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -131,6 +142,9 @@ struct qgs_ctx {
   DevBuf<uint32_t> vals, vals2;
   // per-tile / per-pixel
   DevBuf<uint2> ranges;
+  DevBuf<uint32_t> tkey, tkey2, torder, torder2;  // heaviest-first tile schedule
+  const uint32_t* tile_order = nullptr;
+  DevBuf<uint8_t> inst_used;                      // per instance: blended by some pixel
   DevBuf<float> T_final;
   DevBuf<uint32_t> n_contrib;
   // backward
@@ -286,7 +300,8 @@ void qgs_destroy(qgs_ctx* c) {
   c->idx2.release(); c->cnt_sorted.release(); c->offs.release(); c->rect.release(); c->inst.release();
   c->inst2.release(); c->vals.release(); c->vals2.release(); c->ranges.release(); c->T_final.release();
   c->n_contrib.release(); c->pgrad.release(); c->hist.release(); c->scan_tmp.release(); c->stats.release();
-  c->dcount.release();
+  c->dcount.release(); c->tkey.release(); c->tkey2.release(); c->torder.release(); c->torder2.release();
+  c->inst_used.release();
   if (c->h_total) cudaFreeHost(c->h_total);
   for (int i = 0; i < 10; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -328,6 +343,10 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   QGS_CU(ctx->offs.reserve(n1 + 1), "alloc offs");
   QGS_CU(ctx->rect.reserve(n1), "alloc rect");
   QGS_CU(ctx->ranges.reserve((size_t)ntiles), "alloc ranges");
+  QGS_CU(ctx->tkey.reserve((size_t)ntiles), "alloc tile keys");
+  QGS_CU(ctx->tkey2.reserve((size_t)ntiles), "alloc tile keys");
+  QGS_CU(ctx->torder.reserve((size_t)ntiles), "alloc tile order");
+  QGS_CU(ctx->torder2.reserve((size_t)ntiles), "alloc tile order");
   QGS_CU(ctx->T_final.reserve((size_t)P), "alloc T_final");
   QGS_CU(ctx->n_contrib.reserve((size_t)P), "alloc n_contrib");
   QGS_CU(ctx->hist.reserve(radix_hist_elems((int64_t)n1)), "alloc hist");
@@ -374,6 +393,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   ctx->vis_list = sm == 0 ? sidx : nullptr;  // depth order puts the visible primitives first
 
   const size_t i1 = (size_t)(I > 0 ? I : 1);
+  QGS_CU(ctx->inst_used.reserve(i1), "alloc inst flags");
   QGS_CU(ctx->inst.reserve(i1), "alloc inst");
   QGS_CU(ctx->inst2.reserve(i1), "alloc inst2");
   if (sm == 1) {
@@ -428,11 +448,22 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
     ++launch_counter();
     QGS_CU(cudaGetLastError(), "ranges");
   }
+  // heaviest-first tile schedule (one 5-bit radix pass over the tiles)
+  k_tile_sched_keys<<<nblk(ntiles), 256, 0, st>>>(ntiles, ctx->ranges.p, ctx->tkey.p, ctx->torder.p);
+  ++launch_counter();
+  QGS_CU(cudaGetLastError(), "tile schedule");
+  {
+    const bool fl = radix_sort_u32_pairs(ctx->tkey.p, ctx->torder.p, ctx->tkey2.p, ctx->torder2.p, ntiles, 0, 5, tmp,
+                                         st, &e);
+    QGS_CU(e, "tile schedule sort");
+    ctx->tile_order = fl ? ctx->torder2.p : ctx->torder.p;
+  }
   QGS_CU(cudaMemsetAsync(ctx->stats.p, 0, sizeof(RasterStats), st), "memset stats");
   mark(ctx, 5, st);
   k_raster_fwd<<<(unsigned)ntiles, BLOCK, 0, st>>>(ctx->ranges.p, ctx->ids, ctx->id_stride, ctx->state.p, rp,
                                                    out->rgb, out->alpha, out->depth, out->normal, ctx->T_final.p,
-                                                   ctx->n_contrib.p, ctx->stats.p);
+                                                   ctx->n_contrib.p, ctx->stats.p, ctx->tile_order,
+                                                   ctx->inst_used.p);
   ++launch_counter();
   QGS_CU(cudaGetLastError(), "k_raster_fwd");
   mark(ctx, 6, st);
@@ -489,7 +520,8 @@ qgs_status render_backward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camer
   k_raster_bwd<<<(unsigned)ntiles, BLOCK, RASTER_BWD_SMEM, st>>>(ctx->ranges.p, ctx->ids, ctx->id_stride,
                                                                  ctx->state.p, rp, grad_out->rgb, grad_out->alpha,
                                                                  grad_out->depth, grad_out->normal, ctx->T_final.p,
-                                                                 ctx->n_contrib.p, ctx->pgrad.p, ctx->stats.p);
+                                                                 ctx->n_contrib.p, ctx->pgrad.p, ctx->stats.p,
+                                                                 ctx->tile_order, ctx->inst_used.p);
   ++launch_counter();
   QGS_CU(cudaGetLastError(), "k_raster_bwd");
   mark(ctx, 8, st);
@@ -761,7 +793,7 @@ extern "C" qgs_status render_forward_noalloc(const qgs_scene* scene, const qgs_c
   }
   k_raster_fwd<<<(unsigned)ntiles, BLOCK, 0, st>>>(ranges, reinterpret_cast<const uint32_t*>(sorted), 2, state, rp,
                                                    out->rgb, out->alpha, out->depth, out->normal, T_final,
-                                                   n_contrib, stats);
+                                                   n_contrib, stats, nullptr, nullptr);
   QGS_CU(cudaGetLastError(), "k_raster_fwd");
   return QGS_OK;
 }

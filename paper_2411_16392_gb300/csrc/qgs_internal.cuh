@@ -78,11 +78,13 @@ inline int64_t& launch_counter() {
 
 __global__ void k_raster_fwd(const uint2* ranges, const uint32_t* ids, int id_stride, const PrimState* state,
                              RasterParams rp, float* out_rgb, float* out_alpha, float* out_depth,
-                             float* out_normal, float* T_final, uint32_t* n_contrib, RasterStats* stats);
+                             float* out_normal, float* T_final, uint32_t* n_contrib, RasterStats* stats,
+                             const uint32_t* tile_order, uint8_t* inst_used);
 constexpr size_t RASTER_BWD_SMEM = sizeof(PrimState) * BLOCK + sizeof(float) * BLOCK * NGRAD + sizeof(int) * BLOCK;
 __global__ void k_raster_bwd(const uint2* ranges, const uint32_t* ids, int id_stride, const PrimState* state,
                              RasterParams rp, const float* g_rgb, const float* g_alpha, const float* g_depth,
                              const float* g_normal, const float* T_final, const uint32_t* n_contrib,
-                             float* pgrad, RasterStats* stats);
+                             float* pgrad, RasterStats* stats, const uint32_t* tile_order,
+                             const uint8_t* inst_used);
 
 }  // namespace qgs

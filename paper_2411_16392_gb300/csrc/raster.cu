@@ -52,15 +52,24 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   return r;
 }
 
-// F(u) = l(a, rho) / rho with u = 2 a rho (the arc-length closed form of Sec. 3.2,
-// divided by rho); Taylor series for |u| < 1e-3.
+// F(u) = l(a, rho) / rho with u = 2 a rho: the arc-length closed form of Sec. 3.2 divided
+// by rho, (asinh(u)/u + sqrt(1 + u^2)) / 2. For |u| < 0.25 its Taylor series
+// 1 + u^2/6 - u^4/40 + u^6/112 - 5u^8/1152 + 7u^10/2816 (truncation < 1e-10 there; for
+// |u| < 1e-3 only the first three terms matter in FP32); above, the closed form with
+// asinh(|u|) = log(|u| + sqrt(1 + u^2)), well conditioned for |u| >= 0.25.
 __device__ __forceinline__ float arc_ratio(float u) {
   const float au = fabsf(u);
-  if (au < 1e-3f) {
+  if (au < 0.25f) {
     const float u2 = __fmul_rn(u, u);
-    return __fmaf_rn(u2, __fmaf_rn(u2, -0.025f, 0.16666667f), 1.f);
+    float p = 7.f / 2816.f;
+    p = __fmaf_rn(p, u2, -5.f / 1152.f);
+    p = __fmaf_rn(p, u2, 1.f / 112.f);
+    p = __fmaf_rn(p, u2, -0.025f);
+    p = __fmaf_rn(p, u2, 1.f / 6.f);
+    return __fmaf_rn(p, u2, 1.f);
   }
-  return __fmul_rn(0.5f, __fadd_rn(__fdividef(asinhf(au), au), __fsqrt_rn(__fmaf_rn(au, au, 1.f))));
+  const float r = sqrt_approx(__fmaf_rn(au, au, 1.f));
+  return __fmul_rn(0.5f, __fadd_rn(__fdividef(__logf(__fadd_rn(au, r)), au), r));
 }
 
 // dF/du. Series u (1/3 - u^2/10 + 3u^4/56 - 5u^6/144 + 35u^8/1408 - 63u^10/3328) for
@@ -107,7 +116,29 @@ __device__ __forceinline__ bool eval_pair(const PrimState& P, float X, float Y, 
   const float Bh = __fmaf_rn(adx, bx, __fmaf_rn(bdy, by, __fmul_rn(-0.5f, dz)));
   const float C = __fmaf_rn(__fmul_rn(a, bx), bx, __fmaf_rn(__fmul_rn(b, by), by, -bz));
   const float Dq = __fmaf_rn(Bh, Bh, -__fmul_rn(A, C));
-  float s1, s2;
+  const float smin = __fsub_rn(rp.near_plane, f2.w);  // t > near  <=>  s > near - z_mu
+  const float iu = f6.x, iv = f6.y;
+  // candidate test: within 3 sigma(theta) <=> F(u)^2 E <= 9 (F >= sqrt(1 + u^2/4) >= 1)
+  auto accept = [&](float s) -> bool {
+    if (!(s > smin)) return false;
+    const float x = __fmaf_rn(s, dx, bx), y = __fmaf_rn(s, dy, by);
+    const float x2 = __fmul_rn(x, x), y2 = __fmul_rn(y, y);
+    const float E = __fmaf_rn(iu, x2, __fmul_rn(iv, y2));
+    if (!(E <= 9.f)) return false;
+    const float rho2 = __fadd_rn(x2, y2);
+    const float zs = __fmaf_rn(a, x2, __fmul_rn(b, y2));
+    const float v = rho2 > 0.f ? __fmul_rn(zs, rsqrtf(rho2)) : 0.f;  // u / 2
+    if (!(__fmul_rn(E, __fmaf_rn(v, v, 1.f)) <= 9.f)) return false;  // chord: F^2 >= 1 + u^2/4
+    const float u = __fmul_rn(2.f, v);
+    const float F = arc_ratio(u);
+    const float Q = __fmul_rn(__fmul_rn(F, F), E);
+    if (!(Q <= 9.f)) return false;
+    h.s = s; h.x = x; h.y = y; h.zs = zs;
+    h.dx = dx; h.dy = dy; h.dz = dz;
+    h.rho2 = rho2; h.u = u; h.F = F; h.E = E;
+    h.G = __expf(__fmul_rn(-0.5f, Q));
+    return true;
+  };
   if (fabsf(Dq) <= __fmul_rn(rp.grazing_eps, __fmul_rn(Bh, Bh))) {
     // grazing ray: re-solve in FP64 from the FP32 local ray
     grazed = true;
@@ -119,53 +150,24 @@ __device__ __forceinline__ bool eval_pair(const PrimState& P, float X, float Y, 
     if (Dd < 0.0) return false;
     const double sq = sqrt(Dd);
     const double qd = -(Bd + (Bd >= 0.0 ? sq : -sq));
-    s1 = qd != 0.0 ? (float)(Cd / qd) : __int_as_float(0x7fc00000);
-    s2 = Ad != 0.0 ? (float)(qd / Ad) : __int_as_float(0x7fc00000);
-  } else {
-    if (Dq < 0.f) return false;
-    const float sq = sqrt_approx(Dq);
-    const float q = -__fadd_rn(Bh, Bh >= 0.f ? sq : -sq);
-    s1 = __fdividef(C, q);
-    s2 = __fdividef(q, A);
+    const float r1 = qd != 0.0 ? (float)(Cd / qd) : __int_as_float(0x7fc00000);
+    const float r2 = Ad != 0.0 ? (float)(qd / Ad) : __int_as_float(0x7fc00000);
+    const bool e1 = isfinite(r1), e2 = isfinite(r2);
+    const float s0 = (e1 && e2) ? fminf(r1, r2) : (e1 ? r1 : r2);
+    const float s1 = (e1 && e2) ? fmaxf(r1, r2) : __int_as_float(0x7fc00000);
+    if (isfinite(s0) && accept(s0)) return true;
+    return isfinite(s1) && accept(s1);
   }
-  const bool e1 = isfinite(s1), e2 = isfinite(s2);
-  float sn, sf;
-  bool hasf;
-  if (e1 && e2) {
-    sn = fminf(s1, s2);
-    sf = fmaxf(s1, s2);
-    hasf = true;
-  } else if (e1 || e2) {
-    sn = e1 ? s1 : s2;
-    sf = sn;
-    hasf = false;
-  } else {
-    return false;
-  }
-  const float smin = __fsub_rn(rp.near_plane, f2.w);  // t > near  <=>  s > near - z_mu
-  const float iu = f6.x, iv = f6.y;
-#pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    const float s = c ? sf : sn;
-    if (c && !hasf) break;
-    if (!(s > smin)) continue;
-    const float x = __fmaf_rn(s, dx, bx), y = __fmaf_rn(s, dy, by);
-    const float x2 = __fmul_rn(x, x), y2 = __fmul_rn(y, y);
-    const float E = __fmaf_rn(iu, x2, __fmul_rn(iv, y2));
-    if (!(E <= 9.f)) continue;  // F >= 1: outside the 3-sigma ellipse already
-    const float rho2 = __fadd_rn(x2, y2);
-    const float zs = __fmaf_rn(a, x2, __fmul_rn(b, y2));
-    const float u = rho2 > 0.f ? __fmul_rn(__fmul_rn(2.f, zs), rsqrtf(rho2)) : 0.f;
-    const float F = arc_ratio(u);
-    const float Q = __fmul_rn(__fmul_rn(F, F), E);
-    if (!(Q <= 9.f)) continue;
-    h.s = s; h.x = x; h.y = y; h.zs = zs;
-    h.dx = dx; h.dy = dy; h.dz = dz;
-    h.rho2 = rho2; h.u = u; h.F = F; h.E = E;
-    h.G = __expf(__fmul_rn(-0.5f, Q));
-    return true;
-  }
-  return false;
+  if (Dq < 0.f) return false;
+  const float sq = sqrt_approx(Dq);
+  const float q = -__fadd_rn(Bh, Bh >= 0.f ? sq : -sq);
+  // q/A is the smaller root iff sign(B') and sign(A) agree (A = 0: the single root C/q)
+  const bool qa_first = (Bh >= 0.f) == (A > 0.f);
+  const float s0 = qa_first ? __fdividef(q, A) : __fdividef(C, q);
+  const bool e0 = isfinite(s0);
+  if (e0 && accept(s0)) return true;
+  const float s1 = qa_first ? __fdividef(C, q) : __fdividef(q, A);
+  return isfinite(s1) && accept(s1);
 }
 
 __device__ __forceinline__ void pixel_of(int tile, int tiles_x, int& px, int& py) {
@@ -189,9 +191,11 @@ __global__ void __launch_bounds__(BLOCK, 3)
     k_raster_fwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids, int id_stride,
                  const PrimState* __restrict__ state, RasterParams rp, float* __restrict__ out_rgb,
                  float* __restrict__ out_alpha, float* __restrict__ out_depth, float* __restrict__ out_normal,
-                 float* __restrict__ T_final, uint32_t* __restrict__ n_contrib, RasterStats* __restrict__ stats) {
+                 float* __restrict__ T_final, uint32_t* __restrict__ n_contrib, RasterStats* __restrict__ stats,
+                 const uint32_t* __restrict__ tile_order, uint8_t* __restrict__ inst_used) {
   __shared__ PrimState sm[BLOCK];
-  const int tile = blockIdx.x;
+  __shared__ uint8_t used[BLOCK];
+  const int tile = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;
   int px, py;
   pixel_of(tile, rp.tiles_x, px, py);
   const bool inside = px < rp.W && py < rp.H;
@@ -206,6 +210,7 @@ __global__ void __launch_bounds__(BLOCK, 3)
     if (__syncthreads_count(done) == BLOCK) break;
     const int cnt = min(BLOCK, n - b0);
     stage_batch(sm, ids, id_stride, state, rg.x + b0, cnt);
+    used[threadIdx.x] = 0;
     __syncthreads();
     if (!done) {
       for (int j = 0; j < cnt; ++j) {
@@ -242,9 +247,13 @@ __global__ void __launch_bounds__(BLOCK, 3)
         nz = fmaf(wn, ncz, nz);
         T = Tn;
         ++blended;
+        used[j] = 1;
         last = (uint32_t)(b0 + j + 1);
       }
     }
+    // one flag per instance: did any pixel of the tile blend it (read by the backward)
+    __syncthreads();
+    if (inst_used && threadIdx.x < cnt) inst_used[rg.x + b0 + threadIdx.x] = used[threadIdx.x];
   }
   if (inside) {
     const size_t P = (size_t)rp.W * rp.H, pix = (size_t)py * rp.W + px;
@@ -301,14 +310,16 @@ __global__ void __launch_bounds__(BLOCK, 2)
                  const float* __restrict__ g_alpha, const float* __restrict__ g_depth,
                  const float* __restrict__ g_normal, const float* __restrict__ T_final,
                  const uint32_t* __restrict__ n_contrib, float* __restrict__ pgrad,
-                 RasterStats* __restrict__ stats) {
+                 RasterStats* __restrict__ stats, const uint32_t* __restrict__ tile_order,
+                 const uint8_t* __restrict__ inst_used) {
   // dynamic shared memory: BLOCK records, then BLOCK x NGRAD accumulators, then flags
   extern __shared__ float4 dyn_smem[];
   PrimState* sm = reinterpret_cast<PrimState*>(dyn_smem);
   float(*sg)[NGRAD] = reinterpret_cast<float(*)[NGRAD]>(sm + BLOCK);
   int* sflag = reinterpret_cast<int*>(&sg[BLOCK][0]);
   __shared__ int smax;
-  const int tile = blockIdx.x;
+  __shared__ uint8_t suse[BLOCK];
+  const int tile = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;
   int px, py;
   pixel_of(tile, rp.tiles_x, px, py);
   const bool inside = px < rp.W && py < rp.H;
@@ -342,8 +353,10 @@ __global__ void __launch_bounds__(BLOCK, 2)
     stage_batch(sm, ids, id_stride, state, rg.x + b0, cnt);
     for (int e = threadIdx.x; e < BLOCK * NGRAD; e += BLOCK) (&sg[0][0])[e] = 0.f;
     sflag[threadIdx.x] = 0;
+    suse[threadIdx.x] = (threadIdx.x < cnt && inst_used) ? inst_used[rg.x + b0 + threadIdx.x] : 1;
     __syncthreads();
     for (int j = cnt - 1; j >= 0; --j) {
+      if (!suse[j]) continue;  // no pixel of this tile blended the instance in the forward
       float v[32];
 #pragma unroll
       for (int k = 0; k < 32; ++k) v[k] = 0.f;
