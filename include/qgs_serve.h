@@ -53,7 +53,9 @@ qgs_status serve_create(qgs_server** out, int32_t device, int64_t hbm_budget_byt
 void serve_destroy(qgs_server* srv);
 
 /* Copy a scene (device pointers, layouts of qgs_scene) into server-owned device memory;
- * *scene_id receives its id. Not counted in the per-request budget. Errors: EINVAL,
+ * *scene_id receives its id. The copy is ordered after work on the legacy default stream
+ * (work on other streams that writes the source must be finished by the caller) and is
+ * complete when the call returns. Not counted in the per-request budget. Errors: EINVAL,
  * ENOMEM, ECUDA. */
 qgs_status serve_load_scene(qgs_server* srv, const qgs_scene* scene, int32_t* scene_id);
 
@@ -64,7 +66,9 @@ qgs_status serve_submit(qgs_server* srv, int32_t scene_id, const qgs_camera* cam
 
 /* Wait up to timeout_ms (< 0: no limit) for a ticket to finish, then copy its planes
  * into `out` (rgb 3HW, alpha HW, depth HW, normal 3HW floats; any plane may be NULL;
- * host or device pointers) and release the ticket. Errors: ENOTFOUND (unknown or
+ * host or device pointers) and release the ticket. The copy is ordered after work on
+ * the legacy default stream; work on other streams that writes `out` must be finished
+ * by the caller. Returns after the copy has completed. Errors: ENOTFOUND (unknown or
  * already released ticket), ETIMEDOUT (still running; the ticket stays valid), the
  * request's own error status, ECUDA. */
 qgs_status serve_wait(qgs_server* srv, uint64_t ticket, int32_t timeout_ms, const qgs_image* out);

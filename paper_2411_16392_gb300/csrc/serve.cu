@@ -183,7 +183,9 @@ qgs_status serve_create(qgs_server** out, int32_t device, int64_t hbm_budget_byt
       uint64_t keep = UINT64_MAX;  // keep freed result buffers cached in the pool
       cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
-    if (cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) != cudaSuccess) return QGS_ECUDA;
+    // result copies go to caller memory: a blocking stream, ordered after the caller's
+    // work on the legacy default stream (e.g. the initialisation of the destination)
+    if (cudaStreamCreate(&s->copy_stream) != cudaSuccess) return QGS_ECUDA;
     for (auto& sl : s->slots) {
       qgs_status st = qgs_create(&sl.ctx, nullptr, device);
       if (st != QGS_OK) {
@@ -257,11 +259,20 @@ qgs_status serve_load_scene(qgs_server* s, const qgs_scene* sc, int32_t* scene_i
           if (*jt.dst) cudaFree(*jt.dst);
         return QGS_ENOMEM;
       }
-      if (cudaMemcpy(*it.dst, it.src, it.bytes, cudaMemcpyDefault) != cudaSuccess) {
+      // a device-to-device cudaMemcpy may return before the copy is done, and the
+      // workers' streams do not wait for the default stream: copy on the server's copy
+      // stream (ordered after the caller's default-stream work) and wait for it here
+      if (cudaMemcpyAsync(*it.dst, it.src, it.bytes, cudaMemcpyDefault, s->copy_stream) != cudaSuccess) {
+        cudaStreamSynchronize(s->copy_stream);
         for (auto& jt : items)
           if (*jt.dst) cudaFree(*jt.dst);
         return QGS_ECUDA;
       }
+    }
+    if (cudaStreamSynchronize(s->copy_stream) != cudaSuccess) {
+      for (auto& jt : items)
+        if (*jt.dst) cudaFree(*jt.dst);
+      return QGS_ECUDA;
     }
   }
   std::lock_guard<std::mutex> lk(s->mu);

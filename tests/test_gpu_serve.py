@@ -35,13 +35,22 @@ def test_results_alone_equal_results_in_the_mix(dev):
     sid = srv.load_scene(ds)
     del ds
     tickets = [srv.submit(sid, cam) for cam in cams]      # all in flight together
-    for t, cam, ref in zip(tickets, cams, alone):
+    for i, (t, cam, ref) in enumerate(zip(tickets, cams, alone)):
         out = {k: torch.full_like(v, 9.0) for k, v in ref.items()}
         srv.wait(t, out=out, timeout_ms=60_000)
         torch.cuda.synchronize()
         for k in ref:
             err = (out[k] - ref[k]).abs().max().item()
-            assert err <= TOL_ABS, (k, err)
+            if err > TOL_ABS:
+                bad = (out[k] - ref[k]).abs().reshape(-1, cam.H, cam.W).amax(0) > TOL_ABS
+                ys, xs = torch.nonzero(bad, as_tuple=True)
+                tiles = sorted(set(((ys // 16) * ((cam.W + 15) // 16) + xs // 16).tolist()))
+                fresh = Rasterizer(dev).forward(DeviceScene.from_host(sc, dev), cam)[k]
+                print(f"request {i} {cam.W}x{cam.H} plane {k}: {int(bad.sum())} px in {len(tiles)} tiles "
+                      f"{tiles[:8]}; served {out[k].reshape(-1, cam.H, cam.W)[:, ys[0], xs[0]].tolist()} "
+                      f"alone {ref[k].reshape(-1, cam.H, cam.W)[:, ys[0], xs[0]].tolist()} "
+                      f"fresh {fresh.reshape(-1, cam.H, cam.W)[:, ys[0], xs[0]].tolist()}")
+            assert err <= TOL_ABS, (i, k, err)
     st = srv.stats()
     print("serve stats", st)
     assert st["completed"] == len(cams) and st["failed"] == 0
