@@ -545,14 +545,8 @@ qgs_status qgs_get_frame_stats(qgs_ctx* ctx, qgs_frame_stats* out) {
   QGS_CU(cudaStreamSynchronize(ctx->last_stream), "sync");
   RasterStats rs;
   QGS_CU(cudaMemcpy(&rs, ctx->stats.p, sizeof(rs), cudaMemcpyDeviceToHost), "stats");
-  int64_t vis = 0;
-  if (ctx->n > 0) {
-    std::vector<uint32_t> cnt((size_t)ctx->n);
-    QGS_CU(cudaMemcpy(cnt.data(), ctx->count.p, sizeof(uint32_t) * (size_t)ctx->n, cudaMemcpyDeviceToHost), "count");
-    for (uint32_t c : cnt) vis += c > 0;
-  }
   out->n_primitives = ctx->n;
-  out->n_visible = vis;
+  out->n_visible = ctx->n_visible;  // device counter read by the forward
   out->n_instances = ctx->n_inst;
   out->n_tiles = (int64_t)ctx->tiles_x * ctx->tiles_y;
   out->pair_evals = (int64_t)rs.pair_evals;
