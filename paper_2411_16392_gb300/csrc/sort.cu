@@ -1,11 +1,11 @@
 // Device-wide exclusive scan and stable LSD radix sort (hand-written, no library).
 //
 // Radix sort: per pass of at most 8 bits,
-//   1. upsweep  - each CTA histograms the digits of its 4096-key chunk into a
+//   1. upsweep  - each CTA histograms the digits of its 2048-key chunk into a
 //                 digit-major count matrix hist[d * nblocks + b];
 //   2. scan     - one exclusive scan of that matrix gives, for every (digit, chunk), the
 //                 global position of the chunk's first key with that digit;
-//   3. downsweep - each warp ranks its 512 keys in order with __match_any_sync
+//   3. downsweep - each warp ranks its 256 keys in order with __match_any_sync
 //                 (peers with the same digit), warp-level digit counters are scanned
 //                 across the CTA's warps, and every key is written to
 //                 base(d, chunk) + (keys with digit d in earlier warps) + rank in warp.
@@ -20,8 +20,8 @@ namespace {
 constexpr int SCAN_ITEMS = 16;
 constexpr int SCAN_CHUNK = BLOCK * SCAN_ITEMS;  // 4096 values per CTA
 constexpr int RS_WARPS = 8;
-constexpr int RS_ITEMS = 16;                    // keys per lane
-constexpr int RS_CHUNK = RS_WARPS * 32 * RS_ITEMS;  // 4096 keys per CTA
+constexpr int RS_ITEMS = 8;                     // keys per lane
+constexpr int RS_CHUNK = RS_WARPS * 32 * RS_ITEMS;  // 2048 keys per CTA
 constexpr unsigned FULL = 0xffffffffu;
 
 // Exclusive scan of the CTA's values in shared memory (SCAN_CHUNK of them); returns the
@@ -149,19 +149,25 @@ __global__ void __launch_bounds__(BLOCK) k_radix_downsweep(const K* __restrict__
   K kk[RS_ITEMS];
   uint32_t vv[RS_ITEMS];
   uint32_t rk[RS_ITEMS];
+  // all loads first (independent, in flight together), then the ranking below, whose
+  // warp barriers would otherwise serialise each load's latency
+#pragma unroll
+  for (int it = 0; it < RS_ITEMS; ++it) {
+    const int64_t i = wbase + it * 32 + lane;
+    kk[it] = i < n ? kin[i] : (K)0;
+    if (HAS_VAL) vv[it] = i < n ? vin[i] : 0u;
+  }
 #pragma unroll
   for (int it = 0; it < RS_ITEMS; ++it) {
     const int64_t i = wbase + it * 32 + lane;
     const bool valid = i < n;
-    const K key = valid ? kin[i] : (K)0;
-    if (HAS_VAL) vv[it] = valid ? vin[i] : 0u;
+    const K key = kk[it];
     const uint32_t d = valid ? digit_of(key, shift, mask) : 0x100u + (uint32_t)lane;
     const uint32_t peers = __match_any_sync(FULL, d);
     const uint32_t before = valid ? wh[warp][d] : 0u;
     __syncwarp();
     if (valid && (peers & lt) == 0) wh[warp][d] = before + __popc(peers);
     __syncwarp();
-    kk[it] = key;
     rk[it] = valid ? before + __popc(peers & lt) : 0xFFFFFFFFu;
   }
   __syncthreads();
