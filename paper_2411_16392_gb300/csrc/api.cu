@@ -657,7 +657,7 @@ constexpr int64_t NA_MAX_TILES = 4096;
 constexpr int64_t NA_MAX_INSTANCES = 1 << 20;  // (tile, primitive) pairs per frame
 
 constexpr size_t na_align(size_t b) { return (b + 255) & ~(size_t)255; }
-constexpr size_t NA_HIST = (size_t)256 * ((NA_MAX_INSTANCES + 4095) / 4096) + 1;  // radix histogram (u32)
+constexpr size_t NA_HIST = (size_t)256 * ((NA_MAX_INSTANCES + kRadixChunk - 1) / kRadixChunk) + 1;  // u32
 constexpr size_t NA_SCAN = 8192;                                                  // scan block sums (u32)
 // byte offsets of each region inside the array
 constexpr size_t NA_OFF_STATE = 0;

@@ -39,6 +39,9 @@ __global__ void k_preprocess_bwd(int64_t n, const uint32_t* list, SceneView sc, 
                                  const float* pgrad, GradView gd);
 
 // ---------------------------------------------------------------- sorting / scan
+// Keys per CTA of the radix sort (histogram sizes depend on it).
+constexpr int kRadixChunk = 2048;
+
 // Temporary storage of the device-wide scan and radix sort.
 struct SortTemp {
   uint32_t* hist = nullptr;   // [256 * max_blocks]

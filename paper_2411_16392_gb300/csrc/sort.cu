@@ -22,6 +22,7 @@ constexpr int SCAN_CHUNK = BLOCK * SCAN_ITEMS;  // 4096 values per CTA
 constexpr int RS_WARPS = 8;
 constexpr int RS_ITEMS = 8;                     // keys per lane
 constexpr int RS_CHUNK = RS_WARPS * 32 * RS_ITEMS;  // 2048 keys per CTA
+static_assert(RS_CHUNK == kRadixChunk, "histogram sizing assumes kRadixChunk keys per CTA");
 constexpr unsigned FULL = 0xffffffffu;
 
 // Exclusive scan of the CTA's values in shared memory (SCAN_CHUNK of them); returns the
@@ -241,6 +242,10 @@ bool radix_sort_impl(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, int be
     const int pb = (bits - (shift - begin_bit) + (passes - p) - 1) / (passes - p);  // spread bits evenly
     const uint32_t mask = (1u << pb) - 1u;
     const int64_t m = (int64_t)(mask + 1) * nblocks;
+    if ((size_t)m + 1 > tmp.hist_cap) {
+      *err = cudaErrorInvalidValue;  // histogram buffer too small for this sort
+      return flipped;
+    }
     K* kin = flipped ? k1 : k0;
     K* kout = flipped ? k0 : k1;
     uint32_t* vin = flipped ? v1 : v0;
