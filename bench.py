@@ -158,7 +158,7 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- GPU
-def serve_measure(dev_index, ds, n_req, lam, slots, seed=0, budget=64 << 30):
+def serve_measure(dev_index, ds, n_req, lam, slots, batch=1, seed=0, budget=64 << 30):
     """Open-loop serving run: Poisson arrivals at `lam` requests/s, cameras on a radius-2
     orbit with resolutions drawn from {256^2, 512x384, 1024x768, 1920x1080}; returns the
     server's latency statistics (submit -> result ready on the device)."""
@@ -169,7 +169,7 @@ def serve_measure(dev_index, ds, n_req, lam, slots, seed=0, budget=64 << 30):
     rng = np.random.default_rng(seed)
     cams = [orbit_camera(rng) for _ in range(n_req)]
     gaps = rng.exponential(1.0 / lam, n_req)
-    srv = Server(dev_index, budget_bytes=budget, slots=slots, queue=max(64, n_req))
+    srv = Server(dev_index, budget_bytes=budget, slots=slots, queue=max(64, n_req), batch=batch)
     sid = srv.load_scene(ds)
     for cam in cams[:4]:                        # warm-up (buffers, kernels)
         srv.wait(srv.submit(sid, cam))
@@ -205,7 +205,8 @@ def serve_measure(dev_index, ds, n_req, lam, slots, seed=0, budget=64 << 30):
     th.join()
     st = srv.stats()
     srv.close()
-    return {k: st[k] for k in ("p50_ms", "p99_ms", "mean_ms", "frames_per_s", "completed", "max_in_flight")}
+    return {k: st[k] for k in ("p50_ms", "p99_ms", "mean_ms", "frames_per_s", "completed", "max_in_flight",
+                               "batches", "max_batch")}
 
 
 def run_gpu(args):
@@ -382,18 +383,24 @@ def _report(args, rank, world, sc, cam, st, stage, clk, ms_max, value, e2e_value
 
 
 def _serving_leg(args):
-    """Served p50/p99 latency and frames/s of the 1M-quadric serving workload: plain
-    one-at-a-time (1 slot) against continuous batching (args.serve_slots slots), same
-    arrival process."""
+    """Served p50/p99 latency and frames/s of the 1M-quadric serving workload at each
+    arrival rate: plain one-at-a-time (1 slot, no batching), concurrent slots without
+    batching, and continuous batching (slots that each render up to --serve-batch queued
+    views in shared launches); the same arrival process for all three."""
     import torch
     from paper_2411_16392_gb300.render import DeviceScene
     from paper_2411_16392_gb300.scenes import serving_scene
     dev = torch.device("cuda", torch.cuda.current_device())
     ds = DeviceScene.from_host(serving_scene(0, 1_000_000), dev)
-    res = {"workload": "serving_1m_mixed_res", "arrival_rate_per_s": args.serve_rate,
-           "requests": args.serve_requests}
-    for name, slots in (("one_at_a_time", 1), ("batched", args.serve_slots)):
-        res[name] = serve_measure(dev.index, ds, args.serve_requests, args.serve_rate, slots)
+    res = {"workload": "serving_1m_mixed_res", "requests": args.serve_requests, "rates": []}
+    legs = (("one_at_a_time", 1, 1), (f"slots{args.serve_slots}", args.serve_slots, 1),
+            ("batched", args.serve_slots, args.serve_batch))
+    for rate in args.serve_rate:
+        r = {"arrival_rate_per_s": rate}
+        for name, slots, batch in legs:
+            r[name] = serve_measure(dev.index, ds, args.serve_requests, rate, slots, batch)
+        r["batched_config"] = {"slots": args.serve_slots, "max_batch": args.serve_batch}
+        res["rates"].append(r)
     del ds
     return res
 
@@ -410,8 +417,10 @@ def main():
                     help="primitive count (the benchmark workload is 3,000,000; smaller counts are for profiling)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--serve-requests", type=int, default=600, help="requests per serving run (0: skip)")
-    ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, requests/s")
+    ap.add_argument("--serve-rate", type=lambda v: [float(x) for x in v.split(",")], default=[200.0, 1000.0],
+                    help="Poisson arrival rates, requests/s (comma-separated)")
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-batch", type=int, default=8, help="most views per batch in the batched leg")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -162,6 +162,22 @@ const char* qgs_last_error(const qgs_ctx* ctx);
 qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera* cam,
                           const qgs_image* out, qgs_stream stream);
 
+/* Forward render of n_views views of ONE scene in shared launches: the serving path's
+ * batch (the paper renders one view at a time, Sec. 4.1; the per-view arithmetic is that
+ * of render_forward, Sec. 3.1-3.2 and the supplementary). cams[v] and outs[v] (host
+ * arrays of n_views structs; the planes are device pointers, W*H of cams[v]) may all
+ * differ in resolution. One preprocessing launch covers views x primitives, one depth
+ * sort orders all (view, primitive) entries, the tile instances of view v are numbered
+ * from the sum of the earlier views' tile counts, one tile sort and one compositing
+ * launch cover every view. Each view's planes equal render_forward's for that camera
+ * bit for bit. Work buffers scale with n_views * n primitive entries; n_views * n must
+ * stay below 2^31 and n_views in [1, 1024]. The instance order is always the
+ * factorised one (qgs_config.sort_mode is ignored). No residue is kept:
+ * render_backward cannot follow it, and the context's last frame is cleared.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_views,
+                                const qgs_camera* cams, const qgs_image* outs, qgs_stream stream);
+
 /* Backward of the last render_forward on this context (same scene pointers, same camera):
  * reverse-order traversal per pixel with transmittance recomputed from the residue
  * (supplementary, dX/d(alpha) back-to-front form), then the chain rule to every primitive

@@ -12,6 +12,10 @@
  *     memory (projected primitives, tile keys and their sort buffers, residue, result
  *     planes) fits in the remaining HBM budget; requests that arrive while others run
  *     are admitted as slots and memory free up, and their kernels overlap on the GPU;
+ *   - a slot that takes the head also takes up to max_batch - 1 further queued requests
+ *     of the same scene (queue order, each only while the budget still holds it) and
+ *     renders all of them, at their own resolutions, in shared launches
+ *     (render_forward_batch); a batch of one runs render_forward;
  *   - serve_wait returns a finished result (host or device destination) with a bounded
  *     wait; serve_stats reports p50/p99 latency (submit to result ready) and frames/s.
  * All functions are thread-safe. Status codes as in qgs.h; nothing aborts.
@@ -37,16 +41,19 @@ typedef struct {
   double frames_per_s;     /* completed / (last completion - first submission) */
   int64_t bytes_budget;    /* HBM budget given to serve_create */
   int64_t bytes_reserved_peak; /* most estimated bytes admitted at once */
+  int64_t batches;         /* batches started (each of >= 1 request) */
+  int64_t max_batch;       /* most requests in one batch */
 } qgs_serve_stats;
 
-/* Create a server on CUDA device `device` with `max_slots` worker slots (1 = plain
- * one-request-at-a-time), a queue of `queue_capacity` requests and an HBM budget for
- * in-flight requests. device = -1 creates a host-only server whose workers do not
- * touch a GPU and take `fake_us_per_mpix` microseconds per million pixels per request
- * (for testing the queue, admission and accounting without a GPU; results are zero).
- * Errors: EINVAL, ECUDA, ENOMEM. */
+/* Create a server on CUDA device `device` with `max_slots` worker slots in [1, 64],
+ * batches of at most `max_batch` requests in [1, 1024] (max_slots = max_batch = 1 is
+ * plain one-request-at-a-time serving), a queue of `queue_capacity` requests and an HBM
+ * budget for in-flight requests. device = -1 creates a host-only server whose workers
+ * do not touch a GPU and take `fake_us_per_mpix` microseconds per million pixels of a
+ * batch (for testing the queue, admission, batching and accounting without a GPU;
+ * results are zero). Errors: EINVAL, ECUDA, ENOMEM. */
 qgs_status serve_create(qgs_server** out, int32_t device, int64_t hbm_budget_bytes, int32_t max_slots,
-                        int32_t queue_capacity, double fake_us_per_mpix);
+                        int32_t max_batch, int32_t queue_capacity, double fake_us_per_mpix);
 
 /* Stop the workers after the running requests finish, drop queued requests, free
  * everything. NULL is ignored. */

@@ -58,7 +58,8 @@ class qgs_serve_stats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
                 ("rejected", C.c_int64), ("max_in_flight", C.c_int64), ("p50_ms", C.c_double),
                 ("p99_ms", C.c_double), ("mean_ms", C.c_double), ("frames_per_s", C.c_double),
-                ("bytes_budget", C.c_int64), ("bytes_reserved_peak", C.c_int64)]
+                ("bytes_budget", C.c_int64), ("bytes_reserved_peak", C.c_int64), ("batches", C.c_int64),
+                ("max_batch", C.c_int64)]
 
 
 # (name, restype, argtypes) of every exported entry point declared in include/*.h
@@ -75,8 +76,11 @@ EXPORTS = [
     ("qgs_copy_binning", C.c_int, [_P, _P, _P, C.c_int64, _P, _P, C.POINTER(C.c_int64)]),
     ("qgs_copy_residue", C.c_int, [_P, _P, _P]),
     ("qgs_set_profiling", C.c_int, [_P, C.c_int32]),
+    ("render_forward_batch", C.c_int, [_P, C.POINTER(qgs_scene), C.c_int32, C.POINTER(qgs_camera),
+                                       C.POINTER(qgs_image), _P]),
     ("render_forward_noalloc", C.c_int, [C.POINTER(qgs_scene), C.POINTER(qgs_camera), C.POINTER(qgs_image), _P]),
-    ("serve_create", C.c_int, [C.POINTER(_P), C.c_int32, C.c_int64, C.c_int32, C.c_int32, C.c_double]),
+    ("serve_create", C.c_int, [C.POINTER(_P), C.c_int32, C.c_int64, C.c_int32, C.c_int32, C.c_int32,
+                               C.c_double]),
     ("serve_destroy", None, [_P]),
     ("serve_load_scene", C.c_int, [_P, C.POINTER(qgs_scene), C.POINTER(C.c_int32)]),
     ("serve_submit", C.c_int, [_P, C.c_int32, C.POINTER(qgs_camera), C.POINTER(C.c_uint64)]),

@@ -96,6 +96,46 @@ __global__ void k_emit(int64_t n, const uint32_t* __restrict__ sidx, const uint3
   }
 }
 
+// Several views of one scene (render_forward_batch): entry pid = v * n_per_view + i, its
+// tiles numbered from the view's base (vt[v] = (tiles_x, tile base)); depth order only.
+__global__ void k_emit_views(int64_t n, const uint32_t* __restrict__ sidx, const uint32_t* __restrict__ count,
+                             const short4* __restrict__ rect, const uint32_t* __restrict__ offs, uint32_t n_per_view,
+                             const int2* __restrict__ vt, uint64_t* __restrict__ keys) {
+  const int lane = threadIdx.x & 31;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t pid = 0, c = 0, off = 0;
+  int tx = 0, base = 0;
+  short4 r = make_short4(0, 0, 0, 0);
+  if (j < n) {
+    pid = sidx[j];
+    c = count[pid];
+    if (c) {
+      off = offs[j];
+      r = rect[pid];
+      const int2 t = vt[pid / n_per_view];
+      tx = t.x;
+      base = t.y;
+    }
+  }
+  for (int k = 0; k < 32; ++k) {
+    const uint32_t cc = __shfl_sync(0xffffffffu, c, k);
+    if (!cc) continue;
+    const uint32_t pp = __shfl_sync(0xffffffffu, pid, k);
+    const uint32_t oo = __shfl_sync(0xffffffffu, off, k);
+    const int txk = __shfl_sync(0xffffffffu, tx, k);
+    const int bk = __shfl_sync(0xffffffffu, base, k);
+    const int rx0 = __shfl_sync(0xffffffffu, (int)r.x, k);
+    const int rx1 = __shfl_sync(0xffffffffu, (int)r.y, k);
+    const int ry0 = __shfl_sync(0xffffffffu, (int)r.z, k);
+    const uint32_t w = (uint32_t)(rx1 - rx0 + 1);
+    for (uint32_t e = lane; e < cc; e += 32) {
+      const uint32_t dy = e / w, dx = e - dy * w;
+      const uint32_t tile = (uint32_t)bk + (uint32_t)(ry0 + (int)dy) * (uint32_t)txk + (uint32_t)(rx0 + (int)dx);
+      keys[(size_t)oo + e] = ((uint64_t)tile << 32) | pp;
+    }
+  }
+}
+
 __global__ void k_tile_ranges(int64_t n, const uint64_t* __restrict__ keys, uint2* __restrict__ ranges) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -173,6 +213,14 @@ struct qgs_ctx {
   int64_t launches_fwd = 0, launches_bwd = 0;
   CamParams cp{};
   RasterParams rp{};
+  // counters of the last forward (single or batched)
+  bool have_stats = false;
+  int64_t n_tiles_total = 0;
+  // batched forward: view descriptors (device) and their pinned host staging
+  DevBuf<uint8_t> vdesc;
+  uint8_t* h_vdesc = nullptr;
+  size_t h_vdesc_cap = 0;
+  cudaEvent_t vdesc_done = nullptr;  // the staging buffer's last upload has completed
 };
 
 namespace {
@@ -302,6 +350,9 @@ void qgs_destroy(qgs_ctx* c) {
   c->n_contrib.release(); c->pgrad.release(); c->hist.release(); c->scan_tmp.release(); c->stats.release();
   c->dcount.release(); c->tkey.release(); c->tkey2.release(); c->torder.release(); c->torder2.release();
   c->inst_used.release();
+  c->vdesc.release();
+  if (c->h_vdesc) cudaFreeHost(c->h_vdesc);
+  if (c->vdesc_done) cudaEventDestroy(c->vdesc_done);
   if (c->h_total) cudaFreeHost(c->h_total);
   for (int i = 0; i < 10; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -359,6 +410,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
 
   const int64_t launches0 = launch_counter();
   ctx->have_fwd_times = false;
+  ctx->have_stats = false;
   QGS_CU(cudaMemsetAsync(ctx->dcount.p, 0, sizeof(uint32_t) * 4, st), "memset counters");
   mark(ctx, 0, st);
   SceneView sv{scene->mean, scene->quat, scene->scale, scene->curv, scene->opacity, scene->sh};
@@ -472,6 +524,8 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   ctx->launches_fwd = launch_counter() - launches0;
   ctx->launches_bwd = 0;
   ctx->have_frame = true;
+  ctx->have_stats = true;
+  ctx->n_tiles_total = ntiles;
   ctx->n = N;
   ctx->n_inst = I;
   ctx->W = cam->W;
@@ -482,6 +536,183 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   ctx->last_stream = st;
   ctx->cp = cp;
   ctx->rp = rp;
+  return QGS_OK;
+}
+
+qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_views, const qgs_camera* cams,
+                                const qgs_image* outs, qgs_stream stream) {
+  if (!ctx) return QGS_EINVAL;
+  ctx->err.clear();
+  qgs_status s = check_scene(ctx, scene);
+  if (s != QGS_OK) return s;
+  if (n_views < 1 || n_views > 1024) return fail(ctx, QGS_EINVAL, "n_views must be in [1, 1024]");
+  if (!cams || !outs) return fail(ctx, QGS_EINVAL, "camera/output array is NULL");
+  const int64_t N = scene->n;
+  const int V = n_views;
+  const int64_t VN = (int64_t)V * N;
+  if (VN > (int64_t)0x7FFFFFFF) return fail(ctx, QGS_EINVAL, "n_views * n must be below 2^31");
+  std::vector<CamParams> cps((size_t)V);
+  std::vector<RasterParams> rps((size_t)V);
+  std::vector<uint32_t> base((size_t)V);
+  int64_t T_all = 0;
+  for (int v = 0; v < V; ++v) {
+    const qgs_camera* cam = &cams[v];
+    const qgs_image* o = &outs[v];
+    if (cam->W <= 0 || cam->H <= 0 || cam->W > 32768 || cam->H > 32768)
+      return fail(ctx, QGS_EINVAL, "view " + std::to_string(v) + ": image size must be in [1, 32768]");
+    if (!finite_cam(cam))
+      return fail(ctx, QGS_EINVAL, "view " + std::to_string(v) + ": non-finite or non-positive intrinsics");
+    if (!o->rgb || !o->alpha || !o->depth || !o->normal)
+      return fail(ctx, QGS_EINVAL, "view " + std::to_string(v) + ": output plane is NULL");
+    make_params(ctx, cam, cps[v], rps[v]);
+    base[v] = (uint32_t)T_all;
+    T_all += (int64_t)cps[v].tiles_x * cps[v].tiles_y;
+    if (T_all > (int64_t)0x7FFFFFFF) return fail(ctx, QGS_EINVAL, "too many tiles in the batch (2^31)");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  QGS_CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+  ctx->have_frame = false;
+  ctx->have_stats = false;
+  ctx->have_fwd_times = false;
+  ctx->have_bwd_times = false;
+
+  // view descriptors: CamParams[V] | ViewDesc[V] | tile base u32[V] | (tiles_x, base) int2[V]
+  auto al16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  const size_t off_vd = al16(sizeof(CamParams) * V);
+  const size_t off_tb = al16(off_vd + sizeof(ViewDesc) * V);
+  const size_t off_vt = al16(off_tb + sizeof(uint32_t) * V);
+  const size_t vbytes = off_vt + sizeof(int2) * V;
+  if (!ctx->vdesc_done) QGS_CU(cudaEventCreateWithFlags(&ctx->vdesc_done, cudaEventDisableTiming), "event");
+  QGS_CU(cudaEventSynchronize(ctx->vdesc_done), "staging wait");
+  if (ctx->h_vdesc_cap < vbytes) {
+    if (ctx->h_vdesc) cudaFreeHost(ctx->h_vdesc);
+    ctx->h_vdesc = nullptr;
+    ctx->h_vdesc_cap = 0;
+    QGS_CU(cudaHostAlloc((void**)&ctx->h_vdesc, vbytes, cudaHostAllocDefault), "alloc view staging");
+    ctx->h_vdesc_cap = vbytes;
+  }
+  QGS_CU(ctx->vdesc.reserve(vbytes), "alloc view descriptors");
+  {
+    uint8_t* h = ctx->h_vdesc;
+    CamParams* hc = reinterpret_cast<CamParams*>(h);
+    ViewDesc* hv = reinterpret_cast<ViewDesc*>(h + off_vd);
+    uint32_t* hb = reinterpret_cast<uint32_t*>(h + off_tb);
+    int2* ht = reinterpret_cast<int2*>(h + off_vt);
+    for (int v = 0; v < V; ++v) {
+      hc[v] = cps[v];
+      hv[v].rp = rps[v];
+      hv[v].rgb = outs[v].rgb;
+      hv[v].alpha = outs[v].alpha;
+      hv[v].depth = outs[v].depth;
+      hv[v].normal = outs[v].normal;
+      hv[v].T_final = nullptr;
+      hv[v].n_contrib = nullptr;
+      hb[v] = base[v];
+      ht[v] = make_int2(cps[v].tiles_x, (int)base[v]);
+    }
+  }
+  const CamParams* d_cp = reinterpret_cast<const CamParams*>(ctx->vdesc.p);
+  const ViewDesc* d_vd = reinterpret_cast<const ViewDesc*>(ctx->vdesc.p + off_vd);
+  const uint32_t* d_tb = reinterpret_cast<const uint32_t*>(ctx->vdesc.p + off_tb);
+  const int2* d_vt = reinterpret_cast<const int2*>(ctx->vdesc.p + off_vt);
+
+  const size_t n1 = (size_t)(VN > 0 ? VN : 1);
+  QGS_CU(ctx->state.reserve(n1), "alloc state");
+  QGS_CU(ctx->count.reserve(n1), "alloc count");
+  QGS_CU(ctx->zkey.reserve(n1), "alloc zkey");
+  QGS_CU(ctx->idx.reserve(n1), "alloc idx");
+  QGS_CU(ctx->zkey2.reserve(n1), "alloc zkey2");
+  QGS_CU(ctx->idx2.reserve(n1), "alloc idx2");
+  QGS_CU(ctx->cnt_sorted.reserve(n1), "alloc cnt");
+  QGS_CU(ctx->offs.reserve(n1 + 1), "alloc offs");
+  QGS_CU(ctx->rect.reserve(n1), "alloc rect");
+  QGS_CU(ctx->ranges.reserve((size_t)T_all), "alloc ranges");
+  QGS_CU(ctx->tkey.reserve((size_t)T_all), "alloc tile keys");
+  QGS_CU(ctx->tkey2.reserve((size_t)T_all), "alloc tile keys");
+  QGS_CU(ctx->torder.reserve((size_t)T_all), "alloc tile order");
+  QGS_CU(ctx->torder2.reserve((size_t)T_all), "alloc tile order");
+  QGS_CU(ctx->hist.reserve(radix_hist_elems((int64_t)n1)), "alloc hist");
+  QGS_CU(ctx->scan_tmp.reserve(scan_tmp_elems((int64_t)radix_hist_elems((int64_t)n1) + (int64_t)n1)), "alloc scan");
+  SortTemp tmp;
+  tmp.hist = ctx->hist.p;
+  tmp.hist_cap = ctx->hist.cap;
+  tmp.scan_tmp = ctx->scan_tmp.p;
+  tmp.scan_cap = ctx->scan_tmp.cap;
+
+  const int64_t launches0 = launch_counter();
+  QGS_CU(cudaMemcpyAsync(ctx->vdesc.p, ctx->h_vdesc, vbytes, cudaMemcpyHostToDevice, st), "upload views");
+  QGS_CU(cudaEventRecord(ctx->vdesc_done, st), "event");
+  QGS_CU(cudaMemsetAsync(ctx->dcount.p, 0, sizeof(uint32_t) * 4, st), "memset counters");
+  SceneView sv{scene->mean, scene->quat, scene->scale, scene->curv, scene->opacity, scene->sh};
+  if (N > 0) {
+    k_preprocess_views<<<dim3(nblk(N), (unsigned)V), 256, 0, st>>>(N, sv, d_cp, ctx->state.p, ctx->count.p,
+                                                                   ctx->zkey.p, ctx->idx.p, ctx->rect.p,
+                                                                   ctx->dcount.p);
+    ++launch_counter();
+    QGS_CU(cudaGetLastError(), "k_preprocess_views");
+  }
+  cudaError_t e = cudaSuccess;
+  const bool fl0 = radix_sort_u32_pairs(ctx->zkey.p, ctx->idx.p, ctx->zkey2.p, ctx->idx2.p, VN, 0, 32, tmp, st, &e);
+  QGS_CU(e, "depth sort");
+  const uint32_t* sidx = fl0 ? ctx->idx2.p : ctx->idx.p;
+  if (VN > 0) {
+    k_gather_u32<<<nblk(VN), 256, 0, st>>>(VN, sidx, ctx->count.p, ctx->cnt_sorted.p);
+    ++launch_counter();
+    QGS_CU(cudaGetLastError(), "gather");
+  }
+  QGS_CU(scan_exclusive_u32(ctx->cnt_sorted.p, ctx->offs.p, VN, ctx->scan_tmp.p, ctx->scan_tmp.cap, st), "scan");
+  QGS_CU(cudaMemcpyAsync(ctx->h_total, ctx->offs.p + VN, sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "total");
+  QGS_CU(cudaMemcpyAsync(ctx->h_total + 1, ctx->dcount.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "visible");
+  QGS_CU(cudaStreamSynchronize(st), "sync");
+  const int64_t I = (int64_t)ctx->h_total[0];
+  ctx->n_visible = (int64_t)ctx->h_total[1];
+
+  const size_t i1 = (size_t)(I > 0 ? I : 1);
+  QGS_CU(ctx->inst.reserve(i1), "alloc inst");
+  QGS_CU(ctx->inst2.reserve(i1), "alloc inst2");
+  QGS_CU(ctx->hist.reserve(radix_hist_elems((int64_t)i1)), "alloc hist");
+  QGS_CU(ctx->scan_tmp.reserve(scan_tmp_elems((int64_t)radix_hist_elems((int64_t)i1))), "alloc scan");
+  tmp.hist = ctx->hist.p;
+  tmp.hist_cap = ctx->hist.cap;
+  tmp.scan_tmp = ctx->scan_tmp.p;
+  tmp.scan_cap = ctx->scan_tmp.cap;
+
+  const uint64_t* sorted = ctx->inst.p;
+  if (VN > 0 && I > 0) {
+    k_emit_views<<<nblk(VN), 256, 0, st>>>(VN, sidx, ctx->count.p, ctx->rect.p, ctx->offs.p, (uint32_t)N, d_vt,
+                                           ctx->inst.p);
+    ++launch_counter();
+    QGS_CU(cudaGetLastError(), "emit");
+    const bool fl = radix_sort_u64_keys(ctx->inst.p, ctx->inst2.p, I, 32, 32 + bits_for(T_all), tmp, st, &e);
+    QGS_CU(e, "tile sort");
+    sorted = fl ? ctx->inst2.p : ctx->inst.p;
+  }
+  const uint32_t* ids = reinterpret_cast<const uint32_t*>(sorted);
+  QGS_CU(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(uint2) * (size_t)T_all, st), "memset ranges");
+  if (I > 0) {
+    k_tile_ranges<<<nblk(I), 256, 0, st>>>(I, sorted, ctx->ranges.p);
+    ++launch_counter();
+    QGS_CU(cudaGetLastError(), "ranges");
+  }
+  k_tile_sched_keys<<<nblk(T_all), 256, 0, st>>>(T_all, ctx->ranges.p, ctx->tkey.p, ctx->torder.p);
+  ++launch_counter();
+  QGS_CU(cudaGetLastError(), "tile schedule");
+  const bool flt =
+      radix_sort_u32_pairs(ctx->tkey.p, ctx->torder.p, ctx->tkey2.p, ctx->torder2.p, T_all, 0, 5, tmp, st, &e);
+  QGS_CU(e, "tile schedule sort");
+  const uint32_t* order = flt ? ctx->torder2.p : ctx->torder.p;
+  QGS_CU(cudaMemsetAsync(ctx->stats.p, 0, sizeof(RasterStats), st), "memset stats");
+  k_raster_fwd_views<<<(unsigned)T_all, BLOCK, 0, st>>>(ctx->ranges.p, ids, 2, ctx->state.p, d_vd, V, d_tb,
+                                                        ctx->stats.p, order);
+  ++launch_counter();
+  QGS_CU(cudaGetLastError(), "k_raster_fwd_views");
+  ctx->launches_fwd = launch_counter() - launches0;
+  ctx->launches_bwd = 0;
+  ctx->have_stats = true;
+  ctx->n = VN;
+  ctx->n_inst = I;
+  ctx->n_tiles_total = T_all;
+  ctx->last_stream = st;
   return QGS_OK;
 }
 
@@ -540,7 +771,7 @@ qgs_status render_backward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camer
 
 qgs_status qgs_get_frame_stats(qgs_ctx* ctx, qgs_frame_stats* out) {
   if (!ctx || !out) return QGS_EINVAL;
-  if (!ctx->have_frame) return fail(ctx, QGS_ESTATE, "no frame rendered yet");
+  if (!ctx->have_stats) return fail(ctx, QGS_ESTATE, "no frame rendered yet");
   QGS_CU(cudaSetDevice(ctx->device), "cudaSetDevice");
   QGS_CU(cudaStreamSynchronize(ctx->last_stream), "sync");
   RasterStats rs;
@@ -548,7 +779,7 @@ qgs_status qgs_get_frame_stats(qgs_ctx* ctx, qgs_frame_stats* out) {
   out->n_primitives = ctx->n;
   out->n_visible = ctx->n_visible;  // device counter read by the forward
   out->n_instances = ctx->n_inst;
-  out->n_tiles = (int64_t)ctx->tiles_x * ctx->tiles_y;
+  out->n_tiles = ctx->n_tiles_total;
   out->pair_evals = (int64_t)rs.pair_evals;
   out->pair_isect = (int64_t)rs.pair_isect;
   out->pair_hits = (int64_t)rs.pair_hits;

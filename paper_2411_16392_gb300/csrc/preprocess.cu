@@ -155,7 +155,7 @@ __device__ __forceinline__ float3 slab_of(float nx, float ny, float smin, float 
 __device__ __forceinline__ bool preprocess_one(int64_t i, const SceneView& sc, const CamParams& cp,
                                                PrimState* __restrict__ state, uint32_t* __restrict__ count,
                                                uint32_t* __restrict__ zkey, uint32_t* __restrict__ idx,
-                                               short4* __restrict__ rect);
+                                               short4* __restrict__ rect, uint32_t idx_base = 0);
 
 __global__ void __launch_bounds__(256) k_preprocess(int64_t n, SceneView sc, CamParams cp, PrimState* __restrict__ state,
                                                     uint32_t* __restrict__ count, uint32_t* __restrict__ zkey,
@@ -172,11 +172,27 @@ __global__ void __launch_bounds__(256) k_preprocess(int64_t n, SceneView sc, Cam
   }
 }
 
+// Several views (blockIdx.y) of one scene: entry v*n + i of every per-primitive array.
+__global__ void __launch_bounds__(256) k_preprocess_views(int64_t n, SceneView sc, const CamParams* __restrict__ cps,
+                                                          PrimState* __restrict__ state, uint32_t* __restrict__ count,
+                                                          uint32_t* __restrict__ zkey, uint32_t* __restrict__ idx,
+                                                          short4* __restrict__ rect, uint32_t* __restrict__ n_visible) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t off = (int64_t)blockIdx.y * n;
+  const CamParams cp = cps[blockIdx.y];
+  uint32_t vis = 0;
+  if (i < n)
+    vis = preprocess_one(i, sc, cp, state + off, count + off, zkey + off, idx + off, rect + off, (uint32_t)off) ? 1u
+                                                                                                              : 0u;
+  vis = __reduce_add_sync(0xffffffffu, vis);
+  if ((threadIdx.x & 31) == 0 && vis) atomicAdd(n_visible, vis);
+}
+
 __device__ __forceinline__ bool preprocess_one(int64_t i, const SceneView& sc, const CamParams& cp,
                                                PrimState* __restrict__ state, uint32_t* __restrict__ count,
                                                uint32_t* __restrict__ zkey, uint32_t* __restrict__ idx,
-                                               short4* __restrict__ rect) {
-  idx[i] = (uint32_t)i;
+                                               short4* __restrict__ rect, uint32_t idx_base) {
+  idx[i] = idx_base + (uint32_t)i;
   const float mx = sc.mean[3 * i], my = sc.mean[3 * i + 1], mz = sc.mean[3 * i + 2];
   const float4 q = reinterpret_cast<const float4*>(sc.quat)[i];
   const float2 s = reinterpret_cast<const float2*>(sc.scale)[i];

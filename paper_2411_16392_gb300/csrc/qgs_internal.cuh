@@ -34,6 +34,8 @@ struct CamParams {
 // ---------------------------------------------------------------- preprocessing
 __global__ void k_preprocess(int64_t n, SceneView sc, CamParams cp, PrimState* state, uint32_t* count,
                              uint32_t* zkey, uint32_t* idx, short4* rect, uint32_t* n_visible);
+__global__ void k_preprocess_views(int64_t n, SceneView sc, const CamParams* cps, PrimState* state, uint32_t* count,
+                                   uint32_t* zkey, uint32_t* idx, short4* rect, uint32_t* n_visible);
 // list == nullptr: threads 0..n-1 are primitives 0..n-1; else primitive list[j].
 __global__ void k_preprocess_bwd(int64_t n, const uint32_t* list, SceneView sc, CamParams cp, const uint32_t* count,
                                  const float* pgrad, GradView gd);
@@ -79,6 +81,17 @@ inline int64_t& launch_counter() {
   return n;
 }
 
+// One view of a batched forward: its raster constants and output planes (device).
+struct ViewDesc {
+  RasterParams rp;
+  float *rgb, *alpha, *depth, *normal;
+  float* T_final;        // may be null (no residue kept)
+  uint32_t* n_contrib;   // may be null
+};
+
+__global__ void k_raster_fwd_views(const uint2* ranges, const uint32_t* ids, int id_stride, const PrimState* state,
+                                   const ViewDesc* views, int n_views, const uint32_t* tile_base,
+                                   RasterStats* stats, const uint32_t* tile_order);
 __global__ void k_raster_fwd(const uint2* ranges, const uint32_t* ids, int id_stride, const PrimState* state,
                              RasterParams rp, float* out_rgb, float* out_alpha, float* out_depth,
                              float* out_normal, float* T_final, uint32_t* n_contrib, RasterStats* stats,

@@ -187,17 +187,18 @@ __device__ __forceinline__ void stage_batch(PrimState* sm, const uint32_t* ids, 
 
 }  // namespace
 
-__global__ void __launch_bounds__(BLOCK, 3)
-    k_raster_fwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids, int id_stride,
-                 const PrimState* __restrict__ state, RasterParams rp, float* __restrict__ out_rgb,
-                 float* __restrict__ out_alpha, float* __restrict__ out_depth, float* __restrict__ out_normal,
-                 float* __restrict__ T_final, uint32_t* __restrict__ n_contrib, RasterStats* __restrict__ stats,
-                 const uint32_t* __restrict__ tile_order, uint8_t* __restrict__ inst_used) {
-  __shared__ PrimState sm[BLOCK];
-  __shared__ uint8_t used[BLOCK];
-  const int tile = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;
+// Composite one tile: `tile` indexes the sorted instance ranges, `local_tile` the tile
+// grid of the view (they differ when several views share one launch).
+__device__ __forceinline__ void raster_fwd_tile(PrimState* sm, uint8_t* used, int tile, int local_tile,
+                                                const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids,
+                                                int id_stride, const PrimState* __restrict__ state,
+                                                const RasterParams& rp, float* __restrict__ out_rgb,
+                                                float* __restrict__ out_alpha, float* __restrict__ out_depth,
+                                                float* __restrict__ out_normal, float* __restrict__ T_final,
+                                                uint32_t* __restrict__ n_contrib, RasterStats* __restrict__ stats,
+                                                uint8_t* __restrict__ inst_used) {
   int px, py;
-  pixel_of(tile, rp.tiles_x, px, py);
+  pixel_of(local_tile, rp.tiles_x, px, py);
   const bool inside = px < rp.W && py < rp.H;
   const uint2 rg = ranges[tile];
   const int n = (int)(rg.y - rg.x);
@@ -255,7 +256,7 @@ __global__ void __launch_bounds__(BLOCK, 3)
     __syncthreads();
     if (inst_used && threadIdx.x < cnt) inst_used[rg.x + b0 + threadIdx.x] = used[threadIdx.x];
   }
-  if (inside) {
+  if (inside && out_rgb) {
     const size_t P = (size_t)rp.W * rp.H, pix = (size_t)py * rp.W + px;
     out_rgb[pix] = cr;
     out_rgb[P + pix] = cg;
@@ -265,8 +266,8 @@ __global__ void __launch_bounds__(BLOCK, 3)
     out_normal[pix] = nx;
     out_normal[P + pix] = ny;
     out_normal[2 * P + pix] = nz;
-    T_final[pix] = T;
-    n_contrib[pix] = last;
+    if (T_final) T_final[pix] = T;
+    if (n_contrib) n_contrib[pix] = last;
   }
   // counters: one atomic per warp and counter
   if (stats) {
@@ -281,6 +282,40 @@ __global__ void __launch_bounds__(BLOCK, 3)
       if (gzz) atomicAdd(&stats->grazing, (unsigned long long)gzz);
     }
   }
+}
+
+__global__ void __launch_bounds__(BLOCK, 3)
+    k_raster_fwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids, int id_stride,
+                 const PrimState* __restrict__ state, RasterParams rp, float* __restrict__ out_rgb,
+                 float* __restrict__ out_alpha, float* __restrict__ out_depth, float* __restrict__ out_normal,
+                 float* __restrict__ T_final, uint32_t* __restrict__ n_contrib, RasterStats* __restrict__ stats,
+                 const uint32_t* __restrict__ tile_order, uint8_t* __restrict__ inst_used) {
+  __shared__ PrimState sm[BLOCK];
+  __shared__ uint8_t used[BLOCK];
+  const int tile = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;
+  raster_fwd_tile(sm, used, tile, tile, ranges, ids, id_stride, state, rp, out_rgb, out_alpha, out_depth, out_normal,
+                  T_final, n_contrib, stats, inst_used);
+}
+
+// Several views of one scene in one launch: global tile t belongs to the view v with
+// tile_base[v] <= t < tile_base[v + 1].
+__global__ void __launch_bounds__(BLOCK, 3)
+    k_raster_fwd_views(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids, int id_stride,
+                       const PrimState* __restrict__ state, const ViewDesc* __restrict__ views, int n_views,
+                       const uint32_t* __restrict__ tile_base, RasterStats* __restrict__ stats,
+                       const uint32_t* __restrict__ tile_order) {
+  __shared__ PrimState sm[BLOCK];
+  __shared__ uint8_t used[BLOCK];
+  const int tile = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;
+  int lo = 0, hi = n_views;  // largest v with tile_base[v] <= tile
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (tile_base[mid] <= (uint32_t)tile) lo = mid; else hi = mid;
+  }
+  const ViewDesc& vd = views[lo];
+  const RasterParams rp = vd.rp;
+  raster_fwd_tile(sm, used, tile, tile - (int)tile_base[lo], ranges, ids, id_stride, state, rp, vd.rgb, vd.alpha,
+                  vd.depth, vd.normal, vd.T_final, vd.n_contrib, stats, nullptr);
 }
 
 namespace {

@@ -1,6 +1,8 @@
 // Serving loop: resident scenes, bounded FIFO queue, memory-budget admission, worker
 // slots with their own rendering context and stream (continuous batching: requests are
-// admitted as slots and budget free up, and the kernels of in-flight requests overlap).
+// admitted as slots and budget free up, a free slot takes the queue's head together with
+// the other queued views of the same scene and renders them in shared launches
+// (render_forward_batch), and the kernels of the slots in flight overlap).
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -67,6 +69,7 @@ struct qgs_server {
   double fake_us_per_mpix = 0;
   int64_t budget = 0;
   int queue_cap = 0;
+  int max_batch = 1;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Request*> queue;
@@ -81,53 +84,71 @@ struct qgs_server {
   // statistics
   std::vector<double> lat_ms;
   int64_t submitted = 0, completed = 0, failed = 0, rejected = 0, max_in_flight = 0, reserved_peak = 0;
+  int64_t batches = 0, max_batch_seen = 0;
   bool have_first = false;
   Clock::time_point t_first, t_last;
 
   void worker(int slot_index);
-  void run_one(Slot& s, Request* r);
+  void run_batch(Slot& s, std::vector<Request*>& batch);
 };
 
-void qgs_server::run_one(Slot& s, Request* r) {
-  const int64_t P = (int64_t)r->cam.W * r->cam.H;
+void qgs_server::run_batch(Slot& s, std::vector<Request*>& batch) {
   if (fake) {
-    r->result = static_cast<float*>(calloc((size_t)P * 8, sizeof(float)));
-    r->result_on_host = true;
-    if (!r->result) {
-      r->status = QGS_ENOMEM;
-      return;
+    int64_t P_all = 0;
+    for (Request* r : batch) {
+      const int64_t P = (int64_t)r->cam.W * r->cam.H;
+      P_all += P;
+      r->result = static_cast<float*>(calloc((size_t)P * 8, sizeof(float)));
+      r->result_on_host = true;
+      r->status = r->result ? QGS_OK : QGS_ENOMEM;
     }
-    const double us = fake_us_per_mpix * (double)P / 1e6;
+    const double us = fake_us_per_mpix * (double)P_all / 1e6;
     std::this_thread::sleep_for(std::chrono::microseconds((int64_t)us));
-    r->status = QGS_OK;
     return;
   }
   cudaSetDevice(device);
-  const SceneDev& sc = r->scn;
-  void* buf = nullptr;
-  cudaError_t e = cudaMallocAsync(&buf, sizeof(float) * 8 * (size_t)P, s.stream);
-  if (e != cudaSuccess) {
-    r->status = e == cudaErrorMemoryAllocation ? QGS_ENOMEM : QGS_ECUDA;
-    return;
+  const SceneDev& sc = batch[0]->scn;
+  std::vector<qgs_camera> cams;
+  std::vector<qgs_image> outs;
+  int64_t P_all = 0;
+  qgs_status st = QGS_OK;
+  for (Request* r : batch) {
+    const int64_t P = (int64_t)r->cam.W * r->cam.H;
+    void* buf = nullptr;
+    cudaError_t e = cudaMallocAsync(&buf, sizeof(float) * 8 * (size_t)P, s.stream);
+    if (e != cudaSuccess) {
+      st = e == cudaErrorMemoryAllocation ? QGS_ENOMEM : QGS_ECUDA;
+      break;
+    }
+    r->result = static_cast<float*>(buf);
+    cams.push_back(r->cam);
+    outs.push_back(qgs_image{r->result, r->result + 3 * P, r->result + 4 * P, r->result + 5 * P});
+    P_all += P;
   }
-  r->result = static_cast<float*>(buf);
   qgs_scene scn{sc.n, sc.mean, sc.quat, sc.scale, sc.curv, sc.opacity, sc.sh};
-  qgs_image img{r->result, r->result + 3 * P, r->result + 4 * P, r->result + 5 * P};
-  r->status = render_forward(s.ctx, &scn, &r->cam, &img, s.stream);
-  if (r->status == QGS_OK && cudaStreamSynchronize(s.stream) != cudaSuccess) r->status = QGS_ECUDA;
-  if (r->status == QGS_OK) {
+  if (st == QGS_OK) {
+    if (batch.size() == 1)
+      st = render_forward(s.ctx, &scn, &cams[0], &outs[0], s.stream);
+    else
+      st = render_forward_batch(s.ctx, &scn, (int32_t)batch.size(), cams.data(), outs.data(), s.stream);
+  }
+  if (st == QGS_OK && cudaStreamSynchronize(s.stream) != cudaSuccess) st = QGS_ECUDA;
+  for (Request* r : batch) r->status = st;
+  if (st == QGS_OK) {
     const int64_t inst = qgs::last_instance_count(s.ctx);
     std::lock_guard<std::mutex> lk(mu);
-    SceneDev& sd = scenes[r->scene];
-    sd.inst_per_pixel = 0.7 * sd.inst_per_pixel + 0.3 * ((double)inst / (double)std::max<int64_t>(P, 1));
+    SceneDev& sd = scenes[batch[0]->scene];
+    sd.inst_per_pixel = 0.7 * sd.inst_per_pixel + 0.3 * ((double)inst / (double)std::max<int64_t>(P_all, 1));
   }
 }
 
 void qgs_server::worker(int si) {
   Slot& s = slots[si];
   if (!fake) cudaSetDevice(device);
+  std::vector<Request*> batch;
   for (;;) {
-    Request* r = nullptr;
+    int64_t est = 0;
+    batch.clear();
     {
       std::unique_lock<std::mutex> lk(mu);
       cv_work.wait(lk, [&] {
@@ -137,25 +158,43 @@ void qgs_server::worker(int si) {
         return running == 0 || reserved + queue.front()->est_bytes <= budget;
       });
       if (stop) return;
-      r = queue.front();
+      Request* head = queue.front();
       queue.pop_front();
-      r->state = 1;
-      reserved += r->est_bytes;
-      ++running;
+      batch.push_back(head);
+      est = head->est_bytes;
+      // the other queued views of the same scene that still fit join the head's launches
+      for (auto it = queue.begin(); it != queue.end() && (int)batch.size() < max_batch;) {
+        Request* r = *it;
+        if (r->scene == head->scene && reserved + est + r->est_bytes <= budget) {
+          batch.push_back(r);
+          est += r->est_bytes;
+          it = queue.erase(it);
+        } else {
+          ++it;
+        }
+      }
+      for (Request* r : batch) r->state = 1;
+      reserved += est;
+      running += (int)batch.size();
+      ++batches;
+      max_batch_seen = std::max<int64_t>(max_batch_seen, (int64_t)batch.size());
       max_in_flight = std::max<int64_t>(max_in_flight, running);
       reserved_peak = std::max(reserved_peak, reserved);
     }
-    run_one(s, r);
+    run_batch(s, batch);
     {
       std::lock_guard<std::mutex> lk(mu);
-      r->t_done = Clock::now();
-      r->state = 2;
-      reserved -= r->est_bytes;
-      --running;
-      ++completed;
-      if (r->status != QGS_OK) ++failed;
-      lat_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
-      t_last = r->t_done;
+      const Clock::time_point now = Clock::now();
+      for (Request* r : batch) {
+        r->t_done = now;
+        r->state = 2;
+        ++completed;
+        if (r->status != QGS_OK) ++failed;
+        lat_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+      }
+      reserved -= est;
+      running -= (int)batch.size();
+      t_last = now;
     }
     cv_done.notify_all();
     cv_work.notify_all();
@@ -165,8 +204,10 @@ void qgs_server::worker(int si) {
 extern "C" {
 
 qgs_status serve_create(qgs_server** out, int32_t device, int64_t hbm_budget_bytes, int32_t max_slots,
-                        int32_t queue_capacity, double fake_us_per_mpix) {
-  if (!out || max_slots < 1 || max_slots > 64 || queue_capacity < 1 || hbm_budget_bytes <= 0) return QGS_EINVAL;
+                        int32_t max_batch, int32_t queue_capacity, double fake_us_per_mpix) {
+  if (!out || max_slots < 1 || max_slots > 64 || max_batch < 1 || max_batch > 1024 || queue_capacity < 1 ||
+      hbm_budget_bytes <= 0)
+    return QGS_EINVAL;
   *out = nullptr;
   std::unique_ptr<qgs_server> s(new (std::nothrow) qgs_server());
   if (!s) return QGS_ENOMEM;
@@ -175,6 +216,7 @@ qgs_status serve_create(qgs_server** out, int32_t device, int64_t hbm_budget_byt
   s->fake_us_per_mpix = fake_us_per_mpix;
   s->budget = hbm_budget_bytes;
   s->queue_cap = queue_capacity;
+  s->max_batch = max_batch;
   s->slots.resize(max_slots);
   if (!s->fake) {
     if (cudaSetDevice(device) != cudaSuccess) return QGS_ECUDA;
@@ -380,6 +422,8 @@ qgs_status serve_stats(qgs_server* s, qgs_serve_stats* out) {
   out->max_in_flight = s->max_in_flight;
   out->bytes_budget = s->budget;
   out->bytes_reserved_peak = s->reserved_peak;
+  out->batches = s->batches;
+  out->max_batch = s->max_batch_seen;
   if (!s->lat_ms.empty()) {
     std::vector<double> v = s->lat_ms;
     std::sort(v.begin(), v.end());
@@ -400,6 +444,7 @@ qgs_status serve_reset_stats(qgs_server* s) {
   std::lock_guard<std::mutex> lk(s->mu);
   s->lat_ms.clear();
   s->submitted = s->completed = s->failed = s->rejected = 0;
+  s->batches = s->max_batch_seen = 0;
   s->max_in_flight = s->running;
   s->reserved_peak = s->reserved;
   s->have_first = false;

@@ -104,6 +104,27 @@ class Rasterizer:
         self._last = (scene, cam)
         return out
 
+    def forward_batch(self, scene: DeviceScene, cams, outs: list | None = None) -> list:
+        """Render several views of one scene in shared launches (render_forward_batch);
+        returns one plane dict per camera. Leaves no residue for backward."""
+        V = len(cams)
+        if outs is None:
+            outs = []
+            for cam in cams:
+                H, W = int(cam.H), int(cam.W)
+                outs.append(dict(rgb=torch.empty(3, H, W, device=self.device),
+                                 alpha=torch.empty(H, W, device=self.device),
+                                 depth=torch.empty(H, W, device=self.device),
+                                 normal=torch.empty(3, H, W, device=self.device)))
+        cc = (L.qgs_camera * V)(*[camera_to_c(c) for c in cams])
+        im = (L.qgs_image * V)(*[L.qgs_image(o["rgb"].data_ptr(), o["alpha"].data_ptr(), o["depth"].data_ptr(),
+                                             o["normal"].data_ptr()) for o in outs])
+        sc = scene.to_c()
+        L.check(self.lib.render_forward_batch(self._ctx, C.byref(sc), V, cc, im,
+                                              C.c_void_p(_stream_ptr(self.device))), self._ctx)
+        self._last = None
+        return outs
+
     # ------------------------------------------------------------------ backward
     def backward(self, scene: DeviceScene, cam, grad_out: dict, grads: dict | None = None) -> dict:
         """Gradients of sum(grad_out * outputs) of the last forward; added into `grads`

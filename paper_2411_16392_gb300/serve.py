@@ -12,13 +12,14 @@ from .render import DeviceScene, camera_to_c
 
 class Server:
     """Continuous-batching server: resident scenes, bounded queue, memory-budget admission,
-    `slots` concurrent worker contexts (1 = plain one-at-a-time)."""
+    `slots` concurrent worker contexts, each rendering up to `batch` queued views of one
+    scene in shared launches (slots = batch = 1: plain one-at-a-time)."""
 
     def __init__(self, device: int = 0, budget_bytes: int = 8 << 30, slots: int = 4, queue: int = 1024,
-                 fake_us_per_mpix: float = 0.0):
+                 fake_us_per_mpix: float = 0.0, batch: int = 1):
         self.lib = L.load()
         self._srv = C.c_void_p()
-        L.check(self.lib.serve_create(C.byref(self._srv), device, int(budget_bytes), slots, queue,
+        L.check(self.lib.serve_create(C.byref(self._srv), device, int(budget_bytes), slots, batch, queue,
                                       float(fake_us_per_mpix)))
         self.device = device
 

@@ -1,5 +1,6 @@
 """Serving on the GPU: each result is the same alone (render_forward) and in the mix
-(several requests of mixed resolutions in flight on a 4-slot server)."""
+(several requests of mixed resolutions in flight on a 4-slot server, or batched into
+shared launches on a 2-slot server)."""
 import numpy as np
 import pytest
 import torch
@@ -19,7 +20,8 @@ def dev():
     return torch.device("cuda", 0)
 
 
-def test_results_alone_equal_results_in_the_mix(dev):
+@pytest.mark.parametrize("slots,batch", [(4, 1), (2, 4)])
+def test_results_alone_equal_results_in_the_mix(dev, slots, batch):
     from paper_2411_16392_gb300.render import DeviceScene, Rasterizer
     from paper_2411_16392_gb300.serve import Server
     sc = serving_scene(0, 200_000)
@@ -31,7 +33,7 @@ def test_results_alone_equal_results_in_the_mix(dev):
     for cam in cams:
         o = ras.forward(ds, cam)
         alone.append({k: v.clone() for k, v in o.items()})
-    srv = Server(dev.index or 0, budget_bytes=16 << 30, slots=4)
+    srv = Server(dev.index or 0, budget_bytes=16 << 30, slots=slots, batch=batch)
     sid = srv.load_scene(ds)
     del ds
     tickets = [srv.submit(sid, cam) for cam in cams]      # all in flight together
@@ -55,4 +57,6 @@ def test_results_alone_equal_results_in_the_mix(dev):
     print("serve stats", st)
     assert st["completed"] == len(cams) and st["failed"] == 0
     assert st["max_in_flight"] >= 2
+    if batch > 1:
+        assert st["max_batch"] >= 2
     srv.close()

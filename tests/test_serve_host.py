@@ -150,3 +150,37 @@ def test_invalid_arguments(lib):
         s.submit(sid, huge)                # alone larger than the budget
     assert e.value.status == 3
     s.close()
+
+
+def test_queued_views_of_one_scene_are_batched(lib):
+    """One slot, batches of up to 4: while the first request runs, 8 more queue up and
+    are taken 4 at a time; views of another scene never join them."""
+    s = _server(budget_bytes=1 << 40, slots=1, batch=4, fake_us_per_mpix=1_000_000.0)  # ~65 ms per view
+    a = s.load_scene(n=10)
+    b = s.load_scene(n=10)
+    ts = [s.submit(a, CAM)]
+    time.sleep(0.02)
+    ts += [s.submit(a, CAM) for _ in range(8)] + [s.submit(b, CAM)]
+    for t in ts:
+        s.wait(t)
+    st = s.stats()
+    assert st["completed"] == 10 and st["failed"] == 0
+    assert st["max_batch"] == 4
+    assert st["batches"] == 4          # [a], [a a a a], [a a a a], [b]
+    assert st["max_in_flight"] == 4
+    s.close()
+
+
+def test_batch_size_is_bounded_by_the_budget(lib):
+    per = (10 * 168 + 64 * 65536 * 16 + 64 * 65536 / 16 + 65536 * 40) + (1 << 20)
+    s = _server(budget_bytes=int(2.5 * per), slots=1, batch=8, fake_us_per_mpix=500_000.0)
+    sid = s.load_scene(n=10)
+    ts = [s.submit(sid, CAM)]
+    time.sleep(0.01)
+    ts += [s.submit(sid, CAM) for _ in range(6)]
+    for t in ts:
+        s.wait(t)
+    st = s.stats()
+    assert st["max_batch"] == 2 and st["max_in_flight"] == 2, st
+    assert st["bytes_reserved_peak"] <= st["bytes_budget"]
+    s.close()
