@@ -26,6 +26,14 @@ What it computes, step by step, and where each step is defined in the paper
     supplementary's X_hat = sum alpha_i T_i X_i): front to back, in sorted order.
   * Tile binning (supplementary, per-tile sorting): 16x16 tiles, one 64-bit key
     (tile << 32 | float bits of the view depth) per (tile, primitive) pair, stable sort.
+  * Extra channels (render(..., extras=True)): the curvature map sum w_i K_i with the
+    Gaussian curvature of Sec. 3.2.1 at each hit; the depth distortion of Sec. 3.3,
+    sum_i sum_{j<i} w_i w_j (t_i - t_j)^2, summed as written; the median depth of
+    Sec. 4.1, the largest t_i among blended pairs whose transmittance before them
+    exceeds 0.5 (0 when none does).
+  * Density variant (render(..., density="euclid")): the Euclidean-distance Gaussian
+    that Sec. 3.2 argues against and Sec. 4.3 ablates, same sigma(theta), distance
+    sqrt(rho^2 + z^2) from the vertex.
 
 Readings where the paper is silent (each one is listed with its reason in the
 design notes of the repository):
@@ -35,7 +43,9 @@ design notes of the repository):
   * Roots are accepted only in front of the near plane (t > near, near = 0.2);
     primitives whose centre is not in front of the near plane are culled.
   * t is the camera-space z depth of the hit; the depth map is sum w_i t_i
-    (unnormalised), the normal map sum w_i n_i (unnormalised), in camera space.
+    (unnormalised), the normal map sum w_i n_i (unnormalised), in camera space; the
+    distortion uses the same t (the paper's "depth at the ray-splat intersection"); the
+    median depth carries no gradient (the paper uses it for mesh extraction only).
   * The roots are the exact roots of the quadratic (evaluated without cancellation);
     the paper's |A| < 1e-6 tangent-plane fallback t = -C/B is the A -> 0 limit of
     the near root and is not used as a separate approximation.
@@ -299,6 +309,31 @@ def geodesic_gaussian(x, y, a, b, s1, s2):
     return G, l, sig
 
 
+def euclid_gaussian(x, y, a, b, s1, s2):
+    """The Euclidean-distance density that the paper contrasts with its geodesic one
+    (Sec. 3.2, the disk -> paraboloid deformation argument; ablated as "w/ Euclid" in
+    Sec. 4.3): the same sigma(theta), with l the straight-line distance from the vertex to
+    the surface point, sqrt(rho^2 + z^2), z = a x^2 + b y^2. Returns (G, l, sigma)."""
+    rho2 = x * x + y * y
+    zero = rho2 == 0
+    xs = torch.where(zero, torch.ones_like(x), x)
+    ys = torch.where(zero, torch.zeros_like(y), y)
+    theta = torch.atan2(ys, xs)
+    z = a * x * x + b * y * y
+    l = torch.sqrt(rho2 + z * z)
+    sig = sigma_theta(theta, s1, s2)
+    G = torch.exp(-(l * l) / (2.0 * sig * sig))
+    return G, l, sig
+
+
+def gaussian_curvature(x, y, a, b):
+    """Gaussian curvature of z = a x^2 + b y^2 at local (x, y) (Sec. 3.2.1 curvature Eq.,
+    derived in the supplementary's "Details of Curvature"; lambda_1 = a, lambda_2 = b):
+    4ab / (1 + 4a^2 x^2 + 4b^2 y^2)^2."""
+    S = 1.0 + 4.0 * a * a * x * x + 4.0 * b * b * y * y
+    return 4.0 * a * b / (S * S)
+
+
 def quadratic_roots(A, B, C):
     """Both real roots (t1 <= t2) of A t^2 + B t + C = 0 and whether they exist.
     q = -(B + sgn(B) sqrt(D)) / 2 with sgn(0) = +1; the roots are C/q and q/A, each
@@ -394,10 +429,13 @@ class CamF64:
 
 
 # =========================================================================== per-pair evaluation
-def _eval_pairs(prm: Params, cam: CamF64, idx: torch.Tensor, px: torch.Tensor, py: torch.Tensor):
+def _eval_pairs(prm: Params, cam: CamF64, idx: torch.Tensor, px: torch.Tensor, py: torch.Tensor,
+                density: str = "geodesic"):
     """Evaluate every (pixel, primitive) pair of a pixel set [P] and a primitive list [L].
     Returns per-pair tensors [P, L]: alpha (0 where no contribution), validity, depth t,
-    colour [P, L, 3] (broadcast), camera-space unit normal [P, L, 3] and decision margins."""
+    colour [P, L, 3] (broadcast), camera-space unit normal [P, L, 3], Gaussian curvature
+    at the hit and decision margins. density: "geodesic" (the paper's) or "euclid"."""
+    weight_fn = {"geodesic": geodesic_gaussian, "euclid": euclid_gaussian}[density]
     mu = prm.mean[idx]
     R = quat_to_rot(prm.quat[idx])                  # [L,3,3] columns = local axes (world)
     su, sv = prm.scale[idx].unbind(-1)
@@ -447,7 +485,7 @@ def _eval_pairs(prm: Params, cam: CamF64, idx: torch.Tensor, px: torch.Tensor, p
         ts = torch.where(ok, t, torch.zeros_like(t))
         x = ox + ts * dx
         y = oy + ts * dy
-        G, l, sig = geodesic_gaussian(x, y, a, b, su, sv)
+        G, l, sig = weight_fn(x, y, a, b, su, sv)
         inside = ok & (l <= CUTOFF * sig)
         margin = torch.where(ok, (l - CUTOFF * sig).abs() / (CUTOFF * sig), torch.full_like(l, np.inf))
         return ts, x, y, G, inside, margin.detach()
@@ -488,12 +526,34 @@ def _eval_pairs(prm: Params, cam: CamF64, idx: torch.Tensor, px: torch.Tensor, p
     margin = torch.minimum(torch.minimum(m_D, m_near),
                            torch.minimum(m_sig, torch.minimum(m_amin, m_amax)))
     cond = torch.where(valid, m_cond, torch.full_like(m_cond, np.inf))
-    return dict(alpha=alpha, valid=valid, hit=hit, t=t, rgb=rgb, normal=n_c, margin=margin, cond=cond)
+    K = gaussian_curvature(x, y, a, b)
+    return dict(alpha=alpha, valid=valid, hit=hit, t=t, rgb=rgb, normal=n_c, curvature=K, margin=margin, cond=cond)
 
 
-def _composite(prm, cam, idx, px, py, chunk=4096):
+MEDIAN_T = 0.5   # median depth: the largest hit depth among blended pairs with T_i > 0.5
+
+
+def _distortion(w: torch.Tensor, t: torch.Tensor, block: int = 32) -> torch.Tensor:
+    """Depth distortion of each pixel (Sec. 3.3, depth distortion Eq.):
+    sum_i sum_{j<i} w_i w_j (t_i - t_j)^2 over the pixel's blended pairs in order, summed
+    as written (blocks of i only bound the memory)."""
+    P, L = w.shape
+    out = torch.zeros(P, dtype=F64)
+    jj = torch.arange(L)
+    for i0 in range(0, L, block):
+        i1 = min(i0 + block, L)
+        diff = t[:, i0:i1, None] - t[:, None, :i1]                        # [P, B, i1]
+        below = (jj[None, :i1] < torch.arange(i0, i1)[:, None]).to(F64)  # j < i
+        out = out + (w[:, i0:i1, None] * w[:, None, :i1] * diff * diff * below[None]).sum((1, 2))
+    return out
+
+
+def _composite(prm, cam, idx, px, py, chunk=4096, density="geodesic", extras=False):
     """Front-to-back alpha blending of a pixel set over one sorted primitive list
-    (blending Eq. of Sec. 3.1 and X_hat = sum alpha_i T_i X_i of the supplementary)."""
+    (blending Eq. of Sec. 3.1 and X_hat = sum alpha_i T_i X_i of the supplementary).
+    extras: also the curvature map (Sec. 3.2.1, N/K rendering Eq.), the depth distortion
+    (Sec. 3.3) and the median depth (Sec. 4.1, max t_i with T_i > 0.5; 0 where no blended
+    pair qualifies)."""
     P = px.shape[0]
     dev = dict(dtype=F64)
     T = torch.ones(P, **dev)
@@ -506,11 +566,16 @@ def _composite(prm, cam, idx, px, py, chunk=4096):
     margin = torch.full((P,), np.inf, **dev)
     cond = torch.full((P,), np.inf, **dev)
     list_cond = None
+    curv = torch.zeros(P, **dev)
+    curv_scale = torch.zeros(P, **dev)
+    median = torch.zeros(P, **dev)
+    m_median = torch.full((P,), np.inf, **dev)
+    w_cols, t_cols = [], []
     L = idx.shape[0]
     for c0 in range(0, L, chunk):
         sl = idx[c0:c0 + chunk]
         Lc = sl.shape[0]
-        pe = _eval_pairs(prm, cam, sl, px, py)
+        pe = _eval_pairs(prm, cam, sl, px, py, density)
         al, v = pe["alpha"], pe["valid"]
         onem = 1.0 - al
         cp = torch.cumprod(onem, dim=1)
@@ -527,6 +592,16 @@ def _composite(prm, cam, idx, px, py, chunk=4096):
         rgb = rgb + (w[..., None] * pe["rgb"][None, :, :]).sum(1)
         depth = depth + (w * pe["t"]).sum(1)
         normal = normal + (w[..., None] * pe["normal"]).sum(1)
+        if extras:
+            curv = curv + (w * pe["curvature"]).sum(1)
+            curv_scale = curv_scale + (w * pe["curvature"].abs()).sum(1).detach()
+            med_ok = keep & (Tex > MEDIAN_T)
+            tm = torch.where(med_ok, pe["t"], torch.zeros_like(pe["t"])).detach()
+            median = torch.maximum(median, tm.max(1).values)
+            mm_ = torch.where(keep, (Tex - MEDIAN_T).abs().detach() / MEDIAN_T, torch.full_like(Tex, np.inf))
+            m_median = torch.minimum(m_median, mm_.min(1).values)
+            w_cols.append(w)
+            t_cols.append(torch.where(keep, pe["t"], torch.zeros_like(pe["t"])))
         T = T * torch.where(keep, onem, torch.ones_like(onem)).prod(1)
         mm = torch.minimum(pe["margin"], m_T)
         margin = torch.minimum(margin, torch.where(seen, mm, torch.full_like(mm, np.inf)).min(1).values)
@@ -543,12 +618,21 @@ def _composite(prm, cam, idx, px, py, chunk=4096):
     if list_cond is None or list_cond.shape[0] < L:
         pad = torch.full((L - (0 if list_cond is None else list_cond.shape[0]),), np.inf, **dev)
         list_cond = pad if list_cond is None else torch.cat([list_cond, pad])
-    return dict(rgb=rgb, alpha=1.0 - T, depth=depth, normal=normal, T_final=T,
-                n_eval=n_eval, n_contrib=n_contrib, margin=margin, cond=cond, list_cond=list_cond)
+    res = dict(rgb=rgb, alpha=1.0 - T, depth=depth, normal=normal, T_final=T,
+               n_eval=n_eval, n_contrib=n_contrib, margin=margin, cond=cond, list_cond=list_cond)
+    if extras:
+        if w_cols:
+            dist = _distortion(torch.cat(w_cols, 1), torch.cat(t_cols, 1))
+        else:
+            dist = torch.zeros(P, **dev)
+        res.update(curvature=curv, curvature_scale=curv_scale, distortion=dist, median_depth=median,
+                   margin_median=m_median)
+    return res
 
 
 # =========================================================================== images
 OUT_KEYS = ("rgb", "alpha", "depth", "normal")
+EXTRA_KEYS = ("curvature", "distortion", "median_depth")
 
 
 def _tile_pixels(cam, tile, TX):
@@ -558,12 +642,16 @@ def _tile_pixels(cam, tile, TX):
     return xs.reshape(-1), ys.reshape(-1)
 
 
-def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=None):
+def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=None, density="geodesic",
+           extras=False):
     """Render the full image (or the listed tiles). Returns a dict of numpy arrays:
     rgb [3,H,W], alpha [H,W], depth [H,W], normal [3,H,W], margin [H,W], n_eval [H,W],
-    n_contrib [H,W], T_final [H,W]. With `grad_images` (a dict of upstream gradients
-    with the same shapes as the outputs), also returns `grads`: the exact FP64 gradient
-    of sum(grad * output) with respect to every scene parameter."""
+    n_contrib [H,W], T_final [H,W]; with `extras` also curvature, distortion,
+    median_depth, curvature_scale (sum w |K|) and margin_median [H,W]. With
+    `grad_images` (a dict of upstream gradients with the same shapes as the outputs;
+    curvature and distortion may be included, the median depth has none), also returns
+    `grads`: the exact FP64 gradient of sum(grad * output) with respect to every scene
+    parameter. density: "geodesic" (the paper's) or "euclid"."""
     if binning is None:
         binning = bin_fp32(scene, cam)
     want_grad = grad_images is not None
@@ -574,6 +662,10 @@ def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=N
                normal=np.zeros((3, H, W)), margin=np.full((H, W), np.inf), cond=np.full((H, W), np.inf),
                n_eval=np.zeros((H, W), np.int64), n_contrib=np.zeros((H, W), np.int64),
                T_final=np.ones((H, W)), prim_cond=np.full(scene.n, np.inf))
+    if extras:
+        for k in ("curvature", "distortion", "median_depth", "curvature_scale"):
+            out[k] = np.zeros((H, W))
+        out["margin_median"] = np.full((H, W), np.inf)
     TX = binning.tiles_x
     if tiles is None:
         tiles = range(binning.tiles_x * binning.tiles_y)
@@ -593,11 +685,16 @@ def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=N
         px = torch.tensor(xs, dtype=F64)
         py = torch.tensor(ys, dtype=F64)
         with torch.set_grad_enabled(want_grad):
-            r = _composite(prm, c64, idx, px, py)
+            r = _composite(prm, c64, idx, px, py, density=density, extras=extras)
             if want_grad:
                 loss = ((g["rgb"][:, ys, xs].T * r["rgb"]).sum() + (g["alpha"][ys, xs] * r["alpha"]).sum()
                         + (g["depth"][ys, xs] * r["depth"]).sum()
                         + (g["normal"][:, ys, xs].T * r["normal"]).sum())
+                for k in ("curvature", "distortion"):
+                    if k in g:
+                        if not extras:
+                            raise ValueError(f"grad_images[{k!r}] needs extras=True")
+                        loss = loss + (g[k][ys, xs] * r[k]).sum()
                 if loss.requires_grad:
                     loss.backward()
         out["rgb"][:, ys, xs] = r["rgb"].detach().numpy().T
@@ -610,6 +707,9 @@ def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=N
         out["n_eval"][ys, xs] = r["n_eval"].numpy()
         out["n_contrib"][ys, xs] = r["n_contrib"].numpy()
         out["T_final"][ys, xs] = r["T_final"].detach().numpy()
+        if extras:
+            for k in ("curvature", "distortion", "median_depth", "curvature_scale", "margin_median"):
+                out[k][ys, xs] = r[k].detach().numpy()
     if want_grad:
         grads = {}
         for k, v in prm.leaves().items():
@@ -621,7 +721,7 @@ def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=N
     return out
 
 
-def render_pixels(scene, cam, pixels, binning: Binning | None = None):
+def render_pixels(scene, cam, pixels, binning: Binning | None = None, density="geodesic", extras=False):
     """Render individual pixels [(x, y), ...] one at a time (same lists and order as
     the full image). Returns dict of arrays indexed like `pixels`."""
     if binning is None:
@@ -629,7 +729,10 @@ def render_pixels(scene, cam, pixels, binning: Binning | None = None):
     prm = Params(scene)
     c64 = CamF64(cam)
     TX = binning.tiles_x
-    res = {k: [] for k in ("rgb", "alpha", "depth", "normal", "margin", "cond", "n_eval", "n_contrib")}
+    keys = ["rgb", "alpha", "depth", "normal", "margin", "cond", "n_eval", "n_contrib"]
+    if extras:
+        keys += ["curvature", "distortion", "median_depth", "curvature_scale", "margin_median"]
+    res = {k: [] for k in keys}
     lists = {}
     for (x, y) in pixels:
         tile = (y // TILE) * TX + (x // TILE)
@@ -643,7 +746,7 @@ def render_pixels(scene, cam, pixels, binning: Binning | None = None):
         idx = torch.from_numpy(lst.astype(np.int64))
         with torch.no_grad():
             r = _composite(prm, c64, idx, torch.tensor([float(x)], dtype=F64),
-                           torch.tensor([float(y)], dtype=F64))
+                           torch.tensor([float(y)], dtype=F64), density=density, extras=extras)
         for k in res:
             res[k].append(r[k][0].numpy())
     return {k: np.array(v) for k, v in res.items()}
