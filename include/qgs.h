@@ -80,12 +80,20 @@ typedef struct {
 } qgs_scene;
 
 /* Image planes (device pointers). Output of render_forward (fully overwritten) or the
- * upstream gradient given to render_backward (read only). */
+ * upstream gradient given to render_backward (read only). The last three planes are
+ * optional extra channels (NULL: not rendered / zero gradient); the first four are
+ * required in a forward. Planar layout, row-major, w_i = alpha_i T_i of the i-th blended
+ * pair in list order, t_i its hit depth. */
 typedef struct {
   float* rgb;      /* [3*H*W] */
   float* alpha;    /* [H*W]   1 - final transmittance */
   float* depth;    /* [H*W]   sum_i w_i t_i (unnormalised expected z depth) */
   float* normal;   /* [3*H*W] sum_i w_i n_i, camera space, each n_i facing the camera */
+  float* curvature;    /* [H*W] sum_i w_i K_i, K_i the Gaussian curvature 4ab/(1+4a^2x^2+4b^2y^2)^2
+                          at the local hit (x, y) (Sec. 3.2.1, curvature and N/K Eqs.) */
+  float* distortion;   /* [H*W] sum_i sum_{j<i} w_i w_j (t_i - t_j)^2 (Sec. 3.3 depth distortion) */
+  float* median_depth; /* [H*W] max t_i over blended pairs with T_i > 0.5, 0 if none (Sec. 4.1);
+                          forward only: its gradient plane must be NULL */
 } qgs_image;
 
 /* Gradients of a scalar loss with respect to the scene parameters (device pointers,
@@ -103,7 +111,7 @@ typedef struct {
 /* Blending constants and pipeline options. qgs_config_default() gives the values the
  * oracle and the tests use: alpha_max 0.99, alpha_min 1/255, T_min 1e-4,
  * grazing_eps 1e-5 (roots whose discriminant D satisfies |D| <= grazing_eps * B^2 are
- * re-solved in FP64), sort_mode 0. */
+ * re-solved in FP64), sort_mode 0, density 0. */
 typedef struct {
   float alpha_max;
   float alpha_min;
@@ -113,7 +121,9 @@ typedef struct {
                           (tile, primitive) instances by tile: the same order as sorting
                           the 64-bit keys, with fewer passes over the instances.
                           1: one radix sort of the full 64-bit tile|depth keys. */
-  int32_t reserved;
+  int32_t density;     /* 0: geodesic Gaussian (the paper's, Sec. 3.2); 1: Euclidean-distance
+                          Gaussian, l = sqrt(rho^2 + z^2) from the vertex with the same
+                          sigma(theta) (the "w/ Euclid" variant of Sec. 4.3) */
 } qgs_config;
 
 /* Counters of the last render_forward / render_backward. Pair counters classify the
@@ -155,9 +165,10 @@ void qgs_destroy(qgs_ctx* ctx);
 const char* qgs_last_error(const qgs_ctx* ctx);
 
 /* Forward render (Sec. 3.1-3.2, supplementary): preprocessing, tile binning, radix sort,
- * per-tile compositing. Writes all four planes of `out` (W*H from `cam`). Keeps the
- * per-pixel residue (final transmittance and the count of listed primitives up to the
- * last blended one) and the sorted lists in the context for render_backward.
+ * per-tile compositing. Writes the four base planes of `out` (W*H from `cam`) and each
+ * non-NULL extra plane. Keeps the per-pixel residue (final transmittance, the count of
+ * listed primitives up to the last blended one and, when an extra plane was requested,
+ * the distortion's moments) and the sorted lists in the context for render_backward.
  * Errors: EINVAL, ENOMEM, ECUDA. */
 qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera* cam,
                           const qgs_image* out, qgs_stream stream);
@@ -171,8 +182,9 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
  * from the sum of the earlier views' tile counts, one tile sort and one compositing
  * launch cover every view. Each view's planes equal render_forward's for that camera
  * bit for bit. Work buffers scale with n_views * n primitive entries; n_views * n must
- * stay below 2^31 and n_views in [1, 1024]. The instance order is always the
- * factorised one (qgs_config.sort_mode is ignored). No residue is kept:
+ * stay below 2^31 and n_views in [1, 1024]. Extra planes may be requested per view.
+ * The instance order is always the factorised one (qgs_config.sort_mode is ignored). No
+ * residue is kept:
  * render_backward cannot follow it, and the context's last frame is cleared.
  * Errors: EINVAL, ENOMEM, ECUDA. */
 qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_views,
@@ -181,7 +193,9 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
 /* Backward of the last render_forward on this context (same scene pointers, same camera):
  * reverse-order traversal per pixel with transmittance recomputed from the residue
  * (supplementary, dX/d(alpha) back-to-front form), then the chain rule to every primitive
- * parameter. grad_out holds dL/d(rgb, alpha, depth, normal); a NULL plane means zero.
+ * parameter. grad_out holds dL/d(rgb, alpha, depth, normal, curvature, distortion); a
+ * NULL plane means zero; median_depth must be NULL (EINVAL). A distortion gradient needs
+ * a forward that rendered at least one extra plane (ESTATE otherwise).
  * Results are ADDED into `grad`. Errors: EINVAL, ESTATE, ENOMEM, ECUDA. */
 qgs_status render_backward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera* cam,
                            const qgs_image* grad_out, const qgs_scene_grad* grad,
@@ -226,9 +240,9 @@ qgs_status qgs_copy_residue(qgs_ctx* ctx, float* T_final, uint32_t* n_contrib);
  *   All calls in the process share the array and leave their contents in it (each call
  *   clears what must start at zero): calls whose GPU work overlaps (concurrent streams,
  *   host threads) race and corrupt each other's results; serialise them.
- *   Scene/camera/output pointers follow the conventions above; the call synchronises
- *   `stream` once. Errors: EINVAL, ECAPACITY, ECUDA. No per-call residue is kept, so
- *   render_backward cannot follow it. */
+ *   Scene/camera/output pointers follow the conventions above (base planes only: the
+ *   extra planes must be NULL); the call synchronises `stream` once. Errors: EINVAL,
+ *   ECAPACITY, ECUDA. No per-call residue is kept, so render_backward cannot follow it. */
 qgs_status render_forward_noalloc(const qgs_scene* scene, const qgs_camera* cam, const qgs_image* out,
                                   qgs_stream stream);
 

@@ -73,7 +73,8 @@ qgs_status serve_submit(qgs_server* srv, int32_t scene_id, const qgs_camera* cam
 
 /* Wait up to timeout_ms (< 0: no limit) for a ticket to finish, then copy its planes
  * into `out` (rgb 3HW, alpha HW, depth HW, normal 3HW floats; any plane may be NULL;
- * host or device pointers) and release the ticket. The copy is ordered after work on
+ * host or device pointers; the extra planes of qgs_image are not served and must be
+ * NULL) and release the ticket. The copy is ordered after work on
  * the legacy default stream; work on other streams that writes `out` must be finished
  * by the caller. Returns after the copy has completed. Errors: ENOTFOUND (unknown or
  * already released ticket), ETIMEDOUT (still running; the ticket stays valid), the

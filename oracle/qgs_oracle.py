@@ -648,8 +648,9 @@ def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=N
     rgb [3,H,W], alpha [H,W], depth [H,W], normal [3,H,W], margin [H,W], n_eval [H,W],
     n_contrib [H,W], T_final [H,W]; with `extras` also curvature, distortion,
     median_depth, curvature_scale (sum w |K|) and margin_median [H,W]. With
-    `grad_images` (a dict of upstream gradients with the same shapes as the outputs;
-    curvature and distortion may be included, the median depth has none), also returns
+    `grad_images` (a dict of upstream gradients with the same shapes as the outputs,
+    missing ones zero; curvature and distortion may be included, the median depth has
+    none), also returns
     `grads`: the exact FP64 gradient of sum(grad * output) with respect to every scene
     parameter. density: "geodesic" (the paper's) or "euclid"."""
     if binning is None:
@@ -687,12 +688,13 @@ def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=N
         with torch.set_grad_enabled(want_grad):
             r = _composite(prm, c64, idx, px, py, density=density, extras=extras)
             if want_grad:
-                loss = ((g["rgb"][:, ys, xs].T * r["rgb"]).sum() + (g["alpha"][ys, xs] * r["alpha"]).sum()
-                        + (g["depth"][ys, xs] * r["depth"]).sum()
-                        + (g["normal"][:, ys, xs].T * r["normal"]).sum())
-                for k in ("curvature", "distortion"):
+                loss = torch.zeros((), dtype=F64)
+                for k in ("rgb", "normal"):
                     if k in g:
-                        if not extras:
+                        loss = loss + (g[k][:, ys, xs].T * r[k]).sum()
+                for k in ("alpha", "depth", "curvature", "distortion"):
+                    if k in g:
+                        if k not in r:
                             raise ValueError(f"grad_images[{k!r}] needs extras=True")
                         loss = loss + (g[k][ys, xs] * r[k]).sum()
                 if loss.requires_grad:

@@ -33,7 +33,8 @@ class qgs_scene(C.Structure):
 
 
 class qgs_image(C.Structure):
-    _fields_ = [("rgb", C.c_void_p), ("alpha", C.c_void_p), ("depth", C.c_void_p), ("normal", C.c_void_p)]
+    _fields_ = [("rgb", C.c_void_p), ("alpha", C.c_void_p), ("depth", C.c_void_p), ("normal", C.c_void_p),
+                ("curvature", C.c_void_p), ("distortion", C.c_void_p), ("median_depth", C.c_void_p)]
 
 
 class qgs_scene_grad(C.Structure):
@@ -43,7 +44,7 @@ class qgs_scene_grad(C.Structure):
 
 class qgs_config(C.Structure):
     _fields_ = [("alpha_max", C.c_float), ("alpha_min", C.c_float), ("T_min", C.c_float),
-                ("grazing_eps", C.c_float), ("sort_mode", C.c_int32), ("reserved", C.c_int32)]
+                ("grazing_eps", C.c_float), ("sort_mode", C.c_int32), ("density", C.c_int32)]
 
 
 class qgs_frame_stats(C.Structure):

@@ -205,7 +205,8 @@ struct qgs_ctx {
   int id_stride = 1;
   const uint64_t* sorted_keys = nullptr;
   cudaStream_t last_stream = nullptr;
-  bool bwd_attr_set = false;
+  DevBuf<float> resid;            // extra-channel residue (c, A1, A2) [3P] of the last forward
+  bool have_resid = false;        // the last forward rendered the extra channels
   // profiling: events at stage boundaries (forward 0..6, backward 7..9)
   bool profiling = false;
   bool have_fwd_times = false, have_bwd_times = false;
@@ -305,7 +306,7 @@ void qgs_config_default(qgs_config* cfg) {
   cfg->T_min = 1e-4f;
   cfg->grazing_eps = 1e-5f;
   cfg->sort_mode = 0;
-  cfg->reserved = 0;
+  cfg->density = 0;
 }
 
 qgs_status qgs_create(qgs_ctx** out, const qgs_config* cfg, int32_t device) {
@@ -316,7 +317,8 @@ qgs_status qgs_create(qgs_ctx** out, const qgs_config* cfg, int32_t device) {
   qgs_config_default(&c->cfg);
   if (cfg) {
     if (!(cfg->alpha_max > 0 && cfg->alpha_max < 1 && cfg->alpha_min >= 0 && cfg->alpha_min < cfg->alpha_max &&
-          cfg->T_min > 0 && cfg->T_min < 1 && cfg->grazing_eps >= 0 && (cfg->sort_mode == 0 || cfg->sort_mode == 1))) {
+          cfg->T_min > 0 && cfg->T_min < 1 && cfg->grazing_eps >= 0 && (cfg->sort_mode == 0 || cfg->sort_mode == 1) &&
+          (cfg->density == 0 || cfg->density == 1))) {
       delete c;
       return QGS_EINVAL;
     }
@@ -351,6 +353,7 @@ void qgs_destroy(qgs_ctx* c) {
   c->dcount.release(); c->tkey.release(); c->tkey2.release(); c->torder.release(); c->torder2.release();
   c->inst_used.release();
   c->vdesc.release();
+  c->resid.release();
   if (c->h_vdesc) cudaFreeHost(c->h_vdesc);
   if (c->vdesc_done) cudaEventDestroy(c->vdesc_done);
   if (c->h_total) cudaFreeHost(c->h_total);
@@ -400,6 +403,8 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   QGS_CU(ctx->torder2.reserve((size_t)ntiles), "alloc tile order");
   QGS_CU(ctx->T_final.reserve((size_t)P), "alloc T_final");
   QGS_CU(ctx->n_contrib.reserve((size_t)P), "alloc n_contrib");
+  const bool extra = out->curvature || out->distortion || out->median_depth;
+  if (extra) QGS_CU(ctx->resid.reserve((size_t)P * 3), "alloc residue");
   QGS_CU(ctx->hist.reserve(radix_hist_elems((int64_t)n1)), "alloc hist");
   QGS_CU(ctx->scan_tmp.reserve(scan_tmp_elems((int64_t)radix_hist_elems((int64_t)n1) + (int64_t)n1)), "alloc scan");
   SortTemp tmp;
@@ -512,18 +517,19 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   }
   QGS_CU(cudaMemsetAsync(ctx->stats.p, 0, sizeof(RasterStats), st), "memset stats");
   mark(ctx, 5, st);
-  k_raster_fwd<<<(unsigned)ntiles, BLOCK, 0, st>>>(ctx->ranges.p, ctx->ids, ctx->id_stride, ctx->state.p, rp,
-                                                   out->rgb, out->alpha, out->depth, out->normal, ctx->T_final.p,
-                                                   ctx->n_contrib.p, ctx->stats.p, ctx->tile_order,
-                                                   ctx->inst_used.p);
+  const ExtraPlanes ex{out->curvature, out->distortion, out->median_depth, extra ? ctx->resid.p : nullptr};
+  QGS_CU(launch_raster_fwd(ctx->cfg.density == 1, extra, (unsigned)ntiles, st, ctx->ranges.p, ctx->ids,
+                           ctx->id_stride, ctx->state.p, rp, out->rgb, out->alpha, out->depth, out->normal,
+                           ctx->T_final.p, ctx->n_contrib.p, ex, ctx->stats.p, ctx->tile_order, ctx->inst_used.p),
+         "k_raster_fwd");
   ++launch_counter();
-  QGS_CU(cudaGetLastError(), "k_raster_fwd");
   mark(ctx, 6, st);
   ctx->have_fwd_times = ctx->profiling;
   ctx->have_bwd_times = false;
   ctx->launches_fwd = launch_counter() - launches0;
   ctx->launches_bwd = 0;
   ctx->have_frame = true;
+  ctx->have_resid = extra;
   ctx->have_stats = true;
   ctx->n_tiles_total = ntiles;
   ctx->n = N;
@@ -572,6 +578,7 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
   cudaStream_t st = (cudaStream_t)stream;
   QGS_CU(cudaSetDevice(ctx->device), "cudaSetDevice");
   ctx->have_frame = false;
+  ctx->have_resid = false;
   ctx->have_stats = false;
   ctx->have_fwd_times = false;
   ctx->have_bwd_times = false;
@@ -592,6 +599,7 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
     ctx->h_vdesc_cap = vbytes;
   }
   QGS_CU(ctx->vdesc.reserve(vbytes), "alloc view descriptors");
+  bool extra = false;
   {
     uint8_t* h = ctx->h_vdesc;
     CamParams* hc = reinterpret_cast<CamParams*>(h);
@@ -607,6 +615,8 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
       hv[v].normal = outs[v].normal;
       hv[v].T_final = nullptr;
       hv[v].n_contrib = nullptr;
+      hv[v].ex = ExtraPlanes{outs[v].curvature, outs[v].distortion, outs[v].median_depth, nullptr};
+      extra = extra || outs[v].curvature || outs[v].distortion || outs[v].median_depth;
       hb[v] = base[v];
       ht[v] = make_int2(cps[v].tiles_x, (int)base[v]);
     }
@@ -702,10 +712,10 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
   QGS_CU(e, "tile schedule sort");
   const uint32_t* order = flt ? ctx->torder2.p : ctx->torder.p;
   QGS_CU(cudaMemsetAsync(ctx->stats.p, 0, sizeof(RasterStats), st), "memset stats");
-  k_raster_fwd_views<<<(unsigned)T_all, BLOCK, 0, st>>>(ctx->ranges.p, ids, 2, ctx->state.p, d_vd, V, d_tb,
-                                                        ctx->stats.p, order);
+  QGS_CU(launch_raster_fwd_views(ctx->cfg.density == 1, extra, (unsigned)T_all, st, ctx->ranges.p, ids, 2,
+                                 ctx->state.p, d_vd, V, d_tb, ctx->stats.p, order),
+         "k_raster_fwd_views");
   ++launch_counter();
-  QGS_CU(cudaGetLastError(), "k_raster_fwd_views");
   ctx->launches_fwd = launch_counter() - launches0;
   ctx->launches_bwd = 0;
   ctx->have_stats = true;
@@ -726,6 +736,10 @@ qgs_status render_backward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camer
   if (!ctx->have_frame) return fail(ctx, QGS_ESTATE, "render_backward without a preceding render_forward");
   if (scene->n != ctx->n || scene->mean != ctx->scene_mean || cam->W != ctx->W || cam->H != ctx->H)
     return fail(ctx, QGS_ESTATE, "render_backward scene/camera differ from the last render_forward");
+  if (grad_out->median_depth)
+    return fail(ctx, QGS_EINVAL, "the median depth has no gradient: grad_out->median_depth must be NULL");
+  if (grad_out->distortion && !ctx->have_resid)
+    return fail(ctx, QGS_ESTATE, "a distortion gradient needs a forward that rendered an extra channel");
   if (scene->n > 0 && (!grad->mean || !grad->quat || !grad->scale || !grad->curv || !grad->opacity || !grad->sh))
     return fail(ctx, QGS_EINVAL, "gradient buffer is NULL");
   if (scene->n > 0 && ((((uintptr_t)grad->quat) & 15) || (((uintptr_t)grad->sh) & 15) ||
@@ -742,19 +756,16 @@ qgs_status render_backward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camer
   QGS_CU(cudaMemsetAsync(ctx->pgrad.p, 0, sizeof(float) * (size_t)N * NGRAD_PAD, st), "memset pgrad");
   const int64_t ntiles = (int64_t)cp.tiles_x * cp.tiles_y;
   const int64_t launches0 = launch_counter();
-  if (!ctx->bwd_attr_set) {
-    QGS_CU(cudaFuncSetAttribute(k_raster_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RASTER_BWD_SMEM),
-           "smem attribute");
-    ctx->bwd_attr_set = true;
-  }
+  const bool euclid = ctx->cfg.density == 1;
+  const bool extra = grad_out->curvature || grad_out->distortion;
+  const ExtraGrads eg{grad_out->curvature, grad_out->distortion, ctx->have_resid ? ctx->resid.p : nullptr};
   mark(ctx, 7, st);
-  k_raster_bwd<<<(unsigned)ntiles, BLOCK, RASTER_BWD_SMEM, st>>>(ctx->ranges.p, ctx->ids, ctx->id_stride,
-                                                                 ctx->state.p, rp, grad_out->rgb, grad_out->alpha,
-                                                                 grad_out->depth, grad_out->normal, ctx->T_final.p,
-                                                                 ctx->n_contrib.p, ctx->pgrad.p, ctx->stats.p,
-                                                                 ctx->tile_order, ctx->inst_used.p);
+  QGS_CU(launch_raster_bwd(euclid, extra, (unsigned)ntiles, st, ctx->ranges.p, ctx->ids, ctx->id_stride,
+                           ctx->state.p, rp, grad_out->rgb, grad_out->alpha, grad_out->depth, grad_out->normal,
+                           ctx->T_final.p, ctx->n_contrib.p, eg, ctx->pgrad.p, ctx->stats.p, ctx->tile_order,
+                           ctx->inst_used.p),
+         "k_raster_bwd");
   ++launch_counter();
-  QGS_CU(cudaGetLastError(), "k_raster_bwd");
   mark(ctx, 8, st);
   SceneView sv{scene->mean, scene->quat, scene->scale, scene->curv, scene->opacity, scene->sh};
   GradView gv{grad->mean, grad->quat, grad->scale, grad->curv, grad->opacity, grad->sh};
@@ -933,6 +944,7 @@ extern "C" qgs_status render_forward_noalloc(const qgs_scene* scene, const qgs_c
     return QGS_EINVAL;
   if (cam->W <= 0 || cam->H <= 0 || !finite_cam(cam)) return QGS_EINVAL;
   if (!out->rgb || !out->alpha || !out->depth || !out->normal) return QGS_EINVAL;
+  if (out->curvature || out->distortion || out->median_depth) return QGS_EINVAL;  // base planes only
   const int64_t N = scene->n;
   const int64_t P = (int64_t)cam->W * cam->H;
   const int64_t TX = (cam->W + TILE - 1) / TILE, TY = (cam->H + TILE - 1) / TILE;
@@ -1016,9 +1028,9 @@ extern "C" qgs_status render_forward_noalloc(const qgs_scene* scene, const qgs_c
     k_tile_ranges<<<nblk(I), 256, 0, st>>>(I, sorted, ranges);
     QGS_CU(cudaGetLastError(), "ranges");
   }
-  k_raster_fwd<<<(unsigned)ntiles, BLOCK, 0, st>>>(ranges, reinterpret_cast<const uint32_t*>(sorted), 2, state, rp,
-                                                   out->rgb, out->alpha, out->depth, out->normal, T_final,
-                                                   n_contrib, stats, nullptr, nullptr);
-  QGS_CU(cudaGetLastError(), "k_raster_fwd");
+  QGS_CU(launch_raster_fwd(false, false, (unsigned)ntiles, st, ranges, reinterpret_cast<const uint32_t*>(sorted), 2,
+                           state, rp, out->rgb, out->alpha, out->depth, out->normal, T_final, n_contrib,
+                           ExtraPlanes{}, stats, nullptr, nullptr),
+         "k_raster_fwd");
   return QGS_OK;
 }

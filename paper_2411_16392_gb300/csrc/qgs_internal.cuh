@@ -81,26 +81,43 @@ inline int64_t& launch_counter() {
   return n;
 }
 
+// Optional extra output planes of the forward (device, any may be null): curvature map,
+// depth distortion, median depth, and the per-pixel residue (c, A1, A2) [3P] that the
+// distortion's backward reads.
+struct ExtraPlanes {
+  float *curvature, *distortion, *median_depth, *resid;
+};
+// Upstream gradients of the extra planes (null: zero) and the forward's residue.
+struct ExtraGrads {
+  const float *g_curvature, *g_distortion, *resid;
+};
+
 // One view of a batched forward: its raster constants and output planes (device).
 struct ViewDesc {
   RasterParams rp;
   float *rgb, *alpha, *depth, *normal;
   float* T_final;        // may be null (no residue kept)
   uint32_t* n_contrib;   // may be null
+  ExtraPlanes ex;        // extra planes (EXTRA instantiation only)
 };
 
-__global__ void k_raster_fwd_views(const uint2* ranges, const uint32_t* ids, int id_stride, const PrimState* state,
-                                   const ViewDesc* views, int n_views, const uint32_t* tile_base,
-                                   RasterStats* stats, const uint32_t* tile_order);
-__global__ void k_raster_fwd(const uint2* ranges, const uint32_t* ids, int id_stride, const PrimState* state,
-                             RasterParams rp, float* out_rgb, float* out_alpha, float* out_depth,
-                             float* out_normal, float* T_final, uint32_t* n_contrib, RasterStats* stats,
-                             const uint32_t* tile_order, uint8_t* inst_used);
+// Compositing launches (defined with the kernels). euclid: Euclidean-distance density
+// instead of the geodesic one; extra: the curvature, distortion and median-depth
+// channels. Each returns the launch's error status.
+cudaError_t launch_raster_fwd(bool euclid, bool extra, unsigned grid, cudaStream_t st, const uint2* ranges,
+                              const uint32_t* ids, int id_stride, const PrimState* state, const RasterParams& rp,
+                              float* out_rgb, float* out_alpha, float* out_depth, float* out_normal, float* T_final,
+                              uint32_t* n_contrib, const ExtraPlanes& ex, RasterStats* stats,
+                              const uint32_t* tile_order, uint8_t* inst_used);
+cudaError_t launch_raster_fwd_views(bool euclid, bool extra, unsigned grid, cudaStream_t st, const uint2* ranges,
+                                    const uint32_t* ids, int id_stride, const PrimState* state,
+                                    const ViewDesc* views, int n_views, const uint32_t* tile_base,
+                                    RasterStats* stats, const uint32_t* tile_order);
 constexpr size_t RASTER_BWD_SMEM = sizeof(PrimState) * BLOCK + sizeof(float) * BLOCK * NGRAD + sizeof(int) * BLOCK;
-__global__ void k_raster_bwd(const uint2* ranges, const uint32_t* ids, int id_stride, const PrimState* state,
-                             RasterParams rp, const float* g_rgb, const float* g_alpha, const float* g_depth,
-                             const float* g_normal, const float* T_final, const uint32_t* n_contrib,
-                             float* pgrad, RasterStats* stats, const uint32_t* tile_order,
-                             const uint8_t* inst_used);
+cudaError_t launch_raster_bwd(bool euclid, bool extra, unsigned grid, cudaStream_t st, const uint2* ranges,
+                              const uint32_t* ids, int id_stride, const PrimState* state, const RasterParams& rp,
+                              const float* g_rgb, const float* g_alpha, const float* g_depth, const float* g_normal,
+                              const float* T_final, const uint32_t* n_contrib, const ExtraGrads& eg, float* pgrad,
+                              RasterStats* stats, const uint32_t* tile_order, const uint8_t* inst_used);
 
 }  // namespace qgs

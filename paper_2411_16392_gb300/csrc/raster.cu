@@ -43,7 +43,7 @@ struct Hit {
   float s;            // root offset: t = z_mu + s
   float x, y, zs;     // local hit point (zs = a x^2 + b y^2)
   float dx, dy, dz;   // local ray direction (camera-space ray with z component 1)
-  float rho2, u, F, E, G;
+  float rho2, u, F2, E, G;  // F2 = F(u)^2: l^2 / sigma(theta)^2 = F2 * E
 };
 
 __device__ __forceinline__ float sqrt_approx(float x) {
@@ -88,8 +88,22 @@ __device__ __forceinline__ float arc_ratio_prime(float u, float F) {
   return (sqrtf(fmaf(u, u, 1.f)) - F) / u;
 }
 
+// d(F^2)/du: geodesic 2 F F'(u); Euclidean (F^2 = 1 + u^2/4) u/2.
+template <bool EUCLID>
+__device__ __forceinline__ float f2_prime(float u, float F2) {
+  if constexpr (EUCLID) {
+    return 0.5f * u;
+  } else {
+    const float F = sqrtf(F2);
+    return 2.f * F * arc_ratio_prime(u, F);
+  }
+}
+
 // Evaluate one (pixel, primitive) pair. Returns true when a root in front of the near
-// plane lies within 3 sigma(theta) (the selected hit is in h, G included).
+// plane lies within 3 sigma(theta) (the selected hit is in h, G included). EUCLID: the
+// Euclidean-distance density (straight-line distance sqrt(rho^2 + z^2) instead of the
+// arc length), for which F(u)^2 = 1 + u^2/4 exactly.
+template <bool EUCLID>
 __device__ __forceinline__ bool eval_pair(const PrimState& P, float X, float Y, const RasterParams& rp, Hit& h,
                                           bool& grazed, uint32_t& isect) {
   const float4 f0 = P.f[0], f1 = P.f[1], f2 = P.f[2];
@@ -128,14 +142,23 @@ __device__ __forceinline__ bool eval_pair(const PrimState& P, float X, float Y, 
     const float rho2 = __fadd_rn(x2, y2);
     const float zs = __fmaf_rn(a, x2, __fmul_rn(b, y2));
     const float v = rho2 > 0.f ? __fmul_rn(zs, rsqrtf(rho2)) : 0.f;  // u / 2
-    if (!(__fmul_rn(E, __fmaf_rn(v, v, 1.f)) <= 9.f)) return false;  // chord: F^2 >= 1 + u^2/4
+    const float F2c = __fmaf_rn(v, v, 1.f);                           // chord: 1 + u^2/4
+    const float Qc = __fmul_rn(E, F2c);
+    if (!(Qc <= 9.f)) return false;  // geodesic: F^2 >= 1 + u^2/4; Euclidean: equality
     const float u = __fmul_rn(2.f, v);
-    const float F = arc_ratio(u);
-    const float Q = __fmul_rn(__fmul_rn(F, F), E);
-    if (!(Q <= 9.f)) return false;
+    float F2, Q;
+    if constexpr (EUCLID) {
+      F2 = F2c;
+      Q = Qc;
+    } else {
+      const float F = arc_ratio(u);
+      F2 = __fmul_rn(F, F);
+      Q = __fmul_rn(F2, E);
+      if (!(Q <= 9.f)) return false;
+    }
     h.s = s; h.x = x; h.y = y; h.zs = zs;
     h.dx = dx; h.dy = dy; h.dz = dz;
-    h.rho2 = rho2; h.u = u; h.F = F; h.E = E;
+    h.rho2 = rho2; h.u = u; h.F2 = F2; h.E = E;
     h.G = __expf(__fmul_rn(-0.5f, Q));
     return true;
   };
@@ -187,16 +210,44 @@ __device__ __forceinline__ void stage_batch(PrimState* sm, const uint32_t* ids, 
 
 }  // namespace
 
+// Gaussian curvature of z = a x^2 + b y^2 at local (x, y) (Sec. 3.2.1 curvature Eq.) and
+// its partial derivatives with respect to a, b, x, y.
+struct Curv {
+  float K, dKda, dKdb, dKdx, dKdy;
+};
+__device__ __forceinline__ float curvature(float a, float b, float x, float y) {
+  const float S = fmaf(4.f * a * a, x * x, fmaf(4.f * b * b, y * y, 1.f));
+  return 4.f * a * b / (S * S);
+}
+__device__ __forceinline__ Curv curvature_grad(float a, float b, float x, float y) {
+  const float S = fmaf(4.f * a * a, x * x, fmaf(4.f * b * b, y * y, 1.f));
+  const float iS = 1.f / S, iS2 = iS * iS;
+  Curv c;
+  c.K = 4.f * a * b * iS2;
+  const float c3 = 2.f * c.K * iS;  // 8ab / S^3
+  c.dKda = 4.f * b * iS2 - c3 * 8.f * a * x * x;
+  c.dKdb = 4.f * a * iS2 - c3 * 8.f * b * y * y;
+  c.dKdx = -c3 * 8.f * a * a * x;
+  c.dKdy = -c3 * 8.f * b * b * y;
+  return c;
+}
+
 // Composite one tile: `tile` indexes the sorted instance ranges, `local_tile` the tile
-// grid of the view (they differ when several views share one launch).
+// grid of the view (they differ when several views share one launch). EXTRA adds the
+// curvature map (Sec. 3.2.1), the depth distortion (Sec. 3.3) and the median depth
+// (Sec. 4.1). The distortion sum_i sum_{j<i} w_i w_j (t_i - t_j)^2 equals
+// A0 A2 - A1^2 with A_k = sum_i w_i tau_i^k for any shift tau = t - c; c is the pixel's
+// first blended depth, which keeps the two terms small (no cancellation at the camera
+// distance). The per-pixel residue (c, A1, A2) serves its backward.
+template <bool EUCLID, bool EXTRA>
 __device__ __forceinline__ void raster_fwd_tile(PrimState* sm, uint8_t* used, int tile, int local_tile,
                                                 const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids,
                                                 int id_stride, const PrimState* __restrict__ state,
                                                 const RasterParams& rp, float* __restrict__ out_rgb,
                                                 float* __restrict__ out_alpha, float* __restrict__ out_depth,
                                                 float* __restrict__ out_normal, float* __restrict__ T_final,
-                                                uint32_t* __restrict__ n_contrib, RasterStats* __restrict__ stats,
-                                                uint8_t* __restrict__ inst_used) {
+                                                uint32_t* __restrict__ n_contrib, const ExtraPlanes& ex,
+                                                RasterStats* __restrict__ stats, uint8_t* __restrict__ inst_used) {
   int px, py;
   pixel_of(local_tile, rp.tiles_x, px, py);
   const bool inside = px < rp.W && py < rp.H;
@@ -205,6 +256,7 @@ __device__ __forceinline__ void raster_fwd_tile(PrimState* sm, uint8_t* used, in
   const float X = (float)px + 0.5f, Y = (float)py + 0.5f;
   const float xn = (X - rp.cx) * rp.inv_fx, yn = (Y - rp.cy) * rp.inv_fy;
   float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, dep = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
+  float kc = 0.f, tref = 0.f, A1 = 0.f, A2 = 0.f, med = 0.f;  // EXTRA channels
   uint32_t last = 0, evals = 0, grazes = 0, isect = 0, hits = 0, blended = 0;
   bool done = !inside;
   for (int b0 = 0; b0 < n; b0 += BLOCK) {
@@ -218,7 +270,7 @@ __device__ __forceinline__ void raster_fwd_tile(PrimState* sm, uint8_t* used, in
         ++evals;
         Hit h;
         bool gz = false;
-        const bool hit = eval_pair(sm[j], X, Y, rp, h, gz, isect);
+        const bool hit = eval_pair<EUCLID>(sm[j], X, Y, rp, h, gz, isect);
         grazes += gz;
         if (!hit) continue;
         ++hits;
@@ -246,6 +298,15 @@ __device__ __forceinline__ void raster_fwd_tile(PrimState* sm, uint8_t* used, in
         nx = fmaf(wn, ncx, nx);
         ny = fmaf(wn, ncy, ny);
         nz = fmaf(wn, ncz, nz);
+        if constexpr (EXTRA) {
+          const float t = f2.w + h.s;
+          kc = fmaf(w, curvature(f5.y, f5.z, h.x, h.y), kc);
+          if (blended == 0) tref = t;
+          const float tau = t - tref;
+          A1 = fmaf(w, tau, A1);
+          A2 = fmaf(w * tau, tau, A2);
+          if (T > 0.5f) med = fmaxf(med, t);
+        }
         T = Tn;
         ++blended;
         used[j] = 1;
@@ -268,6 +329,16 @@ __device__ __forceinline__ void raster_fwd_tile(PrimState* sm, uint8_t* used, in
     out_normal[2 * P + pix] = nz;
     if (T_final) T_final[pix] = T;
     if (n_contrib) n_contrib[pix] = last;
+    if constexpr (EXTRA) {
+      if (ex.curvature) ex.curvature[pix] = kc;
+      if (ex.distortion) ex.distortion[pix] = fmaf(1.f - T, A2, -A1 * A1);
+      if (ex.median_depth) ex.median_depth[pix] = med;
+      if (ex.resid) {
+        ex.resid[pix] = tref;
+        ex.resid[P + pix] = A1;
+        ex.resid[2 * P + pix] = A2;
+      }
+    }
   }
   // counters: one atomic per warp and counter
   if (stats) {
@@ -284,21 +355,24 @@ __device__ __forceinline__ void raster_fwd_tile(PrimState* sm, uint8_t* used, in
   }
 }
 
+template <bool EUCLID, bool EXTRA>
 __global__ void __launch_bounds__(BLOCK, 3)
     k_raster_fwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids, int id_stride,
                  const PrimState* __restrict__ state, RasterParams rp, float* __restrict__ out_rgb,
                  float* __restrict__ out_alpha, float* __restrict__ out_depth, float* __restrict__ out_normal,
-                 float* __restrict__ T_final, uint32_t* __restrict__ n_contrib, RasterStats* __restrict__ stats,
-                 const uint32_t* __restrict__ tile_order, uint8_t* __restrict__ inst_used) {
+                 float* __restrict__ T_final, uint32_t* __restrict__ n_contrib, ExtraPlanes ex,
+                 RasterStats* __restrict__ stats, const uint32_t* __restrict__ tile_order,
+                 uint8_t* __restrict__ inst_used) {
   __shared__ PrimState sm[BLOCK];
   __shared__ uint8_t used[BLOCK];
   const int tile = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;
-  raster_fwd_tile(sm, used, tile, tile, ranges, ids, id_stride, state, rp, out_rgb, out_alpha, out_depth, out_normal,
-                  T_final, n_contrib, stats, inst_used);
+  raster_fwd_tile<EUCLID, EXTRA>(sm, used, tile, tile, ranges, ids, id_stride, state, rp, out_rgb, out_alpha,
+                                 out_depth, out_normal, T_final, n_contrib, ex, stats, inst_used);
 }
 
 // Several views of one scene in one launch: global tile t belongs to the view v with
 // tile_base[v] <= t < tile_base[v + 1].
+template <bool EUCLID, bool EXTRA>
 __global__ void __launch_bounds__(BLOCK, 3)
     k_raster_fwd_views(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids, int id_stride,
                        const PrimState* __restrict__ state, const ViewDesc* __restrict__ views, int n_views,
@@ -314,8 +388,9 @@ __global__ void __launch_bounds__(BLOCK, 3)
   }
   const ViewDesc& vd = views[lo];
   const RasterParams rp = vd.rp;
-  raster_fwd_tile(sm, used, tile, tile - (int)tile_base[lo], ranges, ids, id_stride, state, rp, vd.rgb, vd.alpha,
-                  vd.depth, vd.normal, vd.T_final, vd.n_contrib, stats, nullptr);
+  raster_fwd_tile<EUCLID, EXTRA>(sm, used, tile, tile - (int)tile_base[lo], ranges, ids, id_stride, state, rp,
+                                 vd.rgb, vd.alpha, vd.depth, vd.normal, vd.T_final, vd.n_contrib, vd.ex, stats,
+                                 nullptr);
 }
 
 namespace {
@@ -339,12 +414,17 @@ __device__ __forceinline__ float warp_transpose_sum(float v[32]) {
 
 }  // namespace
 
+// EXTRA: also the gradients of the curvature map and of the depth distortion. With
+// D = A0 A2 - A1^2 (A0 = 1 - T_final, A1, A2 the forward's shifted moments), dL/dA0 =
+// g_D A2 joins the alpha gradient, and tau = t - c and tau^2 act as two more blended
+// channels with upstream gradients -2 g_D A1 and g_D A0.
+template <bool EUCLID, bool EXTRA>
 __global__ void __launch_bounds__(BLOCK, 2)
     k_raster_bwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids, int id_stride,
                  const PrimState* __restrict__ state, RasterParams rp, const float* __restrict__ g_rgb,
                  const float* __restrict__ g_alpha, const float* __restrict__ g_depth,
                  const float* __restrict__ g_normal, const float* __restrict__ T_final,
-                 const uint32_t* __restrict__ n_contrib, float* __restrict__ pgrad,
+                 const uint32_t* __restrict__ n_contrib, ExtraGrads eg, float* __restrict__ pgrad,
                  RasterStats* __restrict__ stats, const uint32_t* __restrict__ tile_order,
                  const uint8_t* __restrict__ inst_used) {
   // dynamic shared memory: BLOCK records, then BLOCK x NGRAD accumulators, then flags
@@ -371,6 +451,20 @@ __global__ void __launch_bounds__(BLOCK, 2)
     if (g_alpha) gA = g_alpha[pix];
     if (g_depth) gD = g_depth[pix];
     if (g_normal) { gNx = g_normal[pix]; gNy = g_normal[P + pix]; gNz = g_normal[2 * P + pix]; }
+  }
+  float gK = 0.f, tref = 0.f, g_tau = 0.f, g_tau2 = 0.f;
+  if constexpr (EXTRA) {
+    if (inside) {
+      if (eg.g_curvature) gK = eg.g_curvature[pix];
+      const float gDist = eg.g_distortion ? eg.g_distortion[pix] : 0.f;
+      if (gDist != 0.f) {
+        tref = eg.resid[pix];
+        const float A1 = eg.resid[P + pix], A2 = eg.resid[2 * P + pix];
+        gA += gDist * A2;
+        g_tau = -2.f * gDist * A1;
+        g_tau2 = gDist * (1.f - T);
+      }
+    }
   }
   if (threadIdx.x == 0) smax = 0;
   __syncthreads();
@@ -400,7 +494,7 @@ __global__ void __launch_bounds__(BLOCK, 2)
         Hit h;
         bool gz = false;
         ++n_pairs;
-        if (eval_pair(sm[j], X, Y, rp, h, gz, isect)) {
+        if (eval_pair<EUCLID>(sm[j], X, Y, rp, h, gz, isect)) {
           const float4 f2 = sm[j].f[2], f3 = sm[j].f[3], f4 = sm[j].f[4], f5 = sm[j].f[5], f6 = sm[j].f[6],
                        f7 = sm[j].f[7];
           const float a = f5.y, b = f5.z, o = f5.w;
@@ -424,13 +518,20 @@ __global__ void __launch_bounds__(BLOCK, 2)
             const float hx = ncx * inn, hy = ncy * inn, hz = ncz * inn;  // unsigned unit normal
             const float nox = sg_ * hx, noy = sg_ * hy, noz = sg_ * hz;
             const float t = f2.w + h.s;
-            const float gX = gR * f7.y + gG * f7.z + gB * f7.w + gD * t + gNx * nox + gNy * noy + gNz * noz;
+            float gX = gR * f7.y + gG * f7.z + gB * f7.w + gD * t + gNx * nox + gNy * noy + gNz * noz;
+            float d_t = w * gD;
+            Curv kv{};
+            if constexpr (EXTRA) {
+              kv = curvature_grad(a, b, x, y);
+              const float tau = t - tref;
+              gX += gK * kv.K + tau * fmaf(g_tau2, tau, g_tau);
+              d_t += w * fmaf(2.f * g_tau2, tau, g_tau);
+            }
             const float dal = T * gX - (Sdot - gA * Tfin) / onem;
             Sdot = fmaf(w, gX, Sdot);
             v[17] = w * gR;
             v[18] = w * gG;
             v[19] = w * gB;
-            const float d_t = w * gD;
             // alpha = min(alpha_max, o G)
             float dG = 0.f;
             if (oG < rp.alpha_max) {
@@ -438,15 +539,21 @@ __global__ void __launch_bounds__(BLOCK, 2)
               dG = dal * o;
             }
             const float dQ = -0.5f * h.G * dG;
-            const float dF = dQ * 2.f * h.F * h.E;
-            const float dE = dQ * h.F * h.F;
+            const float dE = dQ * h.F2;
             v[14] = dE * x * x;
             v[15] = dE * y * y;
             float gx = dE * 2.f * f6.x * x, gy = dE * 2.f * f6.y * y;
             float da = 0.f, db = 0.f;
+            if constexpr (EXTRA) {
+              const float dK = w * gK;
+              da += dK * kv.dKda;
+              db += dK * kv.dKdb;
+              gx += dK * kv.dKdx;
+              gy += dK * kv.dKdy;
+            }
             if (h.rho2 > 0.f) {
               const float irho = rsqrtf(h.rho2);
-              const float du = dF * arc_ratio_prime(h.u, h.F);
+              const float du = dQ * h.E * f2_prime<EUCLID>(h.u, h.F2);
               const float ur = h.u * irho * irho;
               gx += du * (4.f * a * x * irho - ur * x);
               gy += du * (4.f * b * y * irho - ur * y);
@@ -517,5 +624,60 @@ __global__ void __launch_bounds__(BLOCK, 2)
     }
   }
 }
+
+// Host-side selection of the instantiation: runs the statement(s) with the constants
+// E_ (EUCLID) and X_ (EXTRA) set.
+#define QGS_RASTER_DISPATCH(euclid, extra, ...)                          \
+  do {                                                                   \
+    if (euclid) {                                                        \
+      if (extra) { constexpr bool E_ = true, X_ = true; __VA_ARGS__; }   \
+      else { constexpr bool E_ = true, X_ = false; __VA_ARGS__; }        \
+    } else {                                                             \
+      if (extra) { constexpr bool E_ = false, X_ = true; __VA_ARGS__; }  \
+      else { constexpr bool E_ = false, X_ = false; __VA_ARGS__; }       \
+    }                                                                    \
+  } while (0)
+
+cudaError_t launch_raster_fwd(bool euclid, bool extra, unsigned grid, cudaStream_t st, const uint2* ranges,
+                              const uint32_t* ids, int id_stride, const PrimState* state, const RasterParams& rp,
+                              float* out_rgb, float* out_alpha, float* out_depth, float* out_normal, float* T_final,
+                              uint32_t* n_contrib, const ExtraPlanes& ex, RasterStats* stats,
+                              const uint32_t* tile_order, uint8_t* inst_used) {
+  QGS_RASTER_DISPATCH(euclid, extra,
+                      k_raster_fwd<E_, X_><<<grid, BLOCK, 0, st>>>(ranges, ids, id_stride, state, rp, out_rgb,
+                                                                   out_alpha, out_depth, out_normal, T_final,
+                                                                   n_contrib, ex, stats, tile_order, inst_used));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_raster_fwd_views(bool euclid, bool extra, unsigned grid, cudaStream_t st, const uint2* ranges,
+                                    const uint32_t* ids, int id_stride, const PrimState* state,
+                                    const ViewDesc* views, int n_views, const uint32_t* tile_base,
+                                    RasterStats* stats, const uint32_t* tile_order) {
+  QGS_RASTER_DISPATCH(euclid, extra,
+                      k_raster_fwd_views<E_, X_><<<grid, BLOCK, 0, st>>>(ranges, ids, id_stride, state, views,
+                                                                         n_views, tile_base, stats, tile_order));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_raster_bwd(bool euclid, bool extra, unsigned grid, cudaStream_t st, const uint2* ranges,
+                              const uint32_t* ids, int id_stride, const PrimState* state, const RasterParams& rp,
+                              const float* g_rgb, const float* g_alpha, const float* g_depth, const float* g_normal,
+                              const float* T_final, const uint32_t* n_contrib, const ExtraGrads& eg, float* pgrad,
+                              RasterStats* stats, const uint32_t* tile_order, const uint8_t* inst_used) {
+  cudaError_t e = cudaSuccess;
+  QGS_RASTER_DISPATCH(euclid, extra, {
+    // the records, accumulators and flags exceed the 48 KB static limit
+    e = cudaFuncSetAttribute(k_raster_bwd<E_, X_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)RASTER_BWD_SMEM);
+    if (e == cudaSuccess)
+      k_raster_bwd<E_, X_><<<grid, BLOCK, RASTER_BWD_SMEM, st>>>(ranges, ids, id_stride, state, rp, g_rgb, g_alpha,
+                                                                 g_depth, g_normal, T_final, n_contrib, eg, pgrad,
+                                                                 stats, tile_order, inst_used);
+  });
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+#undef QGS_RASTER_DISPATCH
 
 }  // namespace qgs

@@ -362,6 +362,7 @@ qgs_status serve_submit(qgs_server* s, int32_t scene_id, const qgs_camera* cam, 
 
 qgs_status serve_wait(qgs_server* s, uint64_t ticket, int32_t timeout_ms, const qgs_image* out) {
   if (!s) return QGS_EINVAL;
+  if (out && (out->curvature || out->distortion || out->median_depth)) return QGS_EINVAL;  // base planes only
   Request* r = nullptr;
   {
     std::unique_lock<std::mutex> lk(s->mu);

@@ -57,6 +57,10 @@ def camera_to_c(cam) -> L.qgs_camera:
     return c
 
 
+IMAGE_KEYS = ("rgb", "alpha", "depth", "normal", "curvature", "distortion", "median_depth")
+EXTRA_KEYS = IMAGE_KEYS[4:]
+
+
 def _stream_ptr(device) -> int:
     return torch.cuda.current_stream(device).cuda_stream
 
@@ -64,12 +68,15 @@ def _stream_ptr(device) -> int:
 class Rasterizer:
     """One rendering context (libqgs qgs_ctx) on one CUDA device."""
 
-    def __init__(self, device: int | torch.device = 0, sort_mode: int = 0, **consts):
+    DENSITIES = {"geodesic": 0, "euclid": 1}
+
+    def __init__(self, device: int | torch.device = 0, sort_mode: int = 0, density: str = "geodesic", **consts):
         self.lib = L.load()
         self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
         cfg = L.qgs_config()
         self.lib.qgs_config_default(C.byref(cfg))
         cfg.sort_mode = sort_mode
+        cfg.density = self.DENSITIES[density]
         for k, v in consts.items():
             setattr(cfg, k, v)
         self._ctx = C.c_void_p()
@@ -89,14 +96,17 @@ class Rasterizer:
             pass
 
     # ------------------------------------------------------------------ forward
-    def forward(self, scene: DeviceScene, cam, out: dict | None = None) -> dict:
-        """Render; returns dict rgb [3,H,W], alpha [H,W], depth [H,W], normal [3,H,W]."""
+    def forward(self, scene: DeviceScene, cam, out: dict | None = None, extras: bool = False) -> dict:
+        """Render; returns dict rgb [3,H,W], alpha [H,W], depth [H,W], normal [3,H,W] and,
+        with `extras` (or when `out` holds them), curvature, distortion, median_depth [H,W]."""
         H, W = int(cam.H), int(cam.W)
         if out is None:
             out = dict(rgb=torch.empty(3, H, W, device=self.device), alpha=torch.empty(H, W, device=self.device),
                        depth=torch.empty(H, W, device=self.device), normal=torch.empty(3, H, W, device=self.device))
-        img = L.qgs_image(out["rgb"].data_ptr(), out["alpha"].data_ptr(), out["depth"].data_ptr(),
-                          out["normal"].data_ptr())
+            if extras:
+                for k in EXTRA_KEYS:
+                    out[k] = torch.empty(H, W, device=self.device)
+        img = L.qgs_image(*[(out[k].data_ptr() if out.get(k) is not None else None) for k in IMAGE_KEYS])
         sc = scene.to_c()
         cc = camera_to_c(cam)
         L.check(self.lib.render_forward(self._ctx, C.byref(sc), C.byref(cc), C.byref(img),
@@ -117,8 +127,8 @@ class Rasterizer:
                                  depth=torch.empty(H, W, device=self.device),
                                  normal=torch.empty(3, H, W, device=self.device)))
         cc = (L.qgs_camera * V)(*[camera_to_c(c) for c in cams])
-        im = (L.qgs_image * V)(*[L.qgs_image(o["rgb"].data_ptr(), o["alpha"].data_ptr(), o["depth"].data_ptr(),
-                                             o["normal"].data_ptr()) for o in outs])
+        im = (L.qgs_image * V)(*[L.qgs_image(*[(o[k].data_ptr() if o.get(k) is not None else None)
+                                               for k in IMAGE_KEYS]) for o in outs])
         sc = scene.to_c()
         L.check(self.lib.render_forward_batch(self._ctx, C.byref(sc), V, cc, im,
                                               C.c_void_p(_stream_ptr(self.device))), self._ctx)
@@ -142,7 +152,7 @@ class Rasterizer:
                 raise ValueError(f"grad_out[{k}] must be contiguous float32")
             return v.data_ptr()
 
-        img = L.qgs_image(p("rgb"), p("alpha"), p("depth"), p("normal"))
+        img = L.qgs_image(*[p(k) for k in IMAGE_KEYS])
         g = L.qgs_scene_grad(grads["mean"].data_ptr(), grads["quat"].data_ptr(), grads["scale"].data_ptr(),
                              grads["curv"].data_ptr(), grads["opacity"].data_ptr(), grads["sh"].data_ptr())
         sc = scene.to_c()
@@ -187,28 +197,35 @@ class QGSRender(torch.autograd.Function):
     Use Rasterizer.backward directly for float32 SH gradients."""
 
     @staticmethod
-    def forward(ctx, rasterizer: Rasterizer, cam, mean, quat, scale, curv, opacity, sh):
+    def forward(ctx, rasterizer: Rasterizer, cam, extras, mean, quat, scale, curv, opacity, sh):
         scene = DeviceScene(mean.detach().contiguous(), quat.detach().contiguous(), scale.detach().contiguous(),
                             curv.detach().contiguous(), opacity.detach().contiguous(),
                             sh.detach().contiguous())
-        out = rasterizer.forward(scene, cam)
+        out = rasterizer.forward(scene, cam, extras=extras)
         ctx.rasterizer = rasterizer
         ctx.cam = cam
         ctx.scene = scene
+        ctx.extras = extras
+        if extras:
+            ctx.mark_non_differentiable(out["median_depth"])
+            return tuple(out[k] for k in IMAGE_KEYS)
         return out["rgb"], out["alpha"], out["depth"], out["normal"]
 
     @staticmethod
-    def backward(ctx, g_rgb, g_alpha, g_depth, g_normal):
-        go = {k: (v.contiguous().float() if v is not None else None)
-              for k, v in zip(("rgb", "alpha", "depth", "normal"), (g_rgb, g_alpha, g_depth, g_normal))}
+    def backward(ctx, *grads):
+        keys = IMAGE_KEYS[:len(grads)]
+        go = {k: (v.contiguous().float() if v is not None else None) for k, v in zip(keys, grads)}
+        go.pop("median_depth", None)          # no gradient flows through the median depth
         r = ctx.rasterizer
         if r._last is None or r._last[0] is not ctx.scene:
             # another forward ran on this rasterizer since: re-render to restore its residue
-            r.forward(ctx.scene, ctx.cam)
+            r.forward(ctx.scene, ctx.cam, extras=ctx.extras)
         g = r.backward(ctx.scene, ctx.cam, go)
-        return None, None, g["mean"], g["quat"], g["scale"], g["curv"], g["opacity"], g["sh"]
+        return None, None, None, g["mean"], g["quat"], g["scale"], g["curv"], g["opacity"], g["sh"]
 
 
-def render(rasterizer: Rasterizer, cam, mean, quat, scale, curv, opacity, sh):
-    """Differentiable render through libqgs; returns (rgb, alpha, depth, normal)."""
-    return QGSRender.apply(rasterizer, cam, mean, quat, scale, curv, opacity, sh)
+def render(rasterizer: Rasterizer, cam, mean, quat, scale, curv, opacity, sh, extras: bool = False):
+    """Differentiable render through libqgs; returns (rgb, alpha, depth, normal) and, with
+    `extras`, also (curvature, distortion, median_depth) (the median depth carries no
+    gradient)."""
+    return QGSRender.apply(rasterizer, cam, extras, mean, quat, scale, curv, opacity, sh)

@@ -3,6 +3,14 @@
 Tolerances (FP32 CUDA path vs the FP64 oracle):
   rgb, alpha, normal   <= 1e-4 absolute
   depth                <= 1e-4 relative (against max(|d*|, 1e-6))
+  median depth         <= 1e-4 relative (one hit depth), pixels whose transmittance is
+                          within MARGIN of 0.5 at a blended pair excluded
+  curvature map        <= 1e-4 relative against max(sum w |K|, 1) (K = 4ab/S^2 reaches
+                          1e6 on strongly curved patches), widened like gradients to
+                          PERTURB_FACTOR x the oracle's own deviation under input noise
+  distortion           <= 1e-4 (D* + depth* sqrt(D*)): the relative depth bar carried
+                          through dD/dt_i = 2 w_i (A0 t_i - A1), whose sum is bounded by
+                          2 A0 t_max sqrt(2 D) (Cauchy-Schwarz)
   gradients            <= 1e-3 relative, per element against
                           max(|g*|, 1e-3 * max|g*| over the parameter group)
 Pixels whose smallest decision margin in the oracle is below MARGIN are ambiguous
@@ -112,12 +120,13 @@ def perturbed(scene, seed, rel=PERTURB):
     return sc
 
 
-def oracle_grads_with_spread(O, scene, cam, grad_images, binning=None, tiles=None):
-    """Oracle gradient and its per-element deviation under FP32-sized input noise."""
-    ref = O.render(scene, cam, binning, tiles=tiles, grad_images=grad_images)
+def oracle_grads_with_spread(O, scene, cam, grad_images, binning=None, tiles=None, samples=PERTURB_SAMPLES, **kw):
+    """Oracle gradient and its per-element deviation under FP32-sized input noise
+    (kw: density, extras of the oracle's render)."""
+    ref = O.render(scene, cam, binning, tiles=tiles, grad_images=grad_images, **kw)
     spread = {k: np.zeros_like(v) for k, v in ref["grads"].items()}
-    for s in range(PERTURB_SAMPLES):
-        r = O.render(perturbed(scene, 1000 + s), cam, ref["binning"], tiles=tiles, grad_images=grad_images)
+    for s in range(samples):
+        r = O.render(perturbed(scene, 1000 + s), cam, ref["binning"], tiles=tiles, grad_images=grad_images, **kw)
         for k in spread:
             spread[k] = np.maximum(spread[k], np.abs(r["grads"][k] - ref["grads"][k]))
     return ref, spread
@@ -133,3 +142,61 @@ def grad_mask(ref, extra=None):
     else:
         frac = 1.0 - ok.mean()
     return ok.astype(np.float64), float(frac)
+
+
+TOL_CURV_REL = 1e-4
+TOL_DIST = 1e-4
+
+
+def oracle_spread(O, scene, cam, ref, keys, tiles=None, **kw):
+    """Per-pixel deviation of oracle output planes under FP32-sized input noise (the same
+    perturbation as for gradients)."""
+    spread = {k: np.zeros_like(ref[k]) for k in keys}
+    for s in range(PERTURB_SAMPLES):
+        r = O.render(perturbed(scene, 1000 + s), cam, ref["binning"], tiles=tiles, **kw)
+        for k in keys:
+            spread[k] = np.maximum(spread[k], np.abs(r[k] - ref[k]))
+    return spread
+
+
+def extra_errors(gpu: dict, ref: dict, mask=None, spread=None):
+    """Errors of the extra channels over unambiguous pixels, each in units of its
+    tolerance (<= 1 passes), plus plain relative errors for the record. With `spread`
+    (oracle_spread of "curvature"), the curvature tolerance is widened to PERTURB_FACTOR
+    times the oracle's own deviation, as for gradients: K = 4ab/S^2 with
+    S = 1 + 4a^2x^2 + 4b^2y^2 moves by about 4 dx/x, and on strongly curved patches the
+    hit point x itself is ill-conditioned."""
+    ok = ref["margin"] > MARGIN
+    if mask is not None:
+        ok = ok & mask
+    okm = ok & (ref["margin_median"] > MARGIN)
+    cs = np.maximum(ref["curvature_scale"], 1.0)
+    tolK = TOL_CURV_REL * cs
+    widened = 0.0
+    if spread is not None:
+        allow = PERTURB_FACTOR * spread["curvature"]
+        widened = float((allow > tolK)[ok].mean()) if ok.any() else 0.0
+        tolK = np.maximum(tolK, allow)
+    ek = np.abs(np.asarray(gpu["curvature"], np.float64) - ref["curvature"]) / cs
+    rk = np.abs(np.asarray(gpu["curvature"], np.float64) - ref["curvature"]) / tolK
+    D = ref["distortion"]
+    dD = np.abs(np.asarray(gpu["distortion"], np.float64) - D)
+    tolD = TOL_DIST * (D + np.abs(ref["depth"]) * np.sqrt(np.maximum(D, 0.0))) + 1e-9
+    m = ref["median_depth"]
+    em = np.abs(np.asarray(gpu["median_depth"], np.float64) - m) / np.maximum(np.abs(m), 1e-6)
+    return dict(curvature=float(rk[ok].max(initial=0.0)), curvature_widened=widened,
+                distortion=float((dD[ok] / tolD[ok]).max(initial=0.0)),
+                median_depth=float((em[okm] / TOL_DEPTH_REL).max(initial=0.0)),
+                curvature_rel=float(ek[ok].max(initial=0.0)),
+                distortion_rel=float((dD / np.maximum(D, 1e-12))[ok].max(initial=0.0)),
+                median_excluded=float(1.0 - okm.sum() / max(1, ok.sum())))
+
+
+def assert_extras_close(gpu, ref, mask=None, label="", spread=None):
+    e = extra_errors(gpu, ref, mask, spread)
+    print(f"[{label}] extra-channel errors {e}")
+    assert e["curvature"] <= 1.0, (label, e)
+    assert e["distortion"] <= 1.0, (label, e)
+    assert e["median_depth"] <= 1.0, (label, e)
+    assert e["median_excluded"] <= 0.01, (label, e)
+    return e

@@ -44,7 +44,7 @@ def test_struct_layouts_match_header():
     from paper_2411_16392_gb300 import _lib as L
     assert ctypes.sizeof(L.qgs_camera) == 4 * (2 + 4 + 9 + 3 + 1)
     assert ctypes.sizeof(L.qgs_scene) == 8 * 7
-    assert ctypes.sizeof(L.qgs_image) == 8 * 4
+    assert ctypes.sizeof(L.qgs_image) == 8 * 7
     assert ctypes.sizeof(L.qgs_scene_grad) == 8 * 6
     assert ctypes.sizeof(L.qgs_config) == 4 * 6
     assert ctypes.sizeof(L.qgs_frame_stats) == 8 * 13 + 4 * 7 + 4
