@@ -356,7 +356,7 @@ __device__ __forceinline__ void raster_fwd_tile(PrimState* sm, uint8_t* used, in
 }
 
 template <bool EUCLID, bool EXTRA>
-__global__ void __launch_bounds__(BLOCK, 3)
+__global__ void __launch_bounds__(BLOCK, 4)
     k_raster_fwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids, int id_stride,
                  const PrimState* __restrict__ state, RasterParams rp, float* __restrict__ out_rgb,
                  float* __restrict__ out_alpha, float* __restrict__ out_depth, float* __restrict__ out_normal,
@@ -419,7 +419,7 @@ __device__ __forceinline__ float warp_transpose_sum(float v[32]) {
 // g_D A2 joins the alpha gradient, and tau = t - c and tau^2 act as two more blended
 // channels with upstream gradients -2 g_D A1 and g_D A0.
 template <bool EUCLID, bool EXTRA>
-__global__ void __launch_bounds__(BLOCK, 2)
+__global__ void __launch_bounds__(BLOCK, 3)
     k_raster_bwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids, int id_stride,
                  const PrimState* __restrict__ state, RasterParams rp, const float* __restrict__ g_rgb,
                  const float* __restrict__ g_alpha, const float* __restrict__ g_depth,
@@ -486,9 +486,11 @@ __global__ void __launch_bounds__(BLOCK, 2)
     __syncthreads();
     for (int j = cnt - 1; j >= 0; --j) {
       if (!suse[j]) continue;  // no pixel of this tile blended the instance in the forward
+      // gradient record of this pixel's pair (entries 0..NGRAD-1, all written by a
+      // contributing lane; zeroed for the others only when the warp reduces)
       float v[32];
 #pragma unroll
-      for (int k = 0; k < 32; ++k) v[k] = 0.f;
+      for (int k = NGRAD; k < 32; ++k) v[k] = 0.f;
       bool contrib = false;
       if ((uint32_t)(b0 + j) < last) {
         Hit h;
@@ -534,6 +536,7 @@ __global__ void __launch_bounds__(BLOCK, 2)
             v[19] = w * gB;
             // alpha = min(alpha_max, o G)
             float dG = 0.f;
+            v[16] = 0.f;
             if (oG < rp.alpha_max) {
               v[16] = dal * h.G;
               dG = dal * o;
@@ -598,6 +601,10 @@ __global__ void __launch_bounds__(BLOCK, 2)
         }
       }
       if (__any_sync(FULL, contrib)) {
+        if (!contrib) {
+#pragma unroll
+          for (int k = 0; k < NGRAD; ++k) v[k] = 0.f;
+        }
         const float r = warp_transpose_sum(v);
         const int lane = threadIdx.x & 31;
         if (lane < NGRAD && r != 0.f) atomicAdd(&sg[j][lane], r);
