@@ -136,6 +136,88 @@ __global__ void k_emit_views(int64_t n, const uint32_t* __restrict__ sidx, const
   }
 }
 
+// Visible primitives in index order: position vpos[i] (exclusive scan of the visibility
+// flags) receives the depth key and the index.
+__global__ void k_compact(int64_t n, const uint32_t* __restrict__ count, const uint32_t* __restrict__ zkey,
+                          const uint32_t* __restrict__ vpos, uint32_t* __restrict__ ckey, uint32_t* __restrict__ cidx) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || count[i] == 0) return;
+  const uint32_t p = vpos[i];
+  ckey[p] = zkey[i];
+  cidx[p] = (uint32_t)i;
+}
+
+// Depth order r = 0..V-1 (sidx[r] = primitive): the projected state and the tile count
+// gathered into that order (8 threads per 128-byte record).
+__global__ void k_gather_state(int64_t V, const uint32_t* __restrict__ sidx, const PrimState* __restrict__ state,
+                               const uint32_t* __restrict__ count, PrimState* __restrict__ dstate,
+                               uint32_t* __restrict__ cnt_sorted) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= V * 8) return;
+  const int64_t r = e >> 3;
+  const int c = (int)(e & 7);
+  const uint32_t pid = sidx[r];
+  reinterpret_cast<float4*>(dstate + r)[c] = __ldg(reinterpret_cast<const float4*>(state + pid) + c);
+  if (c == 0) cnt_sorted[r] = count[pid];
+}
+
+// Tile instances of the depth-ordered visible primitives, packed as (tile << rb) | r with
+// r the depth rank (rb bits); K = uint32_t when tile and rank bits fit in 32, else
+// uint64_t with rb = 32. One warp writes 32 consecutive primitives' tiles (coalesced).
+template <typename K>
+__global__ void k_emit_packed(int64_t V, const uint32_t* __restrict__ sidx, const uint32_t* __restrict__ cnt_sorted,
+                              const short4* __restrict__ rect, const uint32_t* __restrict__ offs, int tiles_x, int rb,
+                              K* __restrict__ keys) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t c = 0, off = 0;
+  short4 rc = make_short4(0, 0, 0, 0);
+  if (r < V) {
+    c = cnt_sorted[r];
+    off = offs[r];
+    rc = rect[sidx[r]];
+  }
+  for (int k = 0; k < 32; ++k) {
+    const uint32_t cc = __shfl_sync(0xffffffffu, c, k);
+    if (!cc) continue;
+    const uint32_t rr = (uint32_t)(r - lane + k);
+    const uint32_t oo = __shfl_sync(0xffffffffu, off, k);
+    const int rx0 = __shfl_sync(0xffffffffu, (int)rc.x, k);
+    const int rx1 = __shfl_sync(0xffffffffu, (int)rc.y, k);
+    const int ry0 = __shfl_sync(0xffffffffu, (int)rc.z, k);
+    const uint32_t w = (uint32_t)(rx1 - rx0 + 1);
+    for (uint32_t e = lane; e < cc; e += 32) {
+      const uint32_t dy = e / w, dx = e - dy * w;
+      const uint32_t tile = (uint32_t)(ry0 + (int)dy) * (uint32_t)tiles_x + (uint32_t)(rx0 + (int)dx);
+      keys[(size_t)oo + e] = ((K)tile << rb) | (K)rr;
+    }
+  }
+}
+
+// [start, end) of every tile's run in keys sorted by tile = key >> shift.
+template <typename K>
+__global__ void k_tile_ranges_t(int64_t n, const K* __restrict__ keys, int shift, uint2* __restrict__ ranges) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t t = (uint32_t)(keys[i] >> shift);
+  if (i == 0 || (uint32_t)(keys[i - 1] >> shift) != t) ranges[t].x = (uint32_t)i;
+  if (i == n - 1 || (uint32_t)(keys[i + 1] >> shift) != t) ranges[t].y = (uint32_t)(i + 1);
+}
+
+// Host copy of packed-key binning: keys (tile << 32 | depth bits), values = primitive.
+template <typename K>
+__global__ void k_debug_packed(int64_t n, const K* __restrict__ inst, int rb, const uint32_t* __restrict__ sidx,
+                               const PrimState* __restrict__ dstate, uint64_t* __restrict__ keys,
+                               uint32_t* __restrict__ vals) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const K v = inst[i];
+  const uint32_t tile = (uint32_t)(v >> rb);
+  const uint32_t r = (uint32_t)(v & (((K)1 << rb) - 1));
+  keys[i] = ((uint64_t)tile << 32) | __float_as_uint(dstate[r].f[2].w);  // z_mu: the depth key's float
+  vals[i] = sidx[r];
+}
+
 __global__ void k_tile_ranges(int64_t n, const uint64_t* __restrict__ keys, uint2* __restrict__ ranges) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -155,15 +237,6 @@ __global__ void k_tile_sched_keys(int64_t ntiles, const uint2* __restrict__ rang
   val[t] = (uint32_t)t;
 }
 
-__global__ void k_debug_keys(int64_t n, const uint64_t* __restrict__ inst, const PrimState* __restrict__ state,
-                             uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint64_t v = inst[i];
-  const uint32_t pid = (uint32_t)v;
-  keys[i] = (v & 0xFFFFFFFF00000000ull) | __float_as_uint(state[pid].f[2].w);
-  vals[i] = pid;
-}
 
 inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b); }
 
@@ -203,8 +276,14 @@ struct qgs_ctx {
   const float* scene_mean = nullptr;
   const uint32_t* ids = nullptr;  // sorted primitive ids of the last frame
   int id_stride = 1;
-  const uint64_t* sorted_keys = nullptr;
+  const void* sorted_keys = nullptr;
   cudaStream_t last_stream = nullptr;
+  DevBuf<uint32_t> vpos;          // visibility flags, then their exclusive scan
+  DevBuf<PrimState> dstate;       // projected state of the visible primitives in depth order
+  const PrimState* raster_state = nullptr;  // state the sorted ids index (dstate or state)
+  bool pgrad_by_pos = false;      // gradient records indexed like raster_state's depth order
+  bool packed32 = false;          // instances are u32 (tile << rank_bits | depth rank)
+  int rank_bits = 32;
   DevBuf<float> resid;            // extra-channel residue (c, A1, A2) [3P] of the last forward
   bool have_resid = false;        // the last forward rendered the extra channels
   // profiling: events at stage boundaries (forward 0..6, backward 7..9)
@@ -279,6 +358,7 @@ void make_params(const qgs_ctx* ctx, const qgs_camera* cam, CamParams& cp, Raste
   rp.near_plane = cam->near_plane;
   rp.alpha_max = ctx->cfg.alpha_max; rp.alpha_min = ctx->cfg.alpha_min;
   rp.T_min = ctx->cfg.T_min; rp.grazing_eps = ctx->cfg.grazing_eps;
+  rp.id_mask = 0xFFFFFFFFu;
 }
 
 inline void mark(qgs_ctx* c, int i, cudaStream_t st) {
@@ -354,6 +434,8 @@ void qgs_destroy(qgs_ctx* c) {
   c->inst_used.release();
   c->vdesc.release();
   c->resid.release();
+  c->vpos.release();
+  c->dstate.release();
   if (c->h_vdesc) cudaFreeHost(c->h_vdesc);
   if (c->vdesc_done) cudaEventDestroy(c->vdesc_done);
   if (c->h_total) cudaFreeHost(c->h_total);
@@ -396,6 +478,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   QGS_CU(ctx->cnt_sorted.reserve(n1), "alloc cnt");
   QGS_CU(ctx->offs.reserve(n1 + 1), "alloc offs");
   QGS_CU(ctx->rect.reserve(n1), "alloc rect");
+  if (sm == 0) QGS_CU(ctx->vpos.reserve(n1 + 1), "alloc visibility scan");
   QGS_CU(ctx->ranges.reserve((size_t)ntiles), "alloc ranges");
   QGS_CU(ctx->tkey.reserve((size_t)ntiles), "alloc tile keys");
   QGS_CU(ctx->tkey2.reserve((size_t)ntiles), "alloc tile keys");
@@ -420,34 +503,21 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   mark(ctx, 0, st);
   SceneView sv{scene->mean, scene->quat, scene->scale, scene->curv, scene->opacity, scene->sh};
   if (N > 0) {
-    k_preprocess<<<nblk(N), 256, 0, st>>>(N, sv, cp, ctx->state.p, ctx->count.p, ctx->zkey.p, ctx->idx.p,
-                                          ctx->rect.p, ctx->dcount.p);
+    k_preprocess<<<nblk(N), 256, 0, st>>>(N, sv, cp, ctx->state.p, ctx->count.p, ctx->zkey.p,
+                                          sm == 0 ? nullptr : ctx->idx.p, ctx->rect.p, ctx->dcount.p,
+                                          sm == 0 ? ctx->vpos.p : nullptr);
     ++launch_counter();
     QGS_CU(cudaGetLastError(), "k_preprocess");
   }
   mark(ctx, 1, st);
-  const uint32_t* sidx = nullptr;
-  cudaError_t e = cudaSuccess;
-  if (sm == 0) {
-    const bool fl = radix_sort_u32_pairs(ctx->zkey.p, ctx->idx.p, ctx->zkey2.p, ctx->idx2.p, N, 0, 32, tmp, st, &e);
-    QGS_CU(e, "depth sort");
-    sidx = fl ? ctx->idx2.p : ctx->idx.p;
-    if (N > 0) {
-      k_gather_u32<<<nblk(N), 256, 0, st>>>(N, sidx, ctx->count.p, ctx->cnt_sorted.p);
-      ++launch_counter();
-      QGS_CU(cudaGetLastError(), "gather");
-    }
-    QGS_CU(scan_exclusive_u32(ctx->cnt_sorted.p, ctx->offs.p, N, ctx->scan_tmp.p, ctx->scan_tmp.cap, st), "scan");
-  } else {
-    QGS_CU(scan_exclusive_u32(ctx->count.p, ctx->offs.p, N, ctx->scan_tmp.p, ctx->scan_tmp.cap, st), "scan");
-  }
-  mark(ctx, 2, st);
-  QGS_CU(cudaMemcpyAsync(ctx->h_total, ctx->offs.p + N, sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "total");
-  QGS_CU(cudaMemcpyAsync(ctx->h_total + 1, ctx->dcount.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "visible");
+  // positions of the visible primitives (index order)
+  if (sm == 0) QGS_CU(scan_exclusive_u32(ctx->vpos.p, ctx->vpos.p, N, ctx->scan_tmp.p, ctx->scan_tmp.cap, st), "scan");
+  // the frame's one synchronisation: visible and instance totals size what follows
+  QGS_CU(cudaMemcpyAsync(ctx->h_total, ctx->dcount.p, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "totals");
   QGS_CU(cudaStreamSynchronize(st), "sync");
-  const int64_t I = (int64_t)ctx->h_total[0];
-  ctx->n_visible = (int64_t)ctx->h_total[1];
-  ctx->vis_list = sm == 0 ? sidx : nullptr;  // depth order puts the visible primitives first
+  const int64_t V = (int64_t)ctx->h_total[0];
+  const int64_t I = (int64_t)ctx->h_total[1];
+  ctx->n_visible = V;
 
   const size_t i1 = (size_t)(I > 0 ? I : 1);
   QGS_CU(ctx->inst_used.reserve(i1), "alloc inst flags");
@@ -457,6 +527,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
     QGS_CU(ctx->vals.reserve(i1), "alloc vals");
     QGS_CU(ctx->vals2.reserve(i1), "alloc vals2");
   }
+  if (sm == 0) QGS_CU(ctx->dstate.reserve((size_t)(V > 0 ? V : 1)), "alloc ordered state");
   QGS_CU(ctx->hist.reserve(radix_hist_elems((int64_t)i1)), "alloc hist");
   QGS_CU(ctx->scan_tmp.reserve(scan_tmp_elems((int64_t)radix_hist_elems((int64_t)i1))), "alloc scan");
   tmp.hist = ctx->hist.p;
@@ -465,21 +536,72 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   tmp.scan_cap = ctx->scan_tmp.cap;
 
   const int tb = bits_for(ntiles);
-  const uint64_t* sorted = nullptr;
-  mark(ctx, 3, st);
-  if (N > 0 && I > 0) {
-    if (sm == 0) {
-      k_emit<<<nblk(N), 256, 0, st>>>(N, sidx, ctx->count.p, ctx->rect.p, ctx->offs.p, nullptr, cp.tiles_x,
-                                      ctx->inst.p, nullptr);
+  cudaError_t e = cudaSuccess;
+  const void* sorted = ctx->inst.p;
+  int shift = 32;
+  if (sm == 0) {
+    // visible primitives (index order) -> depth sort -> state, counts and offsets in
+    // depth order -> instances (tile << rb | depth rank) -> stable sort on the tile bits
+    if (N > 0 && V > 0) {
+      k_compact<<<nblk(N), 256, 0, st>>>(N, ctx->count.p, ctx->zkey.p, ctx->vpos.p, ctx->zkey2.p, ctx->idx2.p);
       ++launch_counter();
-      QGS_CU(cudaGetLastError(), "emit");
-      mark(ctx, 4, st);
-      const bool fl = radix_sort_u64_keys(ctx->inst.p, ctx->inst2.p, I, 32, 32 + tb, tmp, st, &e);
-      QGS_CU(e, "tile sort");
-      sorted = fl ? ctx->inst2.p : ctx->inst.p;
-      ctx->ids = reinterpret_cast<const uint32_t*>(sorted);
-      ctx->id_stride = 2;
+      QGS_CU(cudaGetLastError(), "compact");
+    }
+    const bool fl = radix_sort_u32_pairs(ctx->zkey2.p, ctx->idx2.p, ctx->zkey.p, ctx->idx.p, V, 0, 32, tmp, st, &e);
+    QGS_CU(e, "depth sort");
+    const uint32_t* sidx = fl ? ctx->idx.p : ctx->idx2.p;
+    ctx->vis_list = sidx;
+    if (V > 0) {
+      k_gather_state<<<nblk(V * 8), 256, 0, st>>>(V, sidx, ctx->state.p, ctx->count.p, ctx->dstate.p,
+                                                  ctx->cnt_sorted.p);
+      ++launch_counter();
+      QGS_CU(cudaGetLastError(), "gather state");
+    }
+    QGS_CU(scan_exclusive_u32(ctx->cnt_sorted.p, ctx->offs.p, V, ctx->scan_tmp.p, ctx->scan_tmp.cap, st), "scan");
+    mark(ctx, 2, st);
+    const int rb = bits_for(V > 1 ? V : 2);
+    ctx->packed32 = rb + tb <= 32;
+    ctx->rank_bits = ctx->packed32 ? rb : 32;
+    mark(ctx, 3, st);
+    if (V > 0 && I > 0) {
+      if (ctx->packed32) {
+        uint32_t* k0 = reinterpret_cast<uint32_t*>(ctx->inst.p);
+        uint32_t* k1 = reinterpret_cast<uint32_t*>(ctx->inst2.p);
+        k_emit_packed<uint32_t><<<nblk(V), 256, 0, st>>>(V, sidx, ctx->cnt_sorted.p, ctx->rect.p, ctx->offs.p,
+                                                         cp.tiles_x, rb, k0);
+        ++launch_counter();
+        QGS_CU(cudaGetLastError(), "emit");
+        mark(ctx, 4, st);
+        const bool f2 = radix_sort_u32_keys(k0, k1, I, rb, rb + tb, tmp, st, &e);
+        QGS_CU(e, "tile sort");
+        sorted = f2 ? (const void*)k1 : (const void*)k0;
+      } else {
+        k_emit_packed<uint64_t><<<nblk(V), 256, 0, st>>>(V, sidx, ctx->cnt_sorted.p, ctx->rect.p, ctx->offs.p,
+                                                         cp.tiles_x, 32, ctx->inst.p);
+        ++launch_counter();
+        QGS_CU(cudaGetLastError(), "emit");
+        mark(ctx, 4, st);
+        const bool f2 = radix_sort_u64_keys(ctx->inst.p, ctx->inst2.p, I, 32, 32 + tb, tmp, st, &e);
+        QGS_CU(e, "tile sort");
+        sorted = f2 ? (const void*)ctx->inst2.p : (const void*)ctx->inst.p;
+      }
     } else {
+      mark(ctx, 4, st);
+    }
+    shift = ctx->rank_bits;
+    ctx->ids = reinterpret_cast<const uint32_t*>(sorted);
+    ctx->id_stride = ctx->packed32 ? 1 : 2;
+    rp.id_mask = ctx->packed32 ? (uint32_t)((1ull << rb) - 1ull) : 0xFFFFFFFFu;
+    ctx->raster_state = ctx->dstate.p;
+    ctx->pgrad_by_pos = true;
+  } else {
+    // sort_mode 1: 64-bit (tile << 32 | depth bits) keys in primitive order, one sort
+    QGS_CU(scan_exclusive_u32(ctx->count.p, ctx->offs.p, N, ctx->scan_tmp.p, ctx->scan_tmp.cap, st), "scan");
+    mark(ctx, 2, st);
+    mark(ctx, 3, st);
+    ctx->packed32 = false;
+    ctx->rank_bits = 32;
+    if (N > 0 && I > 0) {
       k_emit<<<nblk(N), 256, 0, st>>>(N, nullptr, ctx->count.p, ctx->rect.p, ctx->offs.p, ctx->zkey.p, cp.tiles_x,
                                       ctx->inst.p, ctx->vals.p);
       ++launch_counter();
@@ -490,18 +612,25 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
       QGS_CU(e, "key sort");
       sorted = fl ? ctx->inst2.p : ctx->inst.p;
       ctx->ids = fl ? ctx->vals2.p : ctx->vals.p;
-      ctx->id_stride = 1;
+    } else {
+      ctx->ids = ctx->vals.p;
+      mark(ctx, 4, st);
     }
-  } else {
-    ctx->ids = reinterpret_cast<const uint32_t*>(ctx->inst.p);
-    ctx->id_stride = sm == 0 ? 2 : 1;
-    if (sm == 1) ctx->ids = ctx->vals.p;
-    mark(ctx, 4, st);
+    ctx->id_stride = 1;
+    rp.id_mask = 0xFFFFFFFFu;
+    ctx->raster_state = ctx->state.p;
+    ctx->pgrad_by_pos = false;
+    ctx->vis_list = nullptr;
   }
   ctx->sorted_keys = sorted;
   QGS_CU(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(uint2) * (size_t)ntiles, st), "memset ranges");
   if (I > 0) {
-    k_tile_ranges<<<nblk(I), 256, 0, st>>>(I, sorted, ctx->ranges.p);
+    if (ctx->packed32)
+      k_tile_ranges_t<uint32_t><<<nblk(I), 256, 0, st>>>(I, reinterpret_cast<const uint32_t*>(sorted), shift,
+                                                         ctx->ranges.p);
+    else
+      k_tile_ranges_t<uint64_t><<<nblk(I), 256, 0, st>>>(I, reinterpret_cast<const uint64_t*>(sorted), shift,
+                                                         ctx->ranges.p);
     ++launch_counter();
     QGS_CU(cudaGetLastError(), "ranges");
   }
@@ -519,7 +648,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   mark(ctx, 5, st);
   const ExtraPlanes ex{out->curvature, out->distortion, out->median_depth, extra ? ctx->resid.p : nullptr};
   QGS_CU(launch_raster_fwd(ctx->cfg.density == 1, extra, (unsigned)ntiles, st, ctx->ranges.p, ctx->ids,
-                           ctx->id_stride, ctx->state.p, rp, out->rgb, out->alpha, out->depth, out->normal,
+                           ctx->id_stride, ctx->raster_state, rp, out->rgb, out->alpha, out->depth, out->normal,
                            ctx->T_final.p, ctx->n_contrib.p, ex, ctx->stats.p, ctx->tile_order, ctx->inst_used.p),
          "k_raster_fwd");
   ++launch_counter();
@@ -752,8 +881,11 @@ qgs_status render_backward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camer
   CamParams cp;
   RasterParams rp;
   make_params(ctx, cam, cp, rp);
-  QGS_CU(ctx->pgrad.reserve((size_t)N * NGRAD_PAD), "alloc pgrad");
-  QGS_CU(cudaMemsetAsync(ctx->pgrad.p, 0, sizeof(float) * (size_t)N * NGRAD_PAD, st), "memset pgrad");
+  rp.id_mask = ctx->rp.id_mask;
+  const int64_t NG = ctx->pgrad_by_pos ? ctx->n_visible : N;  // gradient records
+  QGS_CU(ctx->pgrad.reserve((size_t)(NG > 0 ? NG : 1) * NGRAD_PAD), "alloc pgrad");
+  if (NG > 0)
+    QGS_CU(cudaMemsetAsync(ctx->pgrad.p, 0, sizeof(float) * (size_t)NG * NGRAD_PAD, st), "memset pgrad");
   const int64_t ntiles = (int64_t)cp.tiles_x * cp.tiles_y;
   const int64_t launches0 = launch_counter();
   const bool euclid = ctx->cfg.density == 1;
@@ -761,7 +893,7 @@ qgs_status render_backward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camer
   const ExtraGrads eg{grad_out->curvature, grad_out->distortion, ctx->have_resid ? ctx->resid.p : nullptr};
   mark(ctx, 7, st);
   QGS_CU(launch_raster_bwd(euclid, extra, (unsigned)ntiles, st, ctx->ranges.p, ctx->ids, ctx->id_stride,
-                           ctx->state.p, rp, grad_out->rgb, grad_out->alpha, grad_out->depth, grad_out->normal,
+                           ctx->raster_state, rp, grad_out->rgb, grad_out->alpha, grad_out->depth, grad_out->normal,
                            ctx->T_final.p, ctx->n_contrib.p, eg, ctx->pgrad.p, ctx->stats.p, ctx->tile_order,
                            ctx->inst_used.p),
          "k_raster_bwd");
@@ -770,7 +902,9 @@ qgs_status render_backward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camer
   SceneView sv{scene->mean, scene->quat, scene->scale, scene->curv, scene->opacity, scene->sh};
   GradView gv{grad->mean, grad->quat, grad->scale, grad->curv, grad->opacity, grad->sh};
   const int64_t nb = ctx->vis_list ? ctx->n_visible : N;
-  if (nb > 0) k_preprocess_bwd<<<nblk(nb), 256, 0, st>>>(nb, ctx->vis_list, sv, cp, ctx->count.p, ctx->pgrad.p, gv);
+  if (nb > 0)
+    k_preprocess_bwd<<<nblk(nb), 256, 0, st>>>(nb, ctx->vis_list, sv, cp, ctx->count.p, ctx->pgrad.p,
+                                               ctx->pgrad_by_pos, gv);
   ++launch_counter();
   QGS_CU(cudaGetLastError(), "k_preprocess_bwd");
   mark(ctx, 9, st);
@@ -843,7 +977,12 @@ qgs_status qgs_copy_binning(qgs_ctx* ctx, uint64_t* keys, uint32_t* vals, int64_
       return fail(ctx, QGS_ENOMEM, "alloc");
     }
     if (ctx->cfg.sort_mode == 0) {
-      k_debug_keys<<<nblk(I), 256>>>(I, ctx->sorted_keys, ctx->state.p, dk.p, dv.p);
+      if (ctx->packed32)
+        k_debug_packed<uint32_t><<<nblk(I), 256>>>(I, reinterpret_cast<const uint32_t*>(ctx->sorted_keys),
+                                                   ctx->rank_bits, ctx->vis_list, ctx->dstate.p, dk.p, dv.p);
+      else
+        k_debug_packed<uint64_t><<<nblk(I), 256>>>(I, reinterpret_cast<const uint64_t*>(ctx->sorted_keys),
+                                                   ctx->rank_bits, ctx->vis_list, ctx->dstate.p, dk.p, dv.p);
     } else {
       cudaMemcpy(dk.p, ctx->sorted_keys, sizeof(uint64_t) * (size_t)I, cudaMemcpyDeviceToDevice);
       cudaMemcpy(dv.p, ctx->ids, sizeof(uint32_t) * (size_t)I, cudaMemcpyDeviceToDevice);
@@ -1001,7 +1140,7 @@ extern "C" qgs_status render_forward_noalloc(const qgs_scene* scene, const qgs_c
   QGS_CU(cudaMemsetAsync(stats, 0, sizeof(RasterStats), st), "memset");
   SceneView sv{scene->mean, scene->quat, scene->scale, scene->curv, scene->opacity, scene->sh};
   if (N > 0) {
-    k_preprocess<<<nblk(N), 256, 0, st>>>(N, sv, cp, state, count, zkey, idx, rect, visible);
+    k_preprocess<<<nblk(N), 256, 0, st>>>(N, sv, cp, state, count, zkey, idx, rect, visible, nullptr);
     QGS_CU(cudaGetLastError(), "k_preprocess");
   }
   cudaError_t e = cudaSuccess;

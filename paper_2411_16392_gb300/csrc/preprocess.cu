@@ -152,23 +152,27 @@ __device__ __forceinline__ float3 slab_of(float nx, float ny, float smin, float 
 
 }  // namespace
 
-__device__ __forceinline__ bool preprocess_one(int64_t i, const SceneView& sc, const CamParams& cp,
-                                               PrimState* __restrict__ state, uint32_t* __restrict__ count,
-                                               uint32_t* __restrict__ zkey, uint32_t* __restrict__ idx,
-                                               short4* __restrict__ rect, uint32_t idx_base = 0);
+// Returns the primitive's tile count (0: culled).
+__device__ __forceinline__ uint32_t preprocess_one(int64_t i, const SceneView& sc, const CamParams& cp,
+                                                   PrimState* __restrict__ state, uint32_t* __restrict__ count,
+                                                   uint32_t* __restrict__ zkey, uint32_t* __restrict__ idx,
+                                                   short4* __restrict__ rect, uint32_t idx_base = 0);
 
 __global__ void __launch_bounds__(256) k_preprocess(int64_t n, SceneView sc, CamParams cp, PrimState* __restrict__ state,
                                                     uint32_t* __restrict__ count, uint32_t* __restrict__ zkey,
                                                     uint32_t* __restrict__ idx, short4* __restrict__ rect,
-                                                    uint32_t* __restrict__ n_visible) {
+                                                    uint32_t* __restrict__ counters, uint32_t* __restrict__ vflag) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  {
-    // visible-primitive count: one atomic per warp
-    const bool active = i < n;
-    uint32_t vis = 0;
-    if (active) vis = preprocess_one(i, sc, cp, state, count, zkey, idx, rect) ? 1u : 0u;
-    vis = __reduce_add_sync(0xffffffffu, vis);
-    if ((threadIdx.x & 31) == 0 && vis) atomicAdd(n_visible, vis);
+  // visible primitives and tile instances: one atomic per warp and counter
+  const bool active = i < n;
+  uint32_t cnt = 0;
+  if (active) cnt = preprocess_one(i, sc, cp, state, count, zkey, idx, rect);
+  if (active && vflag) vflag[i] = cnt ? 1u : 0u;
+  const uint32_t vis = __reduce_add_sync(0xffffffffu, cnt ? 1u : 0u);
+  const uint32_t tot = __reduce_add_sync(0xffffffffu, cnt);
+  if ((threadIdx.x & 31) == 0) {
+    if (vis) atomicAdd(&counters[0], vis);
+    if (tot) atomicAdd(&counters[1], tot);
   }
 }
 
@@ -188,11 +192,11 @@ __global__ void __launch_bounds__(256) k_preprocess_views(int64_t n, SceneView s
   if ((threadIdx.x & 31) == 0 && vis) atomicAdd(n_visible, vis);
 }
 
-__device__ __forceinline__ bool preprocess_one(int64_t i, const SceneView& sc, const CamParams& cp,
-                                               PrimState* __restrict__ state, uint32_t* __restrict__ count,
-                                               uint32_t* __restrict__ zkey, uint32_t* __restrict__ idx,
-                                               short4* __restrict__ rect, uint32_t idx_base) {
-  idx[i] = idx_base + (uint32_t)i;
+__device__ __forceinline__ uint32_t preprocess_one(int64_t i, const SceneView& sc, const CamParams& cp,
+                                                   PrimState* __restrict__ state, uint32_t* __restrict__ count,
+                                                   uint32_t* __restrict__ zkey, uint32_t* __restrict__ idx,
+                                                   short4* __restrict__ rect, uint32_t idx_base) {
+  if (idx) idx[i] = idx_base + (uint32_t)i;
   const float mx = sc.mean[3 * i], my = sc.mean[3 * i + 1], mz = sc.mean[3 * i + 2];
   const float4 q = reinterpret_cast<const float4*>(sc.quat)[i];
   const float2 s = reinterpret_cast<const float2*>(sc.scale)[i];
@@ -290,7 +294,7 @@ __device__ __forceinline__ bool preprocess_one(int64_t i, const SceneView& sc, c
   count[i] = cnt;
   zkey[i] = key;
   rect[i] = rc;
-  if (!cnt) return false;
+  if (!cnt) return 0u;
 
   // --- projected state (ordinary FP32/FP64 arithmetic) ---------------------------
   const float zmu = muc[2];
@@ -335,17 +339,18 @@ __device__ __forceinline__ bool preprocess_one(int64_t i, const SceneView& sc, c
   ps.f[6] = make_float4(1.f / (s.x * s.x), 1.f / (s.y * s.y), W[6], W[7]);
   ps.f[7] = make_float4(W[8], fmaxf(col[0], 0.f), fmaxf(col[1], 0.f), fmaxf(col[2], 0.f));
   state[i] = ps;
-  return true;
+  return cnt;
 }
 
 __global__ void __launch_bounds__(256) k_preprocess_bwd(int64_t n, const uint32_t* __restrict__ list, SceneView sc,
                                                         CamParams cp, const uint32_t* __restrict__ count,
-                                                        const float* __restrict__ pgrad, GradView gd) {
+                                                        const float* __restrict__ pgrad, bool pgrad_by_pos,
+                                                        GradView gd) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const int64_t i = list ? (int64_t)list[j] : j;
   if (count[i] == 0) return;
-  const float* pg = pgrad + (size_t)NGRAD_PAD * i;
+  const float* pg = pgrad + (size_t)NGRAD_PAD * (pgrad_by_pos ? j : i);
   float P[9], Hh[3];
 #pragma unroll
   for (int k = 0; k < 9; ++k) P[k] = pg[k];

@@ -36,6 +36,7 @@ struct RasterParams {
   float cx, cy, inv_fx, inv_fy;
   float near_plane;
   float alpha_max, alpha_min, T_min, grazing_eps;
+  uint32_t id_mask;  // projected-state index = sorted id & id_mask (low bits of a packed key)
 };
 
 }  // namespace qgs

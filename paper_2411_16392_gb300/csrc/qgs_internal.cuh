@@ -32,13 +32,18 @@ struct CamParams {
 };
 
 // ---------------------------------------------------------------- preprocessing
+// Per primitive i: projected state (visible ones only), tile count, depth key, tile
+// rectangle; idx[i] = i and vflag[i] = (count > 0) when given. counters[0] += visible,
+// counters[1] += tile instances.
 __global__ void k_preprocess(int64_t n, SceneView sc, CamParams cp, PrimState* state, uint32_t* count,
-                             uint32_t* zkey, uint32_t* idx, short4* rect, uint32_t* n_visible);
+                             uint32_t* zkey, uint32_t* idx, short4* rect, uint32_t* counters, uint32_t* vflag);
 __global__ void k_preprocess_views(int64_t n, SceneView sc, const CamParams* cps, PrimState* state, uint32_t* count,
                                    uint32_t* zkey, uint32_t* idx, short4* rect, uint32_t* n_visible);
 // list == nullptr: threads 0..n-1 are primitives 0..n-1; else primitive list[j].
+// pgrad_by_pos: the gradient record of thread j is pgrad[j] (state gathered in list
+// order), else pgrad[primitive].
 __global__ void k_preprocess_bwd(int64_t n, const uint32_t* list, SceneView sc, CamParams cp, const uint32_t* count,
-                                 const float* pgrad, GradView gd);
+                                 const float* pgrad, bool pgrad_by_pos, GradView gd);
 
 // ---------------------------------------------------------------- sorting / scan
 // Keys per CTA of the radix sort (histogram sizes depend on it).
@@ -60,6 +65,9 @@ size_t scan_tmp_elems(int64_t n);
 // Ping-pongs between (k0, v0) and (k1, v1); returns true if the result ends in (k1, v1).
 bool radix_sort_u32_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t n, int begin_bit,
                           int end_bit, SortTemp& tmp, cudaStream_t st, cudaError_t* err);
+// Stable LSD radix sort of u32 keys (no values) over bits [begin_bit, end_bit).
+bool radix_sort_u32_keys(uint32_t* k0, uint32_t* k1, int64_t n, int begin_bit, int end_bit, SortTemp& tmp,
+                         cudaStream_t st, cudaError_t* err);
 // Stable LSD radix sort of u64 keys (no values) over bits [begin_bit, end_bit).
 bool radix_sort_u64_keys(uint64_t* k0, uint64_t* k1, int64_t n, int begin_bit, int end_bit, SortTemp& tmp,
                          cudaStream_t st, cudaError_t* err);

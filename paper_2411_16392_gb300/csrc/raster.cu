@@ -199,11 +199,11 @@ __device__ __forceinline__ void pixel_of(int tile, int tiles_x, int& px, int& py
   py = (tile / tiles_x) * TILE + (warp >> 1) * 4 + (lane >> 3);
 }
 
-__device__ __forceinline__ void stage_batch(PrimState* sm, const uint32_t* ids, int id_stride, const PrimState* state,
-                                            uint32_t first, int cnt) {
+__device__ __forceinline__ void stage_batch(PrimState* sm, const uint32_t* ids, int id_stride, uint32_t id_mask,
+                                            const PrimState* state, uint32_t first, int cnt) {
   for (int e = threadIdx.x; e < cnt * 8; e += BLOCK) {
     const int r = e >> 3, c = e & 7;
-    const uint32_t pid = __ldg(ids + (size_t)(first + r) * id_stride);
+    const uint32_t pid = __ldg(ids + (size_t)(first + r) * id_stride) & id_mask;
     reinterpret_cast<float4*>(sm)[r * 8 + c] = __ldg(reinterpret_cast<const float4*>(state + pid) + c);
   }
 }
@@ -262,7 +262,7 @@ __device__ __forceinline__ void raster_fwd_tile(PrimState* sm, uint8_t* used, in
   for (int b0 = 0; b0 < n; b0 += BLOCK) {
     if (__syncthreads_count(done) == BLOCK) break;
     const int cnt = min(BLOCK, n - b0);
-    stage_batch(sm, ids, id_stride, state, rg.x + b0, cnt);
+    stage_batch(sm, ids, id_stride, rp.id_mask, state, rg.x + b0, cnt);
     used[threadIdx.x] = 0;
     __syncthreads();
     if (!done) {
@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(BLOCK, 3)
   for (int b0 = ((maxlast - 1) / BLOCK) * BLOCK; maxlast > 0 && b0 >= 0; b0 -= BLOCK) {
     const int cnt = min(BLOCK, maxlast - b0);
     __syncthreads();
-    stage_batch(sm, ids, id_stride, state, rg.x + b0, cnt);
+    stage_batch(sm, ids, id_stride, rp.id_mask, state, rg.x + b0, cnt);
     for (int e = threadIdx.x; e < BLOCK * NGRAD; e += BLOCK) (&sg[0][0])[e] = 0.f;
     sflag[threadIdx.x] = 0;
     suse[threadIdx.x] = (threadIdx.x < cnt && inst_used) ? inst_used[rg.x + b0 + threadIdx.x] : 1;
@@ -617,7 +617,7 @@ __global__ void __launch_bounds__(BLOCK, 3)
       if (sflag[r]) {
         const float val = sg[r][c];
         if (val != 0.f) {
-          const uint32_t pid = __ldg(ids + (size_t)(rg.x + b0 + r) * id_stride);
+          const uint32_t pid = __ldg(ids + (size_t)(rg.x + b0 + r) * id_stride) & rp.id_mask;
           atomicAdd(pgrad + (size_t)pid * NGRAD_PAD + c, val);
         }
       }

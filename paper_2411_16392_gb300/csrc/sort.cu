@@ -110,9 +110,16 @@ __global__ void __launch_bounds__(BLOCK) k_radix_upsweep(const K* __restrict__ k
   h[threadIdx.x] = 0;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * RS_CHUNK;
-  for (int k = threadIdx.x; k < RS_CHUNK; k += BLOCK) {
-    const int64_t i = base + k;
-    if (i < n) atomicAdd(&h[digit_of(keys[i], shift, mask)], 1u);
+  K kk[RS_CHUNK / BLOCK];  // all loads in flight before the first count
+#pragma unroll
+  for (int it = 0; it < RS_CHUNK / BLOCK; ++it) {
+    const int64_t i = base + it * BLOCK + threadIdx.x;
+    kk[it] = i < n ? keys[i] : (K)0;
+  }
+#pragma unroll
+  for (int it = 0; it < RS_CHUNK / BLOCK; ++it) {
+    const int64_t i = base + it * BLOCK + threadIdx.x;
+    if (i < n) atomicAdd(&h[digit_of(kk[it], shift, mask)], 1u);
   }
   __syncthreads();
   if (threadIdx.x <= mask) hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
@@ -141,30 +148,44 @@ __global__ void __launch_bounds__(BLOCK) k_radix_downsweep(const K* __restrict__
   __shared__ uint32_t lstart[256];
   __shared__ uint32_t wsum[RS_WARPS];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int e = threadIdx.x; e < RS_WARPS * 256; e += BLOCK) (&wh[0][0])[e] = 0;
-  if (threadIdx.x <= mask) boff[threadIdx.x] = offs[(size_t)threadIdx.x * nblocks + blockIdx.x];
-  __syncthreads();
   const int64_t cbase = (int64_t)blockIdx.x * RS_CHUNK;
   const int64_t wbase = cbase + (int64_t)warp * 32 * RS_ITEMS;
   const uint32_t lt = (1u << lane) - 1u;
+  const int nbits = 32 - __clz(mask);
   K kk[RS_ITEMS];
   uint32_t vv[RS_ITEMS];
   uint32_t rk[RS_ITEMS];
-  // all loads first (independent, in flight together), then the ranking below, whose
-  // warp barriers would otherwise serialise each load's latency
+  // every global load first (the chunk's keys and its digit offsets, independent and in
+  // flight together), then the ranking below, whose barriers would otherwise serialise
+  // each load's latency
+  const uint32_t my_off = threadIdx.x <= mask ? offs[(size_t)threadIdx.x * nblocks + blockIdx.x] : 0u;
 #pragma unroll
   for (int it = 0; it < RS_ITEMS; ++it) {
     const int64_t i = wbase + it * 32 + lane;
     kk[it] = i < n ? kin[i] : (K)0;
     if (HAS_VAL) vv[it] = i < n ? vin[i] : 0u;
   }
+  for (int e = threadIdx.x; e < RS_WARPS * 256; e += BLOCK) (&wh[0][0])[e] = 0;
+  if (threadIdx.x <= mask) boff[threadIdx.x] = my_off;
+  __syncthreads();
 #pragma unroll
   for (int it = 0; it < RS_ITEMS; ++it) {
     const int64_t i = wbase + it * 32 + lane;
     const bool valid = i < n;
     const K key = kk[it];
     const uint32_t d = valid ? digit_of(key, shift, mask) : 0x100u + (uint32_t)lane;
-    const uint32_t peers = __match_any_sync(FULL, d);
+    // lanes holding the same digit: one ballot per digit bit (invalid lanes carry a
+    // lane-unique value above the digit range and match nobody)
+    const uint32_t vmask = __ballot_sync(FULL, valid);  // every lane takes part in each ballot
+    uint32_t peers = valid ? vmask : (1u << lane);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      if (b < nbits) {  // uniform across the grid
+        const uint32_t bal = __ballot_sync(FULL, (d >> b) & 1u);
+        peers &= ((d >> b) & 1u) ? bal : ~bal;
+      }
+    }
+    if (!valid) peers = 1u << lane;
     const uint32_t before = valid ? wh[warp][d] : 0u;
     __syncwarp();
     if (valid && (peers & lt) == 0) wh[warp][d] = before + __popc(peers);
@@ -310,6 +331,11 @@ cudaError_t scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, uin
 bool radix_sort_u32_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t n, int begin_bit,
                           int end_bit, SortTemp& tmp, cudaStream_t st, cudaError_t* err) {
   return radix_sort_impl<uint32_t, true>(k0, v0, k1, v1, n, begin_bit, end_bit, tmp, st, err);
+}
+
+bool radix_sort_u32_keys(uint32_t* k0, uint32_t* k1, int64_t n, int begin_bit, int end_bit, SortTemp& tmp,
+                         cudaStream_t st, cudaError_t* err) {
+  return radix_sort_impl<uint32_t, false>(k0, nullptr, k1, nullptr, n, begin_bit, end_bit, tmp, st, err);
 }
 
 bool radix_sort_u64_keys(uint64_t* k0, uint64_t* k1, int64_t n, int begin_bit, int end_bit, SortTemp& tmp,
