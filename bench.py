@@ -27,15 +27,31 @@ METRIC = "fwd+bwd Mpix/s at 3M quadrics (1297x840)"
 UNIT = "Mpix/s"
 WORKLOAD = "unbounded_3m_1297x840"
 
-# FP32 operations (FMA = 2) per pair class, counted from the kernel source
-# (raster.cu): a pair inside the primitive's pixel box solves the quadratic and tests
-# its candidates (FLOP_ISECT); a hit adds the arc-length ratio and G (FLOP_HIT); a
-# blended pair adds colour/depth/normal accumulation (FLOP_BLEND); a pair that produces
-# a gradient in the backward adds the chain rule and the warp reduction (FLOP_GRAD).
-FLOP_ISECT = 55
-FLOP_HIT = 20
-FLOP_BLEND = 44
-FLOP_GRAD = 190
+# FP32 operations (FMA = 2, MUFU = 1) per pair class, counted from the kernel source
+# (raster.cu, eval_pair and the two compositing loops) along the shortest path of each
+# class: every evaluated pair forms its pixel offset and tests the screen parallelogram
+# (FLOP_EVAL); a pair inside it forms the local ray, the quadratic and its first root up
+# to the E <= 9 test (FLOP_ISECT); a hit adds the chord test, F(u), l^2/sigma^2 and G
+# (FLOP_HIT); a blended pair adds alpha, transmittance, colour, depth and the normal
+# (FLOP_BLEND); a pair that produces a gradient in the backward adds the chain rule and
+# its share of the warp reduction (FLOP_GRAD).
+FLOP_EVAL = 12
+FLOP_ISECT = 54
+FLOP_HIT = 24
+FLOP_BLEND = 46
+FLOP_GRAD = 200
+
+# Algorithmic HBM bytes of the memory-bound stages (minimal traffic of what each stage
+# computes): per primitive read 144 B of parameters (mean 12, quaternion 16, scales 8,
+# curvatures 8, opacity 4, bf16 SH 96) and write count, depth key, rectangle and flag
+# (20 B); per visible primitive the 128-byte state record. Binning per visible primitive:
+# a 4-pass (key, index) sort (20 B per pass) and the state gather (256 B); per
+# instance: the 4-byte emitted key, two stable tile passes (12 B each) and the range
+# scan (4 B). Preprocess backward per visible primitive: the 80-byte gradient record,
+# the parameters (144 B) and a read-modify-write of the float32 gradients (240 B x 2).
+B_PRE_PRIM, B_PRE_VIS = 164, 128
+B_BIN_VIS, B_BIN_INST = 4 * 20 + 256, 4 + 2 * 12 + 4
+B_PREBWD_VIS = 80 + 144 + 480
 
 
 def _rank_env():
@@ -336,10 +352,12 @@ def _report(args, rank, world, sc, cam, st, stage, clk, ms_max, value, e2e_value
     peaks, peak_kind = _peaks()
     mean = {k: (sum(v) / len(v) if v and min(v) >= 0 else None) for k, v in stage.items()}
     bwd_ms, fwd_ms = mean["ms_raster_bwd"], mean["ms_raster_fwd"]
-    flops_fwd = st["pair_isect"] * FLOP_ISECT + st["pair_hits"] * FLOP_HIT + st["pair_blended"] * FLOP_BLEND
+    flops_fwd = (st["pair_evals"] * FLOP_EVAL + st["pair_isect"] * FLOP_ISECT + st["pair_hits"] * FLOP_HIT
+                 + st["pair_blended"] * FLOP_BLEND)
     # backward recomputes the pairs up to each pixel's last blended one
     isect_frac = st["pair_isect"] / max(1, st["pair_evals"])
-    flops_bwd = (st["bwd_pairs"] * isect_frac * FLOP_ISECT + st["bwd_contrib"] * (FLOP_HIT + FLOP_GRAD))
+    flops_bwd = (st["bwd_pairs"] * (FLOP_EVAL + isect_frac * FLOP_ISECT)
+                 + st["bwd_contrib"] * (FLOP_HIT + FLOP_GRAD))
     sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     peak_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     if bwd_ms is not None and (fwd_ms is None or bwd_ms >= fwd_ms):
@@ -353,6 +371,29 @@ def _report(args, rank, world, sc, cam, st, stage, clk, ms_max, value, e2e_value
                              f"sampled during the timed region)",
                 "ms_per_launch": dom_ms,
                 "flops_per_launch": dom_flops}
+    # ---- every stage against its own roof; the frame against the sum of the roofs
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    V, I, N = st["n_visible"], st["n_instances"], sc.n
+    work = {"ms_preprocess": ("hbm", N * B_PRE_PRIM + V * B_PRE_VIS),
+            "ms_binning": ("hbm", V * B_BIN_VIS + I * B_BIN_INST),
+            "ms_raster_fwd": ("alu", flops_fwd),
+            "ms_raster_bwd": ("alu", flops_bwd),
+            "ms_preprocess_bwd": ("hbm", V * B_PREBWD_VIS)}
+    stage_t = dict(mean)
+    if all(stage_t.get(k) is not None for k in ("ms_depth_sort", "ms_emit", "ms_tile_sort")):
+        stage_t["ms_binning"] = stage_t["ms_depth_sort"] + stage_t["ms_emit"] + stage_t["ms_tile_sort"]
+    stages, roof_sum = {}, 0.0
+    for k, (bound, amount) in work.items():
+        ms = stage_t.get(k)
+        peak_v = hbm * 1e9 if bound == "hbm" else peak_tflops * 1e12
+        roof_ms = amount / peak_v * 1e3
+        roof_sum += roof_ms
+        if ms:
+            ach = amount / (ms * 1e-3)
+            stages[k[3:]] = {"bound": bound, "ms": ms, "roof_ms": roof_ms,
+                             "achieved": ach / (1e9 if bound == "hbm" else 1e12),
+                             "unit": "GB/s" if bound == "hbm" else "TFLOP/s", "frac": ach / peak_v}
+    frame_roof = {"ms_roof_sum": roof_sum, "ms_measured": ms_max, "frac": roof_sum / ms_max if ms_max else None}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -365,7 +406,7 @@ def _report(args, rank, world, sc, cam, st, stage, clk, ms_max, value, e2e_value
             "stage_ms": mean, "counters": {k: st[k] for k in ("pair_evals", "pair_isect", "pair_hits",
                                                                "pair_blended", "grazing_resolves",
                                                                "bwd_pairs", "bwd_contrib")},
-            "roofline": roofline, "peak_source": peak_kind,
+            "roofline": roofline, "peak_source": peak_kind, "stage_roofline": stages, "frame_roofline": frame_roof,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int((st["launches_fwd"] + st["launches_bwd"]) * args.steps),
             "clocks": clk}
