@@ -50,8 +50,24 @@ FLOP_GRAD = 200
 # scan (4 B). Preprocess backward per visible primitive: the 80-byte gradient record,
 # the parameters (144 B) and a read-modify-write of the float32 gradients (240 B x 2).
 B_PRE_PRIM, B_PRE_VIS = 164, 128
+# DRAM bytes (read + write) per launch of the compositing kernels at 3M / 1297x840, from
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, summary under profiles/),
+# valid only while the kernels' sources hash to the recorded value.
+TRAFFIC_SRC = ("paper_2411_16392_gb300/csrc/raster.cu", "paper_2411_16392_gb300/csrc/qgs_common.cuh")
+TRAFFIC = {"hash": "4050c0e82b1a4bd9", "k_raster_fwd": 20106752 + 2951424, "k_raster_bwd": 66314496 + 136192}
 B_BIN_VIS, B_BIN_INST = 4 * 20 + 256, 4 + 2 * 12 + 4
 B_PREBWD_VIS = 80 + 144 + 480
+
+
+def _traffic(kernel, n_prims):
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SRC:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != TRAFFIC["hash"] or n_prims != 3_000_000:
+        return None
+    return TRAFFIC.get(kernel)
 
 
 def _rank_env():
@@ -366,7 +382,7 @@ def _report(args, rank, world, sc, cam, st, stage, clk, ms_max, value, e2e_value
         dom, dom_ms, dom_flops = "k_raster_fwd", fwd_ms, flops_fwd
     achieved = dom_flops / (dom_ms * 1e-3) / 1e12 if dom_ms else None
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": (achieved / peak_tflops) if achieved else None, "traffic": None,
+                "frac": (achieved / peak_tflops) if achieved else None, "traffic": _traffic(dom, sc.n),
                 "peak_note": f"FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM clock "
                              f"sampled during the timed region)",
                 "ms_per_launch": dom_ms,
