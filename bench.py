@@ -190,25 +190,28 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- GPU
-def serve_measure(dev_index, ds, n_req, lam, slots, batch=1, seed=0, budget=64 << 30):
-    """Open-loop serving run: Poisson arrivals at `lam` requests/s, cameras on a radius-2
-    orbit with resolutions drawn from {256^2, 512x384, 1024x768, 1920x1080}; returns the
-    server's latency statistics (submit -> result ready on the device)."""
+def serve_measure(dev_index, scenes, jobs, gaps, slots, batch=1, budget=64 << 30, grad_sets=None):
+    """Open-loop serving run: job k = (scene index, camera, backward?) is submitted at the
+    cumulative time of gaps[:k+1] (Poisson arrivals); backward jobs carry one of the
+    `grad_sets` upstream planes (pinned host tensors). Returns the server's latency
+    statistics (submit -> result ready on the device)."""
     import threading
-    import numpy as np
-    from paper_2411_16392_gb300.scenes import orbit_camera
     from paper_2411_16392_gb300.serve import Server
-    rng = np.random.default_rng(seed)
-    cams = [orbit_camera(rng) for _ in range(n_req)]
-    gaps = rng.exponential(1.0 / lam, n_req)
+    n_req = len(jobs)
     srv = Server(dev_index, budget_bytes=budget, slots=slots, queue=max(64, n_req), batch=batch)
-    sid = srv.load_scene(ds)
-    for cam in cams[:4]:                        # warm-up (buffers, kernels)
-        srv.wait(srv.submit(sid, cam))
+    sids = [srv.load_scene(ds) for ds in scenes]
+
+    def submit(k):
+        si, cam, bwd = jobs[k]
+        if bwd:
+            return srv.submit(sids[si], cam, backward=True, grad_out=grad_sets[k % len(grad_sets)])
+        return srv.submit(sids[si], cam)
+
+    for k in range(min(4, n_req)):              # warm-up (buffers, kernels)
+        srv.wait(submit(k))
     srv.reset_stats()
     tickets = []
     lock = threading.Lock()
-    done = threading.Event()
 
     def waiter():
         k = 0
@@ -220,18 +223,16 @@ def serve_measure(dev_index, ds, n_req, lam, slots, batch=1, seed=0, budget=64 <
                 k += 1
             else:
                 time.sleep(0.0002)
-        done.set()
 
     th = threading.Thread(target=waiter)
     th.start()
-    t0 = time.perf_counter()
-    t_next = t0
-    for cam, gap in zip(cams, gaps):
+    t_next = time.perf_counter()
+    for k, gap in enumerate(gaps):
         t_next += gap
         dt = t_next - time.perf_counter()
         if dt > 0:
             time.sleep(dt)
-        t = srv.submit(sid, cam)
+        t = submit(k)
         with lock:
             tickets.append(t)
     th.join()
@@ -447,18 +448,62 @@ def _serving_leg(args):
     import torch
     from paper_2411_16392_gb300.render import DeviceScene
     from paper_2411_16392_gb300.scenes import serving_scene
+    import numpy as np
+    from paper_2411_16392_gb300.scenes import orbit_camera
     dev = torch.device("cuda", torch.cuda.current_device())
     ds = DeviceScene.from_host(serving_scene(0, 1_000_000), dev)
     res = {"workload": "serving_1m_mixed_res", "requests": args.serve_requests, "rates": []}
     legs = (("one_at_a_time", 1, 1), (f"slots{args.serve_slots}", args.serve_slots, 1),
             ("batched", args.serve_slots, args.serve_batch))
+    n = args.serve_requests
     for rate in args.serve_rate:
+        rng = np.random.default_rng(0)
+        jobs = [(0, orbit_camera(rng), False) for _ in range(n)]
+        gaps = rng.exponential(1.0 / rate, n)
         r = {"arrival_rate_per_s": rate}
         for name, slots, batch in legs:
-            r[name] = serve_measure(dev.index, ds, args.serve_requests, rate, slots, batch)
+            r[name] = serve_measure(dev.index, [ds], jobs, gaps, slots, batch)
         r["batched_config"] = {"slots": args.serve_slots, "max_batch": args.serve_batch}
         res["rates"].append(r)
     del ds
+    if args.serve_mixed_rate > 0:
+        res["mixed"] = _serving_mixed_leg(args, dev)
+    return res
+
+
+def _serving_mixed_leg(args, dev):
+    """Six resident scenes of 0.2/0.5/1/2/3/4 M quadrics; each request picks a scene
+    uniformly; 80 % are forward views at the serving resolutions, 20 % forward + backward
+    at 1297x840 with N(0, 1) upstream gradients; HBM-budget admission. Plain one-at-a-time
+    against slots with batching, same arrivals."""
+    import numpy as np
+    import torch
+    from paper_2411_16392_gb300.render import DeviceScene
+    from paper_2411_16392_gb300.scenes import orbit_camera, serving_scene
+    sizes = (200_000, 500_000, 1_000_000, 2_000_000, 3_000_000, 4_000_000)
+    scenes = [DeviceScene.from_host(serving_scene(10 + k, m), dev) for k, m in enumerate(sizes)]
+    n = args.serve_requests
+    rng = np.random.default_rng(1)
+    jobs = []
+    for _ in range(n):
+        si = int(rng.integers(len(sizes)))
+        if rng.random() < 0.2:
+            jobs.append((si, orbit_camera(rng, res=(1297, 840)), True))
+        else:
+            jobs.append((si, orbit_camera(rng), False))
+    gaps = rng.exponential(1.0 / args.serve_mixed_rate, n)
+    gen = torch.Generator().manual_seed(2)
+    grad_sets = []
+    for _ in range(4):
+        g = {"rgb": torch.randn(3, 840, 1297, generator=gen), "alpha": torch.randn(840, 1297, generator=gen),
+             "depth": torch.randn(840, 1297, generator=gen), "normal": torch.randn(3, 840, 1297, generator=gen)}
+        grad_sets.append({k: v.pin_memory() for k, v in g.items()})
+    res = {"workload": "serving_6_scenes_0.2-4m_80fwd_20fwdbwd", "requests": n,
+           "arrival_rate_per_s": args.serve_mixed_rate, "backward_share": 0.2}
+    for name, slots, batch in (("one_at_a_time", 1, 1), ("batched", args.serve_slots, args.serve_batch)):
+        res[name] = serve_measure(dev.index, scenes, jobs, gaps, slots, batch, grad_sets=grad_sets)
+    res["batched_config"] = {"slots": args.serve_slots, "max_batch": args.serve_batch}
+    del scenes
     return res
 
 
@@ -478,6 +523,8 @@ def main():
                     help="Poisson arrival rates, requests/s (comma-separated)")
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-batch", type=int, default=8, help="most views per batch in the batched leg")
+    ap.add_argument("--serve-mixed-rate", type=float, default=100.0,
+                    help="arrival rate of the six-scene forward/backward serving leg (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

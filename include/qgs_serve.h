@@ -6,7 +6,8 @@
  * (include/qgs.h: render_forward, Sec. 3.1-3.2 and the supplementary). It implements
  * continuous batching:
  *   - scenes are copied once into server-owned device memory (serve_load_scene);
- *   - serve_submit enqueues a view request and returns at once (bounded FIFO queue);
+ *   - serve_submit enqueues a view request (forward, or forward + backward with upstream
+ *     gradients) and returns at once (bounded FIFO queue);
  *   - worker slots, each with its own rendering context and CUDA stream, take requests
  *     from the head of the queue as soon as a slot is free AND the request's estimated
  *     memory (projected primitives, tile keys and their sort buffers, residue, result
@@ -66,20 +67,30 @@ void serve_destroy(qgs_server* srv);
  * ENOMEM, ECUDA. */
 qgs_status serve_load_scene(qgs_server* srv, const qgs_scene* scene, int32_t* scene_id);
 
-/* Enqueue a forward render of scene `scene_id` from `cam`; returns immediately with a
- * ticket. Errors: EINVAL (bad camera or size), ENOTFOUND (scene), EBUSY (queue full),
- * ECAPACITY (the request alone exceeds the budget). */
-qgs_status serve_submit(qgs_server* srv, int32_t scene_id, const qgs_camera* cam, uint64_t* ticket);
+/* Enqueue a render of scene `scene_id` from `cam`; returns with a ticket once queued.
+ * want_backward = 0: forward only (batched with other queued forward views of the scene).
+ * want_backward = 1: forward, then the backward of sum(grad_out . planes) (render_backward;
+ * the paper's training step, Sec. 3.3, without the optimiser); grad_out's four base planes
+ * (rgb 3HW, alpha HW, depth HW, normal 3HW; host or device; a NULL plane or grad_out = NULL
+ * means zero) are copied before the call returns; its extra planes must be NULL. A backward
+ * request runs alone and its parameter gradients are returned by serve_wait.
+ * Errors: EINVAL (bad camera, size or plane), ENOTFOUND (scene), EBUSY (queue full),
+ * ECAPACITY (the request alone exceeds the budget), ENOMEM/ECUDA (upstream copy). */
+qgs_status serve_submit(qgs_server* srv, int32_t scene_id, const qgs_camera* cam, int32_t want_backward,
+                        const qgs_image* grad_out, uint64_t* ticket);
 
 /* Wait up to timeout_ms (< 0: no limit) for a ticket to finish, then copy its planes
  * into `out` (rgb 3HW, alpha HW, depth HW, normal 3HW floats; any plane may be NULL;
  * host or device pointers; the extra planes of qgs_image are not served and must be
- * NULL) and release the ticket. The copy is ordered after work on
- * the legacy default stream; work on other streams that writes `out` must be finished
- * by the caller. Returns after the copy has completed. Errors: ENOTFOUND (unknown or
- * already released ticket), ETIMEDOUT (still running; the ticket stays valid), the
- * request's own error status, ECUDA. */
-qgs_status serve_wait(qgs_server* srv, uint64_t ticket, int32_t timeout_ms, const qgs_image* out);
+ * NULL) and, for a backward request, its parameter gradients into `grad` (float32 arrays
+ * in qgs_scene layouts, sh float32 [n*48]; overwritten, not added; any array may be NULL;
+ * grad must be NULL for a forward request: EINVAL), then release the ticket. The copies
+ * are ordered after work on the legacy default stream; work on other streams that writes
+ * the destinations must be finished by the caller. Returns after the copies have
+ * completed. Errors: ENOTFOUND (unknown or already released ticket), ETIMEDOUT (still
+ * running; the ticket stays valid), EINVAL, the request's own error status, ECUDA. */
+qgs_status serve_wait(qgs_server* srv, uint64_t ticket, int32_t timeout_ms, const qgs_image* out,
+                      const qgs_scene_grad* grad);
 
 /* Statistics since creation or the last serve_reset_stats. */
 qgs_status serve_stats(qgs_server* srv, qgs_serve_stats* stats);

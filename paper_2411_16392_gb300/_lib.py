@@ -84,8 +84,9 @@ EXPORTS = [
                                C.c_double]),
     ("serve_destroy", None, [_P]),
     ("serve_load_scene", C.c_int, [_P, C.POINTER(qgs_scene), C.POINTER(C.c_int32)]),
-    ("serve_submit", C.c_int, [_P, C.c_int32, C.POINTER(qgs_camera), C.POINTER(C.c_uint64)]),
-    ("serve_wait", C.c_int, [_P, C.c_uint64, C.c_int32, C.POINTER(qgs_image)]),
+    ("serve_submit", C.c_int, [_P, C.c_int32, C.POINTER(qgs_camera), C.c_int32, C.POINTER(qgs_image),
+                               C.POINTER(C.c_uint64)]),
+    ("serve_wait", C.c_int, [_P, C.c_uint64, C.c_int32, C.POINTER(qgs_image), C.POINTER(qgs_scene_grad)]),
     ("serve_stats", C.c_int, [_P, C.POINTER(qgs_serve_stats)]),
     ("serve_reset_stats", C.c_int, [_P]),
 ]

@@ -40,7 +40,17 @@ struct Request {
   int64_t est_bytes = 0;
   float* result = nullptr;       // 8 planes of W*H floats (device, or host in fake mode)
   bool result_on_host = false;
+  bool want_bwd = false;         // forward + backward request
+  float* grad_in = nullptr;      // upstream gradient planes, 8 x W*H (device; null: zero)
+  float* grads = nullptr;        // parameter gradients, 60 floats per primitive (device or host)
 };
+
+// Parameter-gradient layout of a backward request's result: mean 3n, quat 4n, scale 2n,
+// curv 2n, opacity n, sh 48n floats (the qgs_scene_grad arrays, back to back).
+constexpr int kGradFloats = 60;
+inline qgs_scene_grad grad_view(float* g, int64_t n) {
+  return qgs_scene_grad{g, g + 3 * n, g + 7 * n, g + 9 * n, g + 11 * n, g + 12 * n};
+}
 
 struct Slot {
   qgs_ctx* ctx = nullptr;
@@ -48,12 +58,15 @@ struct Slot {
   std::thread th;
 };
 
-int64_t request_bytes(const SceneDev& s, const qgs_camera& c) {
+int64_t request_bytes(const SceneDev& s, const qgs_camera& c, bool bwd) {
   const double P = (double)c.W * c.H;
   const double inst = s.inst_per_pixel * P;
   // projected state + per-primitive keys/indices/offsets, instance ping-pong buffers,
-  // radix histogram, residue, and the 8 result planes
-  return (int64_t)(s.n * 168.0 + inst * 16.0 + inst / 16.0 + P * 8.0 + P * 32.0) + (1 << 20);
+  // radix histogram, residue, and the 8 result planes; a backward adds the per-primitive
+  // gradient records, the parameter gradients and the upstream planes
+  double b = s.n * 168.0 + inst * 16.0 + inst / 16.0 + P * 8.0 + P * 32.0;
+  if (bwd) b += s.n * (80.0 + 4.0 * kGradFloats) + P * 32.0;
+  return (int64_t)b + (1 << 20);
 }
 
 }  // namespace
@@ -97,10 +110,14 @@ void qgs_server::run_batch(Slot& s, std::vector<Request*>& batch) {
     int64_t P_all = 0;
     for (Request* r : batch) {
       const int64_t P = (int64_t)r->cam.W * r->cam.H;
-      P_all += P;
+      P_all += r->want_bwd ? 3 * P : P;  // a backward costs about twice a forward
       r->result = static_cast<float*>(calloc((size_t)P * 8, sizeof(float)));
       r->result_on_host = true;
       r->status = r->result ? QGS_OK : QGS_ENOMEM;
+      if (r->want_bwd) {
+        r->grads = static_cast<float*>(calloc((size_t)std::max<int64_t>(r->scn.n, 1) * kGradFloats, sizeof(float)));
+        if (!r->grads) r->status = QGS_ENOMEM;
+      }
     }
     const double us = fake_us_per_mpix * (double)P_all / 1e6;
     std::this_thread::sleep_for(std::chrono::microseconds((int64_t)us));
@@ -132,6 +149,23 @@ void qgs_server::run_batch(Slot& s, std::vector<Request*>& batch) {
     else
       st = render_forward_batch(s.ctx, &scn, (int32_t)batch.size(), cams.data(), outs.data(), s.stream);
   }
+  if (st == QGS_OK && batch.size() == 1 && batch[0]->want_bwd) {
+    // a backward request runs alone: gradients of sum(grad_in . planes) into its buffer
+    Request* r = batch[0];
+    const int64_t P = (int64_t)r->cam.W * r->cam.H;
+    void* g = nullptr;
+    cudaError_t e = cudaMallocAsync(&g, sizeof(float) * kGradFloats * (size_t)std::max<int64_t>(sc.n, 1), s.stream);
+    if (e != cudaSuccess) {
+      st = e == cudaErrorMemoryAllocation ? QGS_ENOMEM : QGS_ECUDA;
+    } else {
+      r->grads = static_cast<float*>(g);
+      if (cudaMemsetAsync(g, 0, sizeof(float) * kGradFloats * (size_t)sc.n, s.stream) != cudaSuccess) st = QGS_ECUDA;
+      float* gi = r->grad_in;
+      qgs_image gin{gi, gi ? gi + 3 * P : nullptr, gi ? gi + 4 * P : nullptr, gi ? gi + 5 * P : nullptr};
+      const qgs_scene_grad gv = grad_view(r->grads, sc.n);
+      if (st == QGS_OK) st = render_backward(s.ctx, &scn, &r->cam, &gin, &gv, s.stream);
+    }
+  }
   if (st == QGS_OK && cudaStreamSynchronize(s.stream) != cudaSuccess) st = QGS_ECUDA;
   for (Request* r : batch) r->status = st;
   if (st == QGS_OK) {
@@ -162,10 +196,11 @@ void qgs_server::worker(int si) {
       queue.pop_front();
       batch.push_back(head);
       est = head->est_bytes;
-      // the other queued views of the same scene that still fit join the head's launches
-      for (auto it = queue.begin(); it != queue.end() && (int)batch.size() < max_batch;) {
+      // the other queued forward views of the same scene that still fit join the head's
+      // launches (a backward request runs alone)
+      for (auto it = queue.begin(); it != queue.end() && !head->want_bwd && (int)batch.size() < max_batch;) {
         Request* r = *it;
-        if (r->scene == head->scene && reserved + est + r->est_bytes <= budget) {
+        if (!r->want_bwd && r->scene == head->scene && reserved + est + r->est_bytes <= budget) {
           batch.push_back(r);
           est += r->est_bytes;
           it = queue.erase(it);
@@ -259,12 +294,14 @@ void serve_destroy(qgs_server* s) {
   if (!s->fake) cudaSetDevice(s->device);
   for (auto& kv : s->reqs) {
     Request* r = kv.second.get();
-    if (r->result) {
-      if (r->result_on_host)
-        free(r->result);
-      else
-        cudaFree(r->result);
+    if (r->result_on_host) {
+      free(r->result);
+      free(r->grads);
+    } else {
+      if (r->result) cudaFree(r->result);
+      if (r->grads) cudaFree(r->grads);
     }
+    if (r->grad_in) cudaFree(r->grad_in);
   }
   for (auto& sl : s->slots) {
     if (sl.ctx) qgs_destroy(sl.ctx);
@@ -323,24 +360,57 @@ qgs_status serve_load_scene(qgs_server* s, const qgs_scene* sc, int32_t* scene_i
   return QGS_OK;
 }
 
-qgs_status serve_submit(qgs_server* s, int32_t scene_id, const qgs_camera* cam, uint64_t* ticket) {
+qgs_status serve_submit(qgs_server* s, int32_t scene_id, const qgs_camera* cam, int32_t want_backward,
+                        const qgs_image* grad_out, uint64_t* ticket) {
   if (!s || !cam || !ticket) return QGS_EINVAL;
   if (cam->W <= 0 || cam->H <= 0 || cam->W > 32768 || cam->H > 32768 || !(cam->fx > 0) || !(cam->fy > 0) ||
       !(cam->near_plane > 0))
     return QGS_EINVAL;
+  if (grad_out && (grad_out->curvature || grad_out->distortion || grad_out->median_depth)) return QGS_EINVAL;
   std::unique_ptr<Request> r(new (std::nothrow) Request());
   if (!r) return QGS_ENOMEM;
+  r->want_bwd = want_backward != 0;
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if (scene_id < 0 || scene_id >= (int32_t)s->scenes.size()) return QGS_ENOTFOUND;
+    r->scn = s->scenes[scene_id];
+  }
+  const int64_t P = (int64_t)cam->W * cam->H;
+  if (r->want_bwd && !s->fake && grad_out &&
+      (grad_out->rgb || grad_out->alpha || grad_out->depth || grad_out->normal)) {
+    // the upstream planes are copied now, so the caller may reuse its buffers at once
+    cudaSetDevice(s->device);
+    void* g = nullptr;
+    if (cudaMalloc(&g, sizeof(float) * 8 * (size_t)P) != cudaSuccess) return QGS_ENOMEM;
+    r->grad_in = static_cast<float*>(g);
+    const float* src[4] = {grad_out->rgb, grad_out->alpha, grad_out->depth, grad_out->normal};
+    const size_t off[4] = {0, 3 * (size_t)P, 4 * (size_t)P, 5 * (size_t)P};
+    const size_t cnt[4] = {3 * (size_t)P, (size_t)P, (size_t)P, 3 * (size_t)P};
+    bool ok = true;
+    for (int k = 0; k < 4 && ok; ++k) {
+      if (src[k])
+        ok = cudaMemcpyAsync(r->grad_in + off[k], src[k], sizeof(float) * cnt[k], cudaMemcpyDefault,
+                             s->copy_stream) == cudaSuccess;
+      else
+        ok = cudaMemsetAsync(r->grad_in + off[k], 0, sizeof(float) * cnt[k], s->copy_stream) == cudaSuccess;
+    }
+    if (cudaStreamSynchronize(s->copy_stream) != cudaSuccess) ok = false;
+    if (!ok) {
+      cudaFree(r->grad_in);
+      return QGS_ECUDA;
+    }
+  }
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
     if ((int)s->queue.size() >= s->queue_cap) {
       ++s->rejected;
+      if (r->grad_in) cudaFree(r->grad_in);
       return QGS_EBUSY;
     }
-    r->scn = s->scenes[scene_id];
-    r->est_bytes = request_bytes(r->scn, *cam);
+    r->est_bytes = request_bytes(r->scn, *cam, r->want_bwd);
     if (r->est_bytes > s->budget) {
       ++s->rejected;
+      if (r->grad_in) cudaFree(r->grad_in);
       return QGS_ECAPACITY;
     }
     r->ticket = s->next_ticket++;
@@ -360,7 +430,8 @@ qgs_status serve_submit(qgs_server* s, int32_t scene_id, const qgs_camera* cam, 
   return QGS_OK;
 }
 
-qgs_status serve_wait(qgs_server* s, uint64_t ticket, int32_t timeout_ms, const qgs_image* out) {
+qgs_status serve_wait(qgs_server* s, uint64_t ticket, int32_t timeout_ms, const qgs_image* out,
+                      const qgs_scene_grad* grad) {
   if (!s) return QGS_EINVAL;
   if (out && (out->curvature || out->distortion || out->median_depth)) return QGS_EINVAL;  // base planes only
   Request* r = nullptr;
@@ -369,6 +440,7 @@ qgs_status serve_wait(qgs_server* s, uint64_t ticket, int32_t timeout_ms, const 
     auto it = s->reqs.find(ticket);
     if (it == s->reqs.end()) return QGS_ENOTFOUND;
     r = it->second.get();
+    if (grad && !r->want_bwd) return QGS_EINVAL;  // a forward request has no gradients
     auto done = [&] { return r->state == 2; };
     if (timeout_ms < 0) {
       s->cv_done.wait(lk, done);
@@ -398,15 +470,39 @@ qgs_status serve_wait(qgs_server* s, uint64_t ticket, int32_t timeout_ms, const 
       if (cudaStreamSynchronize(s->copy_stream) != cudaSuccess) st = QGS_ECUDA;
     }
   }
-  if (r->result) {
+  if (st == QGS_OK && grad && r->grads) {
+    const int64_t n = r->scn.n;
+    float* dst[6] = {grad->mean, grad->quat, grad->scale, grad->curv, grad->opacity, grad->sh};
+    const qgs_scene_grad gv = grad_view(r->grads, n);
+    const float* src[6] = {gv.mean, gv.quat, gv.scale, gv.curv, gv.opacity, gv.sh};
+    const size_t cnt[6] = {3 * (size_t)n, 4 * (size_t)n, 2 * (size_t)n, 2 * (size_t)n, (size_t)n, 48 * (size_t)n};
     if (r->result_on_host) {
-      free(r->result);
+      for (int k = 0; k < 6; ++k)
+        if (dst[k] && n > 0) memcpy(dst[k], src[k], sizeof(float) * cnt[k]);
     } else {
       cudaSetDevice(s->device);
-      cudaFreeAsync(r->result, s->copy_stream);
+      for (int k = 0; k < 6 && st == QGS_OK; ++k)
+        if (dst[k] && n > 0 &&
+            cudaMemcpyAsync(dst[k], src[k], sizeof(float) * cnt[k], cudaMemcpyDefault, s->copy_stream) != cudaSuccess)
+          st = QGS_ECUDA;
+      if (cudaStreamSynchronize(s->copy_stream) != cudaSuccess) st = QGS_ECUDA;
     }
-    r->result = nullptr;
   }
+  if (r->result_on_host) {
+    free(r->result);
+    free(r->grads);
+  } else {
+    cudaSetDevice(s->device);
+    if (r->result) cudaFreeAsync(r->result, s->copy_stream);
+    if (r->grads) cudaFreeAsync(r->grads, s->copy_stream);
+  }
+  if (r->grad_in) {
+    cudaSetDevice(s->device);
+    cudaFree(r->grad_in);
+  }
+  r->result = nullptr;
+  r->grads = nullptr;
+  r->grad_in = nullptr;
   std::lock_guard<std::mutex> lk(s->mu);
   s->reqs.erase(ticket);
   return st;

@@ -10,6 +10,14 @@ from . import _lib as L
 from .render import DeviceScene, camera_to_c
 
 
+def _ptr(v):
+    if v is None:
+        return None
+    if isinstance(v, torch.Tensor):
+        return v.data_ptr()
+    return v.ctypes.data
+
+
 class Server:
     """Continuous-batching server: resident scenes, bounded queue, memory-budget admission,
     `slots` concurrent worker contexts, each rendering up to `batch` queued views of one
@@ -43,29 +51,35 @@ class Server:
         L.check(self.lib.serve_load_scene(self._srv, C.byref(sc), C.byref(sid)))
         return sid.value
 
-    def submit(self, scene_id: int, cam) -> int:
+    def submit(self, scene_id: int, cam, backward: bool = False, grad_out: dict | None = None) -> int:
+        """Queue a forward render, or with `backward` a forward + backward whose upstream
+        gradient planes are `grad_out` (dict of rgb/alpha/depth/normal, host or device;
+        missing planes are zero; copied before this returns)."""
         t = C.c_uint64()
         cc = camera_to_c(cam)
-        st = self.lib.serve_submit(self._srv, scene_id, C.byref(cc), C.byref(t))
+        g = None
+        if grad_out is not None:
+            g = L.qgs_image(*[_ptr(grad_out.get(k)) for k in ("rgb", "alpha", "depth", "normal")])
+        st = self.lib.serve_submit(self._srv, scene_id, C.byref(cc), int(bool(backward)),
+                                   C.byref(g) if g is not None else None, C.byref(t))
         if st != 0:
             raise L.QGSError(st, "serve_submit")
         return t.value
 
-    def wait(self, ticket: int, cam=None, timeout_ms: int = -1, out: dict | None = None):
+    def wait(self, ticket: int, cam=None, timeout_ms: int = -1, out: dict | None = None,
+             grads: dict | None = None):
         """Wait for a ticket; copy its planes into `out` (dict of tensors/arrays, host or
-        device) when given. Returns `out`."""
-        def ptr(v):
-            if v is None:
-                return None
-            if isinstance(v, torch.Tensor):
-                return v.data_ptr()
-            return v.ctypes.data
+        device) and, for a backward request, its parameter gradients into `grads` (dict of
+        mean/quat/scale/curv/opacity/sh float32 arrays) when given. Returns `out`."""
         img = None
         if out is not None:
-            img = L.qgs_image(ptr(out.get("rgb")), ptr(out.get("alpha")), ptr(out.get("depth")),
-                              ptr(out.get("normal")))
+            img = L.qgs_image(*[_ptr(out.get(k)) for k in ("rgb", "alpha", "depth", "normal")])
+        gr = None
+        if grads is not None:
+            gr = L.qgs_scene_grad(*[_ptr(grads.get(k)) for k in ("mean", "quat", "scale", "curv", "opacity", "sh")])
         st = self.lib.serve_wait(self._srv, C.c_uint64(ticket), int(timeout_ms),
-                                 C.byref(img) if img is not None else None)
+                                 C.byref(img) if img is not None else None,
+                                 C.byref(gr) if gr is not None else None)
         if st != 0:
             raise L.QGSError(st, "serve_wait")
         return out

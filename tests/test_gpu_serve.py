@@ -60,3 +60,47 @@ def test_results_alone_equal_results_in_the_mix(dev, slots, batch):
     if batch > 1:
         assert st["max_batch"] >= 2
     srv.close()
+
+
+def test_served_backward_equals_plain_backward(dev):
+    """A backward request (forward + backward with upstream planes given on the host) gives
+    the planes and parameter gradients of Rasterizer.forward/backward, up to the order of
+    the floating-point atomic accumulation; forward requests queued with it still batch."""
+    from paper_2411_16392_gb300.render import DeviceScene, Rasterizer
+    from paper_2411_16392_gb300.serve import Server
+    sc = serving_scene(3, 100_000)
+    ds = DeviceScene.from_host(sc, dev)
+    rng = np.random.default_rng(4)
+    cam = orbit_camera(rng, res=(320, 240))
+    H, W = cam.H, cam.W
+    g_host = {"rgb": rng.normal(size=(3, H, W)).astype(np.float32),
+              "alpha": rng.normal(size=(H, W)).astype(np.float32),
+              "depth": rng.normal(size=(H, W)).astype(np.float32),
+              "normal": rng.normal(size=(3, H, W)).astype(np.float32)}
+    ras = Rasterizer(dev)
+    ref_out = {k: v.clone() for k, v in ras.forward(ds, cam).items()}
+    ref_g = {k: v.cpu().numpy() for k, v in
+             ras.backward(ds, cam, {k: torch.from_numpy(v).to(dev) for k, v in g_host.items()}).items()}
+    srv = Server(dev.index or 0, budget_bytes=16 << 30, slots=2, batch=4)
+    sid = srv.load_scene(ds)
+    others = [orbit_camera(rng) for _ in range(5)]
+    t_fwd = [srv.submit(sid, c) for c in others[:3]]
+    t_bwd = srv.submit(sid, cam, backward=True, grad_out=g_host)
+    t_fwd += [srv.submit(sid, c) for c in others[3:]]
+    n = sc.n
+    got_g = {k: np.zeros(s, np.float32) for k, s in (("mean", (n, 3)), ("quat", (n, 4)), ("scale", (n, 2)),
+                                                     ("curv", (n, 2)), ("opacity", (n,)), ("sh", (n, 48)))}
+    got_out = {k: torch.zeros_like(v) for k, v in ref_out.items()}
+    srv.wait(t_bwd, out=got_out, grads=got_g, timeout_ms=60_000)
+    for t in t_fwd:
+        srv.wait(t, timeout_ms=60_000)
+    torch.cuda.synchronize()
+    for k in ref_out:
+        assert torch.equal(got_out[k], ref_out[k]), k
+    for k in ref_g:
+        scale = max(np.abs(ref_g[k]).max(), 1e-30)
+        assert np.abs(got_g[k] - ref_g[k]).max() <= 1e-5 * scale, k
+    assert np.abs(got_g["mean"]).max() > 0
+    st = srv.stats()
+    assert st["completed"] == 6 and st["failed"] == 0
+    srv.close()

@@ -184,3 +184,28 @@ def test_batch_size_is_bounded_by_the_budget(lib):
     assert st["max_batch"] == 2 and st["max_in_flight"] == 2, st
     assert st["bytes_reserved_peak"] <= st["bytes_budget"]
     s.close()
+
+
+def test_backward_requests_return_gradients_and_run_alone(lib):
+    from paper_2411_16392_gb300._lib import QGSError
+    s = _server(budget_bytes=1 << 40, slots=1, batch=8, fake_us_per_mpix=2_000_000.0)  # ~130 ms a view
+    sid = s.load_scene(n=100)
+    first = s.submit(sid, CAM)
+    time.sleep(0.02)
+    fwd = [s.submit(sid, CAM) for _ in range(3)]
+    bwd = s.submit(sid, CAM, backward=True, grad_out={"rgb": np.ones((3, 256, 256), np.float32)})
+    fwd += [s.submit(sid, CAM) for _ in range(2)]
+    with pytest.raises(QGSError) as e:        # a forward ticket has no gradients
+        s.wait(fwd[0], grads={"mean": np.zeros((100, 3), np.float32)})
+    assert e.value.status == 1
+    grads = {k: np.full(shape, 7.0, np.float32) for k, shape in
+             (("mean", (100, 3)), ("quat", (100, 4)), ("scale", (100, 2)), ("curv", (100, 2)),
+              ("opacity", (100,)), ("sh", (100, 48)))}
+    s.wait(bwd, grads=grads)
+    assert all(np.all(v == 0) for v in grads.values())   # host executor: zero gradients
+    for t in [first] + fwd:
+        s.wait(t)
+    st = s.stats()
+    assert st["completed"] == 7 and st["failed"] == 0
+    assert st["batches"] == 3, st                          # [f], [f f f f f], [b]
+    s.close()
