@@ -31,6 +31,14 @@ What it computes, step by step, and where each step is defined in the paper
     sum_i sum_{j<i} w_i w_j (t_i - t_j)^2, summed as written; the median depth of
     Sec. 4.1, the largest t_i among blended pairs whose transmittance before them
     exceeds 0.5 (0 when none does).
+  * StopThePop ordering (render(..., order="stp"), supplementary "Details of Per-tile
+    Sorting and Per-pixel Resorting"): tile lists sorted by the depth where the ray of the
+    tile pixel closest to the projected vertex meets the paraboloid (an FP32 recipe,
+    hit_keys, shared with the kernels as a specification), then per-pixel resorting of
+    the contributing pairs in a buffer of 8 (nearest first when full, the rest nearest
+    first at the end). Readings: the ray meets the untruncated paraboloid, nearest root
+    in front of the near plane, the centre depth when it misses; ties in the buffer go to
+    the earlier list entry; the transmittance stop applies when an entry is blended.
   * Density variant (render(..., density="euclid")): the Euclidean-distance Gaussian
     that Sec. 3.2 argues against and Sec. 4.3 ablates, same sigma(theta), distance
     sqrt(rho^2 + z^2) from the vertex.
@@ -87,9 +95,65 @@ class Binning:
     tiles_x: int
     tiles_y: int
     pix_bbox: np.ndarray    # float32 [N, 4] (xmin, xmax, ymin, ymax) in pixels
+    order: str = "centre"   # "centre": key = centre depth; "hit": per-tile hit depth
+    geo: dict | None = None  # float32 mu_c, W, a, b, camera (for per-tile hit keys)
 
 
-def bin_fp32(scene, cam, emit: bool = True) -> Binning:
+def hit_keys(binning: Binning, prims: np.ndarray, tile: int) -> np.ndarray:
+    """Per-tile sort depth of StopThePop's ordering as adopted by the supplementary
+    ("Details of Per-tile Sorting and Per-pixel Resorting"): the depth where the ray of
+    the tile's pixel closest to the projected vertex meets the paraboloid, shared by all
+    pixels of the tile. Returns the float32 depths' bits [len(prims)].
+
+    Specified in FP32 with correctly rounded + - * / sqrt, each rounded, in the order
+    written (the kernels follow the same recipe):
+      uc = fx*(x/z) + cx, vc likewise (the centre mu_c, from the binning recipe);
+      px = min(max(floor(uc), 16 tx), min(16 tx + 15, W - 1)), py likewise;
+      dx = ((px + 0.5) - cx)/fx, dy likewise, d = (dx, dy, 1);
+      ex = dx*z - x, ey = dy*z - y (offset from the centre at the centre's depth);
+      b_k = W[0][k]*ex + W[1][k]*ey, d_k = (W[0][k]*dx + W[1][k]*dy) + W[2][k];
+      A = (a*d0)*d0 + (b*d1)*d1;  B' = ((a*b0)*d0 + (b*b1)*d1) - 0.5*d2;
+      C = ((a*b0)*b0 + (b*b1)*b1) - b2;  D' = B'*B' - A*C;
+      q = -(B' + sgn(B') sqrt(D')) (sgn(0) = +1), s in {C/q, q/A}, t = z + s;
+      the smallest finite t > near; the centre depth z when D' < 0 or no root qualifies.
+    The ray is taken relative to the point where it crosses the centre's depth, so the
+    quadratic's coefficients have the size of the primitive (no cancellation at the
+    camera distance)."""
+    f = np.float32
+    g = binning.geo
+    prims = np.asarray(prims, np.int64)
+    ty_, tx_ = divmod(int(tile), binning.tiles_x)
+    x, y, z = (g["muc"][k][prims] for k in range(3))
+    Wm = [[g["Wm"][r][c][prims] for c in range(3)] for r in range(3)]
+    a, b = g["a"][prims], g["b"][prims]
+    fx, fy, cx, cy, near, Wimg, Himg = (g[k] for k in ("fx", "fy", "cx", "cy", "near", "img_w", "img_h"))
+    with np.errstate(all="ignore"):
+        uc = fx * (x / z) + cx
+        vc = fy * (y / z) + cy
+        px = np.minimum(np.maximum(np.floor(uc), f(16 * tx_)), f(min(16 * tx_ + 15, Wimg - 1)))
+        py = np.minimum(np.maximum(np.floor(vc), f(16 * ty_)), f(min(16 * ty_ + 15, Himg - 1)))
+        half = f(0.5)
+        dx = ((px + half) - cx) / fx
+        dy = ((py + half) - cy) / fy
+        ex = dx * z - x
+        ey = dy * z - y
+        bk = [Wm[0][k] * ex + Wm[1][k] * ey for k in range(3)]
+        dk = [(Wm[0][k] * dx + Wm[1][k] * dy) + Wm[2][k] for k in range(3)]
+        A = (a * dk[0]) * dk[0] + (b * dk[1]) * dk[1]
+        Bh = ((a * bk[0]) * dk[0] + (b * bk[1]) * dk[1]) - half * dk[2]
+        C = ((a * bk[0]) * bk[0] + (b * bk[1]) * bk[1]) - bk[2]
+        D = Bh * Bh - A * C
+        sq = np.sqrt(np.maximum(D, f(0.0)))
+        q = -(Bh + np.where(Bh >= f(0.0), sq, -sq))
+        t1 = z + C / q
+        t2 = z + q / A
+        ok1 = np.isfinite(t1) & (t1 > near) & (D >= f(0.0))
+        ok2 = np.isfinite(t2) & (t2 > near) & (D >= f(0.0))
+        t = np.where(ok1 & ok2, np.minimum(t1, t2), np.where(ok1, t1, np.where(ok2, t2, z)))
+    return t.astype(f).view(np.uint32)
+
+
+def bin_fp32(scene, cam, emit: bool = True, order: str = "centre") -> Binning:
     """Conservative screen bound, tile rectangle and sort key of every primitive.
 
     FP32, correctly rounded + - * / sqrt only, each operation rounded separately in
@@ -222,8 +286,15 @@ def bin_fp32(scene, cam, emit: bool = True) -> Binning:
         zbits = muc[2].astype(f).view(np.uint32).copy()
 
     pix_bbox = np.stack([xmin, xmax, ymin, ymax], 1).astype(np.float32)
+    geo = None
+    if order == "hit":
+        geo = dict(muc=[c.astype(f) for c in muc], Wm=Wm, a=a, b=b, fx=fx, fy=fy, cx=cx, cy=cy, near=near,
+                   img_w=cam.W, img_h=cam.H)
+    elif order != "centre":
+        raise ValueError(order)
+    bn = Binning(vis, zbits, rect, count, None, None, None, TX, TY, pix_bbox, order, geo)
     if not emit:
-        return Binning(vis, zbits, rect, count, None, None, None, TX, TY, pix_bbox)
+        return bn
     # instances in primitive order, tiles row-major inside each rectangle
     I = int(count.sum())
     keys = np.empty(I, np.uint64)
@@ -232,20 +303,24 @@ def bin_fp32(scene, cam, emit: bool = True) -> Binning:
     for i in np.nonzero(count)[0]:
         x0, x1, y0, y1 = rect[i]
         ty, tx = np.meshgrid(np.arange(y0, y1 + 1), np.arange(x0, x1 + 1), indexing="ij")
-        tiles = (ty * TX + tx).reshape(-1).astype(np.uint64)
+        tiles = (ty * TX + tx).reshape(-1)
         c = tiles.size
-        keys[pos:pos + c] = (tiles << np.uint64(32)) | np.uint64(zbits[i])
+        if order == "hit":
+            low = np.array([hit_keys(bn, np.array([i]), t)[0] for t in tiles], np.uint64)
+        else:
+            low = np.uint64(zbits[i])
+        keys[pos:pos + c] = (tiles.astype(np.uint64) << np.uint64(32)) | low
         vals[pos:pos + c] = i
         pos += c
-    order = np.argsort(keys, kind="stable")
-    keys = keys[order]
-    vals = vals[order]
+    srt = np.argsort(keys, kind="stable")
+    keys = keys[srt]
+    vals = vals[srt]
     tiles_sorted = (keys >> np.uint64(32)).astype(np.int64)
     ntiles = TX * TY
     starts = np.searchsorted(tiles_sorted, np.arange(ntiles), side="left")
     ends = np.searchsorted(tiles_sorted, np.arange(ntiles), side="right")
     ranges = np.stack([starts, ends], 1).astype(np.int64)
-    return Binning(vis, zbits, rect, count, keys, vals, ranges, TX, TY, pix_bbox)
+    return Binning(vis, zbits, rect, count, keys, vals, ranges, TX, TY, pix_bbox, order, geo)
 
 
 def tile_list(binning: Binning, tile: int) -> np.ndarray:
@@ -254,7 +329,8 @@ def tile_list(binning: Binning, tile: int) -> np.ndarray:
     ty, tx = divmod(int(tile), binning.tiles_x)
     r = binning.rect
     sel = np.nonzero((binning.count > 0) & (r[:, 0] <= tx) & (tx <= r[:, 1]) & (r[:, 2] <= ty) & (ty <= r[:, 3]))[0]
-    order = np.lexsort((sel, binning.zbits[sel]))
+    depth = hit_keys(binning, sel, tile) if binning.order == "hit" else binning.zbits[sel]
+    order = np.lexsort((sel, depth))
     return sel[order].astype(np.uint32)
 
 
@@ -630,6 +706,121 @@ def _composite(prm, cam, idx, px, py, chunk=4096, density="geodesic", extras=Fal
     return res
 
 
+RESORT = 8   # per-pixel resort buffer length of the supplementary's resorting
+
+
+def _composite_resort(prm, cam, idx, px, py, density="geodesic", extras=False, buf=RESORT):
+    """Front-to-back blending with StopThePop's per-pixel local resorting as adopted by
+    the supplementary ("Details of Per-tile Sorting and Per-pixel Resorting"): each pixel
+    walks its tile's list and puts every contributing pair (alpha >= 1/255) into a buffer
+    of `buf` entries; whenever the buffer is full, the entry with the smallest hit depth
+    (ties: earlier in the list) is blended and removed; at the end of the list the rest
+    is blended nearest first. The transmittance rule is unchanged: a pixel stops before
+    a pair that would take T below 1e-4. Same outputs as _composite; the order decision
+    (smallest depth in the buffer) adds its relative gap to the decision margins."""
+    P = px.shape[0]
+    L = idx.shape[0]
+    dev = dict(dtype=F64)
+    pe = _eval_pairs(prm, cam, idx, px, py, density)
+    al, valid, tt = pe["alpha"], pe["valid"], pe["t"]
+    rows = torch.arange(P)
+    T = torch.ones(P, **dev)
+    alive = torch.ones(P, dtype=torch.bool)
+    rgb = torch.zeros(P, 3, **dev)
+    depth = torch.zeros(P, **dev)
+    normal = torch.zeros(P, 3, **dev)
+    curv = torch.zeros(P, **dev)
+    curv_scale = torch.zeros(P, **dev)
+    median = torch.zeros(P, **dev)
+    m_median = torch.full((P,), np.inf, **dev)
+    margin = torch.full((P,), np.inf, **dev)
+    cond = torch.full((P,), np.inf, **dev)
+    n_contrib = torch.zeros(P, dtype=torch.int64)
+    stop_at = torch.full((P,), L - 1, dtype=torch.int64)    # last list entry each pixel evaluated
+    bt = torch.full((P, buf), np.inf, **dev)                 # buffered depths (decisions only)
+    bj = torch.full((P, buf), -1, dtype=torch.int64)         # buffered list positions
+    w_cols, t_cols = [], []
+    state = dict(T=T, alive=alive, rgb=rgb, depth=depth, normal=normal, curv=curv, curv_scale=curv_scale,
+                 median=median, m_median=m_median, margin=margin, cond=cond, n_contrib=n_contrib)
+
+    def pop(mask, j_now):
+        st = state
+        big = torch.iinfo(torch.int64).max
+        mn = bt.min(1).values
+        cand = (bt == mn[:, None]) & (bj >= 0)
+        jsel = torch.where(cand, bj, torch.full_like(bj, big)).min(1).values
+        sel = mask & (jsel != big)
+        if not bool(sel.any()):
+            return
+        slot = (bj == jsel[:, None]).long().argmax(1)
+        if buf > 1:
+            srt = bt.sort(1).values
+            gap = torch.where(torch.isfinite(srt[:, 1]), (srt[:, 1] - srt[:, 0]).abs() / srt[:, 0].abs(),
+                              torch.full_like(mn, np.inf))
+        else:
+            gap = torch.full_like(mn, np.inf)
+        st["margin"] = torch.minimum(st["margin"], torch.where(sel, gap, torch.full_like(gap, np.inf)))
+        js = torch.where(sel, jsel, torch.zeros_like(jsel))
+        a = al[rows, js]
+        Tn = st["T"] * (1.0 - a)
+        m_T = ((Tn - T_MIN).abs() / T_MIN).detach()
+        st["margin"] = torch.minimum(st["margin"], torch.where(sel, m_T, torch.full_like(m_T, np.inf)))
+        stop = sel & (Tn < T_MIN)
+        keep = sel & ~stop
+        w = torch.where(keep, a * st["T"], torch.zeros_like(a))
+        t_sel = tt[rows, js]
+        st["rgb"] = st["rgb"] + w[:, None] * pe["rgb"][js]
+        st["depth"] = st["depth"] + w * t_sel
+        st["normal"] = st["normal"] + w[:, None] * pe["normal"][rows, js]
+        st["cond"] = torch.minimum(st["cond"], torch.where(keep, pe["cond"][rows, js],
+                                                           torch.full_like(m_T, np.inf)))
+        if extras:
+            K = pe["curvature"][rows, js]
+            st["curv"] = st["curv"] + w * K
+            st["curv_scale"] = st["curv_scale"] + (w * K.abs()).detach()
+            med_ok = keep & (st["T"] > MEDIAN_T)
+            st["median"] = torch.maximum(st["median"], torch.where(med_ok, t_sel, torch.zeros_like(t_sel)).detach())
+            mm_ = torch.where(keep, (st["T"] - MEDIAN_T).abs().detach() / MEDIAN_T, torch.full_like(m_T, np.inf))
+            st["m_median"] = torch.minimum(st["m_median"], mm_)
+            w_cols.append(w[:, None])
+            t_cols.append(torch.where(keep, t_sel, torch.zeros_like(t_sel))[:, None])
+        st["T"] = torch.where(keep, Tn, st["T"])
+        st["n_contrib"] = st["n_contrib"] + keep.long()
+        st["alive"] = st["alive"] & ~stop
+        stop_at[stop] = j_now
+        bt[rows[sel], slot[sel]] = np.inf
+        bj[rows[sel], slot[sel]] = -1
+
+    for j in range(L):
+        m = state["alive"] & valid[:, j]
+        if bool(m.any()):
+            slot = (bj == -1).long().argmax(1)
+            r = rows[m]
+            bt[r, slot[m]] = tt[m, j].detach()
+            bj[r, slot[m]] = j
+            full = m & ((bj >= 0).sum(1) == buf)
+            if bool(full.any()):
+                pop(full, j)
+    for _ in range(buf):
+        pending = state["alive"] & ((bj >= 0).sum(1) > 0)
+        if not bool(pending.any()):
+            break
+        pop(pending, L - 1)
+    # decision margins of every pair each pixel evaluated
+    seen = torch.arange(L)[None, :] <= stop_at[:, None]
+    pm = torch.where(seen, pe["margin"], torch.full_like(pe["margin"], np.inf)).min(1).values
+    st = state
+    res = dict(rgb=st["rgb"], alpha=1.0 - st["T"], depth=st["depth"], normal=st["normal"], T_final=st["T"],
+               n_eval=stop_at + 1, n_contrib=st["n_contrib"], margin=torch.minimum(st["margin"], pm),
+               cond=st["cond"],
+               list_cond=torch.where(valid, pe["cond"], torch.full_like(pe["cond"], np.inf)).min(0).values)
+    if extras:
+        dist = _distortion(torch.cat(w_cols, 1), torch.cat(t_cols, 1)) if w_cols else torch.zeros(P, **dev)
+        res.update(curvature=st["curv"], curvature_scale=st["curv_scale"], distortion=dist,
+                   median_depth=st["median"], margin_median=st["m_median"])
+    return res
+
+
 # =========================================================================== images
 OUT_KEYS = ("rgb", "alpha", "depth", "normal")
 EXTRA_KEYS = ("curvature", "distortion", "median_depth")
@@ -643,7 +834,7 @@ def _tile_pixels(cam, tile, TX):
 
 
 def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=None, density="geodesic",
-           extras=False):
+           extras=False, order="centre"):
     """Render the full image (or the listed tiles). Returns a dict of numpy arrays:
     rgb [3,H,W], alpha [H,W], depth [H,W], normal [3,H,W], margin [H,W], n_eval [H,W],
     n_contrib [H,W], T_final [H,W]; with `extras` also curvature, distortion,
@@ -652,9 +843,12 @@ def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=N
     missing ones zero; curvature and distortion may be included, the median depth has
     none), also returns
     `grads`: the exact FP64 gradient of sum(grad * output) with respect to every scene
-    parameter. density: "geodesic" (the paper's) or "euclid"."""
+    parameter. density: "geodesic" (the paper's) or "euclid". order: "centre" (tile lists
+    by centre depth) or "stp" (StopThePop: per-tile hit depth, then per-pixel resorting
+    in a buffer of RESORT entries)."""
     if binning is None:
-        binning = bin_fp32(scene, cam)
+        binning = bin_fp32(scene, cam, order="hit" if order == "stp" else "centre")
+    comp = _composite_resort if order == "stp" else _composite
     want_grad = grad_images is not None
     prm = Params(scene, requires_grad=want_grad)
     c64 = CamF64(cam)
@@ -686,7 +880,7 @@ def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=N
         px = torch.tensor(xs, dtype=F64)
         py = torch.tensor(ys, dtype=F64)
         with torch.set_grad_enabled(want_grad):
-            r = _composite(prm, c64, idx, px, py, density=density, extras=extras)
+            r = comp(prm, c64, idx, px, py, density=density, extras=extras)
             if want_grad:
                 loss = torch.zeros((), dtype=F64)
                 for k in ("rgb", "normal"):
@@ -723,11 +917,12 @@ def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=N
     return out
 
 
-def render_pixels(scene, cam, pixels, binning: Binning | None = None, density="geodesic", extras=False):
+def render_pixels(scene, cam, pixels, binning: Binning | None = None, density="geodesic", extras=False,
+                  order="centre"):
     """Render individual pixels [(x, y), ...] one at a time (same lists and order as
     the full image). Returns dict of arrays indexed like `pixels`."""
     if binning is None:
-        binning = bin_fp32(scene, cam)
+        binning = bin_fp32(scene, cam, order="hit" if order == "stp" else "centre")
     prm = Params(scene)
     c64 = CamF64(cam)
     TX = binning.tiles_x
@@ -747,8 +942,9 @@ def render_pixels(scene, cam, pixels, binning: Binning | None = None, density="g
             lst = lists[tile]
         idx = torch.from_numpy(lst.astype(np.int64))
         with torch.no_grad():
-            r = _composite(prm, c64, idx, torch.tensor([float(x)], dtype=F64),
-                           torch.tensor([float(y)], dtype=F64), density=density, extras=extras)
+            comp = _composite_resort if order == "stp" else _composite
+            r = comp(prm, c64, idx, torch.tensor([float(x)], dtype=F64),
+                     torch.tensor([float(y)], dtype=F64), density=density, extras=extras)
         for k in res:
             res[k].append(r[k][0].numpy())
     return {k: np.array(v) for k, v in res.items()}
