@@ -395,6 +395,150 @@ __global__ void __launch_bounds__(BLOCK, 3)
 
 namespace {
 
+// Per-pixel upstream gradients (and the forward's residue) of the backward.
+struct PixGrads {
+  float gR, gG, gB, gA, gD, gNx, gNy, gNz;
+  float gK, tref, g_tau, g_tau2;  // extra channels
+  float Tfin;
+};
+
+// The pixel's upstream gradients; with EXTRA, the distortion's per-pixel constants from
+// the forward's residue (c, A1, A2): dL/dA0 = g A2 joins the alpha gradient, tau and tau^2
+// carry -2 g A1 and g A0 (A0 = 1 - T_final).
+template <bool EXTRA>
+__device__ __forceinline__ PixGrads load_pix_grads(bool inside, size_t pix, size_t P, float Tfin,
+                                                   const float* __restrict__ g_rgb, const float* __restrict__ g_alpha,
+                                                   const float* __restrict__ g_depth,
+                                                   const float* __restrict__ g_normal, const ExtraGrads& eg) {
+  PixGrads pg{};
+  pg.Tfin = Tfin;
+  if (inside) {
+    if (g_rgb) { pg.gR = g_rgb[pix]; pg.gG = g_rgb[P + pix]; pg.gB = g_rgb[2 * P + pix]; }
+    if (g_alpha) pg.gA = g_alpha[pix];
+    if (g_depth) pg.gD = g_depth[pix];
+    if (g_normal) { pg.gNx = g_normal[pix]; pg.gNy = g_normal[P + pix]; pg.gNz = g_normal[2 * P + pix]; }
+    if constexpr (EXTRA) {
+      if (eg.g_curvature) pg.gK = eg.g_curvature[pix];
+      const float gDist = eg.g_distortion ? eg.g_distortion[pix] : 0.f;
+      if (gDist != 0.f) {
+        pg.tref = eg.resid[pix];
+        const float A1 = eg.resid[P + pix], A2 = eg.resid[2 * P + pix];
+        pg.gA += gDist * A2;
+        pg.g_tau = -2.f * gDist * A1;
+        pg.g_tau2 = gDist * (1.f - Tfin);
+      }
+    }
+  }
+  return pg;
+}
+
+// Gradient record of one blended pair (entries 0..NGRAD-1 of v): the back-to-front (or,
+// FWD_ORDER, front-to-back) dX/d(alpha) of the supplementary, then the chain rule through
+// the alpha clamp, G, F(u), E, the normal and the implicit root. T is the transmittance
+// before the pair; S_ref is the sum of w_j (g . X_j) over the pixel's later blended
+// pairs, or (FWD_ORDER) over all of them, S_prefix then being that sum over the pairs up
+// to and excluding this one. Returns the pair's own term w (g . X).
+template <bool EUCLID, bool EXTRA, bool FWD_ORDER>
+__device__ __forceinline__ float pair_grad(const PrimState& P, const Hit& h, float oG, float al, float T, float xn,
+                                           float yn, const RasterParams& rp, const PixGrads& pg, float S_ref,
+                                           float S_prefix, float v[32]) {
+  const float4 f2 = P.f[2], f3 = P.f[3], f4 = P.f[4], f5 = P.f[5], f6 = P.f[6], f7 = P.f[7];
+  const float a = f5.y, b = f5.z, o = f5.w;
+  const float onem = 1.f - al;
+  const float w = al * T;
+  const float W00 = f3.x, W10 = f3.y, W01 = f3.z, W11 = f3.w, W02 = f4.x, W12 = f4.y, W20 = f6.z,
+              W21 = f6.w, W22 = f7.x;
+  const float x = h.x, y = h.y;
+  const float nlx = 2.f * a * x, nly = 2.f * b * y;
+  const float ncx = fmaf(W00, nlx, fmaf(W01, nly, -W02));
+  const float ncy = fmaf(W10, nlx, fmaf(W11, nly, -W12));
+  const float ncz = fmaf(W20, nlx, fmaf(W21, nly, -W22));
+  const float inn = rsqrtf(fmaf(ncx, ncx, fmaf(ncy, ncy, ncz * ncz)));
+  const float sg_ = fmaf(ncx, xn, fmaf(ncy, yn, ncz)) > 0.f ? -1.f : 1.f;
+  const float hx = ncx * inn, hy = ncy * inn, hz = ncz * inn;  // unsigned unit normal
+  const float nox = sg_ * hx, noy = sg_ * hy, noz = sg_ * hz;
+  const float t = f2.w + h.s;
+  float gX = pg.gR * f7.y + pg.gG * f7.z + pg.gB * f7.w + pg.gD * t + pg.gNx * nox + pg.gNy * noy + pg.gNz * noz;
+  float d_t = w * pg.gD;
+  Curv kv{};
+  if constexpr (EXTRA) {
+    kv = curvature_grad(a, b, x, y);
+    const float tau = t - pg.tref;
+    gX += pg.gK * kv.K + tau * fmaf(pg.g_tau2, tau, pg.g_tau);
+    d_t += w * fmaf(2.f * pg.g_tau2, tau, pg.g_tau);
+  }
+  const float wgx = w * gX;
+  const float after = FWD_ORDER ? S_ref - (S_prefix + wgx) : S_ref;  // sum of w_j g.X_j, j after i
+  const float dal = T * gX - (after - pg.gA * pg.Tfin) / onem;
+  v[17] = w * pg.gR;
+  v[18] = w * pg.gG;
+  v[19] = w * pg.gB;
+  // alpha = min(alpha_max, o G)
+  float dG = 0.f;
+  v[16] = 0.f;
+  if (oG < rp.alpha_max) {
+    v[16] = dal * h.G;
+    dG = dal * o;
+  }
+  const float dQ = -0.5f * h.G * dG;
+  const float dE = dQ * h.F2;
+  v[14] = dE * x * x;
+  v[15] = dE * y * y;
+  float gx = dE * 2.f * f6.x * x, gy = dE * 2.f * f6.y * y;
+  float da = 0.f, db = 0.f;
+  if constexpr (EXTRA) {
+    const float dK = w * pg.gK;
+    da += dK * kv.dKda;
+    db += dK * kv.dKdb;
+    gx += dK * kv.dKdx;
+    gy += dK * kv.dKdy;
+  }
+  if (h.rho2 > 0.f) {
+    const float irho = rsqrtf(h.rho2);
+    const float du = dQ * h.E * f2_prime<EUCLID>(h.u, h.F2);
+    const float ur = h.u * irho * irho;
+    gx += du * (4.f * a * x * irho - ur * x);
+    gy += du * (4.f * b * y * irho - ur * y);
+    da += du * 2.f * x * x * irho;
+    db += du * 2.f * y * y * irho;
+  }
+  // normal: n_out = sg * n_c / |n_c|, n_c = W n_l
+  const float dnx = w * pg.gNx, dny = w * pg.gNy, dnz = w * pg.gNz;
+  const float dd = hx * dnx + hy * dny + hz * dnz;
+  const float sc_ = sg_ * inn;
+  const float dcx = sc_ * (dnx - hx * dd), dcy = sc_ * (dny - hy * dd), dcz = sc_ * (dnz - hz * dd);
+  const float gmx = W00 * dcx + W10 * dcy + W20 * dcz;
+  const float gmy = W01 * dcx + W11 * dcy + W21 * dcz;
+  const float gmz = W02 * dcx + W12 * dcy + W22 * dcz;
+  gx += 2.f * a * gmx;
+  gy += 2.f * b * gmy;
+  da += 2.f * x * gmx;
+  db += 2.f * y * gmy;
+  // the root moves with the parameters: t(theta) from f(p_hat(t)) = 0
+  const float den = nlx * h.dx + nly * h.dy - h.dz;
+  const float kk = den != 0.f ? (gx * h.dx + gy * h.dy + d_t) / den : 0.f;
+  const float hhx = gx - kk * nlx, hhy = gy - kk * nly, hhz = kk;
+  da -= kk * x * x;
+  db -= kk * y * y;
+  v[12] = da;
+  v[13] = db;
+  v[9] = hhx;
+  v[10] = hhy;
+  v[11] = hhz;
+  // P = p_hat h^T + gamma n_l^T, p_hat = (x, y, zs), n_l = (nlx, nly, -1)
+  const float pz = h.zs;
+  v[0] = x * hhx + gmx * nlx;
+  v[1] = x * hhy + gmx * nly;
+  v[2] = x * hhz - gmx;
+  v[3] = y * hhx + gmy * nlx;
+  v[4] = y * hhy + gmy * nly;
+  v[5] = y * hhz - gmy;
+  v[6] = pz * hhx + gmz * nlx;
+  v[7] = pz * hhy + gmz * nly;
+  v[8] = pz * hhz - gmz;
+  return wgx;
+}
+
 // Butterfly reduce-scatter of 32 per-lane values across the warp: afterwards lane l
 // holds the warp-wide sum of component l.
 __device__ __forceinline__ float warp_transpose_sum(float v[32]) {
@@ -443,29 +587,9 @@ __global__ void __launch_bounds__(BLOCK, 3)
   const float xn = (X - rp.cx) * rp.inv_fx, yn = (Y - rp.cy) * rp.inv_fy;
   const size_t P = (size_t)rp.W * rp.H, pix = inside ? (size_t)py * rp.W + px : 0;
   float T = inside ? T_final[pix] : 1.f;
-  const float Tfin = T;
   const uint32_t last = inside ? n_contrib[pix] : 0u;
-  float gR = 0.f, gG = 0.f, gB = 0.f, gA = 0.f, gD = 0.f, gNx = 0.f, gNy = 0.f, gNz = 0.f;
-  if (inside) {
-    if (g_rgb) { gR = g_rgb[pix]; gG = g_rgb[P + pix]; gB = g_rgb[2 * P + pix]; }
-    if (g_alpha) gA = g_alpha[pix];
-    if (g_depth) gD = g_depth[pix];
-    if (g_normal) { gNx = g_normal[pix]; gNy = g_normal[P + pix]; gNz = g_normal[2 * P + pix]; }
-  }
-  float gK = 0.f, tref = 0.f, g_tau = 0.f, g_tau2 = 0.f;
-  if constexpr (EXTRA) {
-    if (inside) {
-      if (eg.g_curvature) gK = eg.g_curvature[pix];
-      const float gDist = eg.g_distortion ? eg.g_distortion[pix] : 0.f;
-      if (gDist != 0.f) {
-        tref = eg.resid[pix];
-        const float A1 = eg.resid[P + pix], A2 = eg.resid[2 * P + pix];
-        gA += gDist * A2;
-        g_tau = -2.f * gDist * A1;
-        g_tau2 = gDist * (1.f - T);
-      }
-    }
-  }
+  const PixGrads pg =
+      load_pix_grads<EXTRA>(inside, pix, P, T, g_rgb, g_alpha, g_depth, g_normal, eg);
   if (threadIdx.x == 0) smax = 0;
   __syncthreads();
   {
@@ -497,106 +621,13 @@ __global__ void __launch_bounds__(BLOCK, 3)
         bool gz = false;
         ++n_pairs;
         if (eval_pair<EUCLID>(sm[j], X, Y, rp, h, gz, isect)) {
-          const float4 f2 = sm[j].f[2], f3 = sm[j].f[3], f4 = sm[j].f[4], f5 = sm[j].f[5], f6 = sm[j].f[6],
-                       f7 = sm[j].f[7];
-          const float a = f5.y, b = f5.z, o = f5.w;
-          const float oG = __fmul_rn(o, h.G);
+          const float oG = __fmul_rn(sm[j].f[5].w, h.G);
           const float al = fminf(rp.alpha_max, oG);
           if (al >= rp.alpha_min) {
             contrib = true;
             ++n_contrib_pairs;
-            const float onem = 1.f - al;
-            T = T / onem;  // T_i from T_{i+1}
-            const float w = al * T;
-            const float W00 = f3.x, W10 = f3.y, W01 = f3.z, W11 = f3.w, W02 = f4.x, W12 = f4.y, W20 = f6.z,
-                        W21 = f6.w, W22 = f7.x;
-            const float x = h.x, y = h.y;
-            const float nlx = 2.f * a * x, nly = 2.f * b * y;
-            const float ncx = fmaf(W00, nlx, fmaf(W01, nly, -W02));
-            const float ncy = fmaf(W10, nlx, fmaf(W11, nly, -W12));
-            const float ncz = fmaf(W20, nlx, fmaf(W21, nly, -W22));
-            const float inn = rsqrtf(fmaf(ncx, ncx, fmaf(ncy, ncy, ncz * ncz)));
-            const float sg_ = fmaf(ncx, xn, fmaf(ncy, yn, ncz)) > 0.f ? -1.f : 1.f;
-            const float hx = ncx * inn, hy = ncy * inn, hz = ncz * inn;  // unsigned unit normal
-            const float nox = sg_ * hx, noy = sg_ * hy, noz = sg_ * hz;
-            const float t = f2.w + h.s;
-            float gX = gR * f7.y + gG * f7.z + gB * f7.w + gD * t + gNx * nox + gNy * noy + gNz * noz;
-            float d_t = w * gD;
-            Curv kv{};
-            if constexpr (EXTRA) {
-              kv = curvature_grad(a, b, x, y);
-              const float tau = t - tref;
-              gX += gK * kv.K + tau * fmaf(g_tau2, tau, g_tau);
-              d_t += w * fmaf(2.f * g_tau2, tau, g_tau);
-            }
-            const float dal = T * gX - (Sdot - gA * Tfin) / onem;
-            Sdot = fmaf(w, gX, Sdot);
-            v[17] = w * gR;
-            v[18] = w * gG;
-            v[19] = w * gB;
-            // alpha = min(alpha_max, o G)
-            float dG = 0.f;
-            v[16] = 0.f;
-            if (oG < rp.alpha_max) {
-              v[16] = dal * h.G;
-              dG = dal * o;
-            }
-            const float dQ = -0.5f * h.G * dG;
-            const float dE = dQ * h.F2;
-            v[14] = dE * x * x;
-            v[15] = dE * y * y;
-            float gx = dE * 2.f * f6.x * x, gy = dE * 2.f * f6.y * y;
-            float da = 0.f, db = 0.f;
-            if constexpr (EXTRA) {
-              const float dK = w * gK;
-              da += dK * kv.dKda;
-              db += dK * kv.dKdb;
-              gx += dK * kv.dKdx;
-              gy += dK * kv.dKdy;
-            }
-            if (h.rho2 > 0.f) {
-              const float irho = rsqrtf(h.rho2);
-              const float du = dQ * h.E * f2_prime<EUCLID>(h.u, h.F2);
-              const float ur = h.u * irho * irho;
-              gx += du * (4.f * a * x * irho - ur * x);
-              gy += du * (4.f * b * y * irho - ur * y);
-              da += du * 2.f * x * x * irho;
-              db += du * 2.f * y * y * irho;
-            }
-            // normal: n_out = sg * n_c / |n_c|, n_c = W n_l
-            const float dnx = w * gNx, dny = w * gNy, dnz = w * gNz;
-            const float dd = hx * dnx + hy * dny + hz * dnz;
-            const float sc_ = sg_ * inn;
-            const float dcx = sc_ * (dnx - hx * dd), dcy = sc_ * (dny - hy * dd), dcz = sc_ * (dnz - hz * dd);
-            const float gmx = W00 * dcx + W10 * dcy + W20 * dcz;
-            const float gmy = W01 * dcx + W11 * dcy + W21 * dcz;
-            const float gmz = W02 * dcx + W12 * dcy + W22 * dcz;
-            gx += 2.f * a * gmx;
-            gy += 2.f * b * gmy;
-            da += 2.f * x * gmx;
-            db += 2.f * y * gmy;
-            // the root moves with the parameters: t(theta) from f(p_hat(t)) = 0
-            const float den = nlx * h.dx + nly * h.dy - h.dz;
-            const float kk = den != 0.f ? (gx * h.dx + gy * h.dy + d_t) / den : 0.f;
-            const float hhx = gx - kk * nlx, hhy = gy - kk * nly, hhz = kk;
-            da -= kk * x * x;
-            db -= kk * y * y;
-            v[12] = da;
-            v[13] = db;
-            v[9] = hhx;
-            v[10] = hhy;
-            v[11] = hhz;
-            // P = p_hat h^T + gamma n_l^T, p_hat = (x, y, zs), n_l = (nlx, nly, -1)
-            const float pz = h.zs;
-            v[0] = x * hhx + gmx * nlx;
-            v[1] = x * hhy + gmx * nly;
-            v[2] = x * hhz - gmx;
-            v[3] = y * hhx + gmy * nlx;
-            v[4] = y * hhy + gmy * nly;
-            v[5] = y * hhz - gmy;
-            v[6] = pz * hhx + gmz * nlx;
-            v[7] = pz * hhy + gmz * nly;
-            v[8] = pz * hhz - gmz;
+            T = T / (1.f - al);  // T_i from T_{i+1}
+            Sdot += pair_grad<EUCLID, EXTRA, false>(sm[j], h, oG, al, T, xn, yn, rp, pg, Sdot, 0.f, v);
           }
         }
       }
