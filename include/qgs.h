@@ -111,7 +111,7 @@ typedef struct {
 /* Blending constants and pipeline options. qgs_config_default() gives the values the
  * oracle and the tests use: alpha_max 0.99, alpha_min 1/255, T_min 1e-4,
  * grazing_eps 1e-5 (roots whose discriminant D satisfies |D| <= grazing_eps * B^2 are
- * re-solved in FP64), sort_mode 0, density 0. */
+ * re-solved in FP64), sort_mode 0, density 0, order 0. */
 typedef struct {
   float alpha_max;
   float alpha_min;
@@ -124,6 +124,12 @@ typedef struct {
   int32_t density;     /* 0: geodesic Gaussian (the paper's, Sec. 3.2); 1: Euclidean-distance
                           Gaussian, l = sqrt(rho^2 + z^2) from the vertex with the same
                           sigma(theta) (the "w/ Euclid" variant of Sec. 4.3) */
+  int32_t order;       /* 0: tile lists by centre depth; 1: StopThePop ordering
+                          (supplementary, per-tile sorting and per-pixel resorting): lists
+                          sorted by each primitive's depth on the tile pixel ray closest to
+                          its projected vertex, then per-pixel resorting in a buffer of 8
+                          entries, with a front-to-back backward. sort_mode is ignored;
+                          render_forward_batch refuses it (EINVAL). */
 } qgs_config;
 
 /* Counters of the last render_forward / render_backward. Pair counters classify the

@@ -707,6 +707,10 @@ def _composite(prm, cam, idx, px, py, chunk=4096, density="geodesic", extras=Fal
 
 
 RESORT = 8   # per-pixel resort buffer length of the supplementary's resorting
+# The resort decision compares two hit depths t = z + s that an FP32 implementation forms
+# to about one ulp (6e-8 relative); its margin is the relative gap scaled so that a gap
+# of 1e-6 (16 ulp) meets the common 1e-5 margin threshold.
+ORDER_GAP_SCALE = 10.0
 
 
 def _composite_resort(prm, cam, idx, px, py, density="geodesic", extras=False, buf=RESORT):
@@ -755,7 +759,8 @@ def _composite_resort(prm, cam, idx, px, py, density="geodesic", extras=False, b
         slot = (bj == jsel[:, None]).long().argmax(1)
         if buf > 1:
             srt = bt.sort(1).values
-            gap = torch.where(torch.isfinite(srt[:, 1]), (srt[:, 1] - srt[:, 0]).abs() / srt[:, 0].abs(),
+            gap = torch.where(torch.isfinite(srt[:, 1]),
+                              ORDER_GAP_SCALE * (srt[:, 1] - srt[:, 0]).abs() / srt[:, 0].abs(),
                               torch.full_like(mn, np.inf))
         else:
             gap = torch.full_like(mn, np.inf)

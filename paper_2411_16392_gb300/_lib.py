@@ -44,7 +44,8 @@ class qgs_scene_grad(C.Structure):
 
 class qgs_config(C.Structure):
     _fields_ = [("alpha_max", C.c_float), ("alpha_min", C.c_float), ("T_min", C.c_float),
-                ("grazing_eps", C.c_float), ("sort_mode", C.c_int32), ("density", C.c_int32)]
+                ("grazing_eps", C.c_float), ("sort_mode", C.c_int32), ("density", C.c_int32),
+                ("order", C.c_int32)]
 
 
 class qgs_frame_stats(C.Structure):

@@ -278,6 +278,8 @@ struct qgs_ctx {
   int id_stride = 1;
   const void* sorted_keys = nullptr;
   cudaStream_t last_stream = nullptr;
+  DevBuf<float> xres;             // StopThePop order: the forward's outputs for its backward
+  bool stp = false;               // the last forward used the StopThePop order
   DevBuf<uint32_t> vpos;          // visibility flags, then their exclusive scan
   DevBuf<PrimState> dstate;       // projected state of the visible primitives in depth order
   const PrimState* raster_state = nullptr;  // state the sorted ids index (dstate or state)
@@ -387,6 +389,7 @@ void qgs_config_default(qgs_config* cfg) {
   cfg->grazing_eps = 1e-5f;
   cfg->sort_mode = 0;
   cfg->density = 0;
+  cfg->order = 0;
 }
 
 qgs_status qgs_create(qgs_ctx** out, const qgs_config* cfg, int32_t device) {
@@ -398,7 +401,7 @@ qgs_status qgs_create(qgs_ctx** out, const qgs_config* cfg, int32_t device) {
   if (cfg) {
     if (!(cfg->alpha_max > 0 && cfg->alpha_max < 1 && cfg->alpha_min >= 0 && cfg->alpha_min < cfg->alpha_max &&
           cfg->T_min > 0 && cfg->T_min < 1 && cfg->grazing_eps >= 0 && (cfg->sort_mode == 0 || cfg->sort_mode == 1) &&
-          (cfg->density == 0 || cfg->density == 1))) {
+          (cfg->density == 0 || cfg->density == 1) && (cfg->order == 0 || cfg->order == 1))) {
       delete c;
       return QGS_EINVAL;
     }
@@ -435,6 +438,7 @@ void qgs_destroy(qgs_ctx* c) {
   c->vdesc.release();
   c->resid.release();
   c->vpos.release();
+  c->xres.release();
   c->dstate.release();
   if (c->h_vdesc) cudaFreeHost(c->h_vdesc);
   if (c->vdesc_done) cudaEventDestroy(c->vdesc_done);
@@ -466,7 +470,8 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   make_params(ctx, cam, cp, rp);
   const int64_t ntiles = (int64_t)cp.tiles_x * cp.tiles_y;
   const int64_t P = (int64_t)cam->W * cam->H;
-  const int sm = ctx->cfg.sort_mode;
+  const bool stp = ctx->cfg.order == 1;
+  const int sm = stp ? 1 : ctx->cfg.sort_mode;  // the StopThePop keys take the 64-bit key path
 
   const size_t n1 = (size_t)(N > 0 ? N : 1);
   QGS_CU(ctx->state.reserve(n1), "alloc state");
@@ -488,6 +493,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   QGS_CU(ctx->n_contrib.reserve((size_t)P), "alloc n_contrib");
   const bool extra = out->curvature || out->distortion || out->median_depth;
   if (extra) QGS_CU(ctx->resid.reserve((size_t)P * 3), "alloc residue");
+  if (stp) QGS_CU(ctx->xres.reserve((size_t)P * 8), "alloc output residue");
   QGS_CU(ctx->hist.reserve(radix_hist_elems((int64_t)n1)), "alloc hist");
   QGS_CU(ctx->scan_tmp.reserve(scan_tmp_elems((int64_t)radix_hist_elems((int64_t)n1) + (int64_t)n1)), "alloc scan");
   SortTemp tmp;
@@ -602,8 +608,12 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
     ctx->packed32 = false;
     ctx->rank_bits = 32;
     if (N > 0 && I > 0) {
-      k_emit<<<nblk(N), 256, 0, st>>>(N, nullptr, ctx->count.p, ctx->rect.p, ctx->offs.p, ctx->zkey.p, cp.tiles_x,
-                                      ctx->inst.p, ctx->vals.p);
+      if (stp)
+        k_emit_hit<<<nblk(N), 256, 0, st>>>(N, sv, cp, ctx->count.p, ctx->rect.p, ctx->offs.p, ctx->inst.p,
+                                            ctx->vals.p);
+      else
+        k_emit<<<nblk(N), 256, 0, st>>>(N, nullptr, ctx->count.p, ctx->rect.p, ctx->offs.p, ctx->zkey.p, cp.tiles_x,
+                                        ctx->inst.p, ctx->vals.p);
       ++launch_counter();
       QGS_CU(cudaGetLastError(), "emit");
       mark(ctx, 4, st);
@@ -647,10 +657,17 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   QGS_CU(cudaMemsetAsync(ctx->stats.p, 0, sizeof(RasterStats), st), "memset stats");
   mark(ctx, 5, st);
   const ExtraPlanes ex{out->curvature, out->distortion, out->median_depth, extra ? ctx->resid.p : nullptr};
-  QGS_CU(launch_raster_fwd(ctx->cfg.density == 1, extra, (unsigned)ntiles, st, ctx->ranges.p, ctx->ids,
-                           ctx->id_stride, ctx->raster_state, rp, out->rgb, out->alpha, out->depth, out->normal,
-                           ctx->T_final.p, ctx->n_contrib.p, ex, ctx->stats.p, ctx->tile_order, ctx->inst_used.p),
-         "k_raster_fwd");
+  if (stp)
+    QGS_CU(launch_raster_fwd_stp(ctx->cfg.density == 1, extra, (unsigned)ntiles, st, ctx->ranges.p, ctx->ids,
+                                 ctx->raster_state, rp, out->rgb, out->alpha, out->depth, out->normal,
+                                 ctx->T_final.p, ctx->n_contrib.p, ctx->xres.p, ex, ctx->stats.p, ctx->tile_order),
+           "k_raster_fwd_stp");
+  else
+    QGS_CU(launch_raster_fwd(ctx->cfg.density == 1, extra, (unsigned)ntiles, st, ctx->ranges.p, ctx->ids,
+                             ctx->id_stride, ctx->raster_state, rp, out->rgb, out->alpha, out->depth, out->normal,
+                             ctx->T_final.p, ctx->n_contrib.p, ex, ctx->stats.p, ctx->tile_order, ctx->inst_used.p),
+           "k_raster_fwd");
+  ctx->stp = stp;
   ++launch_counter();
   mark(ctx, 6, st);
   ctx->have_fwd_times = ctx->profiling;
@@ -681,6 +698,7 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
   qgs_status s = check_scene(ctx, scene);
   if (s != QGS_OK) return s;
   if (n_views < 1 || n_views > 1024) return fail(ctx, QGS_EINVAL, "n_views must be in [1, 1024]");
+  if (ctx->cfg.order != 0) return fail(ctx, QGS_EINVAL, "the batched forward uses the centre-depth order only");
   if (!cams || !outs) return fail(ctx, QGS_EINVAL, "camera/output array is NULL");
   const int64_t N = scene->n;
   const int V = n_views;
@@ -892,11 +910,17 @@ qgs_status render_backward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camer
   const bool extra = grad_out->curvature || grad_out->distortion;
   const ExtraGrads eg{grad_out->curvature, grad_out->distortion, ctx->have_resid ? ctx->resid.p : nullptr};
   mark(ctx, 7, st);
-  QGS_CU(launch_raster_bwd(euclid, extra, (unsigned)ntiles, st, ctx->ranges.p, ctx->ids, ctx->id_stride,
-                           ctx->raster_state, rp, grad_out->rgb, grad_out->alpha, grad_out->depth, grad_out->normal,
-                           ctx->T_final.p, ctx->n_contrib.p, eg, ctx->pgrad.p, ctx->stats.p, ctx->tile_order,
-                           ctx->inst_used.p),
-         "k_raster_bwd");
+  if (ctx->stp)
+    QGS_CU(launch_raster_bwd_stp(euclid, extra, (unsigned)ntiles, st, ctx->ranges.p, ctx->ids, ctx->raster_state,
+                                 rp, grad_out->rgb, grad_out->alpha, grad_out->depth, grad_out->normal,
+                                 ctx->T_final.p, ctx->xres.p, eg, ctx->pgrad.p, ctx->stats.p, ctx->tile_order),
+           "k_raster_bwd_stp");
+  else
+    QGS_CU(launch_raster_bwd(euclid, extra, (unsigned)ntiles, st, ctx->ranges.p, ctx->ids, ctx->id_stride,
+                             ctx->raster_state, rp, grad_out->rgb, grad_out->alpha, grad_out->depth,
+                             grad_out->normal, ctx->T_final.p, ctx->n_contrib.p, eg, ctx->pgrad.p, ctx->stats.p,
+                             ctx->tile_order, ctx->inst_used.p),
+           "k_raster_bwd");
   ++launch_counter();
   mark(ctx, 8, st);
   SceneView sv{scene->mean, scene->quat, scene->scale, scene->curv, scene->opacity, scene->sh};
@@ -976,7 +1000,7 @@ qgs_status qgs_copy_binning(qgs_ctx* ctx, uint64_t* keys, uint32_t* vals, int64_
       dk.release();
       return fail(ctx, QGS_ENOMEM, "alloc");
     }
-    if (ctx->cfg.sort_mode == 0) {
+    if (ctx->cfg.sort_mode == 0 && !ctx->stp) {
       if (ctx->packed32)
         k_debug_packed<uint32_t><<<nblk(I), 256>>>(I, reinterpret_cast<const uint32_t*>(ctx->sorted_keys),
                                                    ctx->rank_bits, ctx->vis_list, ctx->dstate.p, dk.p, dv.p);

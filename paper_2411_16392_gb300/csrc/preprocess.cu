@@ -473,4 +473,98 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(int64_t n, const uint32_
   gd.opacity[i] += d_o;
 }
 
+// ---------------------------------------------------------------------------------------
+// StopThePop ordering (supplementary, "Details of Per-tile Sorting and Per-pixel
+// Resorting"): one key per (tile, primitive) instance, (tile << 32) | float bits of the
+// depth where the ray of the tile pixel closest to the projected vertex meets the
+// paraboloid. Correctly rounded FP32 in the order below (the same specification as the
+// oracle's FP32 key recipe); the ray is re-based at the centre's depth so the quadratic's
+// coefficients have the size of the primitive. Instances in primitive order, tiles
+// row-major, values = primitive (a stable sort of the keys then orders each tile's list
+// by that depth, ties by primitive index).
+namespace {
+
+__device__ __forceinline__ void frame_exact(int64_t i, const SceneView& sc, const CamParams& cp, float muc[3],
+                                            float W[9]) {
+  const float mx = sc.mean[3 * i], my = sc.mean[3 * i + 1], mz = sc.mean[3 * i + 2];
+  const float4 q = reinterpret_cast<const float4*>(sc.quat)[i];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+    muc[r] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(cp.Rc[3 * r], mx), __fmul_rn(cp.Rc[3 * r + 1], my)),
+                                 __fmul_rn(cp.Rc[3 * r + 2], mz)),
+                       cp.tc[r]);
+  float R[9];
+  quat_rot_exact(q.x, q.y, q.z, q.w, R);  // visible primitives only: the norm is positive
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      W[3 * r + c] = __fadd_rn(__fadd_rn(__fmul_rn(cp.Rc[3 * r], R[c]), __fmul_rn(cp.Rc[3 * r + 1], R[3 + c])),
+                               __fmul_rn(cp.Rc[3 * r + 2], R[6 + c]));
+}
+
+__device__ __forceinline__ uint32_t hit_key_bits(const float muc[3], const float W[9], float a, float b, float uc,
+                                                 float vc, int tx, int ty, const CamParams& cp) {
+  const float x = muc[0], y = muc[1], z = muc[2];
+  const float px = fminf(fmaxf(floorf(uc), (float)(16 * tx)), (float)min(16 * tx + 15, cp.W - 1));
+  const float py = fminf(fmaxf(floorf(vc), (float)(16 * ty)), (float)min(16 * ty + 15, cp.H - 1));
+  const float dx = __fdiv_rn(__fsub_rn(__fadd_rn(px, 0.5f), cp.cx), cp.fx);
+  const float dy = __fdiv_rn(__fsub_rn(__fadd_rn(py, 0.5f), cp.cy), cp.fy);
+  const float ex = __fsub_rn(__fmul_rn(dx, z), x);
+  const float ey = __fsub_rn(__fmul_rn(dy, z), y);
+  float bk[3], dk[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    bk[k] = __fadd_rn(__fmul_rn(W[k], ex), __fmul_rn(W[3 + k], ey));
+    dk[k] = __fadd_rn(__fadd_rn(__fmul_rn(W[k], dx), __fmul_rn(W[3 + k], dy)), W[6 + k]);
+  }
+  const float A = __fadd_rn(__fmul_rn(__fmul_rn(a, dk[0]), dk[0]), __fmul_rn(__fmul_rn(b, dk[1]), dk[1]));
+  const float Bh = __fsub_rn(__fadd_rn(__fmul_rn(__fmul_rn(a, bk[0]), dk[0]), __fmul_rn(__fmul_rn(b, bk[1]), dk[1])),
+                             __fmul_rn(0.5f, dk[2]));
+  const float C = __fsub_rn(__fadd_rn(__fmul_rn(__fmul_rn(a, bk[0]), bk[0]), __fmul_rn(__fmul_rn(b, bk[1]), bk[1])),
+                            bk[2]);
+  const float D = __fsub_rn(__fmul_rn(Bh, Bh), __fmul_rn(A, C));
+  const float sq = __fsqrt_rn(fmaxf(D, 0.f));
+  const float q = -__fadd_rn(Bh, Bh >= 0.f ? sq : -sq);
+  const float t1 = __fadd_rn(z, __fdiv_rn(C, q));
+  const float t2 = __fadd_rn(z, __fdiv_rn(q, A));
+  const bool ok1 = D >= 0.f && isfinite(t1) && t1 > cp.near;
+  const bool ok2 = D >= 0.f && isfinite(t2) && t2 > cp.near;
+  const float t = (ok1 && ok2) ? fminf(t1, t2) : (ok1 ? t1 : (ok2 ? t2 : z));
+  return __float_as_uint(t);
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_emit_hit(int64_t n, SceneView sc, CamParams cp,
+                                                  const uint32_t* __restrict__ count,
+                                                  const short4* __restrict__ rect,
+                                                  const uint32_t* __restrict__ offs, uint64_t* __restrict__ keys,
+                                                  uint32_t* __restrict__ vals) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t wbase = i - lane;
+  const uint32_t c = i < n ? count[i] : 0u;
+  for (int k = 0; k < 32; ++k) {
+    const uint32_t cc = __shfl_sync(0xffffffffu, c, k);
+    if (!cc) continue;
+    const int64_t p = wbase + k;  // every lane recomputes the primitive's frame (broadcast loads)
+    float muc[3], W[9];
+    frame_exact(p, sc, cp, muc, W);
+    const float2 ab = reinterpret_cast<const float2*>(sc.curv)[p];
+    const float uc = __fadd_rn(__fmul_rn(cp.fx, __fdiv_rn(muc[0], muc[2])), cp.cx);
+    const float vc = __fadd_rn(__fmul_rn(cp.fy, __fdiv_rn(muc[1], muc[2])), cp.cy);
+    const short4 r = rect[p];
+    const uint32_t off = offs[p];
+    const uint32_t w = (uint32_t)(r.y - r.x + 1);
+    for (uint32_t e = lane; e < cc; e += 32) {
+      const uint32_t dy = e / w, dx = e - dy * w;
+      const int tx = r.x + (int)dx, ty = r.z + (int)dy;
+      const uint32_t tile = (uint32_t)ty * (uint32_t)cp.tiles_x + (uint32_t)tx;
+      keys[(size_t)off + e] = ((uint64_t)tile << 32) | hit_key_bits(muc, W, ab.x, ab.y, uc, vc, tx, ty, cp);
+      vals[(size_t)off + e] = (uint32_t)p;
+    }
+  }
+}
+
 }  // namespace qgs

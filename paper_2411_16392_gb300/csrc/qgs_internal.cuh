@@ -39,6 +39,11 @@ __global__ void k_preprocess(int64_t n, SceneView sc, CamParams cp, PrimState* s
                              uint32_t* zkey, uint32_t* idx, short4* rect, uint32_t* counters, uint32_t* vflag);
 __global__ void k_preprocess_views(int64_t n, SceneView sc, const CamParams* cps, PrimState* state, uint32_t* count,
                                    uint32_t* zkey, uint32_t* idx, short4* rect, uint32_t* n_visible);
+// StopThePop ordering: per (tile, primitive) instance, in primitive order,
+// key = (tile << 32) | bits of the depth where the ray of the tile pixel closest to the
+// projected vertex meets the paraboloid; value = primitive.
+__global__ void k_emit_hit(int64_t n, SceneView sc, CamParams cp, const uint32_t* count, const short4* rect,
+                           const uint32_t* offs, uint64_t* keys, uint32_t* vals);
 // list == nullptr: threads 0..n-1 are primitives 0..n-1; else primitive list[j].
 // pgrad_by_pos: the gradient record of thread j is pgrad[j] (state gathered in list
 // order), else pgrad[primitive].
@@ -121,6 +126,21 @@ cudaError_t launch_raster_fwd_views(bool euclid, bool extra, unsigned grid, cuda
                                     const uint32_t* ids, int id_stride, const PrimState* state,
                                     const ViewDesc* views, int n_views, const uint32_t* tile_base,
                                     RasterStats* stats, const uint32_t* tile_order);
+// StopThePop ordering (per-tile hit-depth lists, per-pixel resorting in a buffer of 8):
+// forward keeps T_final, the blended count and the outputs (xres, 8 planes: rgb, depth,
+// normal, curvature) for the front-to-back backward, which adds per-pixel gradient
+// records to pgrad (indexed by the sorted ids).
+cudaError_t launch_raster_fwd_stp(bool euclid, bool extra, unsigned grid, cudaStream_t st, const uint2* ranges,
+                                  const uint32_t* ids, const PrimState* state, const RasterParams& rp,
+                                  float* out_rgb, float* out_alpha, float* out_depth, float* out_normal,
+                                  float* T_final, uint32_t* n_blended, float* xres, const ExtraPlanes& ex,
+                                  RasterStats* stats, const uint32_t* tile_order);
+cudaError_t launch_raster_bwd_stp(bool euclid, bool extra, unsigned grid, cudaStream_t st, const uint2* ranges,
+                                  const uint32_t* ids, const PrimState* state, const RasterParams& rp,
+                                  const float* g_rgb, const float* g_alpha, const float* g_depth,
+                                  const float* g_normal, const float* T_final, const float* xres,
+                                  const ExtraGrads& eg, float* pgrad, RasterStats* stats,
+                                  const uint32_t* tile_order);
 constexpr size_t RASTER_BWD_SMEM = sizeof(PrimState) * BLOCK + sizeof(float) * BLOCK * NGRAD + sizeof(int) * BLOCK;
 cudaError_t launch_raster_bwd(bool euclid, bool extra, unsigned grid, cudaStream_t st, const uint2* ranges,
                               const uint32_t* ids, int id_stride, const PrimState* state, const RasterParams& rp,

@@ -663,6 +663,281 @@ __global__ void __launch_bounds__(BLOCK, 3)
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// StopThePop ordering (supplementary, "Details of Per-tile Sorting and Per-pixel
+// Resorting"): the tile lists are sorted by each primitive's hit depth on the tile's
+// representative ray; each pixel keeps its contributing pairs in a buffer of 8 (hit depth,
+// list position) entries and blends the nearest one whenever the buffer is full, the rest
+// nearest first at the end of the list. An entry is re-evaluated when it is blended (its
+// state record is read again from global memory), so a buffered entry costs two
+// registers. The backward replays the same sequence front to back with the
+// supplementary's front-to-back dX/d(alpha) and adds each pair's gradient record to
+// global memory per pixel.
+namespace {
+
+constexpr int RESORT = 8;
+
+struct ResortBuf {
+  float t[RESORT];
+  uint32_t pos[RESORT];
+  int n = 0;
+  __device__ __forceinline__ void push(float tt, uint32_t p) {
+#pragma unroll
+    for (int k = 0; k < RESORT; ++k)
+      if (k == n) { t[k] = tt; pos[k] = p; }
+    ++n;
+  }
+  // remove and return the entry with the smallest (depth, list position)
+  __device__ __forceinline__ uint32_t pop() {
+    float bt = INFINITY;
+    uint32_t bp = 0xFFFFFFFFu;
+    int bk = 0;
+#pragma unroll
+    for (int k = 0; k < RESORT; ++k)
+      if (k < n && (t[k] < bt || (t[k] == bt && pos[k] < bp))) { bt = t[k]; bp = pos[k]; bk = k; }
+    float lt = 0.f;
+    uint32_t lp = 0;
+#pragma unroll
+    for (int k = 0; k < RESORT; ++k)
+      if (k == n - 1) { lt = t[k]; lp = pos[k]; }
+#pragma unroll
+    for (int k = 0; k < RESORT; ++k)
+      if (k == bk) { t[k] = lt; pos[k] = lp; }
+    --n;
+    return bp;
+  }
+};
+
+__device__ __forceinline__ PrimState load_state(const PrimState* __restrict__ state, uint32_t pid) {
+  PrimState P;
+  const float4* src = reinterpret_cast<const float4*>(state + pid);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) P.f[c] = __ldg(src + c);
+  return P;
+}
+
+}  // namespace
+
+template <bool EUCLID, bool EXTRA>
+__global__ void __launch_bounds__(BLOCK, 3)
+    k_raster_fwd_stp(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids,
+                     const PrimState* __restrict__ state, RasterParams rp, float* __restrict__ out_rgb,
+                     float* __restrict__ out_alpha, float* __restrict__ out_depth, float* __restrict__ out_normal,
+                     float* __restrict__ T_final, uint32_t* __restrict__ n_blended, float* __restrict__ xres,
+                     ExtraPlanes ex, RasterStats* __restrict__ stats, const uint32_t* __restrict__ tile_order) {
+  __shared__ PrimState sm[BLOCK];
+  const int tile = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;
+  int px, py;
+  pixel_of(tile, rp.tiles_x, px, py);
+  const bool inside = px < rp.W && py < rp.H;
+  const uint2 rg = ranges[tile];
+  const int n = (int)(rg.y - rg.x);
+  const float X = (float)px + 0.5f, Y = (float)py + 0.5f;
+  const float xn = (X - rp.cx) * rp.inv_fx, yn = (Y - rp.cy) * rp.inv_fy;
+  float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, dep = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
+  float kc = 0.f, tref = 0.f, A1 = 0.f, A2 = 0.f, med = 0.f;
+  uint32_t evals = 0, grazes = 0, isect = 0, hits = 0, blended = 0, dummy = 0;
+  bool done = !inside;
+  ResortBuf buf;
+  // blend the entry at list position pos (re-evaluated from its state record)
+  auto blend = [&](uint32_t pos) {
+    const PrimState P = load_state(state, __ldg(ids + pos) & rp.id_mask);
+    Hit h;
+    bool gz = false;
+    if (!eval_pair<EUCLID>(P, X, Y, rp, h, gz, dummy)) return;  // deterministic: it hit when buffered
+    const float4 f2 = P.f[2], f3 = P.f[3], f4 = P.f[4], f5 = P.f[5], f6 = P.f[6], f7 = P.f[7];
+    const float al = fminf(rp.alpha_max, __fmul_rn(f5.w, h.G));
+    const float Tn = __fmul_rn(T, __fsub_rn(1.f, al));
+    if (Tn < rp.T_min) {
+      done = true;
+      return;
+    }
+    const float w = al * T;
+    cr = fmaf(w, f7.y, cr);
+    cg = fmaf(w, f7.z, cg);
+    cb = fmaf(w, f7.w, cb);
+    const float t = f2.w + h.s;
+    dep = fmaf(w, t, dep);
+    const float nlx = 2.f * f5.y * h.x, nly = 2.f * f5.z * h.y;
+    const float ncx = fmaf(f3.x, nlx, fmaf(f3.z, nly, -f4.x));
+    const float ncy = fmaf(f3.y, nlx, fmaf(f3.w, nly, -f4.y));
+    const float ncz = fmaf(f6.z, nlx, fmaf(f6.w, nly, -f7.x));
+    float inn = rsqrtf(fmaf(ncx, ncx, fmaf(ncy, ncy, ncz * ncz)));
+    if (fmaf(ncx, xn, fmaf(ncy, yn, ncz)) > 0.f) inn = -inn;
+    const float wn = w * inn;
+    nx = fmaf(wn, ncx, nx);
+    ny = fmaf(wn, ncy, ny);
+    nz = fmaf(wn, ncz, nz);
+    if constexpr (EXTRA) {
+      kc = fmaf(w, curvature(f5.y, f5.z, h.x, h.y), kc);
+      if (blended == 0) tref = t;
+      const float tau = t - tref;
+      A1 = fmaf(w, tau, A1);
+      A2 = fmaf(w * tau, tau, A2);
+      if (T > 0.5f) med = fmaxf(med, t);
+    }
+    T = Tn;
+    ++blended;
+  };
+  for (int b0 = 0; b0 < n; b0 += BLOCK) {
+    if (__syncthreads_count(done) == BLOCK) break;
+    const int cnt = min(BLOCK, n - b0);
+    stage_batch(sm, ids, 1, rp.id_mask, state, rg.x + b0, cnt);
+    __syncthreads();
+    if (!done) {
+      for (int j = 0; j < cnt; ++j) {
+        ++evals;
+        Hit h;
+        bool gz = false;
+        const bool hit = eval_pair<EUCLID>(sm[j], X, Y, rp, h, gz, isect);
+        grazes += gz;
+        if (!hit) continue;
+        ++hits;
+        const float al = fminf(rp.alpha_max, __fmul_rn(sm[j].f[5].w, h.G));
+        if (al < rp.alpha_min) continue;
+        buf.push(sm[j].f[2].w + h.s, rg.x + (uint32_t)(b0 + j));
+        if (buf.n == RESORT) {
+          blend(buf.pop());
+          if (done) break;
+        }
+      }
+    }
+  }
+  while (!done && buf.n > 0) blend(buf.pop());
+  if (inside) {
+    const size_t P = (size_t)rp.W * rp.H, pix = (size_t)py * rp.W + px;
+    out_rgb[pix] = cr;
+    out_rgb[P + pix] = cg;
+    out_rgb[2 * P + pix] = cb;
+    out_alpha[pix] = 1.f - T;
+    out_depth[pix] = dep;
+    out_normal[pix] = nx;
+    out_normal[P + pix] = ny;
+    out_normal[2 * P + pix] = nz;
+    T_final[pix] = T;
+    n_blended[pix] = blended;
+    // the outputs again, for the front-to-back backward (the caller may reuse its planes)
+    xres[pix] = cr;
+    xres[P + pix] = cg;
+    xres[2 * P + pix] = cb;
+    xres[3 * P + pix] = dep;
+    xres[4 * P + pix] = nx;
+    xres[5 * P + pix] = ny;
+    xres[6 * P + pix] = nz;
+    xres[7 * P + pix] = kc;
+    if constexpr (EXTRA) {
+      if (ex.curvature) ex.curvature[pix] = kc;
+      if (ex.distortion) ex.distortion[pix] = fmaf(1.f - T, A2, -A1 * A1);
+      if (ex.median_depth) ex.median_depth[pix] = med;
+      if (ex.resid) {
+        ex.resid[pix] = tref;
+        ex.resid[P + pix] = A1;
+        ex.resid[2 * P + pix] = A2;
+      }
+    }
+  }
+  if (stats) {
+    const unsigned ev = __reduce_add_sync(FULL, evals), is = __reduce_add_sync(FULL, isect);
+    const unsigned hi = __reduce_add_sync(FULL, hits), bl = __reduce_add_sync(FULL, blended);
+    const unsigned gzz = __reduce_add_sync(FULL, grazes);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&stats->pair_evals, (unsigned long long)ev);
+      atomicAdd(&stats->pair_isect, (unsigned long long)is);
+      atomicAdd(&stats->pair_hits, (unsigned long long)hi);
+      atomicAdd(&stats->pair_blended, (unsigned long long)bl);
+      if (gzz) atomicAdd(&stats->grazing, (unsigned long long)gzz);
+    }
+  }
+}
+
+template <bool EUCLID, bool EXTRA>
+__global__ void __launch_bounds__(BLOCK, 2)
+    k_raster_bwd_stp(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids,
+                     const PrimState* __restrict__ state, RasterParams rp, const float* __restrict__ g_rgb,
+                     const float* __restrict__ g_alpha, const float* __restrict__ g_depth,
+                     const float* __restrict__ g_normal, const float* __restrict__ T_final,
+                     const float* __restrict__ xres, ExtraGrads eg, float* __restrict__ pgrad,
+                     RasterStats* __restrict__ stats, const uint32_t* __restrict__ tile_order) {
+  __shared__ PrimState sm[BLOCK];
+  const int tile = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;
+  int px, py;
+  pixel_of(tile, rp.tiles_x, px, py);
+  const bool inside = px < rp.W && py < rp.H;
+  const uint2 rg = ranges[tile];
+  const int n = (int)(rg.y - rg.x);
+  const float X = (float)px + 0.5f, Y = (float)py + 0.5f;
+  const float xn = (X - rp.cx) * rp.inv_fx, yn = (Y - rp.cy) * rp.inv_fy;
+  const size_t P = (size_t)rp.W * rp.H, pix = inside ? (size_t)py * rp.W + px : 0;
+  const float Tfin = inside ? T_final[pix] : 1.f;
+  const PixGrads pg = load_pix_grads<EXTRA>(inside, pix, P, Tfin, g_rgb, g_alpha, g_depth, g_normal, eg);
+  // sum over all blended pairs of w (g . X): from the forward's outputs
+  float S_total = 0.f;
+  if (inside) {
+    S_total = pg.gR * xres[pix] + pg.gG * xres[P + pix] + pg.gB * xres[2 * P + pix] + pg.gD * xres[3 * P + pix] +
+              pg.gNx * xres[4 * P + pix] + pg.gNy * xres[5 * P + pix] + pg.gNz * xres[6 * P + pix];
+    if constexpr (EXTRA) {
+      S_total += pg.gK * xres[7 * P + pix];
+      if (pg.g_tau != 0.f || pg.g_tau2 != 0.f) S_total += pg.g_tau * eg.resid[P + pix] + pg.g_tau2 * eg.resid[2 * P + pix];
+    }
+  }
+  float T = 1.f, S_prefix = 0.f;
+  uint32_t n_pairs = 0, n_contrib_pairs = 0, dummy = 0;
+  bool done = !inside;
+  ResortBuf buf;
+  auto blend = [&](uint32_t pos) {
+    const uint32_t pid = __ldg(ids + pos) & rp.id_mask;
+    const PrimState Ps = load_state(state, pid);
+    Hit h;
+    bool gz = false;
+    if (!eval_pair<EUCLID>(Ps, X, Y, rp, h, gz, dummy)) return;
+    const float oG = __fmul_rn(Ps.f[5].w, h.G);
+    const float al = fminf(rp.alpha_max, oG);
+    const float Tn = __fmul_rn(T, __fsub_rn(1.f, al));
+    if (Tn < rp.T_min) {
+      done = true;
+      return;
+    }
+    float v[32];
+    S_prefix += pair_grad<EUCLID, EXTRA, true>(Ps, h, oG, al, T, xn, yn, rp, pg, S_total, S_prefix, v);
+    ++n_contrib_pairs;
+    float* dst = pgrad + (size_t)pid * NGRAD_PAD;
+#pragma unroll
+    for (int k = 0; k < NGRAD; ++k)
+      if (v[k] != 0.f) atomicAdd(dst + k, v[k]);
+    T = Tn;
+  };
+  for (int b0 = 0; b0 < n; b0 += BLOCK) {
+    if (__syncthreads_count(done) == BLOCK) break;
+    const int cnt = min(BLOCK, n - b0);
+    __syncthreads();
+    stage_batch(sm, ids, 1, rp.id_mask, state, rg.x + b0, cnt);
+    __syncthreads();
+    if (!done) {
+      for (int j = 0; j < cnt; ++j) {
+        ++n_pairs;
+        Hit h;
+        bool gz = false;
+        if (!eval_pair<EUCLID>(sm[j], X, Y, rp, h, gz, dummy)) continue;
+        const float al = fminf(rp.alpha_max, __fmul_rn(sm[j].f[5].w, h.G));
+        if (al < rp.alpha_min) continue;
+        buf.push(sm[j].f[2].w + h.s, rg.x + (uint32_t)(b0 + j));
+        if (buf.n == RESORT) {
+          blend(buf.pop());
+          if (done) break;
+        }
+      }
+    }
+  }
+  while (!done && buf.n > 0) blend(buf.pop());
+  if (stats) {
+    const unsigned np = __reduce_add_sync(FULL, n_pairs), nc = __reduce_add_sync(FULL, n_contrib_pairs);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&stats->bwd_pairs, (unsigned long long)np);
+      atomicAdd(&stats->bwd_contrib, (unsigned long long)nc);
+    }
+  }
+}
+
 // Host-side selection of the instantiation: runs the statement(s) with the constants
 // E_ (EUCLID) and X_ (EXTRA) set.
 #define QGS_RASTER_DISPATCH(euclid, extra, ...)                          \
@@ -714,6 +989,30 @@ cudaError_t launch_raster_bwd(bool euclid, bool extra, unsigned grid, cudaStream
                                                                  stats, tile_order, inst_used);
   });
   if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+cudaError_t launch_raster_fwd_stp(bool euclid, bool extra, unsigned grid, cudaStream_t st, const uint2* ranges,
+                                  const uint32_t* ids, const PrimState* state, const RasterParams& rp,
+                                  float* out_rgb, float* out_alpha, float* out_depth, float* out_normal,
+                                  float* T_final, uint32_t* n_blended, float* xres, const ExtraPlanes& ex,
+                                  RasterStats* stats, const uint32_t* tile_order) {
+  QGS_RASTER_DISPATCH(euclid, extra,
+                      k_raster_fwd_stp<E_, X_><<<grid, BLOCK, 0, st>>>(ranges, ids, state, rp, out_rgb, out_alpha,
+                                                                       out_depth, out_normal, T_final, n_blended,
+                                                                       xres, ex, stats, tile_order));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_raster_bwd_stp(bool euclid, bool extra, unsigned grid, cudaStream_t st, const uint2* ranges,
+                                  const uint32_t* ids, const PrimState* state, const RasterParams& rp,
+                                  const float* g_rgb, const float* g_alpha, const float* g_depth,
+                                  const float* g_normal, const float* T_final, const float* xres,
+                                  const ExtraGrads& eg, float* pgrad, RasterStats* stats,
+                                  const uint32_t* tile_order) {
+  QGS_RASTER_DISPATCH(euclid, extra,
+                      k_raster_bwd_stp<E_, X_><<<grid, BLOCK, 0, st>>>(ranges, ids, state, rp, g_rgb, g_alpha,
+                                                                       g_depth, g_normal, T_final, xres, eg, pgrad,
+                                                                       stats, tile_order));
   return cudaGetLastError();
 }
 #undef QGS_RASTER_DISPATCH

@@ -70,13 +70,17 @@ class Rasterizer:
 
     DENSITIES = {"geodesic": 0, "euclid": 1}
 
-    def __init__(self, device: int | torch.device = 0, sort_mode: int = 0, density: str = "geodesic", **consts):
+    ORDERS = {"centre": 0, "stp": 1}
+
+    def __init__(self, device: int | torch.device = 0, sort_mode: int = 0, density: str = "geodesic",
+                 order: str = "centre", **consts):
         self.lib = L.load()
         self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
         cfg = L.qgs_config()
         self.lib.qgs_config_default(C.byref(cfg))
         cfg.sort_mode = sort_mode
         cfg.density = self.DENSITIES[density]
+        cfg.order = self.ORDERS[order]
         for k, v in consts.items():
             setattr(cfg, k, v)
         self._ctx = C.c_void_p()

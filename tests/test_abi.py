@@ -46,7 +46,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(L.qgs_scene) == 8 * 7
     assert ctypes.sizeof(L.qgs_image) == 8 * 7
     assert ctypes.sizeof(L.qgs_scene_grad) == 8 * 6
-    assert ctypes.sizeof(L.qgs_config) == 4 * 6
+    assert ctypes.sizeof(L.qgs_config) == 4 * 7
     assert ctypes.sizeof(L.qgs_frame_stats) == 8 * 13 + 4 * 7 + 4
 
 
