@@ -320,7 +320,52 @@ def run_gpu(args):
         e2e_value, h2d, d2h = None, 0, 0
     else:
         e2e_value, h2d, d2h = _e2e(args, ras, ds, cam, gout, grads, out, dev, world, P)
-    return _report(args, rank, world, sc, cam, st, stage, clk, ms_max, value, e2e_value, h2d, d2h)
+    variants = None
+    if rank == 0 and world == 1 and args.variant_steps > 0:
+        variants = _variants(args, ds, cam, gout, grads, dev)
+    return _report(args, rank, world, sc, cam, st, stage, clk, ms_max, value, e2e_value, h2d, d2h, variants)
+
+
+def _variants(args, ds, cam, gout, grads, dev):
+    """The same fwd+bwd step with each optional path of the renderer (not the headline):
+    the extra channels (curvature, distortion, median depth with their gradients), the
+    Euclidean density, and the StopThePop ordering."""
+    import torch
+    from paper_2411_16392_gb300.render import Rasterizer
+    H, W = cam.H, cam.W
+    res = {}
+    gx = dict(gout)
+    gx["curvature"] = torch.randn(H, W, device=dev)
+    gx["distortion"] = torch.randn(H, W, device=dev)
+    for name, kw, extras in (("extra_channels", {}, True), ("euclid", {"density": "euclid"}, False),
+                             ("stopthepop", {"order": "stp"}, False)):
+        ras = Rasterizer(dev, **kw)
+        g = gx if extras else gout
+
+        def step():
+            ras.forward(ds, cam, extras=extras)
+            ras.backward(ds, cam, g, grads)
+
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        stream = torch.cuda.current_stream(dev)
+        e0.record(stream)
+        for _ in range(args.variant_steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.variant_steps
+        ras.lib.qgs_set_profiling(ras._ctx, 1)
+        step()
+        st = ras.stats()
+        res[name] = {"mpix_per_s": H * W / (ms * 1e-3) / 1e6, "ms_per_step": ms,
+                     "ms_raster_fwd": st["ms_raster_fwd"], "ms_raster_bwd": st["ms_raster_bwd"],
+                     "pair_blended": st["pair_blended"]}
+        ras.close()
+    return res
 
 
 def _e2e(args, ras, ds, cam, gout, grads, out, dev, world, P):
@@ -362,7 +407,7 @@ def _e2e(args, ras, ds, cam, gout, grads, out, dev, world, P):
     return e2e_value, h2d, d2h
 
 
-def _report(args, rank, world, sc, cam, st, stage, clk, ms_max, value, e2e_value, h2d, d2h):
+def _report(args, rank, world, sc, cam, st, stage, clk, ms_max, value, e2e_value, h2d, d2h, variants=None):
     import torch.distributed as dist
     H, W = cam.H, cam.W
     # ---- roofline of the dominant kernel (FP32 ALU bound)
@@ -427,6 +472,8 @@ def _report(args, rank, world, sc, cam, st, stage, clk, ms_max, value, e2e_value
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int((st["launches_fwd"] + st["launches_bwd"]) * args.steps),
             "clocks": clk}
+    if variants:
+        line["variants"] = variants
     if rank == 0 and world == 1 and args.serve_requests > 0:
         line["serving"] = _serving_leg(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -523,6 +570,8 @@ def main():
                     help="Poisson arrival rates, requests/s (comma-separated)")
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-batch", type=int, default=8, help="most views per batch in the batched leg")
+    ap.add_argument("--variant-steps", type=int, default=5,
+                    help="timed steps of each optional renderer path (extra channels, Euclid, StopThePop; 0: skip)")
     ap.add_argument("--serve-mixed-rate", type=float, default=100.0,
                     help="arrival rate of the six-scene forward/backward serving leg (0: skip)")
     args = ap.parse_args()

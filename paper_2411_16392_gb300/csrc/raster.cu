@@ -850,6 +850,10 @@ __global__ void __launch_bounds__(BLOCK, 3)
   }
 }
 
+// Each pixel adds the gradient record of each blended pair to global memory (vector
+// atomics, 16 bytes each): the pixels of a tile pop different pairs at the same step, so
+// the warp reduction of the list-order backward does not apply, and per-tile shared
+// accumulators serialise on the many pixels that blend the same near primitive.
 template <bool EUCLID, bool EXTRA>
 __global__ void __launch_bounds__(BLOCK, 2)
     k_raster_bwd_stp(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids,
@@ -900,16 +904,17 @@ __global__ void __launch_bounds__(BLOCK, 2)
     float v[32];
     S_prefix += pair_grad<EUCLID, EXTRA, true>(Ps, h, oG, al, T, xn, yn, rp, pg, S_total, S_prefix, v);
     ++n_contrib_pairs;
-    float* dst = pgrad + (size_t)pid * NGRAD_PAD;
+    float4* dst = reinterpret_cast<float4*>(pgrad + (size_t)pid * NGRAD_PAD);  // 80-byte records
 #pragma unroll
-    for (int k = 0; k < NGRAD; ++k)
-      if (v[k] != 0.f) atomicAdd(dst + k, v[k]);
+    for (int k = 0; k < NGRAD / 4; ++k) {
+      const float4 q = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+      if (q.x != 0.f || q.y != 0.f || q.z != 0.f || q.w != 0.f) atomicAdd(dst + k, q);
+    }
     T = Tn;
   };
   for (int b0 = 0; b0 < n; b0 += BLOCK) {
     if (__syncthreads_count(done) == BLOCK) break;
     const int cnt = min(BLOCK, n - b0);
-    __syncthreads();
     stage_batch(sm, ids, 1, rp.id_mask, state, rg.x + b0, cnt);
     __syncthreads();
     if (!done) {
