@@ -141,6 +141,21 @@ __device__ __forceinline__ void screen_normal(const CamParams& cp, const float* 
   }
 }
 
+// Projected centre f (x / z) + c as an unevaluated sum hi + lo of floats (about 44
+// significant bits), from error-free transformations: the division's remainder by fma,
+// the product's rounding error by fma, and a two-sum with the principal point.
+__device__ __forceinline__ void centre_df(float x, float z, float f, float c, float& hi, float& lo) {
+  const float qh = x / z;
+  const float ql = fmaf(-qh, z, x) / z;          // x/z = qh + ql (to ~2^-48 relative)
+  const float ph = f * qh;
+  const float pl = fmaf(f, qh, -ph) + f * ql;    // f (qh + ql) = ph + pl
+  const float sh = ph + c;                       // two-sum of ph and c
+  const float bb = sh - ph;
+  const float sl = ((ph - (sh - bb)) + (c - bb)) + pl;
+  hi = sh + sl;
+  lo = sl - (hi - sh);
+}
+
 // Scaled slab of the parallelogram: (p_x, p_y, p_c) with |p_x dx + p_y dy - p_c| <= 1
 // for every pixel offset (dx, dy) from the projected centre inside the span.
 __device__ __forceinline__ float3 slab_of(float nx, float ny, float smin, float smax) {
@@ -168,11 +183,20 @@ __global__ void __launch_bounds__(256) k_preprocess(int64_t n, SceneView sc, Cam
   uint32_t cnt = 0;
   if (active) cnt = preprocess_one(i, sc, cp, state, count, zkey, idx, rect);
   if (active && vflag) vflag[i] = cnt ? 1u : 0u;
+  // one atomic per CTA and counter (per-warp atomics on two addresses serialise)
+  __shared__ uint32_t red[2][8];
   const uint32_t vis = __reduce_add_sync(0xffffffffu, cnt ? 1u : 0u);
   const uint32_t tot = __reduce_add_sync(0xffffffffu, cnt);
   if ((threadIdx.x & 31) == 0) {
-    if (vis) atomicAdd(&counters[0], vis);
-    if (tot) atomicAdd(&counters[1], tot);
+    red[0][threadIdx.x >> 5] = vis;
+    red[1][threadIdx.x >> 5] = tot;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    uint32_t t = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += red[threadIdx.x][w];
+    if (t) atomicAdd(&counters[threadIdx.x], t);
   }
 }
 
@@ -189,7 +213,15 @@ __global__ void __launch_bounds__(256) k_preprocess_views(int64_t n, SceneView s
     vis = preprocess_one(i, sc, cp, state + off, count + off, zkey + off, idx + off, rect + off, (uint32_t)off) ? 1u
                                                                                                               : 0u;
   vis = __reduce_add_sync(0xffffffffu, vis);
-  if ((threadIdx.x & 31) == 0 && vis) atomicAdd(n_visible, vis);
+  __shared__ uint32_t red[8];  // one atomic per CTA
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = vis;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += red[w];
+    if (t) atomicAdd(n_visible, t);
+  }
 }
 
 __device__ __forceinline__ uint32_t preprocess_one(int64_t i, const SceneView& sc, const CamParams& cp,
@@ -198,10 +230,7 @@ __device__ __forceinline__ uint32_t preprocess_one(int64_t i, const SceneView& s
                                                    short4* __restrict__ rect, uint32_t idx_base) {
   if (idx) idx[i] = idx_base + (uint32_t)i;
   const float mx = sc.mean[3 * i], my = sc.mean[3 * i + 1], mz = sc.mean[3 * i + 2];
-  const float4 q = reinterpret_cast<const float4*>(sc.quat)[i];
   const float2 s = reinterpret_cast<const float2*>(sc.scale)[i];
-  const float2 ab = reinterpret_cast<const float2*>(sc.curv)[i];
-  const float op = sc.opacity[i];
 
   uint32_t cnt = 0;
   short4 rc = make_short4(-1, -1, -1, -1);
@@ -214,6 +243,32 @@ __device__ __forceinline__ uint32_t preprocess_one(int64_t i, const SceneView& s
     muc[r] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(cp.Rc[3 * r], mx), __fmul_rn(cp.Rc[3 * r + 1], my)),
                                  __fmul_rn(cp.Rc[3 * r + 2], mz)),
                        cp.tc[r]);
+  // Early exit for primitives the recipe below culls anyway: centre not in front of the
+  // near plane, or the sphere that holds the support box (every corner lies within
+  // 3 sqrt(3) max(s_u, s_v) of the centre) entirely beyond one side plane of the image
+  // (then every projected box point, near-plane points included, falls outside it). The
+  // sphere is enlarged by 1 % + 1e-6 |mu_c| against rounding, so no primitive the exact
+  // recipe keeps is dropped.
+  {
+    const float rad = 5.1961524f * fmaxf(s.x, s.y) * 1.01f +
+                      1e-6f * (fabsf(muc[0]) + fabsf(muc[1]) + fabsf(muc[2]));
+    const float x = muc[0], y = muc[1], z = muc[2];
+    const float rx = (float)cp.W - cp.cx, ry = (float)cp.H - cp.cy;
+    const bool outside = !(z > cp.near) ||
+                         -(cp.fx * x + cp.cx * z) > rad * sqrtf(cp.fx * cp.fx + cp.cx * cp.cx) ||
+                         (cp.fx * x - rx * z) > rad * sqrtf(cp.fx * cp.fx + rx * rx) ||
+                         -(cp.fy * y + cp.cy * z) > rad * sqrtf(cp.fy * cp.fy + cp.cy * cp.cy) ||
+                         (cp.fy * y - ry * z) > rad * sqrtf(cp.fy * cp.fy + ry * ry);
+    if (outside) {
+      count[i] = 0u;
+      zkey[i] = 0xFFFFFFFFu;
+      rect[i] = rc;
+      return 0u;
+    }
+  }
+  const float4 q = reinterpret_cast<const float4*>(sc.quat)[i];
+  const float2 ab = reinterpret_cast<const float2*>(sc.curv)[i];
+  const float op = sc.opacity[i];
   float R[9], W[9];
   bool finite_in = isfinite(mx) && isfinite(my) && isfinite(mz) && isfinite(q.x) && isfinite(q.y) && isfinite(q.z) &&
                    isfinite(q.w) && isfinite(s.x) && isfinite(s.y) && isfinite(ab.x) && isfinite(ab.y) && isfinite(op);
@@ -249,8 +304,9 @@ __device__ __forceinline__ uint32_t preprocess_one(int64_t i, const SceneView& s
     // parallelogram directions: normals of the projected local x and y axes
     screen_normal(cp, muc, W[0], W[3], W[6], bx.n1x, bx.n1y);
     screen_normal(cp, muc, W[1], W[4], W[7], bx.n2x, bx.n2y);
-    bx.pcx = (float)((double)cp.fx * ((double)muc[0] / (double)muc[2]) + (double)cp.cx);
-    bx.pcy = (float)((double)cp.fy * ((double)muc[1] / (double)muc[2]) + (double)cp.cy);
+    // reference point of the spans (FP32; its rounding, ~1e-4 px, is inside the slab padding)
+    bx.pcx = cp.fx * (muc[0] / muc[2]) + cp.cx;
+    bx.pcy = cp.fy * (muc[1] / muc[2]) + cp.cy;
     float P[8][3];
     bool in[8];
 #pragma unroll
@@ -296,17 +352,15 @@ __device__ __forceinline__ uint32_t preprocess_one(int64_t i, const SceneView& s
   rect[i] = rc;
   if (!cnt) return 0u;
 
-  // --- projected state (ordinary FP32/FP64 arithmetic) ---------------------------
+  // --- projected state (ordinary FP32 arithmetic; FP64 is slow on this GPU) -------
   const float zmu = muc[2];
-  const double iz = 1.0 / (double)zmu;
-  const double pcx = (double)cp.fx * ((double)muc[0] * iz) + (double)cp.cx;
-  const double pcy = (double)cp.fy * ((double)muc[1] * iz) + (double)cp.cy;
-  const float pcx_hi = (float)pcx, pcy_hi = (float)pcy;
-  const float pcx_lo = (float)(pcx - (double)pcx_hi), pcy_lo = (float)(pcy - (double)pcy_hi);
+  const float iz = 1.f / zmu;
+  float pcx_hi, pcx_lo, pcy_hi, pcy_lo;
+  centre_df(muc[0], zmu, cp.fx, cp.cx, pcx_hi, pcx_lo);
+  centre_df(muc[1], zmu, cp.fy, cp.cy, pcy_hi, pcy_lo);
   float g[3];
 #pragma unroll
-  for (int c = 0; c < 3; ++c)
-    g[c] = (float)(((double)W[c] * muc[0] + (double)W[3 + c] * muc[1] + (double)W[6 + c] * muc[2]) * iz);
+  for (int c = 0; c < 3; ++c) g[c] = fmaf(W[c], muc[0], fmaf(W[3 + c], muc[1], W[6 + c] * zmu)) * iz;
   const float3 p1 = slab_of(bx.n1x, bx.n1y, bx.s1min, bx.s1max);
   const float3 p2 = slab_of(bx.n2x, bx.n2y, bx.s2min, bx.s2max);
 
@@ -332,7 +386,7 @@ __device__ __forceinline__ uint32_t preprocess_one(int64_t i, const SceneView& s
   PrimState ps;
   ps.f[0] = make_float4(p1.x, p1.y, p1.z, p2.x);
   ps.f[1] = make_float4(pcx_hi, pcx_lo, pcy_hi, pcy_lo);
-  ps.f[2] = make_float4(p2.y, p2.z, (float)iz, zmu);
+  ps.f[2] = make_float4(p2.y, p2.z, iz, zmu);
   ps.f[3] = make_float4(W[0], W[3], W[1], W[4]);
   ps.f[4] = make_float4(W[2], W[5], g[0], g[1]);
   ps.f[5] = make_float4(g[2], ab.x, ab.y, op);
