@@ -927,7 +927,7 @@ qgs_status render_backward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camer
   GradView gv{grad->mean, grad->quat, grad->scale, grad->curv, grad->opacity, grad->sh};
   const int64_t nb = ctx->vis_list ? ctx->n_visible : N;
   if (nb > 0)
-    k_preprocess_bwd<<<nblk(nb), 256, 0, st>>>(nb, ctx->vis_list, sv, cp, ctx->count.p, ctx->pgrad.p,
+    k_preprocess_bwd<<<nblk(nb, 128), 128, 0, st>>>(nb, ctx->vis_list, sv, cp, ctx->count.p, ctx->pgrad.p,
                                                ctx->pgrad_by_pos, gv);
   ++launch_counter();
   QGS_CU(cudaGetLastError(), "k_preprocess_bwd");

@@ -396,7 +396,7 @@ __device__ __forceinline__ uint32_t preprocess_one(int64_t i, const SceneView& s
   return cnt;
 }
 
-__global__ void __launch_bounds__(256) k_preprocess_bwd(int64_t n, const uint32_t* __restrict__ list, SceneView sc,
+__global__ void __launch_bounds__(128, 4) k_preprocess_bwd(int64_t n, const uint32_t* __restrict__ list, SceneView sc,
                                                         CamParams cp, const uint32_t* __restrict__ count,
                                                         const float* __restrict__ pgrad, bool pgrad_by_pos,
                                                         GradView gd) {
