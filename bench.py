@@ -54,7 +54,7 @@ B_PRE_PRIM, B_PRE_VIS = 164, 128
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, summary under profiles/),
 # valid only while the kernels' sources hash to the recorded value.
 TRAFFIC_SRC = ("paper_2411_16392_gb300/csrc/raster.cu", "paper_2411_16392_gb300/csrc/qgs_common.cuh")
-TRAFFIC = {"hash": "4050c0e82b1a4bd9", "k_raster_fwd": 20106752 + 2951424, "k_raster_bwd": 66314496 + 136192}
+TRAFFIC = {"hash": "ee5f5b9dd22cca0e", "k_raster_fwd": 20117504 + 3080448, "k_raster_bwd": 66375168 + 101888}
 B_BIN_VIS, B_BIN_INST = 4 * 20 + 256, 4 + 2 * 12 + 4
 B_PREBWD_VIS = 80 + 144 + 480
 
