@@ -539,22 +539,45 @@ __device__ __forceinline__ float pair_grad(const PrimState& P, const Hit& h, flo
   return wgx;
 }
 
-// Butterfly reduce-scatter of 32 per-lane values across the warp: afterwards lane l
-// holds the warp-wide sum of component l.
-__device__ __forceinline__ float warp_transpose_sum(float v[32]) {
+// Reduce-scatter of the 20 gradient components across the warp in 21 shuffles (halving
+// the number of partial sums a lane holds at each butterfly stage: 20, 10, 5, 3|2, 2|1,
+// 1): afterwards 20 of the lanes each hold the warp-wide sum of one component, k, and the
+// others return k = -1.
+__device__ __forceinline__ float warp_reduce_scatter20(const float v[32], int& k) {
   const int lane = threadIdx.x & 31;
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2, b0 = lane & 1;
+  float r[10], s[5], t[3];
 #pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) {
-    const bool up = (lane & off) != 0;
-#pragma unroll
-    for (int k = 0; k < off; ++k) {
-      const float send = up ? v[k] : v[k + off];
-      const float keep = up ? v[k + off] : v[k];
-      v[k] = keep + __shfl_xor_sync(FULL, send, off);
-    }
+  for (int i = 0; i < 10; ++i) {  // 20 -> 10: lanes with bit 4 keep components 10..19
+    const float recv = __shfl_xor_sync(FULL, b4 ? v[i] : v[i + 10], 16);
+    r[i] = (b4 ? v[i + 10] : v[i]) + recv;
   }
-  return v[0];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {  // 10 -> 5
+    const float recv = __shfl_xor_sync(FULL, b3 ? r[i] : r[5 + i], 8);
+    s[i] = (b3 ? r[5 + i] : r[i]) + recv;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {  // 5 -> 3 (bit 2 clear) or 2 (bit 2 set)
+    const float send = b2 ? s[i] : (i < 2 ? s[3 + i] : 0.f);
+    const float recv = __shfl_xor_sync(FULL, send, 4);
+    t[i] = b2 ? (i < 2 ? s[3 + i] + recv : 0.f) : s[i] + recv;
+  }
+  const bool c3 = !b2;  // three partial sums held, else two
+  // 3 -> 2|1, 2 -> 1|1
+  const float recv1 = __shfl_xor_sync(FULL, b1 ? t[0] : (c3 ? t[2] : t[1]), 2);
+  const float recv2 = __shfl_xor_sync(FULL, (b1 && c3) ? t[1] : 0.f, 2);
+  const float u0 = (b1 ? (c3 ? t[2] : t[1]) : t[0]) + recv1;
+  const float u1 = (!b1 && c3) ? t[1] + recv2 : 0.f;
+  const bool two = !b1 && c3;  // two partial sums held, else one
+  // 2 -> 1|1, or the pair adds its single partial sums (the lane with bit 0 clear owns it)
+  const float recv = __shfl_xor_sync(FULL, two ? (b0 ? u0 : u1) : u0, 1);
+  const float out = two ? (b0 ? u1 + recv : u0 + recv) : u0 + recv;
+  const int base = (b4 ? 10 : 0) + (b3 ? 5 : 0) + (b2 ? 3 : 0) + (b1 ? (c3 ? 2 : 1) : 0);
+  k = two ? base + (b0 ? 1 : 0) : (b0 ? -1 : base);
+  return out;
 }
+
 
 }  // namespace
 
@@ -636,10 +659,10 @@ __global__ void __launch_bounds__(BLOCK, 3)
 #pragma unroll
           for (int k = 0; k < NGRAD; ++k) v[k] = 0.f;
         }
-        const float r = warp_transpose_sum(v);
-        const int lane = threadIdx.x & 31;
-        if (lane < NGRAD && r != 0.f) atomicAdd(&sg[j][lane], r);
-        if (lane == 0) sflag[j] = 1;
+        int kc;
+        const float r = warp_reduce_scatter20(v, kc);
+        if (kc >= 0 && r != 0.f) atomicAdd(&sg[j][kc], r);
+        if ((threadIdx.x & 31) == 0) sflag[j] = 1;
       }
     }
     __syncthreads();
