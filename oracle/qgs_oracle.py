@@ -97,6 +97,46 @@ class Binning:
     pix_bbox: np.ndarray    # float32 [N, 4] (xmin, xmax, ymin, ymax) in pixels
     order: str = "centre"   # "centre": key = centre depth; "hit": per-tile hit depth
     geo: dict | None = None  # float32 mu_c, W, a, b, camera (for per-tile hit keys)
+    slabs: dict | None = None  # float32 screen parallelogram per primitive (tile test)
+
+
+def _rect_tiles(rect, prims):
+    """(primitive, tx, ty) of every tile of the primitives' rectangles, row-major."""
+    prims = np.asarray(prims, np.int64)
+    w = (rect[prims, 1] - rect[prims, 0] + 1).astype(np.int64)
+    h = (rect[prims, 3] - rect[prims, 2] + 1).astype(np.int64)
+    n = w * h
+    p = np.repeat(prims, n)
+    e = np.arange(int(n.sum())) - np.repeat(np.cumsum(n) - n, n)
+    ww = np.repeat(w, n)
+    return p, rect[p, 0] + e % ww, rect[p, 2] + e // ww
+
+
+def _tile_pass(sl, p, tx, ty):
+    """Whether tile (tx, ty) meets primitive p's screen parallelogram: the two slabs
+    |n_k . (x - c)| within [smin_k, smax_k] (spans of the projected support box along the
+    normals of the projected local axes, from the projected centre c) against the range
+    of n_k . (x - c) over the tile's pixel centres, padded by 2e-3 px + 1e-5 of the span
+    ends for rounding. FP32, correctly rounded, in the order written (the kernels follow
+    the same specification)."""
+    f = np.float32
+    half = f(0.5)
+    x0 = (16 * tx).astype(f) + half
+    x1 = np.minimum(16 * tx + 15, sl["img_w"] - 1).astype(f) + half
+    y0 = (16 * ty).astype(f) + half
+    y1 = np.minimum(16 * ty + 15, sl["img_h"] - 1).astype(f) + half
+    a0, a1 = x0 - sl["uc"][p], x1 - sl["uc"][p]
+    b0, b1 = y0 - sl["vc"][p], y1 - sl["vc"][p]
+    ok = np.ones(p.shape, bool)
+    for k in ("1", "2"):
+        nx, ny = sl["n" + k + "x"][p], sl["n" + k + "y"][p]
+        smin, smax = sl["s" + k + "min"][p], sl["s" + k + "max"][p]
+        e = [nx * a + ny * b for a in (a0, a1) for b in (b0, b1)]
+        lo = np.minimum(np.minimum(e[0], e[1]), np.minimum(e[2], e[3]))
+        hi = np.maximum(np.maximum(e[0], e[1]), np.maximum(e[2], e[3]))
+        pad = f(2e-3) + f(1e-5) * (np.abs(smin) + np.abs(smax))
+        ok &= ~(hi < smin - pad) & ~(lo > smax + pad)
+    return ok
 
 
 def hit_keys(binning: Binning, prims: np.ndarray, tile: int) -> np.ndarray:
@@ -237,6 +277,25 @@ def bin_fp32(scene, cam, emit: bool = True, order: str = "centre") -> Binning:
         ymin = np.full(N, inf, f)
         ymax = np.full(N, -inf, f)
         anyp = np.zeros(N, bool)
+        # screen parallelogram: spans of the projected points along the normals of the
+        # projected local x and y axes, measured from the projected centre (uc, vc)
+        uc = fx * (muc[0] / muc[2]) + cx
+        vc = fy * (muc[1] / muc[2]) + cy
+
+        def axis_normal(a):
+            du = fx * (Wm[0][a] * muc[2] - muc[0] * Wm[2][a])
+            dv = fy * (Wm[1][a] * muc[2] - muc[1] * Wm[2][a])
+            l2 = du * du + dv * dv
+            l = np.sqrt(l2)
+            ok = (l2 > zero) & np.isfinite(l2)
+            return np.where(ok, -(dv / l), one), np.where(ok, du / l, zero)
+
+        n1x, n1y = axis_normal(0)
+        n2x, n2y = axis_normal(1)
+        s1min = np.full(N, inf, f)
+        s1max = np.full(N, -inf, f)
+        s2min = np.full(N, inf, f)
+        s2max = np.full(N, -inf, f)
 
         def add_point(mask, px, py, pz):
             u = fx * (px / pz) + cx
@@ -245,6 +304,13 @@ def bin_fp32(scene, cam, emit: bool = True, order: str = "centre") -> Binning:
             xmax[mask] = np.maximum(xmax[mask], u[mask])
             ymin[mask] = np.minimum(ymin[mask], v[mask])
             ymax[mask] = np.maximum(ymax[mask], v[mask])
+            du_, dv_ = u - uc, v - vc
+            t1 = n1x * du_ + n1y * dv_
+            t2 = n2x * du_ + n2y * dv_
+            s1min[mask] = np.minimum(s1min[mask], t1[mask])
+            s1max[mask] = np.maximum(s1max[mask], t1[mask])
+            s2min[mask] = np.minimum(s2min[mask], t2[mask])
+            s2max[mask] = np.maximum(s2max[mask], t2[mask])
             anyp[mask] = True
 
         inside = [c[2] >= near for c in corners]
@@ -281,8 +347,25 @@ def bin_fp32(scene, cam, emit: bool = True, order: str = "centre") -> Binning:
         rect[vis, 1] = tx1[vis].astype(np.int32)
         rect[vis, 2] = ty0[vis].astype(np.int32)
         rect[vis, 3] = ty1[vis].astype(np.int32)
-        count = np.where(vis, (rect[:, 1] - rect[:, 0] + 1).astype(np.int64)
-                         * (rect[:, 3] - rect[:, 2] + 1), 0)
+        slabs = dict(n1x=n1x, n1y=n1y, s1min=s1min, s1max=s1max, n2x=n2x, n2y=n2y, s2min=s2min, s2max=s2max,
+                     uc=uc, vc=vc, img_w=cam.W, img_h=cam.H)
+        # tiles of the rectangle that meet the parallelogram (row-major), counted in chunks
+        count = np.zeros(N, np.int64)
+        vidx = np.nonzero(vis)[0]
+        per = ((rect[vidx, 1] - rect[vidx, 0] + 1).astype(np.int64) * (rect[vidx, 3] - rect[vidx, 2] + 1))
+        start = 0
+        while start < vidx.size:
+            stop = start + 1
+            tot = per[start]
+            while stop < vidx.size and tot + per[stop] <= 4_000_000:
+                tot += per[stop]
+                stop += 1
+            p_, tx_, ty_ = _rect_tiles(rect, vidx[start:stop])
+            ok = _tile_pass(slabs, p_, tx_, ty_)
+            count += np.bincount(p_[ok], minlength=N)
+            start = stop
+        vis &= count > 0
+        rect[~vis] = 0
         zbits = muc[2].astype(f).view(np.uint32).copy()
 
     pix_bbox = np.stack([xmin, xmax, ymin, ymax], 1).astype(np.float32)
@@ -292,18 +375,19 @@ def bin_fp32(scene, cam, emit: bool = True, order: str = "centre") -> Binning:
                    img_w=cam.W, img_h=cam.H)
     elif order != "centre":
         raise ValueError(order)
-    bn = Binning(vis, zbits, rect, count, None, None, None, TX, TY, pix_bbox, order, geo)
+    bn = Binning(vis, zbits, rect, count, None, None, None, TX, TY, pix_bbox, order, geo, slabs)
     if not emit:
         return bn
-    # instances in primitive order, tiles row-major inside each rectangle
+    # instances in primitive order, tiles row-major inside each rectangle (those that meet
+    # the parallelogram)
     I = int(count.sum())
     keys = np.empty(I, np.uint64)
     vals = np.empty(I, np.uint32)
     pos = 0
     for i in np.nonzero(count)[0]:
-        x0, x1, y0, y1 = rect[i]
-        ty, tx = np.meshgrid(np.arange(y0, y1 + 1), np.arange(x0, x1 + 1), indexing="ij")
-        tiles = (ty * TX + tx).reshape(-1)
+        p_, tx_, ty_ = _rect_tiles(rect, np.array([i]))
+        ok = _tile_pass(slabs, p_, tx_, ty_)
+        tiles = (ty_[ok] * TX + tx_[ok]).astype(np.int64)
         c = tiles.size
         if order == "hit":
             low = np.array([hit_keys(bn, np.array([i]), t)[0] for t in tiles], np.uint64)
@@ -320,7 +404,7 @@ def bin_fp32(scene, cam, emit: bool = True, order: str = "centre") -> Binning:
     starts = np.searchsorted(tiles_sorted, np.arange(ntiles), side="left")
     ends = np.searchsorted(tiles_sorted, np.arange(ntiles), side="right")
     ranges = np.stack([starts, ends], 1).astype(np.int64)
-    return Binning(vis, zbits, rect, count, keys, vals, ranges, TX, TY, pix_bbox, order, geo)
+    return Binning(vis, zbits, rect, count, keys, vals, ranges, TX, TY, pix_bbox, order, geo, slabs)
 
 
 def tile_list(binning: Binning, tile: int) -> np.ndarray:
@@ -329,6 +413,7 @@ def tile_list(binning: Binning, tile: int) -> np.ndarray:
     ty, tx = divmod(int(tile), binning.tiles_x)
     r = binning.rect
     sel = np.nonzero((binning.count > 0) & (r[:, 0] <= tx) & (tx <= r[:, 1]) & (r[:, 2] <= ty) & (ty <= r[:, 3]))[0]
+    sel = sel[_tile_pass(binning.slabs, sel, np.full(sel.shape, tx), np.full(sel.shape, ty))]
     depth = hit_keys(binning, sel, tile) if binning.order == "hit" else binning.zbits[sel]
     order = np.lexsort((sel, depth))
     return sel[order].astype(np.uint32)

@@ -525,8 +525,8 @@ def _brute_support(sc, cam):
 @pytest.mark.parametrize("inside,kappa", [(False, 1.0), (True, 1.0), (False, 4.0), (False, 0.0)])
 def test_screen_bound_is_conservative(inside, kappa):
     """Every pixel where a primitive has a hit within 3 sigma lies inside the primitive's
-    tile rectangle and inside its pixel AABB (box of the support, clipped to the near
-    plane). `inside` puts the camera among the primitives; `kappa` scales the curvatures
+    tile rectangle, inside its pixel AABB (box of the support, clipped to the near plane)
+    and in a tile that the screen-parallelogram test keeps in its list. `inside` puts the camera among the primitives; `kappa` scales the curvatures
     (4: |kappa| up to 20 as in the object scene, 0: planar)."""
     sc, cam = _small_scene(n=300, W=40, seed=11)
     sc.curv *= np.float32(kappa)
@@ -548,8 +548,16 @@ def test_screen_bound_is_conservative(inside, kappa):
         bb = b.pix_bbox[i]
         assert ((xs[hit] + 0.5 >= bb[0]) & (xs[hit] + 0.5 <= bb[1]) & (ys[hit] + 0.5 >= bb[2])
                 & (ys[hit] + 0.5 <= bb[3])).all(), i
+        # and inside the screen parallelogram: every tile with a hit pixel is listed
+        for t in np.unique(ty * b.tiles_x + tx):
+            s, e = b.ranges[t]
+            assert i in b.vals[s:e], (i, t)
         n_in += 1
     assert n_in > 50
+    # the parallelogram removes tiles the rectangle would list
+    full = int(sum((b.rect[i, 1] - b.rect[i, 0] + 1) * (b.rect[i, 3] - b.rect[i, 2] + 1)
+                   for i in range(sc.n) if b.visible[i]))
+    assert len(b.keys) < full
 
 
 def test_keys_are_tile_and_depth_bits():
