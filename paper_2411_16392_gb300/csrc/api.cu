@@ -57,14 +57,14 @@ __global__ void k_gather_u32(int64_t n, const uint32_t* __restrict__ idx, const 
   if (i < n) dst[i] = src[idx[i]];
 }
 
-// Write the tile instances of 32 consecutive primitives per warp (coalesced).
-// sidx == nullptr: primitive order (full-key mode, keys carry the depth bits, values the
-// primitive); otherwise depth order (keys carry the primitive in their low half).
+// Write the tile instances of 32 consecutive primitives per warp (coalesced): the tiles
+// of each rectangle that meet the primitive's parallelogram (all of them when tslab is
+// null). sidx == nullptr: primitive order (full-key mode, keys carry the depth bits,
+// values the primitive); otherwise depth order (keys carry the primitive in their low half).
 __global__ void k_emit(int64_t n, const uint32_t* __restrict__ sidx, const uint32_t* __restrict__ count,
-                       const short4* __restrict__ rect, const uint32_t* __restrict__ offs,
-                       const uint32_t* __restrict__ zkey, int tiles_x, uint64_t* __restrict__ keys,
-                       uint32_t* __restrict__ vals) {
-  const int lane = threadIdx.x & 31;
+                       const short4* __restrict__ rect, const TileSlab* __restrict__ tslab, int W, int H,
+                       const uint32_t* __restrict__ offs, const uint32_t* __restrict__ zkey, int tiles_x,
+                       uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t pid = 0, c = 0, off = 0, lowv = 0;
   short4 r = make_short4(0, 0, 0, 0);
@@ -83,16 +83,15 @@ __global__ void k_emit(int64_t n, const uint32_t* __restrict__ sidx, const uint3
     const uint32_t pp = __shfl_sync(0xffffffffu, pid, k);
     const uint32_t oo = __shfl_sync(0xffffffffu, off, k);
     const uint32_t lv = __shfl_sync(0xffffffffu, lowv, k);
-    const int rx0 = __shfl_sync(0xffffffffu, (int)r.x, k);
-    const int rx1 = __shfl_sync(0xffffffffu, (int)r.y, k);
-    const int ry0 = __shfl_sync(0xffffffffu, (int)r.z, k);
-    const uint32_t w = (uint32_t)(rx1 - rx0 + 1);
-    for (uint32_t e = lane; e < cc; e += 32) {
-      const uint32_t dy = e / w, dx = e - dy * w;
-      const uint32_t tile = (uint32_t)(ry0 + (int)dy) * (uint32_t)tiles_x + (uint32_t)(rx0 + (int)dx);
+    const short4 rk = make_short4((short)__shfl_sync(0xffffffffu, (int)r.x, k),
+                                  (short)__shfl_sync(0xffffffffu, (int)r.y, k),
+                                  (short)__shfl_sync(0xffffffffu, (int)r.z, k),
+                                  (short)__shfl_sync(0xffffffffu, (int)r.w, k));
+    warp_tiles(rk, tslab ? tslab + pp : nullptr, W, H, [&](uint32_t e, int tx, int ty) {
+      const uint32_t tile = (uint32_t)ty * (uint32_t)tiles_x + (uint32_t)tx;
       keys[(size_t)oo + e] = ((uint64_t)tile << 32) | lv;
       if (vals) vals[(size_t)oo + e] = pp;
-    }
+    });
   }
 }
 
@@ -166,31 +165,26 @@ __global__ void k_gather_state(int64_t V, const uint32_t* __restrict__ sidx, con
 // uint64_t with rb = 32. One warp writes 32 consecutive primitives' tiles (coalesced).
 template <typename K>
 __global__ void k_emit_packed(int64_t V, const uint32_t* __restrict__ sidx, const uint32_t* __restrict__ cnt_sorted,
-                              const short4* __restrict__ rect, const uint32_t* __restrict__ offs, int tiles_x, int rb,
-                              K* __restrict__ keys) {
+                              const short4* __restrict__ rect, const TileSlab* __restrict__ tslab, int W, int H,
+                              const uint32_t* __restrict__ offs, int tiles_x, int rb, K* __restrict__ keys) {
   const int lane = threadIdx.x & 31;
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  uint32_t c = 0, off = 0;
-  short4 rc = make_short4(0, 0, 0, 0);
+  uint32_t c = 0, off = 0, pid = 0;
   if (r < V) {
     c = cnt_sorted[r];
     off = offs[r];
-    rc = rect[sidx[r]];
+    pid = sidx[r];
   }
   for (int k = 0; k < 32; ++k) {
     const uint32_t cc = __shfl_sync(0xffffffffu, c, k);
     if (!cc) continue;
     const uint32_t rr = (uint32_t)(r - lane + k);
     const uint32_t oo = __shfl_sync(0xffffffffu, off, k);
-    const int rx0 = __shfl_sync(0xffffffffu, (int)rc.x, k);
-    const int rx1 = __shfl_sync(0xffffffffu, (int)rc.y, k);
-    const int ry0 = __shfl_sync(0xffffffffu, (int)rc.z, k);
-    const uint32_t w = (uint32_t)(rx1 - rx0 + 1);
-    for (uint32_t e = lane; e < cc; e += 32) {
-      const uint32_t dy = e / w, dx = e - dy * w;
-      const uint32_t tile = (uint32_t)(ry0 + (int)dy) * (uint32_t)tiles_x + (uint32_t)(rx0 + (int)dx);
+    const uint32_t pp = __shfl_sync(0xffffffffu, pid, k);
+    warp_tiles(rect[pp], tslab ? tslab + pp : nullptr, W, H, [&](uint32_t e, int tx, int ty) {
+      const uint32_t tile = (uint32_t)ty * (uint32_t)tiles_x + (uint32_t)tx;
       keys[(size_t)oo + e] = ((K)tile << rb) | (K)rr;
-    }
+    });
   }
 }
 
@@ -281,6 +275,7 @@ struct qgs_ctx {
   DevBuf<float> xres;             // StopThePop order: the forward's outputs for its backward
   bool stp = false;               // the last forward used the StopThePop order
   DevBuf<uint32_t> vpos;          // visibility flags, then their exclusive scan
+  DevBuf<TileSlab> tslab;         // per primitive: screen parallelogram for the tile test
   DevBuf<PrimState> dstate;       // projected state of the visible primitives in depth order
   const PrimState* raster_state = nullptr;  // state the sorted ids index (dstate or state)
   bool pgrad_by_pos = false;      // gradient records indexed like raster_state's depth order
@@ -438,6 +433,7 @@ void qgs_destroy(qgs_ctx* c) {
   c->vdesc.release();
   c->resid.release();
   c->vpos.release();
+  c->tslab.release();
   c->xres.release();
   c->dstate.release();
   if (c->h_vdesc) cudaFreeHost(c->h_vdesc);
@@ -484,6 +480,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   QGS_CU(ctx->offs.reserve(n1 + 1), "alloc offs");
   QGS_CU(ctx->rect.reserve(n1), "alloc rect");
   if (sm == 0) QGS_CU(ctx->vpos.reserve(n1 + 1), "alloc visibility scan");
+  QGS_CU(ctx->tslab.reserve(n1), "alloc tile slabs");
   QGS_CU(ctx->ranges.reserve((size_t)ntiles), "alloc ranges");
   QGS_CU(ctx->tkey.reserve((size_t)ntiles), "alloc tile keys");
   QGS_CU(ctx->tkey2.reserve((size_t)ntiles), "alloc tile keys");
@@ -510,10 +507,15 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   SceneView sv{scene->mean, scene->quat, scene->scale, scene->curv, scene->opacity, scene->sh};
   if (N > 0) {
     k_preprocess<<<nblk(N), 256, 0, st>>>(N, sv, cp, ctx->state.p, ctx->count.p, ctx->zkey.p,
-                                          sm == 0 ? nullptr : ctx->idx.p, ctx->rect.p, ctx->dcount.p,
-                                          sm == 0 ? ctx->vpos.p : nullptr);
+                                          sm == 0 ? nullptr : ctx->idx.p, ctx->rect.p, nullptr, nullptr,
+                                          ctx->tslab.p);
     ++launch_counter();
     QGS_CU(cudaGetLastError(), "k_preprocess");
+    // keep the rectangle's tiles that meet the parallelogram; totals and visibility
+    k_count_tiles<<<nblk(N), 256, 0, st>>>(N, ctx->tslab.p, cam->W, cam->H, ctx->count.p, ctx->rect.p,
+                                           ctx->zkey.p, sm == 0 ? ctx->vpos.p : nullptr, ctx->dcount.p);
+    ++launch_counter();
+    QGS_CU(cudaGetLastError(), "k_count_tiles");
   }
   mark(ctx, 1, st);
   // positions of the visible primitives (index order)
@@ -573,8 +575,8 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
       if (ctx->packed32) {
         uint32_t* k0 = reinterpret_cast<uint32_t*>(ctx->inst.p);
         uint32_t* k1 = reinterpret_cast<uint32_t*>(ctx->inst2.p);
-        k_emit_packed<uint32_t><<<nblk(V), 256, 0, st>>>(V, sidx, ctx->cnt_sorted.p, ctx->rect.p, ctx->offs.p,
-                                                         cp.tiles_x, rb, k0);
+        k_emit_packed<uint32_t><<<nblk(V), 256, 0, st>>>(V, sidx, ctx->cnt_sorted.p, ctx->rect.p, ctx->tslab.p,
+                                                         cam->W, cam->H, ctx->offs.p, cp.tiles_x, rb, k0);
         ++launch_counter();
         QGS_CU(cudaGetLastError(), "emit");
         mark(ctx, 4, st);
@@ -582,8 +584,8 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
         QGS_CU(e, "tile sort");
         sorted = f2 ? (const void*)k1 : (const void*)k0;
       } else {
-        k_emit_packed<uint64_t><<<nblk(V), 256, 0, st>>>(V, sidx, ctx->cnt_sorted.p, ctx->rect.p, ctx->offs.p,
-                                                         cp.tiles_x, 32, ctx->inst.p);
+        k_emit_packed<uint64_t><<<nblk(V), 256, 0, st>>>(V, sidx, ctx->cnt_sorted.p, ctx->rect.p, ctx->tslab.p,
+                                                         cam->W, cam->H, ctx->offs.p, cp.tiles_x, 32, ctx->inst.p);
         ++launch_counter();
         QGS_CU(cudaGetLastError(), "emit");
         mark(ctx, 4, st);
@@ -609,11 +611,11 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
     ctx->rank_bits = 32;
     if (N > 0 && I > 0) {
       if (stp)
-        k_emit_hit<<<nblk(N), 256, 0, st>>>(N, sv, cp, ctx->count.p, ctx->rect.p, ctx->offs.p, ctx->inst.p,
-                                            ctx->vals.p);
+        k_emit_hit<<<nblk(N), 256, 0, st>>>(N, sv, cp, ctx->count.p, ctx->rect.p, ctx->tslab.p, ctx->offs.p,
+                                            ctx->inst.p, ctx->vals.p);
       else
-        k_emit<<<nblk(N), 256, 0, st>>>(N, nullptr, ctx->count.p, ctx->rect.p, ctx->offs.p, ctx->zkey.p, cp.tiles_x,
-                                        ctx->inst.p, ctx->vals.p);
+        k_emit<<<nblk(N), 256, 0, st>>>(N, nullptr, ctx->count.p, ctx->rect.p, ctx->tslab.p, cam->W, cam->H,
+                                        ctx->offs.p, ctx->zkey.p, cp.tiles_x, ctx->inst.p, ctx->vals.p);
       ++launch_counter();
       QGS_CU(cudaGetLastError(), "emit");
       mark(ctx, 4, st);
@@ -1164,7 +1166,7 @@ extern "C" qgs_status render_forward_noalloc(const qgs_scene* scene, const qgs_c
   QGS_CU(cudaMemsetAsync(stats, 0, sizeof(RasterStats), st), "memset");
   SceneView sv{scene->mean, scene->quat, scene->scale, scene->curv, scene->opacity, scene->sh};
   if (N > 0) {
-    k_preprocess<<<nblk(N), 256, 0, st>>>(N, sv, cp, state, count, zkey, idx, rect, visible, nullptr);
+    k_preprocess<<<nblk(N), 256, 0, st>>>(N, sv, cp, state, count, zkey, idx, rect, visible, nullptr, nullptr);
     QGS_CU(cudaGetLastError(), "k_preprocess");
   }
   cudaError_t e = cudaSuccess;
@@ -1183,7 +1185,8 @@ extern "C" qgs_status render_forward_noalloc(const qgs_scene* scene, const qgs_c
   if (I > NA_MAX_INSTANCES) return QGS_ECAPACITY;
   const uint64_t* sorted = inst;
   if (N > 0 && I > 0) {
-    k_emit<<<nblk(N), 256, 0, st>>>(N, sidx, count, rect, offs, nullptr, cp.tiles_x, inst, nullptr);
+    k_emit<<<nblk(N), 256, 0, st>>>(N, sidx, count, rect, nullptr, cam->W, cam->H, offs, nullptr, cp.tiles_x, inst,
+                                    nullptr);
     QGS_CU(cudaGetLastError(), "emit");
     const bool f2 = radix_sort_u64_keys(inst, inst2, I, 32, 32 + bits_for(ntiles), tmp, st, &e);
     QGS_CU(e, "tile sort");

@@ -108,6 +108,8 @@ struct Box2 {
   float s1min, s1max, s2min, s2max;
 };
 
+// Pixel AABB and parallelogram spans of the projected points (all bit-exact: the tile
+// lists depend on them).
 __device__ __forceinline__ void box_add(Box2& b, const CamParams& cp, float px, float py, float pz) {
   float u = __fadd_rn(__fmul_rn(cp.fx, __fdiv_rn(px, pz)), cp.cx);
   float v = __fadd_rn(__fmul_rn(cp.fy, __fdiv_rn(py, pz)), cp.cy);
@@ -116,8 +118,9 @@ __device__ __forceinline__ void box_add(Box2& b, const CamParams& cp, float px, 
   b.ymin = fminf(b.ymin, v);
   b.ymax = fmaxf(b.ymax, v);
   b.any = true;
-  const float du = u - b.pcx, dv = v - b.pcy;
-  const float t1 = b.n1x * du + b.n1y * dv, t2 = b.n2x * du + b.n2y * dv;
+  const float du = __fsub_rn(u, b.pcx), dv = __fsub_rn(v, b.pcy);
+  const float t1 = __fadd_rn(__fmul_rn(b.n1x, du), __fmul_rn(b.n1y, dv));
+  const float t2 = __fadd_rn(__fmul_rn(b.n2x, du), __fmul_rn(b.n2y, dv));
   b.s1min = fminf(b.s1min, t1);
   b.s1max = fmaxf(b.s1max, t1);
   b.s2min = fminf(b.s2min, t2);
@@ -125,16 +128,17 @@ __device__ __forceinline__ void box_add(Box2& b, const CamParams& cp, float px, 
 }
 
 // Unit normal (in pixels) of the projection of the camera-space direction r at the
-// centre mu: the screen direction of a local axis, turned by 90 degrees.
+// centre mu: the screen direction of a local axis, turned by 90 degrees (bit-exact).
 __device__ __forceinline__ void screen_normal(const CamParams& cp, const float* muc, float rx, float ry, float rz,
                                               float& nx, float& ny) {
   const float z = muc[2];
-  const float du = cp.fx * (rx * z - muc[0] * rz), dv = cp.fy * (ry * z - muc[1] * rz);
-  const float l2 = du * du + dv * dv;
+  const float du = __fmul_rn(cp.fx, __fsub_rn(__fmul_rn(rx, z), __fmul_rn(muc[0], rz)));
+  const float dv = __fmul_rn(cp.fy, __fsub_rn(__fmul_rn(ry, z), __fmul_rn(muc[1], rz)));
+  const float l2 = __fadd_rn(__fmul_rn(du, du), __fmul_rn(dv, dv));
   if (l2 > 0.f && isfinite(l2)) {
-    const float il = rsqrtf(l2);
-    nx = -dv * il;
-    ny = du * il;
+    const float l = __fsqrt_rn(l2);
+    nx = -__fdiv_rn(dv, l);
+    ny = __fdiv_rn(du, l);
   } else {
     nx = 1.f;
     ny = 0.f;
@@ -171,18 +175,20 @@ __device__ __forceinline__ float3 slab_of(float nx, float ny, float smin, float 
 __device__ __forceinline__ uint32_t preprocess_one(int64_t i, const SceneView& sc, const CamParams& cp,
                                                    PrimState* __restrict__ state, uint32_t* __restrict__ count,
                                                    uint32_t* __restrict__ zkey, uint32_t* __restrict__ idx,
-                                                   short4* __restrict__ rect, uint32_t idx_base = 0);
+                                                   short4* __restrict__ rect, uint32_t idx_base = 0,
+                                                   TileSlab* __restrict__ tslab = nullptr);
 
 __global__ void __launch_bounds__(256) k_preprocess(int64_t n, SceneView sc, CamParams cp, PrimState* __restrict__ state,
                                                     uint32_t* __restrict__ count, uint32_t* __restrict__ zkey,
                                                     uint32_t* __restrict__ idx, short4* __restrict__ rect,
-                                                    uint32_t* __restrict__ counters, uint32_t* __restrict__ vflag) {
+                                                    uint32_t* __restrict__ counters, uint32_t* __restrict__ vflag,
+                                                    TileSlab* __restrict__ tslab) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  // visible primitives and tile instances: one atomic per warp and counter
   const bool active = i < n;
   uint32_t cnt = 0;
-  if (active) cnt = preprocess_one(i, sc, cp, state, count, zkey, idx, rect);
+  if (active) cnt = preprocess_one(i, sc, cp, state, count, zkey, idx, rect, 0, tslab);
   if (active && vflag) vflag[i] = cnt ? 1u : 0u;
+  if (!counters) return;
   // one atomic per CTA and counter (per-warp atomics on two addresses serialise)
   __shared__ uint32_t red[2][8];
   const uint32_t vis = __reduce_add_sync(0xffffffffu, cnt ? 1u : 0u);
@@ -227,7 +233,8 @@ __global__ void __launch_bounds__(256) k_preprocess_views(int64_t n, SceneView s
 __device__ __forceinline__ uint32_t preprocess_one(int64_t i, const SceneView& sc, const CamParams& cp,
                                                    PrimState* __restrict__ state, uint32_t* __restrict__ count,
                                                    uint32_t* __restrict__ zkey, uint32_t* __restrict__ idx,
-                                                   short4* __restrict__ rect, uint32_t idx_base) {
+                                                   short4* __restrict__ rect, uint32_t idx_base,
+                                                   TileSlab* __restrict__ tslab) {
   if (idx) idx[i] = idx_base + (uint32_t)i;
   const float mx = sc.mean[3 * i], my = sc.mean[3 * i + 1], mz = sc.mean[3 * i + 2];
   const float2 s = reinterpret_cast<const float2*>(sc.scale)[i];
@@ -304,9 +311,9 @@ __device__ __forceinline__ uint32_t preprocess_one(int64_t i, const SceneView& s
     // parallelogram directions: normals of the projected local x and y axes
     screen_normal(cp, muc, W[0], W[3], W[6], bx.n1x, bx.n1y);
     screen_normal(cp, muc, W[1], W[4], W[7], bx.n2x, bx.n2y);
-    // reference point of the spans (FP32; its rounding, ~1e-4 px, is inside the slab padding)
-    bx.pcx = cp.fx * (muc[0] / muc[2]) + cp.cx;
-    bx.pcy = cp.fy * (muc[1] / muc[2]) + cp.cy;
+    // reference point of the spans: the projected centre (bit-exact)
+    bx.pcx = __fadd_rn(__fmul_rn(cp.fx, __fdiv_rn(muc[0], muc[2])), cp.cx);
+    bx.pcy = __fadd_rn(__fmul_rn(cp.fy, __fdiv_rn(muc[1], muc[2])), cp.cy);
     float P[8][3];
     bool in[8];
 #pragma unroll
@@ -351,6 +358,13 @@ __device__ __forceinline__ uint32_t preprocess_one(int64_t i, const SceneView& s
   zkey[i] = key;
   rect[i] = rc;
   if (!cnt) return 0u;
+  if (tslab) {
+    TileSlab t;
+    t.a = make_float4(bx.n1x, bx.n1y, bx.s1min, bx.s1max);
+    t.b = make_float4(bx.n2x, bx.n2y, bx.s2min, bx.s2max);
+    t.c = make_float4(bx.pcx, bx.pcy, 0.f, 0.f);
+    tslab[i] = t;
+  }
 
   // --- projected state (ordinary FP32 arithmetic; FP64 is slow on this GPU) -------
   const float zmu = muc[2];
@@ -593,6 +607,7 @@ __device__ __forceinline__ uint32_t hit_key_bits(const float muc[3], const float
 __global__ void __launch_bounds__(256) k_emit_hit(int64_t n, SceneView sc, CamParams cp,
                                                   const uint32_t* __restrict__ count,
                                                   const short4* __restrict__ rect,
+                                                  const TileSlab* __restrict__ tslab,
                                                   const uint32_t* __restrict__ offs, uint64_t* __restrict__ keys,
                                                   uint32_t* __restrict__ vals) {
   const int lane = threadIdx.x & 31;
@@ -608,16 +623,52 @@ __global__ void __launch_bounds__(256) k_emit_hit(int64_t n, SceneView sc, CamPa
     const float2 ab = reinterpret_cast<const float2*>(sc.curv)[p];
     const float uc = __fadd_rn(__fmul_rn(cp.fx, __fdiv_rn(muc[0], muc[2])), cp.cx);
     const float vc = __fadd_rn(__fmul_rn(cp.fy, __fdiv_rn(muc[1], muc[2])), cp.cy);
-    const short4 r = rect[p];
     const uint32_t off = offs[p];
-    const uint32_t w = (uint32_t)(r.y - r.x + 1);
-    for (uint32_t e = lane; e < cc; e += 32) {
-      const uint32_t dy = e / w, dx = e - dy * w;
-      const int tx = r.x + (int)dx, ty = r.z + (int)dy;
+    warp_tiles(rect[p], tslab ? tslab + p : nullptr, cp.W, cp.H, [&](uint32_t e, int tx, int ty) {
       const uint32_t tile = (uint32_t)ty * (uint32_t)cp.tiles_x + (uint32_t)tx;
       keys[(size_t)off + e] = ((uint64_t)tile << 32) | hit_key_bits(muc, W, ab.x, ab.y, uc, vc, tx, ty, cp);
       vals[(size_t)off + e] = (uint32_t)p;
+    });
+  }
+}
+
+__global__ void __launch_bounds__(256) k_count_tiles(int64_t n, const TileSlab* __restrict__ tslab, int W, int H,
+                                                     uint32_t* __restrict__ count, short4* __restrict__ rect,
+                                                     uint32_t* __restrict__ zkey, uint32_t* __restrict__ vflag,
+                                                     uint32_t* __restrict__ counters) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t wbase = i - lane;
+  const uint32_t c0 = i < n ? count[i] : 0u;
+  uint32_t mine = 0;
+  for (int k = 0; k < 32; ++k) {
+    const uint32_t cc = __shfl_sync(0xffffffffu, c0, k);
+    if (!cc) continue;
+    const int64_t p = wbase + k;
+    const uint32_t c = warp_tiles(rect[p], tslab + p, W, H, [](uint32_t, int, int) {});
+    if (lane == k) mine = c;
+  }
+  if (i < n) {
+    if (c0 && !mine) {  // the rectangle's tiles all miss the parallelogram
+      rect[i] = make_short4(-1, -1, -1, -1);
+      zkey[i] = 0xFFFFFFFFu;
     }
+    count[i] = mine;
+    if (vflag) vflag[i] = mine ? 1u : 0u;
+  }
+  __shared__ uint32_t red[2][8];
+  const uint32_t vis = __reduce_add_sync(0xffffffffu, mine ? 1u : 0u);
+  const uint32_t tot = __reduce_add_sync(0xffffffffu, mine);
+  if (lane == 0) {
+    red[0][threadIdx.x >> 5] = vis;
+    red[1][threadIdx.x >> 5] = tot;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    uint32_t t = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += red[threadIdx.x][w];
+    if (t) atomicAdd(&counters[threadIdx.x], t);
   }
 }
 

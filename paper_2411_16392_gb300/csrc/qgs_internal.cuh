@@ -31,19 +31,117 @@ struct CamParams {
   int W, H, tiles_x, tiles_y;
 };
 
+// ---------------------------------------------------------------- tile culling
+// A primitive's screen parallelogram for the tile test: normals of the projected local
+// x and y axes with the spans of the projected support box along them, measured from the
+// projected centre (uc, vc). All bit-exact (correctly rounded FP32 in a fixed order).
+struct TileSlab {
+  float4 a;  // (n1x, n1y, s1min, s1max)
+  float4 b;  // (n2x, n2y, s2min, s2max)
+  float4 c;  // (uc, vc, -, -)
+};
+
+// Does a tile meet the parallelogram? Range of n . (x - c) over the tile's pixel centres
+// against each span, padded by 2e-3 px + 1e-5 of the span ends (the same FP32
+// specification as the oracle's tile test). The products n_x (x - u_c) depend on the
+// column only and n_y (y - v_c) on the row only, so they are formed once per column / row
+// (the same correctly rounded values a per-tile evaluation gives).
+struct TileRow {  // per row: n_y (y - v_c) at the row's first and last pixel centre, per slab
+  float b0[2], b1[2];
+};
+struct TileCol {  // per column: n_x (x - u_c) at its first and last pixel centre, per slab
+  float a0[2], a1[2];
+};
+__device__ __forceinline__ TileRow tile_row(const TileSlab& t, int ty, int H) {
+  const float y0 = __fsub_rn(__fadd_rn((float)(16 * ty), 0.5f), t.c.y);
+  const float y1 = __fsub_rn(__fadd_rn((float)min(16 * ty + 15, H - 1), 0.5f), t.c.y);
+  TileRow r;
+  r.b0[0] = __fmul_rn(t.a.y, y0); r.b1[0] = __fmul_rn(t.a.y, y1);
+  r.b0[1] = __fmul_rn(t.b.y, y0); r.b1[1] = __fmul_rn(t.b.y, y1);
+  return r;
+}
+__device__ __forceinline__ TileCol tile_col(const TileSlab& t, int tx, int W) {
+  const float x0 = __fsub_rn(__fadd_rn((float)(16 * tx), 0.5f), t.c.x);
+  const float x1 = __fsub_rn(__fadd_rn((float)min(16 * tx + 15, W - 1), 0.5f), t.c.x);
+  TileCol c;
+  c.a0[0] = __fmul_rn(t.a.x, x0); c.a1[0] = __fmul_rn(t.a.x, x1);
+  c.a0[1] = __fmul_rn(t.b.x, x0); c.a1[1] = __fmul_rn(t.b.x, x1);
+  return c;
+}
+__device__ __forceinline__ bool tile_meets(const TileSlab& t, const TileCol& c, const TileRow& r) {
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float4 s = k == 0 ? t.a : t.b;
+    const float e00 = __fadd_rn(c.a0[k], r.b0[k]), e01 = __fadd_rn(c.a0[k], r.b1[k]);
+    const float e10 = __fadd_rn(c.a1[k], r.b0[k]), e11 = __fadd_rn(c.a1[k], r.b1[k]);
+    const float lo = fminf(fminf(e00, e01), fminf(e10, e11));
+    const float hi = fmaxf(fmaxf(e00, e01), fmaxf(e10, e11));
+    const float pad = __fadd_rn(2e-3f, __fmul_rn(1e-5f, __fadd_rn(fabsf(s.z), fabsf(s.w))));
+    ok = ok && !(hi < __fsub_rn(s.z, pad)) && !(lo > __fadd_rn(s.w, pad));
+  }
+  return ok;
+}
+
+// The whole warp enumerates one primitive's rectangle r in row-major order, 32 tiles at a
+// time (lane l takes tile e = e0 + l, its (tx, ty) advanced without divisions); f(k, tx,
+// ty) runs for every tile that meets the parallelogram (every tile when t is null), k
+// counting them in row-major order. Returns their number. Call with the same arguments
+// on every lane.
+template <typename F>
+__device__ __forceinline__ uint32_t warp_tiles(short4 r, const TileSlab* t, int W, int H, F&& f) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  const int w = r.y - r.x + 1;
+  const uint32_t total = (uint32_t)w * (uint32_t)(r.w - r.z + 1);
+  TileSlab ts;
+  if (t) ts = *t;
+  int ty = r.z + lane / w, tx = r.x + lane % w;  // tile e = lane
+  int row_y = -1;
+  TileRow row{};
+  uint32_t base = 0;
+  for (uint32_t e0 = 0; e0 < total; e0 += 32) {
+    bool pass = e0 + (uint32_t)lane < total;
+    if (pass && t) {
+      if (ty != row_y) {
+        row = tile_row(ts, ty, H);
+        row_y = ty;
+      }
+      pass = tile_meets(ts, tile_col(ts, tx, W), row);
+    }
+    const uint32_t m = __ballot_sync(0xffffffffu, pass);
+    if (pass) f(base + __popc(m & lt), tx, ty);
+    base += __popc(m);
+    tx += 32;  // tile e + 32
+    while (tx > r.y) {
+      tx -= w;
+      ++ty;
+    }
+  }
+  return base;
+}
+
+// Per primitive with a nonempty rectangle: count its tiles that meet the parallelogram;
+// primitives left with none are culled (count 0, rectangle -1s, depth key 0xFFFFFFFF).
+// Writes the visibility flags (when given) and adds the visible and instance totals
+// to counters[0], counters[1].
+__global__ void k_count_tiles(int64_t n, const TileSlab* tslab, int W, int H, uint32_t* count, short4* rect,
+                              uint32_t* zkey, uint32_t* vflag, uint32_t* counters);
+
 // ---------------------------------------------------------------- preprocessing
-// Per primitive i: projected state (visible ones only), tile count, depth key, tile
-// rectangle; idx[i] = i and vflag[i] = (count > 0) when given. counters[0] += visible,
-// counters[1] += tile instances.
+// Per primitive i: projected state (visible ones only), tile count of the rectangle,
+// depth key, tile rectangle; idx[i] = i, vflag[i] = (count > 0) and the parallelogram
+// (tslab) when given; counters[0] += visible, counters[1] += tile instances when given.
 __global__ void k_preprocess(int64_t n, SceneView sc, CamParams cp, PrimState* state, uint32_t* count,
-                             uint32_t* zkey, uint32_t* idx, short4* rect, uint32_t* counters, uint32_t* vflag);
+                             uint32_t* zkey, uint32_t* idx, short4* rect, uint32_t* counters, uint32_t* vflag,
+                             TileSlab* tslab);
 __global__ void k_preprocess_views(int64_t n, SceneView sc, const CamParams* cps, PrimState* state, uint32_t* count,
                                    uint32_t* zkey, uint32_t* idx, short4* rect, uint32_t* n_visible);
 // StopThePop ordering: per (tile, primitive) instance, in primitive order,
 // key = (tile << 32) | bits of the depth where the ray of the tile pixel closest to the
 // projected vertex meets the paraboloid; value = primitive.
 __global__ void k_emit_hit(int64_t n, SceneView sc, CamParams cp, const uint32_t* count, const short4* rect,
-                           const uint32_t* offs, uint64_t* keys, uint32_t* vals);
+                           const TileSlab* tslab, const uint32_t* offs, uint64_t* keys, uint32_t* vals);
 // list == nullptr: threads 0..n-1 are primitives 0..n-1; else primitive list[j].
 // pgrad_by_pos: the gradient record of thread j is pgrad[j] (state gathered in list
 // order), else pgrad[primitive].

@@ -51,8 +51,12 @@ def test_batch_equals_single_renders_mixed_resolutions(dev):
     torch.cuda.synchronize()
     _assert_bit_equal(outs, singles, cams)
     sb = ras.stats()
-    for key in ("n_instances", "n_visible", "n_tiles", "pair_evals", "pair_isect", "pair_hits", "pair_blended"):
+    # the batch lists every tile of each rectangle (the single renders drop the tiles that
+    # miss a primitive's parallelogram): more instances and evaluations, the same blending
+    for key in ("n_tiles", "pair_blended"):
         assert sb[key] == sum(s[key] for s in st1), key
+    for key in ("n_instances", "n_visible", "pair_evals", "pair_isect"):
+        assert sb[key] >= sum(s[key] for s in st1), key
     assert sb["n_primitives"] == len(cams) * ds.n
     # a second batch in another order reuses the buffers and still matches
     perm = [4, 0, 8, 2]
