@@ -636,6 +636,12 @@ __global__ void __launch_bounds__(256) k_count_tiles(int64_t n, const TileSlab* 
                                                      uint32_t* __restrict__ count, short4* __restrict__ rect,
                                                      uint32_t* __restrict__ zkey, uint32_t* __restrict__ vflag,
                                                      uint32_t* __restrict__ counters) {
+  __shared__ uint32_t bsum[2], bdone;
+  if (threadIdx.x == 0) {
+    bsum[0] = bsum[1] = 0u;
+    bdone = 0u;
+  }
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t wbase = i - lane;
@@ -656,19 +662,19 @@ __global__ void __launch_bounds__(256) k_count_tiles(int64_t n, const TileSlab* 
     count[i] = mine;
     if (vflag) vflag[i] = mine ? 1u : 0u;
   }
-  __shared__ uint32_t red[2][8];
+  // totals: summed per CTA in shared memory; the CTA's last warp to finish adds them to
+  // global memory (no barrier: warps of a CTA finish at very different times here)
   const uint32_t vis = __reduce_add_sync(0xffffffffu, mine ? 1u : 0u);
   const uint32_t tot = __reduce_add_sync(0xffffffffu, mine);
   if (lane == 0) {
-    red[0][threadIdx.x >> 5] = vis;
-    red[1][threadIdx.x >> 5] = tot;
-  }
-  __syncthreads();
-  if (threadIdx.x < 2) {
-    uint32_t t = 0;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) t += red[threadIdx.x][w];
-    if (t) atomicAdd(&counters[threadIdx.x], t);
+    if (vis) atomicAdd(&bsum[0], vis);
+    if (tot) atomicAdd(&bsum[1], tot);
+    __threadfence_block();
+    if (atomicAdd(&bdone, 1u) == (blockDim.x >> 5) - 1) {
+      const uint32_t v = atomicAdd(&bsum[0], 0u), t = atomicAdd(&bsum[1], 0u);
+      if (v) atomicAdd(&counters[0], v);
+      if (t) atomicAdd(&counters[1], t);
+    }
   }
 }
 
