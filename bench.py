@@ -54,7 +54,7 @@ B_PRE_PRIM, B_PRE_VIS = 164, 128
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, summary under profiles/),
 # valid only while the kernels' sources hash to the recorded value.
 TRAFFIC_SRC = ("paper_2411_16392_gb300/csrc/raster.cu", "paper_2411_16392_gb300/csrc/qgs_common.cuh")
-TRAFFIC = {"hash": "ee5f5b9dd22cca0e", "k_raster_fwd": 20117504 + 3080448, "k_raster_bwd": 66375168 + 101888}
+TRAFFIC = {"hash": "7ebac12d9bebcda8", "k_raster_fwd": 16483584 + 2670848, "k_raster_bwd": 61793280 + 32512}
 B_BIN_VIS, B_BIN_INST = 4 * 20 + 256, 4 + 2 * 12 + 4
 B_PREBWD_VIS = 80 + 144 + 480
 
