@@ -136,7 +136,120 @@ def _tile_pass(sl, p, tx, ty):
         hi = np.maximum(np.maximum(e[0], e[1]), np.maximum(e[2], e[3]))
         pad = f(2e-3) + f(1e-5) * (np.abs(smin) + np.abs(smax))
         ok &= ~(hi < smin - pad) & ~(lo > smax + pad)
+    if "qa" in sl:
+        ok &= _conic_pass(sl, p, a0, a1, b0, b1)
     return ok
+
+
+CONIC_KAPPA = 9.02     # squared radius of the padded chord ellipsoid (9 = 3 sigma squared)
+CONIC_SHIFT = 4e-6     # diagonal shift of the quadratic form, relative to its trace
+CONIC_DELTA = 2e-3     # absolute pad in pixels
+
+
+def ellipsoid_conic(muc, Wm, su, sv, m, fx, fy):
+    """Screen-space conic of the chord ellipsoid that holds the support (FP32 recipe).
+
+    Every point of the support has E + z^2/m^2 <= 9 (the inequality (*) of bin_fp32:
+    arc >= chord), i.e. it lies in the ellipsoid |S^-1 x_loc| <= 3 with S = diag(s_u,
+    s_v, m). A pixel ray can only meet the support if its line meets that ellipsoid.
+    In the scaled frame xi = S^-1 W^T (x - mu_c), with the camera at omega and the ray
+    direction delta = S^-1 W^T d, the line meets the ball |xi|^2 <= kappa iff
+    |omega x delta|^2 <= kappa |delta|^2. For a pixel at offset p from the projected
+    centre, d = mu_c / z + (p_x / f_x, p_y / f_y, 0), and the identity
+    (M a) x (M b) = det(M) M^-T (a x b) with M = S^-1 W^T turns the left side into
+    |p_x n_x + p_y n_y|^2 with n_x = S W^T (e_x x mu_c) / (f_x s_u s_v m), n_y likewise
+    (no cancellation: the camera-distance terms drop out exactly), while the right side
+    is kappa |delta_c + p_x h_x + p_y h_y|^2 with h_x = S^-1 W^T e_x / f_x. Hence
+        p^T Q p - 2 L.p <= K,   Q = Gram(n) - kappa Gram(h), L = kappa (delta_c.h), K = kappa |delta_c|^2.
+    Pads: kappa = 9.02 instead of 9 (FP32 rounding of the kernels' own hit test); Q's
+    diagonal lowered by CONIC_SHIFT x its trace (FP32 rounding of Q, which matters along
+    the long axis of an elongated ellipse); the normalised threshold raised so that the
+    ellipse grows by CONIC_DELTA pixels (the tile test measures offsets from the rounded
+    projected centre). The conic is enabled only when the padded Q is positive definite
+    (the ellipsoid lies in front of the camera plane); otherwise every pixel passes.
+    Returned (normalised so that the test reads F(p) = p^T q p - 2 l.p <= 1):
+    qa, qb, qc (q = [[qa, qb], [qb, qc]]), la, lb and the enable flag conic_on.
+    Correctly rounded FP32 operations in the order written (the kernels follow the same
+    specification bit for bit)."""
+    f = np.float32
+    zero, one, two = f(0.0), f(1.0), f(2.0)
+    s = (su, sv, m)
+    oth = (sv * m, su * m, su * sv)        # s_c / (s_u s_v m) = 1 / oth_c
+    nx = [((Wm[2][c] * muc[1] - Wm[1][c] * muc[2]) / fx) / oth[c] for c in range(3)]
+    ny = [((Wm[0][c] * muc[2] - Wm[2][c] * muc[0]) / fy) / oth[c] for c in range(3)]
+    hx = [(Wm[0][c] / fx) / s[c] for c in range(3)]
+    hy = [(Wm[1][c] / fy) / s[c] for c in range(3)]
+    dcx = muc[0] / muc[2]
+    dcy = muc[1] / muc[2]
+    dc = [((Wm[0][c] * dcx + Wm[1][c] * dcy) + Wm[2][c]) / s[c] for c in range(3)]
+
+    def dot(u, v):
+        return (u[0] * v[0] + u[1] * v[1]) + u[2] * v[2]
+
+    kap = f(CONIC_KAPPA)
+    G00, G01, G11 = dot(nx, nx), dot(nx, ny), dot(ny, ny)
+    H00, H01, H11 = dot(hx, hx), dot(hx, hy), dot(hy, hy)
+    tau = f(CONIC_SHIFT) * (G00 + G11)
+    Q00 = (G00 - kap * H00) - tau
+    Q01 = G01 - kap * H01
+    Q11 = (G11 - kap * H11) - tau
+    L0 = kap * dot(dc, hx)
+    L1 = kap * dot(dc, hy)
+    K = kap * dot(dc, dc)
+    det = Q00 * Q11 - Q01 * Q01
+    qa, qb, qc, la, lb = Q00 / K, Q01 / K, Q11 / K, L0 / K, L1 / K
+    dn = qa * qc - qb * qb
+    # R = 1 + l^T q^-1 l: (p - p0)^T q (p - p0) <= R is the same ellipse, p0 = q^-1 l
+    R0 = one + (((qc * la) * la - (two * (qb * la)) * lb) + (qa * lb) * lb) / dn
+    R = np.where(R0 > one, R0, one)
+    tr = qa + qc
+    dl = f(CONIC_DELTA)
+    # growing the ellipse by dl pixels raises F by at most 2 dl sqrt(lmax R) + dl^2 lmax
+    T = (one + (f(3.0) * dl) * np.sqrt(tr * R)) + ((two * dl) * dl) * tr
+    on = (np.isfinite(Q00) & np.isfinite(Q01) & np.isfinite(Q11) & np.isfinite(L0) & np.isfinite(L1)
+          & np.isfinite(K) & (K > zero) & (Q00 > zero) & (Q11 > zero) & (det > f(1e-6) * (Q00 * Q11))
+          & np.isfinite(T) & (dn > zero) & np.isfinite(R0))
+    out = {}
+    for k, v in (("qa", qa / T), ("qb", qb / T), ("qc", qc / T), ("la", la / T), ("lb", lb / T)):
+        out[k] = np.where(on, v, zero).astype(f)
+    out["conic_on"] = on & np.isfinite(out["qa"]) & np.isfinite(out["qb"]) & np.isfinite(out["qc"]) \
+        & np.isfinite(out["la"]) & np.isfinite(out["lb"]) & (out["qa"] > zero) & (out["qc"] > zero)
+    for k in ("qa", "qb", "qc", "la", "lb"):
+        out[k] = np.where(out["conic_on"], out[k], zero).astype(f)
+    return out
+
+
+def conic_value(sl, p, u, v):
+    """F(u, v) = u (qa u + 2 qb v - 2 la) + v (qc v - 2 lb) in the recipe's FP32 order."""
+    two = np.float32(2.0)
+    qa, qb, qc, la, lb = (sl[k][p] for k in ("qa", "qb", "qc", "la", "lb"))
+    return u * ((qa * u + two * (qb * v)) - two * la) + v * (qc * v - two * lb)
+
+
+def _conic_pass(sl, p, x0, x1, y0, y1):
+    """Whether the rectangle [x0, x1] x [y0, y1] of pixel-centre offsets from the projected
+    centre meets the conic F <= 1. F is convex (q positive definite), and F(0) <= 1 (the
+    ray through the projected centre meets the ellipsoid's centre), so the rectangle meets
+    the ellipse iff it holds the origin or the minimum of F over an edge facing the
+    ellipse is <= 1; the edge minima are the clamped stationary points of F along the
+    edge (a vertical edge when 0 is left or right of [x0, x1], a horizontal one when it
+    is above or below [y0, y1]). FP32, correctly rounded, in the order written."""
+    f = np.float32
+    zero, one = f(0.0), f(1.0)
+    qa, qb, qc, la, lb = (sl[k][p] for k in ("qa", "qb", "qc", "la", "lb"))
+    on = sl["conic_on"][p]
+    with np.errstate(all="ignore"):
+        inside = (x0 <= zero) & (zero <= x1) & (y0 <= zero) & (zero <= y1)
+        ue = np.where(x0 > zero, x0, x1)
+        has_u = (x0 > zero) | (x1 < zero)
+        vs = np.minimum(np.maximum((lb - qb * ue) / qc, y0), y1)
+        fu = conic_value(sl, p, ue, vs)
+        ve = np.where(y0 > zero, y0, y1)
+        has_v = (y0 > zero) | (y1 < zero)
+        us = np.minimum(np.maximum((la - qb * ve) / qa, x0), x1)
+        fv = conic_value(sl, p, us, ve)
+        meets = inside | (has_u & (fu <= one)) | (has_v & (fv <= one))
+    return ~on | meets
 
 
 def hit_keys(binning: Binning, prims: np.ndarray, tile: int) -> np.ndarray:
@@ -349,6 +462,7 @@ def bin_fp32(scene, cam, emit: bool = True, order: str = "centre") -> Binning:
         rect[vis, 3] = ty1[vis].astype(np.int32)
         slabs = dict(n1x=n1x, n1y=n1y, s1min=s1min, s1max=s1max, n2x=n2x, n2y=n2y, s2min=s2min, s2max=s2max,
                      uc=uc, vc=vc, img_w=cam.W, img_h=cam.H)
+        slabs.update(ellipsoid_conic(muc, Wm, su, sv, m, fx, fy))
         # tiles of the rectangle that meet the parallelogram (row-major), counted in chunks
         count = np.zeros(N, np.int64)
         vidx = np.nonzero(vis)[0]

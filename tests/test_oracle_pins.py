@@ -642,3 +642,128 @@ def test_sh_basis_orthonormal_and_matches_scipy():
             mine = Y[..., k]
             assert np.allclose(mine, ref, atol=1e-12) or np.allclose(mine, -ref, atol=1e-12), (l, m)
             k += 1
+
+
+# --------------------------------------------------------------------------- chord ellipsoid
+def test_support_lies_in_chord_ellipsoid():
+    """Every point of the support (geodesic distance <= 3 sigma(theta), Sec. 3.2) satisfies
+    x^2/s_u^2 + y^2/s_v^2 + z^2/m^2 <= 9 with m = max(s_u, s_v): the ellipsoid behind the
+    screen-space conic of the tile lists. Points sampled on the paraboloid in FP64 up to
+    the support's rim, for saddles, cups and elongated scales."""
+    rng = np.random.default_rng(4)
+    n = 4000
+    su, sv = np.exp(rng.uniform(np.log(1e-3), np.log(0.1), (2, n)))
+    a = rng.uniform(-10, 10, n) / su
+    b = rng.uniform(-10, 10, n) / sv
+    th = rng.uniform(0, 2 * np.pi, n)
+    c, s = np.cos(th), np.sin(th)
+    at = a * c * c + b * s * s
+    sig = O.sigma_theta(t64(th), t64(su), t64(sv)).numpy()
+    # the rim: l(a(theta), rho) = 3 sigma(theta), by bisection on rho (l increases with rho)
+    lo, hi = np.zeros(n), 3 * sig
+    for _ in range(80):
+        mid = 0.5 * (lo + hi)
+        l = O.arc_length(t64(at), t64(mid)).numpy()
+        lo, hi = np.where(l <= 3 * sig, mid, lo), np.where(l <= 3 * sig, hi, mid)
+    m = np.maximum(su, sv)
+    for frac in (1.0, 0.7, 0.3):
+        rho = lo * frac
+        x, y = rho * c, rho * s
+        z = a * x * x + b * y * y
+        v = x * x / su ** 2 + y * y / sv ** 2 + z * z / m ** 2
+        assert v.max() <= 9.0 * (1 + 1e-9), v.max()
+    assert v.max() > 0.5   # the rim is reached for some primitives
+
+
+def _ellipsoid_line_dist2(sc, cam, i, X, Y):
+    """Squared distance, in the frame scaled by (s_u, s_v, m), from the centre of primitive
+    i to the line through the camera centre and pixel position (X, Y): FP64, world
+    coordinates, by orthogonal projection (no use of the recipe's algebra)."""
+    R = O.quat_to_rot(t64(sc.quat[i:i + 1])).numpy()[0]
+    su, sv = sc.scale[i].astype(np.float64)
+    S = np.diag(1.0 / np.array([su, sv, max(su, sv)]))
+    Rcw = cam.R_cw.astype(np.float64)
+    c_w = -Rcw.T @ cam.t_cw.astype(np.float64)
+    d_cam = np.stack([(X - cam.cx) / cam.fx, (Y - cam.cy) / cam.fy, np.ones_like(X)], -1)
+    d = (S @ R.T @ (Rcw.T @ d_cam.T)).T                     # scaled local directions
+    o = S @ R.T @ (c_w - sc.mean[i].astype(np.float64))    # scaled local camera centre
+    t = -(d @ o) / np.einsum("ij,ij->i", d, d)              # closest point on the line
+    p = o[None, :] + t[:, None] * d
+    return np.einsum("ij,ij->i", p, p)
+
+
+@pytest.mark.parametrize("kappa,aspect", [(1.0, False), (4.0, True), (0.0, True)])
+def test_conic_is_the_projected_chord_ellipsoid(kappa, aspect):
+    """The FP32 conic F(p) <= 1 holds every pixel whose ray line meets the chord ellipsoid
+    (squared scaled distance <= 9) and is no looser than the recipe's pads (9.02 radius
+    squared, a 2e-3 px rim and the diagonal shift, which grows with the ellipse's
+    elongation): pixels with F <= 1 have squared distance <= 9.1 (9.3 with scale ratios up
+    to 50) where the projected ellipse covers a dozen pixel centres or more."""
+    sc, cam = _small_scene(n=300, W=64, seed=5)
+    sc.curv *= np.float32(kappa)
+    if aspect:   # elongated primitives: ratio of scales up to 50
+        sc.scale[:, 1] = (sc.scale[:, 0] * np.exp(np.random.default_rng(2).uniform(-np.log(50), np.log(50), sc.n))
+                          ).astype(np.float32)
+    b = O.bin_fp32(sc, cam, emit=False)
+    sl = b.slabs
+    ys, xs = np.meshgrid(np.arange(-8, cam.H + 8), np.arange(-8, cam.W + 8), indexing="ij")
+    X, Y = xs.reshape(-1) + 0.5, ys.reshape(-1) + 0.5
+    n_on = n_tight = 0
+    for i in np.nonzero(b.visible)[0]:
+        d2 = _ellipsoid_line_dist2(sc, cam, i, X, Y)
+        if not sl["conic_on"][i]:
+            continue
+        n_on += 1
+        p = np.full(X.shape, i)
+        u = (X.astype(np.float32) - sl["uc"][i]).astype(np.float32)
+        v = (Y.astype(np.float32) - sl["vc"][i]).astype(np.float32)
+        F = O.conic_value(sl, p, u, v).astype(np.float64)
+        assert np.all(F[d2 <= 9.0] <= 1.0), i
+        if (d2 <= 9.0).sum() >= 12:
+            assert d2[F <= 1.0].max() <= (9.3 if aspect else 9.1), (i, d2[F <= 1.0].max())
+            n_tight += 1
+    assert n_on >= 0.9 * b.visible.sum() and n_tight > 20
+
+
+def test_conic_tile_test_against_the_rectangle():
+    """The conic part of the tile test (edges of the rectangle of pixel-centre offsets,
+    clamped stationary points) against a direct minimisation of F over the rectangle:
+    a fine grid refined by a bounded quasi-Newton search (FP64). Tiles whose minimum is
+    below 1 - 1e-6 pass, tiles whose minimum is above 1 + 1e-6 fail."""
+    sc, cam = _small_scene(n=200, W=96, seed=6)
+    sc.scale *= np.float32(4.0)     # primitives spanning several tiles
+    sc.curv /= np.float32(4.0)
+    b = O.bin_fp32(sc, cam, emit=False)
+    sl = b.slabs
+    f = np.float32
+    checked = rejected = 0
+    for i in np.nonzero(b.visible & sl["conic_on"])[0][:60]:
+        x0r, x1r, y0r, y1r = b.rect[i]
+        for ty in range(y0r, y1r + 1):
+            for tx in range(x0r, x1r + 1):
+                x0 = f(16 * tx) + f(0.5) - sl["uc"][i]
+                x1 = f(min(16 * tx + 15, cam.W - 1)) + f(0.5) - sl["uc"][i]
+                y0 = f(16 * ty) + f(0.5) - sl["vc"][i]
+                y1 = f(min(16 * ty + 15, cam.H - 1)) + f(0.5) - sl["vc"][i]
+                got = bool(O._conic_pass(sl, np.array([i]), np.array([x0]), np.array([x1]), np.array([y0]),
+                                         np.array([y1]))[0])
+                q = [float(sl[k][i]) for k in ("qa", "qb", "qc", "la", "lb")]
+
+                def F(pt):
+                    u, v = pt
+                    return q[0] * u * u + 2 * q[1] * u * v + q[2] * v * v - 2 * q[3] * u - 2 * q[4] * v
+
+                gu, gv = np.meshgrid(np.linspace(x0, x1, 41), np.linspace(y0, y1, 41))
+                vals = F((gu, gv))
+                k = np.argmin(vals)
+                r = optimize.minimize(F, [gu.flat[k], gv.flat[k]], method="L-BFGS-B",
+                                      bounds=[(float(x0), float(x1)), (float(y0), float(y1))],
+                                      options=dict(ftol=1e-15, gtol=1e-12))
+                fmin = min(float(r.fun), float(vals.flat[k]))
+                if fmin < 1 - 1e-6:
+                    assert got, (i, tx, ty, fmin)
+                elif fmin > 1 + 1e-6:
+                    assert not got, (i, tx, ty, fmin)
+                    rejected += 1
+                checked += 1
+    assert checked > 200 and rejected > 20
