@@ -168,20 +168,23 @@ def ellipsoid_conic(muc, Wm, su, sv, m, fx, fy):
     projected centre). The conic is enabled only when the padded Q is positive definite
     (the ellipsoid lies in front of the camera plane); otherwise every pixel passes.
     Returned (normalised so that the test reads F(p) = p^T q p - 2 l.p <= 1):
-    qa, qb, qc (q = [[qa, qb], [qb, qc]]), la, lb and the enable flag conic_on.
+    qa, qb, qc (q = [[qa, qb], [qb, qc]]), la, lb, the reciprocals iqa = 1/qa and
+    iqc = 1/qc used by the tile test, and the enable flag conic_on (all zero when off).
     Correctly rounded FP32 operations in the order written (the kernels follow the same
     specification bit for bit)."""
     f = np.float32
     zero, one, two = f(0.0), f(1.0), f(2.0)
-    s = (su, sv, m)
-    oth = (sv * m, su * m, su * sv)        # s_c / (s_u s_v m) = 1 / oth_c
-    nx = [((Wm[2][c] * muc[1] - Wm[1][c] * muc[2]) / fx) / oth[c] for c in range(3)]
-    ny = [((Wm[0][c] * muc[2] - Wm[2][c] * muc[0]) / fy) / oth[c] for c in range(3)]
-    hx = [(Wm[0][c] / fx) / s[c] for c in range(3)]
-    hy = [(Wm[1][c] / fy) / s[c] for c in range(3)]
+    ifx, ify = one / fx, one / fy
+    isu, isv, im = one / su, one / sv, one / m
+    rs = (isu, isv, im)                     # 1 / s_c
+    ro = (isv * im, isu * im, isu * isv)    # s_c / (s_u s_v m)
+    nx = [((Wm[2][c] * muc[1] - Wm[1][c] * muc[2]) * ifx) * ro[c] for c in range(3)]
+    ny = [((Wm[0][c] * muc[2] - Wm[2][c] * muc[0]) * ify) * ro[c] for c in range(3)]
+    hx = [(Wm[0][c] * ifx) * rs[c] for c in range(3)]
+    hy = [(Wm[1][c] * ify) * rs[c] for c in range(3)]
     dcx = muc[0] / muc[2]
     dcy = muc[1] / muc[2]
-    dc = [((Wm[0][c] * dcx + Wm[1][c] * dcy) + Wm[2][c]) / s[c] for c in range(3)]
+    dc = [((Wm[0][c] * dcx + Wm[1][c] * dcy) + Wm[2][c]) * rs[c] for c in range(3)]
 
     def dot(u, v):
         return (u[0] * v[0] + u[1] * v[1]) + u[2] * v[2]
@@ -197,7 +200,8 @@ def ellipsoid_conic(muc, Wm, su, sv, m, fx, fy):
     L1 = kap * dot(dc, hy)
     K = kap * dot(dc, dc)
     det = Q00 * Q11 - Q01 * Q01
-    qa, qb, qc, la, lb = Q00 / K, Q01 / K, Q11 / K, L0 / K, L1 / K
+    iK = one / K
+    qa, qb, qc, la, lb = Q00 * iK, Q01 * iK, Q11 * iK, L0 * iK, L1 * iK
     dn = qa * qc - qb * qb
     # R = 1 + l^T q^-1 l: (p - p0)^T q (p - p0) <= R is the same ellipse, p0 = q^-1 l
     R0 = one + (((qc * la) * la - (two * (qb * la)) * lb) + (qa * lb) * lb) / dn
@@ -206,16 +210,19 @@ def ellipsoid_conic(muc, Wm, su, sv, m, fx, fy):
     dl = f(CONIC_DELTA)
     # growing the ellipse by dl pixels raises F by at most 2 dl sqrt(lmax R) + dl^2 lmax
     T = (one + (f(3.0) * dl) * np.sqrt(tr * R)) + ((two * dl) * dl) * tr
+    iT = one / T
     on = (np.isfinite(Q00) & np.isfinite(Q01) & np.isfinite(Q11) & np.isfinite(L0) & np.isfinite(L1)
           & np.isfinite(K) & (K > zero) & (Q00 > zero) & (Q11 > zero) & (det > f(1e-6) * (Q00 * Q11))
           & np.isfinite(T) & (dn > zero) & np.isfinite(R0))
-    out = {}
-    for k, v in (("qa", qa / T), ("qb", qb / T), ("qc", qc / T), ("la", la / T), ("lb", lb / T)):
-        out[k] = np.where(on, v, zero).astype(f)
-    out["conic_on"] = on & np.isfinite(out["qa"]) & np.isfinite(out["qb"]) & np.isfinite(out["qc"]) \
-        & np.isfinite(out["la"]) & np.isfinite(out["lb"]) & (out["qa"] > zero) & (out["qc"] > zero)
-    for k in ("qa", "qb", "qc", "la", "lb"):
-        out[k] = np.where(out["conic_on"], out[k], zero).astype(f)
+    out = {"qa": qa * iT, "qb": qb * iT, "qc": qc * iT, "la": la * iT, "lb": lb * iT}
+    out["iqa"] = one / out["qa"]
+    out["iqc"] = one / out["qc"]
+    for k in out:
+        on &= np.isfinite(out[k])
+    on &= (out["qa"] > zero) & (out["qc"] > zero)
+    for k in list(out):
+        out[k] = np.where(on, out[k], zero).astype(f)
+    out["conic_on"] = on
     return out
 
 
@@ -242,11 +249,11 @@ def _conic_pass(sl, p, x0, x1, y0, y1):
         inside = (x0 <= zero) & (zero <= x1) & (y0 <= zero) & (zero <= y1)
         ue = np.where(x0 > zero, x0, x1)
         has_u = (x0 > zero) | (x1 < zero)
-        vs = np.minimum(np.maximum((lb - qb * ue) / qc, y0), y1)
+        vs = np.minimum(np.maximum((lb - qb * ue) * sl["iqc"][p], y0), y1)
         fu = conic_value(sl, p, ue, vs)
         ve = np.where(y0 > zero, y0, y1)
         has_v = (y0 > zero) | (y1 < zero)
-        us = np.minimum(np.maximum((la - qb * ve) / qa, x0), x1)
+        us = np.minimum(np.maximum((la - qb * ve) * sl["iqa"][p], x0), x1)
         fv = conic_value(sl, p, us, ve)
         meets = inside | (has_u & (fu <= one)) | (has_v & (fv <= one))
     return ~on | meets

@@ -58,7 +58,7 @@ __global__ void k_gather_u32(int64_t n, const uint32_t* __restrict__ idx, const 
 }
 
 // Write the tile instances of 32 consecutive primitives per warp (coalesced): the tiles
-// of each rectangle that meet the primitive's parallelogram (all of them when tslab is
+// of each rectangle that meet the primitive's screen bounds (all of them when tslab is
 // null). sidx == nullptr: primitive order (full-key mode, keys carry the depth bits,
 // values the primitive); otherwise depth order (keys carry the primitive in their low half).
 __global__ void k_emit(int64_t n, const uint32_t* __restrict__ sidx, const uint32_t* __restrict__ count,
@@ -275,7 +275,7 @@ struct qgs_ctx {
   DevBuf<float> xres;             // StopThePop order: the forward's outputs for its backward
   bool stp = false;               // the last forward used the StopThePop order
   DevBuf<uint32_t> vpos;          // visibility flags, then their exclusive scan
-  DevBuf<TileSlab> tslab;         // per primitive: screen parallelogram for the tile test
+  DevBuf<TileSlab> tslab;         // per primitive: parallelogram and conic for the tile test
   DevBuf<PrimState> dstate;       // projected state of the visible primitives in depth order
   const PrimState* raster_state = nullptr;  // state the sorted ids index (dstate or state)
   bool pgrad_by_pos = false;      // gradient records indexed like raster_state's depth order
@@ -511,7 +511,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
                                           ctx->tslab.p);
     ++launch_counter();
     QGS_CU(cudaGetLastError(), "k_preprocess");
-    // keep the rectangle's tiles that meet the parallelogram; totals and visibility
+    // keep the rectangle's tiles that meet the parallelogram and the conic; totals and visibility
     k_count_tiles<<<nblk(N), 256, 0, st>>>(N, ctx->tslab.p, cam->W, cam->H, ctx->count.p, ctx->rect.p,
                                            ctx->zkey.p, sm == 0 ? ctx->vpos.p : nullptr, ctx->dcount.p);
     ++launch_counter();

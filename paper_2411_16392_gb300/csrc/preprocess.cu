@@ -145,6 +145,78 @@ __device__ __forceinline__ void screen_normal(const CamParams& cp, const float* 
   }
 }
 
+// Screen-space conic of the chord ellipsoid x^2/s_u^2 + y^2/s_v^2 + z^2/m^2 <= 9 that holds
+// the support (arc >= chord): the pixels whose ray line meets it, as
+// F(p) = p^T q p - 2 l.p <= 1 for the offset p from the projected centre. With the frame
+// scaled by S = diag(s_u, s_v, m), the line meets the ball iff |omega x delta|^2 <=
+// kappa |delta|^2 (omega: camera, delta: direction); the cross product is formed as
+// S W^T (e x mu_c) / (s_u s_v m), free of the camera distance. Pads: kappa = 9.02, the
+// diagonal of q lowered by 4e-6 of its trace, the threshold raised for a 2e-3 px rim.
+// Disabled (every pixel passes) unless the padded form is positive definite. Correctly
+// rounded FP32 in a fixed order: the tile test built on it is reproduced bit for bit by
+// the oracle's recipe.
+struct Conic {
+  float qa, qb, qc, la, lb, iqa, iqc;
+  bool on;
+};
+__device__ __forceinline__ float dot3_rn(const float* u, const float* v) {
+  return __fadd_rn(__fadd_rn(__fmul_rn(u[0], v[0]), __fmul_rn(u[1], v[1])), __fmul_rn(u[2], v[2]));
+}
+__device__ __forceinline__ Conic ellipsoid_conic(const float* muc, const float* W, float su, float sv, float m,
+                                                 float fx, float fy) {
+  const float ifx = __frcp_rn(fx), ify = __frcp_rn(fy);
+  const float isu = __frcp_rn(su), isv = __frcp_rn(sv), im = __frcp_rn(m);
+  const float rs[3] = {isu, isv, im};                                                // 1 / s_c
+  const float ro[3] = {__fmul_rn(isv, im), __fmul_rn(isu, im), __fmul_rn(isu, isv)};  // s_c / (s_u s_v m)
+  const float dcx = __fdiv_rn(muc[0], muc[2]), dcy = __fdiv_rn(muc[1], muc[2]);
+  float nx[3], ny[3], hx[3], hy[3], dc[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    nx[c] = __fmul_rn(__fmul_rn(__fsub_rn(__fmul_rn(W[6 + c], muc[1]), __fmul_rn(W[3 + c], muc[2])), ifx), ro[c]);
+    ny[c] = __fmul_rn(__fmul_rn(__fsub_rn(__fmul_rn(W[c], muc[2]), __fmul_rn(W[6 + c], muc[0])), ify), ro[c]);
+    hx[c] = __fmul_rn(__fmul_rn(W[c], ifx), rs[c]);
+    hy[c] = __fmul_rn(__fmul_rn(W[3 + c], ify), rs[c]);
+    dc[c] = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(W[c], dcx), __fmul_rn(W[3 + c], dcy)), W[6 + c]), rs[c]);
+  }
+  const float kap = 9.02f;
+  const float G00 = dot3_rn(nx, nx), G01 = dot3_rn(nx, ny), G11 = dot3_rn(ny, ny);
+  const float H00 = dot3_rn(hx, hx), H01 = dot3_rn(hx, hy), H11 = dot3_rn(hy, hy);
+  const float tau = __fmul_rn(4e-6f, __fadd_rn(G00, G11));
+  const float Q00 = __fsub_rn(__fsub_rn(G00, __fmul_rn(kap, H00)), tau);
+  const float Q01 = __fsub_rn(G01, __fmul_rn(kap, H01));
+  const float Q11 = __fsub_rn(__fsub_rn(G11, __fmul_rn(kap, H11)), tau);
+  const float L0 = __fmul_rn(kap, dot3_rn(dc, hx)), L1 = __fmul_rn(kap, dot3_rn(dc, hy));
+  const float K = __fmul_rn(kap, dot3_rn(dc, dc));
+  const float det = __fsub_rn(__fmul_rn(Q00, Q11), __fmul_rn(Q01, Q01));
+  const float iK = __frcp_rn(K);
+  const float qa = __fmul_rn(Q00, iK), qb = __fmul_rn(Q01, iK), qc = __fmul_rn(Q11, iK);
+  const float la = __fmul_rn(L0, iK), lb = __fmul_rn(L1, iK);
+  const float dn = __fsub_rn(__fmul_rn(qa, qc), __fmul_rn(qb, qb));
+  // R = 1 + l^T q^-1 l (the ellipse is (p - p0)^T q (p - p0) <= R); growing it by dl
+  // pixels raises F by at most 2 dl sqrt(lmax R) + dl^2 lmax, lmax <= qa + qc
+  const float num = __fadd_rn(__fsub_rn(__fmul_rn(__fmul_rn(qc, la), la), __fmul_rn(__fmul_rn(2.f, __fmul_rn(qb, la)), lb)),
+                              __fmul_rn(__fmul_rn(qa, lb), lb));
+  const float R0 = __fadd_rn(1.f, __fdiv_rn(num, dn));
+  const float R = R0 > 1.f ? R0 : 1.f;
+  const float tr = __fadd_rn(qa, qc);
+  const float dl = 2e-3f;
+  const float T = __fadd_rn(__fadd_rn(1.f, __fmul_rn(__fmul_rn(3.f, dl), __fsqrt_rn(__fmul_rn(tr, R)))),
+                            __fmul_rn(__fmul_rn(__fmul_rn(2.f, dl), dl), tr));
+  const float iT = __frcp_rn(T);
+  bool on = isfinite(Q00) && isfinite(Q01) && isfinite(Q11) && isfinite(L0) && isfinite(L1) && isfinite(K) &&
+            K > 0.f && Q00 > 0.f && Q11 > 0.f && det > __fmul_rn(1e-6f, __fmul_rn(Q00, Q11)) && isfinite(T) &&
+            dn > 0.f && isfinite(R0);
+  Conic o;
+  o.qa = __fmul_rn(qa, iT); o.qb = __fmul_rn(qb, iT); o.qc = __fmul_rn(qc, iT);
+  o.la = __fmul_rn(la, iT); o.lb = __fmul_rn(lb, iT);
+  o.iqa = __frcp_rn(o.qa); o.iqc = __frcp_rn(o.qc);
+  on = on && isfinite(o.qa) && isfinite(o.qb) && isfinite(o.qc) && isfinite(o.la) && isfinite(o.lb) &&
+       isfinite(o.iqa) && isfinite(o.iqc) && o.qa > 0.f && o.qc > 0.f;
+  if (!on) o.qa = o.qb = o.qc = o.la = o.lb = o.iqa = o.iqc = 0.f;
+  o.on = on;
+  return o;
+}
+
 // Projected centre f (x / z) + c as an unevaluated sum hi + lo of floats (about 44
 // significant bits), from error-free transformations: the division's remainder by fma,
 // the product's rounding error by fma, and a two-sum with the principal point.
@@ -160,14 +232,6 @@ __device__ __forceinline__ void centre_df(float x, float z, float f, float c, fl
   lo = sl - (hi - sh);
 }
 
-// Scaled slab of the parallelogram: (p_x, p_y, p_c) with |p_x dx + p_y dy - p_c| <= 1
-// for every pixel offset (dx, dy) from the projected centre inside the span.
-__device__ __forceinline__ float3 slab_of(float nx, float ny, float smin, float smax) {
-  const float c = 0.5f * (smin + smax);
-  const float w = 0.5f * (smax - smin) * (1.f + 1e-5f) + 2e-3f + 1e-6f * fabsf(c);
-  const float iw = 1.f / w;
-  return make_float3(nx * iw, ny * iw, c * iw);
-}
 
 }  // namespace
 
@@ -283,6 +347,7 @@ __device__ __forceinline__ uint32_t preprocess_one(int64_t i, const SceneView& s
   bool ok = finite_in && quat_rot_exact(q.x, q.y, q.z, q.w, R) && s.x > 0.f && s.y > 0.f && su2 > 0.f &&
             sv2 > 0.f && muc[2] > cp.near;
   Box2 bx;
+  Conic con{};
   bx.xmin = INFINITY; bx.xmax = -INFINITY; bx.ymin = INFINITY; bx.ymax = -INFINITY; bx.any = false;
   bx.s1min = INFINITY; bx.s1max = -INFINITY; bx.s2min = INFINITY; bx.s2max = -INFINITY;
   if (ok) {
@@ -314,6 +379,7 @@ __device__ __forceinline__ uint32_t preprocess_one(int64_t i, const SceneView& s
     // reference point of the spans: the projected centre (bit-exact)
     bx.pcx = __fadd_rn(__fmul_rn(cp.fx, __fdiv_rn(muc[0], muc[2])), cp.cx);
     bx.pcy = __fadd_rn(__fmul_rn(cp.fy, __fdiv_rn(muc[1], muc[2])), cp.cy);
+    con = ellipsoid_conic(muc, W, su, sv, m, cp.fx, cp.fy);
     float P[8][3];
     bool in[8];
 #pragma unroll
@@ -362,7 +428,9 @@ __device__ __forceinline__ uint32_t preprocess_one(int64_t i, const SceneView& s
     TileSlab t;
     t.a = make_float4(bx.n1x, bx.n1y, bx.s1min, bx.s1max);
     t.b = make_float4(bx.n2x, bx.n2y, bx.s2min, bx.s2max);
-    t.c = make_float4(bx.pcx, bx.pcy, 0.f, 0.f);
+    t.c = make_float4(bx.pcx, bx.pcy, con.qa, con.qb);
+    t.d = make_float4(con.qc, con.la, con.lb, con.iqa);
+    t.e = make_float4(con.iqc, 0.f, 0.f, 0.f);
     tslab[i] = t;
   }
 
@@ -375,8 +443,6 @@ __device__ __forceinline__ uint32_t preprocess_one(int64_t i, const SceneView& s
   float g[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) g[c] = fmaf(W[c], muc[0], fmaf(W[3 + c], muc[1], W[6 + c] * zmu)) * iz;
-  const float3 p1 = slab_of(bx.n1x, bx.n1y, bx.s1min, bx.s1max);
-  const float3 p2 = slab_of(bx.n2x, bx.n2y, bx.s2min, bx.s2max);
 
   // colour: degree-3 SH at the direction from the camera centre to the primitive
   float dx = mx - cp.cw[0], dy = my - cp.cw[1], dz = mz - cp.cw[2];
@@ -398,9 +464,9 @@ __device__ __forceinline__ uint32_t preprocess_one(int64_t i, const SceneView& s
     }
   }
   PrimState ps;
-  ps.f[0] = make_float4(p1.x, p1.y, p1.z, p2.x);
+  ps.f[0] = make_float4(con.qa, 2.f * con.qb, con.qc, 2.f * con.la);
   ps.f[1] = make_float4(pcx_hi, pcx_lo, pcy_hi, pcy_lo);
-  ps.f[2] = make_float4(p2.y, p2.z, iz, zmu);
+  ps.f[2] = make_float4(2.f * con.lb, 0.f, iz, zmu);
   ps.f[3] = make_float4(W[0], W[3], W[1], W[4]);
   ps.f[4] = make_float4(W[2], W[5], g[0], g[1]);
   ps.f[5] = make_float4(g[2], ab.x, ab.y, op);
@@ -655,7 +721,7 @@ __global__ void __launch_bounds__(256) k_count_tiles(int64_t n, const TileSlab* 
     if (lane == k) mine = c;
   }
   if (i < n) {
-    if (c0 && !mine) {  // the rectangle's tiles all miss the parallelogram
+    if (c0 && !mine) {  // the rectangle's tiles all miss the screen bounds
       rect[i] = make_short4(-1, -1, -1, -1);
       zkey[i] = 0xFFFFFFFFu;
     }

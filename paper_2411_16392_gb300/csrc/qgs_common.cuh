@@ -16,9 +16,9 @@ constexpr int NGRAD_PAD = 20;       // 80 B: 16-byte aligned records
 // Per-primitive projected state: one 128-byte record (8 x float4), written by the
 // preprocessing kernel for the visible primitives and gathered by the compositing
 // kernels in sorted order (one cache line per primitive).
-//   f[0] = (p1x, p1y, p1c, p2x)   screen-space parallelogram containing the projected
-//   f[2].xy = (p2y, p2c)            support box: |p_x dx + p_y dy - p_c| <= 1 for the
-//                                   pixel offset (dx, dy) from the projected centre
+//   f[0] = (qa, 2qb, qc, 2la)     screen-space conic of the chord ellipsoid holding the
+//   f[2].xy = (2lb, 0)              support: dx (qa dx + 2qb dy - 2la) + dy (qc dy - 2lb) <= 1
+//                                   for the pixel offset (dx, dy) from the projected centre
 //   f[1] = projected centre as double-float (pcx_hi, pcx_lo, pcy_hi, pcy_lo)
 //   f[2].zw = (inv_z, z_mu)
 //   f[3] = (W00, W10, W01, W11)   W = R_cw * R: camera-from-local rotation

@@ -32,13 +32,17 @@ struct CamParams {
 };
 
 // ---------------------------------------------------------------- tile culling
-// A primitive's screen parallelogram for the tile test: normals of the projected local
-// x and y axes with the spans of the projected support box along them, measured from the
-// projected centre (uc, vc). All bit-exact (correctly rounded FP32 in a fixed order).
+// A primitive's screen bounds for the tile test, measured from the projected centre
+// (uc, vc): the parallelogram (normals of the projected local x and y axes with the spans
+// of the projected support box along them) and the conic of the chord ellipsoid
+// (F(p) = p^T q p - 2 l.p <= 1, q = [[qa, qb], [qb, qc]], l = (la, lb)). All bit-exact
+// (correctly rounded FP32 in a fixed order).
 struct TileSlab {
   float4 a;  // (n1x, n1y, s1min, s1max)
   float4 b;  // (n2x, n2y, s2min, s2max)
-  float4 c;  // (uc, vc, -, -)
+  float4 c;  // (uc, vc, qa, qb)
+  float4 d;  // (qc, la, lb, 1/qa)
+  float4 e;  // (1/qc, -, -, -); qa = 0: conic disabled (every tile passes)
 };
 
 // Does a tile meet the parallelogram? Range of n . (x - c) over the tile's pixel centres
@@ -46,28 +50,56 @@ struct TileSlab {
 // specification as the oracle's tile test). The products n_x (x - u_c) depend on the
 // column only and n_y (y - v_c) on the row only, so they are formed once per column / row
 // (the same correctly rounded values a per-tile evaluation gives).
-struct TileRow {  // per row: n_y (y - v_c) at the row's first and last pixel centre, per slab
-  float b0[2], b1[2];
+struct TileRow {  // per row: offsets of its first and last pixel centre, n_y (y - v_c) per slab
+  float y0, y1, b0[2], b1[2];
 };
-struct TileCol {  // per column: n_x (x - u_c) at its first and last pixel centre, per slab
-  float a0[2], a1[2];
+struct TileCol {  // per column: offsets of its first and last pixel centre, n_x (x - u_c) per slab
+  float x0, x1, a0[2], a1[2];
 };
 __device__ __forceinline__ TileRow tile_row(const TileSlab& t, int ty, int H) {
-  const float y0 = __fsub_rn(__fadd_rn((float)(16 * ty), 0.5f), t.c.y);
-  const float y1 = __fsub_rn(__fadd_rn((float)min(16 * ty + 15, H - 1), 0.5f), t.c.y);
   TileRow r;
-  r.b0[0] = __fmul_rn(t.a.y, y0); r.b1[0] = __fmul_rn(t.a.y, y1);
-  r.b0[1] = __fmul_rn(t.b.y, y0); r.b1[1] = __fmul_rn(t.b.y, y1);
+  r.y0 = __fsub_rn(__fadd_rn((float)(16 * ty), 0.5f), t.c.y);
+  r.y1 = __fsub_rn(__fadd_rn((float)min(16 * ty + 15, H - 1), 0.5f), t.c.y);
+  r.b0[0] = __fmul_rn(t.a.y, r.y0); r.b1[0] = __fmul_rn(t.a.y, r.y1);
+  r.b0[1] = __fmul_rn(t.b.y, r.y0); r.b1[1] = __fmul_rn(t.b.y, r.y1);
   return r;
 }
 __device__ __forceinline__ TileCol tile_col(const TileSlab& t, int tx, int W) {
-  const float x0 = __fsub_rn(__fadd_rn((float)(16 * tx), 0.5f), t.c.x);
-  const float x1 = __fsub_rn(__fadd_rn((float)min(16 * tx + 15, W - 1), 0.5f), t.c.x);
   TileCol c;
-  c.a0[0] = __fmul_rn(t.a.x, x0); c.a1[0] = __fmul_rn(t.a.x, x1);
-  c.a0[1] = __fmul_rn(t.b.x, x0); c.a1[1] = __fmul_rn(t.b.x, x1);
+  c.x0 = __fsub_rn(__fadd_rn((float)(16 * tx), 0.5f), t.c.x);
+  c.x1 = __fsub_rn(__fadd_rn((float)min(16 * tx + 15, W - 1), 0.5f), t.c.x);
+  c.a0[0] = __fmul_rn(t.a.x, c.x0); c.a1[0] = __fmul_rn(t.a.x, c.x1);
+  c.a0[1] = __fmul_rn(t.b.x, c.x0); c.a1[1] = __fmul_rn(t.b.x, c.x1);
   return c;
 }
+
+// F(u, v) = u (qa u + 2 qb v - 2 la) + v (qc v - 2 lb): the conic of the chord ellipsoid at
+// the pixel offset (u, v) from the projected centre (F <= 1 inside), FP32 in this order.
+__device__ __forceinline__ float conic_value(const TileSlab& t, float u, float v) {
+  const float inner = __fsub_rn(__fadd_rn(__fmul_rn(t.c.z, u), __fmul_rn(2.f, __fmul_rn(t.c.w, v))),
+                                __fmul_rn(2.f, t.d.y));
+  return __fadd_rn(__fmul_rn(u, inner), __fmul_rn(v, __fsub_rn(__fmul_rn(t.d.x, v), __fmul_rn(2.f, t.d.z))));
+}
+
+// Does the rectangle of the tile's pixel-centre offsets meet the conic F <= 1? F is convex
+// and F(0) <= 1, so: the rectangle holds the origin, or the minimum of F along an edge
+// facing the origin (its stationary point, clamped to the edge) is <= 1.
+__device__ __forceinline__ bool conic_meets(const TileSlab& t, const TileCol& c, const TileRow& r) {
+  if (!(t.c.z > 0.f)) return true;
+  if (c.x0 <= 0.f && 0.f <= c.x1 && r.y0 <= 0.f && 0.f <= r.y1) return true;
+  if (c.x0 > 0.f || c.x1 < 0.f) {
+    const float ue = c.x0 > 0.f ? c.x0 : c.x1;
+    const float vs = fminf(fmaxf(__fmul_rn(__fsub_rn(t.d.z, __fmul_rn(t.c.w, ue)), t.e.x), r.y0), r.y1);
+    if (conic_value(t, ue, vs) <= 1.f) return true;
+  }
+  if (r.y0 > 0.f || r.y1 < 0.f) {
+    const float ve = r.y0 > 0.f ? r.y0 : r.y1;
+    const float us = fminf(fmaxf(__fmul_rn(__fsub_rn(t.d.y, __fmul_rn(t.c.w, ve)), t.d.w), c.x0), c.x1);
+    if (conic_value(t, us, ve) <= 1.f) return true;
+  }
+  return false;
+}
+
 __device__ __forceinline__ bool tile_meets(const TileSlab& t, const TileCol& c, const TileRow& r) {
   bool ok = true;
 #pragma unroll
@@ -80,14 +112,14 @@ __device__ __forceinline__ bool tile_meets(const TileSlab& t, const TileCol& c, 
     const float pad = __fadd_rn(2e-3f, __fmul_rn(1e-5f, __fadd_rn(fabsf(s.z), fabsf(s.w))));
     ok = ok && !(hi < __fsub_rn(s.z, pad)) && !(lo > __fadd_rn(s.w, pad));
   }
-  return ok;
+  return ok && conic_meets(t, c, r);
 }
 
 // The whole warp enumerates one primitive's rectangle r in row-major order, 32 tiles at a
 // time (lane l takes tile e = e0 + l, its (tx, ty) advanced without divisions); f(k, tx,
-// ty) runs for every tile that meets the parallelogram (every tile when t is null), k
-// counting them in row-major order. Returns their number. Call with the same arguments
-// on every lane.
+// ty) runs for every tile that meets the parallelogram and the conic (every tile when t
+// is null), k counting them in row-major order. Returns their number. Call with the same
+// arguments on every lane.
 template <typename F>
 __device__ __forceinline__ uint32_t warp_tiles(short4 r, const TileSlab* t, int W, int H, F&& f) {
   const int lane = threadIdx.x & 31;
@@ -121,7 +153,7 @@ __device__ __forceinline__ uint32_t warp_tiles(short4 r, const TileSlab* t, int 
   return base;
 }
 
-// Per primitive with a nonempty rectangle: count its tiles that meet the parallelogram;
+// Per primitive with a nonempty rectangle: count its tiles that meet its screen bounds;
 // primitives left with none are culled (count 0, rectangle -1s, depth key 0xFFFFFFFF).
 // Writes the visibility flags (when given) and adds the visible and instance totals
 // to counters[0], counters[1].
@@ -130,7 +162,7 @@ __global__ void k_count_tiles(int64_t n, const TileSlab* tslab, int W, int H, ui
 
 // ---------------------------------------------------------------- preprocessing
 // Per primitive i: projected state (visible ones only), tile count of the rectangle,
-// depth key, tile rectangle; idx[i] = i, vflag[i] = (count > 0) and the parallelogram
+// depth key, tile rectangle; idx[i] = i, vflag[i] = (count > 0) and the screen bounds
 // (tslab) when given; counters[0] += visible, counters[1] += tile instances when given.
 __global__ void k_preprocess(int64_t n, SceneView sc, CamParams cp, PrimState* state, uint32_t* count,
                              uint32_t* zkey, uint32_t* idx, short4* rect, uint32_t* counters, uint32_t* vflag,

@@ -107,12 +107,13 @@ template <bool EUCLID>
 __device__ __forceinline__ bool eval_pair(const PrimState& P, float X, float Y, const RasterParams& rp, Hit& h,
                                           bool& grazed, uint32_t& isect) {
   const float4 f0 = P.f[0], f1 = P.f[1], f2 = P.f[2];
-  // pixel offset from the projected centre (double-float centre), parallelogram test
+  // pixel offset from the projected centre (double-float centre); the pixel's ray line
+  // must meet the chord ellipsoid that holds the support: conic F(p) <= 1
   const float dxp = __fsub_rn(__fsub_rn(X, f1.x), f1.y);
   const float dyp = __fsub_rn(__fsub_rn(Y, f1.z), f1.w);
-  const float t1 = __fmaf_rn(f0.x, dxp, __fmaf_rn(f0.y, dyp, -f0.z));
-  const float t2 = __fmaf_rn(f0.w, dxp, __fmaf_rn(f2.x, dyp, -f2.y));
-  if (!(fabsf(t1) <= 1.f && fabsf(t2) <= 1.f)) return false;
+  const float Fc = __fmaf_rn(dxp, __fmaf_rn(f0.x, dxp, __fmaf_rn(f0.y, dyp, -f0.w)),
+                             __fmul_rn(dyp, __fmaf_rn(f0.z, dyp, -f2.x)));
+  if (!(Fc <= 1.f)) return false;
   ++isect;
   const float4 f3 = P.f[3], f4 = P.f[4], f5 = P.f[5], f6 = P.f[6];
   // camera-plane offset at the centre's depth, then the local frame (W^T e, e_z = 0)
