@@ -215,6 +215,14 @@ qgs_status qgs_get_frame_stats(qgs_ctx* ctx, qgs_frame_stats* stats);
  * stream. Off by default; costs a few event records per call. Errors: EINVAL, ECUDA. */
 qgs_status qgs_set_profiling(qgs_ctx* ctx, int32_t enable);
 
+/* Capacity, in 32-bit words, of the context's tile-mask store: the tile-count pass keeps
+ * each primitive's per-tile test results (one bit per tile of its rectangle) so that the
+ * instance emission replays them instead of testing again. Primitives that do not fit are
+ * tested again (same lists, more time); the store grows by itself after a frame that
+ * overflowed it. 0 disables the store until it is set again. Takes effect at the next
+ * forward; does not change any result. Errors: EINVAL (ctx null or words < 0). */
+qgs_status qgs_set_tile_mask_capacity(qgs_ctx* ctx, int64_t words);
+
 /* Copy the last forward's tile binning to HOST memory, for inspection and tests:
  * keys[i] = (tile << 32) | float bits of the primitive's view depth, vals[i] = primitive
  * index, in sorted order (cap entries at most); ranges[2*t], ranges[2*t+1] = [start, end)

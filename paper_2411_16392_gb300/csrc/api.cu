@@ -59,12 +59,13 @@ __global__ void k_gather_u32(int64_t n, const uint32_t* __restrict__ idx, const 
 
 // Write the tile instances of 32 consecutive primitives per warp (coalesced): the tiles
 // of each rectangle that meet the primitive's screen bounds (all of them when tslab is
-// null). sidx == nullptr: primitive order (full-key mode, keys carry the depth bits,
+// null), replayed from the tile-count pass's masks where it stored them (tbits). sidx == nullptr: primitive order (full-key mode, keys carry the depth bits,
 // values the primitive); otherwise depth order (keys carry the primitive in their low half).
 __global__ void k_emit(int64_t n, const uint32_t* __restrict__ sidx, const uint32_t* __restrict__ count,
                        const short4* __restrict__ rect, const TileSlab* __restrict__ tslab, int W, int H,
                        const uint32_t* __restrict__ offs, const uint32_t* __restrict__ zkey, int tiles_x,
-                       uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+                       uint64_t* __restrict__ keys, uint32_t* __restrict__ vals, const uint32_t* __restrict__ tbits,
+                       const uint32_t* __restrict__ tbits_off) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t pid = 0, c = 0, off = 0, lowv = 0;
   short4 r = make_short4(0, 0, 0, 0);
@@ -87,11 +88,12 @@ __global__ void k_emit(int64_t n, const uint32_t* __restrict__ sidx, const uint3
                                   (short)__shfl_sync(0xffffffffu, (int)r.y, k),
                                   (short)__shfl_sync(0xffffffffu, (int)r.z, k),
                                   (short)__shfl_sync(0xffffffffu, (int)r.w, k));
+    const uint32_t wo = tbits ? tbits_off[pp] : kNoTileBits;
     warp_tiles(rk, tslab ? tslab + pp : nullptr, W, H, [&](uint32_t e, int tx, int ty) {
       const uint32_t tile = (uint32_t)ty * (uint32_t)tiles_x + (uint32_t)tx;
       keys[(size_t)oo + e] = ((uint64_t)tile << 32) | lv;
       if (vals) vals[(size_t)oo + e] = pp;
-    });
+    }, nullptr, wo != kNoTileBits ? tbits + wo : nullptr);
   }
 }
 
@@ -166,7 +168,8 @@ __global__ void k_gather_state(int64_t V, const uint32_t* __restrict__ sidx, con
 template <typename K>
 __global__ void k_emit_packed(int64_t V, const uint32_t* __restrict__ sidx, const uint32_t* __restrict__ cnt_sorted,
                               const short4* __restrict__ rect, const TileSlab* __restrict__ tslab, int W, int H,
-                              const uint32_t* __restrict__ offs, int tiles_x, int rb, K* __restrict__ keys) {
+                              const uint32_t* __restrict__ offs, int tiles_x, int rb, K* __restrict__ keys,
+                              const uint32_t* __restrict__ tbits, const uint32_t* __restrict__ tbits_off) {
   const int lane = threadIdx.x & 31;
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t c = 0, off = 0, pid = 0;
@@ -181,10 +184,11 @@ __global__ void k_emit_packed(int64_t V, const uint32_t* __restrict__ sidx, cons
     const uint32_t rr = (uint32_t)(r - lane + k);
     const uint32_t oo = __shfl_sync(0xffffffffu, off, k);
     const uint32_t pp = __shfl_sync(0xffffffffu, pid, k);
+    const uint32_t wo = tbits ? tbits_off[pp] : kNoTileBits;
     warp_tiles(rect[pp], tslab ? tslab + pp : nullptr, W, H, [&](uint32_t e, int tx, int ty) {
       const uint32_t tile = (uint32_t)ty * (uint32_t)tiles_x + (uint32_t)tx;
       keys[(size_t)oo + e] = ((K)tile << rb) | (K)rr;
-    });
+    }, nullptr, wo != kNoTileBits ? tbits + wo : nullptr);
   }
 }
 
@@ -259,8 +263,8 @@ struct qgs_ctx {
   // scratch
   DevBuf<uint32_t> hist, scan_tmp;
   DevBuf<RasterStats> stats;
-  DevBuf<uint32_t> dcount;      // [0] visible primitives of the current frame
-  uint32_t* h_total = nullptr;  // pinned: instance total, visible count
+  DevBuf<uint32_t> dcount;      // [0] visible primitives, [1] instances, [2] tile-mask words
+  uint32_t* h_total = nullptr;  // pinned: the frame's counters read back
   int64_t n_visible = 0;
   const uint32_t* vis_list = nullptr;
   // last frame
@@ -276,6 +280,10 @@ struct qgs_ctx {
   bool stp = false;               // the last forward used the StopThePop order
   DevBuf<uint32_t> vpos;          // visibility flags, then their exclusive scan
   DevBuf<TileSlab> tslab;         // per primitive: parallelogram and conic for the tile test
+  DevBuf<uint32_t> tbits;         // tile-count pass masks (one word per 32 rectangle tiles)
+  DevBuf<uint32_t> tbits_off;     // per primitive: word offset into tbits, or kNoTileBits
+  size_t tbits_want = size_t(1) << 22;  // words to provide (grown from the last frame's demand)
+  bool tbits_fixed = false;             // capacity set by the caller: provide exactly tbits_want
   DevBuf<PrimState> dstate;       // projected state of the visible primitives in depth order
   const PrimState* raster_state = nullptr;  // state the sorted ids index (dstate or state)
   bool pgrad_by_pos = false;      // gradient records indexed like raster_state's depth order
@@ -434,6 +442,8 @@ void qgs_destroy(qgs_ctx* c) {
   c->resid.release();
   c->vpos.release();
   c->tslab.release();
+  c->tbits.release();
+  c->tbits_off.release();
   c->xres.release();
   c->dstate.release();
   if (c->h_vdesc) cudaFreeHost(c->h_vdesc);
@@ -481,6 +491,12 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   QGS_CU(ctx->rect.reserve(n1), "alloc rect");
   if (sm == 0) QGS_CU(ctx->vpos.reserve(n1 + 1), "alloc visibility scan");
   QGS_CU(ctx->tslab.reserve(n1), "alloc tile slabs");
+  QGS_CU(ctx->tbits_off.reserve(n1), "alloc tile mask offsets");
+  if (ctx->tbits_want) QGS_CU(ctx->tbits.reserve(ctx->tbits_want), "alloc tile masks");
+  // words the tile-count pass may fill this frame (0: no masks, the emission tests)
+  const uint32_t cap_words =
+      ctx->tbits_want ? (uint32_t)std::min<size_t>(std::min(ctx->tbits.cap, ctx->tbits_want), 0xFFFFFFF0u) : 0u;
+  const bool tb_on = N > 0 && cap_words > 0;
   QGS_CU(ctx->ranges.reserve((size_t)ntiles), "alloc ranges");
   QGS_CU(ctx->tkey.reserve((size_t)ntiles), "alloc tile keys");
   QGS_CU(ctx->tkey2.reserve((size_t)ntiles), "alloc tile keys");
@@ -513,7 +529,8 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
     QGS_CU(cudaGetLastError(), "k_preprocess");
     // keep the rectangle's tiles that meet the parallelogram and the conic; totals and visibility
     k_count_tiles<<<nblk(N), 256, 0, st>>>(N, ctx->tslab.p, cam->W, cam->H, ctx->count.p, ctx->rect.p,
-                                           ctx->zkey.p, sm == 0 ? ctx->vpos.p : nullptr, ctx->dcount.p);
+                                           ctx->zkey.p, sm == 0 ? ctx->vpos.p : nullptr, ctx->dcount.p,
+                                           tb_on ? ctx->tbits.p : nullptr, ctx->tbits_off.p, cap_words);
     ++launch_counter();
     QGS_CU(cudaGetLastError(), "k_count_tiles");
   }
@@ -521,10 +538,13 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   // positions of the visible primitives (index order)
   if (sm == 0) QGS_CU(scan_exclusive_u32(ctx->vpos.p, ctx->vpos.p, N, ctx->scan_tmp.p, ctx->scan_tmp.cap, st), "scan");
   // the frame's one synchronisation: visible and instance totals size what follows
-  QGS_CU(cudaMemcpyAsync(ctx->h_total, ctx->dcount.p, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "totals");
+  QGS_CU(cudaMemcpyAsync(ctx->h_total, ctx->dcount.p, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "totals");
   QGS_CU(cudaStreamSynchronize(st), "sync");
   const int64_t V = (int64_t)ctx->h_total[0];
   const int64_t I = (int64_t)ctx->h_total[1];
+  // primitives whose masks did not fit are tested again by the emission; provide more next frame
+  if (tb_on && !ctx->tbits_fixed && (size_t)ctx->h_total[2] > cap_words)
+    ctx->tbits_want = (size_t)ctx->h_total[2] + ctx->h_total[2] / 4;
   ctx->n_visible = V;
 
   const size_t i1 = (size_t)(I > 0 ? I : 1);
@@ -576,7 +596,8 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
         uint32_t* k0 = reinterpret_cast<uint32_t*>(ctx->inst.p);
         uint32_t* k1 = reinterpret_cast<uint32_t*>(ctx->inst2.p);
         k_emit_packed<uint32_t><<<nblk(V), 256, 0, st>>>(V, sidx, ctx->cnt_sorted.p, ctx->rect.p, ctx->tslab.p,
-                                                         cam->W, cam->H, ctx->offs.p, cp.tiles_x, rb, k0);
+                                                         cam->W, cam->H, ctx->offs.p, cp.tiles_x, rb, k0,
+                                                         tb_on ? ctx->tbits.p : nullptr, ctx->tbits_off.p);
         ++launch_counter();
         QGS_CU(cudaGetLastError(), "emit");
         mark(ctx, 4, st);
@@ -585,7 +606,8 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
         sorted = f2 ? (const void*)k1 : (const void*)k0;
       } else {
         k_emit_packed<uint64_t><<<nblk(V), 256, 0, st>>>(V, sidx, ctx->cnt_sorted.p, ctx->rect.p, ctx->tslab.p,
-                                                         cam->W, cam->H, ctx->offs.p, cp.tiles_x, 32, ctx->inst.p);
+                                                         cam->W, cam->H, ctx->offs.p, cp.tiles_x, 32, ctx->inst.p,
+                                                         tb_on ? ctx->tbits.p : nullptr, ctx->tbits_off.p);
         ++launch_counter();
         QGS_CU(cudaGetLastError(), "emit");
         mark(ctx, 4, st);
@@ -612,10 +634,11 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
     if (N > 0 && I > 0) {
       if (stp)
         k_emit_hit<<<nblk(N), 256, 0, st>>>(N, sv, cp, ctx->count.p, ctx->rect.p, ctx->tslab.p, ctx->offs.p,
-                                            ctx->inst.p, ctx->vals.p);
+                                            ctx->inst.p, ctx->vals.p, tb_on ? ctx->tbits.p : nullptr, ctx->tbits_off.p);
       else
         k_emit<<<nblk(N), 256, 0, st>>>(N, nullptr, ctx->count.p, ctx->rect.p, ctx->tslab.p, cam->W, cam->H,
-                                        ctx->offs.p, ctx->zkey.p, cp.tiles_x, ctx->inst.p, ctx->vals.p);
+                                        ctx->offs.p, ctx->zkey.p, cp.tiles_x, ctx->inst.p, ctx->vals.p,
+                                        tb_on ? ctx->tbits.p : nullptr, ctx->tbits_off.p);
       ++launch_counter();
       QGS_CU(cudaGetLastError(), "emit");
       mark(ctx, 4, st);
@@ -985,6 +1008,13 @@ qgs_status qgs_set_profiling(qgs_ctx* ctx, int32_t enable) {
   return QGS_OK;
 }
 
+qgs_status qgs_set_tile_mask_capacity(qgs_ctx* ctx, int64_t words) {
+  if (!ctx || words < 0) return QGS_EINVAL;
+  ctx->tbits_want = (size_t)words;
+  ctx->tbits_fixed = true;
+  return QGS_OK;
+}
+
 qgs_status qgs_copy_binning(qgs_ctx* ctx, uint64_t* keys, uint32_t* vals, int64_t cap, uint32_t* ranges,
                             int32_t* rects, int64_t* n_instances) {
   if (!ctx) return QGS_EINVAL;
@@ -1186,7 +1216,7 @@ extern "C" qgs_status render_forward_noalloc(const qgs_scene* scene, const qgs_c
   const uint64_t* sorted = inst;
   if (N > 0 && I > 0) {
     k_emit<<<nblk(N), 256, 0, st>>>(N, sidx, count, rect, nullptr, cam->W, cam->H, offs, nullptr, cp.tiles_x, inst,
-                                    nullptr);
+                                    nullptr, nullptr, nullptr);
     QGS_CU(cudaGetLastError(), "emit");
     const bool f2 = radix_sort_u64_keys(inst, inst2, I, 32, 32 + bits_for(ntiles), tmp, st, &e);
     QGS_CU(e, "tile sort");

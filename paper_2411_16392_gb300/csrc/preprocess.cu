@@ -675,7 +675,8 @@ __global__ void __launch_bounds__(256) k_emit_hit(int64_t n, SceneView sc, CamPa
                                                   const short4* __restrict__ rect,
                                                   const TileSlab* __restrict__ tslab,
                                                   const uint32_t* __restrict__ offs, uint64_t* __restrict__ keys,
-                                                  uint32_t* __restrict__ vals) {
+                                                  uint32_t* __restrict__ vals, const uint32_t* __restrict__ tbits,
+                                                  const uint32_t* __restrict__ tbits_off) {
   const int lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t wbase = i - lane;
@@ -690,18 +691,20 @@ __global__ void __launch_bounds__(256) k_emit_hit(int64_t n, SceneView sc, CamPa
     const float uc = __fadd_rn(__fmul_rn(cp.fx, __fdiv_rn(muc[0], muc[2])), cp.cx);
     const float vc = __fadd_rn(__fmul_rn(cp.fy, __fdiv_rn(muc[1], muc[2])), cp.cy);
     const uint32_t off = offs[p];
+    const uint32_t wo = tbits ? tbits_off[p] : kNoTileBits;
     warp_tiles(rect[p], tslab ? tslab + p : nullptr, cp.W, cp.H, [&](uint32_t e, int tx, int ty) {
       const uint32_t tile = (uint32_t)ty * (uint32_t)cp.tiles_x + (uint32_t)tx;
       keys[(size_t)off + e] = ((uint64_t)tile << 32) | hit_key_bits(muc, W, ab.x, ab.y, uc, vc, tx, ty, cp);
       vals[(size_t)off + e] = (uint32_t)p;
-    });
+    }, nullptr, wo != kNoTileBits ? tbits + wo : nullptr);
   }
 }
 
 __global__ void __launch_bounds__(256) k_count_tiles(int64_t n, const TileSlab* __restrict__ tslab, int W, int H,
                                                      uint32_t* __restrict__ count, short4* __restrict__ rect,
                                                      uint32_t* __restrict__ zkey, uint32_t* __restrict__ vflag,
-                                                     uint32_t* __restrict__ counters) {
+                                                     uint32_t* __restrict__ counters, uint32_t* __restrict__ tbits,
+                                                     uint32_t* __restrict__ tbits_off, uint32_t cap_words) {
   __shared__ uint32_t bsum[2], bdone;
   if (threadIdx.x == 0) {
     bsum[0] = bsum[1] = 0u;
@@ -712,12 +715,32 @@ __global__ void __launch_bounds__(256) k_count_tiles(int64_t n, const TileSlab* 
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t wbase = i - lane;
   const uint32_t c0 = i < n ? count[i] : 0u;
+  // words of pass masks for the warp's 32 primitives: one atomic per warp
+  uint32_t woff = kNoTileBits;
+  if (tbits) {
+    const uint32_t words = (c0 + 31u) >> 5;
+    uint32_t incl = words;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += y;
+    }
+    const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
+    uint32_t wbase_words = 0;
+    if (lane == 31 && wtot) wbase_words = atomicAdd(&counters[2], wtot);
+    wbase_words = __shfl_sync(0xffffffffu, wbase_words, 31);
+    const uint64_t end = (uint64_t)wbase_words + incl;
+    if (words && end <= (uint64_t)cap_words) woff = (uint32_t)(end - words);
+    if (i < n) tbits_off[i] = woff;
+  }
   uint32_t mine = 0;
   for (int k = 0; k < 32; ++k) {
     const uint32_t cc = __shfl_sync(0xffffffffu, c0, k);
     if (!cc) continue;
     const int64_t p = wbase + k;
-    const uint32_t c = warp_tiles(rect[p], tslab + p, W, H, [](uint32_t, int, int) {});
+    const uint32_t wo = __shfl_sync(0xffffffffu, woff, k);
+    const uint32_t c = warp_tiles(rect[p], tslab + p, W, H, [](uint32_t, int, int) {},
+                                  wo != kNoTileBits ? tbits + wo : nullptr);
     if (lane == k) mine = c;
   }
   if (i < n) {

@@ -118,30 +118,42 @@ __device__ __forceinline__ bool tile_meets(const TileSlab& t, const TileCol& c, 
 // The whole warp enumerates one primitive's rectangle r in row-major order, 32 tiles at a
 // time (lane l takes tile e = e0 + l, its (tx, ty) advanced without divisions); f(k, tx,
 // ty) runs for every tile that meets the parallelogram and the conic (every tile when t
-// is null), k counting them in row-major order. Returns their number. Call with the same
-// arguments on every lane.
+// is null), k counting them in row-major order. Returns their number. bits_out (when
+// given) receives the pass mask of each group of 32 tiles; bits_in (when given) replays
+// such masks instead of testing. Call with the same arguments on every lane.
+constexpr uint32_t kNoTileBits = 0xFFFFFFFFu;  // primitive without cached tile masks
+
 template <typename F>
-__device__ __forceinline__ uint32_t warp_tiles(short4 r, const TileSlab* t, int W, int H, F&& f) {
+__device__ __forceinline__ uint32_t warp_tiles(short4 r, const TileSlab* t, int W, int H, F&& f,
+                                               uint32_t* bits_out = nullptr, const uint32_t* bits_in = nullptr) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
   const int w = r.y - r.x + 1;
   const uint32_t total = (uint32_t)w * (uint32_t)(r.w - r.z + 1);
   TileSlab ts;
-  if (t) ts = *t;
+  if (t && !bits_in) ts = *t;
   int ty = r.z + lane / w, tx = r.x + lane % w;  // tile e = lane
   int row_y = -1;
   TileRow row{};
   uint32_t base = 0;
   for (uint32_t e0 = 0; e0 < total; e0 += 32) {
-    bool pass = e0 + (uint32_t)lane < total;
-    if (pass && t) {
-      if (ty != row_y) {
-        row = tile_row(ts, ty, H);
-        row_y = ty;
+    uint32_t m;
+    bool pass;
+    if (bits_in) {
+      m = bits_in[e0 >> 5];
+      pass = (m >> lane) & 1u;
+    } else {
+      pass = e0 + (uint32_t)lane < total;
+      if (pass && t) {
+        if (ty != row_y) {
+          row = tile_row(ts, ty, H);
+          row_y = ty;
+        }
+        pass = tile_meets(ts, tile_col(ts, tx, W), row);
       }
-      pass = tile_meets(ts, tile_col(ts, tx, W), row);
+      m = __ballot_sync(0xffffffffu, pass);
+      if (bits_out && lane == 0) bits_out[e0 >> 5] = m;
     }
-    const uint32_t m = __ballot_sync(0xffffffffu, pass);
     if (pass) f(base + __popc(m & lt), tx, ty);
     base += __popc(m);
     tx += 32;  // tile e + 32
@@ -156,9 +168,12 @@ __device__ __forceinline__ uint32_t warp_tiles(short4 r, const TileSlab* t, int 
 // Per primitive with a nonempty rectangle: count its tiles that meet its screen bounds;
 // primitives left with none are culled (count 0, rectangle -1s, depth key 0xFFFFFFFF).
 // Writes the visibility flags (when given) and adds the visible and instance totals
-// to counters[0], counters[1].
+// to counters[0], counters[1]. With tbits: each primitive's pass masks (one word per 32
+// rectangle tiles) go to tbits + tbits_off[i], words taken from counters[2] (the total
+// requested, even beyond cap_words); a primitive that does not fit gets kNoTileBits.
 __global__ void k_count_tiles(int64_t n, const TileSlab* tslab, int W, int H, uint32_t* count, short4* rect,
-                              uint32_t* zkey, uint32_t* vflag, uint32_t* counters);
+                              uint32_t* zkey, uint32_t* vflag, uint32_t* counters, uint32_t* tbits,
+                              uint32_t* tbits_off, uint32_t cap_words);
 
 // ---------------------------------------------------------------- preprocessing
 // Per primitive i: projected state (visible ones only), tile count of the rectangle,
@@ -173,7 +188,8 @@ __global__ void k_preprocess_views(int64_t n, SceneView sc, const CamParams* cps
 // key = (tile << 32) | bits of the depth where the ray of the tile pixel closest to the
 // projected vertex meets the paraboloid; value = primitive.
 __global__ void k_emit_hit(int64_t n, SceneView sc, CamParams cp, const uint32_t* count, const short4* rect,
-                           const TileSlab* tslab, const uint32_t* offs, uint64_t* keys, uint32_t* vals);
+                           const TileSlab* tslab, const uint32_t* offs, uint64_t* keys, uint32_t* vals,
+                           const uint32_t* tbits, const uint32_t* tbits_off);
 // list == nullptr: threads 0..n-1 are primitives 0..n-1; else primitive list[j].
 // pgrad_by_pos: the gradient record of thread j is pgrad[j] (state gathered in list
 // order), else pgrad[primitive].

@@ -61,10 +61,11 @@ struct Slot {
 int64_t request_bytes(const SceneDev& s, const qgs_camera& c, bool bwd) {
   const double P = (double)c.W * c.H;
   const double inst = s.inst_per_pixel * P;
-  // projected state + per-primitive keys/indices/offsets, instance ping-pong buffers,
-  // radix histogram, residue, and the 8 result planes; a backward adds the per-primitive
-  // gradient records, the parameter gradients and the upstream planes
-  double b = s.n * 168.0 + inst * 16.0 + inst / 16.0 + P * 8.0 + P * 32.0;
+  // projected state + per-primitive keys/indices/offsets, tile-test bounds and mask
+  // offsets, instance ping-pong buffers, radix histogram, residue, the 8 result planes and
+  // the tile masks; a backward adds the per-primitive gradient records, the parameter
+  // gradients and the upstream planes
+  double b = s.n * 252.0 + inst * 16.0 + inst / 16.0 + P * 8.0 + P * 32.0 + 16.0 * (1 << 20);
   if (bwd) b += s.n * (80.0 + 4.0 * kGradFloats) + P * 32.0;
   return (int64_t)b + (1 << 20);
 }

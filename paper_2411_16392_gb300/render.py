@@ -165,6 +165,11 @@ class Rasterizer:
                                          C.c_void_p(_stream_ptr(self.device))), self._ctx)
         return grads
 
+    def set_tile_mask_capacity(self, words: int):
+        """Words of the tile-mask store the emission replays (0: the emission tests every
+        tile again). Results never depend on it."""
+        L.check(self.lib.qgs_set_tile_mask_capacity(self._ctx, int(words)), self._ctx)
+
     # ------------------------------------------------------------------ inspection
     def stats(self) -> dict:
         s = L.qgs_frame_stats()

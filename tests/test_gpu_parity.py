@@ -105,6 +105,31 @@ def test_sort_modes_bit_identical(dev):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("order", ["centre", "stp"])
+def test_tile_mask_store_does_not_change_results(dev, order):
+    """The emission replays the tile-count pass's masks; without the store (capacity 0),
+    with one too small for the frame (some primitives tested again) and with the default,
+    the instances and images are identical (sort modes 0 and 1, both orderings)."""
+    sc, cam = scene_small(2, 3000)
+    sc.scale *= np.float32(2.0)
+    ds = _ds(sc, dev)
+    for mode in ((0, 1) if order == "centre" else (0,)):
+        res = []
+        for cap in (None, 0, 64):
+            ras = _ras(dev, sort_mode=mode, order=order)
+            if cap is not None:
+                ras.set_tile_mask_capacity(cap)
+            out = _np(ras.forward(ds, cam))
+            res.append((out, ras.binning()))
+        for out, b in res[1:]:
+            for k in out:
+                assert np.array_equal(out[k], res[0][0][k]), (mode, k)
+            for x, y in zip(b, res[0][1]):
+                assert np.array_equal(x, y), mode
+    with pytest.raises(Exception):
+        _ras(dev).set_tile_mask_capacity(-1)
+
+
 def test_small_scene_backward(dev):
     sc, cam = scene_small(0, 1000)
     ref0 = O.render(sc, cam)
