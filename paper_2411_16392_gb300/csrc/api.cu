@@ -172,11 +172,16 @@ __global__ void k_emit_packed(int64_t V, const uint32_t* __restrict__ sidx, cons
                               const uint32_t* __restrict__ tbits, const uint32_t* __restrict__ tbits_off) {
   const int lane = threadIdx.x & 31;
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  uint32_t c = 0, off = 0, pid = 0;
-  if (r < V) {
+  uint32_t c = 0, off = 0, pid = 0, wo = kNoTileBits;
+  int rxy = 0, rzw = 0;
+  if (r < V) {  // each lane fetches its primitive's entries up front (independent loads)
     c = cnt_sorted[r];
     off = offs[r];
     pid = sidx[r];
+    const short4 rc = rect[pid];
+    rxy = (int)(((uint32_t)(uint16_t)rc.y << 16) | (uint16_t)rc.x);
+    rzw = (int)(((uint32_t)(uint16_t)rc.w << 16) | (uint16_t)rc.z);
+    if (tbits) wo = tbits_off[pid];
   }
   for (int k = 0; k < 32; ++k) {
     const uint32_t cc = __shfl_sync(0xffffffffu, c, k);
@@ -184,11 +189,13 @@ __global__ void k_emit_packed(int64_t V, const uint32_t* __restrict__ sidx, cons
     const uint32_t rr = (uint32_t)(r - lane + k);
     const uint32_t oo = __shfl_sync(0xffffffffu, off, k);
     const uint32_t pp = __shfl_sync(0xffffffffu, pid, k);
-    const uint32_t wo = tbits ? tbits_off[pp] : kNoTileBits;
-    warp_tiles(rect[pp], tslab ? tslab + pp : nullptr, W, H, [&](uint32_t e, int tx, int ty) {
+    const uint32_t wk = __shfl_sync(0xffffffffu, wo, k);
+    const int a = __shfl_sync(0xffffffffu, rxy, k), b = __shfl_sync(0xffffffffu, rzw, k);
+    const short4 rk = make_short4((short)(a & 0xFFFF), (short)(a >> 16), (short)(b & 0xFFFF), (short)(b >> 16));
+    warp_tiles(rk, tslab ? tslab + pp : nullptr, W, H, [&](uint32_t e, int tx, int ty) {
       const uint32_t tile = (uint32_t)ty * (uint32_t)tiles_x + (uint32_t)tx;
       keys[(size_t)oo + e] = ((K)tile << rb) | (K)rr;
-    }, nullptr, wo != kNoTileBits ? tbits + wo : nullptr);
+    }, nullptr, wk != kNoTileBits ? tbits + wk : nullptr);
   }
 }
 
@@ -522,7 +529,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   mark(ctx, 0, st);
   SceneView sv{scene->mean, scene->quat, scene->scale, scene->curv, scene->opacity, scene->sh};
   if (N > 0) {
-    k_preprocess<<<nblk(N), 256, 0, st>>>(N, sv, cp, ctx->state.p, ctx->count.p, ctx->zkey.p,
+    k_preprocess<<<pre_blocks(N), 256, 0, st>>>(N, sv, cp, ctx->state.p, ctx->count.p, ctx->zkey.p,
                                           sm == 0 ? nullptr : ctx->idx.p, ctx->rect.p, nullptr, nullptr,
                                           ctx->tslab.p);
     ++launch_counter();
@@ -827,7 +834,7 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
   QGS_CU(cudaMemsetAsync(ctx->dcount.p, 0, sizeof(uint32_t) * 4, st), "memset counters");
   SceneView sv{scene->mean, scene->quat, scene->scale, scene->curv, scene->opacity, scene->sh};
   if (N > 0) {
-    k_preprocess_views<<<dim3(nblk(N), (unsigned)V), 256, 0, st>>>(N, sv, d_cp, ctx->state.p, ctx->count.p,
+    k_preprocess_views<<<dim3(pre_blocks(N), (unsigned)V), 256, 0, st>>>(N, sv, d_cp, ctx->state.p, ctx->count.p,
                                                                    ctx->zkey.p, ctx->idx.p, ctx->rect.p,
                                                                    ctx->dcount.p);
     ++launch_counter();
@@ -1196,7 +1203,7 @@ extern "C" qgs_status render_forward_noalloc(const qgs_scene* scene, const qgs_c
   QGS_CU(cudaMemsetAsync(stats, 0, sizeof(RasterStats), st), "memset");
   SceneView sv{scene->mean, scene->quat, scene->scale, scene->curv, scene->opacity, scene->sh};
   if (N > 0) {
-    k_preprocess<<<nblk(N), 256, 0, st>>>(N, sv, cp, state, count, zkey, idx, rect, visible, nullptr, nullptr);
+    k_preprocess<<<pre_blocks(N), 256, 0, st>>>(N, sv, cp, state, count, zkey, idx, rect, visible, nullptr, nullptr);
     QGS_CU(cudaGetLastError(), "k_preprocess");
   }
   cudaError_t e = cudaSuccess;

@@ -242,21 +242,95 @@ __device__ __forceinline__ uint32_t preprocess_one(int64_t i, const SceneView& s
                                                    short4* __restrict__ rect, uint32_t idx_base = 0,
                                                    TileSlab* __restrict__ tslab = nullptr);
 
+// Camera-space centre of primitive i (bit-exact: correctly rounded, fixed order).
+__device__ __forceinline__ void centre_cam(int64_t i, const SceneView& sc, const CamParams& cp, float muc[3]) {
+  const float mx = sc.mean[3 * i], my = sc.mean[3 * i + 1], mz = sc.mean[3 * i + 2];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+    muc[r] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(cp.Rc[3 * r], mx), __fmul_rn(cp.Rc[3 * r + 1], my)),
+                                 __fmul_rn(cp.Rc[3 * r + 2], mz)),
+                       cp.tc[r]);
+}
+
+// Early exit for primitives the full recipe culls anyway: centre not in front of the
+// near plane, or the sphere that holds the support box (every corner lies within
+// 3 sqrt(3) max(s_u, s_v) of the centre) entirely beyond one side plane of the image
+// (then every projected box point, near-plane points included, falls outside it). The
+// sphere is enlarged by 1 % + 1e-6 |mu_c| against rounding, so no primitive the exact
+// recipe keeps is dropped.
+__device__ __forceinline__ bool may_survive(const float muc[3], float2 s, const CamParams& cp) {
+  const float rad = 5.1961524f * fmaxf(s.x, s.y) * 1.01f + 1e-6f * (fabsf(muc[0]) + fabsf(muc[1]) + fabsf(muc[2]));
+  const float x = muc[0], y = muc[1], z = muc[2];
+  const float rx = (float)cp.W - cp.cx, ry = (float)cp.H - cp.cy;
+  const bool outside = !(z > cp.near) || -(cp.fx * x + cp.cx * z) > rad * sqrtf(cp.fx * cp.fx + cp.cx * cp.cx) ||
+                       (cp.fx * x - rx * z) > rad * sqrtf(cp.fx * cp.fx + rx * rx) ||
+                       -(cp.fy * y + cp.cy * z) > rad * sqrtf(cp.fy * cp.fy + cp.cy * cp.cy) ||
+                       (cp.fy * y - ry * z) > rad * sqrtf(cp.fy * cp.fy + ry * ry);
+  return !outside;
+}
+
+// One CTA preprocesses kPreChunks x 256 consecutive primitives in two phases: the early
+// exit for all of them (culled ones get their empty entries), then the full recipe for
+// the survivors gathered in shared memory, so that the expensive phase runs on full warps
+// although only a small fraction of a large scene survives. Returns, for the calling
+// thread, the visible count and tile total of the survivors it handled.
+__device__ __forceinline__ void preprocess_block(int64_t n, const SceneView& sc, const CamParams& cp,
+                                                 PrimState* __restrict__ state, uint32_t* __restrict__ count,
+                                                 uint32_t* __restrict__ zkey, uint32_t* __restrict__ idx,
+                                                 short4* __restrict__ rect, uint32_t idx_base,
+                                                 TileSlab* __restrict__ tslab, uint32_t* __restrict__ vflag,
+                                                 uint32_t& vis, uint32_t& tot) {
+  __shared__ uint32_t list[kPreChunks * 256];
+  __shared__ uint32_t nlist;
+  if (threadIdx.x == 0) nlist = 0;
+  __syncthreads();
+  const int64_t first = (int64_t)blockIdx.x * (kPreChunks * 256);
+  const int lane = threadIdx.x & 31;
+  for (int c = 0; c < kPreChunks; ++c) {
+    const int64_t i = first + c * 256 + threadIdx.x;
+    bool keep = false;
+    if (i < n) {
+      float muc[3];
+      centre_cam(i, sc, cp, muc);
+      keep = may_survive(muc, reinterpret_cast<const float2*>(sc.scale)[i], cp);
+      if (!keep) {
+        if (idx) idx[i] = idx_base + (uint32_t)i;
+        count[i] = 0u;
+        zkey[i] = 0xFFFFFFFFu;
+        rect[i] = make_short4(-1, -1, -1, -1);
+        if (vflag) vflag[i] = 0u;
+      }
+    }
+    const uint32_t m = __ballot_sync(0xffffffffu, keep);
+    uint32_t slot = 0;
+    if (lane == 0 && m) slot = atomicAdd(&nlist, (uint32_t)__popc(m));
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    if (keep) list[slot + __popc(m & ((1u << lane) - 1u))] = (uint32_t)(i - first);
+  }
+  __syncthreads();
+  const uint32_t nl = nlist;
+  vis = tot = 0;
+  for (uint32_t t = threadIdx.x; t < nl; t += 256) {
+    const int64_t i = first + list[t];
+    const uint32_t cnt = preprocess_one(i, sc, cp, state, count, zkey, idx, rect, idx_base, tslab);
+    if (vflag) vflag[i] = cnt ? 1u : 0u;
+    vis += cnt ? 1u : 0u;
+    tot += cnt;
+  }
+}
+
 __global__ void __launch_bounds__(256) k_preprocess(int64_t n, SceneView sc, CamParams cp, PrimState* __restrict__ state,
                                                     uint32_t* __restrict__ count, uint32_t* __restrict__ zkey,
                                                     uint32_t* __restrict__ idx, short4* __restrict__ rect,
                                                     uint32_t* __restrict__ counters, uint32_t* __restrict__ vflag,
                                                     TileSlab* __restrict__ tslab) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = i < n;
-  uint32_t cnt = 0;
-  if (active) cnt = preprocess_one(i, sc, cp, state, count, zkey, idx, rect, 0, tslab);
-  if (active && vflag) vflag[i] = cnt ? 1u : 0u;
+  uint32_t vis, tot;
+  preprocess_block(n, sc, cp, state, count, zkey, idx, rect, 0, tslab, vflag, vis, tot);
   if (!counters) return;
   // one atomic per CTA and counter (per-warp atomics on two addresses serialise)
   __shared__ uint32_t red[2][8];
-  const uint32_t vis = __reduce_add_sync(0xffffffffu, cnt ? 1u : 0u);
-  const uint32_t tot = __reduce_add_sync(0xffffffffu, cnt);
+  vis = __reduce_add_sync(0xffffffffu, vis);
+  tot = __reduce_add_sync(0xffffffffu, tot);
   if ((threadIdx.x & 31) == 0) {
     red[0][threadIdx.x >> 5] = vis;
     red[1][threadIdx.x >> 5] = tot;
@@ -275,13 +349,11 @@ __global__ void __launch_bounds__(256) k_preprocess_views(int64_t n, SceneView s
                                                           PrimState* __restrict__ state, uint32_t* __restrict__ count,
                                                           uint32_t* __restrict__ zkey, uint32_t* __restrict__ idx,
                                                           short4* __restrict__ rect, uint32_t* __restrict__ n_visible) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t off = (int64_t)blockIdx.y * n;
   const CamParams cp = cps[blockIdx.y];
-  uint32_t vis = 0;
-  if (i < n)
-    vis = preprocess_one(i, sc, cp, state + off, count + off, zkey + off, idx + off, rect + off, (uint32_t)off) ? 1u
-                                                                                                              : 0u;
+  uint32_t vis, tot;
+  preprocess_block(n, sc, cp, state + off, count + off, zkey + off, idx + off, rect + off, (uint32_t)off, nullptr,
+                   nullptr, vis, tot);
   vis = __reduce_add_sync(0xffffffffu, vis);
   __shared__ uint32_t red[8];  // one atomic per CTA
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = vis;
@@ -309,33 +381,12 @@ __device__ __forceinline__ uint32_t preprocess_one(int64_t i, const SceneView& s
 
   // --- bit-exact part: centre depth, box, tile rectangle -------------------------
   float muc[3];
-#pragma unroll
-  for (int r = 0; r < 3; ++r)
-    muc[r] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(cp.Rc[3 * r], mx), __fmul_rn(cp.Rc[3 * r + 1], my)),
-                                 __fmul_rn(cp.Rc[3 * r + 2], mz)),
-                       cp.tc[r]);
-  // Early exit for primitives the recipe below culls anyway: centre not in front of the
-  // near plane, or the sphere that holds the support box (every corner lies within
-  // 3 sqrt(3) max(s_u, s_v) of the centre) entirely beyond one side plane of the image
-  // (then every projected box point, near-plane points included, falls outside it). The
-  // sphere is enlarged by 1 % + 1e-6 |mu_c| against rounding, so no primitive the exact
-  // recipe keeps is dropped.
-  {
-    const float rad = 5.1961524f * fmaxf(s.x, s.y) * 1.01f +
-                      1e-6f * (fabsf(muc[0]) + fabsf(muc[1]) + fabsf(muc[2]));
-    const float x = muc[0], y = muc[1], z = muc[2];
-    const float rx = (float)cp.W - cp.cx, ry = (float)cp.H - cp.cy;
-    const bool outside = !(z > cp.near) ||
-                         -(cp.fx * x + cp.cx * z) > rad * sqrtf(cp.fx * cp.fx + cp.cx * cp.cx) ||
-                         (cp.fx * x - rx * z) > rad * sqrtf(cp.fx * cp.fx + rx * rx) ||
-                         -(cp.fy * y + cp.cy * z) > rad * sqrtf(cp.fy * cp.fy + cp.cy * cp.cy) ||
-                         (cp.fy * y - ry * z) > rad * sqrtf(cp.fy * cp.fy + ry * ry);
-    if (outside) {
-      count[i] = 0u;
-      zkey[i] = 0xFFFFFFFFu;
-      rect[i] = rc;
-      return 0u;
-    }
+  centre_cam(i, sc, cp, muc);
+  if (!may_survive(muc, s, cp)) {
+    count[i] = 0u;
+    zkey[i] = 0xFFFFFFFFu;
+    rect[i] = rc;
+    return 0u;
   }
   const float4 q = reinterpret_cast<const float4*>(sc.quat)[i];
   const float2 ab = reinterpret_cast<const float2*>(sc.curv)[i];
@@ -733,13 +784,28 @@ __global__ void __launch_bounds__(256) k_count_tiles(int64_t n, const TileSlab* 
     if (words && end <= (uint64_t)cap_words) woff = (uint32_t)(end - words);
     if (i < n) tbits_off[i] = woff;
   }
+  // the warp's rectangles and screen bounds, loaded up front (independent loads) and
+  // handed out per primitive from registers and shared memory
+  __shared__ TileSlab sts[256];
+  short4 rc0 = make_short4(0, 0, 0, 0);
+  if (c0) {
+    rc0 = rect[i];
+    const float4* src = reinterpret_cast<const float4*>(tslab + i);
+    float4* dst = reinterpret_cast<float4*>(&sts[threadIdx.x]);
+#pragma unroll
+    for (int q = 0; q < (int)(sizeof(TileSlab) / 16); ++q) dst[q] = __ldg(src + q);
+  }
+  __syncwarp();
+  const int rxy = (int)(((uint32_t)(uint16_t)rc0.y << 16) | (uint16_t)rc0.x);
+  const int rzw = (int)(((uint32_t)(uint16_t)rc0.w << 16) | (uint16_t)rc0.z);
   uint32_t mine = 0;
   for (int k = 0; k < 32; ++k) {
     const uint32_t cc = __shfl_sync(0xffffffffu, c0, k);
     if (!cc) continue;
-    const int64_t p = wbase + k;
+    const int a = __shfl_sync(0xffffffffu, rxy, k), b = __shfl_sync(0xffffffffu, rzw, k);
+    const short4 rk = make_short4((short)(a & 0xFFFF), (short)(a >> 16), (short)(b & 0xFFFF), (short)(b >> 16));
     const uint32_t wo = __shfl_sync(0xffffffffu, woff, k);
-    const uint32_t c = warp_tiles(rect[p], tslab + p, W, H, [](uint32_t, int, int) {},
+    const uint32_t c = warp_tiles(rk, &sts[(threadIdx.x & ~31) + k], W, H, [](uint32_t, int, int) {},
                                   wo != kNoTileBits ? tbits + wo : nullptr);
     if (lane == k) mine = c;
   }

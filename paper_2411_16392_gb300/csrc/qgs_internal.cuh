@@ -133,14 +133,21 @@ __device__ __forceinline__ uint32_t warp_tiles(short4 r, const TileSlab* t, int 
   TileSlab ts;
   if (t && !bits_in) ts = *t;
   int ty = r.z + lane / w, tx = r.x + lane % w;  // tile e = lane
+  const int sy = 32 / w, sx = 32 - sy * w;          // tile e + 32: sy rows and sx columns on
   int row_y = -1;
   TileRow row{};
   uint32_t base = 0;
+  uint32_t words = 0;  // bits_in: lane l holds mask word 32 g + l of the current group g
   for (uint32_t e0 = 0; e0 < total; e0 += 32) {
     uint32_t m;
     bool pass;
     if (bits_in) {
-      m = bits_in[e0 >> 5];
+      const uint32_t wi = e0 >> 5;
+      if ((wi & 31u) == 0) {
+        const uint32_t wl = wi + (uint32_t)lane;
+        words = wl < ((total + 31u) >> 5) ? bits_in[wl] : 0u;
+      }
+      m = __shfl_sync(0xffffffffu, words, (int)(wi & 31u));
       pass = (m >> lane) & 1u;
     } else {
       pass = e0 + (uint32_t)lane < total;
@@ -156,8 +163,9 @@ __device__ __forceinline__ uint32_t warp_tiles(short4 r, const TileSlab* t, int 
     }
     if (pass) f(base + __popc(m & lt), tx, ty);
     base += __popc(m);
-    tx += 32;  // tile e + 32
-    while (tx > r.y) {
+    tx += sx;  // tile e + 32
+    ty += sy;
+    if (tx > r.y) {
       tx -= w;
       ++ty;
     }
@@ -176,6 +184,10 @@ __global__ void k_count_tiles(int64_t n, const TileSlab* tslab, int W, int H, ui
                               uint32_t* tbits_off, uint32_t cap_words);
 
 // ---------------------------------------------------------------- preprocessing
+// k_preprocess / k_preprocess_views: 256 threads per CTA, kPreChunks x 256 primitives per
+// CTA (the grid is pre_blocks(n) wide).
+constexpr int kPreChunks = 8;
+inline unsigned pre_blocks(int64_t n) { return (unsigned)((n + kPreChunks * 256 - 1) / (kPreChunks * 256)); }
 // Per primitive i: projected state (visible ones only), tile count of the rectangle,
 // depth key, tile rectangle; idx[i] = i, vflag[i] = (count > 0) and the screen bounds
 // (tslab) when given; counters[0] += visible, counters[1] += tile instances when given.
