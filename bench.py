@@ -281,10 +281,13 @@ def run_gpu(args):
         step()
     torch.cuda.synchronize()
 
-    # ---- timed region: device time of K steps (CUDA events on the launching stream)
+    # ---- timed region: device time of K steps (CUDA events on the launching stream). The
+    # per-pair counters are compiled out of the compositing kernels here (they are collected
+    # in an extra step below); stage events are recorded and the last step's are read after.
     lib = ras.lib
-    import ctypes
     L.check(lib.qgs_set_profiling(ras._ctx, 1), ras._ctx)
+    ras.set_pair_counters(False)
+    step()
     clocks = ClockSampler(local)
     clocks.start()
     if world > 1:
@@ -293,22 +296,31 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    stage = {"ms_raster_fwd": [], "ms_raster_bwd": [], "ms_preprocess": [], "ms_depth_sort": [], "ms_emit": [],
-             "ms_tile_sort": [], "ms_preprocess_bwd": []}
-    st = None
     e0.record(stream)
     for _ in range(args.steps):
         step()
-        st = ras.stats()  # reads this step's stage events (synchronises the stream)
-        for k in stage:
-            stage[k].append(st[k])
     e1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    L.check(lib.qgs_set_profiling(ras._ctx, 0), ras._ctx)
+    st_timed = ras.stats()  # stage times of the last timed step
     ms = e0.elapsed_time(e1) / args.steps
+    # stage times averaged over a few more steps (read after each one), then the pair
+    # counters of one step
+    stage = {"ms_raster_fwd": [], "ms_raster_bwd": [], "ms_preprocess": [], "ms_depth_sort": [], "ms_emit": [],
+             "ms_tile_sort": [], "ms_preprocess_bwd": []}
+    for _ in range(min(args.steps, 5)):
+        step()
+        stt = ras.stats()
+        for k in stage:
+            stage[k].append(stt[k])
+    ras.set_pair_counters(True)
+    step()
+    st = ras.stats()
+    st["ms_raster_bwd_timed"] = st_timed["ms_raster_bwd"]
+    st["ms_raster_fwd_timed"] = st_timed["ms_raster_fwd"]
+    L.check(lib.qgs_set_profiling(ras._ctx, 0), ras._ctx)
     t = torch.tensor([ms], device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -413,7 +425,9 @@ def _report(args, rank, world, sc, cam, st, stage, clk, ms_max, value, e2e_value
     # ---- roofline of the dominant kernel (FP32 ALU bound)
     peaks, peak_kind = _peaks()
     mean = {k: (sum(v) / len(v) if v and min(v) >= 0 else None) for k, v in stage.items()}
-    bwd_ms, fwd_ms = mean["ms_raster_bwd"], mean["ms_raster_fwd"]
+    # the compositing kernels' durations in the last timed step (CUDA events on their stream)
+    bwd_ms = st["ms_raster_bwd_timed"] if st.get("ms_raster_bwd_timed", -1) >= 0 else mean["ms_raster_bwd"]
+    fwd_ms = st["ms_raster_fwd_timed"] if st.get("ms_raster_fwd_timed", -1) >= 0 else mean["ms_raster_fwd"]
     flops_fwd = (st["pair_evals"] * FLOP_EVAL + st["pair_isect"] * FLOP_ISECT + st["pair_hits"] * FLOP_HIT
                  + st["pair_blended"] * FLOP_BLEND)
     # backward recomputes the pairs up to each pixel's last blended one

@@ -79,6 +79,7 @@ EXPORTS = [
     ("qgs_copy_residue", C.c_int, [_P, _P, _P]),
     ("qgs_set_profiling", C.c_int, [_P, C.c_int32]),
     ("qgs_set_tile_mask_capacity", C.c_int, [_P, C.c_int64]),
+    ("qgs_set_pair_counters", C.c_int, [_P, C.c_int32]),
     ("render_forward_batch", C.c_int, [_P, C.POINTER(qgs_scene), C.c_int32, C.POINTER(qgs_camera),
                                        C.POINTER(qgs_image), _P]),
     ("render_forward_noalloc", C.c_int, [C.POINTER(qgs_scene), C.POINTER(qgs_camera), C.POINTER(qgs_image), _P]),

@@ -301,6 +301,8 @@ struct qgs_ctx {
   // profiling: events at stage boundaries (forward 0..6, backward 7..9)
   bool profiling = false;
   bool have_fwd_times = false, have_bwd_times = false;
+  bool pair_counters = true;                   // compile the per-pair counters into the compositing
+  bool counted_fwd = true, counted_bwd = true;  // the last forward / backward collected them
   cudaEvent_t ev[10] = {};
   int64_t launches_fwd = 0, launches_bwd = 0;
   CamParams cp{};
@@ -697,8 +699,11 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   else
     QGS_CU(launch_raster_fwd(ctx->cfg.density == 1, extra, (unsigned)ntiles, st, ctx->ranges.p, ctx->ids,
                              ctx->id_stride, ctx->raster_state, rp, out->rgb, out->alpha, out->depth, out->normal,
-                             ctx->T_final.p, ctx->n_contrib.p, ex, ctx->stats.p, ctx->tile_order, ctx->inst_used.p),
+                             ctx->T_final.p, ctx->n_contrib.p, ex, ctx->pair_counters ? ctx->stats.p : nullptr,
+                             ctx->tile_order, ctx->inst_used.p),
            "k_raster_fwd");
+  ctx->counted_fwd = stp || ctx->pair_counters;
+  ctx->counted_bwd = false;
   ctx->stp = stp;
   ++launch_counter();
   mark(ctx, 6, st);
@@ -950,9 +955,10 @@ qgs_status render_backward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camer
   else
     QGS_CU(launch_raster_bwd(euclid, extra, (unsigned)ntiles, st, ctx->ranges.p, ctx->ids, ctx->id_stride,
                              ctx->raster_state, rp, grad_out->rgb, grad_out->alpha, grad_out->depth,
-                             grad_out->normal, ctx->T_final.p, ctx->n_contrib.p, eg, ctx->pgrad.p, ctx->stats.p,
-                             ctx->tile_order, ctx->inst_used.p),
+                             grad_out->normal, ctx->T_final.p, ctx->n_contrib.p, eg, ctx->pgrad.p,
+                             ctx->pair_counters ? ctx->stats.p : nullptr, ctx->tile_order, ctx->inst_used.p),
            "k_raster_bwd");
+  ctx->counted_bwd = ctx->stp || ctx->pair_counters;
   ++launch_counter();
   mark(ctx, 8, st);
   SceneView sv{scene->mean, scene->quat, scene->scale, scene->curv, scene->opacity, scene->sh};
@@ -981,13 +987,14 @@ qgs_status qgs_get_frame_stats(qgs_ctx* ctx, qgs_frame_stats* out) {
   out->n_visible = ctx->n_visible;  // device counter read by the forward
   out->n_instances = ctx->n_inst;
   out->n_tiles = ctx->n_tiles_total;
-  out->pair_evals = (int64_t)rs.pair_evals;
-  out->pair_isect = (int64_t)rs.pair_isect;
-  out->pair_hits = (int64_t)rs.pair_hits;
-  out->pair_blended = (int64_t)rs.pair_blended;
-  out->grazing_resolves = (int64_t)rs.grazing;
-  out->bwd_pairs = (int64_t)rs.bwd_pairs;
-  out->bwd_contrib = (int64_t)rs.bwd_contrib;
+  const int64_t nf = -1;  // counters not collected (qgs_set_pair_counters)
+  out->pair_evals = ctx->counted_fwd ? (int64_t)rs.pair_evals : nf;
+  out->pair_isect = ctx->counted_fwd ? (int64_t)rs.pair_isect : nf;
+  out->pair_hits = ctx->counted_fwd ? (int64_t)rs.pair_hits : nf;
+  out->pair_blended = ctx->counted_fwd ? (int64_t)rs.pair_blended : nf;
+  out->grazing_resolves = ctx->counted_fwd ? (int64_t)rs.grazing : nf;
+  out->bwd_pairs = ctx->counted_bwd ? (int64_t)rs.bwd_pairs : nf;
+  out->bwd_contrib = ctx->counted_bwd ? (int64_t)rs.bwd_contrib : nf;
   out->launches_fwd = ctx->launches_fwd;
   out->launches_bwd = ctx->launches_bwd;
   auto el = [&](int a, int b) {
@@ -1012,6 +1019,12 @@ qgs_status qgs_set_profiling(qgs_ctx* ctx, int32_t enable) {
     for (int i = 0; i < 10; ++i) QGS_CU(cudaEventCreate(&ctx->ev[i]), "cudaEventCreate");
   }
   ctx->profiling = enable != 0;
+  return QGS_OK;
+}
+
+qgs_status qgs_set_pair_counters(qgs_ctx* ctx, int32_t enable) {
+  if (!ctx) return QGS_EINVAL;
+  ctx->pair_counters = enable != 0;
   return QGS_OK;
 }
 

@@ -764,7 +764,6 @@ __global__ void __launch_bounds__(256) k_count_tiles(int64_t n, const TileSlab* 
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t wbase = i - lane;
   const uint32_t c0 = i < n ? count[i] : 0u;
   // words of pass masks for the warp's 32 primitives: one atomic per warp
   uint32_t woff = kNoTileBits;

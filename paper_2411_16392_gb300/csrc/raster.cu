@@ -85,7 +85,7 @@ __device__ __forceinline__ float arc_ratio_prime(float u, float F) {
     p = fmaf(p, u2, 1.f / 3.f);
     return u * p;
   }
-  return (sqrtf(fmaf(u, u, 1.f)) - F) / u;
+  return __fdividef(sqrt_approx(fmaf(u, u, 1.f)) - F, u);
 }
 
 // d(F^2)/du: geodesic 2 F F'(u); Euclidean (F^2 = 1 + u^2/4) u/2.
@@ -94,7 +94,7 @@ __device__ __forceinline__ float f2_prime(float u, float F2) {
   if constexpr (EUCLID) {
     return 0.5f * u;
   } else {
-    const float F = sqrtf(F2);
+    const float F = sqrt_approx(F2);
     return 2.f * F * arc_ratio_prime(u, F);
   }
 }
@@ -218,11 +218,11 @@ struct Curv {
 };
 __device__ __forceinline__ float curvature(float a, float b, float x, float y) {
   const float S = fmaf(4.f * a * a, x * x, fmaf(4.f * b * b, y * y, 1.f));
-  return 4.f * a * b / (S * S);
+  return __fdividef(4.f * a * b, S * S);
 }
 __device__ __forceinline__ Curv curvature_grad(float a, float b, float x, float y) {
   const float S = fmaf(4.f * a * a, x * x, fmaf(4.f * b * b, y * y, 1.f));
-  const float iS = 1.f / S, iS2 = iS * iS;
+  const float iS = __fdividef(1.f, S), iS2 = iS * iS;
   Curv c;
   c.K = 4.f * a * b * iS2;
   const float c3 = 2.f * c.K * iS;  // 8ab / S^3
@@ -240,7 +240,7 @@ __device__ __forceinline__ Curv curvature_grad(float a, float b, float x, float 
 // A0 A2 - A1^2 with A_k = sum_i w_i tau_i^k for any shift tau = t - c; c is the pixel's
 // first blended depth, which keeps the two terms small (no cancellation at the camera
 // distance). The per-pixel residue (c, A1, A2) serves its backward.
-template <bool EUCLID, bool EXTRA>
+template <bool EUCLID, bool EXTRA, bool STATS>
 __device__ __forceinline__ void raster_fwd_tile(PrimState* sm, uint8_t* used, int tile, int local_tile,
                                                 const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids,
                                                 int id_stride, const PrimState* __restrict__ state,
@@ -341,8 +341,8 @@ __device__ __forceinline__ void raster_fwd_tile(PrimState* sm, uint8_t* used, in
       }
     }
   }
-  // counters: one atomic per warp and counter
-  if (stats) {
+  // counters: one atomic per warp and counter (without STATS the counts are dead code)
+  if (STATS && stats) {
     const unsigned ev = __reduce_add_sync(FULL, evals), is = __reduce_add_sync(FULL, isect);
     const unsigned hi = __reduce_add_sync(FULL, hits), bl = __reduce_add_sync(FULL, blended);
     const unsigned gzz = __reduce_add_sync(FULL, grazes);
@@ -356,7 +356,7 @@ __device__ __forceinline__ void raster_fwd_tile(PrimState* sm, uint8_t* used, in
   }
 }
 
-template <bool EUCLID, bool EXTRA>
+template <bool EUCLID, bool EXTRA, bool STATS>
 __global__ void __launch_bounds__(BLOCK, 4)
     k_raster_fwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids, int id_stride,
                  const PrimState* __restrict__ state, RasterParams rp, float* __restrict__ out_rgb,
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(BLOCK, 4)
   __shared__ PrimState sm[BLOCK];
   __shared__ uint8_t used[BLOCK];
   const int tile = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;
-  raster_fwd_tile<EUCLID, EXTRA>(sm, used, tile, tile, ranges, ids, id_stride, state, rp, out_rgb, out_alpha,
+  raster_fwd_tile<EUCLID, EXTRA, STATS>(sm, used, tile, tile, ranges, ids, id_stride, state, rp, out_rgb, out_alpha,
                                  out_depth, out_normal, T_final, n_contrib, ex, stats, inst_used);
 }
 
@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(BLOCK, 3)
   }
   const ViewDesc& vd = views[lo];
   const RasterParams rp = vd.rp;
-  raster_fwd_tile<EUCLID, EXTRA>(sm, used, tile, tile - (int)tile_base[lo], ranges, ids, id_stride, state, rp,
+  raster_fwd_tile<EUCLID, EXTRA, true>(sm, used, tile, tile - (int)tile_base[lo], ranges, ids, id_stride, state, rp,
                                  vd.rgb, vd.alpha, vd.depth, vd.normal, vd.T_final, vd.n_contrib, vd.ex, stats,
                                  nullptr);
 }
@@ -470,7 +470,7 @@ __device__ __forceinline__ float pair_grad(const PrimState& P, const Hit& h, flo
   }
   const float wgx = w * gX;
   const float after = FWD_ORDER ? S_ref - (S_prefix + wgx) : S_ref;  // sum of w_j g.X_j, j after i
-  const float dal = T * gX - (after - pg.gA * pg.Tfin) / onem;
+  const float dal = T * gX - __fdividef(after - pg.gA * pg.Tfin, onem);
   v[17] = w * pg.gR;
   v[18] = w * pg.gG;
   v[19] = w * pg.gB;
@@ -517,7 +517,7 @@ __device__ __forceinline__ float pair_grad(const PrimState& P, const Hit& h, flo
   db += 2.f * y * gmy;
   // the root moves with the parameters: t(theta) from f(p_hat(t)) = 0
   const float den = nlx * h.dx + nly * h.dy - h.dz;
-  const float kk = den != 0.f ? (gx * h.dx + gy * h.dy + d_t) / den : 0.f;
+  const float kk = den != 0.f ? __fdividef(gx * h.dx + gy * h.dy + d_t, den) : 0.f;
   const float hhx = gx - kk * nlx, hhy = gy - kk * nly, hhz = kk;
   da -= kk * x * x;
   db -= kk * y * y;
@@ -586,7 +586,7 @@ __device__ __forceinline__ float warp_reduce_scatter20(const float v[32], int& k
 // D = A0 A2 - A1^2 (A0 = 1 - T_final, A1, A2 the forward's shifted moments), dL/dA0 =
 // g_D A2 joins the alpha gradient, and tau = t - c and tau^2 act as two more blended
 // channels with upstream gradients -2 g_D A1 and g_D A0.
-template <bool EUCLID, bool EXTRA>
+template <bool EUCLID, bool EXTRA, bool STATS>
 __global__ void __launch_bounds__(BLOCK, 3)
     k_raster_bwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids, int id_stride,
                  const PrimState* __restrict__ state, RasterParams rp, const float* __restrict__ g_rgb,
@@ -650,7 +650,7 @@ __global__ void __launch_bounds__(BLOCK, 3)
           if (al >= rp.alpha_min) {
             contrib = true;
             ++n_contrib_pairs;
-            T = T / (1.f - al);  // T_i from T_{i+1}
+            T = __fdividef(T, 1.f - al);  // T_i from T_{i+1}
             Sdot += pair_grad<EUCLID, EXTRA, false>(sm[j], h, oG, al, T, xn, yn, rp, pg, Sdot, 0.f, v);
           }
         }
@@ -678,7 +678,7 @@ __global__ void __launch_bounds__(BLOCK, 3)
       }
     }
   }
-  if (stats) {
+  if (STATS && stats) {
     const unsigned np = __reduce_add_sync(FULL, n_pairs), nc = __reduce_add_sync(FULL, n_contrib_pairs);
     if ((threadIdx.x & 31) == 0) {
       atomicAdd(&stats->bwd_pairs, (unsigned long long)np);
@@ -980,15 +980,22 @@ __global__ void __launch_bounds__(BLOCK, 2)
     }                                                                    \
   } while (0)
 
+// The same with the pair counters (S_) compiled in or out.
+#define QGS_RASTER_DISPATCH_S(euclid, extra, stats, ...)                        \
+  do {                                                                          \
+    if (stats) { constexpr bool S_ = true; QGS_RASTER_DISPATCH(euclid, extra, __VA_ARGS__); }  \
+    else { constexpr bool S_ = false; QGS_RASTER_DISPATCH(euclid, extra, __VA_ARGS__); }       \
+  } while (0)
+
 cudaError_t launch_raster_fwd(bool euclid, bool extra, unsigned grid, cudaStream_t st, const uint2* ranges,
                               const uint32_t* ids, int id_stride, const PrimState* state, const RasterParams& rp,
                               float* out_rgb, float* out_alpha, float* out_depth, float* out_normal, float* T_final,
                               uint32_t* n_contrib, const ExtraPlanes& ex, RasterStats* stats,
                               const uint32_t* tile_order, uint8_t* inst_used) {
-  QGS_RASTER_DISPATCH(euclid, extra,
-                      k_raster_fwd<E_, X_><<<grid, BLOCK, 0, st>>>(ranges, ids, id_stride, state, rp, out_rgb,
-                                                                   out_alpha, out_depth, out_normal, T_final,
-                                                                   n_contrib, ex, stats, tile_order, inst_used));
+  QGS_RASTER_DISPATCH_S(euclid, extra, stats != nullptr,
+                        k_raster_fwd<E_, X_, S_><<<grid, BLOCK, 0, st>>>(ranges, ids, id_stride, state, rp, out_rgb,
+                                                                         out_alpha, out_depth, out_normal, T_final,
+                                                                         n_contrib, ex, stats, tile_order, inst_used));
   return cudaGetLastError();
 }
 
@@ -1008,14 +1015,14 @@ cudaError_t launch_raster_bwd(bool euclid, bool extra, unsigned grid, cudaStream
                               const float* T_final, const uint32_t* n_contrib, const ExtraGrads& eg, float* pgrad,
                               RasterStats* stats, const uint32_t* tile_order, const uint8_t* inst_used) {
   cudaError_t e = cudaSuccess;
-  QGS_RASTER_DISPATCH(euclid, extra, {
+  QGS_RASTER_DISPATCH_S(euclid, extra, stats != nullptr, {
     // the records, accumulators and flags exceed the 48 KB static limit
-    e = cudaFuncSetAttribute(k_raster_bwd<E_, X_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_raster_bwd<E_, X_, S_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)RASTER_BWD_SMEM);
     if (e == cudaSuccess)
-      k_raster_bwd<E_, X_><<<grid, BLOCK, RASTER_BWD_SMEM, st>>>(ranges, ids, id_stride, state, rp, g_rgb, g_alpha,
-                                                                 g_depth, g_normal, T_final, n_contrib, eg, pgrad,
-                                                                 stats, tile_order, inst_used);
+      k_raster_bwd<E_, X_, S_><<<grid, BLOCK, RASTER_BWD_SMEM, st>>>(ranges, ids, id_stride, state, rp, g_rgb,
+                                                                     g_alpha, g_depth, g_normal, T_final, n_contrib,
+                                                                     eg, pgrad, stats, tile_order, inst_used);
   });
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
@@ -1044,6 +1051,7 @@ cudaError_t launch_raster_bwd_stp(bool euclid, bool extra, unsigned grid, cudaSt
                                                                        stats, tile_order));
   return cudaGetLastError();
 }
+#undef QGS_RASTER_DISPATCH_S
 #undef QGS_RASTER_DISPATCH
 
 }  // namespace qgs

@@ -275,6 +275,7 @@ qgs_status serve_create(qgs_server** out, int32_t device, int64_t hbm_budget_byt
         return st;
       }
       if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess) return QGS_ECUDA;
+      qgs_set_pair_counters(sl.ctx, 0);  // serving reads no per-pair counters
     }
   }
   qgs_server* raw = s.release();

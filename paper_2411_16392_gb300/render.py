@@ -165,6 +165,10 @@ class Rasterizer:
                                          C.c_void_p(_stream_ptr(self.device))), self._ctx)
         return grads
 
+    def set_pair_counters(self, enable: bool):
+        """Collect the per-pair counters of stats() (default) or skip them (faster)."""
+        L.check(self.lib.qgs_set_pair_counters(self._ctx, 1 if enable else 0), self._ctx)
+
     def set_tile_mask_capacity(self, words: int):
         """Words of the tile-mask store the emission replays (0: the emission tests every
         tile again). Results never depend on it."""

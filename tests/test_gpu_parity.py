@@ -130,6 +130,32 @@ def test_tile_mask_store_does_not_change_results(dev, order):
         _ras(dev).set_tile_mask_capacity(-1)
 
 
+def test_pair_counters_switch(dev):
+    """Without the per-pair counters the compositing kernels give bit-identical images and
+    gradients; the counters then read -1 and come back when re-enabled."""
+    sc, cam = scene_small(3, 1500)
+    ds = _ds(sc, dev)
+    g = _to_dev(_grad_images(cam.H, cam.W, 5), dev)
+    res = []
+    for on in (True, False):
+        ras = _ras(dev)
+        ras.set_pair_counters(on)
+        out = _np(ras.forward(ds, cam))
+        gr = {k: v.cpu().numpy() for k, v in ras.backward(ds, cam, g).items()}
+        st = ras.stats()
+        res.append((out, gr, st))
+        if not on:
+            assert st["pair_evals"] == -1 and st["bwd_pairs"] == -1
+            ras.set_pair_counters(True)
+            ras.forward(ds, cam)
+            assert ras.stats()["pair_evals"] == res[0][2]["pair_evals"]
+    assert res[0][2]["pair_evals"] > 0
+    for k in res[0][0]:
+        assert np.array_equal(res[0][0][k], res[1][0][k]), k
+    for k in res[0][1]:   # equal up to the order of the floating-point atomic accumulation
+        assert np.abs(res[0][1][k] - res[1][1][k]).max() <= 1e-5 * max(np.abs(res[0][1][k]).max(), 1e-30), k
+
+
 def test_small_scene_backward(dev):
     sc, cam = scene_small(0, 1000)
     ref0 = O.render(sc, cam)
