@@ -164,17 +164,21 @@ __global__ void k_gather_state(int64_t V, const uint32_t* __restrict__ sidx, con
 
 // Tile instances of the depth-ordered visible primitives, packed as (tile << rb) | r with
 // r the depth rank (rb bits); K = uint32_t when tile and rank bits fit in 32, else
-// uint64_t with rb = 32. One warp writes 32 consecutive primitives' tiles (coalesced).
+// uint64_t with rb = 32. One warp writes kEmitPerWarp consecutive primitives' tiles
+// (coalesced); few primitives per warp keep enough warps in flight, as the visible
+// primitives are a small fraction of a large scene.
+constexpr int kEmitPerWarp = 8;
 template <typename K>
 __global__ void k_emit_packed(int64_t V, const uint32_t* __restrict__ sidx, const uint32_t* __restrict__ cnt_sorted,
                               const short4* __restrict__ rect, const TileSlab* __restrict__ tslab, int W, int H,
                               const uint32_t* __restrict__ offs, int tiles_x, int rb, K* __restrict__ keys,
                               const uint32_t* __restrict__ tbits, const uint32_t* __restrict__ tbits_off) {
   const int lane = threadIdx.x & 31;
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t r0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kEmitPerWarp;
+  const int64_t r = r0 + lane;
   uint32_t c = 0, off = 0, pid = 0, wo = kNoTileBits;
   int rxy = 0, rzw = 0;
-  if (r < V) {  // each lane fetches its primitive's entries up front (independent loads)
+  if (lane < kEmitPerWarp && r < V) {  // lane k fetches primitive k's entries up front
     c = cnt_sorted[r];
     off = offs[r];
     pid = sidx[r];
@@ -183,10 +187,10 @@ __global__ void k_emit_packed(int64_t V, const uint32_t* __restrict__ sidx, cons
     rzw = (int)(((uint32_t)(uint16_t)rc.w << 16) | (uint16_t)rc.z);
     if (tbits) wo = tbits_off[pid];
   }
-  for (int k = 0; k < 32; ++k) {
+  for (int k = 0; k < kEmitPerWarp; ++k) {
     const uint32_t cc = __shfl_sync(0xffffffffu, c, k);
     if (!cc) continue;
-    const uint32_t rr = (uint32_t)(r - lane + k);
+    const uint32_t rr = (uint32_t)(r0 + k);
     const uint32_t oo = __shfl_sync(0xffffffffu, off, k);
     const uint32_t pp = __shfl_sync(0xffffffffu, pid, k);
     const uint32_t wk = __shfl_sync(0xffffffffu, wo, k);
@@ -198,6 +202,8 @@ __global__ void k_emit_packed(int64_t V, const uint32_t* __restrict__ sidx, cons
     }, nullptr, wk != kNoTileBits ? tbits + wk : nullptr);
   }
 }
+
+unsigned emit_blocks(int64_t V) { return (unsigned)((V + 8 * kEmitPerWarp - 1) / (8 * kEmitPerWarp)); }
 
 // [start, end) of every tile's run in keys sorted by tile = key >> shift.
 template <typename K>
@@ -537,7 +543,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
     ++launch_counter();
     QGS_CU(cudaGetLastError(), "k_preprocess");
     // keep the rectangle's tiles that meet the parallelogram and the conic; totals and visibility
-    k_count_tiles<<<nblk(N), 256, 0, st>>>(N, ctx->tslab.p, cam->W, cam->H, ctx->count.p, ctx->rect.p,
+    k_count_tiles<<<(unsigned)((N + kCountBlock - 1) / kCountBlock), kCountBlock, 0, st>>>(N, ctx->tslab.p, cam->W, cam->H, ctx->count.p, ctx->rect.p,
                                            ctx->zkey.p, sm == 0 ? ctx->vpos.p : nullptr, ctx->dcount.p,
                                            tb_on ? ctx->tbits.p : nullptr, ctx->tbits_off.p, cap_words);
     ++launch_counter();
@@ -604,7 +610,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
       if (ctx->packed32) {
         uint32_t* k0 = reinterpret_cast<uint32_t*>(ctx->inst.p);
         uint32_t* k1 = reinterpret_cast<uint32_t*>(ctx->inst2.p);
-        k_emit_packed<uint32_t><<<nblk(V), 256, 0, st>>>(V, sidx, ctx->cnt_sorted.p, ctx->rect.p, ctx->tslab.p,
+        k_emit_packed<uint32_t><<<emit_blocks(V), 256, 0, st>>>(V, sidx, ctx->cnt_sorted.p, ctx->rect.p, ctx->tslab.p,
                                                          cam->W, cam->H, ctx->offs.p, cp.tiles_x, rb, k0,
                                                          tb_on ? ctx->tbits.p : nullptr, ctx->tbits_off.p);
         ++launch_counter();
@@ -614,7 +620,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
         QGS_CU(e, "tile sort");
         sorted = f2 ? (const void*)k1 : (const void*)k0;
       } else {
-        k_emit_packed<uint64_t><<<nblk(V), 256, 0, st>>>(V, sidx, ctx->cnt_sorted.p, ctx->rect.p, ctx->tslab.p,
+        k_emit_packed<uint64_t><<<emit_blocks(V), 256, 0, st>>>(V, sidx, ctx->cnt_sorted.p, ctx->rect.p, ctx->tslab.p,
                                                          cam->W, cam->H, ctx->offs.p, cp.tiles_x, 32, ctx->inst.p,
                                                          tb_on ? ctx->tbits.p : nullptr, ctx->tbits_off.p);
         ++launch_counter();

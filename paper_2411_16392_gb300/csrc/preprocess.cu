@@ -242,9 +242,8 @@ __device__ __forceinline__ uint32_t preprocess_one(int64_t i, const SceneView& s
                                                    short4* __restrict__ rect, uint32_t idx_base = 0,
                                                    TileSlab* __restrict__ tslab = nullptr);
 
-// Camera-space centre of primitive i (bit-exact: correctly rounded, fixed order).
-__device__ __forceinline__ void centre_cam(int64_t i, const SceneView& sc, const CamParams& cp, float muc[3]) {
-  const float mx = sc.mean[3 * i], my = sc.mean[3 * i + 1], mz = sc.mean[3 * i + 2];
+// Camera-space centre of a primitive (bit-exact: correctly rounded, fixed order).
+__device__ __forceinline__ void centre_cam(float mx, float my, float mz, const CamParams& cp, float muc[3]) {
 #pragma unroll
   for (int r = 0; r < 3; ++r)
     muc[r] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(cp.Rc[3 * r], mx), __fmul_rn(cp.Rc[3 * r + 1], my)),
@@ -286,13 +285,27 @@ __device__ __forceinline__ void preprocess_block(int64_t n, const SceneView& sc,
   __syncthreads();
   const int64_t first = (int64_t)blockIdx.x * (kPreChunks * 256);
   const int lane = threadIdx.x & 31;
+  // every chunk's centre and scales in flight at once, then the tests
+  float cm[kPreChunks][3];
+  float2 cs[kPreChunks];
+#pragma unroll
+  for (int c = 0; c < kPreChunks; ++c) {
+    const int64_t i = first + c * 256 + threadIdx.x;
+    if (i < n) {
+      cm[c][0] = __ldg(sc.mean + 3 * i);
+      cm[c][1] = __ldg(sc.mean + 3 * i + 1);
+      cm[c][2] = __ldg(sc.mean + 3 * i + 2);
+      cs[c] = __ldg(reinterpret_cast<const float2*>(sc.scale) + i);
+    }
+  }
+#pragma unroll
   for (int c = 0; c < kPreChunks; ++c) {
     const int64_t i = first + c * 256 + threadIdx.x;
     bool keep = false;
     if (i < n) {
       float muc[3];
-      centre_cam(i, sc, cp, muc);
-      keep = may_survive(muc, reinterpret_cast<const float2*>(sc.scale)[i], cp);
+      centre_cam(cm[c][0], cm[c][1], cm[c][2], cp, muc);
+      keep = may_survive(muc, cs[c], cp);
       if (!keep) {
         if (idx) idx[i] = idx_base + (uint32_t)i;
         count[i] = 0u;
@@ -381,7 +394,7 @@ __device__ __forceinline__ uint32_t preprocess_one(int64_t i, const SceneView& s
 
   // --- bit-exact part: centre depth, box, tile rectangle -------------------------
   float muc[3];
-  centre_cam(i, sc, cp, muc);
+  centre_cam(mx, my, mz, cp, muc);
   if (!may_survive(muc, s, cp)) {
     count[i] = 0u;
     zkey[i] = 0xFFFFFFFFu;
@@ -751,7 +764,7 @@ __global__ void __launch_bounds__(256) k_emit_hit(int64_t n, SceneView sc, CamPa
   }
 }
 
-__global__ void __launch_bounds__(256) k_count_tiles(int64_t n, const TileSlab* __restrict__ tslab, int W, int H,
+__global__ void __launch_bounds__(kCountBlock) k_count_tiles(int64_t n, const TileSlab* __restrict__ tslab, int W, int H,
                                                      uint32_t* __restrict__ count, short4* __restrict__ rect,
                                                      uint32_t* __restrict__ zkey, uint32_t* __restrict__ vflag,
                                                      uint32_t* __restrict__ counters, uint32_t* __restrict__ tbits,
@@ -785,7 +798,7 @@ __global__ void __launch_bounds__(256) k_count_tiles(int64_t n, const TileSlab* 
   }
   // the warp's rectangles and screen bounds, loaded up front (independent loads) and
   // handed out per primitive from registers and shared memory
-  __shared__ TileSlab sts[256];
+  __shared__ TileSlab sts[kCountBlock];
   short4 rc0 = make_short4(0, 0, 0, 0);
   if (c0) {
     rc0 = rect[i];

@@ -179,6 +179,9 @@ __device__ __forceinline__ uint32_t warp_tiles(short4 r, const TileSlab* t, int 
 // to counters[0], counters[1]. With tbits: each primitive's pass masks (one word per 32
 // rectangle tiles) go to tbits + tbits_off[i], words taken from counters[2] (the total
 // requested, even beyond cap_words); a primitive that does not fit gets kNoTileBits.
+// Launched with kCountBlock threads per CTA (small CTAs: the warps' work varies widely and
+// a CTA's slot is held until its slowest warp ends).
+constexpr int kCountBlock = 64;
 __global__ void k_count_tiles(int64_t n, const TileSlab* tslab, int W, int H, uint32_t* count, short4* rect,
                               uint32_t* zkey, uint32_t* vflag, uint32_t* counters, uint32_t* tbits,
                               uint32_t* tbits_off, uint32_t cap_words);

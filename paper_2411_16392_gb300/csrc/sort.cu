@@ -1,13 +1,17 @@
 // Device-wide exclusive scan and stable LSD radix sort (hand-written, no library).
 //
+// Scan: 4096 values per CTA, 16 per thread in registers (vector loads); a reduce pass
+// writes the chunk sums, and the scan pass adds to each chunk the sum of the chunk sums
+// before it (summed by the CTA itself while there are at most 2048 chunks).
+//
 // Radix sort: per pass of at most 8 bits,
 //   1. upsweep  - each CTA histograms the digits of its 2048-key chunk into a
 //                 digit-major count matrix hist[d * nblocks + b];
 //   2. scan     - one exclusive scan of that matrix gives, for every (digit, chunk), the
 //                 global position of the chunk's first key with that digit;
-//   3. downsweep - each warp ranks its 256 keys in order with __match_any_sync
-//                 (peers with the same digit), warp-level digit counters are scanned
-//                 across the CTA's warps, and every key is written to
+//   3. downsweep - each warp ranks its 256 keys in order (the lanes holding the same
+//                 digit found with one ballot per digit bit), warp-level digit counters
+//                 are scanned across the CTA's warps, and every key is written to
 //                 base(d, chunk) + (keys with digit d in earlier warps) + rank in warp.
 // Keys keep their relative order within a digit (stable), so successive passes from
 // the least significant digit up sort by the whole bit range.
@@ -19,56 +23,71 @@ namespace {
 
 constexpr int SCAN_ITEMS = 16;
 constexpr int SCAN_CHUNK = BLOCK * SCAN_ITEMS;  // 4096 values per CTA
+constexpr int kScanDirectPrefix = 2048;          // chunks up to which each CTA sums its own prefix
 constexpr int RS_WARPS = 8;
 constexpr int RS_ITEMS = 8;                     // keys per lane
 constexpr int RS_CHUNK = RS_WARPS * 32 * RS_ITEMS;  // 2048 keys per CTA
 static_assert(RS_CHUNK == kRadixChunk, "histogram sizing assumes kRadixChunk keys per CTA");
 constexpr unsigned FULL = 0xffffffffu;
 
-// Exclusive scan of the CTA's values in shared memory (SCAN_CHUNK of them); returns the
-// CTA total. Thread t scans items [t*16, t*16+16) sequentially, then the thread totals
-// are scanned with warp shuffles and one pass over the warp totals.
-__device__ uint32_t block_exclusive_scan(uint32_t* s) {
+// Load / store 16 consecutive u32 of a chunk (vectorised when the addresses allow it).
+__device__ __forceinline__ void load16(const uint32_t* in, int64_t i0, int64_t n, bool vec,
+                                       uint32_t v[SCAN_ITEMS]) {
+  if (vec && i0 + SCAN_ITEMS <= n) {
+    const uint4* p = reinterpret_cast<const uint4*>(in + i0);
+#pragma unroll
+    for (int q = 0; q < SCAN_ITEMS / 4; ++q) {
+      const uint4 w = p[q];
+      v[4 * q] = w.x; v[4 * q + 1] = w.y; v[4 * q + 2] = w.z; v[4 * q + 3] = w.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) v[k] = i0 + k < n ? in[i0 + k] : 0u;
+  }
+}
+
+// Exclusive scan of the CTA's SCAN_CHUNK values held 16 per thread in registers (thread t
+// holds items [16 t, 16 t + 16)): in-thread scan, warp shuffles over the thread totals,
+// one pass over the warp totals. Returns the CTA total.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v[SCAN_ITEMS]) {
   __shared__ uint32_t warp_tot[BLOCK / 32];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   uint32_t run = 0;
 #pragma unroll
   for (int k = 0; k < SCAN_ITEMS; ++k) {
-    const uint32_t v = s[t * SCAN_ITEMS + k];
-    s[t * SCAN_ITEMS + k] = run;
-    run += v;
+    const uint32_t x = v[k];
+    v[k] = run;
+    run += x;
   }
   uint32_t inc = run;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t n = __shfl_up_sync(FULL, inc, o);
-    if (lane >= o) inc += n;
+    const uint32_t y = __shfl_up_sync(FULL, inc, o);
+    if (lane >= o) inc += y;
   }
   if (lane == 31) warp_tot[warp] = inc;
   __syncthreads();
   uint32_t wbase = 0, total = 0;
 #pragma unroll
   for (int w = 0; w < BLOCK / 32; ++w) {
-    const uint32_t v = warp_tot[w];
-    if (w < warp) wbase += v;
-    total += v;
+    const uint32_t x = warp_tot[w];
+    if (w < warp) wbase += x;
+    total += x;
   }
   const uint32_t base = wbase + inc - run;
 #pragma unroll
-  for (int k = 0; k < SCAN_ITEMS; ++k) s[t * SCAN_ITEMS + k] += base;
-  __syncthreads();
+  for (int k = 0; k < SCAN_ITEMS; ++k) v[k] += base;
   return total;
 }
 
 __global__ void __launch_bounds__(BLOCK) k_scan_reduce(const uint32_t* __restrict__ in, int64_t n,
-                                                       uint32_t* __restrict__ sums) {
+                                                       uint32_t* __restrict__ sums, bool vec) {
   __shared__ uint32_t red[BLOCK / 32];
-  const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK;
+  uint32_t v[SCAN_ITEMS];
+  load16(in, (int64_t)blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_ITEMS, n, vec, v);
   uint32_t acc = 0;
-  for (int k = threadIdx.x; k < SCAN_CHUNK; k += BLOCK) {
-    const int64_t i = base + k;
-    if (i < n) acc += in[i];
-  }
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) acc += v[k];
   acc = __reduce_add_sync(FULL, acc);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
@@ -79,21 +98,58 @@ __global__ void __launch_bounds__(BLOCK) k_scan_reduce(const uint32_t* __restric
   }
 }
 
-// Scan of each chunk plus its chunk offset; the last CTA also writes the total to out[n].
-__global__ void __launch_bounds__(BLOCK) k_scan_down(const uint32_t* __restrict__ in, int64_t n,
-                                                     const uint32_t* __restrict__ offs, uint32_t* __restrict__ out) {
-  __shared__ uint32_t s[SCAN_CHUNK];
-  const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK;
-  for (int k = threadIdx.x; k < SCAN_CHUNK; k += BLOCK) {
-    const int64_t i = base + k;
-    s[k] = i < n ? in[i] : 0u;
+// Scan of each chunk plus the sum of the chunk sums before it (each CTA adds up its own
+// prefix from `sums`); the last CTA also writes the total to out[n]. in and out may be
+// the same array (each thread reads its items before the CTA barrier, writes after).
+__global__ void __launch_bounds__(BLOCK) k_scan_down(const uint32_t* in, int64_t n,
+                                                     const uint32_t* __restrict__ sums, uint32_t* out,
+                                                     bool vec) {
+  __shared__ uint32_t red[BLOCK / 32];
+  uint32_t off = 0;
+  if (sums) {  // prefix of this chunk: sum of the earlier chunk sums
+    uint32_t acc = 0;
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += BLOCK) acc += sums[b];
+    acc = __reduce_add_sync(FULL, acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+#pragma unroll
+    for (int w = 0; w < BLOCK / 32; ++w) off += red[w];
   }
-  __syncthreads();
-  const uint32_t total = block_exclusive_scan(s);
-  const uint32_t off = offs ? offs[blockIdx.x] : 0u;
-  for (int k = threadIdx.x; k < SCAN_CHUNK; k += BLOCK) {
-    const int64_t i = base + k;
-    if (i < n) out[i] = s[k] + off;
+  const int64_t i0 = (int64_t)blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_ITEMS;
+  uint32_t v[SCAN_ITEMS];
+  load16(in, i0, n, vec, v);
+  const uint32_t total = block_exclusive_scan(v);
+  if (vec && i0 + SCAN_ITEMS <= n) {
+    uint4* p = reinterpret_cast<uint4*>(out + i0);
+#pragma unroll
+    for (int q = 0; q < SCAN_ITEMS / 4; ++q)
+      p[q] = make_uint4(v[4 * q] + off, v[4 * q + 1] + off, v[4 * q + 2] + off, v[4 * q + 3] + off);
+  } else {
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k)
+      if (i0 + k < n) out[i0 + k] = v[k] + off;
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = off + total;
+}
+
+// Scan of each chunk plus its precomputed offset offs[blockIdx.x] (many chunks).
+__global__ void __launch_bounds__(BLOCK) k_scan_down_off(const uint32_t* in, int64_t n,
+                                                         const uint32_t* __restrict__ offs, uint32_t* out,
+                                                         bool vec) {
+  const uint32_t off = offs[blockIdx.x];
+  const int64_t i0 = (int64_t)blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_ITEMS;
+  uint32_t v[SCAN_ITEMS];
+  load16(in, i0, n, vec, v);
+  const uint32_t total = block_exclusive_scan(v);
+  if (vec && i0 + SCAN_ITEMS <= n) {
+    uint4* p = reinterpret_cast<uint4*>(out + i0);
+#pragma unroll
+    for (int q = 0; q < SCAN_ITEMS / 4; ++q)
+      p[q] = make_uint4(v[4 * q] + off, v[4 * q + 1] + off, v[4 * q + 2] + off, v[4 * q + 3] + off);
+  } else {
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k)
+      if (i0 + k < n) out[i0 + k] = v[k] + off;
   }
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = off + total;
 }
@@ -310,20 +366,27 @@ cudaError_t scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, uin
   if (n <= 0) {
     return cudaMemsetAsync(out, 0, sizeof(uint32_t), st);
   }
+  const bool vec = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
   const int nb = scan_blocks(n);
   if (nb == 1) {
-    k_scan_down<<<1, BLOCK, 0, st>>>(in, n, nullptr, out);
+    k_scan_down<<<1, BLOCK, 0, st>>>(in, n, nullptr, out, vec);
     ++launch_counter();
     return cudaGetLastError();
   }
   if ((size_t)(2 * nb + 2) > tmp_cap) return cudaErrorInvalidValue;
   uint32_t* sums = tmp;
-  uint32_t* sums_scan = tmp + nb;  // nb + 1 slots
-  k_scan_reduce<<<nb, BLOCK, 0, st>>>(in, n, sums);
+  k_scan_reduce<<<nb, BLOCK, 0, st>>>(in, n, sums, vec);
   ++launch_counter();
+  if (nb <= kScanDirectPrefix) {
+    // few chunks: each CTA of the second pass adds up its own prefix of the chunk sums
+    k_scan_down<<<nb, BLOCK, 0, st>>>(in, n, sums, out, vec);
+    ++launch_counter();
+    return cudaGetLastError();
+  }
+  uint32_t* sums_scan = tmp + nb;  // nb + 1 slots
   cudaError_t e = scan_exclusive_u32(sums, sums_scan, nb, tmp + 2 * nb + 2, tmp_cap - (2 * nb + 2), st);
   if (e != cudaSuccess) return e;
-  k_scan_down<<<nb, BLOCK, 0, st>>>(in, n, sums_scan, out);
+  k_scan_down_off<<<nb, BLOCK, 0, st>>>(in, n, sums_scan, out, vec);
   ++launch_counter();
   return cudaGetLastError();
 }
