@@ -226,6 +226,28 @@ def ellipsoid_conic(muc, Wm, su, sv, m, fx, fy):
     return out
 
 
+def conic_box(cn, uc, vc):
+    """Tile range (floor(x / 16) bounds, as float32) of the bounding box of the conic
+    F(p) <= 1, i.e. of the ellipse (p - p0)^T q (p - p0) <= R with p0 = q^-1 l and
+    R = 1 + l.p0, whose half-extents are sqrt(R (q^-1)_00) and sqrt(R (q^-1)_11), placed at
+    the projected centre (uc, vc). FP32, correctly rounded, in the order written; entries
+    of disabled conics are not used."""
+    f = np.float32
+    one, sixteenth = f(1.0), f(1.0 / 16.0)
+    qa, qb, qc, la, lb = (cn[k] for k in ("qa", "qb", "qc", "la", "lb"))
+    with np.errstate(all="ignore"):
+        dn = qa * qc - qb * qb
+        p0x = (qc * la - qb * lb) / dn
+        p0y = (qa * lb - qb * la) / dn
+        R = (one + la * p0x) + lb * p0y
+        ex = np.sqrt((R * qc) / dn)
+        ey = np.sqrt((R * qa) / dn)
+        cx = uc + p0x
+        cy = vc + p0y
+        return (np.floor((cx - ex) * sixteenth), np.floor((cx + ex) * sixteenth),
+                np.floor((cy - ey) * sixteenth), np.floor((cy + ey) * sixteenth))
+
+
 def conic_value(sl, p, u, v):
     """F(u, v) = u (qa u + 2 qb v - 2 la) + v (qc v - 2 lb) in the recipe's FP32 order."""
     two = np.float32(2.0)
@@ -462,6 +484,14 @@ def bin_fp32(scene, cam, emit: bool = True, order: str = "centre") -> Binning:
         tx1 = np.minimum(np.floor(xmax * sixteenth), f(TX - 1))
         ty0 = np.maximum(np.floor(ymin * sixteenth), zero)
         ty1 = np.minimum(np.floor(ymax * sixteenth), f(TY - 1))
+        # the rectangle shrunk to the tiles of the conic's bounding box (see conic_box)
+        cb = conic_box(slabs_conic := ellipsoid_conic(muc, Wm, su, sv, m, fx, fy), uc, vc)
+        con = slabs_conic["conic_on"]
+        tx0 = np.where(con, np.maximum(tx0, cb[0]), tx0)
+        tx1 = np.where(con, np.minimum(tx1, cb[1]), tx1)
+        ty0 = np.where(con, np.maximum(ty0, cb[2]), ty0)
+        ty1 = np.where(con, np.minimum(ty1, cb[3]), ty1)
+        vis &= ~(tx0 > tx1) & ~(ty0 > ty1)
         rect = np.zeros((N, 4), np.int32)
         rect[vis, 0] = tx0[vis].astype(np.int32)
         rect[vis, 1] = tx1[vis].astype(np.int32)
@@ -469,7 +499,7 @@ def bin_fp32(scene, cam, emit: bool = True, order: str = "centre") -> Binning:
         rect[vis, 3] = ty1[vis].astype(np.int32)
         slabs = dict(n1x=n1x, n1y=n1y, s1min=s1min, s1max=s1max, n2x=n2x, n2y=n2y, s2min=s2min, s2max=s2max,
                      uc=uc, vc=vc, img_w=cam.W, img_h=cam.H)
-        slabs.update(ellipsoid_conic(muc, Wm, su, sv, m, fx, fy))
+        slabs.update(slabs_conic)
         # tiles of the rectangle that meet the parallelogram (row-major), counted in chunks
         count = np.zeros(N, np.int64)
         vidx = np.nonzero(vis)[0]

@@ -738,9 +738,9 @@ def test_conic_tile_test_against_the_rectangle():
     f = np.float32
     checked = rejected = 0
     for i in np.nonzero(b.visible & sl["conic_on"])[0][:60]:
-        x0r, x1r, y0r, y1r = b.rect[i]
-        for ty in range(y0r, y1r + 1):
-            for tx in range(x0r, x1r + 1):
+        x0r, x1r, y0r, y1r = b.rect[i]   # the rectangle and one ring of tiles around it
+        for ty in range(max(y0r - 1, 0), min(y1r + 1, b.tiles_y - 1) + 1):
+            for tx in range(max(x0r - 1, 0), min(x1r + 1, b.tiles_x - 1) + 1):
                 x0 = f(16 * tx) + f(0.5) - sl["uc"][i]
                 x1 = f(min(16 * tx + 15, cam.W - 1)) + f(0.5) - sl["uc"][i]
                 y0 = f(16 * ty) + f(0.5) - sl["vc"][i]
