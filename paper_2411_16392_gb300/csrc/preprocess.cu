@@ -217,6 +217,22 @@ __device__ __forceinline__ Conic ellipsoid_conic(const float* muc, const float* 
   return o;
 }
 
+// Tile range (floor(x / 16) bounds) of the bounding box of the conic F(p) <= 1, i.e. of
+// the ellipse (p - p0)^T q (p - p0) <= R with p0 = q^-1 l, R = 1 + l.p0 and half-extents
+// sqrt(R (q^-1)_00), sqrt(R (q^-1)_11), around the projected centre (uc, vc). Correctly
+// rounded FP32 in a fixed order (bit-exact with the oracle's recipe).
+__device__ __forceinline__ float4 conic_box(const Conic& c, float uc, float vc) {
+  const float dn = __fsub_rn(__fmul_rn(c.qa, c.qc), __fmul_rn(c.qb, c.qb));
+  const float p0x = __fdiv_rn(__fsub_rn(__fmul_rn(c.qc, c.la), __fmul_rn(c.qb, c.lb)), dn);
+  const float p0y = __fdiv_rn(__fsub_rn(__fmul_rn(c.qa, c.lb), __fmul_rn(c.qb, c.la)), dn);
+  const float R = __fadd_rn(__fadd_rn(1.f, __fmul_rn(c.la, p0x)), __fmul_rn(c.lb, p0y));
+  const float ex = __fsqrt_rn(__fdiv_rn(__fmul_rn(R, c.qc), dn));
+  const float ey = __fsqrt_rn(__fdiv_rn(__fmul_rn(R, c.qa), dn));
+  const float cx = __fadd_rn(uc, p0x), cy = __fadd_rn(vc, p0y);
+  return make_float4(floorf(__fmul_rn(__fsub_rn(cx, ex), 0.0625f)), floorf(__fmul_rn(__fadd_rn(cx, ex), 0.0625f)),
+                     floorf(__fmul_rn(__fsub_rn(cy, ey), 0.0625f)), floorf(__fmul_rn(__fadd_rn(cy, ey), 0.0625f)));
+}
+
 // Projected centre f (x / z) + c as an unevaluated sum hi + lo of floats (about 44
 // significant bits), from error-free transformations: the division's remainder by fma,
 // the product's rounding error by fma, and a two-sum with the principal point.
@@ -475,13 +491,20 @@ __device__ __forceinline__ uint32_t preprocess_one(int64_t i, const SceneView& s
     ok = bx.any && isfinite(bx.xmin) && isfinite(bx.xmax) && isfinite(bx.ymin) && isfinite(bx.ymax) &&
          !(bx.xmax < 0.f || bx.ymax < 0.f || bx.xmin >= (float)cp.W || bx.ymin >= (float)cp.H);
     if (ok) {
-      const float tx0 = fmaxf(floorf(__fmul_rn(bx.xmin, 0.0625f)), 0.f);
-      const float tx1 = fminf(floorf(__fmul_rn(bx.xmax, 0.0625f)), (float)(cp.tiles_x - 1));
-      const float ty0 = fmaxf(floorf(__fmul_rn(bx.ymin, 0.0625f)), 0.f);
-      const float ty1 = fminf(floorf(__fmul_rn(bx.ymax, 0.0625f)), (float)(cp.tiles_y - 1));
-      rc = make_short4((short)tx0, (short)tx1, (short)ty0, (short)ty1);
-      cnt = (uint32_t)((rc.y - rc.x + 1) * (rc.w - rc.z + 1));
-      key = __float_as_uint(muc[2]);
+      float tx0 = fmaxf(floorf(__fmul_rn(bx.xmin, 0.0625f)), 0.f);
+      float tx1 = fminf(floorf(__fmul_rn(bx.xmax, 0.0625f)), (float)(cp.tiles_x - 1));
+      float ty0 = fmaxf(floorf(__fmul_rn(bx.ymin, 0.0625f)), 0.f);
+      float ty1 = fminf(floorf(__fmul_rn(bx.ymax, 0.0625f)), (float)(cp.tiles_y - 1));
+      if (con.on) {  // only the tiles of the conic's bounding box can pass the conic test
+        float4 cb = conic_box(con, bx.pcx, bx.pcy);
+        tx0 = fmaxf(tx0, cb.x); tx1 = fminf(tx1, cb.y);
+        ty0 = fmaxf(ty0, cb.z); ty1 = fminf(ty1, cb.w);
+      }
+      if (!(tx0 > tx1) && !(ty0 > ty1)) {
+        rc = make_short4((short)tx0, (short)tx1, (short)ty0, (short)ty1);
+        cnt = (uint32_t)((rc.y - rc.x + 1) * (rc.w - rc.z + 1));
+        key = __float_as_uint(muc[2]);
+      }
     }
   }
   count[i] = cnt;
