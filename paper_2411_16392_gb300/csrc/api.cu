@@ -203,6 +203,31 @@ __global__ void k_emit_packed(int64_t V, const uint32_t* __restrict__ sidx, cons
   }
 }
 
+// The same for u32 keys, four per thread (one vector load; the neighbours of the four
+// are the thread's own keys except at its ends).
+__global__ void k_tile_ranges_x4(int64_t n, const uint32_t* __restrict__ keys, int shift, uint2* __restrict__ ranges) {
+  const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (i0 >= n) return;
+  uint32_t k[6];  // k[0] = keys[i0 - 1], k[1..4] = keys[i0 .. i0 + 3], k[5] = keys[i0 + 4]
+  if (i0 + 4 <= n) {
+    const uint4 v = *reinterpret_cast<const uint4*>(keys + i0);
+    k[1] = v.x; k[2] = v.y; k[3] = v.z; k[4] = v.w;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) k[1 + q] = i0 + q < n ? keys[i0 + q] : 0u;
+  }
+  k[0] = i0 > 0 ? keys[i0 - 1] : 0u;
+  k[5] = i0 + 4 < n ? keys[i0 + 4] : 0u;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t i = i0 + q;
+    if (i >= n) break;
+    const uint32_t t = k[1 + q] >> shift;
+    if (i == 0 || (k[q] >> shift) != t) ranges[t].x = (uint32_t)i;
+    if (i == n - 1 || (k[2 + q] >> shift) != t) ranges[t].y = (uint32_t)(i + 1);
+  }
+}
+
 unsigned emit_blocks(int64_t V) { return (unsigned)((V + 8 * kEmitPerWarp - 1) / (8 * kEmitPerWarp)); }
 
 // [start, end) of every tile's run in keys sorted by tile = key >> shift.
@@ -237,15 +262,61 @@ __global__ void k_tile_ranges(int64_t n, const uint64_t* __restrict__ keys, uint
   if (i == n - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[t].y = (uint32_t)(i + 1);
 }
 
-// Tile schedule key: heaviest tiles (most listed instances) first, bucketed by
-// floor(log2(count + 1)) so that one 5-bit radix pass orders them.
-__global__ void k_tile_sched_keys(int64_t ntiles, const uint2* __restrict__ ranges, uint32_t* __restrict__ key,
-                                  uint32_t* __restrict__ val) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ntiles) return;
-  const uint32_t c = ranges[t].y - ranges[t].x;
-  key[t] = 31u - (31u - (uint32_t)__clz(c + 1u));  // 31 - floor(log2(c + 1)), in [0, 31]
-  val[t] = (uint32_t)t;
+// Tile schedule: heaviest tiles (most listed instances) first, by buckets of
+// floor(log2(count + 1)), ties in tile order. One CTA of 1024 threads: warp w takes a
+// contiguous run of tiles, per-warp bucket counts (lanes of one bucket found with
+// __match_any_sync) are scanned bucket-major, and the same walk writes each tile to its
+// place (stable, so the schedule does not change from run to run).
+__device__ __forceinline__ uint32_t sched_bucket(const uint2* __restrict__ ranges, int t) {
+  const uint2 r = ranges[t];
+  return (uint32_t)__clz(r.y - r.x + 1u);  // 31 - floor(log2(count + 1)): heaviest first
+}
+__global__ void __launch_bounds__(1024) k_tile_schedule(int ntiles, const uint2* __restrict__ ranges,
+                                                        uint32_t* __restrict__ order) {
+  __shared__ uint32_t cnt[32][33];  // [warp][bucket]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  const int per = (ntiles + 31) / 32;
+  const int t0 = warp * per, t1 = min(t0 + per, ntiles);
+  cnt[warp][lane] = 0u;
+  __syncwarp();
+  for (int tb = t0; tb < t1; tb += 32) {
+    const int t = tb + lane;
+    const bool valid = t < t1;
+    const uint32_t b = valid ? sched_bucket(ranges, t) : 32u + (uint32_t)lane;
+    const uint32_t peers = __match_any_sync(0xffffffffu, b);
+    if (valid && (peers & lt) == 0) cnt[warp][b] += (uint32_t)__popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  if (warp == 0) {  // bucket-major exclusive scan: bucket b of warp w starts after all of
+                    // buckets < b and after bucket b of warps < w
+    uint32_t tot = 0;
+    for (int w = 0; w < 32; ++w) tot += cnt[w][lane];
+    uint32_t inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    uint32_t base = inc - tot;
+    for (int w = 0; w < 32; ++w) {
+      const uint32_t c = cnt[w][lane];
+      cnt[w][lane] = base;
+      base += c;
+    }
+  }
+  __syncthreads();
+  for (int tb = t0; tb < t1; tb += 32) {
+    const int t = tb + lane;
+    const bool valid = t < t1;
+    const uint32_t b = valid ? sched_bucket(ranges, t) : 32u + (uint32_t)lane;
+    const uint32_t peers = __match_any_sync(0xffffffffu, b);
+    if (valid) order[cnt[warp][b] + (uint32_t)__popc(peers & lt)] = (uint32_t)t;
+    __syncwarp();
+    if (valid && (peers & lt) == 0) cnt[warp][b] += (uint32_t)__popc(peers);
+    __syncwarp();
+  }
 }
 
 
@@ -266,7 +337,7 @@ struct qgs_ctx {
   DevBuf<uint32_t> vals, vals2;
   // per-tile / per-pixel
   DevBuf<uint2> ranges;
-  DevBuf<uint32_t> tkey, tkey2, torder, torder2;  // heaviest-first tile schedule
+  DevBuf<uint32_t> torder;                        // heaviest-first tile schedule
   const uint32_t* tile_order = nullptr;
   DevBuf<uint8_t> inst_used;                      // per instance: blended by some pixel
   DevBuf<float> T_final;
@@ -451,7 +522,7 @@ void qgs_destroy(qgs_ctx* c) {
   c->idx2.release(); c->cnt_sorted.release(); c->offs.release(); c->rect.release(); c->inst.release();
   c->inst2.release(); c->vals.release(); c->vals2.release(); c->ranges.release(); c->T_final.release();
   c->n_contrib.release(); c->pgrad.release(); c->hist.release(); c->scan_tmp.release(); c->stats.release();
-  c->dcount.release(); c->tkey.release(); c->tkey2.release(); c->torder.release(); c->torder2.release();
+  c->dcount.release(); c->torder.release();
   c->inst_used.release();
   c->vdesc.release();
   c->resid.release();
@@ -513,10 +584,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
       ctx->tbits_want ? (uint32_t)std::min<size_t>(std::min(ctx->tbits.cap, ctx->tbits_want), 0xFFFFFFF0u) : 0u;
   const bool tb_on = N > 0 && cap_words > 0;
   QGS_CU(ctx->ranges.reserve((size_t)ntiles), "alloc ranges");
-  QGS_CU(ctx->tkey.reserve((size_t)ntiles), "alloc tile keys");
-  QGS_CU(ctx->tkey2.reserve((size_t)ntiles), "alloc tile keys");
   QGS_CU(ctx->torder.reserve((size_t)ntiles), "alloc tile order");
-  QGS_CU(ctx->torder2.reserve((size_t)ntiles), "alloc tile order");
   QGS_CU(ctx->T_final.reserve((size_t)P), "alloc T_final");
   QGS_CU(ctx->n_contrib.reserve((size_t)P), "alloc n_contrib");
   const bool extra = out->curvature || out->distortion || out->median_depth;
@@ -676,24 +744,19 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   QGS_CU(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(uint2) * (size_t)ntiles, st), "memset ranges");
   if (I > 0) {
     if (ctx->packed32)
-      k_tile_ranges_t<uint32_t><<<nblk(I), 256, 0, st>>>(I, reinterpret_cast<const uint32_t*>(sorted), shift,
-                                                         ctx->ranges.p);
+      k_tile_ranges_x4<<<nblk((I + 3) / 4), 256, 0, st>>>(I, reinterpret_cast<const uint32_t*>(sorted), shift,
+                                                           ctx->ranges.p);
     else
       k_tile_ranges_t<uint64_t><<<nblk(I), 256, 0, st>>>(I, reinterpret_cast<const uint64_t*>(sorted), shift,
                                                          ctx->ranges.p);
     ++launch_counter();
     QGS_CU(cudaGetLastError(), "ranges");
   }
-  // heaviest-first tile schedule (one 5-bit radix pass over the tiles)
-  k_tile_sched_keys<<<nblk(ntiles), 256, 0, st>>>(ntiles, ctx->ranges.p, ctx->tkey.p, ctx->torder.p);
+  // heaviest-first tile schedule
+  k_tile_schedule<<<1, 1024, 0, st>>>((int)ntiles, ctx->ranges.p, ctx->torder.p);
   ++launch_counter();
   QGS_CU(cudaGetLastError(), "tile schedule");
-  {
-    const bool fl = radix_sort_u32_pairs(ctx->tkey.p, ctx->torder.p, ctx->tkey2.p, ctx->torder2.p, ntiles, 0, 5, tmp,
-                                         st, &e);
-    QGS_CU(e, "tile schedule sort");
-    ctx->tile_order = fl ? ctx->torder2.p : ctx->torder.p;
-  }
+  ctx->tile_order = ctx->torder.p;
   QGS_CU(cudaMemsetAsync(ctx->stats.p, 0, sizeof(RasterStats), st), "memset stats");
   mark(ctx, 5, st);
   const ExtraPlanes ex{out->curvature, out->distortion, out->median_depth, extra ? ctx->resid.p : nullptr};
@@ -827,10 +890,7 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
   QGS_CU(ctx->offs.reserve(n1 + 1), "alloc offs");
   QGS_CU(ctx->rect.reserve(n1), "alloc rect");
   QGS_CU(ctx->ranges.reserve((size_t)T_all), "alloc ranges");
-  QGS_CU(ctx->tkey.reserve((size_t)T_all), "alloc tile keys");
-  QGS_CU(ctx->tkey2.reserve((size_t)T_all), "alloc tile keys");
   QGS_CU(ctx->torder.reserve((size_t)T_all), "alloc tile order");
-  QGS_CU(ctx->torder2.reserve((size_t)T_all), "alloc tile order");
   QGS_CU(ctx->hist.reserve(radix_hist_elems((int64_t)n1)), "alloc hist");
   QGS_CU(ctx->scan_tmp.reserve(scan_tmp_elems((int64_t)radix_hist_elems((int64_t)n1) + (int64_t)n1)), "alloc scan");
   SortTemp tmp;
@@ -894,13 +954,10 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
     ++launch_counter();
     QGS_CU(cudaGetLastError(), "ranges");
   }
-  k_tile_sched_keys<<<nblk(T_all), 256, 0, st>>>(T_all, ctx->ranges.p, ctx->tkey.p, ctx->torder.p);
+  k_tile_schedule<<<1, 1024, 0, st>>>((int)T_all, ctx->ranges.p, ctx->torder.p);
   ++launch_counter();
   QGS_CU(cudaGetLastError(), "tile schedule");
-  const bool flt =
-      radix_sort_u32_pairs(ctx->tkey.p, ctx->torder.p, ctx->tkey2.p, ctx->torder2.p, T_all, 0, 5, tmp, st, &e);
-  QGS_CU(e, "tile schedule sort");
-  const uint32_t* order = flt ? ctx->torder2.p : ctx->torder.p;
+  const uint32_t* order = ctx->torder.p;
   QGS_CU(cudaMemsetAsync(ctx->stats.p, 0, sizeof(RasterStats), st), "memset stats");
   QGS_CU(launch_raster_fwd_views(ctx->cfg.density == 1, extra, (unsigned)T_all, st, ctx->ranges.p, ids, 2,
                                  ctx->state.p, d_vd, V, d_tb, ctx->stats.p, order),
