@@ -29,13 +29,13 @@ WORKLOAD = "unbounded_3m_1297x840"
 
 # FP32 operations (FMA = 2, MUFU = 1) per pair class, counted from the kernel source
 # (raster.cu, eval_pair and the two compositing loops) along the shortest path of each
-# class: every evaluated pair forms its pixel offset and tests the screen parallelogram
-# (FLOP_EVAL); a pair inside it forms the local ray, the quadratic and its first root up
-# to the E <= 9 test (FLOP_ISECT); a hit adds the chord test, F(u), l^2/sigma^2 and G
+# class: every evaluated pair forms its pixel offset and evaluates the screen conic of the
+# chord ellipsoid (FLOP_EVAL); a pair inside it forms the local ray, the quadratic and its
+# first root up to the E <= 9 test (FLOP_ISECT); a hit adds the chord test, F(u), l^2/sigma^2 and G
 # (FLOP_HIT); a blended pair adds alpha, transmittance, colour, depth and the normal
 # (FLOP_BLEND); a pair that produces a gradient in the backward adds the chain rule and
 # its share of the warp reduction (FLOP_GRAD).
-FLOP_EVAL = 12
+FLOP_EVAL = 13
 FLOP_ISECT = 54
 FLOP_HIT = 24
 FLOP_BLEND = 46
@@ -44,17 +44,18 @@ FLOP_GRAD = 200
 # Algorithmic HBM bytes of the memory-bound stages (minimal traffic of what each stage
 # computes): per primitive read 144 B of parameters (mean 12, quaternion 16, scales 8,
 # curvatures 8, opacity 4, bf16 SH 96) and write count, depth key, rectangle and flag
-# (20 B); per visible primitive the 128-byte state record. Binning per visible primitive:
+# (20 B); per visible primitive the 128-byte state record and the 80-byte tile-test bounds,
+# written and read back by the tile-count pass. Binning per visible primitive:
 # a 4-pass (key, index) sort (20 B per pass) and the state gather (256 B); per
 # instance: the 4-byte emitted key, two stable tile passes (12 B each) and the range
 # scan (4 B). Preprocess backward per visible primitive: the 80-byte gradient record,
 # the parameters (144 B) and a read-modify-write of the float32 gradients (240 B x 2).
-B_PRE_PRIM, B_PRE_VIS = 164, 128
+B_PRE_PRIM, B_PRE_VIS = 164, 128 + 2 * 80
 # DRAM bytes (read + write) per launch of the compositing kernels at 3M / 1297x840, from
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, summary under profiles/),
 # valid only while the kernels' sources hash to the recorded value.
 TRAFFIC_SRC = ("paper_2411_16392_gb300/csrc/raster.cu", "paper_2411_16392_gb300/csrc/qgs_common.cuh")
-TRAFFIC = {"hash": "7ebac12d9bebcda8", "k_raster_fwd": 16483584 + 2670848, "k_raster_bwd": 61793280 + 32512}
+TRAFFIC = {"hash": "8150afd27e0d6aff", "k_raster_fwd": 13452800 + 1178624, "k_raster_bwd": 56415232 + 19712}
 B_BIN_VIS, B_BIN_INST = 4 * 20 + 256, 4 + 2 * 12 + 4
 B_PREBWD_VIS = 80 + 144 + 480
 
