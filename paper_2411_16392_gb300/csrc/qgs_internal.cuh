@@ -47,30 +47,51 @@ struct TileSlab {
 
 // Does a tile meet the parallelogram? Range of n . (x - c) over the tile's pixel centres
 // against each span, padded by 2e-3 px + 1e-5 of the span ends (the same FP32
-// specification as the oracle's tile test). The products n_x (x - u_c) depend on the
-// column only and n_y (y - v_c) on the row only, so they are formed once per column / row
-// (the same correctly rounded values a per-tile evaluation gives).
-struct TileRow {  // per row: offsets of its first and last pixel centre, n_y (y - v_c) per slab
-  float y0, y1, b0[2], b1[2];
+// specification as the oracle's tile test: the minimum and maximum over the four corner
+// sums n_x (x - u_c) + n_y (y - v_c), each rounded). Correctly rounded addition is monotone
+// in each operand, so the minimum of the four rounded sums is the rounded sum of the
+// column term's minimum and the row term's minimum (likewise for the maximum): the terms'
+// extremes are formed once per column and per row, and a tile costs one addition per bound.
+struct TileRow {  // per row: offsets of its first and last pixel centre, extremes of n_y (y - v_c)
+  float y0, y1, bmin[2], bmax[2];
 };
-struct TileCol {  // per column: offsets of its first and last pixel centre, n_x (x - u_c) per slab
-  float x0, x1, a0[2], a1[2];
+struct TileCol {  // per column: offsets of its first and last pixel centre, extremes of n_x (x - u_c)
+  float x0, x1, amin[2], amax[2];
 };
 __device__ __forceinline__ TileRow tile_row(const TileSlab& t, int ty, int H) {
   TileRow r;
   r.y0 = __fsub_rn(__fadd_rn((float)(16 * ty), 0.5f), t.c.y);
   r.y1 = __fsub_rn(__fadd_rn((float)min(16 * ty + 15, H - 1), 0.5f), t.c.y);
-  r.b0[0] = __fmul_rn(t.a.y, r.y0); r.b1[0] = __fmul_rn(t.a.y, r.y1);
-  r.b0[1] = __fmul_rn(t.b.y, r.y0); r.b1[1] = __fmul_rn(t.b.y, r.y1);
+  const float p0 = __fmul_rn(t.a.y, r.y0), p1 = __fmul_rn(t.a.y, r.y1);
+  const float q0 = __fmul_rn(t.b.y, r.y0), q1 = __fmul_rn(t.b.y, r.y1);
+  r.bmin[0] = fminf(p0, p1); r.bmax[0] = fmaxf(p0, p1);
+  r.bmin[1] = fminf(q0, q1); r.bmax[1] = fmaxf(q0, q1);
   return r;
 }
 __device__ __forceinline__ TileCol tile_col(const TileSlab& t, int tx, int W) {
   TileCol c;
   c.x0 = __fsub_rn(__fadd_rn((float)(16 * tx), 0.5f), t.c.x);
   c.x1 = __fsub_rn(__fadd_rn((float)min(16 * tx + 15, W - 1), 0.5f), t.c.x);
-  c.a0[0] = __fmul_rn(t.a.x, c.x0); c.a1[0] = __fmul_rn(t.a.x, c.x1);
-  c.a0[1] = __fmul_rn(t.b.x, c.x0); c.a1[1] = __fmul_rn(t.b.x, c.x1);
+  const float p0 = __fmul_rn(t.a.x, c.x0), p1 = __fmul_rn(t.a.x, c.x1);
+  const float q0 = __fmul_rn(t.b.x, c.x0), q1 = __fmul_rn(t.b.x, c.x1);
+  c.amin[0] = fminf(p0, p1); c.amax[0] = fmaxf(p0, p1);
+  c.amin[1] = fminf(q0, q1); c.amax[1] = fmaxf(q0, q1);
   return c;
+}
+// The padded spans of a primitive's two slabs (s_min - pad, s_max + pad), formed once.
+struct TileSpans {
+  float lo[2], hi[2];
+};
+__device__ __forceinline__ TileSpans tile_spans(const TileSlab& t) {
+  TileSpans sp;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float4 s = k == 0 ? t.a : t.b;
+    const float pad = __fadd_rn(2e-3f, __fmul_rn(1e-5f, __fadd_rn(fabsf(s.z), fabsf(s.w))));
+    sp.lo[k] = __fsub_rn(s.z, pad);
+    sp.hi[k] = __fadd_rn(s.w, pad);
+  }
+  return sp;
 }
 
 // F(u, v) = u (qa u + 2 qb v - 2 la) + v (qc v - 2 lb): the conic of the chord ellipsoid at
@@ -100,17 +121,14 @@ __device__ __forceinline__ bool conic_meets(const TileSlab& t, const TileCol& c,
   return false;
 }
 
-__device__ __forceinline__ bool tile_meets(const TileSlab& t, const TileCol& c, const TileRow& r) {
+__device__ __forceinline__ bool tile_meets(const TileSlab& t, const TileSpans& sp, const TileCol& c,
+                                           const TileRow& r) {
   bool ok = true;
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
-    const float4 s = k == 0 ? t.a : t.b;
-    const float e00 = __fadd_rn(c.a0[k], r.b0[k]), e01 = __fadd_rn(c.a0[k], r.b1[k]);
-    const float e10 = __fadd_rn(c.a1[k], r.b0[k]), e11 = __fadd_rn(c.a1[k], r.b1[k]);
-    const float lo = fminf(fminf(e00, e01), fminf(e10, e11));
-    const float hi = fmaxf(fmaxf(e00, e01), fmaxf(e10, e11));
-    const float pad = __fadd_rn(2e-3f, __fmul_rn(1e-5f, __fadd_rn(fabsf(s.z), fabsf(s.w))));
-    ok = ok && !(hi < __fsub_rn(s.z, pad)) && !(lo > __fadd_rn(s.w, pad));
+    const float lo = __fadd_rn(c.amin[k], r.bmin[k]);
+    const float hi = __fadd_rn(c.amax[k], r.bmax[k]);
+    ok = ok && !(hi < sp.lo[k]) && !(lo > sp.hi[k]);
   }
   return ok && conic_meets(t, c, r);
 }
@@ -131,7 +149,11 @@ __device__ __forceinline__ uint32_t warp_tiles(short4 r, const TileSlab* t, int 
   const int w = r.y - r.x + 1;
   const uint32_t total = (uint32_t)w * (uint32_t)(r.w - r.z + 1);
   TileSlab ts;
-  if (t && !bits_in) ts = *t;
+  TileSpans sp{};
+  if (t && !bits_in) {
+    ts = *t;
+    sp = tile_spans(ts);
+  }
   int ty = r.z + lane / w, tx = r.x + lane % w;  // tile e = lane
   const int sy = 32 / w, sx = 32 - sy * w;          // tile e + 32: sy rows and sx columns on
   int row_y = -1;
@@ -156,7 +178,7 @@ __device__ __forceinline__ uint32_t warp_tiles(short4 r, const TileSlab* t, int 
           row = tile_row(ts, ty, H);
           row_y = ty;
         }
-        pass = tile_meets(ts, tile_col(ts, tx, W), row);
+        pass = tile_meets(ts, sp, tile_col(ts, tx, W), row);
       }
       m = __ballot_sync(0xffffffffu, pass);
       if (bits_out && lane == 0) bits_out[e0 >> 5] = m;
