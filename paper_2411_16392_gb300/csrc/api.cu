@@ -97,43 +97,48 @@ __global__ void k_emit(int64_t n, const uint32_t* __restrict__ sidx, const uint3
   }
 }
 
+constexpr int kEmitPerWarp = 8;  // primitives per warp in the emission kernels
+
 // Several views of one scene (render_forward_batch): entry pid = v * n_per_view + i, its
-// tiles numbered from the view's base (vt[v] = (tiles_x, tile base)); depth order only.
+// tiles numbered from the view's base (vt[v] = (tiles_x, tile base)); depth order only. The
+// tiles of each rectangle that meet the entry's screen bounds, replayed from the tile-count
+// pass's masks where it stored them, else tested against tslab with the view's image size.
 __global__ void k_emit_views(int64_t n, const uint32_t* __restrict__ sidx, const uint32_t* __restrict__ count,
                              const short4* __restrict__ rect, const uint32_t* __restrict__ offs, uint32_t n_per_view,
-                             const int2* __restrict__ vt, uint64_t* __restrict__ keys) {
+                             const int2* __restrict__ vt, const CamParams* __restrict__ cps,
+                             const TileSlab* __restrict__ tslab, const uint32_t* __restrict__ tbits,
+                             const uint32_t* __restrict__ tbits_off, uint64_t* __restrict__ keys) {
   const int lane = threadIdx.x & 31;
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  uint32_t pid = 0, c = 0, off = 0;
-  int tx = 0, base = 0;
-  short4 r = make_short4(0, 0, 0, 0);
-  if (j < n) {
+  const int64_t j0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kEmitPerWarp;
+  const int64_t j = j0 + lane;
+  uint32_t pid = 0, c = 0, off = 0, wo = kNoTileBits;
+  int view = 0, rxy = 0, rzw = 0;
+  if (lane < kEmitPerWarp && j < n) {  // lane k fetches entry k's data up front
     pid = sidx[j];
     c = count[pid];
     if (c) {
       off = offs[j];
-      r = rect[pid];
-      const int2 t = vt[pid / n_per_view];
-      tx = t.x;
-      base = t.y;
+      const short4 rc = rect[pid];
+      rxy = (int)(((uint32_t)(uint16_t)rc.y << 16) | (uint16_t)rc.x);
+      rzw = (int)(((uint32_t)(uint16_t)rc.w << 16) | (uint16_t)rc.z);
+      view = (int)(pid / n_per_view);
+      if (tbits) wo = tbits_off[pid];
     }
   }
-  for (int k = 0; k < 32; ++k) {
+  for (int k = 0; k < kEmitPerWarp; ++k) {
     const uint32_t cc = __shfl_sync(0xffffffffu, c, k);
     if (!cc) continue;
     const uint32_t pp = __shfl_sync(0xffffffffu, pid, k);
     const uint32_t oo = __shfl_sync(0xffffffffu, off, k);
-    const int txk = __shfl_sync(0xffffffffu, tx, k);
-    const int bk = __shfl_sync(0xffffffffu, base, k);
-    const int rx0 = __shfl_sync(0xffffffffu, (int)r.x, k);
-    const int rx1 = __shfl_sync(0xffffffffu, (int)r.y, k);
-    const int ry0 = __shfl_sync(0xffffffffu, (int)r.z, k);
-    const uint32_t w = (uint32_t)(rx1 - rx0 + 1);
-    for (uint32_t e = lane; e < cc; e += 32) {
-      const uint32_t dy = e / w, dx = e - dy * w;
-      const uint32_t tile = (uint32_t)bk + (uint32_t)(ry0 + (int)dy) * (uint32_t)txk + (uint32_t)(rx0 + (int)dx);
+    const uint32_t wk = __shfl_sync(0xffffffffu, wo, k);
+    const int vk = __shfl_sync(0xffffffffu, view, k);
+    const int a = __shfl_sync(0xffffffffu, rxy, k), b = __shfl_sync(0xffffffffu, rzw, k);
+    const short4 rk = make_short4((short)(a & 0xFFFF), (short)(a >> 16), (short)(b & 0xFFFF), (short)(b >> 16));
+    const int2 t = vt[vk];
+    warp_tiles(rk, tslab ? tslab + pp : nullptr, cps[vk].W, cps[vk].H, [&](uint32_t e, int tx, int ty) {
+      const uint32_t tile = (uint32_t)t.y + (uint32_t)ty * (uint32_t)t.x + (uint32_t)tx;
       keys[(size_t)oo + e] = ((uint64_t)tile << 32) | pp;
-    }
+    }, nullptr, wk != kNoTileBits ? tbits + wk : nullptr);
   }
 }
 
@@ -167,7 +172,6 @@ __global__ void k_gather_state(int64_t V, const uint32_t* __restrict__ sidx, con
 // uint64_t with rb = 32. One warp writes kEmitPerWarp consecutive primitives' tiles
 // (coalesced); few primitives per warp keep enough warps in flight, as the visible
 // primitives are a small fraction of a large scene.
-constexpr int kEmitPerWarp = 8;
 template <typename K>
 __global__ void k_emit_packed(int64_t V, const uint32_t* __restrict__ sidx, const uint32_t* __restrict__ cnt_sorted,
                               const short4* __restrict__ rect, const TileSlab* __restrict__ tslab, int W, int H,
@@ -889,6 +893,12 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
   QGS_CU(ctx->cnt_sorted.reserve(n1), "alloc cnt");
   QGS_CU(ctx->offs.reserve(n1 + 1), "alloc offs");
   QGS_CU(ctx->rect.reserve(n1), "alloc rect");
+  QGS_CU(ctx->tslab.reserve(n1), "alloc tile slabs");
+  QGS_CU(ctx->tbits_off.reserve(n1), "alloc tile mask offsets");
+  if (ctx->tbits_want) QGS_CU(ctx->tbits.reserve(ctx->tbits_want), "alloc tile masks");
+  const uint32_t cap_words =
+      ctx->tbits_want ? (uint32_t)std::min<size_t>(std::min(ctx->tbits.cap, ctx->tbits_want), 0xFFFFFFF0u) : 0u;
+  const bool tb_on = N > 0 && cap_words > 0;
   QGS_CU(ctx->ranges.reserve((size_t)T_all), "alloc ranges");
   QGS_CU(ctx->torder.reserve((size_t)T_all), "alloc tile order");
   QGS_CU(ctx->hist.reserve(radix_hist_elems((int64_t)n1)), "alloc hist");
@@ -906,10 +916,16 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
   SceneView sv{scene->mean, scene->quat, scene->scale, scene->curv, scene->opacity, scene->sh};
   if (N > 0) {
     k_preprocess_views<<<dim3(pre_blocks(N), (unsigned)V), 256, 0, st>>>(N, sv, d_cp, ctx->state.p, ctx->count.p,
-                                                                   ctx->zkey.p, ctx->idx.p, ctx->rect.p,
-                                                                   ctx->dcount.p);
+                                                                   ctx->zkey.p, ctx->idx.p, ctx->rect.p, nullptr,
+                                                                   ctx->tslab.p);
     ++launch_counter();
     QGS_CU(cudaGetLastError(), "k_preprocess_views");
+    // keep each view's rectangle tiles that meet the parallelogram and the conic
+    k_count_tiles<<<dim3((unsigned)((N + kCountBlock - 1) / kCountBlock), (unsigned)V), kCountBlock, 0, st>>>(
+        N, ctx->tslab.p, 0, 0, ctx->count.p, ctx->rect.p, ctx->zkey.p, nullptr, ctx->dcount.p,
+        tb_on ? ctx->tbits.p : nullptr, ctx->tbits_off.p, cap_words, d_cp);
+    ++launch_counter();
+    QGS_CU(cudaGetLastError(), "k_count_tiles");
   }
   cudaError_t e = cudaSuccess;
   const bool fl0 = radix_sort_u32_pairs(ctx->zkey.p, ctx->idx.p, ctx->zkey2.p, ctx->idx2.p, VN, 0, 32, tmp, st, &e);
@@ -921,11 +937,12 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
     QGS_CU(cudaGetLastError(), "gather");
   }
   QGS_CU(scan_exclusive_u32(ctx->cnt_sorted.p, ctx->offs.p, VN, ctx->scan_tmp.p, ctx->scan_tmp.cap, st), "scan");
-  QGS_CU(cudaMemcpyAsync(ctx->h_total, ctx->offs.p + VN, sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "total");
-  QGS_CU(cudaMemcpyAsync(ctx->h_total + 1, ctx->dcount.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "visible");
+  QGS_CU(cudaMemcpyAsync(ctx->h_total, ctx->dcount.p, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "totals");
   QGS_CU(cudaStreamSynchronize(st), "sync");
-  const int64_t I = (int64_t)ctx->h_total[0];
-  ctx->n_visible = (int64_t)ctx->h_total[1];
+  const int64_t I = (int64_t)ctx->h_total[1];
+  ctx->n_visible = (int64_t)ctx->h_total[0];
+  if (tb_on && !ctx->tbits_fixed && (size_t)ctx->h_total[2] > cap_words)
+    ctx->tbits_want = (size_t)ctx->h_total[2] + ctx->h_total[2] / 4;
 
   const size_t i1 = (size_t)(I > 0 ? I : 1);
   QGS_CU(ctx->inst.reserve(i1), "alloc inst");
@@ -939,8 +956,9 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
 
   const uint64_t* sorted = ctx->inst.p;
   if (VN > 0 && I > 0) {
-    k_emit_views<<<nblk(VN), 256, 0, st>>>(VN, sidx, ctx->count.p, ctx->rect.p, ctx->offs.p, (uint32_t)N, d_vt,
-                                           ctx->inst.p);
+    k_emit_views<<<emit_blocks(VN), 256, 0, st>>>(VN, sidx, ctx->count.p, ctx->rect.p, ctx->offs.p, (uint32_t)N,
+                                                  d_vt, d_cp, ctx->tslab.p, tb_on ? ctx->tbits.p : nullptr,
+                                                  ctx->tbits_off.p, ctx->inst.p);
     ++launch_counter();
     QGS_CU(cudaGetLastError(), "emit");
     const bool fl = radix_sort_u64_keys(ctx->inst.p, ctx->inst2.p, I, 32, 32 + bits_for(T_all), tmp, st, &e);

@@ -377,12 +377,14 @@ __global__ void __launch_bounds__(256) k_preprocess(int64_t n, SceneView sc, Cam
 __global__ void __launch_bounds__(256) k_preprocess_views(int64_t n, SceneView sc, const CamParams* __restrict__ cps,
                                                           PrimState* __restrict__ state, uint32_t* __restrict__ count,
                                                           uint32_t* __restrict__ zkey, uint32_t* __restrict__ idx,
-                                                          short4* __restrict__ rect, uint32_t* __restrict__ n_visible) {
+                                                          short4* __restrict__ rect, uint32_t* __restrict__ n_visible,
+                                                          TileSlab* __restrict__ tslab) {
   const int64_t off = (int64_t)blockIdx.y * n;
   const CamParams cp = cps[blockIdx.y];
   uint32_t vis, tot;
-  preprocess_block(n, sc, cp, state + off, count + off, zkey + off, idx + off, rect + off, (uint32_t)off, nullptr,
-                   nullptr, vis, tot);
+  preprocess_block(n, sc, cp, state + off, count + off, zkey + off, idx + off, rect + off, (uint32_t)off,
+                   tslab ? tslab + off : nullptr, nullptr, vis, tot);
+  if (!n_visible) return;
   vis = __reduce_add_sync(0xffffffffu, vis);
   __shared__ uint32_t red[8];  // one atomic per CTA
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = vis;
@@ -791,7 +793,16 @@ __global__ void __launch_bounds__(kCountBlock) k_count_tiles(int64_t n, const Ti
                                                      uint32_t* __restrict__ count, short4* __restrict__ rect,
                                                      uint32_t* __restrict__ zkey, uint32_t* __restrict__ vflag,
                                                      uint32_t* __restrict__ counters, uint32_t* __restrict__ tbits,
-                                                     uint32_t* __restrict__ tbits_off, uint32_t cap_words) {
+                                                     uint32_t* __restrict__ tbits_off, uint32_t cap_words,
+                                                     const CamParams* __restrict__ cps) {
+  if (cps) {  // several views (blockIdx.y): entries v * n + i, the view's image size
+    const int64_t off = (int64_t)blockIdx.y * n;
+    tslab += off; count += off; rect += off; zkey += off;
+    if (vflag) vflag += off;
+    if (tbits_off) tbits_off += off;
+    W = cps[blockIdx.y].W;
+    H = cps[blockIdx.y].H;
+  }
   __shared__ uint32_t bsum[2], bdone;
   if (threadIdx.x == 0) {
     bsum[0] = bsum[1] = 0u;

@@ -204,9 +204,11 @@ __device__ __forceinline__ uint32_t warp_tiles(short4 r, const TileSlab* t, int 
 // Launched with kCountBlock threads per CTA (small CTAs: the warps' work varies widely and
 // a CTA's slot is held until its slowest warp ends).
 constexpr int kCountBlock = 64;
+// With cps (several views of one scene, blockIdx.y = view): the arrays hold entries
+// v * n + i and each view's image size comes from cps[v].
 __global__ void k_count_tiles(int64_t n, const TileSlab* tslab, int W, int H, uint32_t* count, short4* rect,
                               uint32_t* zkey, uint32_t* vflag, uint32_t* counters, uint32_t* tbits,
-                              uint32_t* tbits_off, uint32_t cap_words);
+                              uint32_t* tbits_off, uint32_t cap_words, const CamParams* cps = nullptr);
 
 // ---------------------------------------------------------------- preprocessing
 // k_preprocess / k_preprocess_views: 256 threads per CTA, kPreChunks x 256 primitives per
@@ -220,7 +222,8 @@ __global__ void k_preprocess(int64_t n, SceneView sc, CamParams cp, PrimState* s
                              uint32_t* zkey, uint32_t* idx, short4* rect, uint32_t* counters, uint32_t* vflag,
                              TileSlab* tslab);
 __global__ void k_preprocess_views(int64_t n, SceneView sc, const CamParams* cps, PrimState* state, uint32_t* count,
-                                   uint32_t* zkey, uint32_t* idx, short4* rect, uint32_t* n_visible);
+                                   uint32_t* zkey, uint32_t* idx, short4* rect, uint32_t* n_visible,
+                                   TileSlab* tslab);
 // StopThePop ordering: per (tile, primitive) instance, in primitive order,
 // key = (tile << 32) | bits of the depth where the ray of the tile pixel closest to the
 // projected vertex meets the paraboloid; value = primitive.
