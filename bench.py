@@ -319,6 +319,7 @@ def run_gpu(args):
     ras.set_pair_counters(True)
     step()
     st = ras.stats()
+    ras.set_pair_counters(False)
     st["ms_raster_bwd_timed"] = st_timed["ms_raster_bwd"]
     st["ms_raster_fwd_timed"] = st_timed["ms_raster_fwd"]
     L.check(lib.qgs_set_profiling(ras._ctx, 0), ras._ctx)
@@ -394,12 +395,29 @@ def _e2e(args, ras, ds, cam, gout, grads, out, dev, world, P):
     h2d = sum(v.numel() * 4 for v in host_g.values())
     d2h = host_rgb.numel() * 4
 
+    # the copies run on a side stream: this step's upstream gradients go up while the
+    # forward renders, its image comes down while the backward runs; the step (timed on the
+    # main stream) ends when both copies are complete
+    cs = torch.cuda.Stream(dev)
+    ev_g = torch.cuda.Event()
+    ev_f = torch.cuda.Event()
+    ev_d = torch.cuda.Event()
+
     def e2e_step():
-        for k in dev_g:
-            dev_g[k].copy_(host_g[k], non_blocking=True)
+        cs.wait_stream(stream)  # the previous step is done with dev_g and host_rgb
+        with torch.cuda.stream(cs):
+            for k in dev_g:
+                dev_g[k].copy_(host_g[k], non_blocking=True)
+            ev_g.record(cs)
         ras.forward(ds, cam, out)
+        ev_f.record(stream)
+        stream.wait_event(ev_g)
         ras.backward(ds, cam, dev_g, grads)
-        host_rgb.copy_(out["rgb"], non_blocking=True)
+        cs.wait_event(ev_f)
+        with torch.cuda.stream(cs):
+            host_rgb.copy_(out["rgb"], non_blocking=True)
+            ev_d.record(cs)
+        stream.wait_event(ev_d)
 
     for _ in range(2):
         e2e_step()

@@ -763,9 +763,11 @@ __global__ void __launch_bounds__(BLOCK, 3)
   uint32_t evals = 0, grazes = 0, isect = 0, hits = 0, blended = 0, dummy = 0;
   bool done = !inside;
   ResortBuf buf;
-  // blend the entry at list position pos (re-evaluated from its state record)
+  // blend the entry at list position pos (re-evaluated from its state record: the staged
+  // copy when it is in the current batch, else global memory)
+  uint32_t cur0 = 0, cur1 = 0;  // list positions [cur0, cur1) staged in sm
   auto blend = [&](uint32_t pos) {
-    const PrimState P = load_state(state, __ldg(ids + pos) & rp.id_mask);
+    const PrimState P = (pos >= cur0 && pos < cur1) ? sm[pos - cur0] : load_state(state, __ldg(ids + pos) & rp.id_mask);
     Hit h;
     bool gz = false;
     if (!eval_pair<EUCLID>(P, X, Y, rp, h, gz, dummy)) return;  // deterministic: it hit when buffered
@@ -807,6 +809,8 @@ __global__ void __launch_bounds__(BLOCK, 3)
     if (__syncthreads_count(done) == BLOCK) break;
     const int cnt = min(BLOCK, n - b0);
     stage_batch(sm, ids, 1, rp.id_mask, state, rg.x + b0, cnt);
+    cur0 = rg.x + (uint32_t)b0;
+    cur1 = cur0 + (uint32_t)cnt;
     __syncthreads();
     if (!done) {
       for (int j = 0; j < cnt; ++j) {
@@ -912,9 +916,10 @@ __global__ void __launch_bounds__(BLOCK, 2)
   uint32_t n_pairs = 0, n_contrib_pairs = 0, dummy = 0;
   bool done = !inside;
   ResortBuf buf;
+  uint32_t cur0 = 0, cur1 = 0;  // list positions [cur0, cur1) staged in sm
   auto blend = [&](uint32_t pos) {
     const uint32_t pid = __ldg(ids + pos) & rp.id_mask;
-    const PrimState Ps = load_state(state, pid);
+    const PrimState Ps = (pos >= cur0 && pos < cur1) ? sm[pos - cur0] : load_state(state, pid);
     Hit h;
     bool gz = false;
     if (!eval_pair<EUCLID>(Ps, X, Y, rp, h, gz, dummy)) return;
@@ -940,6 +945,8 @@ __global__ void __launch_bounds__(BLOCK, 2)
     if (__syncthreads_count(done) == BLOCK) break;
     const int cnt = min(BLOCK, n - b0);
     stage_batch(sm, ids, 1, rp.id_mask, state, rg.x + b0, cnt);
+    cur0 = rg.x + (uint32_t)b0;
+    cur1 = cur0 + (uint32_t)cnt;
     __syncthreads();
     if (!done) {
       for (int j = 0; j < cnt; ++j) {
