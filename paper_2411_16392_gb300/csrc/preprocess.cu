@@ -1,18 +1,21 @@
 // Per-primitive preprocessing (forward and backward) of the quadric rasterizer.
 //
-// Forward (one thread per primitive):
+// Forward (2048 primitives per CTA: an early exit for all of them, then the full recipe
+// for the survivors, one thread each):
 //   - camera-space centre, rotation R from the normalised quaternion and the
 //     camera-from-local rotation W = R_cw R (the congruent transform of Sec. 3.2);
-//   - the conservative screen bound of the curved patch and its 16x16 tile rectangle
-//     (supplementary, "Details of Bounding Box Calculation": the loose box, with a
-//     provable z clamp, clipped to the near plane), and the 32-bit depth key
+//   - the conservative screen bounds of the curved patch (supplementary, "Details of
+//     Bounding Box Calculation", read with arc >= chord): a local support box clipped to
+//     the near plane and projected, a screen parallelogram around it, and the screen
+//     conic of the chord ellipsoid; the 16x16 tile rectangle and the 32-bit depth key
 //     (supplementary, per-tile sorting);
 //   - degree-3 SH colour (Sec. 3.1) from bfloat16 coefficients, evaluated in FP32;
 //   - the 128-byte projected-state record read by the compositing kernels.
-// The centre depth, the box and the tile rectangle are computed with correctly
-// rounded FP32 operations only (__fmul_rn, __fadd_rn, __fdiv_rn, __fsqrt_rn), each in
-// a fixed order, so that the tile lists and keys are reproducible bit for bit by an
-// independent implementation of the same recipe.
+// The centre depth, the box, the screen bounds and the tile rectangle are computed with
+// correctly rounded FP32 operations only (__fmul_rn, __fadd_rn, __fdiv_rn, __frcp_rn,
+// __fsqrt_rn), each in a fixed order, so that the tile lists and keys are reproducible bit
+// for bit by an independent implementation of the same recipe. The tile-count pass
+// (k_count_tiles) keeps the tiles of each rectangle that meet both screen bounds.
 //
 // Backward (one thread per primitive): chain rule from the per-primitive gradient
 // record accumulated by the compositing backward to mean, quaternion, scales,
@@ -99,8 +102,8 @@ __device__ __forceinline__ bool quat_rot_exact(float qw, float qx, float qy, flo
   return true;
 }
 
-// Projected points of the support box: their pixel AABB (bit-exact part) and their
-// spans along the two directions of a screen-space parallelogram (ordinary FP32).
+// Projected points of the support box: their pixel AABB and their spans along the two
+// directions of a screen-space parallelogram.
 struct Box2 {
   float xmin, xmax, ymin, ymax;
   bool any;

@@ -4,6 +4,9 @@
 // tile's sorted primitive list is walked in batches of 256 projected-state records
 // staged in shared memory (one 128-byte line per primitive, gathered by 8 threads per
 // record). Per (pixel, primitive) pair:
+//   - the pixel's offset from the projected centre (double-float) is tested against the
+//     screen conic of the chord ellipsoid x^2/s_u^2 + y^2/s_v^2 + z^2/m^2 <= 9 that holds
+//     the support (arc >= chord): a pixel whose ray line misses it cannot have a hit;
 //   - the pixel ray is expressed in the primitive's local frame relative to the point
 //     where it crosses the depth of the primitive's centre (a translation of the ray
 //     parameter t = z_mu + s); the pixel offset from the projected centre is formed in
@@ -15,8 +18,8 @@
 //   - near-then-far selection within 3 sigma(theta) (Sec. 3.2.1) via the trig-free form
 //     l^2 / sigma(theta)^2 = F(u)^2 E, E = x^2/s_u^2 + y^2/s_v^2, u = 2 a(theta) rho,
 //     F(u) = l / rho = (asinh(u)/u + sqrt(1 + u^2)) / 2 (geodesic Eq. and sigma Eq. of
-//     Sec. 3.2); F >= 1, so E > 9 rejects a candidate before F is evaluated; F uses its
-//     Taylor series 1 + u^2/6 - u^4/40 for |u| < 1e-3;
+//     Sec. 3.2); F >= sqrt(1 + u^2/4) >= 1, so E > 9 and then E (1 + u^2/4) > 9 reject a
+//     candidate before F is evaluated; F uses its Taylor series for |u| < 0.25;
 //   - G = exp(-F^2 E / 2), alpha = min(alpha_max, o G), skip below alpha_min, stop before
 //     the transmittance would fall below T_min (Sec. 3.1 blending Eq.);
 //   - normal = gradient of the implicit function (Sec. 3.2 normal Eq.) in camera space,
@@ -24,9 +27,10 @@
 // The backward walks each pixel's list in reverse from its last blended primitive,
 // recomputing T_i = T_{i+1} / (1 - alpha_i) (supplementary, back-to-front dX/d(alpha)),
 // and differentiates through the implicit root, the geodesic weight and the normal.
-// Per-primitive gradients are reduced across each warp with a transpose reduction,
-// accumulated per batch in shared memory, and added to global memory once per
-// (tile, primitive).
+// Per-primitive gradients are reduced across each warp with a butterfly reduce-scatter
+// (21 shuffles for the 20 components), accumulated per batch in shared memory, and added
+// to global memory once per (tile, primitive). The per-pair statistics counters are a
+// template parameter (compiled out unless requested).
 //
 // Every operation that decides whether a pair contributes is written with explicitly
 // rounded intrinsics, so the forward and the backward (which recomputes the pairs)
