@@ -55,7 +55,7 @@ B_PRE_PRIM, B_PRE_VIS = 164, 128 + 2 * 80
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, summary under profiles/),
 # valid only while the kernels' sources hash to the recorded value.
 TRAFFIC_SRC = ("paper_2411_16392_gb300/csrc/raster.cu", "paper_2411_16392_gb300/csrc/qgs_common.cuh")
-TRAFFIC = {"hash": "8150afd27e0d6aff", "k_raster_fwd": 13452800 + 1178624, "k_raster_bwd": 56415232 + 19712}
+TRAFFIC = {"hash": "aebe601613de2e39", "k_raster_fwd": 13452032 + 1142272, "k_raster_bwd": 56476416 + 27392}
 B_BIN_VIS, B_BIN_INST = 4 * 20 + 256, 4 + 2 * 12 + 4
 B_PREBWD_VIS = 80 + 144 + 480
 
