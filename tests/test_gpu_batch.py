@@ -1,6 +1,7 @@
 """Batched multi-view forward (render_forward_batch): every view's planes equal a plain
-render_forward of that camera bit for bit, at mixed and ragged resolutions, and the
-batch's counters are the sums of the single renders' counters."""
+render_forward of that camera bit for bit, at mixed and ragged resolutions (with and
+without the tile-mask store), and the batch's counters are the sums of the single
+renders' counters."""
 import ctypes as C
 
 import numpy as np
@@ -51,13 +52,19 @@ def test_batch_equals_single_renders_mixed_resolutions(dev):
     torch.cuda.synchronize()
     _assert_bit_equal(outs, singles, cams)
     sb = ras.stats()
-    # the batch lists every tile of each rectangle (the single renders drop the tiles that
-    # miss a primitive's parallelogram): more instances and evaluations, the same blending
-    for key in ("n_tiles", "pair_blended"):
+    # the batch keeps the same tiles of each rectangle as the single renders (tile test
+    # against the parallelogram and the conic): the same lists, evaluations and blending
+    for key in ("n_tiles", "n_instances", "n_visible", "pair_evals", "pair_isect", "pair_hits", "pair_blended"):
         assert sb[key] == sum(s[key] for s in st1), key
-    for key in ("n_instances", "n_visible", "pair_evals", "pair_isect"):
-        assert sb[key] >= sum(s[key] for s in st1), key
     assert sb["n_primitives"] == len(cams) * ds.n
+    # the tile-mask store does not change the batch either: none, too small for the batch
+    for cap in (0, 64):
+        ras.set_tile_mask_capacity(cap)
+        outs2 = [{k: torch.full_like(v, 5.0) for k, v in s.items()} for s in singles]
+        ras.forward_batch(ds, cams, outs2)
+        torch.cuda.synchronize()
+        _assert_bit_equal(outs2, singles, cams)
+        assert ras.stats()["n_instances"] == sb["n_instances"]
     # a second batch in another order reuses the buffers and still matches
     perm = [4, 0, 8, 2]
     outs2 = ras.forward_batch(ds, [cams[i] for i in perm])
