@@ -71,6 +71,19 @@ def _traffic(kernel, n_prims):
     return TRAFFIC.get(kernel)
 
 
+def reduce_step_time(ms_local, world, pixels, device="cpu"):
+    """Whole-job timing over the ranks: the maximum of the ranks' per-step times (every rank
+    takes part in the reduction) and the whole-job throughput in Mpix/s, world x pixels per
+    step over that time. `device` holds the reduction's tensor (cuda under NCCL)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, world * pixels / (ms_max * 1e-3) / 1e6
+
+
 def _rank_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
             int(os.environ.get("LOCAL_RANK", 0)))
@@ -323,11 +336,7 @@ def run_gpu(args):
     st["ms_raster_bwd_timed"] = st_timed["ms_raster_bwd"]
     st["ms_raster_fwd_timed"] = st_timed["ms_raster_fwd"]
     L.check(lib.qgs_set_profiling(ras._ctx, 0), ras._ctx)
-    t = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * P / (ms_max * 1e-3) / 1e6
+    ms_max, value = reduce_step_time(ms, world, P, dev)
 
     # ---- end to end through the public API with host buffers
     if args.no_e2e:
@@ -431,10 +440,7 @@ def _e2e(args, ras, ds, cam, gout, grads, out, dev, world, P):
     e1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = e0.elapsed_time(e1) / ne
-    t = torch.tensor([ms_e2e], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = world * P / (float(t.item()) * 1e-3) / 1e6
+    _, e2e_value = reduce_step_time(ms_e2e, world, P, dev)
     return e2e_value, h2d, d2h
 
 

@@ -1,0 +1,56 @@
+"""The multi-rank path of bench.py on CPU: two gloo ranks (replicas, no data-path
+collective) reduce their step times to the maximum on every rank and report the
+whole-job throughput; the reference arm runs on rank 0 only."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    ms_max, value = bench.reduce_step_time(1.0 + rank, world, 1_000_000)
+    r_env = bench._rank_env()
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((rank, ms_max, value, r_env))
+
+
+def test_two_ranks_take_the_slowest_rank_and_sum_the_work():
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ms_max, value, env in res:
+        assert ms_max == 2.0                              # the slowest rank's step time
+        assert value == pytest.approx(2 * 1.0 / 2e-3)     # 2 x 1 Mpix per step over 2 ms
+        assert env[0] == rank and env[1] == world
+
+
+def test_reference_arm_is_rank_zero_only(monkeypatch, capsys):
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+
+    class Args:
+        steps, warmup, gpus = 1, 1, 2
+
+    assert bench.run_reference(Args()) == 0
+    assert capsys.readouterr().out == ""
