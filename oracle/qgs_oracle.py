@@ -59,9 +59,14 @@ design notes of the repository):
     the near root and is not used as a separate approximation.
   * Screen bound: the 8 corners of a local box that contains the support, clipped to
     the near plane, projected, and their pixel AABB taken (the supplementary's
-    bounding-box section). The box comes from "arc length >= chord" (see bin_fp32);
-    it is evaluated in FP32 with correctly rounded operations in a fixed order so
-    that tile lists and keys can be compared bit for bit.
+    bounding-box section). The box comes from "arc length >= chord" (see bin_fp32).
+    A tile of the AABB is listed only if it also meets a screen parallelogram around the
+    projected box and the screen conic of the ellipsoid x^2/s_u^2 + y^2/s_v^2 + z^2/m^2
+    <= 9 that the same inequality puts around the support (ellipsoid_conic, _tile_pass);
+    the AABB is first cut to the conic's bounding box (conic_box). All of it is
+    evaluated in FP32 with correctly rounded operations in a fixed order so that tile
+    lists and keys can be compared bit for bit; the lists only decide which pairs are
+    evaluated, never a pair's value, and they keep every pair with a hit (pinned).
 
 Gradients are exact derivatives of this FP64 forward, taken by PyTorch autograd.
 """
