@@ -33,7 +33,12 @@ struct DevBuf {
   cudaError_t reserve(size_t n) {
     if (n <= cap) return cudaSuccess;
     size_t want = n + n / 4 + 64;
-    if (p) cudaFree(p);
+    if (p) {
+      // work already enqueued may still use the old buffer (the forward enqueues kernels
+      // before it waits for its totals): let it finish before freeing
+      cudaDeviceSynchronize();
+      cudaFree(p);
+    }
     p = nullptr;
     cap = 0;
     cudaError_t e = cudaMalloc((void**)&p, want * sizeof(T));
@@ -396,6 +401,7 @@ struct qgs_ctx {
   uint8_t* h_vdesc = nullptr;
   size_t h_vdesc_cap = 0;
   cudaEvent_t vdesc_done = nullptr;  // the staging buffer's last upload has completed
+  cudaEvent_t totals_ready = nullptr;  // the frame's totals have reached h_total
 };
 
 namespace {
@@ -538,6 +544,7 @@ void qgs_destroy(qgs_ctx* c) {
   c->dstate.release();
   if (c->h_vdesc) cudaFreeHost(c->h_vdesc);
   if (c->vdesc_done) cudaEventDestroy(c->vdesc_done);
+  if (c->totals_ready) cudaEventDestroy(c->totals_ready);
   if (c->h_total) cudaFreeHost(c->h_total);
   for (int i = 0; i < 10; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -622,11 +629,19 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
     QGS_CU(cudaGetLastError(), "k_count_tiles");
   }
   mark(ctx, 1, st);
-  // positions of the visible primitives (index order)
-  if (sm == 0) QGS_CU(scan_exclusive_u32(ctx->vpos.p, ctx->vpos.p, N, ctx->scan_tmp.p, ctx->scan_tmp.cap, st), "scan");
-  // the frame's one synchronisation: visible and instance totals size what follows
+  // the frame's one synchronisation: visible and instance totals size what follows; the
+  // compaction of the visible primitives (index order), which needs no total, is enqueued
+  // before the host waits, so it runs during the read-back
   QGS_CU(cudaMemcpyAsync(ctx->h_total, ctx->dcount.p, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "totals");
-  QGS_CU(cudaStreamSynchronize(st), "sync");
+  if (!ctx->totals_ready) QGS_CU(cudaEventCreateWithFlags(&ctx->totals_ready, cudaEventDisableTiming), "event");
+  QGS_CU(cudaEventRecord(ctx->totals_ready, st), "event");
+  if (sm == 0 && N > 0) {
+    QGS_CU(scan_exclusive_u32(ctx->vpos.p, ctx->vpos.p, N, ctx->scan_tmp.p, ctx->scan_tmp.cap, st), "scan");
+    k_compact<<<nblk(N), 256, 0, st>>>(N, ctx->count.p, ctx->zkey.p, ctx->vpos.p, ctx->zkey2.p, ctx->idx2.p);
+    ++launch_counter();
+    QGS_CU(cudaGetLastError(), "compact");
+  }
+  QGS_CU(cudaEventSynchronize(ctx->totals_ready), "sync");
   const int64_t V = (int64_t)ctx->h_total[0];
   const int64_t I = (int64_t)ctx->h_total[1];
   // primitives whose masks did not fit are tested again by the emission; provide more next frame
@@ -657,11 +672,6 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   if (sm == 0) {
     // visible primitives (index order) -> depth sort -> state, counts and offsets in
     // depth order -> instances (tile << rb | depth rank) -> stable sort on the tile bits
-    if (N > 0 && V > 0) {
-      k_compact<<<nblk(N), 256, 0, st>>>(N, ctx->count.p, ctx->zkey.p, ctx->vpos.p, ctx->zkey2.p, ctx->idx2.p);
-      ++launch_counter();
-      QGS_CU(cudaGetLastError(), "compact");
-    }
     const bool fl = radix_sort_u32_pairs(ctx->zkey2.p, ctx->idx2.p, ctx->zkey.p, ctx->idx.p, V, 0, 32, tmp, st, &e);
     QGS_CU(e, "depth sort");
     const uint32_t* sidx = fl ? ctx->idx.p : ctx->idx2.p;
@@ -927,6 +937,11 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
     ++launch_counter();
     QGS_CU(cudaGetLastError(), "k_count_tiles");
   }
+  // the totals' read-back; the depth sort, gather and scan (sized by the batch, not by
+  // the totals) are enqueued before the host waits, so they run during the read-back
+  QGS_CU(cudaMemcpyAsync(ctx->h_total, ctx->dcount.p, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "totals");
+  if (!ctx->totals_ready) QGS_CU(cudaEventCreateWithFlags(&ctx->totals_ready, cudaEventDisableTiming), "event");
+  QGS_CU(cudaEventRecord(ctx->totals_ready, st), "event");
   cudaError_t e = cudaSuccess;
   const bool fl0 = radix_sort_u32_pairs(ctx->zkey.p, ctx->idx.p, ctx->zkey2.p, ctx->idx2.p, VN, 0, 32, tmp, st, &e);
   QGS_CU(e, "depth sort");
@@ -937,8 +952,7 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
     QGS_CU(cudaGetLastError(), "gather");
   }
   QGS_CU(scan_exclusive_u32(ctx->cnt_sorted.p, ctx->offs.p, VN, ctx->scan_tmp.p, ctx->scan_tmp.cap, st), "scan");
-  QGS_CU(cudaMemcpyAsync(ctx->h_total, ctx->dcount.p, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "totals");
-  QGS_CU(cudaStreamSynchronize(st), "sync");
+  QGS_CU(cudaEventSynchronize(ctx->totals_ready), "sync");
   const int64_t I = (int64_t)ctx->h_total[1];
   ctx->n_visible = (int64_t)ctx->h_total[0];
   if (tb_on && !ctx->tbits_fixed && (size_t)ctx->h_total[2] > cap_words)
