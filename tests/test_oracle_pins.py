@@ -767,3 +767,39 @@ def test_conic_tile_test_against_the_rectangle():
                     rejected += 1
                 checked += 1
     assert checked > 200 and rejected > 20
+
+
+def test_conic_box_holds_the_conic():
+    """The conic's bounding box (the tiles the rectangle is cut to) holds every pixel
+    offset with F <= 1: brute force over a fine grid around each projected centre (FP64
+    evaluation of the recipe's coefficients), and the box is no wider than the ellipse's
+    exact half-extents sqrt(R (q^-1)_ii) plus one tile."""
+    sc, cam = _small_scene(n=300, W=96, seed=8)
+    sc.scale *= np.float32(3.0)
+    sc.curv /= np.float32(3.0)
+    b = O.bin_fp32(sc, cam, emit=False)
+    sl = b.slabs
+    on = np.nonzero(b.visible & sl["conic_on"])[0]
+    assert on.size > 50
+    cb = O.conic_box({k: sl[k][on] for k in ("qa", "qb", "qc", "la", "lb")}, sl["uc"][on], sl["vc"][on])
+    checked = 0
+    for j, i in enumerate(on[:80]):
+        qa, qb, qc, la, lb = (float(sl[k][i]) for k in ("qa", "qb", "qc", "la", "lb"))
+        q = np.array([[qa, qb], [qb, qc]])
+        p0 = np.linalg.solve(q, np.array([la, lb]))
+        R = 1.0 + la * p0[0] + lb * p0[1]
+        ext = np.sqrt(R * np.diag(np.linalg.inv(q)))
+        u = np.linspace(p0[0] - 1.2 * ext[0], p0[0] + 1.2 * ext[0], 121)
+        v = np.linspace(p0[1] - 1.2 * ext[1], p0[1] + 1.2 * ext[1], 121)
+        U, Vv = np.meshgrid(u, v)
+        F = qa * U * U + 2 * qb * U * Vv + qc * Vv * Vv - 2 * la * U - 2 * lb * Vv
+        inside = F <= 1.0
+        X = float(sl["uc"][i]) + U[inside]
+        Y = float(sl["vc"][i]) + Vv[inside]
+        assert (np.floor(X / 16) >= cb[0][j]).all() and (np.floor(X / 16) <= cb[1][j]).all(), i
+        assert (np.floor(Y / 16) >= cb[2][j]).all() and (np.floor(Y / 16) <= cb[3][j]).all(), i
+        cx, cy = float(sl["uc"][i]) + p0[0], float(sl["vc"][i]) + p0[1]
+        assert cb[0][j] >= np.floor((cx - ext[0]) / 16) - 1 and cb[1][j] <= np.floor((cx + ext[0]) / 16) + 1, i
+        assert cb[2][j] >= np.floor((cy - ext[1]) / 16) - 1 and cb[3][j] <= np.floor((cy + ext[1]) / 16) + 1, i
+        checked += 1
+    assert checked >= 50
