@@ -356,7 +356,8 @@ struct qgs_ctx {
   // scratch
   DevBuf<uint32_t> hist, scan_tmp;
   DevBuf<RasterStats> stats;
-  DevBuf<uint32_t> dcount;      // [0] visible primitives, [1] instances, [2] tile-mask words
+  DevBuf<uint32_t> dcount;      // [0] visible primitives, [1] instances, [2] tile-mask words,
+                                // [3] radix look-back failure (kept across calls)
   uint32_t* h_total = nullptr;  // pinned: the frame's counters read back
   int64_t n_visible = 0;
   const uint32_t* vis_list = nullptr;
@@ -515,7 +516,8 @@ qgs_status qgs_create(qgs_ctx** out, const qgs_config* cfg, int32_t device) {
     delete c;
     return QGS_ENOMEM;
   }
-  if (c->stats.reserve(1) != cudaSuccess || c->dcount.reserve(4) != cudaSuccess) {
+  if (c->stats.reserve(1) != cudaSuccess || c->dcount.reserve(4) != cudaSuccess ||
+      cudaMemset(c->dcount.p, 0, 4 * sizeof(uint32_t)) != cudaSuccess) {
     cudaFreeHost(c->h_total);
     delete c;
     return QGS_ENOMEM;
@@ -608,11 +610,12 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   tmp.hist_cap = ctx->hist.cap;
   tmp.scan_tmp = ctx->scan_tmp.p;
   tmp.scan_cap = ctx->scan_tmp.cap;
+  tmp.err = ctx->dcount.p + 3;
 
   const int64_t launches0 = launch_counter();
   ctx->have_fwd_times = false;
   ctx->have_stats = false;
-  QGS_CU(cudaMemsetAsync(ctx->dcount.p, 0, sizeof(uint32_t) * 4, st), "memset counters");
+  QGS_CU(cudaMemsetAsync(ctx->dcount.p, 0, sizeof(uint32_t) * 3, st), "memset counters");
   mark(ctx, 0, st);
   SceneView sv{scene->mean, scene->quat, scene->scale, scene->curv, scene->opacity, scene->sh};
   if (N > 0) {
@@ -632,7 +635,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   // the frame's one synchronisation: visible and instance totals size what follows; the
   // compaction of the visible primitives (index order), which needs no total, is enqueued
   // before the host waits, so it runs during the read-back
-  QGS_CU(cudaMemcpyAsync(ctx->h_total, ctx->dcount.p, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "totals");
+  QGS_CU(cudaMemcpyAsync(ctx->h_total, ctx->dcount.p, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "totals");
   if (!ctx->totals_ready) QGS_CU(cudaEventCreateWithFlags(&ctx->totals_ready, cudaEventDisableTiming), "event");
   QGS_CU(cudaEventRecord(ctx->totals_ready, st), "event");
   if (sm == 0 && N > 0) {
@@ -642,6 +645,10 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
     QGS_CU(cudaGetLastError(), "compact");
   }
   QGS_CU(cudaEventSynchronize(ctx->totals_ready), "sync");
+  if (ctx->h_total[3]) {  // a radix sort of an earlier call gave up waiting for a chunk
+    cudaMemsetAsync(ctx->dcount.p + 3, 0, sizeof(uint32_t), st);
+    return fail(ctx, QGS_ECUDA, "a radix sort pass of an earlier call timed out in its look-back");
+  }
   const int64_t V = (int64_t)ctx->h_total[0];
   const int64_t I = (int64_t)ctx->h_total[1];
   // primitives whose masks did not fit are tested again by the emission; provide more next frame
@@ -664,6 +671,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   tmp.hist_cap = ctx->hist.cap;
   tmp.scan_tmp = ctx->scan_tmp.p;
   tmp.scan_cap = ctx->scan_tmp.cap;
+  tmp.err = ctx->dcount.p + 3;
 
   const int tb = bits_for(ntiles);
   cudaError_t e = cudaSuccess;
@@ -918,11 +926,12 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
   tmp.hist_cap = ctx->hist.cap;
   tmp.scan_tmp = ctx->scan_tmp.p;
   tmp.scan_cap = ctx->scan_tmp.cap;
+  tmp.err = ctx->dcount.p + 3;
 
   const int64_t launches0 = launch_counter();
   QGS_CU(cudaMemcpyAsync(ctx->vdesc.p, ctx->h_vdesc, vbytes, cudaMemcpyHostToDevice, st), "upload views");
   QGS_CU(cudaEventRecord(ctx->vdesc_done, st), "event");
-  QGS_CU(cudaMemsetAsync(ctx->dcount.p, 0, sizeof(uint32_t) * 4, st), "memset counters");
+  QGS_CU(cudaMemsetAsync(ctx->dcount.p, 0, sizeof(uint32_t) * 3, st), "memset counters");
   SceneView sv{scene->mean, scene->quat, scene->scale, scene->curv, scene->opacity, scene->sh};
   if (N > 0) {
     k_preprocess_views<<<dim3(pre_blocks(N), (unsigned)V), 256, 0, st>>>(N, sv, d_cp, ctx->state.p, ctx->count.p,
@@ -939,7 +948,7 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
   }
   // the totals' read-back; the depth sort, gather and scan (sized by the batch, not by
   // the totals) are enqueued before the host waits, so they run during the read-back
-  QGS_CU(cudaMemcpyAsync(ctx->h_total, ctx->dcount.p, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "totals");
+  QGS_CU(cudaMemcpyAsync(ctx->h_total, ctx->dcount.p, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "totals");
   if (!ctx->totals_ready) QGS_CU(cudaEventCreateWithFlags(&ctx->totals_ready, cudaEventDisableTiming), "event");
   QGS_CU(cudaEventRecord(ctx->totals_ready, st), "event");
   cudaError_t e = cudaSuccess;
@@ -953,6 +962,10 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
   }
   QGS_CU(scan_exclusive_u32(ctx->cnt_sorted.p, ctx->offs.p, VN, ctx->scan_tmp.p, ctx->scan_tmp.cap, st), "scan");
   QGS_CU(cudaEventSynchronize(ctx->totals_ready), "sync");
+  if (ctx->h_total[3]) {  // a radix sort of an earlier call gave up waiting for a chunk
+    cudaMemsetAsync(ctx->dcount.p + 3, 0, sizeof(uint32_t), st);
+    return fail(ctx, QGS_ECUDA, "a radix sort pass of an earlier call timed out in its look-back");
+  }
   const int64_t I = (int64_t)ctx->h_total[1];
   ctx->n_visible = (int64_t)ctx->h_total[0];
   if (tb_on && !ctx->tbits_fixed && (size_t)ctx->h_total[2] > cap_words)
@@ -967,6 +980,7 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
   tmp.hist_cap = ctx->hist.cap;
   tmp.scan_tmp = ctx->scan_tmp.p;
   tmp.scan_cap = ctx->scan_tmp.cap;
+  tmp.err = ctx->dcount.p + 3;
 
   const uint64_t* sorted = ctx->inst.p;
   if (VN > 0 && I > 0) {

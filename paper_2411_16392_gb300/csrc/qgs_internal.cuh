@@ -242,9 +242,10 @@ constexpr int kRadixChunk = 2048;
 
 // Temporary storage of the device-wide scan and radix sort.
 struct SortTemp {
-  uint32_t* hist = nullptr;   // [256 * max_blocks]
+  uint32_t* hist = nullptr;   // radix_hist_elems(n): count matrix, or the single-pass status words
   uint32_t* scan_tmp = nullptr;
   size_t hist_cap = 0, scan_cap = 0;
+  uint32_t* err = nullptr;    // device word set to nonzero if a look-back gave up (optional)
 };
 
 // Exclusive prefix sum of n u32 values; out[n] receives the total (out has n + 1 slots).

@@ -4,7 +4,8 @@
 // writes the chunk sums, and the scan pass adds to each chunk the sum of the chunk sums
 // before it (summed by the CTA itself while there are at most 2048 chunks).
 //
-// Radix sort: per pass of at most 8 bits,
+// Radix sort: per pass of at most 8 bits (sorts of up to 2M keys run each pass as one
+// kernel, see k_radix_downsweep's look-back),
 //   1. upsweep  - each CTA histograms the digits of its 2048-key chunk into a
 //                 digit-major count matrix hist[d * nblocks + b];
 //   2. scan     - one exclusive scan of that matrix gives, for every (digit, chunk), the
@@ -15,6 +16,8 @@
 //                 base(d, chunk) + (keys with digit d in earlier warps) + rank in warp.
 // Keys keep their relative order within a digit (stable), so successive passes from
 // the least significant digit up sort by the whole bit range.
+#include <algorithm>
+
 #include "qgs_internal.cuh"
 
 namespace qgs {
@@ -186,16 +189,31 @@ constexpr size_t downsweep_smem() {
   return sizeof(K) * RS_CHUNK + (HAS_VAL ? sizeof(uint32_t) * RS_CHUNK : 0);
 }
 
-// Stable scatter of one 4096-key chunk. Keys are ranked per warp (match_any peers), the
-// per-warp digit counts are scanned across warps and digits, the chunk is reordered by
-// digit in shared memory, and then written out so that consecutive threads store
-// consecutive keys of a digit run (coalesced).
-template <typename K, bool HAS_VAL>
+// Look-back status words of the single-pass scatter: bits 30..31 = 0 (not yet published),
+// 1 (the chunk's own digit count) or 2 (the inclusive prefix over chunks 0..b), bits 0..29
+// the count. A chunk waits at most kLookbackSpins polls for a predecessor, then sets the
+// error word and continues (no hang; the result is then reported as a failure).
+constexpr uint32_t kStAgg = 1u << 30, kStInc = 2u << 30, kStVal = (1u << 30) - 1u;
+constexpr int kLookbackSpins = 1 << 22;
+constexpr int kLookbackMaxChunks = 1024;  // sorts of up to 2M keys use the single-pass scatter
+
+// Stable scatter of one 2048-key chunk. Keys are ranked per warp (lanes of one digit found
+// with one ballot per digit bit), the per-warp digit counts are scanned across warps and
+// digits, the chunk is reordered by digit in shared memory, and then written out so that
+// consecutive threads store consecutive keys of a digit run (coalesced). The chunk's
+// global digit offsets come either from the scanned count matrix `offs` (LOOKBACK false)
+// or, in a single pass (LOOKBACK true), from the whole array's digit counts `ghist` plus
+// the counts of the earlier chunks, found by decoupled look-back: chunks take their index
+// from a ticket, publish their own counts, then add up their predecessors' published
+// counts until one that published its inclusive prefix (a chunk only ever waits for
+// chunks with smaller tickets, which have already started and publish before waiting).
+template <typename K, bool HAS_VAL, bool LOOKBACK>
 __global__ void __launch_bounds__(BLOCK) k_radix_downsweep(const K* __restrict__ kin, K* __restrict__ kout,
                                                            const uint32_t* __restrict__ vin,
                                                            uint32_t* __restrict__ vout, int64_t n, int shift,
                                                            uint32_t mask, const uint32_t* __restrict__ offs,
-                                                           int nblocks) {
+                                                           int nblocks, const uint32_t* __restrict__ ghist,
+                                                           uint32_t* status, uint32_t* ticket, uint32_t* err) {
   extern __shared__ __align__(16) unsigned char dsm[];
   K* skeys = reinterpret_cast<K*>(dsm);
   uint32_t* svals = reinterpret_cast<uint32_t*>(skeys + RS_CHUNK);
@@ -203,8 +221,15 @@ __global__ void __launch_bounds__(BLOCK) k_radix_downsweep(const K* __restrict__
   __shared__ uint32_t boff[256];
   __shared__ uint32_t lstart[256];
   __shared__ uint32_t wsum[RS_WARPS];
+  __shared__ uint32_t s_chunk;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t cbase = (int64_t)blockIdx.x * RS_CHUNK;
+  int chunk = blockIdx.x;
+  if constexpr (LOOKBACK) {
+    if (threadIdx.x == 0) s_chunk = atomicAdd(ticket, 1u);
+    __syncthreads();
+    chunk = (int)s_chunk;
+  }
+  const int64_t cbase = (int64_t)chunk * RS_CHUNK;
   const int64_t wbase = cbase + (int64_t)warp * 32 * RS_ITEMS;
   const uint32_t lt = (1u << lane) - 1u;
   const int nbits = 32 - __clz(mask);
@@ -214,7 +239,12 @@ __global__ void __launch_bounds__(BLOCK) k_radix_downsweep(const K* __restrict__
   // every global load first (the chunk's keys and its digit offsets, independent and in
   // flight together), then the ranking below, whose barriers would otherwise serialise
   // each load's latency
-  const uint32_t my_off = threadIdx.x <= mask ? offs[(size_t)threadIdx.x * nblocks + blockIdx.x] : 0u;
+  uint32_t my_off = 0;
+  if constexpr (LOOKBACK) {
+    my_off = threadIdx.x <= mask ? ghist[threadIdx.x] : 0u;  // scanned into the global base below
+  } else {
+    my_off = threadIdx.x <= mask ? offs[(size_t)threadIdx.x * nblocks + blockIdx.x] : 0u;
+  }
 #pragma unroll
   for (int it = 0; it < RS_ITEMS; ++it) {
     const int64_t i = wbase + it * 32 + lane;
@@ -222,7 +252,7 @@ __global__ void __launch_bounds__(BLOCK) k_radix_downsweep(const K* __restrict__
     if (HAS_VAL) vv[it] = i < n ? vin[i] : 0u;
   }
   for (int e = threadIdx.x; e < RS_WARPS * 256; e += BLOCK) (&wh[0][0])[e] = 0;
-  if (threadIdx.x <= mask) boff[threadIdx.x] = my_off;
+  if (!LOOKBACK && threadIdx.x <= mask) boff[threadIdx.x] = my_off;
   __syncthreads();
 #pragma unroll
   for (int it = 0; it < RS_ITEMS; ++it) {
@@ -273,6 +303,49 @@ __global__ void __launch_bounds__(BLOCK) k_radix_downsweep(const K* __restrict__
       if (w < warp) base += wsum[w];
     lstart[d] = base + inc - tot;
   }
+  if constexpr (LOOKBACK) {
+    const int d = threadIdx.x;
+    const bool live = (uint32_t)d <= mask;
+    // publish this chunk's count of digit d (its inclusive prefix if it is the first)
+    if (live) atomicExch(status + (size_t)chunk * 256 + d, (chunk == 0 ? kStInc : kStAgg) | tot);
+    // the whole array's digit counts -> exclusive scan across digits (the digit's base)
+    uint32_t inc = my_off;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(FULL, inc, o);
+      if (lane >= o) inc += v;
+    }
+    __syncthreads();  // wsum is reused
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    uint32_t gbase = 0;
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w)
+      if (w < warp) gbase += wsum[w];
+    gbase += inc - my_off;
+    // look back over the earlier chunks' counts of digit d
+    uint32_t excl = 0;
+    if (live) {
+      for (int k = chunk - 1; k >= 0; --k) {
+        const volatile uint32_t* sw = status + (size_t)k * 256 + d;
+        uint32_t sv = *sw;
+        int spins = 0;
+        while ((sv & ~kStVal) == 0u && spins < kLookbackSpins) {
+          __nanosleep(32);
+          sv = *sw;
+          ++spins;
+        }
+        if ((sv & ~kStVal) == 0u) {  // gave up: report, do not hang
+          atomicOr(err, 1u);
+          break;
+        }
+        excl += sv & kStVal;
+        if (sv & kStInc) break;
+      }
+      if (chunk > 0) atomicExch(status + (size_t)chunk * 256 + d, kStInc | (excl + tot));
+      boff[d] = gbase + excl;
+    }
+  }
   __syncthreads();
 #pragma unroll
   for (int it = 0; it < RS_ITEMS; ++it) {
@@ -293,6 +366,31 @@ __global__ void __launch_bounds__(BLOCK) k_radix_downsweep(const K* __restrict__
   }
 }
 
+// Digit counts of every pass over the whole array, from one read of the keys.
+struct PassSpec {
+  int passes;
+  int shift[8];
+  uint32_t mask[8];
+};
+template <typename K>
+__global__ void __launch_bounds__(BLOCK) k_radix_hist_all(const K* __restrict__ keys, int64_t n, PassSpec ps,
+                                                          uint32_t* __restrict__ ghist) {
+  __shared__ uint32_t h[8][256];
+  for (int e = threadIdx.x; e < 8 * 256; e += BLOCK) (&h[0][0])[e] = 0u;
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x; i < n; i += (int64_t)gridDim.x * BLOCK) {
+    const K key = keys[i];
+#pragma unroll
+    for (int p = 0; p < 8; ++p)
+      if (p < ps.passes) atomicAdd(&h[p][digit_of(key, ps.shift[p], ps.mask[p])], 1u);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int p = 0; p < 8; ++p)
+    if (p < ps.passes && (uint32_t)threadIdx.x <= ps.mask[p] && h[p][threadIdx.x])
+      atomicAdd(&ghist[p * 256 + threadIdx.x], h[p][threadIdx.x]);
+}
+
 int scan_blocks(int64_t n) { return (int)((n + SCAN_CHUNK - 1) / SCAN_CHUNK); }
 
 template <typename K, bool HAS_VAL>
@@ -309,15 +407,57 @@ bool radix_sort_impl(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, int be
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-    *err = cudaFuncSetAttribute(k_radix_downsweep<K, HAS_VAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    *err = cudaFuncSetAttribute(k_radix_downsweep<K, HAS_VAL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem);
+    if (*err == cudaSuccess)
+      *err = cudaFuncSetAttribute(k_radix_downsweep<K, HAS_VAL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem);
     if (*err != cudaSuccess) return false;
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
-  int shift = begin_bit;
+  PassSpec ps{};
+  ps.passes = passes;
+  {
+    int shift = begin_bit;
+    for (int p = 0; p < passes; ++p) {
+      const int pb = (bits - (shift - begin_bit) + (passes - p) - 1) / (passes - p);  // spread bits evenly
+      ps.shift[p] = shift;
+      ps.mask[p] = (1u << pb) - 1u;
+      shift += pb;
+    }
+  }
+  // single-pass scatter with look-back: status words [passes][nblocks][256], the passes'
+  // digit counts [passes][256] and one ticket per pass, zeroed together
+  const size_t lb_words = (size_t)passes * nblocks * 256 + (size_t)passes * 256 + passes + 1;
+  // (for small sorts: its per-digit look-back walks grow with the chunks in flight, so large
+  // sorts keep the count-matrix passes)
+  if (nblocks <= kLookbackMaxChunks && passes <= 8 && lb_words <= tmp.hist_cap) {
+    uint32_t* status = tmp.hist;
+    uint32_t* ghist = status + (size_t)passes * nblocks * 256;
+    uint32_t* tickets = ghist + (size_t)passes * 256;
+    uint32_t* errw = tmp.err ? tmp.err : tickets + passes;  // a spare word when nobody reads the error
+    *err = cudaMemsetAsync(status, 0, lb_words * sizeof(uint32_t), st);
+    if (*err != cudaSuccess) return false;
+    k_radix_hist_all<K><<<(unsigned)std::min(nblocks, 1024), BLOCK, 0, st>>>(k0, n, ps, ghist);
+    ++launch_counter();
+    for (int p = 0; p < passes; ++p) {
+      K* kin = flipped ? k1 : k0;
+      K* kout = flipped ? k0 : k1;
+      uint32_t* vin = flipped ? v1 : v0;
+      uint32_t* vout = flipped ? v0 : v1;
+      k_radix_downsweep<K, HAS_VAL, true><<<nblocks, BLOCK, smem, st>>>(
+          kin, kout, vin, vout, n, ps.shift[p], ps.mask[p], nullptr, nblocks, ghist + (size_t)p * 256,
+          status + (size_t)p * nblocks * 256, tickets + p, errw);
+      ++launch_counter();
+      *err = cudaGetLastError();
+      if (*err != cudaSuccess) return flipped;
+      flipped = !flipped;
+    }
+    return flipped;
+  }
   for (int p = 0; p < passes; ++p) {
-    const int pb = (bits - (shift - begin_bit) + (passes - p) - 1) / (passes - p);  // spread bits evenly
-    const uint32_t mask = (1u << pb) - 1u;
+    const int shift = ps.shift[p];
+    const uint32_t mask = ps.mask[p];
     const int64_t m = (int64_t)(mask + 1) * nblocks;
     if ((size_t)m + 1 > tmp.hist_cap) {
       *err = cudaErrorInvalidValue;  // histogram buffer too small for this sort
@@ -331,13 +471,12 @@ bool radix_sort_impl(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, int be
     ++launch_counter();
     *err = scan_exclusive_u32(tmp.hist, tmp.hist, m, tmp.scan_tmp, tmp.scan_cap, st);
     if (*err != cudaSuccess) return flipped;
-    k_radix_downsweep<K, HAS_VAL><<<nblocks, BLOCK, smem, st>>>(kin, kout, vin, vout, n, shift, mask, tmp.hist,
-                                                                nblocks);
+    k_radix_downsweep<K, HAS_VAL, false><<<nblocks, BLOCK, smem, st>>>(kin, kout, vin, vout, n, shift, mask, tmp.hist,
+                                                                       nblocks, nullptr, nullptr, nullptr, nullptr);
     ++launch_counter();
     *err = cudaGetLastError();
     if (*err != cudaSuccess) return flipped;
     flipped = !flipped;
-    shift += pb;
   }
   return flipped;
 }
@@ -357,8 +496,10 @@ size_t scan_tmp_elems(int64_t n) {
 }
 
 size_t radix_hist_elems(int64_t n) {
+  // the single-pass scatter's status words, digit counts, tickets and a spare word for up
+  // to 8 passes
   const int64_t nblocks = (n + RS_CHUNK - 1) / RS_CHUNK;
-  return (size_t)256 * (size_t)(nblocks > 0 ? nblocks : 1) + 1;
+  return (size_t)8 * 256 * (size_t)(nblocks > 0 ? nblocks : 1) + 8 * 256 + 8 + 1;
 }
 
 cudaError_t scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, size_t tmp_cap,
