@@ -28,6 +28,13 @@
  *     All device work is enqueued on it. render_forward synchronises the stream once
  *     (to size the tile-instance buffers from the instance count); render_backward
  *     does not synchronise.
+ *   - The radix sorts wait for each other's chunks with bounded waits. A wait that runs
+ *     out (which should not happen on a healthy GPU) makes the frame's later kernels do
+ *     nothing, and render_forward has already returned by then: the failure is reported
+ *     as QGS_ECUDA by the first later call on the context that waits for the frame:
+ *     qgs_check_frame, render_backward, qgs_get_frame_stats, qgs_copy_binning,
+ *     qgs_copy_residue, or else the next render_forward / render_forward_batch. The
+ *     frame is then discarded (render_backward refuses it).
  *   - A context is not thread-safe; use one per host thread. The serving object
  *     (qgs_server) is thread-safe.
  *   - Images are planar float32: rgb[c*H*W + y*W + x], alpha[y*W + x], ...
@@ -230,6 +237,22 @@ qgs_status qgs_set_pair_counters(qgs_ctx* ctx, int32_t enable);
  * forward; does not change any result. Errors: EINVAL (ctx null or words < 0). */
 qgs_status qgs_set_tile_mask_capacity(qgs_ctx* ctx, int64_t words);
 
+/* Wait until the sorts of the last render_forward / render_forward_batch have run and
+ * report them: QGS_OK, or QGS_ECUDA when a look-back wait ran out (the frame's lists and
+ * images are invalid and the frame is discarded). Returns QGS_OK at once when the frame
+ * has already been checked. Errors: EINVAL, ECUDA. */
+qgs_status qgs_check_frame(qgs_ctx* ctx);
+
+/* Test hook for the failure path of the sorts' bounded waits (the paper has no
+ * counterpart). With spins > 0, the next forward's first radix sort that runs its passes
+ * as single kernels with decoupled look-back (sorts of 2,049 to 2M keys: the depth sort
+ * of that many visible primitives) withholds chunk 0 of its first pass, so the chunks
+ * after it wait for digit counts that are never published; each wait gives up after
+ * `spins` polls (about a microsecond each), the sort's failure word is set, and the
+ * frame fails as described in the conventions above. One-shot: the hook is consumed by
+ * the next forward. spins <= 0 clears it. Errors: EINVAL. */
+qgs_status qgs_debug_withhold_sort_chunk(qgs_ctx* ctx, int32_t spins);
+
 /* Copy the last forward's tile binning to HOST memory, for inspection and tests:
  * keys[i] = (tile << 32) | float bits of the primitive's view depth, vals[i] = primitive
  * index, in sorted order (cap entries at most); ranges[2*t], ranges[2*t+1] = [start, end)
@@ -247,14 +270,16 @@ qgs_status qgs_copy_residue(qgs_ctx* ctx, float* T_final, uint32_t* n_contrib);
  * exists for callers that cannot allocate device memory at render time, e.g. a host
  * process whose memory manager takes the GPU's memory in one pool at start-up and
  * refuses other allocations, or a real-time loop that forbids cudaMalloc/cudaFree after
- * warm-up because they can block and fragment memory. It computes the same images as
- * render_forward with the default qgs_config (same kernels), but takes every work
- * buffer from one statically sized device array (about 24 MB) that each GPU loading the
- * library holds until the process exits; it calls no cudaMalloc, cudaFree or allocating
- * library routine, and needs no context.
+ * warm-up because they can block and fragment memory. It computes the same planes as
+ * render_forward with the default qgs_config, bit for bit: the same kernels and the same
+ * tile lists (the tile test against the parallelogram and the conic), with only the
+ * intermediate layout changed (64-bit instances, primitive-indexed state, no tile-mask
+ * store). Every work buffer comes from one statically sized device array (about 27 MB)
+ * that each GPU loading the library holds until the process exits; it calls no
+ * cudaMalloc, cudaFree or allocating library routine, and needs no context.
  *   Limits: n <= 32768 primitives, W*H <= 262144 pixels, at most 4096 16x16 tiles, and at
  *   most 1,048,576 (tile, primitive) instances in the frame; beyond them it returns
- *   QGS_ECAPACITY (the instance count is known only after preprocessing, so that case is
+ *   QGS_ECAPACITY (the instance count is known only after the tile test, so that case is
  *   reported after a synchronisation of `stream`, with `out` unspecified).
  *   The first call on a device looks up the array's device address (cudaGetSymbolAddress)
  *   with that device current; make that first call before any stream capture.
@@ -262,8 +287,10 @@ qgs_status qgs_copy_residue(qgs_ctx* ctx, float* T_final, uint32_t* n_contrib);
  *   clears what must start at zero): calls whose GPU work overlaps (concurrent streams,
  *   host threads) race and corrupt each other's results; serialise them.
  *   Scene/camera/output pointers follow the conventions above (base planes only: the
- *   extra planes must be NULL); the call synchronises `stream` once. Errors: EINVAL,
- *   ECAPACITY, ECUDA. No per-call residue is kept, so render_backward cannot follow it. */
+ *   extra planes must be NULL); the call synchronises `stream` twice (for the instance
+ *   count, and at the end to read its sorts' failure word, so a look-back wait that ran
+ *   out is reported by this call as QGS_ECUDA). Errors: EINVAL, ECAPACITY, ECUDA. No
+ *   per-call residue is kept, so render_backward cannot follow it. */
 qgs_status render_forward_noalloc(const qgs_scene* scene, const qgs_camera* cam, const qgs_image* out,
                                   qgs_stream stream);
 

@@ -651,13 +651,20 @@ def gaussian_curvature(x, y, a, b):
     return 4.0 * a * b / (S * S)
 
 
-def quadratic_roots(A, B, C):
+def quadratic_roots(A, B, C, flip_real=None, d_shift=None):
     """Both real roots (t1 <= t2) of A t^2 + B t + C = 0 and whether they exist.
     q = -(B + sgn(B) sqrt(D)) / 2 with sgn(0) = +1; the roots are C/q and q/A, each
-    missing when its denominator is zero (A = 0 leaves the single root -C/B)."""
+    missing when its denominator is zero (A = 0 leaves the single root -C/B).
+    Bracketing (decisions taken the other way, see bracket_pixels): flip_real inverts the
+    decision D >= 0 (a negative D then counts as 0, the double root); d_shift is added to
+    D before anything else."""
     D = B * B - 4.0 * A * C
+    if d_shift is not None:
+        D = D + d_shift
     real = D >= 0
-    Ds = torch.where(real, D, torch.zeros_like(D))
+    if flip_real is not None:
+        real = real ^ flip_real
+    Ds = torch.where(real & (D > 0), D, torch.zeros_like(D))
     sgn = torch.where(B >= 0, torch.ones_like(B), -torch.ones_like(B))
     q = -0.5 * (B + sgn * torch.sqrt(Ds))
     ok1 = real & (q != 0)
@@ -713,12 +720,17 @@ def sh_basis(d: torch.Tensor) -> torch.Tensor:
 
 
 # =========================================================================== params
+def bf16_to_f64(bits) -> np.ndarray:
+    """Values of bfloat16 bit patterns: a bfloat16 is the upper half of an IEEE binary32,
+    so the pattern shifted up by 16 bits is that binary32 exactly (widened to FP64)."""
+    b = np.asarray(bits, np.uint16).astype(np.uint32) << np.uint32(16)
+    return b.view(np.float32).astype(np.float64)
+
+
 class Params:
     """FP64 leaf tensors of a scene (SH decoded from its bfloat16 storage)."""
 
     def __init__(self, scene, requires_grad=False):
-        from paper_2411_16392_gb300.scenes import bf16_bits_to_f32
-
         def t(x):
             return torch.tensor(np.asarray(x, np.float64), dtype=F64, requires_grad=requires_grad)
 
@@ -727,7 +739,7 @@ class Params:
         self.scale = t(scene.scale)
         self.curv = t(scene.curv)
         self.opacity = t(scene.opacity)
-        self.sh = t(bf16_bits_to_f32(scene.sh).reshape(-1, 16, 3))
+        self.sh = t(bf16_to_f64(scene.sh).reshape(-1, 16, 3))
 
     def leaves(self):
         return dict(mean=self.mean, quat=self.quat, scale=self.scale, curv=self.curv,
@@ -746,13 +758,32 @@ class CamF64:
 
 
 # =========================================================================== per-pair evaluation
+DECISIONS = ("D", "near1", "near2", "in1", "in2", "amin", "amax")
+
+
 def _eval_pairs(prm: Params, cam: CamF64, idx: torch.Tensor, px: torch.Tensor, py: torch.Tensor,
-                density: str = "geodesic"):
+                density: str = "geodesic", flip: dict | None = None, d_shift=None):
     """Evaluate every (pixel, primitive) pair of a pixel set [P] and a primitive list [L].
     Returns per-pair tensors [P, L]: alpha (0 where no contribution), validity, depth t,
     colour [P, L, 3] (broadcast), camera-space unit normal [P, L, 3], Gaussian curvature
-    at the hit and decision margins. density: "geodesic" (the paper's) or "euclid"."""
+    at the hit and decision margins. density: "geodesic" (the paper's) or "euclid".
+
+    The pair's discrete decisions, each with its relative margin (how far the deciding
+    quantity is from its threshold; infinite where the decision cannot change the pair's
+    contribution) in `margins`:
+      D      real roots, D >= 0 (counted only where the double root lies on the support);
+      near1  the near root is in front of the near plane (t > near);
+      near2  the same for the far root;
+      in1    the near root's hit is within 3 sigma(theta) (l <= 3 sigma, Sec. 3.2.1);
+      in2    the same for the far root (counted only where the near root is not taken);
+      amin   alpha >= 1/255 (blended at all);
+      amax   o G < 0.99 (alpha not clamped: the same value either way, another derivative).
+    `flip` (bracketing, see bracket_pixels) maps decision names to bool tensors
+    broadcastable to [P, L] that take those decisions the other way; `d_shift` [P, L] is
+    added to the discriminant (its value in units of B0^2 + 4|A C0|, the scale of its
+    rounding, below)."""
     weight_fn = {"geodesic": geodesic_gaussian, "euclid": euclid_gaussian}[density]
+    fl = flip or {}
     mu = prm.mean[idx]
     R = quat_to_rot(prm.quat[idx])                  # [L,3,3] columns = local axes (world)
     su, sv = prm.scale[idx].unbind(-1)
@@ -770,16 +801,19 @@ def _eval_pairs(prm: Params, cam: CamF64, idx: torch.Tensor, px: torch.Tensor, p
     A_ = a * dx * dx + b * dy * dy
     B_ = 2.0 * (a * ox * dx + b * oy * dy) - dz
     C_ = (a * ox * ox + b * oy * oy - oz).expand_as(A_)
-    t1, t2, e1, e2, _ = quadratic_roots(A_, B_, C_)
-    # Margin of the decision D >= 0, measured in a translation-invariant way: D is the
-    # same for the ray re-parametrised as s = t - t0 around the depth t0 of the centre,
-    # where B and C are of the size of the primitive instead of the camera distance.
+    # Scale of the discriminant's rounding: D is the same for the ray re-parametrised as
+    # s = t - t0 around the depth t0 of the centre, where B and C are of the size of the
+    # primitive instead of the camera distance.
     with torch.no_grad():
         t0 = (mu @ cam.R[2] + cam.t[2])[None, :]
-        D_ = B_ * B_ - 4.0 * A_ * C_
         B0 = B_ + 2.0 * A_ * t0
         C0 = (A_ * t0 + B_) * t0 + C_
-        m_D = D_.abs() / (B0 * B0 + 4.0 * (A_ * C0).abs()).clamp_min(1e-300)
+        d_scale = (B0 * B0 + 4.0 * (A_ * C0).abs()).clamp_min(1e-300)
+    shift = None if d_shift is None else d_shift * d_scale
+    t1, t2, e1, e2, _ = quadratic_roots(A_, B_, C_, fl.get("D"), shift)
+    with torch.no_grad():
+        D_ = B_ * B_ - 4.0 * A_ * C_ + (0.0 if shift is None else shift)
+        m_D = D_.abs() / d_scale
         # Conditioning of a hit's derivative: at a root, d f / d t = +-sqrt(D), so the
         # derivative of the root (and everything downstream of it) scales like 1/sqrt(D);
         # relative input perturbations e move it by about e * B^2 / D.
@@ -793,23 +827,31 @@ def _eval_pairs(prm: Params, cam: CamF64, idx: torch.Tensor, px: torch.Tensor, p
         m_D = torch.where((A_ != 0) & (ev <= 10.0), m_D, torch.full_like(m_D, np.inf))
 
     near = cam.near
-    f1 = e1 & (t1 > near)
-    f2 = e2 & (t2 > near)
-    m_near = torch.minimum(torch.where(e1, (t1 - near).abs() / near, torch.full_like(t1, np.inf)),
-                           torch.where(e2, (t2 - near).abs() / near, torch.full_like(t2, np.inf))).detach()
 
-    def at(t, ok):
+    def front(t, e, name):
+        ok = t > near
+        if name in fl:
+            ok = ok ^ fl[name]
+        m = torch.where(e, (t - near).abs() / near, torch.full_like(t, np.inf)).detach()
+        return e & ok, m
+
+    f1, m_near1 = front(t1, e1, "near1")
+    f2, m_near2 = front(t2, e2, "near2")
+
+    def at(t, ok, name):
         ts = torch.where(ok, t, torch.zeros_like(t))
         x = ox + ts * dx
         y = oy + ts * dy
         G, l, sig = weight_fn(x, y, a, b, su, sv)
-        inside = ok & (l <= CUTOFF * sig)
+        within = l <= CUTOFF * sig
+        if name in fl:
+            within = within ^ fl[name]
         margin = torch.where(ok, (l - CUTOFF * sig).abs() / (CUTOFF * sig), torch.full_like(l, np.inf))
-        return ts, x, y, G, inside, margin.detach()
+        return ts, x, y, G, ok & within, margin.detach()
 
     # candidates in increasing t: the near root first, then the far one (Sec. 3.2.1)
-    tn, xn, yn, Gn, in_n, m_n = at(t1, f1)
-    tf, xf, yf, Gf, in_f, m_f = at(t2, f2)
+    tn, xn, yn, Gn, in_n, m_in1 = at(t1, f1, "in1")
+    tf, xf, yf, Gf, in_f, m_in2 = at(t2, f2, "in2")
     pick_n = in_n
     pick_f = ~in_n & in_f
     hit = pick_n | pick_f
@@ -817,11 +859,17 @@ def _eval_pairs(prm: Params, cam: CamF64, idx: torch.Tensor, px: torch.Tensor, p
     x = torch.where(pick_n, xn, xf)
     y = torch.where(pick_n, yn, yf)
     G = torch.where(pick_n, Gn, torch.where(pick_f, Gf, torch.zeros_like(Gf)))
-    m_sig = torch.minimum(m_n, torch.where(in_n, torch.full_like(m_f, np.inf), m_f))
+    m_in2 = torch.where(in_n, torch.full_like(m_in2, np.inf), m_in2)
 
     oG = o * G
-    alpha = torch.clamp(oG, max=ALPHA_MAX)
-    valid = hit & (alpha >= ALPHA_MIN)
+    clamped = oG > ALPHA_MAX
+    if "amax" in fl:
+        clamped = clamped ^ fl["amax"]
+    alpha = torch.where(clamped, torch.full_like(oG, ALPHA_MAX), oG)
+    blend = alpha >= ALPHA_MIN
+    if "amin" in fl:
+        blend = blend ^ fl["amin"]
+    valid = hit & blend
     alpha = torch.where(valid, alpha, torch.zeros_like(alpha))
     m_amin = torch.where(hit, (oG - ALPHA_MIN).abs() / ALPHA_MIN, torch.full_like(oG, np.inf)).detach()
     m_amax = torch.where(valid, (oG - ALPHA_MAX).abs() / ALPHA_MAX, torch.full_like(oG, np.inf)).detach()
@@ -840,11 +888,14 @@ def _eval_pairs(prm: Params, cam: CamF64, idx: torch.Tensor, px: torch.Tensor, p
     dv = dv / torch.linalg.vector_norm(dv, dim=-1, keepdim=True)
     rgb = torch.clamp((sh_basis(dv)[:, :, None] * prm.sh[idx]).sum(1) + 0.5, min=0.0)   # [L,3]
 
-    margin = torch.minimum(torch.minimum(m_D, m_near),
-                           torch.minimum(m_sig, torch.minimum(m_amin, m_amax)))
+    margins = dict(D=m_D, near1=m_near1, near2=m_near2, in1=m_in1, in2=m_in2, amin=m_amin, amax=m_amax)
+    margin = m_D
+    for k in DECISIONS[1:]:
+        margin = torch.minimum(margin, margins[k])
     cond = torch.where(valid, m_cond, torch.full_like(m_cond, np.inf))
     K = gaussian_curvature(x, y, a, b)
-    return dict(alpha=alpha, valid=valid, hit=hit, t=t, rgb=rgb, normal=n_c, curvature=K, margin=margin, cond=cond)
+    return dict(alpha=alpha, valid=valid, hit=hit, t=t, rgb=rgb, normal=n_c, curvature=K, margin=margin,
+                cond=cond, margins=margins)
 
 
 MEDIAN_T = 0.5   # median depth: the largest hit depth among blended pairs with T_i > 0.5

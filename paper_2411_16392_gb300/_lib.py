@@ -77,6 +77,8 @@ EXPORTS = [
     ("qgs_get_frame_stats", C.c_int, [_P, C.POINTER(qgs_frame_stats)]),
     ("qgs_copy_binning", C.c_int, [_P, _P, _P, C.c_int64, _P, _P, C.POINTER(C.c_int64)]),
     ("qgs_copy_residue", C.c_int, [_P, _P, _P]),
+    ("qgs_check_frame", C.c_int, [_P]),
+    ("qgs_debug_withhold_sort_chunk", C.c_int, [_P, C.c_int32]),
     ("qgs_set_profiling", C.c_int, [_P, C.c_int32]),
     ("qgs_set_tile_mask_capacity", C.c_int, [_P, C.c_int64]),
     ("qgs_set_pair_counters", C.c_int, [_P, C.c_int32]),

@@ -56,8 +56,14 @@ struct DevBuf {
   }
 };
 
+// Kernels that read a radix sort's output (an index permutation or sorted tile keys)
+// return at once when the sort's error word is set: an abandoned sort leaves indices that
+// are not a permutation, and using them could read or write out of range.
+__device__ __forceinline__ bool sort_failed(const uint32_t* err) { return err && *(volatile const uint32_t*)err; }
+
 __global__ void k_gather_u32(int64_t n, const uint32_t* __restrict__ idx, const uint32_t* __restrict__ src,
-                             uint32_t* __restrict__ dst) {
+                             uint32_t* __restrict__ dst, const uint32_t* err) {
+  if (sort_failed(err)) return;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) dst[i] = src[idx[i]];
 }
@@ -70,7 +76,8 @@ __global__ void k_emit(int64_t n, const uint32_t* __restrict__ sidx, const uint3
                        const short4* __restrict__ rect, const TileSlab* __restrict__ tslab, int W, int H,
                        const uint32_t* __restrict__ offs, const uint32_t* __restrict__ zkey, int tiles_x,
                        uint64_t* __restrict__ keys, uint32_t* __restrict__ vals, const uint32_t* __restrict__ tbits,
-                       const uint32_t* __restrict__ tbits_off) {
+                       const uint32_t* __restrict__ tbits_off, const uint32_t* err) {
+  if (sort_failed(err)) return;
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t pid = 0, c = 0, off = 0, lowv = 0;
   short4 r = make_short4(0, 0, 0, 0);
@@ -112,7 +119,9 @@ __global__ void k_emit_views(int64_t n, const uint32_t* __restrict__ sidx, const
                              const short4* __restrict__ rect, const uint32_t* __restrict__ offs, uint32_t n_per_view,
                              const int2* __restrict__ vt, const CamParams* __restrict__ cps,
                              const TileSlab* __restrict__ tslab, const uint32_t* __restrict__ tbits,
-                             const uint32_t* __restrict__ tbits_off, uint64_t* __restrict__ keys) {
+                             const uint32_t* __restrict__ tbits_off, uint64_t* __restrict__ keys,
+                             const uint32_t* err) {
+  if (sort_failed(err)) return;
   const int lane = threadIdx.x & 31;
   const int64_t j0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kEmitPerWarp;
   const int64_t j = j0 + lane;
@@ -162,7 +171,8 @@ __global__ void k_compact(int64_t n, const uint32_t* __restrict__ count, const u
 // gathered into that order (8 threads per 128-byte record).
 __global__ void k_gather_state(int64_t V, const uint32_t* __restrict__ sidx, const PrimState* __restrict__ state,
                                const uint32_t* __restrict__ count, PrimState* __restrict__ dstate,
-                               uint32_t* __restrict__ cnt_sorted) {
+                               uint32_t* __restrict__ cnt_sorted, const uint32_t* err) {
+  if (sort_failed(err)) return;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= V * 8) return;
   const int64_t r = e >> 3;
@@ -181,7 +191,9 @@ template <typename K>
 __global__ void k_emit_packed(int64_t V, const uint32_t* __restrict__ sidx, const uint32_t* __restrict__ cnt_sorted,
                               const short4* __restrict__ rect, const TileSlab* __restrict__ tslab, int W, int H,
                               const uint32_t* __restrict__ offs, int tiles_x, int rb, K* __restrict__ keys,
-                              const uint32_t* __restrict__ tbits, const uint32_t* __restrict__ tbits_off) {
+                              const uint32_t* __restrict__ tbits, const uint32_t* __restrict__ tbits_off,
+                              const uint32_t* err) {
+  if (sort_failed(err)) return;
   const int lane = threadIdx.x & 31;
   const int64_t r0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kEmitPerWarp;
   const int64_t r = r0 + lane;
@@ -214,7 +226,9 @@ __global__ void k_emit_packed(int64_t V, const uint32_t* __restrict__ sidx, cons
 
 // The same for u32 keys, four per thread (one vector load; the neighbours of the four
 // are the thread's own keys except at its ends).
-__global__ void k_tile_ranges_x4(int64_t n, const uint32_t* __restrict__ keys, int shift, uint2* __restrict__ ranges) {
+__global__ void k_tile_ranges_x4(int64_t n, const uint32_t* __restrict__ keys, int shift, uint2* __restrict__ ranges,
+                                 const uint32_t* err) {
+  if (sort_failed(err)) return;
   const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
   if (i0 >= n) return;
   uint32_t k[6];  // k[0] = keys[i0 - 1], k[1..4] = keys[i0 .. i0 + 3], k[5] = keys[i0 + 4]
@@ -241,7 +255,9 @@ unsigned emit_blocks(int64_t V) { return (unsigned)((V + 8 * kEmitPerWarp - 1) /
 
 // [start, end) of every tile's run in keys sorted by tile = key >> shift.
 template <typename K>
-__global__ void k_tile_ranges_t(int64_t n, const K* __restrict__ keys, int shift, uint2* __restrict__ ranges) {
+__global__ void k_tile_ranges_t(int64_t n, const K* __restrict__ keys, int shift, uint2* __restrict__ ranges,
+                                const uint32_t* err) {
+  if (sort_failed(err)) return;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint32_t t = (uint32_t)(keys[i] >> shift);
@@ -263,7 +279,9 @@ __global__ void k_debug_packed(int64_t n, const K* __restrict__ inst, int rb, co
   vals[i] = sidx[r];
 }
 
-__global__ void k_tile_ranges(int64_t n, const uint64_t* __restrict__ keys, uint2* __restrict__ ranges) {
+__global__ void k_tile_ranges(int64_t n, const uint64_t* __restrict__ keys, uint2* __restrict__ ranges,
+                              const uint32_t* err) {
+  if (sort_failed(err)) return;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint32_t t = (uint32_t)(keys[i] >> 32);
@@ -357,8 +375,13 @@ struct qgs_ctx {
   DevBuf<uint32_t> hist, scan_tmp;
   DevBuf<RasterStats> stats;
   DevBuf<uint32_t> dcount;      // [0] visible primitives, [1] instances, [2] tile-mask words,
-                                // [3] radix look-back failure (kept across calls)
-  uint32_t* h_total = nullptr;  // pinned: the frame's counters read back
+                                // [3] radix look-back failure (kept until reported)
+  uint32_t* h_total = nullptr;  // pinned: [0..3] the frame's counters read back, [4] the
+                                // look-back failure word read back after the frame's sorts
+  cudaEvent_t sorts_done = nullptr;  // recorded after that read-back
+  bool sorts_pending = false;        // the last forward's sort status has not been checked
+  int test_withhold = 0;             // test hook: chunks the next forward's first sort withholds
+  int test_spins = kLookbackSpins;   // poll limit of the look-back waits
   int64_t n_visible = 0;
   const uint32_t* vis_list = nullptr;
   // last frame
@@ -473,6 +496,53 @@ int bits_for(int64_t v) {
   return b;
 }
 
+// Sort temporaries of a forward: the context's buffers, its failure word and poll limit,
+// and the test hook (consumed by the first sort that reads it).
+SortTemp sort_temp(qgs_ctx* ctx) {
+  SortTemp tmp;
+  tmp.hist = ctx->hist.p;
+  tmp.hist_cap = ctx->hist.cap;
+  tmp.scan_tmp = ctx->scan_tmp.p;
+  tmp.scan_cap = ctx->scan_tmp.cap;
+  tmp.err = ctx->dcount.p + 3;
+  tmp.spins = ctx->test_spins;
+  tmp.withhold_chunks = ctx->test_withhold;
+  ctx->test_withhold = 0;
+  ctx->test_spins = kLookbackSpins;
+  return tmp;
+}
+
+// After the frame's last sort: read its failure word back and mark the point.
+qgs_status enqueue_sort_check(qgs_ctx* ctx, cudaStream_t st) {
+  QGS_CU(cudaMemcpyAsync(ctx->h_total + 4, ctx->dcount.p + 3, sizeof(uint32_t), cudaMemcpyDeviceToHost, st),
+         "sort status");
+  QGS_CU(cudaEventRecord(ctx->sorts_done, st), "event");
+  ctx->sorts_pending = true;
+  return QGS_OK;
+}
+
+// Wait for the last forward's sorts and report a look-back wait that ran out: the frame is
+// then discarded (its lists and images are invalid) and the failure word cleared.
+qgs_status check_sorts(qgs_ctx* ctx) {
+  if (!ctx->sorts_pending) return QGS_OK;
+  ctx->sorts_pending = false;
+  const cudaError_t e = cudaEventSynchronize(ctx->sorts_done);
+  if (e != cudaSuccess) {
+    ctx->have_frame = false;
+    return cuda_fail(ctx, e, "waiting for the frame's sorts");
+  }
+  if (ctx->h_total[4]) {
+    ctx->h_total[4] = 0;
+    ctx->have_frame = false;
+    cudaMemsetAsync(ctx->dcount.p + 3, 0, sizeof(uint32_t), ctx->last_stream);
+    cudaStreamSynchronize(ctx->last_stream);
+    return fail(ctx, QGS_ECUDA,
+                "a radix sort pass of the last forward gave up waiting for an earlier chunk's digit counts; "
+                "the frame's tile lists and images are invalid");
+  }
+  return QGS_OK;
+}
+
 }  // namespace
 
 namespace qgs {
@@ -512,12 +582,14 @@ qgs_status qgs_create(qgs_ctx** out, const qgs_config* cfg, int32_t device) {
     delete c;
     return QGS_ECUDA;
   }
-  if (cudaHostAlloc((void**)&c->h_total, 16, cudaHostAllocDefault) != cudaSuccess) {
+  if (cudaHostAlloc((void**)&c->h_total, 32, cudaHostAllocDefault) != cudaSuccess) {
     delete c;
     return QGS_ENOMEM;
   }
+  memset(c->h_total, 0, 32);
   if (c->stats.reserve(1) != cudaSuccess || c->dcount.reserve(4) != cudaSuccess ||
-      cudaMemset(c->dcount.p, 0, 4 * sizeof(uint32_t)) != cudaSuccess) {
+      cudaMemset(c->dcount.p, 0, 4 * sizeof(uint32_t)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->sorts_done, cudaEventDisableTiming) != cudaSuccess) {
     cudaFreeHost(c->h_total);
     delete c;
     return QGS_ENOMEM;
@@ -547,6 +619,7 @@ void qgs_destroy(qgs_ctx* c) {
   if (c->h_vdesc) cudaFreeHost(c->h_vdesc);
   if (c->vdesc_done) cudaEventDestroy(c->vdesc_done);
   if (c->totals_ready) cudaEventDestroy(c->totals_ready);
+  if (c->sorts_done) cudaEventDestroy(c->sorts_done);
   if (c->h_total) cudaFreeHost(c->h_total);
   for (int i = 0; i < 10; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -568,6 +641,8 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   if (!out->rgb || !out->alpha || !out->depth || !out->normal) return fail(ctx, QGS_EINVAL, "output plane is NULL");
   cudaStream_t st = (cudaStream_t)stream;
   QGS_CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+  s = check_sorts(ctx);  // an unreported failure of the previous frame
+  if (s != QGS_OK) return s;
   ctx->have_frame = false;
   const int64_t N = scene->n;
   CamParams cp;
@@ -605,12 +680,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   if (stp) QGS_CU(ctx->xres.reserve((size_t)P * 8), "alloc output residue");
   QGS_CU(ctx->hist.reserve(radix_hist_elems((int64_t)n1)), "alloc hist");
   QGS_CU(ctx->scan_tmp.reserve(scan_tmp_elems((int64_t)radix_hist_elems((int64_t)n1) + (int64_t)n1)), "alloc scan");
-  SortTemp tmp;
-  tmp.hist = ctx->hist.p;
-  tmp.hist_cap = ctx->hist.cap;
-  tmp.scan_tmp = ctx->scan_tmp.p;
-  tmp.scan_cap = ctx->scan_tmp.cap;
-  tmp.err = ctx->dcount.p + 3;
+  SortTemp tmp = sort_temp(ctx);
 
   const int64_t launches0 = launch_counter();
   ctx->have_fwd_times = false;
@@ -671,7 +741,6 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   tmp.hist_cap = ctx->hist.cap;
   tmp.scan_tmp = ctx->scan_tmp.p;
   tmp.scan_cap = ctx->scan_tmp.cap;
-  tmp.err = ctx->dcount.p + 3;
 
   const int tb = bits_for(ntiles);
   cudaError_t e = cudaSuccess;
@@ -686,7 +755,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
     ctx->vis_list = sidx;
     if (V > 0) {
       k_gather_state<<<nblk(V * 8), 256, 0, st>>>(V, sidx, ctx->state.p, ctx->count.p, ctx->dstate.p,
-                                                  ctx->cnt_sorted.p);
+                                                  ctx->cnt_sorted.p, tmp.err);
       ++launch_counter();
       QGS_CU(cudaGetLastError(), "gather state");
     }
@@ -702,7 +771,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
         uint32_t* k1 = reinterpret_cast<uint32_t*>(ctx->inst2.p);
         k_emit_packed<uint32_t><<<emit_blocks(V), 256, 0, st>>>(V, sidx, ctx->cnt_sorted.p, ctx->rect.p, ctx->tslab.p,
                                                          cam->W, cam->H, ctx->offs.p, cp.tiles_x, rb, k0,
-                                                         tb_on ? ctx->tbits.p : nullptr, ctx->tbits_off.p);
+                                                         tb_on ? ctx->tbits.p : nullptr, ctx->tbits_off.p, tmp.err);
         ++launch_counter();
         QGS_CU(cudaGetLastError(), "emit");
         mark(ctx, 4, st);
@@ -712,7 +781,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
       } else {
         k_emit_packed<uint64_t><<<emit_blocks(V), 256, 0, st>>>(V, sidx, ctx->cnt_sorted.p, ctx->rect.p, ctx->tslab.p,
                                                          cam->W, cam->H, ctx->offs.p, cp.tiles_x, 32, ctx->inst.p,
-                                                         tb_on ? ctx->tbits.p : nullptr, ctx->tbits_off.p);
+                                                         tb_on ? ctx->tbits.p : nullptr, ctx->tbits_off.p, tmp.err);
         ++launch_counter();
         QGS_CU(cudaGetLastError(), "emit");
         mark(ctx, 4, st);
@@ -743,7 +812,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
       else
         k_emit<<<nblk(N), 256, 0, st>>>(N, nullptr, ctx->count.p, ctx->rect.p, ctx->tslab.p, cam->W, cam->H,
                                         ctx->offs.p, ctx->zkey.p, cp.tiles_x, ctx->inst.p, ctx->vals.p,
-                                        tb_on ? ctx->tbits.p : nullptr, ctx->tbits_off.p);
+                                        tb_on ? ctx->tbits.p : nullptr, ctx->tbits_off.p, nullptr);
       ++launch_counter();
       QGS_CU(cudaGetLastError(), "emit");
       mark(ctx, 4, st);
@@ -767,10 +836,10 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   if (I > 0) {
     if (ctx->packed32)
       k_tile_ranges_x4<<<nblk((I + 3) / 4), 256, 0, st>>>(I, reinterpret_cast<const uint32_t*>(sorted), shift,
-                                                           ctx->ranges.p);
+                                                           ctx->ranges.p, tmp.err);
     else
       k_tile_ranges_t<uint64_t><<<nblk(I), 256, 0, st>>>(I, reinterpret_cast<const uint64_t*>(sorted), shift,
-                                                         ctx->ranges.p);
+                                                         ctx->ranges.p, tmp.err);
     ++launch_counter();
     QGS_CU(cudaGetLastError(), "ranges");
   }
@@ -778,6 +847,8 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   k_tile_schedule<<<1, 1024, 0, st>>>((int)ntiles, ctx->ranges.p, ctx->torder.p);
   ++launch_counter();
   QGS_CU(cudaGetLastError(), "tile schedule");
+  s = enqueue_sort_check(ctx, st);
+  if (s != QGS_OK) return s;
   ctx->tile_order = ctx->torder.p;
   QGS_CU(cudaMemsetAsync(ctx->stats.p, 0, sizeof(RasterStats), st), "memset stats");
   mark(ctx, 5, st);
@@ -852,6 +923,8 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
   }
   cudaStream_t st = (cudaStream_t)stream;
   QGS_CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+  s = check_sorts(ctx);  // an unreported failure of the previous frame
+  if (s != QGS_OK) return s;
   ctx->have_frame = false;
   ctx->have_resid = false;
   ctx->have_stats = false;
@@ -921,12 +994,7 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
   QGS_CU(ctx->torder.reserve((size_t)T_all), "alloc tile order");
   QGS_CU(ctx->hist.reserve(radix_hist_elems((int64_t)n1)), "alloc hist");
   QGS_CU(ctx->scan_tmp.reserve(scan_tmp_elems((int64_t)radix_hist_elems((int64_t)n1) + (int64_t)n1)), "alloc scan");
-  SortTemp tmp;
-  tmp.hist = ctx->hist.p;
-  tmp.hist_cap = ctx->hist.cap;
-  tmp.scan_tmp = ctx->scan_tmp.p;
-  tmp.scan_cap = ctx->scan_tmp.cap;
-  tmp.err = ctx->dcount.p + 3;
+  SortTemp tmp = sort_temp(ctx);
 
   const int64_t launches0 = launch_counter();
   QGS_CU(cudaMemcpyAsync(ctx->vdesc.p, ctx->h_vdesc, vbytes, cudaMemcpyHostToDevice, st), "upload views");
@@ -956,7 +1024,7 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
   QGS_CU(e, "depth sort");
   const uint32_t* sidx = fl0 ? ctx->idx2.p : ctx->idx.p;
   if (VN > 0) {
-    k_gather_u32<<<nblk(VN), 256, 0, st>>>(VN, sidx, ctx->count.p, ctx->cnt_sorted.p);
+    k_gather_u32<<<nblk(VN), 256, 0, st>>>(VN, sidx, ctx->count.p, ctx->cnt_sorted.p, tmp.err);
     ++launch_counter();
     QGS_CU(cudaGetLastError(), "gather");
   }
@@ -980,13 +1048,12 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
   tmp.hist_cap = ctx->hist.cap;
   tmp.scan_tmp = ctx->scan_tmp.p;
   tmp.scan_cap = ctx->scan_tmp.cap;
-  tmp.err = ctx->dcount.p + 3;
 
   const uint64_t* sorted = ctx->inst.p;
   if (VN > 0 && I > 0) {
     k_emit_views<<<emit_blocks(VN), 256, 0, st>>>(VN, sidx, ctx->count.p, ctx->rect.p, ctx->offs.p, (uint32_t)N,
                                                   d_vt, d_cp, ctx->tslab.p, tb_on ? ctx->tbits.p : nullptr,
-                                                  ctx->tbits_off.p, ctx->inst.p);
+                                                  ctx->tbits_off.p, ctx->inst.p, tmp.err);
     ++launch_counter();
     QGS_CU(cudaGetLastError(), "emit");
     const bool fl = radix_sort_u64_keys(ctx->inst.p, ctx->inst2.p, I, 32, 32 + bits_for(T_all), tmp, st, &e);
@@ -996,13 +1063,15 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
   const uint32_t* ids = reinterpret_cast<const uint32_t*>(sorted);
   QGS_CU(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(uint2) * (size_t)T_all, st), "memset ranges");
   if (I > 0) {
-    k_tile_ranges<<<nblk(I), 256, 0, st>>>(I, sorted, ctx->ranges.p);
+    k_tile_ranges<<<nblk(I), 256, 0, st>>>(I, sorted, ctx->ranges.p, tmp.err);
     ++launch_counter();
     QGS_CU(cudaGetLastError(), "ranges");
   }
   k_tile_schedule<<<1, 1024, 0, st>>>((int)T_all, ctx->ranges.p, ctx->torder.p);
   ++launch_counter();
   QGS_CU(cudaGetLastError(), "tile schedule");
+  s = enqueue_sort_check(ctx, st);
+  if (s != QGS_OK) return s;
   const uint32_t* order = ctx->torder.p;
   QGS_CU(cudaMemsetAsync(ctx->stats.p, 0, sizeof(RasterStats), st), "memset stats");
   QGS_CU(launch_raster_fwd_views(ctx->cfg.density == 1, extra, (unsigned)T_all, st, ctx->ranges.p, ids, 2,
@@ -1027,6 +1096,9 @@ qgs_status render_backward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camer
   if (s != QGS_OK) return s;
   if (!cam || !grad_out || !grad) return fail(ctx, QGS_EINVAL, "camera/grad_out/grad is NULL");
   if (!ctx->have_frame) return fail(ctx, QGS_ESTATE, "render_backward without a preceding render_forward");
+  QGS_CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+  s = check_sorts(ctx);
+  if (s != QGS_OK) return s;
   if (scene->n != ctx->n || scene->mean != ctx->scene_mean || cam->W != ctx->W || cam->H != ctx->H)
     return fail(ctx, QGS_ESTATE, "render_backward scene/camera differ from the last render_forward");
   if (grad_out->median_depth)
@@ -1089,6 +1161,8 @@ qgs_status qgs_get_frame_stats(qgs_ctx* ctx, qgs_frame_stats* out) {
   if (!ctx || !out) return QGS_EINVAL;
   if (!ctx->have_stats) return fail(ctx, QGS_ESTATE, "no frame rendered yet");
   QGS_CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+  const qgs_status s = check_sorts(ctx);
+  if (s != QGS_OK) return s;
   QGS_CU(cudaStreamSynchronize(ctx->last_stream), "sync");
   RasterStats rs;
   QGS_CU(cudaMemcpy(&rs, ctx->stats.p, sizeof(rs), cudaMemcpyDeviceToHost), "stats");
@@ -1144,11 +1218,31 @@ qgs_status qgs_set_tile_mask_capacity(qgs_ctx* ctx, int64_t words) {
   return QGS_OK;
 }
 
+qgs_status qgs_check_frame(qgs_ctx* ctx) {
+  if (!ctx) return QGS_EINVAL;
+  QGS_CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+  return check_sorts(ctx);
+}
+
+qgs_status qgs_debug_withhold_sort_chunk(qgs_ctx* ctx, int32_t spins) {
+  if (!ctx) return QGS_EINVAL;
+  if (spins <= 0) {
+    ctx->test_withhold = 0;
+    ctx->test_spins = kLookbackSpins;
+    return QGS_OK;
+  }
+  ctx->test_withhold = 1;
+  ctx->test_spins = spins;
+  return QGS_OK;
+}
+
 qgs_status qgs_copy_binning(qgs_ctx* ctx, uint64_t* keys, uint32_t* vals, int64_t cap, uint32_t* ranges,
                             int32_t* rects, int64_t* n_instances) {
   if (!ctx) return QGS_EINVAL;
   if (!ctx->have_frame) return fail(ctx, QGS_ESTATE, "no frame rendered yet");
   QGS_CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+  const qgs_status s = check_sorts(ctx);
+  if (s != QGS_OK) return s;
   QGS_CU(cudaStreamSynchronize(ctx->last_stream), "sync");
   const int64_t I = ctx->n_inst;
   if (n_instances) *n_instances = I;
@@ -1201,6 +1295,8 @@ qgs_status qgs_copy_residue(qgs_ctx* ctx, float* T_final, uint32_t* n_contrib) {
   if (!ctx) return QGS_EINVAL;
   if (!ctx->have_frame) return fail(ctx, QGS_ESTATE, "no frame rendered yet");
   QGS_CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+  const qgs_status s = check_sorts(ctx);
+  if (s != QGS_OK) return s;
   QGS_CU(cudaStreamSynchronize(ctx->last_stream), "sync");
   const size_t P = (size_t)ctx->W * ctx->H;
   if (T_final) QGS_CU(cudaMemcpy(T_final, ctx->T_final.p, sizeof(float) * P, cudaMemcpyDeviceToHost), "copy T");
@@ -1214,7 +1310,11 @@ qgs_status qgs_copy_residue(qgs_ctx* ctx, float* T_final, uint32_t* n_contrib) {
 // ---------------------------------------------------------------------------------------
 // render_forward_noalloc: the forward render with every work buffer carved out of one
 // statically sized device array (no cudaMalloc, cudaFree or allocating library call).
-// It runs the same kernels as render_forward, with fixed capacities.
+// It runs render_forward's kernels (preprocessing, the tile test against the
+// parallelogram and the conic, the depth sort, the emission of the same tile lists, the
+// tile sort, the compositing) with fixed capacities; only the intermediate layout differs
+// (64-bit instances, primitive-indexed state, no tile-mask store), so the planes are the
+// same bit for bit.
 namespace {
 
 constexpr int64_t NA_MAX_PRIMS = 32768;
@@ -1235,7 +1335,8 @@ constexpr size_t NA_OFF_IDX2 = NA_OFF_ZKEY2 + na_align(4 * NA_MAX_PRIMS);
 constexpr size_t NA_OFF_CNT = NA_OFF_IDX2 + na_align(4 * NA_MAX_PRIMS);
 constexpr size_t NA_OFF_OFFS = NA_OFF_CNT + na_align(4 * NA_MAX_PRIMS);
 constexpr size_t NA_OFF_RECT = NA_OFF_OFFS + na_align(4 * (NA_MAX_PRIMS + 1));
-constexpr size_t NA_OFF_INST = NA_OFF_RECT + na_align(sizeof(short4) * NA_MAX_PRIMS);
+constexpr size_t NA_OFF_TSLAB = NA_OFF_RECT + na_align(sizeof(short4) * NA_MAX_PRIMS);
+constexpr size_t NA_OFF_INST = NA_OFF_TSLAB + na_align(sizeof(TileSlab) * NA_MAX_PRIMS);
 constexpr size_t NA_OFF_INST2 = NA_OFF_INST + na_align(8 * NA_MAX_INSTANCES);
 constexpr size_t NA_OFF_RANGES = NA_OFF_INST2 + na_align(8 * NA_MAX_INSTANCES);
 constexpr size_t NA_OFF_TFIN = NA_OFF_RANGES + na_align(sizeof(uint2) * NA_MAX_TILES);
@@ -1246,7 +1347,7 @@ constexpr size_t NA_OFF_STATS = NA_OFF_SCAN + na_align(4 * NA_SCAN);
 constexpr size_t NA_OFF_VIS = NA_OFF_STATS + na_align(sizeof(RasterStats));
 constexpr size_t NA_BYTES = NA_OFF_VIS + na_align(16);
 
-// The scratch itself (about 24 MB). Every GPU that loads the library holds it until the
+// The scratch itself (about 27 MB). Every GPU that loads the library holds it until the
 // process exits. Host code must not use this name as a device address.
 __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
@@ -1297,6 +1398,7 @@ extern "C" qgs_status render_forward_noalloc(const qgs_scene* scene, const qgs_c
   uint32_t* cnt_sorted = reinterpret_cast<uint32_t*>(base + NA_OFF_CNT);
   uint32_t* offs = reinterpret_cast<uint32_t*>(base + NA_OFF_OFFS);
   short4* rect = reinterpret_cast<short4*>(base + NA_OFF_RECT);
+  TileSlab* tslab = reinterpret_cast<TileSlab*>(base + NA_OFF_TSLAB);
   uint64_t* inst = reinterpret_cast<uint64_t*>(base + NA_OFF_INST);
   uint64_t* inst2 = reinterpret_cast<uint64_t*>(base + NA_OFF_INST2);
   uint2* ranges = reinterpret_cast<uint2*>(base + NA_OFF_RANGES);
@@ -1308,7 +1410,9 @@ extern "C" qgs_status render_forward_noalloc(const qgs_scene* scene, const qgs_c
   tmp.scan_tmp = reinterpret_cast<uint32_t*>(base + NA_OFF_SCAN);
   tmp.scan_cap = NA_SCAN;
   RasterStats* stats = reinterpret_cast<RasterStats*>(base + NA_OFF_STATS);
+  // [0] visible primitives, [1] tile instances, [2] unused, [3] sort failure word
   uint32_t* visible = reinterpret_cast<uint32_t*>(base + NA_OFF_VIS);
+  tmp.err = visible + 3;
 
   qgs_config cfg;
   qgs_config_default(&cfg);
@@ -1319,43 +1423,53 @@ extern "C" qgs_status render_forward_noalloc(const qgs_scene* scene, const qgs_c
   make_params(&defaults, cam, cp, rp);
   const int64_t ntiles = TX * TY;
 
-  // everything that must start at zero: the visible counter, tile ranges, counters
+  // everything that must start at zero: the counters and the sort failure word, the tile
+  // ranges, the pair counters
   QGS_CU(cudaMemsetAsync(visible, 0, 16, st), "memset");
   QGS_CU(cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)ntiles, st), "memset");
   QGS_CU(cudaMemsetAsync(stats, 0, sizeof(RasterStats), st), "memset");
   SceneView sv{scene->mean, scene->quat, scene->scale, scene->curv, scene->opacity, scene->sh};
   if (N > 0) {
-    k_preprocess<<<pre_blocks(N), 256, 0, st>>>(N, sv, cp, state, count, zkey, idx, rect, visible, nullptr, nullptr);
+    k_preprocess<<<pre_blocks(N), 256, 0, st>>>(N, sv, cp, state, count, zkey, idx, rect, nullptr, nullptr, tslab);
     QGS_CU(cudaGetLastError(), "k_preprocess");
+    // keep the rectangle's tiles that meet the parallelogram and the conic (as render_forward)
+    k_count_tiles<<<(unsigned)((N + kCountBlock - 1) / kCountBlock), kCountBlock, 0, st>>>(
+        N, tslab, cam->W, cam->H, count, rect, zkey, nullptr, visible, nullptr, nullptr, 0u);
+    QGS_CU(cudaGetLastError(), "k_count_tiles");
   }
   cudaError_t e = cudaSuccess;
   const bool fl = radix_sort_u32_pairs(zkey, idx, zkey2, idx2, N, 0, 32, tmp, st, &e);
   QGS_CU(e, "depth sort");
   const uint32_t* sidx = fl ? idx2 : idx;
   if (N > 0) {
-    k_gather_u32<<<nblk(N), 256, 0, st>>>(N, sidx, count, cnt_sorted);
+    k_gather_u32<<<nblk(N), 256, 0, st>>>(N, sidx, count, cnt_sorted, tmp.err);
     QGS_CU(cudaGetLastError(), "gather");
   }
   QGS_CU(scan_exclusive_u32(cnt_sorted, offs, N, tmp.scan_tmp, tmp.scan_cap, st), "scan");
-  uint32_t total = 0;  // pageable host word: a copy, not an allocation
-  QGS_CU(cudaMemcpyAsync(&total, offs + N, sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "total");
+  uint32_t hv[4] = {0, 0, 0, 0};  // pageable host words: a copy, not an allocation
+  QGS_CU(cudaMemcpyAsync(hv, visible, sizeof(hv), cudaMemcpyDeviceToHost, st), "totals");
   QGS_CU(cudaStreamSynchronize(st), "sync");
-  const int64_t I = (int64_t)total;
+  if (hv[3]) return QGS_ECUDA;  // the depth sort gave up waiting in its look-back
+  const int64_t I = (int64_t)hv[1];
   if (I > NA_MAX_INSTANCES) return QGS_ECAPACITY;
   const uint64_t* sorted = inst;
   if (N > 0 && I > 0) {
-    k_emit<<<nblk(N), 256, 0, st>>>(N, sidx, count, rect, nullptr, cam->W, cam->H, offs, nullptr, cp.tiles_x, inst,
-                                    nullptr, nullptr, nullptr);
+    k_emit<<<nblk(N), 256, 0, st>>>(N, sidx, count, rect, tslab, cam->W, cam->H, offs, nullptr, cp.tiles_x, inst,
+                                    nullptr, nullptr, nullptr, tmp.err);
     QGS_CU(cudaGetLastError(), "emit");
     const bool f2 = radix_sort_u64_keys(inst, inst2, I, 32, 32 + bits_for(ntiles), tmp, st, &e);
     QGS_CU(e, "tile sort");
     sorted = f2 ? inst2 : inst;
-    k_tile_ranges<<<nblk(I), 256, 0, st>>>(I, sorted, ranges);
+    k_tile_ranges<<<nblk(I), 256, 0, st>>>(I, sorted, ranges, tmp.err);
     QGS_CU(cudaGetLastError(), "ranges");
   }
   QGS_CU(launch_raster_fwd(false, false, (unsigned)ntiles, st, ranges, reinterpret_cast<const uint32_t*>(sorted), 2,
                            state, rp, out->rgb, out->alpha, out->depth, out->normal, T_final, n_contrib,
                            ExtraPlanes{}, stats, nullptr, nullptr),
          "k_raster_fwd");
+  // the tile sort's failure word (its look-back waits are bounded too)
+  QGS_CU(cudaMemcpyAsync(hv + 3, visible + 3, sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "sort status");
+  QGS_CU(cudaStreamSynchronize(st), "sync");
+  if (hv[3]) return QGS_ECUDA;
   return QGS_OK;
 }

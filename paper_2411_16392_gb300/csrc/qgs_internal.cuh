@@ -240,12 +240,23 @@ __global__ void k_preprocess_bwd(int64_t n, const uint32_t* list, SceneView sc, 
 // Keys per CTA of the radix sort (histogram sizes depend on it).
 constexpr int kRadixChunk = 2048;
 
+// Polls a look-back chunk makes for a predecessor's digit counts before it gives up.
+constexpr int kLookbackSpins = 1 << 22;
+
 // Temporary storage of the device-wide scan and radix sort.
 struct SortTemp {
   uint32_t* hist = nullptr;   // radix_hist_elems(n): count matrix, or the single-pass status words
   uint32_t* scan_tmp = nullptr;
   size_t hist_cap = 0, scan_cap = 0;
-  uint32_t* err = nullptr;    // device word set to nonzero if a look-back gave up (optional)
+  // Device word set to nonzero when a look-back wait gave up (optional). Once it is set,
+  // the following look-back passes (and the kernels of the pipeline that read a sort's
+  // output) do nothing, so an abandoned sort never leads to an out-of-range access.
+  uint32_t* err = nullptr;
+  int spins = kLookbackSpins;  // poll limit of each look-back wait
+  // Test hook (0 in normal use): the first look-back pass starts its chunk tickets at this
+  // value and launches that many fewer CTAs, so chunk 0 never publishes its digit counts
+  // and the waits for it run out.
+  int withhold_chunks = 0;
 };
 
 // Exclusive prefix sum of n u32 values; out[n] receives the total (out has n + 1 slots).

@@ -168,6 +168,7 @@ void qgs_server::run_batch(Slot& s, std::vector<Request*>& batch) {
     }
   }
   if (st == QGS_OK && cudaStreamSynchronize(s.stream) != cudaSuccess) st = QGS_ECUDA;
+  if (st == QGS_OK) st = qgs_check_frame(s.ctx);  // the frame's sorts completed their waits
   for (Request* r : batch) r->status = st;
   if (st == QGS_OK) {
     const int64_t inst = qgs::last_instance_count(s.ctx);

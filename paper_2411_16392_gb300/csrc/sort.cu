@@ -191,10 +191,12 @@ constexpr size_t downsweep_smem() {
 
 // Look-back status words of the single-pass scatter: bits 30..31 = 0 (not yet published),
 // 1 (the chunk's own digit count) or 2 (the inclusive prefix over chunks 0..b), bits 0..29
-// the count. A chunk waits at most kLookbackSpins polls for a predecessor, then sets the
-// error word and continues (no hang; the result is then reported as a failure).
+// the count. A chunk waits at most `spins` polls for a predecessor, then sets the error
+// word and continues (no hang; the result is then reported as a failure). Its keys still
+// land inside the output: the digit offsets it found are never larger than the true ones.
+// A pass that starts with the error word already set does nothing (its input would no
+// longer match the digit counts taken before the first pass).
 constexpr uint32_t kStAgg = 1u << 30, kStInc = 2u << 30, kStVal = (1u << 30) - 1u;
-constexpr int kLookbackSpins = 1 << 22;
 constexpr int kLookbackMaxChunks = 1024;  // sorts of up to 2M keys use the single-pass scatter
 
 // Stable scatter of one 2048-key chunk. Keys are ranked per warp (lanes of one digit found
@@ -213,7 +215,8 @@ __global__ void __launch_bounds__(BLOCK) k_radix_downsweep(const K* __restrict__
                                                            uint32_t* __restrict__ vout, int64_t n, int shift,
                                                            uint32_t mask, const uint32_t* __restrict__ offs,
                                                            int nblocks, const uint32_t* __restrict__ ghist,
-                                                           uint32_t* status, uint32_t* ticket, uint32_t* err) {
+                                                           uint32_t* status, uint32_t* ticket, uint32_t* err,
+                                                           int spins_max) {
   extern __shared__ __align__(16) unsigned char dsm[];
   K* skeys = reinterpret_cast<K*>(dsm);
   uint32_t* svals = reinterpret_cast<uint32_t*>(skeys + RS_CHUNK);
@@ -221,12 +224,16 @@ __global__ void __launch_bounds__(BLOCK) k_radix_downsweep(const K* __restrict__
   __shared__ uint32_t boff[256];
   __shared__ uint32_t lstart[256];
   __shared__ uint32_t wsum[RS_WARPS];
-  __shared__ uint32_t s_chunk;
+  __shared__ uint32_t s_chunk, s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int chunk = blockIdx.x;
   if constexpr (LOOKBACK) {
-    if (threadIdx.x == 0) s_chunk = atomicAdd(ticket, 1u);
+    if (threadIdx.x == 0) {
+      s_abort = *(volatile const uint32_t*)err;  // an earlier pass gave up: nothing to do
+      s_chunk = atomicAdd(ticket, 1u);
+    }
     __syncthreads();
+    if (s_abort) return;
     chunk = (int)s_chunk;
   }
   const int64_t cbase = (int64_t)chunk * RS_CHUNK;
@@ -330,7 +337,7 @@ __global__ void __launch_bounds__(BLOCK) k_radix_downsweep(const K* __restrict__
         const volatile uint32_t* sw = status + (size_t)k * 256 + d;
         uint32_t sv = *sw;
         int spins = 0;
-        while ((sv & ~kStVal) == 0u && spins < kLookbackSpins) {
+        while ((sv & ~kStVal) == 0u && spins < spins_max) {
           __nanosleep(32);
           sv = *sw;
           ++spins;
@@ -365,6 +372,8 @@ __global__ void __launch_bounds__(BLOCK) k_radix_downsweep(const K* __restrict__
     if (HAS_VAL) vout[pos] = svals[i];
   }
 }
+
+__global__ void k_set_u32(uint32_t* p, uint32_t v) { *p = v; }
 
 // Digit counts of every pass over the whole array, from one read of the keys.
 struct PassSpec {
@@ -438,6 +447,13 @@ bool radix_sort_impl(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, int be
     uint32_t* errw = tmp.err ? tmp.err : tickets + passes;  // a spare word when nobody reads the error
     *err = cudaMemsetAsync(status, 0, lb_words * sizeof(uint32_t), st);
     if (*err != cudaSuccess) return false;
+    // test hook: the first pass's tickets start after the withheld chunks, which never run
+    const int withheld = std::min(std::max(tmp.withhold_chunks, 0), nblocks - 1);
+    tmp.withhold_chunks = 0;
+    if (withheld > 0) {
+      k_set_u32<<<1, 1, 0, st>>>(tickets, (uint32_t)withheld);
+      ++launch_counter();
+    }
     k_radix_hist_all<K><<<(unsigned)std::min(nblocks, 1024), BLOCK, 0, st>>>(k0, n, ps, ghist);
     ++launch_counter();
     for (int p = 0; p < passes; ++p) {
@@ -445,9 +461,10 @@ bool radix_sort_impl(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, int be
       K* kout = flipped ? k0 : k1;
       uint32_t* vin = flipped ? v1 : v0;
       uint32_t* vout = flipped ? v0 : v1;
-      k_radix_downsweep<K, HAS_VAL, true><<<nblocks, BLOCK, smem, st>>>(
+      const int ctas = nblocks - (p == 0 ? withheld : 0);
+      k_radix_downsweep<K, HAS_VAL, true><<<ctas, BLOCK, smem, st>>>(
           kin, kout, vin, vout, n, ps.shift[p], ps.mask[p], nullptr, nblocks, ghist + (size_t)p * 256,
-          status + (size_t)p * nblocks * 256, tickets + p, errw);
+          status + (size_t)p * nblocks * 256, tickets + p, errw, tmp.spins);
       ++launch_counter();
       *err = cudaGetLastError();
       if (*err != cudaSuccess) return flipped;
@@ -472,7 +489,7 @@ bool radix_sort_impl(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int64_t n, int be
     *err = scan_exclusive_u32(tmp.hist, tmp.hist, m, tmp.scan_tmp, tmp.scan_cap, st);
     if (*err != cudaSuccess) return flipped;
     k_radix_downsweep<K, HAS_VAL, false><<<nblocks, BLOCK, smem, st>>>(kin, kout, vin, vout, n, shift, mask, tmp.hist,
-                                                                       nblocks, nullptr, nullptr, nullptr, nullptr);
+                                                                       nblocks, nullptr, nullptr, nullptr, nullptr, 0);
     ++launch_counter();
     *err = cudaGetLastError();
     if (*err != cudaSuccess) return flipped;

@@ -174,6 +174,16 @@ class Rasterizer:
         tile again). Results never depend on it."""
         L.check(self.lib.qgs_set_tile_mask_capacity(self._ctx, int(words)), self._ctx)
 
+    def check_frame(self):
+        """Wait for the last forward's sorts; raises QGSError (QGS_ECUDA) if one of their
+        bounded look-back waits ran out (the frame is then discarded)."""
+        L.check(self.lib.qgs_check_frame(self._ctx), self._ctx)
+
+    def debug_withhold_sort_chunk(self, spins: int):
+        """Test hook: the next forward's first look-back radix sort withholds its first
+        chunk, so the waits for it give up after `spins` polls (0 clears the hook)."""
+        L.check(self.lib.qgs_debug_withhold_sort_chunk(self._ctx, int(spins)), self._ctx)
+
     # ------------------------------------------------------------------ inspection
     def stats(self) -> dict:
         s = L.qgs_frame_stats()

@@ -2,9 +2,12 @@
 
 render_forward_noalloc serves callers that cannot allocate device memory while rendering
 (a host whose memory manager owns the GPU's memory pool, or a real-time loop that bans
-cudaMalloc/cudaFree after warm-up). It must produce the same images as the allocating
-entry point, twice in a row (the static scratch keeps the previous call's contents), and
-must not grow the device's memory use after its first call.
+cudaMalloc/cudaFree after warm-up). It runs the same kernels on the same tile lists as
+the allocating entry point, so its planes must be the same bit for bit, twice in a row
+(the static scratch keeps the previous call's contents), and it must not grow the
+device's memory use after its first call. Frames beyond its fixed capacities are refused
+with QGS_ECAPACITY, including one whose tile-instance count (known only after the tile
+test) exceeds the array's share for instances, and the next call works again.
 """
 import ctypes as C
 
@@ -13,7 +16,6 @@ import pytest
 import torch
 
 from paper_2411_16392_gb300.scenes import Camera, scene_small
-from tests.parity_util import TOL_ABS
 
 pytestmark = pytest.mark.gpu
 
@@ -43,15 +45,20 @@ def _noalloc(lib, ds, cam, out, dev):
     return lib.render_forward_noalloc(C.byref(sc), C.byref(cc), C.byref(img), st)
 
 
+def _cases():
+    cases = [scene_small(0, 1000), scene_small(3, 2000), scene_small(5, 20000)]
+    cases[1] = (cases[1][0], Camera(200, 120, 150.0, 150.0, 100.0, 60.0))
+    cases[2] = (cases[2][0], Camera(333, 257, 260.0, 260.0, 166.5, 128.5))   # ragged tiles
+    return cases
+
+
 def test_noalloc_forward_matches_render_forward_twice(dev):
     from paper_2411_16392_gb300 import _lib as L
     from paper_2411_16392_gb300.render import DeviceScene, Rasterizer
     lib = L.load()
-    cases = [scene_small(0, 1000), scene_small(3, 2000)]
-    cases[1] = (cases[1][0], Camera(200, 120, 150.0, 150.0, 100.0, 60.0))
     ras = Rasterizer(dev)
     prepared = []
-    for sc, cam in cases:
+    for sc, cam in _cases():
         ds = DeviceScene.from_host(sc, dev)
         want = {k: v.clone() for k, v in ras.forward(ds, cam).items()}
         prepared.append((ds, cam, want, [_outputs(dev, cam.H, cam.W) for _ in range(2)]))
@@ -62,26 +69,40 @@ def test_noalloc_forward_matches_render_forward_twice(dev):
     free_before = torch.cuda.mem_get_info(dev)[0]
     for rep in range(2):
         for ds, cam, want, outs in prepared:
-            got = outs[rep]
-            status = _noalloc(lib, ds, cam, got, dev)
+            status = _noalloc(lib, ds, cam, outs[rep], dev)
             assert status == 0, L.STATUS.get(status, status)
         torch.cuda.synchronize()
         for ds, cam, want, outs in prepared:
             for k in want:
-                err = (outs[rep][k] - want[k]).abs().max().item()
-                assert err <= TOL_ABS, (rep, k, err)
+                assert torch.equal(outs[rep][k], want[k]), (rep, k, (outs[rep][k] - want[k]).abs().max().item())
     # the calls allocated no device memory (the scratch is static)
     assert torch.cuda.mem_get_info(dev)[0] == free_before
 
 
 def test_noalloc_rejects_sizes_beyond_its_limits(dev):
     from paper_2411_16392_gb300 import _lib as L
-    from paper_2411_16392_gb300.render import DeviceScene
+    from paper_2411_16392_gb300.render import DeviceScene, Rasterizer
     lib = L.load()
     sc, cam = scene_small(0, 1000)
     ds = DeviceScene.from_host(sc, dev)
     big = Camera(1024, 1024, 512.0, 512.0, 512.0, 512.0)   # 1M pixels > 262144
-    got = _outputs(dev, big.H, big.W)
-    assert _noalloc(lib, ds, big, got, dev) == 3            # QGS_ECAPACITY
+    assert _noalloc(lib, ds, big, _outputs(dev, big.H, big.W), dev) == 3            # QGS_ECAPACITY
     many, _ = scene_small(1, 40000)                          # > 32768 primitives
     assert _noalloc(lib, DeviceScene.from_host(many, dev), cam, _outputs(dev, cam.H, cam.W), dev) == 3
+    # within the primitive, pixel and tile limits, but more than 1,048,576 tile instances:
+    # refused after the tile test
+    wide, _ = scene_small(2, 30000)
+    wide.scale *= np.float32(20.0)
+    cam512 = Camera(512, 512, 512.0, 512.0, 256.0, 256.0)
+    dw = DeviceScene.from_host(wide, dev)
+    ras = Rasterizer(dev)
+    ras.forward(dw, cam512)
+    assert ras.stats()["n_instances"] > (1 << 20)
+    assert _noalloc(lib, dw, cam512, _outputs(dev, cam512.H, cam512.W), dev) == 3
+    # the next call renders correctly again
+    want = {k: v.clone() for k, v in ras.forward(ds, cam).items()}
+    got = _outputs(dev, cam.H, cam.W)
+    assert _noalloc(lib, ds, cam, got, dev) == 0
+    torch.cuda.synchronize()
+    for k in want:
+        assert torch.equal(got[k], want[k]), k
