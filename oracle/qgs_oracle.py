@@ -656,11 +656,12 @@ def quadratic_roots(A, B, C, flip_real=None, d_shift=None):
     q = -(B + sgn(B) sqrt(D)) / 2 with sgn(0) = +1; the roots are C/q and q/A, each
     missing when its denominator is zero (A = 0 leaves the single root -C/B).
     Bracketing (decisions taken the other way, see bracket_pixels): flip_real inverts the
-    decision D >= 0 (a negative D then counts as 0, the double root); d_shift is added to
-    D before anything else."""
-    D = B * B - 4.0 * A * C
+    decision D >= 0 (a negative D then counts as 0, the double root); d_shift moves the
+    discriminant by that much, by solving the quadratic with C - d_shift / (4A) (A != 0)."""
     if d_shift is not None:
-        D = D + d_shift
+        A_s = torch.where(A != 0, A, torch.ones_like(A))
+        C = torch.where(A != 0, C - d_shift / (4.0 * A_s), C)
+    D = B * B - 4.0 * A * C
     real = D >= 0
     if flip_real is not None:
         real = real ^ flip_real
@@ -762,7 +763,8 @@ DECISIONS = ("D", "near1", "near2", "in1", "in2", "amin", "amax")
 
 
 def _eval_pairs(prm: Params, cam: CamF64, idx: torch.Tensor, px: torch.Tensor, py: torch.Tensor,
-                density: str = "geodesic", flip: dict | None = None, d_shift=None):
+                density: str = "geodesic", flip: dict | None = None, d_shift=None, root_leaves: bool = False,
+                ray_noise=None):
     """Evaluate every (pixel, primitive) pair of a pixel set [P] and a primitive list [L].
     Returns per-pair tensors [P, L]: alpha (0 where no contribution), validity, depth t,
     colour [P, L, 3] (broadcast), camera-space unit normal [P, L, 3], Gaussian curvature
@@ -780,8 +782,12 @@ def _eval_pairs(prm: Params, cam: CamF64, idx: torch.Tensor, px: torch.Tensor, p
       amax   o G < 0.99 (alpha not clamped: the same value either way, another derivative).
     `flip` (bracketing, see bracket_pixels) maps decision names to bool tensors
     broadcastable to [P, L] that take those decisions the other way; `d_shift` [P, L] is
-    added to the discriminant (its value in units of B0^2 + 4|A C0|, the scale of its
-    rounding, below)."""
+    added to the discriminant (in units of the scale of its rounding, below). With
+    root_leaves, the two roots are made leaves of the autograd graph (returned as "roots"),
+    so that a backward pass yields the derivative of the outputs with respect to each root
+    (see graze_bands). ray_noise [P, L, 6] (see ray_sensitivity) perturbs each pair's local
+    ray: its origin where it crosses the centre's depth and its direction, componentwise
+    and relatively."""
     weight_fn = {"geodesic": geodesic_gaussian, "euclid": euclid_gaussian}[density]
     fl = flip or {}
     mu = prm.mean[idx]
@@ -798,25 +804,39 @@ def _eval_pairs(prm: Params, cam: CamF64, idx: torch.Tensor, px: torch.Tensor, p
     d_hat = torch.einsum("lji,pj->pli", R, d_w)                            # [P,L,3]
     ox, oy, oz = (o_hat[:, k][None, :] for k in range(3))
     dx, dy, dz = d_hat.unbind(-1)
+    if ray_noise is not None:
+        t0n = (mu @ cam.R[2] + cam.t[2])[None, :]
+        o0 = [(o + t0n * d) * (1.0 + ray_noise[..., k]) for k, (o, d) in enumerate(((ox, dx), (oy, dy), (oz, dz)))]
+        dx, dy, dz = (d * (1.0 + ray_noise[..., 3 + k]) for k, d in enumerate((dx, dy, dz)))
+        ox, oy, oz = o0[0] - t0n * dx, o0[1] - t0n * dy, o0[2] - t0n * dz
     A_ = a * dx * dx + b * dy * dy
     B_ = 2.0 * (a * ox * dx + b * oy * dy) - dz
     C_ = (a * ox * ox + b * oy * oy - oz).expand_as(A_)
     # Scale of the discriminant's rounding: D is the same for the ray re-parametrised as
-    # s = t - t0 around the depth t0 of the centre, where B and C are of the size of the
-    # primitive instead of the camera distance.
+    # s = t - t0 around the depth t0 of the centre, where the ray starts at o0 = o + t0 d,
+    # of the size of the primitive instead of the camera distance. A, B0 and C0 are sums of
+    # terms that cancel on saddles (a b < 0) and near tangency, so an implementation that
+    # rounds them knows D to a fraction of the same sums taken over the terms' absolute
+    # values, not of |B0|^2 + 4 |A C0|.
     with torch.no_grad():
         t0 = (mu @ cam.R[2] + cam.t[2])[None, :]
-        B0 = B_ + 2.0 * A_ * t0
-        C0 = (A_ * t0 + B_) * t0 + C_
-        d_scale = (B0 * B0 + 4.0 * (A_ * C0).abs()).clamp_min(1e-300)
+        o0x, o0y, o0z = ox + t0 * dx, oy + t0 * dy, oz + t0 * dz
+        Aab = a.abs() * dx * dx + b.abs() * dy * dy
+        Bab = 2.0 * ((a * o0x * dx).abs() + (b * o0y * dy).abs()) + dz.abs()
+        Cab = a.abs() * o0x * o0x + b.abs() * o0y * o0y + o0z.abs()
+        d_scale = (Bab * Bab + 4.0 * Aab * Cab).clamp_min(1e-300)
     shift = None if d_shift is None else d_shift * d_scale
     t1, t2, e1, e2, _ = quadratic_roots(A_, B_, C_, fl.get("D"), shift)
+    if root_leaves:
+        t1 = t1.detach().requires_grad_(True)
+        t2 = t2.detach().requires_grad_(True)
+    roots = (t1, t2)
     with torch.no_grad():
-        D_ = B_ * B_ - 4.0 * A_ * C_ + (0.0 if shift is None else shift)
+        D_ = B_ * B_ - 4.0 * A_ * C_ + (0.0 if shift is None else torch.where(A_ != 0, shift, 0.0 * shift))
         m_D = D_.abs() / d_scale
         # Conditioning of a hit's derivative: at a root, d f / d t = +-sqrt(D), so the
         # derivative of the root (and everything downstream of it) scales like 1/sqrt(D);
-        # relative input perturbations e move it by about e * B^2 / D.
+        # a rounding error e d_scale of D moves it by about e d_scale / (2 D).
         m_cond = m_D.clone()
         # The decision only matters where the double root t* = -B/(2A) lies on the
         # support (x^2/s_u^2 + y^2/s_v^2 <= 9, with slack); elsewhere both outcomes
@@ -895,7 +915,7 @@ def _eval_pairs(prm: Params, cam: CamF64, idx: torch.Tensor, px: torch.Tensor, p
     cond = torch.where(valid, m_cond, torch.full_like(m_cond, np.inf))
     K = gaussian_curvature(x, y, a, b)
     return dict(alpha=alpha, valid=valid, hit=hit, t=t, rgb=rgb, normal=n_c, curvature=K, margin=margin,
-                cond=cond, margins=margins)
+                cond=cond, margins=margins, roots=roots, pick_near=pick_n)
 
 
 MEDIAN_T = 0.5   # median depth: the largest hit depth among blended pairs with T_i > 0.5
@@ -916,7 +936,7 @@ def _distortion(w: torch.Tensor, t: torch.Tensor, block: int = 32) -> torch.Tens
     return out
 
 
-def _composite(prm, cam, idx, px, py, chunk=4096, density="geodesic", extras=False):
+def _composite(prm, cam, idx, px, py, chunk=4096, density="geodesic", extras=False, collect=None, noise=None):
     """Front-to-back alpha blending of a pixel set over one sorted primitive list
     (blending Eq. of Sec. 3.1 and X_hat = sum alpha_i T_i X_i of the supplementary).
     extras: also the curvature map (Sec. 3.2.1, N/K rendering Eq.), the depth distortion
@@ -943,7 +963,10 @@ def _composite(prm, cam, idx, px, py, chunk=4096, density="geodesic", extras=Fal
     for c0 in range(0, L, chunk):
         sl = idx[c0:c0 + chunk]
         Lc = sl.shape[0]
-        pe = _eval_pairs(prm, cam, sl, px, py, density)
+        rn = None if noise is None else noise(P, sl.shape[0], c0)
+        pe = _eval_pairs(prm, cam, sl, px, py, density, root_leaves=collect is not None, ray_noise=rn)
+        if collect is not None:
+            collect.append((c0, pe))
         al, v = pe["alpha"], pe["valid"]
         onem = 1.0 - al
         cp = torch.cumprod(onem, dim=1)
@@ -1005,7 +1028,8 @@ RESORT = 8   # per-pixel resort buffer length of the supplementary's resorting
 ORDER_GAP_SCALE = 10.0
 
 
-def _composite_resort(prm, cam, idx, px, py, density="geodesic", extras=False, buf=RESORT):
+def _composite_resort(prm, cam, idx, px, py, density="geodesic", extras=False, buf=RESORT, collect=None,
+                      noise=None):
     """Front-to-back blending with StopThePop's per-pixel local resorting as adopted by
     the supplementary ("Details of Per-tile Sorting and Per-pixel Resorting"): each pixel
     walks its tile's list and puts every contributing pair (alpha >= 1/255) into a buffer
@@ -1017,7 +1041,10 @@ def _composite_resort(prm, cam, idx, px, py, density="geodesic", extras=False, b
     P = px.shape[0]
     L = idx.shape[0]
     dev = dict(dtype=F64)
-    pe = _eval_pairs(prm, cam, idx, px, py, density)
+    rn = None if noise is None else noise(P, L, 0)
+    pe = _eval_pairs(prm, cam, idx, px, py, density, root_leaves=collect is not None, ray_noise=rn)
+    if collect is not None:
+        collect.append((0, pe))
     al, valid, tt = pe["alpha"], pe["valid"], pe["t"]
     rows = torch.arange(P)
     T = torch.ones(P, **dev)
@@ -1131,7 +1158,7 @@ def _tile_pixels(cam, tile, TX):
 
 
 def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=None, density="geodesic",
-           extras=False, order="centre"):
+           extras=False, order="centre", ray_noise_seed=None):
     """Render the full image (or the listed tiles). Returns a dict of numpy arrays:
     rgb [3,H,W], alpha [H,W], depth [H,W], normal [3,H,W], margin [H,W], n_eval [H,W],
     n_contrib [H,W], T_final [H,W]; with `extras` also curvature, distortion,
@@ -1142,7 +1169,9 @@ def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=N
     `grads`: the exact FP64 gradient of sum(grad * output) with respect to every scene
     parameter. density: "geodesic" (the paper's) or "euclid". order: "centre" (tile lists
     by centre depth) or "stp" (StopThePop: per-tile hit depth, then per-pixel resorting
-    in a buffer of RESORT entries)."""
+    in a buffer of RESORT entries). ray_noise_seed: perturb every pair's local ray by
+    uniform relative noise of RAY_EPS per component, drawn from a generator seeded by
+    (seed, tile, list position) (see ray_sensitivity)."""
     if binning is None:
         binning = bin_fp32(scene, cam, order="hit" if order == "stp" else "centre")
     comp = _composite_resort if order == "stp" else _composite
@@ -1176,8 +1205,13 @@ def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=N
         idx = torch.from_numpy(lst.astype(np.int64))
         px = torch.tensor(xs, dtype=F64)
         py = torch.tensor(ys, dtype=F64)
+        noise = None
+        if ray_noise_seed is not None:
+            def noise(P_, L_, c0, _t=tile):
+                gen = torch.Generator().manual_seed(int(ray_noise_seed) * 1_000_003 + _t * 4099 + c0)
+                return (2.0 * torch.rand(P_, L_, 6, generator=gen, dtype=F64) - 1.0) * RAY_EPS
         with torch.set_grad_enabled(want_grad):
-            r = comp(prm, c64, idx, px, py, density=density, extras=extras)
+            r = comp(prm, c64, idx, px, py, density=density, extras=extras, noise=noise)
             if want_grad:
                 loss = torch.zeros((), dtype=F64)
                 for k in ("rgb", "normal"):
@@ -1256,3 +1290,445 @@ def pair_count(binning: Binning, cam) -> int:
         xs, _ = _tile_pixels(cam, tile, TX)
         tot += int(e - s) * xs.size
     return tot
+
+
+# =========================================================================== bracketing
+# Where an FP32 implementation and this FP64 oracle can take a discrete decision differently
+# (a quantity within rounding distance of its threshold), both outcomes are correct
+# renderings of the same inputs. bracket_pixels enumerates, per pixel, the outputs of every
+# combination of such decisions (each taken both ways); a rendering matches the oracle at
+# that pixel if it matches one of them. The same combinations bound the gradients: each
+# pixel's gradient contribution lies between those of its branches.
+BRACKET_MARGIN = 1e-5     # relative margin below which a decision is taken both ways
+BRACKET_LEAVES = 512      # most branches enumerated per pixel (more: the pixel is unresolved)
+GRAZE_MARGIN = 1e-2       # blended pairs whose discriminant margin is below this ...
+GRAZE_SHIFT = 1e-6        # ... are also evaluated with D moved by this fraction of its scale
+GRAZE_FULL = 20 * GRAZE_SHIFT   # below this margin a shifted pair is re-evaluated, above it linearised
+ORDER_GAP = 2.0 ** -20    # list-free order: neighbours whose centre depths are this close may swap
+# An FP32 implementation forms each pair's local ray (where it crosses the centre's depth,
+# and its direction) in a handful of rounded operations from rounded per-primitive state:
+# about 8 units in the last place of each component, relative.
+RAY_EPS = 8.0 * 2.0 ** -24
+OUT_LEN = {"rgb": 3, "alpha": 1, "depth": 1, "normal": 3, "curvature": 1, "distortion": 1, "median_depth": 1}
+
+
+def listfree_candidates(scene, cam, x: int, y: int):
+    """Primitives that can have a hit on the ray of pixel (x, y), without tile lists or any
+    FP32 recipe: every valid primitive whose centre lies in front of the near plane and whose
+    centre is within 3 max(s_u, s_v) of the ray's line. A support point p has l <= 3 sigma
+    (Sec. 3.2.1), the arc from the vertex is no shorter than its chord |p - mu|, and
+    sigma(theta) <= max(s_u, s_v) (Sec. 3.2, sigma Eq.), so |p - mu| <= 3 max(s_u, s_v):
+    a ray with a hit passes that close to the centre. Returned in (FP64 centre depth, index)
+    order, the order of the tile lists' keys, with the depths."""
+    mean = np.asarray(scene.mean, np.float64)
+    R = np.asarray(cam.R_cw, np.float32).astype(np.float64)
+    tc = np.asarray(cam.t_cw, np.float32).astype(np.float64)
+    fx, fy, cx, cy = (float(np.float32(v)) for v in (cam.fx, cam.fy, cam.cx, cam.cy))
+    c_w = -(R.T @ tc)
+    d_cam = np.array([(x + 0.5 - cx) / fx, (y + 0.5 - cy) / fy, 1.0])
+    d_w = R.T @ d_cam
+    d_w = d_w / np.linalg.norm(d_w)
+    z = mean @ R[2] + tc[2]
+    rel = mean - c_w
+    cr = np.cross(rel, d_w)
+    dist2 = (cr * cr).sum(1)
+    m = np.max(np.asarray(scene.scale, np.float64), 1)
+    q = np.asarray(scene.quat, np.float64)
+    ok = (np.isfinite(mean).all(1) & np.isfinite(q).all(1) & np.isfinite(scene.scale).all(1)
+          & np.isfinite(scene.curv).all(1) & np.isfinite(scene.opacity) & ((q * q).sum(1) > 0)
+          & (np.min(scene.scale, 1) > 0))
+    near = float(np.float32(cam.near))
+    sel = np.nonzero(ok & (z > near * (1.0 - BRACKET_MARGIN)) & (dist2 <= (3.0 * m) ** 2 * (1.0 + 1e-9)))[0]
+    order = np.lexsort((sel, z[sel]))
+    return sel[order].astype(np.int64), z[sel[order]]
+
+
+def _order_outputs(pe, order, extras, margin=BRACKET_MARGIN):
+    """Outputs of one branch: the pairs of list positions `order` blended in that order by
+    the blending Eq. of Sec. 3.1 (w_k = alpha_k T_k), and the extra channels. The median
+    depth's own decision (T_k > 0.5, Sec. 4.1) is bracketed as an interval: median_lo /
+    median_hi leave out / take in the pairs whose T_k is within `margin` of 0.5."""
+    idx = torch.tensor(order, dtype=torch.long)
+    al = pe["alpha"][0, idx]
+    t = pe["t"][0, idx]
+    onem = 1.0 - al
+    Tex = torch.cat([torch.ones(1, dtype=F64), torch.cumprod(onem, 0)[:-1]]) if len(order) else al
+    w = al * Tex
+    out = {"rgb": (w[:, None] * pe["rgb"][idx]).sum(0), "alpha": 1.0 - torch.prod(onem)[None],
+           "depth": (w * t).sum()[None], "normal": (w[:, None] * pe["normal"][0, idx]).sum(0)}
+    if extras:
+        out["curvature"] = (w * pe["curvature"][0, idx]).sum()[None]
+        out["curvature_scale"] = (w * pe["curvature"][0, idx].abs()).sum()[None].detach()
+        out["distortion"] = _distortion(w[None], t[None]) if len(order) else torch.zeros(1, dtype=F64)
+        zero = torch.zeros(1, dtype=F64)
+        for nm, thr in (("median_depth", MEDIAN_T), ("median_lo", MEDIAN_T * (1.0 + margin)),
+                        ("median_hi", MEDIAN_T * (1.0 - margin))):
+            sel = Tex > thr
+            out[nm] = (t[sel].max()[None] if bool(sel.any()) else zero).detach()
+    return out
+
+
+def _list_orders(pe, perm, margin):
+    """Blend orders of the list order `perm` (the base ordering: front to back in list
+    order) for every place where the pixel may stop: the transmittance rule of Sec. 4.1
+    (stop before a pair that would take T below 1e-4), taken both ways where T after the
+    pair is within `margin` of the threshold. Returns [(order, n_contrib)], the nominal
+    branch (every decision taken as computed) first."""
+    al = pe["alpha"][0].detach().tolist()
+    v = pe["valid"][0].tolist()
+    res, order, T = [], [], 1.0
+    nominal = None
+
+    def leaf():
+        return (list(order), (max(perm.index(k) for k in order) + 1) if order else 0)
+
+    for j in perm:
+        if not v[j]:
+            continue
+        ta = T * (1.0 - al[j])
+        if abs(ta - T_MIN) / T_MIN < margin:
+            res.append(leaf())
+            if ta < T_MIN and nominal is None:
+                nominal = len(res) - 1
+        elif ta < T_MIN:
+            res.append(leaf())
+            if nominal is None:
+                nominal = len(res) - 1
+            break
+        order.append(j)
+        T = ta
+    else:
+        res.append(leaf())
+        if nominal is None:
+            nominal = len(res) - 1
+    return [res[nominal]] + res[:nominal] + res[nominal + 1:]
+
+
+def _resort_orders(pe, buf, margin, max_branches):
+    """Blend orders of StopThePop's per-pixel resorting (supplementary, "Details of Per-tile
+    Sorting and Per-pixel Resorting", as in _composite_resort): contributing pairs enter a
+    buffer of `buf`; when it is full the nearest hit is blended (ties: earlier in the list),
+    the rest nearest first at the end; the transmittance stop applies when an entry is
+    blended. Branches where the two nearest buffered depths are within the order margin
+    (their relative gap times ORDER_GAP_SCALE below `margin`: either may come first) and
+    where the stop rule is within `margin`. Returns [(order, n_blended)], the nominal branch
+    first, or None when the branches exceed max_branches."""
+    al = pe["alpha"][0].detach().tolist()
+    v = pe["valid"][0].tolist()
+    tt = pe["t"][0].detach().tolist()
+    L = len(v)
+    res = []   # (order, n_blended, nominal path?)
+    stack = [(0, (), 1.0, (), True)]   # (next list position, buffer of (t, j), T, blended, nominal)
+    while stack:
+        if len(res) + len(stack) > max_branches:
+            return None
+        j, bufr, T, order, nom = stack.pop()
+        while True:
+            if j < L and len(bufr) < buf:
+                if v[j]:
+                    bufr = bufr + ((tt[j], j),)
+                j += 1
+                if len(bufr) < buf:
+                    continue
+            if not bufr:
+                res.append((list(order), len(order), nom))
+                break
+            srt = sorted(bufr)
+            cands = [(srt[0], True)]
+            if len(srt) > 1 and abs(srt[1][0] - srt[0][0]) * ORDER_GAP_SCALE < margin * abs(srt[0][0]):
+                cands.append((srt[1], False))
+            outs = []   # ("stop" | "go", order, state, nominal)
+            for c, c_nom in cands:
+                rest = tuple(e for e in bufr if e != c)
+                ta = T * (1.0 - al[c[1]])
+                stop_nom = ta < T_MIN
+                if abs(ta - T_MIN) / T_MIN < margin:
+                    outs.append(("stop", order, None, nom and c_nom and stop_nom))
+                    outs.append(("go", order + (c[1],), (rest, ta), nom and c_nom and not stop_nom))
+                elif stop_nom:
+                    outs.append(("stop", order, None, nom and c_nom))
+                else:
+                    outs.append(("go", order + (c[1],), (rest, ta), nom and c_nom))
+            cont = None
+            for kind, od, st, nn in outs:
+                if kind == "stop":
+                    res.append((list(od), len(od), nn))
+                elif cont is None:
+                    cont = (od, st, nn)
+                else:
+                    stack.append((j, st[0], st[1], od, nn))
+            if cont is None:
+                break
+            order, (bufr, T), nom = cont
+    k = next(i for i, r in enumerate(res) if r[2])
+    res = [res[k]] + res[:k] + res[k + 1:]
+    return [(od, nb) for od, nb, _ in res]
+
+
+def bracket_pixels(scene, cam, pixels, binning: Binning | None = None, list_free: bool = False,
+                   density: str = "geodesic", extras: bool = False, grad_images=None, order: str = "centre",
+                   margin: float = BRACKET_MARGIN, max_leaves: int = BRACKET_LEAVES, graze: bool = True):
+    """Outputs (and gradients) of pixels [(x, y), ...] on every branch of their near-threshold
+    decisions. Per pixel, the list is its tile's list (binning, the per-tile sorting of the
+    supplementary) or, with list_free, listfree_candidates. A decision is taken both ways
+    when its relative margin is below `margin`: the pair decisions of _eval_pairs (real
+    roots, the near plane for either root, 3 sigma for either root, alpha >= 1/255, and,
+    with gradients, the 0.99 clamp, which changes only the derivative), the transmittance
+    stop, the order of two neighbours whose centre depths are within ORDER_GAP of each
+    other (list-free), and, with order="stp", which of the two nearest buffered hits is
+    blended first (_resort_orders). With `graze`, each blended pair whose discriminant
+    margin is below GRAZE_FULL is also evaluated with D moved by +-GRAZE_SHIFT of its
+    scale: near a grazing ray the root's derivative goes like 1/sqrt(D), and an FP32
+    implementation knows D only to about that much (graze_bands covers the margins from
+    GRAZE_FULL to GRAZE_MARGIN to first order). These shifts are small and independent,
+    so they are taken one pair at a time (their effects add to first order), on the
+    nominal branch of the discrete decisions, which are taken in every combination.
+    Returns one dict per pixel: "leaves" (list of output dicts of numpy arrays, the first
+    the nominal branch), "groups" per leaf ("d" for a combination of discrete decisions,
+    ("g", j) for list position j's shifted discriminant), "n_contrib" per leaf, "resolved"
+    (False when the discrete combinations exceed max_leaves: only the nominal one is
+    returned), "n_branch_decisions"; with grad_images (dict of upstream planes as in
+    render) also "prims" (the list's primitive indices) and "grads" (per leaf, dict of
+    gradient arrays [len(prims), ...] of sum(g * outputs) at this pixel)."""
+    if order == "stp":
+        if list_free:
+            raise ValueError("the list-free mode uses the centre order")
+        if binning is None or binning.order != "hit":
+            binning = bin_fp32(scene, cam, order="hit") if binning is None else binning
+    want_grad = grad_images is not None
+    c64 = CamF64(cam)
+    res = []
+    names = DECISIONS if want_grad else tuple(n for n in DECISIONS if n != "amax")
+    outkeys = OUT_KEYS + (EXTRA_KEYS + ("median_lo", "median_hi", "curvature_scale") if extras else ())
+    g = None
+    if want_grad:
+        g = {k: torch.tensor(np.asarray(v, np.float64)) for k, v in grad_images.items()}
+    for (x, y) in pixels:
+        x, y = int(x), int(y)
+        if list_free:
+            lst, zc = listfree_candidates(scene, cam, x, y)
+        else:
+            tile = (y // TILE) * binning.tiles_x + (x // TILE)
+            if binning.ranges is not None:
+                s_, e_ = binning.ranges[tile]
+                lst = binning.vals[s_:e_].astype(np.int64)
+            else:
+                lst = tile_list(binning, tile).astype(np.int64)
+            zc = None
+        L = int(lst.size)
+        item = {"x": x, "y": y, "leaves": [], "groups": [], "n_contrib": [], "resolved": True,
+                "n_branch_decisions": 0}
+        if want_grad:
+            item["prims"] = lst
+            item["grads"] = []
+        if L == 0:
+            item["leaves"].append({k: np.zeros(OUT_LEN.get(k, 1)) for k in outkeys})
+            item["groups"].append("d")
+            item["n_contrib"].append(0)
+            if want_grad:
+                item["grads"].append(None)
+            res.append(item)
+            continue
+        prm = Params(scene.subset(lst), requires_grad=want_grad)
+        idx = torch.arange(L)
+        px = torch.tensor([float(x)], dtype=F64)
+        py = torch.tensor([float(y)], dtype=F64)
+        with torch.no_grad():
+            pe0 = _eval_pairs(prm, c64, idx, px, py, density)
+        # per pair: the decisions within the margin; where a decision can flip, the pair may
+        # contribute (or not) on some branch
+        per_pair = {}
+        for nm in names:
+            for j in torch.nonzero(pe0["margins"][nm][0] < margin).flatten().tolist():
+                per_pair.setdefault(j, []).append(nm)
+        maybe = pe0["valid"][0].clone()
+        for j in per_pair:
+            maybe[j] = True
+        if list_free:  # a centre at the near plane may be culled or not
+            near = float(np.float32(cam.near))
+            for j in np.nonzero(np.abs(zc - near) / near < margin)[0].tolist():
+                per_pair.setdefault(j, []).append("cull")
+            keep_c = torch.from_numpy(zc > near)
+        choices = []   # (kind, payload) binary (ternary for graze) choices
+        for j, nms in sorted(per_pair.items()):
+            for nm in nms:
+                choices.append(("flip", (j, nm)))
+        grazing = torch.nonzero(pe0["cond"][0] < GRAZE_FULL).flatten().tolist() if graze else []
+        if list_free:
+            cj = torch.nonzero(maybe).flatten().tolist()
+            for a_, b_ in zip(cj[:-1], cj[1:]):
+                if abs(zc[b_] - zc[a_]) <= ORDER_GAP * abs(zc[a_]):
+                    choices.append(("swap", (a_, b_)))
+        item["n_branch_decisions"] = len(choices) + len(grazing)
+        if 2 ** len(choices) > max_leaves:
+            item["resolved"] = False
+            choices = []
+        combos = [[]]
+        for kind, pl in choices:
+            combos = [c + [(kind, pl, o)] for c in combos for o in (False, True)]
+        runs = [("d", c) for c in combos]
+        runs += [(("g", j), [("graze", j, sg)]) for j in grazing for sg in (-1.0, 1.0)]
+        for group, combo in runs:
+            flip = {}
+            shift = None
+            perm = list(range(L))
+            culled = []
+            for kind, pl, o in combo:
+                if kind == "flip" and o:
+                    j, nm = pl
+                    if nm == "cull":
+                        culled.append(j)
+                        continue
+                    flip.setdefault(nm, torch.zeros(1, L, dtype=torch.bool))[0, j] = True
+                elif kind == "graze" and o is not None:
+                    if shift is None:
+                        shift = torch.zeros(1, L, dtype=F64)
+                    shift[0, pl] = o * GRAZE_SHIFT
+                elif kind == "swap" and o:
+                    a_, b_ = pl
+                    ia, ib = perm.index(a_), perm.index(b_)
+                    perm[ia], perm[ib] = perm[ib], perm[ia]
+            with torch.set_grad_enabled(want_grad):
+                pe = _eval_pairs(prm, c64, idx, px, py, density, flip=flip, d_shift=shift)
+                if list_free:
+                    kc = keep_c.clone()
+                    for j in culled:
+                        kc[j] = ~kc[j]
+                    pe["valid"] = pe["valid"] & kc[None]
+                    pe["alpha"] = torch.where(pe["valid"], pe["alpha"], torch.zeros_like(pe["alpha"]))
+                if order == "stp":
+                    branches = _resort_orders(pe, RESORT, margin, max_leaves)
+                    if branches is None:
+                        item["resolved"] = False
+                        branches = _resort_orders(pe, RESORT, 0.0, 1)
+                else:
+                    branches = _list_orders(pe, perm, margin)
+                if group != "d":
+                    branches = branches[:1]
+                for od, nc in branches:
+                    out = _order_outputs(pe, od, extras, margin)
+                    item["leaves"].append({k: v.detach().numpy().copy() for k, v in out.items()})
+                    item["groups"].append(group)
+                    item["n_contrib"].append(nc)
+                    if want_grad:
+                        loss = torch.zeros((), dtype=F64)
+                        for k in ("rgb", "normal"):
+                            if k in g:
+                                loss = loss + (g[k][:, y, x] * out[k]).sum()
+                        for k in ("alpha", "depth", "curvature", "distortion"):
+                            if k in g and k in out:
+                                loss = loss + g[k][y, x] * out[k][0]
+                        leaves_t = prm.leaves()
+                        if loss.requires_grad:
+                            gr = torch.autograd.grad(loss, list(leaves_t.values()), retain_graph=True,
+                                                     allow_unused=True)
+                        else:
+                            gr = [None] * len(leaves_t)
+                        gd = {}
+                        for (k, v), gk in zip(leaves_t.items(), gr):
+                            gd[k] = (gk if gk is not None else torch.zeros_like(v)).detach().numpy().copy()
+                        gd["sh"] = gd["sh"].reshape(-1, 48)
+                        item["grads"].append(gd)
+        res.append(item)
+    return res
+
+
+def pixel_vector(out: dict, keys) -> np.ndarray:
+    """Concatenated outputs of one pixel (rgb 3, alpha, depth, normal 3, then `keys` extras)."""
+    return np.concatenate([np.asarray(out[k], np.float64).reshape(-1) for k in OUT_KEYS + tuple(keys)])
+
+
+
+def graze_bands(scene, cam, binning: Binning, tiles, grad_images, density: str = "geodesic", extras: bool = False,
+                order: str = "centre", lo: float = GRAZE_FULL, hi: float = GRAZE_MARGIN,
+                shift: float = GRAZE_SHIFT):
+    """First-order bounds on how far each primitive's gradient moves when the discriminant of
+    each of its blended grazing pairs (margin in [lo, hi)) is moved by `shift` of its
+    rounding scale. Near a grazing ray the derivative of the root t with respect to the
+    primitive's parameters goes like 1/sqrt(D) (at a root, df/dt = +-sqrt(D)), so moving D by
+    e scales that derivative by about 1 -+ e / (2 D); the part of a pixel's gradient that
+    flows through the root, (dL_p/dt) (dt/dtheta), moves by as much. Per element, the band
+    sums |shift / (2 margin)| |dL_p/dt| |dt/dtheta| over the primitive's grazing pairs (one
+    pixel's error may have either sign). dL_p/dt comes from one backward pass per tile with
+    the roots as leaves; dt/dtheta from the single pair. Returns {parameter: (primitive
+    indices, band array)} over the primitives that have such pairs in `tiles`."""
+    comp = _composite_resort if order == "stp" else _composite
+    c64 = CamF64(cam)
+    g = {k: torch.tensor(np.asarray(v, np.float64)) for k, v in grad_images.items()}
+    prm_nograd = Params(scene)
+    pairs = []   # (primitive, x, y, kappa * |dL/dt|)
+    for tile in tiles:
+        lst = tile_list(binning, tile) if binning.ranges is None else binning.vals[slice(*binning.ranges[tile])]
+        if len(lst) == 0:
+            continue
+        xs, ys = _tile_pixels(cam, tile, binning.tiles_x)
+        idx = torch.from_numpy(np.asarray(lst, np.int64))
+        px = torch.tensor(xs, dtype=F64)
+        py = torch.tensor(ys, dtype=F64)
+        collect = []
+        r = comp(prm_nograd, c64, idx, px, py, density=density, extras=extras, collect=collect)
+        loss = torch.zeros((), dtype=F64)
+        for k in ("rgb", "normal"):
+            if k in g:
+                loss = loss + (g[k][:, ys, xs].T * r[k]).sum()
+        for k in ("alpha", "depth", "curvature", "distortion"):
+            if k in g and k in r:
+                loss = loss + (g[k][ys, xs] * r[k]).sum()
+        leaves = [t for _, pe in collect for t in pe["roots"]]
+        if not loss.requires_grad:
+            continue
+        grads = torch.autograd.grad(loss, leaves, allow_unused=True)
+        for q, (c0, pe) in enumerate(collect):
+            g1, g2 = grads[2 * q], grads[2 * q + 1]
+            g1 = torch.zeros_like(pe["roots"][0]) if g1 is None else g1
+            g2 = torch.zeros_like(pe["roots"][1]) if g2 is None else g2
+            dLdt = torch.where(pe["pick_near"], g1, g2)
+            cond = pe["cond"]
+            sel = (cond >= lo) & (cond < hi) & pe["valid"]
+            for pi, jj in torch.nonzero(sel).tolist():
+                kap = shift / (2.0 * float(cond[pi, jj]))
+                pairs.append((int(idx[c0 + jj]), int(xs[pi]), int(ys[pi]), kap * abs(float(dLdt[pi, jj]))))
+    bands = {}
+    by_prim = {}
+    for i, x, y, c in pairs:
+        by_prim.setdefault(i, []).append((x, y, c))
+    for i, lst in by_prim.items():
+        prm = Params(scene.subset(np.array([i])), requires_grad=True)
+        px = torch.tensor([float(x) for x, _, _ in lst], dtype=F64)
+        py = torch.tensor([float(y) for _, y, _ in lst], dtype=F64)
+        pe = _eval_pairs(prm, c64, torch.tensor([0]), px, py, density)
+        acc = None
+        for r_, (_, _, c) in enumerate(lst):
+            gr = torch.autograd.grad(pe["t"][r_, 0], list(prm.leaves().values()), retain_graph=True, allow_unused=True)
+            vec = {k: (v if v is not None else torch.zeros_like(l)).detach().numpy()[0] * c
+                   for (k, l), v in zip(prm.leaves().items(), gr)}
+            vec = {k: np.abs(v) for k, v in vec.items()}
+            acc = vec if acc is None else {k: acc[k] + vec[k] for k in acc}
+        bands[i] = acc
+    out = {}
+    prims = np.array(sorted(bands), np.int64)
+    for k in ("mean", "quat", "scale", "curv", "opacity", "sh"):
+        if prims.size:
+            arr = np.stack([bands[i][k] for i in prims])
+            out[k] = (prims, arr.reshape(prims.size, -1) if k == "sh" else arr)
+        else:
+            out[k] = (prims, None)
+    return out
+
+
+def ray_sensitivity(scene, cam, binning: Binning, tiles, grad_images, ref_grads, samples: int = 3,
+                    density: str = "geodesic", extras: bool = False, order: str = "centre"):
+    """How far the exact gradients move under the rounding an FP32 implementation incurs in
+    forming each pair's local ray: the largest change, over `samples` renders whose every
+    (pixel, primitive) pair has its local ray perturbed by independent uniform relative
+    noise of RAY_EPS per component (origin and direction). Near tangency (the ray meeting a
+    steep flank of a strongly curved patch) and where the pixels' contributions to a
+    parameter cancel, the exact gradient itself is defined by FP32 inputs only to this much.
+    Returns {parameter: array like ref_grads}."""
+    spread = {k: np.zeros_like(v) for k, v in ref_grads.items()}
+    for smp in range(samples):
+        r = render(scene, cam, binning, tiles=tiles, grad_images=grad_images, density=density, extras=extras,
+                   order=order, ray_noise_seed=smp + 1)
+        for k in spread:
+            spread[k] = np.maximum(spread[k], np.abs(r["grads"][k] - ref_grads[k]))
+    return spread

@@ -236,12 +236,42 @@ __device__ __forceinline__ float4 conic_box(const Conic& c, float uc, float vc) 
                      floorf(__fmul_rn(__fsub_rn(cy, ey), 0.0625f)), floorf(__fmul_rn(__fadd_rn(cy, ey), 0.0625f)));
 }
 
+// s + e = a + b exactly (Knuth's two-sum), each operation rounded as written.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Row r of the camera-space centre R_cw mu + t_cw as an unevaluated sum hi + lo (about 44
+// significant bits): the products' rounding errors by fma, the sums' by two-sum. The
+// bit-exact FP32 centre of the binning recipe is rounded at every step (an error of a few
+// units in the last place of |mu_c|, which is 1e-4 of a small primitive's size at the
+// workloads' distances); the compositing measures pixel offsets from this one instead.
+__device__ __forceinline__ void centre_cam_df(float mx, float my, float mz, const CamParams& cp, int r, float& hi,
+                                              float& lo) {
+  const float a = cp.Rc[3 * r], b = cp.Rc[3 * r + 1], c = cp.Rc[3 * r + 2];
+  const float p0 = __fmul_rn(a, mx), e0 = __fmaf_rn(a, mx, -p0);
+  const float p1 = __fmul_rn(b, my), e1 = __fmaf_rn(b, my, -p1);
+  const float p2 = __fmul_rn(c, mz), e2 = __fmaf_rn(c, mz, -p2);
+  float s1, w1, s2, w2, s3, w3;
+  two_sum(p0, p1, s1, w1);
+  two_sum(s1, p2, s2, w2);
+  two_sum(s2, cp.tc[r], s3, w3);
+  const float err = __fadd_rn(__fadd_rn(__fadd_rn(e0, e1), __fadd_rn(e2, w1)), __fadd_rn(w2, w3));
+  hi = __fadd_rn(s3, err);
+  lo = __fsub_rn(err, __fsub_rn(hi, s3));
+}
+
 // Projected centre f (x / z) + c as an unevaluated sum hi + lo of floats (about 44
-// significant bits), from error-free transformations: the division's remainder by fma,
-// the product's rounding error by fma, and a two-sum with the principal point.
-__device__ __forceinline__ void centre_df(float x, float z, float f, float c, float& hi, float& lo) {
-  const float qh = x / z;
-  const float ql = fmaf(-qh, z, x) / z;          // x/z = qh + ql (to ~2^-48 relative)
+// significant bits) from the double-float centre (x, z) = (xh + xl, zh + zl), by
+// error-free transformations: the division's remainder by fma, the product's rounding
+// error by fma, and a two-sum with the principal point.
+__device__ __forceinline__ void centre_df(float xh, float xl, float zh, float zl, float f, float c, float& hi,
+                                          float& lo) {
+  const float qh = __fdiv_rn(xh, zh);
+  // x/z - qh = ((xh - qh zh) + (xl - qh zl)) / z
+  const float ql = __fdiv_rn(__fadd_rn(__fmaf_rn(-qh, zh, xh), __fsub_rn(xl, __fmul_rn(qh, zl))), zh);
   const float ph = f * qh;
   const float pl = fmaf(f, qh, -ph) + f * ql;    // f (qh + ql) = ph + pl
   const float sh = ph + c;                       // two-sum of ph and c
@@ -529,9 +559,11 @@ __device__ __forceinline__ uint32_t preprocess_one(int64_t i, const SceneView& s
   // --- projected state (ordinary FP32 arithmetic; FP64 is slow on this GPU) -------
   const float zmu = muc[2];
   const float iz = 1.f / zmu;
-  float pcx_hi, pcx_lo, pcy_hi, pcy_lo;
-  centre_df(muc[0], zmu, cp.fx, cp.cx, pcx_hi, pcx_lo);
-  centre_df(muc[1], zmu, cp.fy, cp.cy, pcy_hi, pcy_lo);
+  float pcx_hi, pcx_lo, pcy_hi, pcy_lo, ch[3], cl[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) centre_cam_df(mx, my, mz, cp, r, ch[r], cl[r]);
+  centre_df(ch[0], cl[0], ch[2], cl[2], cp.fx, cp.cx, pcx_hi, pcx_lo);
+  centre_df(ch[1], cl[1], ch[2], cl[2], cp.fy, cp.cy, pcy_hi, pcy_lo);
   float g[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) g[c] = fmaf(W[c], muc[0], fmaf(W[3 + c], muc[1], W[6 + c] * zmu)) * iz;
