@@ -8,7 +8,14 @@ alpha, depth and normal) through the C ABI, inputs resident in HBM. The scene (4
 and the per-frame instance buffers (~1 GB) are larger than the 129 MB L2, so no flush is
 needed between steps.
 
-Prints ONE JSON line (rank 0). `--impl reference` times the FP64 CPU oracle instead.
+Prints ONE JSON line (rank 0). Beside the headline (value, e2e with every upstream plane
+uploaded and every output plane read back, roofline of the dominant kernel, stages against
+their roofs) it carries: fwd_only (the same frame forward only); configs (the 1,000-quadric
+128x128 and 300k-quadric 1600x1200 workloads, forward and forward + backward, with the
+oracle beside); cpu_baseline (the FP64 oracle on a stratified 32-tile sample of the
+frame, extrapolated); parity (the benchmarked frame's per-output error against the oracle
+on those tiles); variants and serving. `--impl reference` times the FP64 CPU oracle
+instead.
 """
 from __future__ import annotations
 
@@ -150,31 +157,129 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def oracle_sample(sc, cam, n_tiles=1, seed=0):
-    """Time the FP64 oracle (as it stands) on a bounded sample of the workload: the FP32
-    binning of all primitives plus forward and backward of `n_tiles` 16x16 tiles of the
-    frame, extrapolated to the whole frame (binning + tile time x tile count)."""
+def _stratified_tiles(tile_counts, n, seed):
+    """One tile drawn from each of n strata of equal size, the frame's tiles ordered by
+    their list length; returns the drawn tiles and the strata sizes."""
+    import numpy as np
+    order = np.argsort(tile_counts, kind="stable")
+    strata = [st for st in np.array_split(order, min(n, order.size)) if st.size]
+    rng = np.random.default_rng(seed)
+    return [int(st[rng.integers(st.size)]) for st in strata], [int(st.size) for st in strata]
+
+
+def _tile_mask(cam, tiles):
+    import numpy as np
+    TX = (cam.W + 15) // 16
+    m = np.zeros((cam.H, cam.W), bool)
+    for t in tiles:
+        ty, tx = divmod(int(t), TX)
+        m[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16] = True
+    return m
+
+
+def oracle_sample(sc, cam, n_tiles=32, seed=0, keep=False):
+    """Time the FP64 oracle (as it stands) on a bounded, stratified sample of one frame: the
+    FP32 binning of every primitive, then forward + backward (N(0, 1) upstream gradients) of
+    n_tiles 16x16 tiles, one drawn from each of n_tiles equal strata of the frame's tiles
+    ordered by list length. Frame time = binning + per-call set-up + sum over strata of
+    (tiles in the stratum) x (time of its drawn tile): a stratified estimate, extrapolated.
+    keep: also return the oracle's outputs and gradients of those tiles (for the parity
+    block)."""
     import numpy as np
     import torch
     import oracle.qgs_oracle as O
     t0 = time.perf_counter()
     binning = O.bin_fp32(sc, cam, emit=False)
     t_bin = time.perf_counter() - t0
-    rng = np.random.default_rng(seed)
-    ntiles = binning.tiles_x * binning.tiles_y
-    tiles = [int(t) for t in rng.integers(0, ntiles, n_tiles)]
-    g = {"rgb": np.ones((3, cam.H, cam.W)), "alpha": np.ones((cam.H, cam.W)),
-         "depth": np.ones((cam.H, cam.W)), "normal": np.ones((3, cam.H, cam.W))}
+    tiles, sizes = _stratified_tiles(binning.tile_counts, n_tiles, seed)
+    rng = np.random.default_rng(seed + 17)
+    mask = _tile_mask(cam, tiles).astype(np.float64)
+    H, W = cam.H, cam.W
+    g = {"rgb": rng.normal(size=(3, H, W)) * mask, "alpha": rng.normal(size=(H, W)) * mask,
+         "depth": rng.normal(size=(H, W)) * mask, "normal": rng.normal(size=(3, H, W)) * mask}
+    g = {k: v.astype(np.float32).astype(np.float64) for k, v in g.items()}
+    times = {}
     t0 = time.perf_counter()
-    O.render(sc, cam, binning, tiles=tiles, grad_images=g)
+    ref = O.render(sc, cam, binning, tiles=tiles, grad_images=g, timings=times)
     t_tiles = time.perf_counter() - t0
-    frame_s = t_bin + t_tiles / len(tiles) * ntiles
-    return {"value": cam.W * cam.H / frame_s / 1e6, "unit": UNIT, "cores": torch.get_num_threads(),
-            "kind": "oracle",
-            "sample": (f"FP32 binning of all {sc.n} primitives ({t_bin:.2f} s) + FP64 forward+backward of "
-                       f"{len(tiles)} random 16x16 tile(s) ({t_tiles:.2f} s), extrapolated to the "
-                       f"{ntiles}-tile frame"),
-            "frame_s_extrapolated": frame_s}
+    setup = t_tiles - sum(times.values())
+    frame_s = t_bin + setup + sum(n * times[t] for t, n in zip(tiles, sizes))
+    res = {"value": W * H / frame_s / 1e6, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+           "extrapolated": True,
+           "sample": (f"FP32 binning of all {sc.n} primitives ({t_bin:.2f} s) + FP64 forward+backward of "
+                      f"{len(tiles)} 16x16 tiles, one per stratum of the {binning.tiles_x * binning.tiles_y} "
+                      f"tiles ordered by list length ({t_tiles:.2f} s), extrapolated to the frame by stratum "
+                      f"size"),
+           "sample_wall_s": t_bin + t_tiles, "frame_s_extrapolated": frame_s}
+    if keep:
+        res["_keep"] = (binning, tiles, g, ref)
+    return res
+
+
+def oracle_full_frame(sc, cam, seed=0):
+    """The FP64 oracle on a whole frame, forward + backward, timed (no extrapolation)."""
+    import numpy as np
+    import torch
+    import oracle.qgs_oracle as O
+    rng = np.random.default_rng(seed)
+    H, W = cam.H, cam.W
+    g = {"rgb": rng.normal(size=(3, H, W)), "alpha": rng.normal(size=(H, W)), "depth": rng.normal(size=(H, W)),
+         "normal": rng.normal(size=(3, H, W))}
+    t0 = time.perf_counter()
+    O.render(sc, cam, grad_images=g)
+    dt = time.perf_counter() - t0
+    return {"value": W * H / dt / 1e6, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "extrapolated": False, "sample": f"whole {W}x{H} frame, FP32 binning + FP64 forward+backward",
+            "sample_wall_s": dt}
+
+
+def parity_block(sc, cam, ras, ds, kept, dev):
+    """Per-output error of the benchmarked frame against the FP64 oracle on the CPU
+    baseline's sampled tiles (spec precision pattern: the error against the oracle is
+    stated for each output): the GPU's forward planes and, with the same upstream
+    gradients (zero outside those tiles), its parameter gradients. Errors are in units of
+    the bars and as plain maxima; near-threshold pixels are compared to their branches
+    (tests/parity_util)."""
+    import numpy as np
+    import torch
+    from tests.parity_util import TOL_ABS, TOL_DEPTH_REL, compare_grads, compare_images, near_pixels
+    import oracle.qgs_oracle as O
+    binning, tiles, g, ref = kept
+    t0 = time.perf_counter()
+    out = {k: v.detach().cpu().numpy().astype(np.float64) for k, v in ras.forward(ds, cam).items()}
+    gd = {k: torch.from_numpy(v.astype(np.float32)).to(dev) for k, v in g.items()}
+    gg = {k: v.cpu().numpy() for k, v in ras.backward(ds, cam, gd).items()}
+    mask = _tile_mask(cam, tiles)
+    st = compare_images(out, ref, sc, cam, binning, mask)
+    far = mask & ~near_pixels(ref, mask)
+    plain = {k: float(np.abs(out[k] - ref[k])[..., far].max(initial=0.0)) for k in ("rgb", "alpha", "normal")}
+    plain["depth_rel"] = float((np.abs(out["depth"] - ref["depth"]) / np.maximum(np.abs(ref["depth"]), 1e-6))[far]
+                               .max(initial=0.0))
+    touched = np.unique(np.concatenate([O.tile_list(binning, t) for t in tiles])).astype(np.int64)
+    gr, npix, unres = compare_grads(gg, ref, sc, cam, g, binning, mask, touched)
+    grel = {}
+    for k, v in ref["grads"].items():
+        a = v[touched]
+        scale = np.maximum(np.abs(a), 1e-3 * np.abs(a).max(initial=0.0))
+        scale = np.where(scale > 0, scale, 1.0)
+        grel[k] = float((np.abs(np.asarray(gg[k], np.float64).reshape(v.shape)[touched] - a) / scale).max(initial=0.0))
+    return {"tiles": len(tiles), "pixels": int(mask.sum()), "primitives_compared": int(touched.size),
+            "bars": {"rgb_alpha_normal_abs": TOL_ABS, "depth_rel": TOL_DEPTH_REL, "grad_rel": 1e-3},
+            "max_err": plain, "max_err_of_bar": st["errors"], "near_threshold_pixel_frac": st["near_frac"],
+            "near_threshold_worst_of_bar": st["near_worst"], "ambiguous_pixels": st["ambiguous"],
+            "grad_max_rel_err": grel,
+            "grad_of_bar": {k: v["ratio"] for k, v in gr.items()},
+            "grad_plain_of_bar": {k: v["strict"] for k, v in gr.items()},
+            "grad_widened_frac": {k: v["widened"] for k, v in gr.items()},
+            "grad_banded_frac": {k: v["banded"] for k, v in gr.items()},
+            "bracketed_pixels": npix, "wall_s": time.perf_counter() - t0}
+
+
+def _config(sc, cam, world=1):
+    return {"workload": WORKLOAD if sc.n == 3_000_000 else f"unbounded_{sc.n}_1297x840", "primitives": sc.n,
+            "width": cam.W, "height": cam.H,
+            "l2": "inputs larger than L2 (scene 432 MB, instances ~1 GB per frame)",
+            "parallelism": f"replicas x{world}"}
 
 
 def run_reference(args):
@@ -182,21 +287,26 @@ def run_reference(args):
     if rank != 0:
         return 0
     from paper_2411_16392_gb300.scenes import scene_unbounded
-    sc, cam = scene_unbounded(0)
+    sc, cam = scene_unbounded(0, args.prims)
     for w in range(args.warmup):
-        oracle_sample(sc, cam, 1, seed=1000 + w)
+        oracle_sample(sc, cam, 4, seed=1000 + w)
     vals = []
     t0 = time.perf_counter()
     for k in range(args.steps):
-        vals.append(oracle_sample(sc, cam, 1, seed=k))
+        vals.append(oracle_sample(sc, cam, args.ref_tiles, seed=k))
     wall = time.perf_counter() - t0
     frame_s = sum(v["frame_s_extrapolated"] for v in vals) / len(vals)
     value = cam.W * cam.H / frame_s / 1e6
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": frame_s * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "primitives": sc.n, "width": cam.W, "height": cam.H},
+            "config": _config(sc, cam, args.gpus),
+            "extrapolated": True,
+            "timed_wall_s": wall,
+            "note": ("ms_per_step is the oracle's extrapolated time for one whole frame (a stratified "
+                     "estimate from the sampled tiles of each step); the steps' own wall time is timed_wall_s"),
             "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": vals[0]["cores"],
+                             "extrapolated": True,
                              "sample": vals[0]["sample"] + f"; {args.steps} steps, wall {wall:.1f} s"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -320,6 +430,14 @@ def run_gpu(args):
     clk = clocks.stop()
     st_timed = ras.stats()  # stage times of the last timed step
     ms = e0.elapsed_time(e1) / args.steps
+    # forward alone (the same frame, rendered K times)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        ras.forward(ds, cam, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_fwd = e0.elapsed_time(e1) / args.steps
     # stage times averaged over a few more steps (read after each one), then the pair
     # counters of one step
     stage = {"ms_raster_fwd": [], "ms_raster_bwd": [], "ms_preprocess": [], "ms_depth_sort": [], "ms_emit": [],
@@ -346,7 +464,99 @@ def run_gpu(args):
     variants = None
     if rank == 0 and world == 1 and args.variant_steps > 0:
         variants = _variants(args, ds, cam, gout, grads, dev)
-    return _report(args, rank, world, sc, cam, st, stage, clk, ms_max, value, e2e_value, h2d, d2h, variants)
+    legs = None
+    if rank == 0 and world == 1 and args.config_steps > 0:
+        legs = _config_legs(args, dev)
+    return _report(args, rank, world, sc, cam, st, stage, clk, ms_max, value, e2e_value, h2d, d2h, variants,
+                   ms_fwd=ms_fwd, ras=ras, ds=ds, dev=dev, legs=legs)
+
+
+def fp32_peak_tflops(n_sm, sm_mhz):
+    """FP32 FMA throughput: SMs x 128 FP32 lanes x 2 flop per FMA x clock."""
+    return n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def _time_steps(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _config_legs(args, dev):
+    """The two smaller workloads: 1,000 quadrics at 128x128 (the oracle renders it whole)
+    and the 300k-quadric object scene at 1600x1200 (the oracle samples it): forward and
+    forward + backward Mpix/s, pair evaluations/s, the compositing kernels against the FP32
+    roof, and the oracle beside (cpu_baseline)."""
+    import torch
+    from paper_2411_16392_gb300 import _lib as L
+    from paper_2411_16392_gb300.render import DeviceScene, Rasterizer
+    from paper_2411_16392_gb300.scenes import scene_object, scene_small
+    res = {}
+    stream = torch.cuda.current_stream(dev)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    for name, (sc, cam), full in (("small_1k_128x128", scene_small(0, 1000), True),
+                                  ("object_300k_1600x1200", scene_object(0), False)):
+        ds = DeviceScene.from_host(sc, dev)
+        ras = Rasterizer(dev)
+        H, W = cam.H, cam.W
+        gen = torch.Generator(device=dev).manual_seed(7)
+        gout = {"rgb": torch.randn(3, H, W, device=dev, generator=gen),
+                "alpha": torch.randn(H, W, device=dev, generator=gen),
+                "depth": torch.randn(H, W, device=dev, generator=gen),
+                "normal": torch.randn(3, H, W, device=dev, generator=gen)}
+        out = ras.forward(ds, cam)
+        grads = ras.backward(ds, cam, gout)
+        ras.set_pair_counters(False)
+        ms_fwd = _time_steps(lambda: ras.forward(ds, cam, out), args.config_steps, 3, stream)
+        ms_step = _time_steps(lambda: (ras.forward(ds, cam, out), ras.backward(ds, cam, gout, grads)),
+                              args.config_steps, 3, stream)
+        L.check(ras.lib.qgs_set_profiling(ras._ctx, 1), ras._ctx)
+        ras.forward(ds, cam, out)
+        ras.backward(ds, cam, gout, grads)
+        tim = ras.stats()
+        ras.set_pair_counters(True)
+        ras.forward(ds, cam, out)
+        ras.backward(ds, cam, gout, grads)
+        st = ras.stats()
+        L.check(ras.lib.qgs_set_profiling(ras._ctx, 0), ras._ctx)
+        flops_fwd = (st["pair_evals"] * FLOP_EVAL + st["pair_isect"] * FLOP_ISECT + st["pair_hits"] * FLOP_HIT
+                     + st["pair_blended"] * FLOP_BLEND)
+        isect_frac = st["pair_isect"] / max(1, st["pair_evals"])
+        flops_bwd = (st["bwd_pairs"] * (FLOP_EVAL + isect_frac * FLOP_ISECT)
+                     + st["bwd_contrib"] * (FLOP_HIT + FLOP_GRAD))
+        peak = fp32_peak_tflops(n_sm, 2070.0)
+        leg = {"primitives": sc.n, "width": W, "height": H, "visible": st["n_visible"],
+               "instances": st["n_instances"],
+               "fwd_mpix_per_s": H * W / (ms_fwd * 1e-3) / 1e6, "fwd_ms": ms_fwd,
+               "fwd_bwd_mpix_per_s": H * W / (ms_step * 1e-3) / 1e6, "fwd_bwd_ms": ms_step,
+               "pair_evals_per_s_fwd": st["pair_evals"] / (ms_fwd * 1e-3),
+               "raster_fwd": {"ms": tim["ms_raster_fwd"], "frac_fp32_roof":
+                              flops_fwd / (tim["ms_raster_fwd"] * 1e-3) / 1e12 / peak if tim["ms_raster_fwd"] > 0
+                              else None},
+               "raster_bwd": {"ms": tim["ms_raster_bwd"], "frac_fp32_roof":
+                              flops_bwd / (tim["ms_raster_bwd"] * 1e-3) / 1e12 / peak if tim["ms_raster_bwd"] > 0
+                              else None},
+               "roof_note": f"FP32 roof at the maximum clock ({peak:.1f} TFLOP/s, {n_sm} SMs)"}
+        if not args.no_cpu_baseline:
+            if full:
+                leg["cpu_baseline"] = oracle_full_frame(sc, cam)
+            else:
+                cb = oracle_sample(sc, cam, 16)
+                cb.pop("frame_s_extrapolated", None)
+                leg["cpu_baseline"] = cb
+        res[name] = leg
+        ras.close()
+        del ds
+    return res
 
 
 def _variants(args, ds, cam, gout, grads, dev):
@@ -399,21 +609,21 @@ def _e2e(args, ras, ds, cam, gout, grads, out, dev, world, P):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     host_g = {k: v.cpu().pin_memory() for k, v in gout.items()}
-    host_rgb = torch.empty(3, H, W, pin_memory=True)
+    host_out = {k: torch.empty(v.shape, pin_memory=True) for k, v in out.items()}
     dev_g = {k: torch.empty_like(v) for k, v in gout.items()}
     h2d = sum(v.numel() * 4 for v in host_g.values())
-    d2h = host_rgb.numel() * 4
+    d2h = sum(v.numel() * 4 for v in host_out.values())
 
     # the copies run on a side stream: this step's upstream gradients go up while the
-    # forward renders, its image comes down while the backward runs; the step (timed on the
-    # main stream) ends when both copies are complete
+    # forward renders, its four planes come down while the backward runs; the step (timed on
+    # the main stream) ends when both copies are complete
     cs = torch.cuda.Stream(dev)
     ev_g = torch.cuda.Event()
     ev_f = torch.cuda.Event()
     ev_d = torch.cuda.Event()
 
     def e2e_step():
-        cs.wait_stream(stream)  # the previous step is done with dev_g and host_rgb
+        cs.wait_stream(stream)  # the previous step is done with dev_g and host_out
         with torch.cuda.stream(cs):
             for k in dev_g:
                 dev_g[k].copy_(host_g[k], non_blocking=True)
@@ -424,7 +634,8 @@ def _e2e(args, ras, ds, cam, gout, grads, out, dev, world, P):
         ras.backward(ds, cam, dev_g, grads)
         cs.wait_event(ev_f)
         with torch.cuda.stream(cs):
-            host_rgb.copy_(out["rgb"], non_blocking=True)
+            for k in host_out:
+                host_out[k].copy_(out[k], non_blocking=True)
             ev_d.record(cs)
         stream.wait_event(ev_d)
 
@@ -444,7 +655,9 @@ def _e2e(args, ras, ds, cam, gout, grads, out, dev, world, P):
     return e2e_value, h2d, d2h
 
 
-def _report(args, rank, world, sc, cam, st, stage, clk, ms_max, value, e2e_value, h2d, d2h, variants=None):
+def _report(args, rank, world, sc, cam, st, stage, clk, ms_max, value, e2e_value, h2d, d2h, variants=None,
+            ms_fwd=None, ras=None, ds=None, dev=None, legs=None):
+    import torch
     import torch.distributed as dist
     H, W = cam.H, cam.W
     # ---- roofline of the dominant kernel (FP32 ALU bound)
@@ -460,7 +673,8 @@ def _report(args, rank, world, sc, cam, st, stage, clk, ms_max, value, e2e_value
     flops_bwd = (st["bwd_pairs"] * (FLOP_EVAL + isect_frac * FLOP_ISECT)
                  + st["bwd_contrib"] * (FLOP_HIT + FLOP_GRAD))
     sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    peak_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count if dev is not None else 152
+    peak_tflops = fp32_peak_tflops(n_sm, sm_mhz)
     if bwd_ms is not None and (fwd_ms is None or bwd_ms >= fwd_ms):
         dom, dom_ms, dom_flops = "k_raster_bwd", bwd_ms, flops_bwd
     else:
@@ -468,8 +682,8 @@ def _report(args, rank, world, sc, cam, st, stage, clk, ms_max, value, e2e_value
     achieved = dom_flops / (dom_ms * 1e-3) / 1e12 if dom_ms else None
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": (achieved / peak_tflops) if achieved else None, "traffic": _traffic(dom, sc.n),
-                "peak_note": f"FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM clock "
-                             f"sampled during the timed region)",
+                "peak_note": f"FP32 FMA pipe: {n_sm} SMs (read from the device) x 128 lanes x 2 flop x "
+                             f"{sm_mhz:.0f} MHz (median SM clock sampled during the timed region)",
                 "ms_per_launch": dom_ms,
                 "flops_per_launch": dom_flops}
     # ---- every stage against its own roof; the frame against the sum of the roofs
@@ -498,11 +712,10 @@ def _report(args, rank, world, sc, cam, st, stage, clk, ms_max, value, e2e_value
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD if sc.n == 3_000_000 else f"unbounded_{sc.n}_1297x840",
-                       "primitives": sc.n, "width": W, "height": H,
-                       "visible": st["n_visible"], "instances": st["n_instances"],
-                       "l2": "inputs larger than L2 (scene 432 MB, instances ~1 GB per frame)",
-                       "parallelism": f"replicas x{world}"},
+            "config": _config(sc, cam, world),
+            "frame": {"visible": st["n_visible"], "instances": st["n_instances"]},
+            "fwd_only": ({"mpix_per_s": world * H * W / (ms_fwd * 1e-3) / 1e6, "ms": ms_fwd}
+                         if ms_fwd else None),
             "pair_evals_per_s": world * st["pair_evals"] / (ms_max * 1e-3),
             "stage_ms": mean, "counters": {k: st[k] for k in ("pair_evals", "pair_isect", "pair_hits",
                                                                "pair_blended", "grazing_resolves",
@@ -515,9 +728,15 @@ def _report(args, rank, world, sc, cam, st, stage, clk, ms_max, value, e2e_value
         line["variants"] = variants
     if rank == 0 and world == 1 and args.serve_requests > 0:
         line["serving"] = _serving_leg(args)
+    if legs:
+        line["configs"] = legs
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_sample(sc, cam, args.cpu_tiles)
-        line["cpu_baseline"].pop("frame_s_extrapolated", None)
+        cb = oracle_sample(sc, cam, args.cpu_tiles, keep=not args.no_parity)
+        kept = cb.pop("_keep", None)
+        cb.pop("frame_s_extrapolated", None)
+        line["cpu_baseline"] = cb
+        if kept is not None:
+            line["parity"] = parity_block(sc, cam, ras, ds, kept, dev)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -600,7 +819,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-tiles", type=int, default=2)
+    ap.add_argument("--cpu-tiles", type=int, default=32, help="stratified tiles of the oracle's CPU baseline")
+    ap.add_argument("--ref-tiles", type=int, default=4, help="stratified tiles per step of the reference arm")
+    ap.add_argument("--no-parity", action="store_true", help="skip the per-output error block")
+    ap.add_argument("--config-steps", type=int, default=10,
+                    help="timed steps of the 1k and 300k workloads (0: skip those legs)")
     ap.add_argument("--prims", type=int, default=3_000_000,
                     help="primitive count (the benchmark workload is 3,000,000; smaller counts are for profiling)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")

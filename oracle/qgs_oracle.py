@@ -103,6 +103,7 @@ class Binning:
     order: str = "centre"   # "centre": key = centre depth; "hit": per-tile hit depth
     geo: dict | None = None  # float32 mu_c, W, a, b, camera (for per-tile hit keys)
     slabs: dict | None = None  # float32 screen parallelogram per primitive (tile test)
+    tile_counts: np.ndarray | None = None  # int64 [n_tiles] listed primitives per tile
 
 
 def _rect_tiles(rect, prims):
@@ -507,6 +508,7 @@ def bin_fp32(scene, cam, emit: bool = True, order: str = "centre") -> Binning:
         slabs.update(slabs_conic)
         # tiles of the rectangle that meet the parallelogram (row-major), counted in chunks
         count = np.zeros(N, np.int64)
+        tile_counts = np.zeros(TX * TY, np.int64)
         vidx = np.nonzero(vis)[0]
         per = ((rect[vidx, 1] - rect[vidx, 0] + 1).astype(np.int64) * (rect[vidx, 3] - rect[vidx, 2] + 1))
         start = 0
@@ -519,6 +521,7 @@ def bin_fp32(scene, cam, emit: bool = True, order: str = "centre") -> Binning:
             p_, tx_, ty_ = _rect_tiles(rect, vidx[start:stop])
             ok = _tile_pass(slabs, p_, tx_, ty_)
             count += np.bincount(p_[ok], minlength=N)
+            tile_counts += np.bincount((ty_[ok] * TX + tx_[ok]).astype(np.int64), minlength=TX * TY)
             start = stop
         vis &= count > 0
         rect[~vis] = 0
@@ -531,7 +534,7 @@ def bin_fp32(scene, cam, emit: bool = True, order: str = "centre") -> Binning:
                    img_w=cam.W, img_h=cam.H)
     elif order != "centre":
         raise ValueError(order)
-    bn = Binning(vis, zbits, rect, count, None, None, None, TX, TY, pix_bbox, order, geo, slabs)
+    bn = Binning(vis, zbits, rect, count, None, None, None, TX, TY, pix_bbox, order, geo, slabs, tile_counts)
     if not emit:
         return bn
     # instances in primitive order, tiles row-major inside each rectangle (those that meet
@@ -560,7 +563,7 @@ def bin_fp32(scene, cam, emit: bool = True, order: str = "centre") -> Binning:
     starts = np.searchsorted(tiles_sorted, np.arange(ntiles), side="left")
     ends = np.searchsorted(tiles_sorted, np.arange(ntiles), side="right")
     ranges = np.stack([starts, ends], 1).astype(np.int64)
-    return Binning(vis, zbits, rect, count, keys, vals, ranges, TX, TY, pix_bbox, order, geo, slabs)
+    return Binning(vis, zbits, rect, count, keys, vals, ranges, TX, TY, pix_bbox, order, geo, slabs, tile_counts)
 
 
 def tile_list(binning: Binning, tile: int) -> np.ndarray:
@@ -1158,7 +1161,7 @@ def _tile_pixels(cam, tile, TX):
 
 
 def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=None, density="geodesic",
-           extras=False, order="centre", ray_noise_seed=None):
+           extras=False, order="centre", ray_noise_seed=None, timings: dict | None = None):
     """Render the full image (or the listed tiles). Returns a dict of numpy arrays:
     rgb [3,H,W], alpha [H,W], depth [H,W], normal [3,H,W], margin [H,W], n_eval [H,W],
     n_contrib [H,W], T_final [H,W]; with `extras` also curvature, distortion,
@@ -1171,7 +1174,8 @@ def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=N
     by centre depth) or "stp" (StopThePop: per-tile hit depth, then per-pixel resorting
     in a buffer of RESORT entries). ray_noise_seed: perturb every pair's local ray by
     uniform relative noise of RAY_EPS per component, drawn from a generator seeded by
-    (seed, tile, list position) (see ray_sensitivity)."""
+    (seed, tile, list position) (see ray_sensitivity). timings: if a dict, receives the
+    seconds spent on each rendered tile (forward and, with grad_images, backward)."""
     if binning is None:
         binning = bin_fp32(scene, cam, order="hit" if order == "stp" else "centre")
     comp = _composite_resort if order == "stp" else _composite
@@ -1193,7 +1197,9 @@ def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=N
     g = None
     if want_grad:
         g = {k: torch.tensor(np.asarray(v, np.float64)) for k, v in grad_images.items()}
+    import time as _time
     for tile in tiles:
+        t_start = _time.perf_counter()
         if binning.ranges is not None:
             s, e = binning.ranges[tile]
             lst = binning.vals[s:e]
@@ -1224,6 +1230,8 @@ def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=N
                         loss = loss + (g[k][ys, xs] * r[k]).sum()
                 if loss.requires_grad:
                     loss.backward()
+        if timings is not None:
+            timings[int(tile)] = _time.perf_counter() - t_start
         out["rgb"][:, ys, xs] = r["rgb"].detach().numpy().T
         out["alpha"][ys, xs] = r["alpha"].detach().numpy()
         out["depth"][ys, xs] = r["depth"].detach().numpy()
