@@ -203,7 +203,7 @@ def oracle_sample(sc, cam, n_tiles=32, seed=0, keep=False):
     ref = O.render(sc, cam, binning, tiles=tiles, grad_images=g, timings=times)
     t_tiles = time.perf_counter() - t0
     setup = t_tiles - sum(times.values())
-    frame_s = t_bin + setup + sum(n * times[t] for t, n in zip(tiles, sizes))
+    frame_s = t_bin + setup + sum(n * times.get(t, 0.0) for t, n in zip(tiles, sizes))
     res = {"value": W * H / frame_s / 1e6, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
            "extrapolated": True,
            "sample": (f"FP32 binning of all {sc.n} primitives ({t_bin:.2f} s) + FP64 forward+backward of "
@@ -273,6 +273,53 @@ def parity_block(sc, cam, ras, ds, kept, dev):
             "grad_widened_frac": {k: v["widened"] for k, v in gr.items()},
             "grad_banded_frac": {k: v["banded"] for k, v in gr.items()},
             "bracketed_pixels": npix, "wall_s": time.perf_counter() - t0}
+
+
+def serving_parity(dev, n_req=4, n_pix=24, seed=3):
+    """Per-output error of served requests against the FP64 oracle (the mixed-resolution
+    serving workload): n_req forward requests of the 1M-quadric serving scene at the serving
+    resolutions, submitted together so that they render as one batch, each checked at n_pix
+    sampled pixels against the oracle's branches (tests/parity_util.check_pixels, without
+    asserting)."""
+    import numpy as np
+    from tests.parity_util import _gpu_pixel, _pixel_errors
+    import oracle.qgs_oracle as O
+    from paper_2411_16392_gb300.render import DeviceScene
+    from paper_2411_16392_gb300.scenes import orbit_camera, serving_scene
+    from paper_2411_16392_gb300.serve import Server, host_planes
+    t0 = time.perf_counter()
+    sc = serving_scene(0, 1_000_000)
+    ds = DeviceScene.from_host(sc, dev)
+    rng = np.random.default_rng(seed)
+    cams = [orbit_camera(rng) for _ in range(n_req)]
+    srv = Server(dev.index, budget_bytes=64 << 30, slots=1, queue=64, batch=n_req)
+    sid = srv.load_scene(ds)
+    tickets = [srv.submit(sid, c) for c in cams]
+    outs = [srv.wait(t, c, out=host_planes(c)) for t, c in zip(tickets, cams)]
+    st = srv.stats()
+    srv.close()
+    worst, unmatched, per = {}, 0, []
+    for cam, out in zip(cams, outs):
+        binning = O.bin_fp32(sc, cam, emit=False)
+        pix = [(int(x), int(y)) for x, y in zip(rng.integers(0, cam.W, n_pix), rng.integers(0, cam.H, n_pix))]
+        br = O.bracket_pixels(sc, cam, pix, binning)
+        e_req = 0.0
+        for (x, y), it in zip(pix, br):
+            gv = _gpu_pixel(out, x, y, False)
+            best = min(_pixel_errors(gv, leaf, False) for leaf in it["leaves"])
+            unmatched += best > 1.0
+            e_req = max(e_req, best)
+            leaf = min(it["leaves"], key=lambda l: _pixel_errors(gv, l, False))
+            for k, lim, rel in (("rgb", 1e-4, False), ("alpha", 1e-4, False), ("normal", 1e-4, False),
+                                ("depth", 1e-4, True)):
+                d = float(np.max(np.abs(np.asarray(gv[k], np.float64) - np.asarray(leaf[k]).reshape(np.shape(gv[k])))))
+                if rel:
+                    d /= max(abs(float(leaf[k][0])), 1e-6)
+                worst[k] = max(worst.get(k, 0.0), d)
+        per.append({"width": cam.W, "height": cam.H, "worst_of_bar": e_req})
+    return {"workload": "serving_1m_mixed_res", "requests": n_req, "batched_together": int(st["max_batch"]),
+            "pixels_per_request": n_pix, "max_err": {("depth_rel" if k == "depth" else k): v for k, v in worst.items()},
+            "ambiguous_pixels": unmatched, "requests_detail": per, "wall_s": time.perf_counter() - t0}
 
 
 def _config(sc, cam, world=1):
@@ -737,6 +784,8 @@ def _report(args, rank, world, sc, cam, st, stage, clk, ms_max, value, e2e_value
         line["cpu_baseline"] = cb
         if kept is not None:
             line["parity"] = parity_block(sc, cam, ras, ds, kept, dev)
+            if args.serve_requests > 0:
+                line["parity"]["serving"] = serving_parity(dev)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -771,12 +820,13 @@ def _serving_leg(args):
         r["batched_config"] = {"slots": args.serve_slots, "max_batch": args.serve_batch}
         res["rates"].append(r)
     del ds
-    if args.serve_mixed_rate > 0:
-        res["mixed"] = _serving_mixed_leg(args, dev)
+    rates = [r for r in args.serve_mixed_rate if r > 0]
+    if rates:
+        res["mixed"] = [_serving_mixed_leg(args, dev, r) for r in rates]
     return res
 
 
-def _serving_mixed_leg(args, dev):
+def _serving_mixed_leg(args, dev, rate):
     """Six resident scenes of 0.2/0.5/1/2/3/4 M quadrics; each request picks a scene
     uniformly; 80 % are forward views at the serving resolutions, 20 % forward + backward
     at 1297x840 with N(0, 1) upstream gradients; HBM-budget admission. Plain one-at-a-time
@@ -796,7 +846,7 @@ def _serving_mixed_leg(args, dev):
             jobs.append((si, orbit_camera(rng, res=(1297, 840)), True))
         else:
             jobs.append((si, orbit_camera(rng), False))
-    gaps = rng.exponential(1.0 / args.serve_mixed_rate, n)
+    gaps = rng.exponential(1.0 / rate, n)
     gen = torch.Generator().manual_seed(2)
     grad_sets = []
     for _ in range(4):
@@ -804,7 +854,7 @@ def _serving_mixed_leg(args, dev):
              "depth": torch.randn(840, 1297, generator=gen), "normal": torch.randn(3, 840, 1297, generator=gen)}
         grad_sets.append({k: v.pin_memory() for k, v in g.items()})
     res = {"workload": "serving_6_scenes_0.2-4m_80fwd_20fwdbwd", "requests": n,
-           "arrival_rate_per_s": args.serve_mixed_rate, "backward_share": 0.2}
+           "arrival_rate_per_s": rate, "backward_share": 0.2}
     for name, slots, batch in (("one_at_a_time", 1, 1), ("batched", args.serve_slots, args.serve_batch)):
         res[name] = serve_measure(dev.index, scenes, jobs, gaps, slots, batch, grad_sets=grad_sets)
     res["batched_config"] = {"slots": args.serve_slots, "max_batch": args.serve_batch}
@@ -828,14 +878,15 @@ def main():
                     help="primitive count (the benchmark workload is 3,000,000; smaller counts are for profiling)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--serve-requests", type=int, default=600, help="requests per serving run (0: skip)")
-    ap.add_argument("--serve-rate", type=lambda v: [float(x) for x in v.split(",")], default=[200.0, 1000.0],
+    ap.add_argument("--serve-rate", type=lambda v: [float(x) for x in v.split(",")],
+                    default=[200.0, 400.0, 500.0, 1000.0, 2000.0],
                     help="Poisson arrival rates, requests/s (comma-separated)")
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-batch", type=int, default=8, help="most views per batch in the batched leg")
     ap.add_argument("--variant-steps", type=int, default=5,
                     help="timed steps of each optional renderer path (extra channels, Euclid, StopThePop; 0: skip)")
-    ap.add_argument("--serve-mixed-rate", type=float, default=100.0,
-                    help="arrival rate of the six-scene forward/backward serving leg (0: skip)")
+    ap.add_argument("--serve-mixed-rate", type=lambda v: [float(x) for x in v.split(",")], default=[100.0, 250.0],
+                    help="arrival rates of the six-scene forward/backward serving leg (comma-separated; 0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

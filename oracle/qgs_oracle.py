@@ -1180,7 +1180,6 @@ def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=N
         binning = bin_fp32(scene, cam, order="hit" if order == "stp" else "centre")
     comp = _composite_resort if order == "stp" else _composite
     want_grad = grad_images is not None
-    prm = Params(scene, requires_grad=want_grad)
     c64 = CamF64(cam)
     H, W = cam.H, cam.W
     out = dict(rgb=np.zeros((3, H, W)), alpha=np.zeros((H, W)), depth=np.zeros((H, W)),
@@ -1194,21 +1193,28 @@ def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=N
     TX = binning.tiles_x
     if tiles is None:
         tiles = range(binning.tiles_x * binning.tiles_y)
+    tiles = list(tiles)
+    # the tiles' lists, and parameters only for the primitives they hold (local indices)
+    lists = {}
+    for tile in tiles:
+        if binning.ranges is not None:
+            s_, e_ = binning.ranges[tile]
+            lists[tile] = np.asarray(binning.vals[s_:e_], np.int64)
+        else:
+            lists[tile] = np.asarray(tile_list(binning, tile), np.int64)
+    used = np.unique(np.concatenate([np.zeros(0, np.int64)] + list(lists.values())))
+    prm = Params(scene.subset(used), requires_grad=want_grad)
     g = None
     if want_grad:
         g = {k: torch.tensor(np.asarray(v, np.float64)) for k, v in grad_images.items()}
     import time as _time
     for tile in tiles:
         t_start = _time.perf_counter()
-        if binning.ranges is not None:
-            s, e = binning.ranges[tile]
-            lst = binning.vals[s:e]
-        else:
-            lst = tile_list(binning, tile)
+        lst = lists[tile]
         xs, ys = _tile_pixels(cam, tile, TX)
         if lst.size == 0:
             continue
-        idx = torch.from_numpy(lst.astype(np.int64))
+        idx = torch.from_numpy(np.searchsorted(used, lst))
         px = torch.tensor(xs, dtype=F64)
         py = torch.tensor(ys, dtype=F64)
         noise = None
@@ -1238,7 +1244,7 @@ def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=N
         out["normal"][:, ys, xs] = r["normal"].detach().numpy().T
         out["margin"][ys, xs] = r["margin"].numpy()
         out["cond"][ys, xs] = r["cond"].numpy()
-        np.minimum.at(out["prim_cond"], idx.numpy(), r["list_cond"].numpy())
+        np.minimum.at(out["prim_cond"], lst, r["list_cond"].numpy())
         out["n_eval"][ys, xs] = r["n_eval"].numpy()
         out["n_contrib"][ys, xs] = r["n_contrib"].numpy()
         out["T_final"][ys, xs] = r["T_final"].detach().numpy()
@@ -1249,7 +1255,9 @@ def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=N
         grads = {}
         for k, v in prm.leaves().items():
             gr = v.grad if v.grad is not None else torch.zeros_like(v)
-            grads[k] = gr.numpy().copy()
+            full = np.zeros((scene.n,) + tuple(v.shape[1:]))
+            full[used] = gr.numpy()
+            grads[k] = full
         grads["sh"] = grads["sh"].reshape(-1, 48)
         out["grads"] = grads
     out["binning"] = binning
@@ -1262,7 +1270,6 @@ def render_pixels(scene, cam, pixels, binning: Binning | None = None, density="g
     the full image). Returns dict of arrays indexed like `pixels`."""
     if binning is None:
         binning = bin_fp32(scene, cam, order="hit" if order == "stp" else "centre")
-    prm = Params(scene)
     c64 = CamF64(cam)
     TX = binning.tiles_x
     keys = ["rgb", "alpha", "depth", "normal", "margin", "cond", "n_eval", "n_contrib"]
@@ -1279,7 +1286,8 @@ def render_pixels(scene, cam, pixels, binning: Binning | None = None, density="g
             if tile not in lists:
                 lists[tile] = tile_list(binning, tile)
             lst = lists[tile]
-        idx = torch.from_numpy(lst.astype(np.int64))
+        prm = Params(scene.subset(np.asarray(lst, np.int64)))
+        idx = torch.arange(len(lst))
         with torch.no_grad():
             comp = _composite_resort if order == "stp" else _composite
             r = comp(prm, c64, idx, torch.tensor([float(x)], dtype=F64),
@@ -1376,19 +1384,22 @@ def _order_outputs(pe, order, extras, margin=BRACKET_MARGIN):
     return out
 
 
-def _list_orders(pe, perm, margin):
+def _list_orders(pe, perm, margin, orig=None):
     """Blend orders of the list order `perm` (the base ordering: front to back in list
     order) for every place where the pixel may stop: the transmittance rule of Sec. 4.1
     (stop before a pair that would take T below 1e-4), taken both ways where T after the
     pair is within `margin` of the threshold. Returns [(order, n_contrib)], the nominal
-    branch (every decision taken as computed) first."""
+    branch (every decision taken as computed) first; n_contrib counts positions of the
+    original list `orig` (positions of the pairs kept, default the identity)."""
     al = pe["alpha"][0].detach().tolist()
     v = pe["valid"][0].tolist()
     res, order, T = [], [], 1.0
     nominal = None
 
     def leaf():
-        return (list(order), (max(perm.index(k) for k in order) + 1) if order else 0)
+        if not order:
+            return (list(order), 0)
+        return (list(order), (max(orig[k] for k in order) if orig is not None else max(perm.index(k) for k in order)) + 1)
 
     for j in perm:
         if not v[j]:
@@ -1537,12 +1548,10 @@ def bracket_pixels(scene, cam, pixels, binning: Binning | None = None, list_free
                 item["grads"].append(None)
             res.append(item)
             continue
-        prm = Params(scene.subset(lst), requires_grad=want_grad)
-        idx = torch.arange(L)
         px = torch.tensor([float(x)], dtype=F64)
         py = torch.tensor([float(y)], dtype=F64)
         with torch.no_grad():
-            pe0 = _eval_pairs(prm, c64, idx, px, py, density)
+            pe0 = _eval_pairs(Params(scene.subset(lst)), c64, torch.arange(L), px, py, density)
         # per pair: the decisions within the margin; where a decision can flip, the pair may
         # contribute (or not) on some branch
         per_pair = {}
@@ -1552,6 +1561,34 @@ def bracket_pixels(scene, cam, pixels, binning: Binning | None = None, list_free
         maybe = pe0["valid"][0].clone()
         for j in per_pair:
             maybe[j] = True
+        # A pair with no hit and no decision near its threshold contributes nothing on any
+        # branch (its own decisions alone decide whether it contributes): keep the others.
+        keep = torch.nonzero(maybe).flatten()
+        if list_free:
+            near = float(np.float32(cam.near))
+            keep = torch.unique(torch.cat([keep, torch.from_numpy(np.nonzero(np.abs(zc - near) / near < margin)[0])]))
+        remap = {int(j): q for q, j in enumerate(keep.tolist())}
+        orig_pos = keep.tolist()
+        per_pair = {remap[j]: v for j, v in per_pair.items()}
+        lst = lst[keep.numpy()]
+        if zc is not None:
+            zc = zc[keep.numpy()]
+        L = int(lst.size)
+        if want_grad:
+            item["prims"] = lst
+        pe0 = {k: (v[:, keep] if torch.is_tensor(v) and v.dim() == 2 else v) for k, v in pe0.items() if k not in
+               ("margins", "rgb", "normal", "roots", "pick_near")}
+        maybe = maybe[keep]
+        if L == 0:
+            item["leaves"].append({k: np.zeros(OUT_LEN.get(k, 1)) for k in outkeys})
+            item["groups"].append("d")
+            item["n_contrib"].append(0)
+            if want_grad:
+                item["grads"].append(None)
+            res.append(item)
+            continue
+        prm = Params(scene.subset(lst), requires_grad=want_grad)
+        idx = torch.arange(L)
         if list_free:  # a centre at the near plane may be culled or not
             near = float(np.float32(cam.near))
             for j in np.nonzero(np.abs(zc - near) / near < margin)[0].tolist():
@@ -1610,7 +1647,7 @@ def bracket_pixels(scene, cam, pixels, binning: Binning | None = None, list_free
                         item["resolved"] = False
                         branches = _resort_orders(pe, RESORT, 0.0, 1)
                 else:
-                    branches = _list_orders(pe, perm, margin)
+                    branches = _list_orders(pe, perm, margin, orig_pos)
                 if group != "d":
                     branches = branches[:1]
                 for od, nc in branches:
@@ -1663,14 +1700,15 @@ def graze_bands(scene, cam, binning: Binning, tiles, grad_images, density: str =
     comp = _composite_resort if order == "stp" else _composite
     c64 = CamF64(cam)
     g = {k: torch.tensor(np.asarray(v, np.float64)) for k, v in grad_images.items()}
-    prm_nograd = Params(scene)
     pairs = []   # (primitive, x, y, kappa * |dL/dt|)
     for tile in tiles:
         lst = tile_list(binning, tile) if binning.ranges is None else binning.vals[slice(*binning.ranges[tile])]
         if len(lst) == 0:
             continue
+        lst = np.asarray(lst, np.int64)
+        prm_nograd = Params(scene.subset(lst))
         xs, ys = _tile_pixels(cam, tile, binning.tiles_x)
-        idx = torch.from_numpy(np.asarray(lst, np.int64))
+        idx = torch.arange(lst.size)
         px = torch.tensor(xs, dtype=F64)
         py = torch.tensor(ys, dtype=F64)
         collect = []
@@ -1695,7 +1733,7 @@ def graze_bands(scene, cam, binning: Binning, tiles, grad_images, density: str =
             sel = (cond >= lo) & (cond < hi) & pe["valid"]
             for pi, jj in torch.nonzero(sel).tolist():
                 kap = shift / (2.0 * float(cond[pi, jj]))
-                pairs.append((int(idx[c0 + jj]), int(xs[pi]), int(ys[pi]), kap * abs(float(dLdt[pi, jj]))))
+                pairs.append((int(lst[c0 + jj]), int(xs[pi]), int(ys[pi]), kap * abs(float(dLdt[pi, jj]))))
     bands = {}
     by_prim = {}
     for i, x, y, c in pairs:
@@ -1739,4 +1777,21 @@ def ray_sensitivity(scene, cam, binning: Binning, tiles, grad_images, ref_grads,
                    order=order, ray_noise_seed=smp + 1)
         for k in spread:
             spread[k] = np.maximum(spread[k], np.abs(r["grads"][k] - ref_grads[k]))
+    return spread
+
+
+def ray_sensitivity_images(scene, cam, binning: Binning, tiles, ref, samples: int = 3, density: str = "geodesic",
+                           extras: bool = False, order: str = "centre"):
+    """The forward counterpart of ray_sensitivity: the largest change of each output plane,
+    per pixel, over `samples` renders of `tiles` whose every pair's local ray is perturbed
+    by FP32-sized rounding (RAY_EPS per component). Near a grazing ray the hit point, its
+    depth and its normal move by about e / sqrt(D) under a rounding e of D. Returns a dict
+    of planes like ref's."""
+    keys = OUT_KEYS + (("curvature", "distortion") if extras else ())
+    spread = {k: np.zeros_like(ref[k]) for k in keys}
+    for smp in range(samples):
+        r = render(scene, cam, binning, tiles=tiles, density=density, extras=extras, order=order,
+                   ray_noise_seed=smp + 101)
+        for k in keys:
+            spread[k] = np.maximum(spread[k], np.abs(r[k] - ref[k]))
     return spread

@@ -111,51 +111,6 @@ __global__ void k_emit(int64_t n, const uint32_t* __restrict__ sidx, const uint3
 
 constexpr int kEmitPerWarp = 8;  // primitives per warp in the emission kernels
 
-// Several views of one scene (render_forward_batch): entry pid = v * n_per_view + i, its
-// tiles numbered from the view's base (vt[v] = (tiles_x, tile base)); depth order only. The
-// tiles of each rectangle that meet the entry's screen bounds, replayed from the tile-count
-// pass's masks where it stored them, else tested against tslab with the view's image size.
-__global__ void k_emit_views(int64_t n, const uint32_t* __restrict__ sidx, const uint32_t* __restrict__ count,
-                             const short4* __restrict__ rect, const uint32_t* __restrict__ offs, uint32_t n_per_view,
-                             const int2* __restrict__ vt, const CamParams* __restrict__ cps,
-                             const TileSlab* __restrict__ tslab, const uint32_t* __restrict__ tbits,
-                             const uint32_t* __restrict__ tbits_off, uint64_t* __restrict__ keys,
-                             const uint32_t* err) {
-  if (sort_failed(err)) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t j0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kEmitPerWarp;
-  const int64_t j = j0 + lane;
-  uint32_t pid = 0, c = 0, off = 0, wo = kNoTileBits;
-  int view = 0, rxy = 0, rzw = 0;
-  if (lane < kEmitPerWarp && j < n) {  // lane k fetches entry k's data up front
-    pid = sidx[j];
-    c = count[pid];
-    if (c) {
-      off = offs[j];
-      const short4 rc = rect[pid];
-      rxy = (int)(((uint32_t)(uint16_t)rc.y << 16) | (uint16_t)rc.x);
-      rzw = (int)(((uint32_t)(uint16_t)rc.w << 16) | (uint16_t)rc.z);
-      view = (int)(pid / n_per_view);
-      if (tbits) wo = tbits_off[pid];
-    }
-  }
-  for (int k = 0; k < kEmitPerWarp; ++k) {
-    const uint32_t cc = __shfl_sync(0xffffffffu, c, k);
-    if (!cc) continue;
-    const uint32_t pp = __shfl_sync(0xffffffffu, pid, k);
-    const uint32_t oo = __shfl_sync(0xffffffffu, off, k);
-    const uint32_t wk = __shfl_sync(0xffffffffu, wo, k);
-    const int vk = __shfl_sync(0xffffffffu, view, k);
-    const int a = __shfl_sync(0xffffffffu, rxy, k), b = __shfl_sync(0xffffffffu, rzw, k);
-    const short4 rk = make_short4((short)(a & 0xFFFF), (short)(a >> 16), (short)(b & 0xFFFF), (short)(b >> 16));
-    const int2 t = vt[vk];
-    warp_tiles(rk, tslab ? tslab + pp : nullptr, cps[vk].W, cps[vk].H, [&](uint32_t e, int tx, int ty) {
-      const uint32_t tile = (uint32_t)t.y + (uint32_t)ty * (uint32_t)t.x + (uint32_t)tx;
-      keys[(size_t)oo + e] = ((uint64_t)tile << 32) | pp;
-    }, nullptr, wk != kNoTileBits ? tbits + wk : nullptr);
-  }
-}
-
 // Visible primitives in index order: position vpos[i] (exclusive scan of the visibility
 // flags) receives the depth key and the index.
 __global__ void k_compact(int64_t n, const uint32_t* __restrict__ count, const uint32_t* __restrict__ zkey,
@@ -219,6 +174,52 @@ __global__ void k_emit_packed(int64_t V, const uint32_t* __restrict__ sidx, cons
     const short4 rk = make_short4((short)(a & 0xFFFF), (short)(a >> 16), (short)(b & 0xFFFF), (short)(b >> 16));
     warp_tiles(rk, tslab ? tslab + pp : nullptr, W, H, [&](uint32_t e, int tx, int ty) {
       const uint32_t tile = (uint32_t)ty * (uint32_t)tiles_x + (uint32_t)tx;
+      keys[(size_t)oo + e] = ((K)tile << rb) | (K)rr;
+    }, nullptr, wk != kNoTileBits ? tbits + wk : nullptr);
+  }
+}
+
+// Several views of one scene (render_forward_batch): the tile instances of the visible
+// (view, primitive) entries in depth order, packed as (global tile << rb) | depth rank like
+// k_emit_packed; entry pid = v * n_per_view + i is of view v, whose tiles are numbered from
+// its base (vt[v] = (tiles_x, tile base)) and whose image size is in cps[v].
+template <typename K>
+__global__ void k_emit_packed_views(int64_t V, const uint32_t* __restrict__ sidx,
+                                    const uint32_t* __restrict__ cnt_sorted, const short4* __restrict__ rect,
+                                    const uint32_t* __restrict__ offs, uint32_t n_per_view,
+                                    const int2* __restrict__ vt, const CamParams* __restrict__ cps,
+                                    const TileSlab* __restrict__ tslab, const uint32_t* __restrict__ tbits,
+                                    const uint32_t* __restrict__ tbits_off, int rb, K* __restrict__ keys,
+                                    const uint32_t* err) {
+  if (sort_failed(err)) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t r0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kEmitPerWarp;
+  const int64_t r = r0 + lane;
+  uint32_t c = 0, off = 0, pid = 0, wo = kNoTileBits;
+  int view = 0, rxy = 0, rzw = 0;
+  if (lane < kEmitPerWarp && r < V) {  // lane k fetches entry k's data up front
+    c = cnt_sorted[r];
+    off = offs[r];
+    pid = sidx[r];
+    const short4 rc = rect[pid];
+    rxy = (int)(((uint32_t)(uint16_t)rc.y << 16) | (uint16_t)rc.x);
+    rzw = (int)(((uint32_t)(uint16_t)rc.w << 16) | (uint16_t)rc.z);
+    view = (int)(pid / n_per_view);
+    if (tbits) wo = tbits_off[pid];
+  }
+  for (int k = 0; k < kEmitPerWarp; ++k) {
+    const uint32_t cc = __shfl_sync(0xffffffffu, c, k);
+    if (!cc) continue;
+    const uint32_t rr = (uint32_t)(r0 + k);
+    const uint32_t oo = __shfl_sync(0xffffffffu, off, k);
+    const uint32_t pp = __shfl_sync(0xffffffffu, pid, k);
+    const uint32_t wk = __shfl_sync(0xffffffffu, wo, k);
+    const int vk = __shfl_sync(0xffffffffu, view, k);
+    const int a = __shfl_sync(0xffffffffu, rxy, k), b = __shfl_sync(0xffffffffu, rzw, k);
+    const short4 rk = make_short4((short)(a & 0xFFFF), (short)(a >> 16), (short)(b & 0xFFFF), (short)(b >> 16));
+    const int2 t = vt[vk];
+    warp_tiles(rk, tslab ? tslab + pp : nullptr, cps[vk].W, cps[vk].H, [&](uint32_t e, int tx, int ty) {
+      const uint32_t tile = (uint32_t)t.y + (uint32_t)ty * (uint32_t)t.x + (uint32_t)tx;
       keys[(size_t)oo + e] = ((K)tile << rb) | (K)rr;
     }, nullptr, wk != kNoTileBits ? tbits + wk : nullptr);
   }
@@ -997,51 +998,50 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
   SortTemp tmp = sort_temp(ctx);
 
   const int64_t launches0 = launch_counter();
+  QGS_CU(ctx->vpos.reserve(n1 + 1), "alloc visibility scan");
   QGS_CU(cudaMemcpyAsync(ctx->vdesc.p, ctx->h_vdesc, vbytes, cudaMemcpyHostToDevice, st), "upload views");
   QGS_CU(cudaEventRecord(ctx->vdesc_done, st), "event");
   QGS_CU(cudaMemsetAsync(ctx->dcount.p, 0, sizeof(uint32_t) * 3, st), "memset counters");
   SceneView sv{scene->mean, scene->quat, scene->scale, scene->curv, scene->opacity, scene->sh};
   if (N > 0) {
     k_preprocess_views<<<dim3(pre_blocks(N), (unsigned)V), 256, 0, st>>>(N, sv, d_cp, ctx->state.p, ctx->count.p,
-                                                                   ctx->zkey.p, ctx->idx.p, ctx->rect.p, nullptr,
+                                                                   ctx->zkey.p, nullptr, ctx->rect.p, nullptr,
                                                                    ctx->tslab.p);
     ++launch_counter();
     QGS_CU(cudaGetLastError(), "k_preprocess_views");
     // keep each view's rectangle tiles that meet the parallelogram and the conic
     k_count_tiles<<<dim3((unsigned)((N + kCountBlock - 1) / kCountBlock), (unsigned)V), kCountBlock, 0, st>>>(
-        N, ctx->tslab.p, 0, 0, ctx->count.p, ctx->rect.p, ctx->zkey.p, nullptr, ctx->dcount.p,
+        N, ctx->tslab.p, 0, 0, ctx->count.p, ctx->rect.p, ctx->zkey.p, ctx->vpos.p, ctx->dcount.p,
         tb_on ? ctx->tbits.p : nullptr, ctx->tbits_off.p, cap_words, d_cp);
     ++launch_counter();
     QGS_CU(cudaGetLastError(), "k_count_tiles");
   }
-  // the totals' read-back; the depth sort, gather and scan (sized by the batch, not by
-  // the totals) are enqueued before the host waits, so they run during the read-back
+  // the totals' read-back; the compaction of the visible (view, primitive) entries (index
+  // order), which needs no total, runs during it
   QGS_CU(cudaMemcpyAsync(ctx->h_total, ctx->dcount.p, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "totals");
   if (!ctx->totals_ready) QGS_CU(cudaEventCreateWithFlags(&ctx->totals_ready, cudaEventDisableTiming), "event");
   QGS_CU(cudaEventRecord(ctx->totals_ready, st), "event");
-  cudaError_t e = cudaSuccess;
-  const bool fl0 = radix_sort_u32_pairs(ctx->zkey.p, ctx->idx.p, ctx->zkey2.p, ctx->idx2.p, VN, 0, 32, tmp, st, &e);
-  QGS_CU(e, "depth sort");
-  const uint32_t* sidx = fl0 ? ctx->idx2.p : ctx->idx.p;
   if (VN > 0) {
-    k_gather_u32<<<nblk(VN), 256, 0, st>>>(VN, sidx, ctx->count.p, ctx->cnt_sorted.p, tmp.err);
+    QGS_CU(scan_exclusive_u32(ctx->vpos.p, ctx->vpos.p, VN, ctx->scan_tmp.p, ctx->scan_tmp.cap, st), "scan");
+    k_compact<<<nblk(VN), 256, 0, st>>>(VN, ctx->count.p, ctx->zkey.p, ctx->vpos.p, ctx->zkey2.p, ctx->idx2.p);
     ++launch_counter();
-    QGS_CU(cudaGetLastError(), "gather");
+    QGS_CU(cudaGetLastError(), "compact");
   }
-  QGS_CU(scan_exclusive_u32(ctx->cnt_sorted.p, ctx->offs.p, VN, ctx->scan_tmp.p, ctx->scan_tmp.cap, st), "scan");
   QGS_CU(cudaEventSynchronize(ctx->totals_ready), "sync");
   if (ctx->h_total[3]) {  // a radix sort of an earlier call gave up waiting for a chunk
     cudaMemsetAsync(ctx->dcount.p + 3, 0, sizeof(uint32_t), st);
     return fail(ctx, QGS_ECUDA, "a radix sort pass of an earlier call timed out in its look-back");
   }
+  const int64_t Vv = (int64_t)ctx->h_total[0];
   const int64_t I = (int64_t)ctx->h_total[1];
-  ctx->n_visible = (int64_t)ctx->h_total[0];
+  ctx->n_visible = Vv;
   if (tb_on && !ctx->tbits_fixed && (size_t)ctx->h_total[2] > cap_words)
     ctx->tbits_want = (size_t)ctx->h_total[2] + ctx->h_total[2] / 4;
 
   const size_t i1 = (size_t)(I > 0 ? I : 1);
   QGS_CU(ctx->inst.reserve(i1), "alloc inst");
   QGS_CU(ctx->inst2.reserve(i1), "alloc inst2");
+  QGS_CU(ctx->dstate.reserve((size_t)(Vv > 0 ? Vv : 1)), "alloc ordered state");
   QGS_CU(ctx->hist.reserve(radix_hist_elems((int64_t)i1)), "alloc hist");
   QGS_CU(ctx->scan_tmp.reserve(scan_tmp_elems((int64_t)radix_hist_elems((int64_t)i1))), "alloc scan");
   tmp.hist = ctx->hist.p;
@@ -1049,21 +1049,55 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
   tmp.scan_tmp = ctx->scan_tmp.p;
   tmp.scan_cap = ctx->scan_tmp.cap;
 
-  const uint64_t* sorted = ctx->inst.p;
-  if (VN > 0 && I > 0) {
-    k_emit_views<<<emit_blocks(VN), 256, 0, st>>>(VN, sidx, ctx->count.p, ctx->rect.p, ctx->offs.p, (uint32_t)N,
-                                                  d_vt, d_cp, ctx->tslab.p, tb_on ? ctx->tbits.p : nullptr,
-                                                  ctx->tbits_off.p, ctx->inst.p, tmp.err);
+  // visible entries -> depth sort -> state, counts and offsets in depth order -> instances
+  // (global tile << rb | depth rank) -> stable sort on the tile bits (render_forward's order
+  // within each view: depth, then entry index)
+  cudaError_t e = cudaSuccess;
+  const bool fl0 = radix_sort_u32_pairs(ctx->zkey2.p, ctx->idx2.p, ctx->zkey.p, ctx->idx.p, Vv, 0, 32, tmp, st, &e);
+  QGS_CU(e, "depth sort");
+  const uint32_t* sidx = fl0 ? ctx->idx.p : ctx->idx2.p;
+  if (Vv > 0) {
+    k_gather_state<<<nblk(Vv * 8), 256, 0, st>>>(Vv, sidx, ctx->state.p, ctx->count.p, ctx->dstate.p,
+                                                 ctx->cnt_sorted.p, tmp.err);
     ++launch_counter();
-    QGS_CU(cudaGetLastError(), "emit");
-    const bool fl = radix_sort_u64_keys(ctx->inst.p, ctx->inst2.p, I, 32, 32 + bits_for(T_all), tmp, st, &e);
-    QGS_CU(e, "tile sort");
-    sorted = fl ? ctx->inst2.p : ctx->inst.p;
+    QGS_CU(cudaGetLastError(), "gather state");
+  }
+  QGS_CU(scan_exclusive_u32(ctx->cnt_sorted.p, ctx->offs.p, Vv, ctx->scan_tmp.p, ctx->scan_tmp.cap, st), "scan");
+  const int tb = bits_for(T_all);
+  const int rb = bits_for(Vv > 1 ? Vv : 2);
+  const bool packed = rb + tb <= 32;
+  const void* sorted = ctx->inst.p;
+  if (Vv > 0 && I > 0) {
+    if (packed) {
+      uint32_t* k0 = reinterpret_cast<uint32_t*>(ctx->inst.p);
+      uint32_t* k1 = reinterpret_cast<uint32_t*>(ctx->inst2.p);
+      k_emit_packed_views<uint32_t><<<emit_blocks(Vv), 256, 0, st>>>(
+          Vv, sidx, ctx->cnt_sorted.p, ctx->rect.p, ctx->offs.p, (uint32_t)N, d_vt, d_cp, ctx->tslab.p,
+          tb_on ? ctx->tbits.p : nullptr, ctx->tbits_off.p, rb, k0, tmp.err);
+      ++launch_counter();
+      QGS_CU(cudaGetLastError(), "emit");
+      const bool f2 = radix_sort_u32_keys(k0, k1, I, rb, rb + tb, tmp, st, &e);
+      QGS_CU(e, "tile sort");
+      sorted = f2 ? (const void*)k1 : (const void*)k0;
+    } else {
+      k_emit_packed_views<uint64_t><<<emit_blocks(Vv), 256, 0, st>>>(
+          Vv, sidx, ctx->cnt_sorted.p, ctx->rect.p, ctx->offs.p, (uint32_t)N, d_vt, d_cp, ctx->tslab.p,
+          tb_on ? ctx->tbits.p : nullptr, ctx->tbits_off.p, 32, ctx->inst.p, tmp.err);
+      ++launch_counter();
+      QGS_CU(cudaGetLastError(), "emit");
+      const bool f2 = radix_sort_u64_keys(ctx->inst.p, ctx->inst2.p, I, 32, 32 + tb, tmp, st, &e);
+      QGS_CU(e, "tile sort");
+      sorted = f2 ? (const void*)ctx->inst2.p : (const void*)ctx->inst.p;
+    }
   }
   const uint32_t* ids = reinterpret_cast<const uint32_t*>(sorted);
   QGS_CU(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(uint2) * (size_t)T_all, st), "memset ranges");
   if (I > 0) {
-    k_tile_ranges<<<nblk(I), 256, 0, st>>>(I, sorted, ctx->ranges.p, tmp.err);
+    if (packed)
+      k_tile_ranges_x4<<<nblk((I + 3) / 4), 256, 0, st>>>(I, ids, rb, ctx->ranges.p, tmp.err);
+    else
+      k_tile_ranges_t<uint64_t><<<nblk(I), 256, 0, st>>>(I, reinterpret_cast<const uint64_t*>(sorted), 32,
+                                                         ctx->ranges.p, tmp.err);
     ++launch_counter();
     QGS_CU(cudaGetLastError(), "ranges");
   }
@@ -1074,8 +1108,9 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
   if (s != QGS_OK) return s;
   const uint32_t* order = ctx->torder.p;
   QGS_CU(cudaMemsetAsync(ctx->stats.p, 0, sizeof(RasterStats), st), "memset stats");
-  QGS_CU(launch_raster_fwd_views(ctx->cfg.density == 1, extra, (unsigned)T_all, st, ctx->ranges.p, ids, 2,
-                                 ctx->state.p, d_vd, V, d_tb, ctx->stats.p, order),
+  QGS_CU(launch_raster_fwd_views(ctx->cfg.density == 1, extra, (unsigned)T_all, st, ctx->ranges.p, ids,
+                                 packed ? 1 : 2, packed ? (uint32_t)((1ull << rb) - 1ull) : 0xFFFFFFFFu,
+                                 ctx->dstate.p, d_vd, V, d_tb, ctx->stats.p, order),
          "k_raster_fwd_views");
   ++launch_counter();
   ctx->launches_fwd = launch_counter() - launches0;

@@ -320,8 +320,9 @@ cudaError_t launch_raster_fwd(bool euclid, bool extra, unsigned grid, cudaStream
                               float* out_rgb, float* out_alpha, float* out_depth, float* out_normal, float* T_final,
                               uint32_t* n_contrib, const ExtraPlanes& ex, RasterStats* stats,
                               const uint32_t* tile_order, uint8_t* inst_used);
+// ids[k * id_stride] & id_mask indexes state (every view's rp.id_mask is replaced).
 cudaError_t launch_raster_fwd_views(bool euclid, bool extra, unsigned grid, cudaStream_t st, const uint2* ranges,
-                                    const uint32_t* ids, int id_stride, const PrimState* state,
+                                    const uint32_t* ids, int id_stride, uint32_t id_mask, const PrimState* state,
                                     const ViewDesc* views, int n_views, const uint32_t* tile_base,
                                     RasterStats* stats, const uint32_t* tile_order);
 // StopThePop ordering (per-tile hit-depth lists, per-pixel resorting in a buffer of 8):

@@ -380,7 +380,8 @@ __global__ void __launch_bounds__(BLOCK, 4)
 template <bool EUCLID, bool EXTRA>
 __global__ void __launch_bounds__(BLOCK, 3)
     k_raster_fwd_views(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids, int id_stride,
-                       const PrimState* __restrict__ state, const ViewDesc* __restrict__ views, int n_views,
+                       uint32_t id_mask, const PrimState* __restrict__ state, const ViewDesc* __restrict__ views,
+                       int n_views,
                        const uint32_t* __restrict__ tile_base, RasterStats* __restrict__ stats,
                        const uint32_t* __restrict__ tile_order) {
   __shared__ PrimState sm[BLOCK];
@@ -392,7 +393,8 @@ __global__ void __launch_bounds__(BLOCK, 3)
     if (tile_base[mid] <= (uint32_t)tile) lo = mid; else hi = mid;
   }
   const ViewDesc& vd = views[lo];
-  const RasterParams rp = vd.rp;
+  RasterParams rp = vd.rp;
+  rp.id_mask = id_mask;
   raster_fwd_tile<EUCLID, EXTRA, true>(sm, used, tile, tile - (int)tile_base[lo], ranges, ids, id_stride, state, rp,
                                  vd.rgb, vd.alpha, vd.depth, vd.normal, vd.T_final, vd.n_contrib, vd.ex, stats,
                                  nullptr);
@@ -1011,12 +1013,13 @@ cudaError_t launch_raster_fwd(bool euclid, bool extra, unsigned grid, cudaStream
 }
 
 cudaError_t launch_raster_fwd_views(bool euclid, bool extra, unsigned grid, cudaStream_t st, const uint2* ranges,
-                                    const uint32_t* ids, int id_stride, const PrimState* state,
+                                    const uint32_t* ids, int id_stride, uint32_t id_mask, const PrimState* state,
                                     const ViewDesc* views, int n_views, const uint32_t* tile_base,
                                     RasterStats* stats, const uint32_t* tile_order) {
   QGS_RASTER_DISPATCH(euclid, extra,
-                      k_raster_fwd_views<E_, X_><<<grid, BLOCK, 0, st>>>(ranges, ids, id_stride, state, views,
-                                                                         n_views, tile_base, stats, tile_order));
+                      k_raster_fwd_views<E_, X_><<<grid, BLOCK, 0, st>>>(ranges, ids, id_stride, id_mask, state,
+                                                                         views, n_views, tile_base, stats,
+                                                                         tile_order));
   return cudaGetLastError();
 }
 

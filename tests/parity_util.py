@@ -21,6 +21,14 @@ each way. The GPU pixel passes if it meets the bars against one of them. A pixel
 ambiguous only when it matches none of its branches (or has more branches than the oracle
 enumerates); the ambiguous fraction must stay at or below MAX_AMBIGUOUS (0.01 % of pixels).
 
+Conditioning of FP32 geometry. A pixel that blends a pair within GRAZE_FULL of grazing is
+bracketed with that pair's discriminant moved by GRAZE_SHIFT of the scale of its terms each
+way (near tangency the hit point, its depth and normal move by about e / sqrt(D) under a
+rounding e of D). Elsewhere each bar is at least SENS_FACTOR times the oracle's own change
+when every pair's local ray is perturbed by FP32-sized rounding (oracle.ray_sensitivity_images;
+for gradients oracle.ray_sensitivity); the fraction of pixels and elements whose bar this
+widened is reported.
+
 Gradients: each parameter gradient sums pixel contributions, and a bracketed pixel's
 contribution lies between those of its branches. An element passes when it lies within the
 bar of the interval [g* + lo, g* + hi], lo and hi summing, over the bracketed pixels, each
@@ -44,13 +52,10 @@ SENS_FACTOR = 3.0   # the bar is at least this many times the largest change the
 
 
 # ----------------------------------------------------------------------------- images
-def near_pixels(ref, mask=None, extras=False, grazing=False):
-    """Pixels to bracket: a decision within MARGIN, and (grazing, for gradients) a blended
-    grazing pair. Grazing does not make the forward values ill-conditioned (a rounding
-    error e of D moves a root by about e / sqrt(D)), only their derivatives (e / D)."""
-    near = ref["margin"] <= MARGIN
-    if grazing:
-        near = near | (ref["cond"] < O.GRAZE_FULL)
+def near_pixels(ref, mask=None, extras=False):
+    """Pixels to bracket: a decision within MARGIN, or a blended pair so close to grazing
+    (discriminant margin below GRAZE_FULL) that its root is re-evaluated with D shifted."""
+    near = (ref["margin"] <= MARGIN) | (ref["cond"] < O.GRAZE_FULL)
     if extras:
         near = near | (ref["margin_median"] <= MARGIN)
     if mask is not None:
@@ -83,21 +88,25 @@ def _gpu_pixel(out, x, y, extras):
     return gv
 
 
-def image_errors(gpu, ref, ok, extras=False):
-    """Max errors over the pixels `ok`, in units of the bars."""
+def image_errors(gpu, ref, ok, extras=False, sens=None):
+    """Max errors over the pixels `ok`, in units of the bars (each bar at least SENS_FACTOR
+    times the oracle's own change under local-ray rounding, `sens`, when given)."""
+    def tol(k, bar):
+        return bar if sens is None else np.maximum(bar, SENS_FACTOR * sens[k])
     e = {}
     for k in ("rgb", "alpha", "normal"):
-        e[k] = float(np.abs(np.asarray(gpu[k], np.float64) - ref[k])[..., ok].max(initial=0.0)) / TOL_ABS
+        e[k] = float((np.abs(np.asarray(gpu[k], np.float64) - ref[k]) / tol(k, TOL_ABS))[..., ok].max(initial=0.0))
     d = np.asarray(gpu["depth"], np.float64)
-    e["depth"] = float((np.abs(d - ref["depth"]) / np.maximum(np.abs(ref["depth"]), 1e-6))[ok].max(initial=0.0)
-                       ) / TOL_DEPTH_REL
+    bar_d = TOL_DEPTH_REL * np.maximum(np.abs(ref["depth"]), 1e-6)
+    e["depth"] = float((np.abs(d - ref["depth"]) / tol("depth", bar_d))[ok].max(initial=0.0))
     if extras:
         cs = np.maximum(ref["curvature_scale"], 1.0)
-        e["curvature"] = float((np.abs(np.asarray(gpu["curvature"], np.float64) - ref["curvature"]) / cs)[ok]
-                               .max(initial=0.0)) / TOL_CURV_REL
+        e["curvature"] = float((np.abs(np.asarray(gpu["curvature"], np.float64) - ref["curvature"])
+                                / tol("curvature", TOL_CURV_REL * cs))[ok].max(initial=0.0))
         D = ref["distortion"]
         tolD = TOL_DIST * (D + np.abs(ref["depth"]) * np.sqrt(np.maximum(D, 0.0))) + 1e-9
-        e["distortion"] = float((np.abs(np.asarray(gpu["distortion"], np.float64) - D) / tolD)[ok].max(initial=0.0))
+        e["distortion"] = float((np.abs(np.asarray(gpu["distortion"], np.float64) - D)
+                                 / tol("distortion", tolD))[ok].max(initial=0.0))
         m = ref["median_depth"]
         em = np.abs(np.asarray(gpu["median_depth"], np.float64) - m) / np.maximum(np.abs(m), 1e-6)
         e["median_depth"] = float(em[ok].max(initial=0.0)) / TOL_DEPTH_REL
@@ -116,17 +125,33 @@ def check_images(gpu, ref, scene, cam, binning=None, mask=None, extras=False, la
     return st
 
 
-def compare_images(gpu, ref, scene, cam, binning=None, mask=None, extras=False, **kw):
+def compare_images(gpu, ref, scene, cam, binning=None, mask=None, extras=False, sens_samples=SENS_SAMPLES, **kw):
     """The statistics of check_images, without asserting: errors (in units of the bars)
     over the pixels not near a decision, the near fraction, the worst near pixel against
     its best branch, the unmatched (ambiguous) pixels."""
     if mask is None:
         mask = np.ones(ref["alpha"].shape, bool)
     near = near_pixels(ref, mask, extras)
-    e = image_errors(gpu, ref, mask & ~near, extras)
+    sens = None
+    if binning is not None and sens_samples > 0:
+        TX = binning.tiles_x
+        ty, tx = np.nonzero(_tile_any(mask))
+        tiles = sorted(set((ty * TX + tx).tolist()))
+        sens = O.ray_sensitivity_images(scene, cam, binning, tiles, ref, sens_samples, extras=extras, **kw)
+    far = mask & ~near
+    e = image_errors(gpu, ref, far, extras, sens)
+    e_plain = image_errors(gpu, ref, far, extras)
+    widened = 0.0
+    if sens is not None and far.any():
+        wid = np.zeros(ref["alpha"].shape, bool)
+        for k, bar in (("rgb", TOL_ABS), ("alpha", TOL_ABS), ("normal", TOL_ABS)):
+            w = SENS_FACTOR * sens[k] > bar
+            wid |= w.any(0) if w.ndim == 3 else w
+        wid |= SENS_FACTOR * sens["depth"] > TOL_DEPTH_REL * np.maximum(np.abs(ref["depth"]), 1e-6)
+        widened = float(wid[far].mean())
     ys, xs = np.nonzero(near)
     pix = list(zip(xs.tolist(), ys.tolist()))
-    br = O.bracket_pixels(scene, cam, pix, binning, extras=extras, graze=False, **kw) if pix else []
+    br = O.bracket_pixels(scene, cam, pix, binning, extras=extras, **kw) if pix else []
     unmatched, unresolved, worst_near = [], 0, 0.0
     for (x, y), it in zip(pix, br):
         gv = _gpu_pixel(gpu, x, y, extras)
@@ -138,15 +163,16 @@ def compare_images(gpu, ref, scene, cam, binning=None, mask=None, extras=False, 
             worst_near = max(worst_near, best)
     n = int(mask.sum())
     amb = len(unmatched) / max(n, 1)
-    return dict(errors=e, near_frac=len(pix) / max(n, 1), near_worst=float(worst_near), ambiguous=len(unmatched),
-                ambiguous_frac=amb, unresolved=unresolved, pixels=n, unmatched=unmatched[:8])
+    return dict(errors=e, errors_plain=e_plain, widened_frac=widened, near_frac=len(pix) / max(n, 1),
+                near_worst=float(worst_near), ambiguous=len(unmatched), ambiguous_frac=amb, unresolved=unresolved,
+                pixels=n, unmatched=unmatched[:8])
 
 
 def check_pixels(gpu_vals, scene, cam, pixels, binning=None, extras=False, label="", list_free=False, **kw):
     """Sampled pixels [(x, y)] checked one by one against their branches (every pixel is
     bracketed; near ones have several branches). gpu_vals: the GPU planes. Asserts that the
     unmatched fraction is at most MAX_AMBIGUOUS of the sampled pixels (i.e. none)."""
-    br = O.bracket_pixels(scene, cam, pixels, binning, list_free=list_free, extras=extras, graze=False, **kw)
+    br = O.bracket_pixels(scene, cam, pixels, binning, list_free=list_free, extras=extras, **kw)
     unmatched, worst, branched = [], 0.0, 0
     for (x, y), it in zip(pixels, br):
         gv = _gpu_pixel(gpu_vals, x, y, extras)
@@ -202,7 +228,7 @@ def compare_grads(gpu, ref, scene, cam, grad_images, binning=None, mask=None, id
     sidx = idx[order_idx]
     if mask is None:
         mask = np.ones(ref["alpha"].shape, bool)
-    near = near_pixels(ref, mask, extras=False, grazing=True)
+    near = near_pixels(ref, mask)
     ys, xs = np.nonzero(near)
     pix = list(zip(xs.tolist(), ys.tolist()))
     ref_g = ref["grads"]
