@@ -282,7 +282,7 @@ def serving_parity(dev, n_req=4, n_pix=24, seed=3):
     sampled pixels against the oracle's branches (tests/parity_util.check_pixels, without
     asserting)."""
     import numpy as np
-    from tests.parity_util import _gpu_pixel, _pixel_errors
+    from tests.parity_util import _best_branch, _gpu_pixel, _graze_band, _pixel_errors
     import oracle.qgs_oracle as O
     from paper_2411_16392_gb300.render import DeviceScene
     from paper_2411_16392_gb300.scenes import orbit_camera, serving_scene
@@ -306,10 +306,12 @@ def serving_parity(dev, n_req=4, n_pix=24, seed=3):
         e_req = 0.0
         for (x, y), it in zip(pix, br):
             gv = _gpu_pixel(out, x, y, False)
-            best = min(_pixel_errors(gv, leaf, False) for leaf in it["leaves"])
+            best = _best_branch(gv, it, False)
             unmatched += best > 1.0
             e_req = max(e_req, best)
-            leaf = min(it["leaves"], key=lambda l: _pixel_errors(gv, l, False))
+            band = _graze_band(it)
+            leaf = min((l for g_, l in zip(it["groups"], it["leaves"]) if g_ == "d"),
+                       key=lambda l: _pixel_errors(gv, l, False, band))
             for k, lim, rel in (("rgb", 1e-4, False), ("alpha", 1e-4, False), ("normal", 1e-4, False),
                                 ("depth", 1e-4, True)):
                 d = float(np.max(np.abs(np.asarray(gv[k], np.float64) - np.asarray(leaf[k]).reshape(np.shape(gv[k])))))

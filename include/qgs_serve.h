@@ -13,10 +13,13 @@
  *     memory (projected primitives, tile keys and their sort buffers, residue, result
  *     planes) fits in the remaining HBM budget; requests that arrive while others run
  *     are admitted as slots and memory free up, and their kernels overlap on the GPU;
- *   - a slot that takes the head also takes up to max_batch - 1 further queued requests
- *     of the same scene (queue order, each only while the budget still holds it) and
- *     renders all of them, at their own resolutions, in shared launches
- *     (render_forward_batch); a batch of one runs render_forward;
+ *   - a slot that takes the head also takes up to max_batch - 1 further queued forward
+ *     requests of the same scene (queue order, each only while the budget still holds it)
+ *     where sharing launches pays: frames of at most 512x384 pixels, and at most 2^21
+ *     (view, primitive) entries in the batch (larger frames are dominated by their own
+ *     compositing and run as concurrent single renders in other slots); it renders them,
+ *     at their own resolutions, in shared launches (render_forward_batch); a batch of one
+ *     runs render_forward;
  *   - serve_wait returns a finished result (host or device destination) with a bounded
  *     wait; serve_stats reports p50/p99 latency (submit to result ready) and frames/s.
  * All functions are thread-safe. Status codes as in qgs.h; nothing aborts.

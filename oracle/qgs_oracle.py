@@ -767,7 +767,7 @@ DECISIONS = ("D", "near1", "near2", "in1", "in2", "amin", "amax")
 
 def _eval_pairs(prm: Params, cam: CamF64, idx: torch.Tensor, px: torch.Tensor, py: torch.Tensor,
                 density: str = "geodesic", flip: dict | None = None, d_shift=None, root_leaves: bool = False,
-                ray_noise=None):
+                ray_noise=None, coef_noise=None):
     """Evaluate every (pixel, primitive) pair of a pixel set [P] and a primitive list [L].
     Returns per-pair tensors [P, L]: alpha (0 where no contribution), validity, depth t,
     colour [P, L, 3] (broadcast), camera-space unit normal [P, L, 3], Gaussian curvature
@@ -790,7 +790,8 @@ def _eval_pairs(prm: Params, cam: CamF64, idx: torch.Tensor, px: torch.Tensor, p
     so that a backward pass yields the derivative of the outputs with respect to each root
     (see graze_bands). ray_noise [P, L, 6] (see ray_sensitivity) perturbs each pair's local
     ray: its origin where it crosses the centre's depth and its direction, componentwise
-    and relatively."""
+    and relatively; coef_noise [P, L, 3] perturbs the quadratic's coefficients in the frame
+    re-based at the centre's depth, each relative to the magnitudes of its terms."""
     weight_fn = {"geodesic": geodesic_gaussian, "euclid": euclid_gaussian}[density]
     fl = flip or {}
     mu = prm.mean[idx]
@@ -815,6 +816,17 @@ def _eval_pairs(prm: Params, cam: CamF64, idx: torch.Tensor, px: torch.Tensor, p
     A_ = a * dx * dx + b * dy * dy
     B_ = 2.0 * (a * ox * dx + b * oy * dy) - dz
     C_ = (a * ox * ox + b * oy * oy - oz).expand_as(A_)
+    if coef_noise is not None:
+        with torch.no_grad():
+            t0c = (mu @ cam.R[2] + cam.t[2])[None, :]
+            qx, qy, qz = ox + t0c * dx, oy + t0c * dy, oz + t0c * dz
+            sA = a.abs() * dx * dx + b.abs() * dy * dy
+            sB = 2.0 * ((a * qx * dx).abs() + (b * qy * dy).abs()) + dz.abs()
+            sC = a.abs() * qx * qx + b.abs() * qy * qy + qz.abs()
+        A0n = A_ + coef_noise[..., 0] * sA
+        B0n = (B_ + 2.0 * A_ * t0c) + coef_noise[..., 1] * sB
+        C0n = ((A_ * t0c + B_) * t0c + C_) + coef_noise[..., 2] * sC
+        A_, B_, C_ = A0n, B0n - 2.0 * A0n * t0c, (A0n * t0c - B0n) * t0c + C0n
     # Scale of the discriminant's rounding: D is the same for the ray re-parametrised as
     # s = t - t0 around the depth t0 of the centre, where the ray starts at o0 = o + t0 d,
     # of the size of the primitive instead of the camera distance. A, B0 and C0 are sums of
@@ -966,8 +978,9 @@ def _composite(prm, cam, idx, px, py, chunk=4096, density="geodesic", extras=Fal
     for c0 in range(0, L, chunk):
         sl = idx[c0:c0 + chunk]
         Lc = sl.shape[0]
-        rn = None if noise is None else noise(P, sl.shape[0], c0)
-        pe = _eval_pairs(prm, cam, sl, px, py, density, root_leaves=collect is not None, ray_noise=rn)
+        rn, cn = (None, None) if noise is None else noise(P, sl.shape[0], c0)
+        pe = _eval_pairs(prm, cam, sl, px, py, density, root_leaves=collect is not None, ray_noise=rn,
+                         coef_noise=cn)
         if collect is not None:
             collect.append((c0, pe))
         al, v = pe["alpha"], pe["valid"]
@@ -1044,8 +1057,9 @@ def _composite_resort(prm, cam, idx, px, py, density="geodesic", extras=False, b
     P = px.shape[0]
     L = idx.shape[0]
     dev = dict(dtype=F64)
-    rn = None if noise is None else noise(P, L, 0)
-    pe = _eval_pairs(prm, cam, idx, px, py, density, root_leaves=collect is not None, ray_noise=rn)
+    rn, cn = (None, None) if noise is None else noise(P, L, 0)
+    pe = _eval_pairs(prm, cam, idx, px, py, density, root_leaves=collect is not None, ray_noise=rn,
+                     coef_noise=cn)
     if collect is not None:
         collect.append((0, pe))
     al, valid, tt = pe["alpha"], pe["valid"], pe["t"]
@@ -1174,7 +1188,8 @@ def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=N
     by centre depth) or "stp" (StopThePop: per-tile hit depth, then per-pixel resorting
     in a buffer of RESORT entries). ray_noise_seed: perturb every pair's local ray by
     uniform relative noise of RAY_EPS per component, drawn from a generator seeded by
-    (seed, tile, list position) (see ray_sensitivity). timings: if a dict, receives the
+    (seed, tile, list position), and the quadratic's coefficients by as much of the
+    magnitudes of their terms (see ray_sensitivity). timings: if a dict, receives the
     seconds spent on each rendered tile (forward and, with grad_images, backward)."""
     if binning is None:
         binning = bin_fp32(scene, cam, order="hit" if order == "stp" else "centre")
@@ -1221,7 +1236,9 @@ def render(scene, cam, binning: Binning | None = None, tiles=None, grad_images=N
         if ray_noise_seed is not None:
             def noise(P_, L_, c0, _t=tile):
                 gen = torch.Generator().manual_seed(int(ray_noise_seed) * 1_000_003 + _t * 4099 + c0)
-                return (2.0 * torch.rand(P_, L_, 6, generator=gen, dtype=F64) - 1.0) * RAY_EPS
+                rn = (2.0 * torch.rand(P_, L_, 6, generator=gen, dtype=F64) - 1.0) * RAY_EPS
+                cn = (2.0 * torch.rand(P_, L_, 3, generator=gen, dtype=F64) - 1.0) * RAY_EPS
+                return rn, cn
         with torch.set_grad_enabled(want_grad):
             r = comp(prm, c64, idx, px, py, density=density, extras=extras, noise=noise)
             if want_grad:
@@ -1319,7 +1336,7 @@ BRACKET_MARGIN = 1e-5     # relative margin below which a decision is taken both
 BRACKET_LEAVES = 512      # most branches enumerated per pixel (more: the pixel is unresolved)
 GRAZE_MARGIN = 1e-2       # blended pairs whose discriminant margin is below this ...
 GRAZE_SHIFT = 1e-6        # ... are also evaluated with D moved by this fraction of its scale
-GRAZE_FULL = 20 * GRAZE_SHIFT   # below this margin a shifted pair is re-evaluated, above it linearised
+GRAZE_FULL = 20 * GRAZE_SHIFT  # below this margin a shifted pair is re-evaluated (above: graze_bands)
 ORDER_GAP = 2.0 ** -20    # list-free order: neighbours whose centre depths are this close may swap
 # An FP32 implementation forms each pair's local ray (where it crosses the centre's depth,
 # and its direction) in a handful of rounded operations from rounded per-primitive state:
@@ -1765,11 +1782,14 @@ def graze_bands(scene, cam, binning: Binning, tiles, grad_images, density: str =
 def ray_sensitivity(scene, cam, binning: Binning, tiles, grad_images, ref_grads, samples: int = 3,
                     density: str = "geodesic", extras: bool = False, order: str = "centre"):
     """How far the exact gradients move under the rounding an FP32 implementation incurs in
-    forming each pair's local ray: the largest change, over `samples` renders whose every
-    (pixel, primitive) pair has its local ray perturbed by independent uniform relative
-    noise of RAY_EPS per component (origin and direction). Near tangency (the ray meeting a
-    steep flank of a strongly curved patch) and where the pixels' contributions to a
-    parameter cancel, the exact gradient itself is defined by FP32 inputs only to this much.
+    forming each pair's local ray and its quadratic: the largest change, over `samples`
+    renders whose every (pixel, primitive) pair has its local ray perturbed by independent
+    uniform relative noise of RAY_EPS per component (origin and direction) and each
+    coefficient of its quadratic (re-based at the centre's depth) by as much of the
+    magnitudes of its terms. Near tangency
+    (the ray meeting a steep flank of a strongly curved patch, a grazing pair moving a
+    thin primitive's hit) and where the pixels' contributions to a parameter cancel, the
+    exact gradient itself is defined by FP32 inputs only to this much.
     Returns {parameter: array like ref_grads}."""
     spread = {k: np.zeros_like(v) for k, v in ref_grads.items()}
     for smp in range(samples):

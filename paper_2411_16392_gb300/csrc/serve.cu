@@ -58,6 +58,18 @@ struct Slot {
   std::thread th;
 };
 
+// Shared launches save a view its own launches and host round trip, a fixed cost of a
+// few tens of microseconds, while the batch's sorts grow with all its entries and every
+// request waits for the whole batch. They pay for small frames of batches whose (view,
+// primitive) entries stay within the radix sort's single-kernel passes (2M keys); larger
+// frames are dominated by their own compositing and run as concurrent single renders in
+// other slots instead.
+constexpr int64_t kBatchMaxEntries = int64_t(1) << 21;
+constexpr int64_t kBatchMaxPixels = 512 * 384;
+inline bool batch_pays(int64_t n_prims, int64_t n_views, const qgs_camera& c) {
+  return n_views * n_prims <= kBatchMaxEntries && (int64_t)c.W * c.H <= kBatchMaxPixels;
+}
+
 int64_t request_bytes(const SceneDev& s, const qgs_camera& c, bool bwd) {
   const double P = (double)c.W * c.H;
   const double inst = s.inst_per_pixel * P;
@@ -199,10 +211,12 @@ void qgs_server::worker(int si) {
       batch.push_back(head);
       est = head->est_bytes;
       // the other queued forward views of the same scene that still fit join the head's
-      // launches (a backward request runs alone)
-      for (auto it = queue.begin(); it != queue.end() && !head->want_bwd && (int)batch.size() < max_batch;) {
+      // launches where sharing them pays (a backward request runs alone; see batch_pays)
+      for (auto it = queue.begin(); it != queue.end() && !head->want_bwd && (int)batch.size() < max_batch &&
+                                    batch_pays(head->scn.n, (int64_t)batch.size() + 1, head->cam);) {
         Request* r = *it;
-        if (!r->want_bwd && r->scene == head->scene && reserved + est + r->est_bytes <= budget) {
+        if (!r->want_bwd && r->scene == head->scene && batch_pays(r->scn.n, (int64_t)batch.size() + 1, r->cam) &&
+            reserved + est + r->est_bytes <= budget) {
           batch.push_back(r);
           est += r->est_bytes;
           it = queue.erase(it);

@@ -63,20 +63,58 @@ def near_pixels(ref, mask=None, extras=False):
     return near
 
 
-def _pixel_errors(gv, leaf, extras):
-    """Errors of one GPU pixel against one oracle branch, in units of the bars (<= 1 passes)."""
-    e = [np.abs(gv["rgb"] - leaf["rgb"]).max() / TOL_ABS, abs(gv["alpha"] - leaf["alpha"][0]) / TOL_ABS,
-         np.abs(gv["normal"] - leaf["normal"]).max() / TOL_ABS,
-         abs(gv["depth"] - leaf["depth"][0]) / max(abs(leaf["depth"][0]), 1e-6) / TOL_DEPTH_REL]
+def _graze_band(it):
+    """Per-channel band that a pixel's grazing pairs span: for each pair whose discriminant
+    was moved each way (bracket_pixels groups ("g", j)), the larger deviation of its two
+    evaluations from the nominal branch, summed over the pairs (small independent shifts:
+    their effects add). The outputs move continuously with the shift, so every value in
+    between is as correct as the ends."""
+    nom = it["leaves"][0]
+    dev = {}
+    for grp, leaf in zip(it["groups"], it["leaves"]):
+        if grp == "d":
+            continue
+        for k, v in leaf.items():
+            d = np.abs(np.asarray(v, np.float64) - np.asarray(nom[k], np.float64))
+            dev[(grp, k)] = np.maximum(dev.get((grp, k), 0.0), d)
+    band = {}
+    for (grp, k), d in dev.items():
+        band[k] = band.get(k, 0.0) + d
+    return band
+
+
+def _pixel_errors(gv, leaf, extras, band=None):
+    """Errors of one GPU pixel against one oracle branch, in units of the bars (<= 1 passes),
+    each output allowed `band` (per channel, see _graze_band) beyond its bar."""
+    band = band or {}
+
+    def over(k, diff):
+        return np.max(np.maximum(np.abs(diff) - band.get(k, 0.0), 0.0))
+
+    e = [over("rgb", gv["rgb"] - leaf["rgb"]) / TOL_ABS,
+         float(over("alpha", gv["alpha"] - leaf["alpha"][0])) / TOL_ABS,
+         over("normal", gv["normal"] - leaf["normal"]) / TOL_ABS,
+         float(over("depth", gv["depth"] - leaf["depth"][0])) / max(abs(leaf["depth"][0]), 1e-6) / TOL_DEPTH_REL]
     if extras:
-        e.append(abs(gv["curvature"] - leaf["curvature"][0]) / (TOL_CURV_REL * max(leaf["curvature_scale"][0], 1.0)))
+        e.append(float(over("curvature", gv["curvature"] - leaf["curvature"][0]))
+                 / (TOL_CURV_REL * max(leaf["curvature_scale"][0], 1.0)))
         D = leaf["distortion"][0]
-        e.append(abs(gv["distortion"] - D) / (TOL_DIST * (D + abs(leaf["depth"][0]) * np.sqrt(max(D, 0.0))) + 1e-9))
+        e.append(float(over("distortion", gv["distortion"] - D))
+                 / (TOL_DIST * (D + abs(leaf["depth"][0]) * np.sqrt(max(D, 0.0))) + 1e-9))
         lo, hi = leaf["median_lo"][0], leaf["median_hi"][0]
         m = gv["median_depth"]
-        d = max(lo - m, m - hi, 0.0)
+        bm = float(np.max(band.get("median_depth", 0.0)))
+        d = max(lo - bm - m, m - hi - bm, 0.0)
         e.append(d / max(abs(lo), abs(hi), 1e-6) / TOL_DEPTH_REL)
     return max(e)
+
+
+def _best_branch(gv, it, extras):
+    """The smallest error of a GPU pixel over its discrete branches, each widened by the
+    band of its grazing pairs."""
+    band = _graze_band(it)
+    return min(_pixel_errors(gv, leaf, extras, band) for grp, leaf in zip(it["groups"], it["leaves"])
+               if grp == "d")
 
 
 def _gpu_pixel(out, x, y, extras):
@@ -155,7 +193,7 @@ def compare_images(gpu, ref, scene, cam, binning=None, mask=None, extras=False, 
     unmatched, unresolved, worst_near = [], 0, 0.0
     for (x, y), it in zip(pix, br):
         gv = _gpu_pixel(gpu, x, y, extras)
-        best = min(_pixel_errors(gv, leaf, extras) for leaf in it["leaves"])
+        best = _best_branch(gv, it, extras)
         unresolved += not it["resolved"]
         if best > 1.0:
             unmatched.append((x, y, best, len(it["leaves"]), it["resolved"]))
@@ -176,7 +214,7 @@ def check_pixels(gpu_vals, scene, cam, pixels, binning=None, extras=False, label
     unmatched, worst, branched = [], 0.0, 0
     for (x, y), it in zip(pixels, br):
         gv = _gpu_pixel(gpu_vals, x, y, extras)
-        best = min(_pixel_errors(gv, leaf, extras) for leaf in it["leaves"])
+        best = _best_branch(gv, it, extras)
         branched += len(it["leaves"]) > 1
         if best > 1.0:
             unmatched.append((x, y, best, len(it["leaves"])))
