@@ -156,6 +156,19 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
+def _json_default(o):
+    """numpy scalars and arrays in the JSON line (counts and errors computed with numpy)."""
+    if hasattr(o, "tolist"):
+        return o.tolist()
+    if hasattr(o, "item"):
+        return o.item()
+    raise TypeError(f"{type(o).__name__} is not JSON serializable")
+
+
+def _dumps(line):
+    return json.dumps(line, default=_json_default)
+
+
 # ----------------------------------------------------------------------------- CPU oracle
 def _stratified_tiles(tile_counts, n, seed):
     """One tile drawn from each of n strata of equal size, the frame's tiles ordered by
@@ -358,7 +371,7 @@ def run_reference(args):
                              "extrapolated": True,
                              "sample": vals[0]["sample"] + f"; {args.steps} steps, wall {wall:.1f} s"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    print(_dumps(line), flush=True)
     return 0
 
 
@@ -792,7 +805,7 @@ def _report(args, rank, world, sc, cam, st, stage, clk, ms_max, value, e2e_value
         dist.barrier()
         dist.destroy_process_group()
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        print(_dumps(line), flush=True)
     return 0
 
 

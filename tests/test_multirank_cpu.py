@@ -1,6 +1,7 @@
 """The multi-rank path of bench.py on CPU: two gloo ranks (replicas, no data-path
 collective) reduce their step times to the maximum on every rank and report the
 whole-job throughput; the reference arm runs on rank 0 only."""
+import json
 import os
 import socket
 
@@ -54,3 +55,14 @@ def test_reference_arm_is_rank_zero_only(monkeypatch, capsys):
 
     assert bench.run_reference(Args()) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_json_line_takes_numpy_values():
+    """The bench line carries counts and errors computed with numpy (int64, float32,
+    arrays): they serialise as plain JSON numbers and lists."""
+    import numpy as np
+    import bench
+    line = {"parity": {"bracketed_pixels": np.int64(7), "err": np.float32(0.25), "tiles": np.arange(3),
+                       "unmatched": [(1, 2, np.float64(0.5), np.int64(6), True)]}}
+    assert json.loads(bench._dumps(line)) == {"parity": {"bracketed_pixels": 7, "err": 0.25, "tiles": [0, 1, 2],
+                                                         "unmatched": [[1, 2, 0.5, 6, True]]}}
