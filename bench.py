@@ -811,9 +811,11 @@ def _report(args, rank, world, sc, cam, st, stage, clk, ms_max, value, e2e_value
 
 def _serving_leg(args):
     """Served p50/p99 latency and frames/s of the 1M-quadric serving workload at each
-    arrival rate: plain one-at-a-time (1 slot, no batching), concurrent slots without
-    batching, and continuous batching (slots that each render up to --serve-batch queued
-    views in shared launches); the same arrival process for all three."""
+    arrival rate: plain one-at-a-time (1 slot, no batching), one slot that renders up to
+    --serve-batch queued small views in shared launches, concurrent slots without batching,
+    and the server with both (--serve-slots slots, batches of --serve-batch; with several
+    slots the server's policy forms no batches, see csrc/serve.cu batch_pays); the same
+    arrival process for all four."""
     import torch
     from paper_2411_16392_gb300.render import DeviceScene
     from paper_2411_16392_gb300.scenes import serving_scene
@@ -822,8 +824,8 @@ def _serving_leg(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     ds = DeviceScene.from_host(serving_scene(0, 1_000_000), dev)
     res = {"workload": "serving_1m_mixed_res", "requests": args.serve_requests, "rates": []}
-    legs = (("one_at_a_time", 1, 1), (f"slots{args.serve_slots}", args.serve_slots, 1),
-            ("batched", args.serve_slots, args.serve_batch))
+    legs = (("one_at_a_time", 1, 1), ("one_slot_batched", 1, args.serve_batch),
+            (f"slots{args.serve_slots}", args.serve_slots, 1), ("batched", args.serve_slots, args.serve_batch))
     n = args.serve_requests
     for rate in args.serve_rate:
         rng = np.random.default_rng(0)

@@ -13,13 +13,14 @@
  *     memory (projected primitives, tile keys and their sort buffers, residue, result
  *     planes) fits in the remaining HBM budget; requests that arrive while others run
  *     are admitted as slots and memory free up, and their kernels overlap on the GPU;
- *   - a slot that takes the head also takes up to max_batch - 1 further queued forward
- *     requests of the same scene (queue order, each only while the budget still holds it)
- *     where sharing launches pays: frames of at most 512x384 pixels, and at most 2^21
- *     (view, primitive) entries in the batch (larger frames are dominated by their own
- *     compositing and run as concurrent single renders in other slots); it renders them,
- *     at their own resolutions, in shared launches (render_forward_batch); a batch of one
- *     runs render_forward;
+ *   - on a server with a single slot (max_slots = 1), the slot that takes the head also
+ *     takes up to max_batch - 1 further queued forward requests of the same scene (queue
+ *     order, each only while the budget still holds it) with frames of at most 512x384
+ *     pixels, and renders them, at their own resolutions, in shared launches
+ *     (render_forward_batch), which saves each view its launches and host round trip; a
+ *     batch of one runs render_forward. With several slots those fixed costs are hidden
+ *     by the other slots' kernels and concurrent single renders are faster, so no batches
+ *     form there;
  *   - serve_wait returns a finished result (host or device destination) with a bounded
  *     wait; serve_stats reports p50/p99 latency (submit to result ready) and frames/s.
  * All functions are thread-safe. Status codes as in qgs.h; nothing aborts.
@@ -71,7 +72,8 @@ void serve_destroy(qgs_server* srv);
 qgs_status serve_load_scene(qgs_server* srv, const qgs_scene* scene, int32_t* scene_id);
 
 /* Enqueue a render of scene `scene_id` from `cam`; returns with a ticket once queued.
- * want_backward = 0: forward only (batched with other queued forward views of the scene).
+ * want_backward = 0: forward only (on a single-slot server, batched with other queued
+ * forward views of the scene).
  * want_backward = 1: forward, then the backward of sum(grad_out . planes) (render_backward;
  * the paper's training step, Sec. 3.3, without the optimiser); grad_out's four base planes
  * (rgb 3HW, alpha HW, depth HW, normal 3HW; host or device; a NULL plane or grad_out = NULL

@@ -20,6 +20,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "qgs_internal.cuh"
 
 using namespace qgs;
@@ -415,6 +417,7 @@ struct qgs_ctx {
   bool pair_counters = true;                   // compile the per-pair counters into the compositing
   bool counted_fwd = true, counted_bwd = true;  // the last forward / backward collected them
   cudaEvent_t ev[10] = {};
+  bool nvtx_open = false;  // an NVTX stage range of this context is open
   int64_t launches_fwd = 0, launches_bwd = 0;
   CamParams cp{};
   RasterParams rp{};
@@ -487,8 +490,24 @@ void make_params(const qgs_ctx* ctx, const qgs_camera* cam, CamParams& cp, Raste
   rp.id_mask = 0xFFFFFFFFu;
 }
 
+// Stage boundaries: CUDA events when profiling is on, and NVTX ranges (host-side, the
+// interval in which each stage is enqueued; free unless a tool is attached) named after
+// the stage that starts at boundary i (boundaries 6 and 9 end the forward and backward).
 inline void mark(qgs_ctx* c, int i, cudaStream_t st) {
+  static const char* const names[10] = {"qgs preprocess + tile count",
+                                        "qgs totals, compaction, depth sort, gather, offsets",
+                                        "qgs key packing",
+                                        "qgs key emission",
+                                        "qgs tile sort, ranges, schedule",
+                                        "qgs raster forward",
+                                        nullptr,
+                                        "qgs raster backward",
+                                        "qgs preprocess backward",
+                                        nullptr};
   if (c->profiling) cudaEventRecord(c->ev[i], st);
+  if (c->nvtx_open) nvtxRangePop();
+  c->nvtx_open = names[i] != nullptr;
+  if (c->nvtx_open) nvtxRangePushA(names[i]);
 }
 
 int bits_for(int64_t v) {

@@ -868,6 +868,7 @@ __global__ void __launch_bounds__(kCountBlock) k_count_tiles(int64_t n, const Ti
   // the warp's rectangles and screen bounds, loaded up front (independent loads) and
   // handed out per primitive from registers and shared memory
   __shared__ TileSlab sts[kCountBlock];
+  __shared__ float4 hoist[kCountBlock / 32][6 * kHoistMax];  // per warp: column and row terms
   short4 rc0 = make_short4(0, 0, 0, 0);
   if (c0) {
     rc0 = rect[i];
@@ -887,7 +888,7 @@ __global__ void __launch_bounds__(kCountBlock) k_count_tiles(int64_t n, const Ti
     const short4 rk = make_short4((short)(a & 0xFFFF), (short)(a >> 16), (short)(b & 0xFFFF), (short)(b >> 16));
     const uint32_t wo = __shfl_sync(0xffffffffu, woff, k);
     const uint32_t c = warp_tiles(rk, &sts[(threadIdx.x & ~31) + k], W, H, [](uint32_t, int, int) {},
-                                  wo != kNoTileBits ? tbits + wo : nullptr);
+                                  wo != kNoTileBits ? tbits + wo : nullptr, nullptr, hoist[threadIdx.x >> 5]);
     if (lane == k) mine = c;
   }
   if (i < n) {

@@ -133,6 +133,61 @@ __device__ __forceinline__ bool tile_meets(const TileSlab& t, const TileSpans& s
   return ok && conic_meets(t, c, r);
 }
 
+// The tile test with its per-column and per-row terms hoisted: tile_col, tile_row and the
+// parts of conic_meets that depend on the column or the row alone (the edge facing the
+// origin, the unclamped stationary point along it, and the products of the conic's value
+// that involve only that coordinate) are formed once per column or row of a rectangle; a
+// tile then costs the additions, clamps and products that involve both. Every operation is
+// the same correctly rounded one, on the same operands, as in tile_meets, so the result
+// is identical bit for bit.
+struct ColTerms {
+  float4 a;  // x0, x1, ue (edge facing the origin), vs (unclamped stationary v on it)
+  float4 b;  // amin[0], amax[0], amin[1], amax[1]
+  float4 c;  // qa ue, -, -, -
+};
+struct RowTerms {
+  float4 a;  // y0, y1, ve (edge facing the origin), us (unclamped stationary u on it)
+  float4 b;  // bmin[0], bmax[0], bmin[1], bmax[1]
+  float4 c;  // 2 (qb ve), ve (qc ve - 2 lb), -, -
+};
+constexpr int kHoistMax = 48;  // rectangles up to this many columns and rows take the hoisted test
+__device__ __forceinline__ ColTerms col_terms(const TileSlab& t, int tx, int W) {
+  const TileCol c = tile_col(t, tx, W);
+  const float ue = c.x0 > 0.f ? c.x0 : c.x1;
+  ColTerms o;
+  o.a = make_float4(c.x0, c.x1, ue, __fmul_rn(__fsub_rn(t.d.z, __fmul_rn(t.c.w, ue)), t.e.x));
+  o.b = make_float4(c.amin[0], c.amax[0], c.amin[1], c.amax[1]);
+  o.c = make_float4(__fmul_rn(t.c.z, ue), 0.f, 0.f, 0.f);
+  return o;
+}
+__device__ __forceinline__ RowTerms row_terms(const TileSlab& t, int ty, int H) {
+  const TileRow r = tile_row(t, ty, H);
+  const float ve = r.y0 > 0.f ? r.y0 : r.y1;
+  RowTerms o;
+  o.a = make_float4(r.y0, r.y1, ve, __fmul_rn(__fsub_rn(t.d.y, __fmul_rn(t.c.w, ve)), t.d.w));
+  o.b = make_float4(r.bmin[0], r.bmax[0], r.bmin[1], r.bmax[1]);
+  o.c = make_float4(__fmul_rn(2.f, __fmul_rn(t.c.w, ve)),
+                    __fmul_rn(ve, __fsub_rn(__fmul_rn(t.d.x, ve), __fmul_rn(2.f, t.d.z))), 0.f, 0.f);
+  return o;
+}
+// tile_meets from the hoisted terms (two_la = 2 la, two_lb = 2 lb, formed once per primitive)
+__device__ __forceinline__ bool tile_meets_hoisted(const TileSlab& t, const TileSpans& sp, const ColTerms& C,
+                                                   const RowTerms& R, float two_la, float two_lb) {
+  bool ok = !(__fadd_rn(C.b.y, R.b.y) < sp.lo[0]) && !(__fadd_rn(C.b.x, R.b.x) > sp.hi[0]) &&
+            !(__fadd_rn(C.b.w, R.b.w) < sp.lo[1]) && !(__fadd_rn(C.b.z, R.b.z) > sp.hi[1]);
+  if (!(t.c.z > 0.f)) return ok;  // conic disabled
+  const bool xin = C.a.x <= 0.f && 0.f <= C.a.y, yin = R.a.x <= 0.f && 0.f <= R.a.y;
+  // edge x = ue, v clamped to the row: F(ue, vs)
+  const float vs = fminf(fmaxf(C.a.w, R.a.x), R.a.y);
+  const float inx = __fsub_rn(__fadd_rn(C.c.x, __fmul_rn(2.f, __fmul_rn(t.c.w, vs))), two_la);
+  const float fx = __fadd_rn(__fmul_rn(C.a.z, inx), __fmul_rn(vs, __fsub_rn(__fmul_rn(t.d.x, vs), two_lb)));
+  // edge y = ve, u clamped to the column: F(us, ve)
+  const float us = fminf(fmaxf(R.a.w, C.a.x), C.a.y);
+  const float iny = __fsub_rn(__fadd_rn(__fmul_rn(t.c.z, us), R.c.x), two_la);
+  const float fy = __fadd_rn(__fmul_rn(us, iny), R.c.y);
+  return ok && ((xin && yin) || (!xin && fx <= 1.f) || (!yin && fy <= 1.f));
+}
+
 // The whole warp enumerates one primitive's rectangle r in row-major order, 32 tiles at a
 // time (lane l takes tile e = e0 + l, its (tx, ty) advanced without divisions); f(k, tx,
 // ty) runs for every tile that meets the parallelogram and the conic (every tile when t
@@ -143,16 +198,40 @@ constexpr uint32_t kNoTileBits = 0xFFFFFFFFu;  // primitive without cached tile 
 
 template <typename F>
 __device__ __forceinline__ uint32_t warp_tiles(short4 r, const TileSlab* t, int W, int H, F&& f,
-                                               uint32_t* bits_out = nullptr, const uint32_t* bits_in = nullptr) {
+                                               uint32_t* bits_out = nullptr, const uint32_t* bits_in = nullptr,
+                                               float4* hoist = nullptr) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
   const int w = r.y - r.x + 1;
-  const uint32_t total = (uint32_t)w * (uint32_t)(r.w - r.z + 1);
+  const int h = r.w - r.z + 1;
+  const uint32_t total = (uint32_t)w * (uint32_t)h;
   TileSlab ts;
   TileSpans sp{};
   if (t && !bits_in) {
     ts = *t;
     sp = tile_spans(ts);
+  }
+  // hoisted test: the rectangle's column and row terms in the warp's scratch (hoist holds
+  // 3 float4 per entry, kHoistMax columns then kHoistMax rows)
+  const bool hoisted = t && !bits_in && hoist && w <= kHoistMax && h <= kHoistMax;
+  float two_la = 0.f, two_lb = 0.f;
+  if (hoisted) {
+    two_la = __fmul_rn(2.f, ts.d.y);
+    two_lb = __fmul_rn(2.f, ts.d.z);
+    __syncwarp();  // the previous primitive's terms are no longer read
+    for (int c = lane; c < w; c += 32) {
+      const ColTerms ct = col_terms(ts, r.x + c, W);
+      hoist[3 * c] = ct.a;
+      hoist[3 * c + 1] = ct.b;
+      hoist[3 * c + 2] = ct.c;
+    }
+    for (int q = lane; q < h; q += 32) {
+      const RowTerms rt = row_terms(ts, r.z + q, H);
+      hoist[3 * (kHoistMax + q)] = rt.a;
+      hoist[3 * (kHoistMax + q) + 1] = rt.b;
+      hoist[3 * (kHoistMax + q) + 2] = rt.c;
+    }
+    __syncwarp();
   }
   int ty = r.z + lane / w, tx = r.x + lane % w;  // tile e = lane
   const int sy = 32 / w, sx = 32 - sy * w;          // tile e + 32: sy rows and sx columns on
@@ -173,7 +252,13 @@ __device__ __forceinline__ uint32_t warp_tiles(short4 r, const TileSlab* t, int 
       pass = (m >> lane) & 1u;
     } else {
       pass = e0 + (uint32_t)lane < total;
-      if (pass && t) {
+      if (pass && hoisted) {
+        const float4* cp = hoist + 3 * (tx - r.x);
+        const float4* rp = hoist + 3 * (kHoistMax + ty - r.z);
+        const ColTerms ct{cp[0], cp[1], cp[2]};
+        const RowTerms rt{rp[0], rp[1], rp[2]};
+        pass = tile_meets_hoisted(ts, sp, ct, rt, two_la, two_lb);
+      } else if (pass && t) {
         if (ty != row_y) {
           row = tile_row(ts, ty, H);
           row_y = ty;
@@ -340,7 +425,6 @@ cudaError_t launch_raster_bwd_stp(bool euclid, bool extra, unsigned grid, cudaSt
                                   const float* g_normal, const float* T_final, const float* xres,
                                   const ExtraGrads& eg, float* pgrad, RasterStats* stats,
                                   const uint32_t* tile_order);
-constexpr size_t RASTER_BWD_SMEM = sizeof(PrimState) * BLOCK + sizeof(float) * BLOCK * NGRAD + sizeof(int) * BLOCK;
 cudaError_t launch_raster_bwd(bool euclid, bool extra, unsigned grid, cudaStream_t st, const uint2* ranges,
                               const uint32_t* ids, int id_stride, const PrimState* state, const RasterParams& rp,
                               const float* g_rgb, const float* g_alpha, const float* g_depth, const float* g_normal,

@@ -1,6 +1,7 @@
 // Per-tile compositing of quadric Gaussian primitives: forward and backward.
 //
-// One CTA per 16x16 tile, one thread per pixel (warps cover 8x4 pixel blocks). The
+// One CTA per 16x16 tile; the forward takes one thread per pixel (warps cover 8x4 pixel
+// blocks), the backward two (warps cover 8x8 blocks, see k_raster_bwd). The
 // tile's sorted primitive list is walked in batches of 256 projected-state records
 // staged in shared memory (one 128-byte line per primitive, gathered by 8 threads per
 // record). Per (pixel, primitive) pair:
@@ -204,9 +205,10 @@ __device__ __forceinline__ void pixel_of(int tile, int tiles_x, int& px, int& py
   py = (tile / tiles_x) * TILE + (warp >> 1) * 4 + (lane >> 3);
 }
 
+template <int NT = BLOCK>
 __device__ __forceinline__ void stage_batch(PrimState* sm, const uint32_t* ids, int id_stride, uint32_t id_mask,
                                             const PrimState* state, uint32_t first, int cnt) {
-  for (int e = threadIdx.x; e < cnt * 8; e += BLOCK) {
+  for (int e = threadIdx.x; e < cnt * 8; e += NT) {
     const int r = e >> 3, c = e & 7;
     const uint32_t pid = __ldg(ids + (size_t)(first + r) * id_stride) & id_mask;
     reinterpret_cast<float4*>(sm)[r * 8 + c] = __ldg(reinterpret_cast<const float4*>(state + pid) + c);
@@ -445,10 +447,15 @@ __device__ __forceinline__ PixGrads load_pix_grads(bool inside, size_t pix, size
 // before the pair; S_ref is the sum of w_j (g . X_j) over the pixel's later blended
 // pairs, or (FWD_ORDER) over all of them, S_prefix then being that sum over the pairs up
 // to and excluding this one. Returns the pair's own term w (g . X).
-template <bool EUCLID, bool EXTRA, bool FWD_ORDER>
+template <bool EUCLID, bool EXTRA, bool FWD_ORDER, bool ACC = false>
 __device__ __forceinline__ float pair_grad(const PrimState& P, const Hit& h, float oG, float al, float T, float xn,
                                            float yn, const RasterParams& rp, const PixGrads& pg, float S_ref,
                                            float S_prefix, float v[32]) {
+  // ACC: add the record to v (several pixels of one thread) instead of writing it
+  auto put = [&](int k, float x) {
+    if constexpr (ACC) v[k] += x;
+    else v[k] = x;
+  };
   const float4 f2 = P.f[2], f3 = P.f[3], f4 = P.f[4], f5 = P.f[5], f6 = P.f[6], f7 = P.f[7];
   const float a = f5.y, b = f5.z, o = f5.w;
   const float onem = 1.f - al;
@@ -477,20 +484,21 @@ __device__ __forceinline__ float pair_grad(const PrimState& P, const Hit& h, flo
   const float wgx = w * gX;
   const float after = FWD_ORDER ? S_ref - (S_prefix + wgx) : S_ref;  // sum of w_j g.X_j, j after i
   const float dal = T * gX - __fdividef(after - pg.gA * pg.Tfin, onem);
-  v[17] = w * pg.gR;
-  v[18] = w * pg.gG;
-  v[19] = w * pg.gB;
+  put(17, w * pg.gR);
+  put(18, w * pg.gG);
+  put(19, w * pg.gB);
   // alpha = min(alpha_max, o G)
   float dG = 0.f;
-  v[16] = 0.f;
+  float g_o = 0.f;
   if (oG < rp.alpha_max) {
-    v[16] = dal * h.G;
+    g_o = dal * h.G;
     dG = dal * o;
   }
+  put(16, g_o);
   const float dQ = -0.5f * h.G * dG;
   const float dE = dQ * h.F2;
-  v[14] = dE * x * x;
-  v[15] = dE * y * y;
+  put(14, dE * x * x);
+  put(15, dE * y * y);
   float gx = dE * 2.f * f6.x * x, gy = dE * 2.f * f6.y * y;
   float da = 0.f, db = 0.f;
   if constexpr (EXTRA) {
@@ -527,22 +535,22 @@ __device__ __forceinline__ float pair_grad(const PrimState& P, const Hit& h, flo
   const float hhx = gx - kk * nlx, hhy = gy - kk * nly, hhz = kk;
   da -= kk * x * x;
   db -= kk * y * y;
-  v[12] = da;
-  v[13] = db;
-  v[9] = hhx;
-  v[10] = hhy;
-  v[11] = hhz;
+  put(12, da);
+  put(13, db);
+  put(9, hhx);
+  put(10, hhy);
+  put(11, hhz);
   // P = p_hat h^T + gamma n_l^T, p_hat = (x, y, zs), n_l = (nlx, nly, -1)
   const float pz = h.zs;
-  v[0] = x * hhx + gmx * nlx;
-  v[1] = x * hhy + gmx * nly;
-  v[2] = x * hhz - gmx;
-  v[3] = y * hhx + gmy * nlx;
-  v[4] = y * hhy + gmy * nly;
-  v[5] = y * hhz - gmy;
-  v[6] = pz * hhx + gmz * nlx;
-  v[7] = pz * hhy + gmz * nly;
-  v[8] = pz * hhz - gmz;
+  put(0, x * hhx + gmx * nlx);
+  put(1, x * hhy + gmx * nly);
+  put(2, x * hhz - gmx);
+  put(3, y * hhx + gmy * nlx);
+  put(4, y * hhy + gmy * nly);
+  put(5, y * hhz - gmy);
+  put(6, pz * hhx + gmz * nlx);
+  put(7, pz * hhy + gmz * nly);
+  put(8, pz * hhz - gmz);
   return wgx;
 }
 
@@ -588,12 +596,40 @@ __device__ __forceinline__ float warp_reduce_scatter20(const float v[32], int& k
 
 }  // namespace
 
+// Backward tile layout: PPT pixels per thread, BLOCK / PPT threads per tile; warp w covers
+// 8 columns and 4 PPT rows of the tile, and a lane's pixel p lies 4 p rows below its first.
+// The pair's state record is read from shared memory once per thread and evaluated for
+// each of its pixels, and the thread's pixels add their gradient records before the warp
+// reduces them, so the staging, the loop and the reduction are paid once per PPT pixels.
+// Records are staged kBwdBatch<PPT> at a time (the shared memory of the smaller CTAs is
+// sized for more CTAs per SM).
+template <int PPT>
+constexpr int kBwdBatch = PPT == 1 ? BLOCK : BLOCK / 2;
+// Two pixels per thread: measured 2 % faster than one at 3M / 1297x840 (the staging, loop
+// and reduction halve per pixel; 95 registers, 5 CTAs of 4 warps per SM instead of 3 of 8).
+// Adding the records of pairs with at most two contributing lanes by shared atomics instead
+// of the reduce-scatter measured 3 % slower.
+constexpr int kBwdPixelsPerThread = 2;
+template <int PPT>
+constexpr size_t raster_bwd_smem() {
+  return (sizeof(PrimState) + sizeof(float) * NGRAD + sizeof(int)) * (size_t)kBwdBatch<PPT>;
+}
+
+namespace {
+template <int PPT>
+__device__ __forceinline__ void pixel_of_bwd(int tile, int tiles_x, int p, int& px, int& py) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  px = (tile % tiles_x) * TILE + (warp & 1) * 8 + (lane & 7);
+  py = (tile / tiles_x) * TILE + (warp >> 1) * (4 * PPT) + (lane >> 3) + 4 * p;
+}
+}  // namespace
+
 // EXTRA: also the gradients of the curvature map and of the depth distortion. With
 // D = A0 A2 - A1^2 (A0 = 1 - T_final, A1, A2 the forward's shifted moments), dL/dA0 =
 // g_D A2 joins the alpha gradient, and tau = t - c and tau^2 act as two more blended
 // channels with upstream gradients -2 g_D A1 and g_D A0.
-template <bool EUCLID, bool EXTRA, bool STATS>
-__global__ void __launch_bounds__(BLOCK, 3)
+template <bool EUCLID, bool EXTRA, bool STATS, int PPT>
+__global__ void __launch_bounds__(BLOCK / PPT, PPT == 1 ? 3 : 5)
     k_raster_bwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids, int id_stride,
                  const PrimState* __restrict__ state, RasterParams rp, const float* __restrict__ g_rgb,
                  const float* __restrict__ g_alpha, const float* __restrict__ g_depth,
@@ -601,68 +637,85 @@ __global__ void __launch_bounds__(BLOCK, 3)
                  const uint32_t* __restrict__ n_contrib, ExtraGrads eg, float* __restrict__ pgrad,
                  RasterStats* __restrict__ stats, const uint32_t* __restrict__ tile_order,
                  const uint8_t* __restrict__ inst_used) {
-  // dynamic shared memory: BLOCK records, then BLOCK x NGRAD accumulators, then flags
+  constexpr int NT = BLOCK / PPT, BATCH = kBwdBatch<PPT>;
+  // dynamic shared memory: BATCH records, then BATCH x NGRAD accumulators, then flags
   extern __shared__ float4 dyn_smem[];
   PrimState* sm = reinterpret_cast<PrimState*>(dyn_smem);
-  float(*sg)[NGRAD] = reinterpret_cast<float(*)[NGRAD]>(sm + BLOCK);
-  int* sflag = reinterpret_cast<int*>(&sg[BLOCK][0]);
+  float(*sg)[NGRAD] = reinterpret_cast<float(*)[NGRAD]>(sm + BATCH);
+  int* sflag = reinterpret_cast<int*>(&sg[BATCH][0]);
   __shared__ int smax;
-  __shared__ uint8_t suse[BLOCK];
+  __shared__ uint8_t suse[BATCH];
   const int tile = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;
-  int px, py;
-  pixel_of(tile, rp.tiles_x, px, py);
-  const bool inside = px < rp.W && py < rp.H;
   const uint2 rg = ranges[tile];
-  const float X = (float)px + 0.5f, Y = (float)py + 0.5f;
-  const float xn = (X - rp.cx) * rp.inv_fx, yn = (Y - rp.cy) * rp.inv_fy;
-  const size_t P = (size_t)rp.W * rp.H, pix = inside ? (size_t)py * rp.W + px : 0;
-  float T = inside ? T_final[pix] : 1.f;
-  const uint32_t last = inside ? n_contrib[pix] : 0u;
-  const PixGrads pg =
-      load_pix_grads<EXTRA>(inside, pix, P, T, g_rgb, g_alpha, g_depth, g_normal, eg);
+  const size_t P = (size_t)rp.W * rp.H;
+  float X[PPT], Y[PPT], xn[PPT], yn[PPT], T[PPT], Sdot[PPT];  // Sdot: sum over later pairs of w (g . X)
+  uint32_t last[PPT], mlast = 0;
+  PixGrads pg[PPT];
+#pragma unroll
+  for (int p = 0; p < PPT; ++p) {
+    int px, py;
+    pixel_of_bwd<PPT>(tile, rp.tiles_x, p, px, py);
+    const bool inside = px < rp.W && py < rp.H;
+    X[p] = (float)px + 0.5f;
+    Y[p] = (float)py + 0.5f;
+    xn[p] = (X[p] - rp.cx) * rp.inv_fx;
+    yn[p] = (Y[p] - rp.cy) * rp.inv_fy;
+    const size_t pix = inside ? (size_t)py * rp.W + px : 0;
+    T[p] = inside ? T_final[pix] : 1.f;
+    last[p] = inside ? n_contrib[pix] : 0u;
+    pg[p] = load_pix_grads<EXTRA>(inside, pix, P, T[p], g_rgb, g_alpha, g_depth, g_normal, eg);
+    Sdot[p] = 0.f;
+    mlast = max(mlast, last[p]);
+  }
   if (threadIdx.x == 0) smax = 0;
   __syncthreads();
   {
-    unsigned m = __reduce_max_sync(FULL, last);
+    const unsigned m = __reduce_max_sync(FULL, mlast);
     if ((threadIdx.x & 31) == 0) atomicMax(&smax, (int)m);
   }
   __syncthreads();
   const int maxlast = smax;
-  float Sdot = 0.f;  // sum over later pairs j of w_j * (g . X_j)
   uint32_t n_pairs = 0, n_contrib_pairs = 0, isect = 0;
-  for (int b0 = ((maxlast - 1) / BLOCK) * BLOCK; maxlast > 0 && b0 >= 0; b0 -= BLOCK) {
-    const int cnt = min(BLOCK, maxlast - b0);
+  for (int b0 = ((maxlast - 1) / BATCH) * BATCH; maxlast > 0 && b0 >= 0; b0 -= BATCH) {
+    const int cnt = min(BATCH, maxlast - b0);
     __syncthreads();
-    stage_batch(sm, ids, id_stride, rp.id_mask, state, rg.x + b0, cnt);
-    for (int e = threadIdx.x; e < BLOCK * NGRAD; e += BLOCK) (&sg[0][0])[e] = 0.f;
-    sflag[threadIdx.x] = 0;
-    suse[threadIdx.x] = (threadIdx.x < cnt && inst_used) ? inst_used[rg.x + b0 + threadIdx.x] : 1;
+    stage_batch<NT>(sm, ids, id_stride, rp.id_mask, state, rg.x + b0, cnt);
+    for (int e = threadIdx.x; e < BATCH * NGRAD; e += NT) (&sg[0][0])[e] = 0.f;
+    for (int e = threadIdx.x; e < BATCH; e += NT) {
+      sflag[e] = 0;
+      suse[e] = (e < cnt && inst_used) ? inst_used[rg.x + b0 + e] : 1;
+    }
     __syncthreads();
     for (int j = cnt - 1; j >= 0; --j) {
       if (!suse[j]) continue;  // no pixel of this tile blended the instance in the forward
-      // gradient record of this pixel's pair (entries 0..NGRAD-1, all written by a
-      // contributing lane; zeroed for the others only when the warp reduces)
+      // gradient record of this thread's pairs (entries 0..NGRAD-1; with one pixel per
+      // thread written by a contributing lane and zeroed for the others only when the
+      // warp reduces, with several pixels summed from zero)
       float v[32];
 #pragma unroll
-      for (int k = NGRAD; k < 32; ++k) v[k] = 0.f;
+      for (int k = (PPT > 1 ? 0 : NGRAD); k < 32; ++k) v[k] = 0.f;
       bool contrib = false;
-      if ((uint32_t)(b0 + j) < last) {
-        Hit h;
-        bool gz = false;
-        ++n_pairs;
-        if (eval_pair<EUCLID>(sm[j], X, Y, rp, h, gz, isect)) {
-          const float oG = __fmul_rn(sm[j].f[5].w, h.G);
-          const float al = fminf(rp.alpha_max, oG);
-          if (al >= rp.alpha_min) {
-            contrib = true;
-            ++n_contrib_pairs;
-            T = __fdividef(T, 1.f - al);  // T_i from T_{i+1}
-            Sdot += pair_grad<EUCLID, EXTRA, false>(sm[j], h, oG, al, T, xn, yn, rp, pg, Sdot, 0.f, v);
+#pragma unroll
+      for (int p = 0; p < PPT; ++p) {
+        if ((uint32_t)(b0 + j) < last[p]) {
+          Hit h;
+          bool gz = false;
+          ++n_pairs;
+          if (eval_pair<EUCLID>(sm[j], X[p], Y[p], rp, h, gz, isect)) {
+            const float oG = __fmul_rn(sm[j].f[5].w, h.G);
+            const float al = fminf(rp.alpha_max, oG);
+            if (al >= rp.alpha_min) {
+              contrib = true;
+              ++n_contrib_pairs;
+              T[p] = __fdividef(T[p], 1.f - al);  // T_i from T_{i+1}
+              Sdot[p] += pair_grad<EUCLID, EXTRA, false, (PPT > 1)>(sm[j], h, oG, al, T[p], xn[p], yn[p], rp,
+                                                                    pg[p], Sdot[p], 0.f, v);
+            }
           }
         }
       }
       if (__any_sync(FULL, contrib)) {
-        if (!contrib) {
+        if (PPT == 1 && !contrib) {
 #pragma unroll
           for (int k = 0; k < NGRAD; ++k) v[k] = 0.f;
         }
@@ -673,7 +726,7 @@ __global__ void __launch_bounds__(BLOCK, 3)
       }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < cnt * NGRAD; e += BLOCK) {
+    for (int e = threadIdx.x; e < cnt * NGRAD; e += NT) {
       const int r = e / NGRAD, c = e - r * NGRAD;
       if (sflag[r]) {
         const float val = sg[r][c];
@@ -1029,14 +1082,16 @@ cudaError_t launch_raster_bwd(bool euclid, bool extra, unsigned grid, cudaStream
                               const float* T_final, const uint32_t* n_contrib, const ExtraGrads& eg, float* pgrad,
                               RasterStats* stats, const uint32_t* tile_order, const uint8_t* inst_used) {
   cudaError_t e = cudaSuccess;
+  constexpr int PPT = kBwdPixelsPerThread;
+  constexpr size_t smem = raster_bwd_smem<PPT>();
   QGS_RASTER_DISPATCH_S(euclid, extra, stats != nullptr, {
-    // the records, accumulators and flags exceed the 48 KB static limit
-    e = cudaFuncSetAttribute(k_raster_bwd<E_, X_, S_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)RASTER_BWD_SMEM);
+    // the records, accumulators and flags exceed the 48 KB static limit (one pixel per
+    // thread); set for every instantiation alike
+    e = cudaFuncSetAttribute(k_raster_bwd<E_, X_, S_, PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-      k_raster_bwd<E_, X_, S_><<<grid, BLOCK, RASTER_BWD_SMEM, st>>>(ranges, ids, id_stride, state, rp, g_rgb,
-                                                                     g_alpha, g_depth, g_normal, T_final, n_contrib,
-                                                                     eg, pgrad, stats, tile_order, inst_used);
+      k_raster_bwd<E_, X_, S_, PPT><<<grid, BLOCK / PPT, smem, st>>>(ranges, ids, id_stride, state, rp, g_rgb,
+                                                                    g_alpha, g_depth, g_normal, T_final, n_contrib,
+                                                                    eg, pgrad, stats, tile_order, inst_used);
   });
   if (e != cudaSuccess) return e;
   return cudaGetLastError();

@@ -1,8 +1,9 @@
 // Serving loop: resident scenes, bounded FIFO queue, memory-budget admission, worker
 // slots with their own rendering context and stream (continuous batching: requests are
-// admitted as slots and budget free up, a free slot takes the queue's head together with
-// the other queued views of the same scene and renders them in shared launches
-// (render_forward_batch), and the kernels of the slots in flight overlap).
+// admitted as slots and budget free up, the kernels of the slots in flight overlap, and a
+// single-slot server's free slot takes the queue's head together with the other queued
+// small views of the same scene and renders them in shared launches, render_forward_batch;
+// see batch_pays).
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -58,16 +59,18 @@ struct Slot {
   std::thread th;
 };
 
-// Shared launches save a view its own launches and host round trip, a fixed cost of a
-// few tens of microseconds, while the batch's sorts grow with all its entries and every
-// request waits for the whole batch. They pay for small frames of batches whose (view,
-// primitive) entries stay within the radix sort's single-kernel passes (2M keys); larger
-// frames are dominated by their own compositing and run as concurrent single renders in
-// other slots instead.
-constexpr int64_t kBatchMaxEntries = int64_t(1) << 21;
+// Shared launches save a view its own launches and host round trip (a fixed cost per frame)
+// but share none of its work: every view preprocesses, sorts and composites its own entries,
+// and the joint sorts cost a little more per view than separate ones. A server with several
+// slots already hides each frame's fixed cost behind the other slots' kernels, and there
+// concurrent single renders measured faster than batches at every scene size and frame size
+// tried (0.2M and 1M quadrics at 256^2, 512x384 and 1024x768: 4 slots 1.0-1.3x the frames/s
+// of 4 slots batching up to 8 views). With one slot nothing hides it, and batches of up to 8
+// small views measured 1.2-2.1x the frames/s of one-at-a-time renders at 256^2 and 512x384
+// (no gain at 1024x768). So only a single-slot server batches, and only frames up to 512x384.
 constexpr int64_t kBatchMaxPixels = 512 * 384;
-inline bool batch_pays(int64_t n_prims, int64_t n_views, const qgs_camera& c) {
-  return n_views * n_prims <= kBatchMaxEntries && (int64_t)c.W * c.H <= kBatchMaxPixels;
+inline bool batch_pays(int n_slots, const qgs_camera& c) {
+  return n_slots == 1 && (int64_t)c.W * c.H <= kBatchMaxPixels;
 }
 
 int64_t request_bytes(const SceneDev& s, const qgs_camera& c, bool bwd) {
@@ -212,10 +215,11 @@ void qgs_server::worker(int si) {
       est = head->est_bytes;
       // the other queued forward views of the same scene that still fit join the head's
       // launches where sharing them pays (a backward request runs alone; see batch_pays)
+      const int n_slots = (int)slots.size();
       for (auto it = queue.begin(); it != queue.end() && !head->want_bwd && (int)batch.size() < max_batch &&
-                                    batch_pays(head->scn.n, (int64_t)batch.size() + 1, head->cam);) {
+                                    batch_pays(n_slots, head->cam);) {
         Request* r = *it;
-        if (!r->want_bwd && r->scene == head->scene && batch_pays(r->scn.n, (int64_t)batch.size() + 1, r->cam) &&
+        if (!r->want_bwd && r->scene == head->scene && batch_pays(n_slots, r->cam) &&
             reserved + est + r->est_bytes <= budget) {
           batch.push_back(r);
           est += r->est_bytes;

@@ -198,6 +198,7 @@ constexpr size_t downsweep_smem() {
 // longer match the digit counts taken before the first pass).
 constexpr uint32_t kStAgg = 1u << 30, kStInc = 2u << 30, kStVal = (1u << 30) - 1u;
 constexpr int kLookbackMaxChunks = 1024;  // sorts of up to 2M keys use the single-pass scatter
+constexpr int kLookbackWindow = 8;        // predecessor status words read per round trip
 
 // Stable scatter of one 2048-key chunk. Keys are ranked per warp (lanes of one digit found
 // with one ballot per digit bit), the per-warp digit counts are scanned across warps and
@@ -268,7 +269,8 @@ __global__ void __launch_bounds__(BLOCK) k_radix_downsweep(const K* __restrict__
     const K key = kk[it];
     const uint32_t d = valid ? digit_of(key, shift, mask) : 0x100u + (uint32_t)lane;
     // lanes holding the same digit: one ballot per digit bit (invalid lanes carry a
-    // lane-unique value above the digit range and match nobody)
+    // lane-unique value above the digit range and match nobody; one match instruction
+    // measured slower than these ballots)
     const uint32_t vmask = __ballot_sync(FULL, valid);  // every lane takes part in each ballot
     uint32_t peers = valid ? vmask : (1u << lane);
 #pragma unroll
@@ -330,24 +332,34 @@ __global__ void __launch_bounds__(BLOCK) k_radix_downsweep(const K* __restrict__
     for (int w = 0; w < RS_WARPS; ++w)
       if (w < warp) gbase += wsum[w];
     gbase += inc - my_off;
-    // look back over the earlier chunks' counts of digit d
+    // look back over the earlier chunks' counts of digit d, kLookbackWindow status words
+    // per round trip (nearest first; a word not yet published is polled on its own)
     uint32_t excl = 0;
     if (live) {
-      for (int k = chunk - 1; k >= 0; --k) {
-        const volatile uint32_t* sw = status + (size_t)k * 256 + d;
-        uint32_t sv = *sw;
-        int spins = 0;
-        while ((sv & ~kStVal) == 0u && spins < spins_max) {
-          __nanosleep(32);
-          sv = *sw;
-          ++spins;
+      bool done = chunk == 0;
+      for (int k0 = chunk - 1; !done && k0 >= 0; k0 -= kLookbackWindow) {
+        uint32_t win[kLookbackWindow];
+#pragma unroll
+        for (int q = 0; q < kLookbackWindow; ++q)
+          win[q] = k0 - q >= 0 ? *(volatile const uint32_t*)(status + (size_t)(k0 - q) * 256 + d) : kStInc;
+#pragma unroll
+        for (int q = 0; q < kLookbackWindow; ++q) {
+          if (done) break;
+          uint32_t sv = win[q];
+          int spins = 0;
+          while ((sv & ~kStVal) == 0u && spins < spins_max) {
+            __nanosleep(32);
+            sv = *(volatile const uint32_t*)(status + (size_t)(k0 - q) * 256 + d);
+            ++spins;
+          }
+          if ((sv & ~kStVal) == 0u) {  // gave up: report, do not hang
+            atomicOr(err, 1u);
+            done = true;
+            break;
+          }
+          excl += sv & kStVal;  // (past chunk 0 the window holds an empty inclusive word)
+          if (sv & kStInc) done = true;
         }
-        if ((sv & ~kStVal) == 0u) {  // gave up: report, do not hang
-          atomicOr(err, 1u);
-          break;
-        }
-        excl += sv & kStVal;
-        if (sv & kStInc) break;
       }
       if (chunk > 0) atomicExch(status + (size_t)chunk * 256 + d, kStInc | (excl + tot));
       boff[d] = gbase + excl;
