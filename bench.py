@@ -105,9 +105,11 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi sampling of SM clock and throttle reasons (every 20 ms, timestamped);
+    started before the warm-up so that sampling is under way when the timed region begins,
+    and summarised over the samples taken inside the timed region's wall-clock window."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -122,11 +124,14 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "20"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (FileNotFoundError, OSError):
             self.proc = None
 
-    def stop(self):
+    def stop(self, window=None):
+        """Summary of the samples whose timestamps fall in window = (t0, t1) (host
+        time.time() seconds); with no sample inside, the samples within 0.25 s of it."""
+        from datetime import datetime
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -134,26 +139,34 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sms, maxs, reasons = [], [], set()
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sms.append(float(parts[1]))
-                maxs.append(float(parts[2]))
+                ts = datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[2]), float(parts[3]),
+                             {nm for nm, v in zip(names, parts[6:10]) if v.lower() == "active"}))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
         os.unlink(self.path)
-        if not sms:
+        where = "all samples"
+        if window is not None:
+            t0, t1 = window
+            inside = [r for r in rows if t0 <= r[0] <= t1]
+            where = "timed region"
+            if not inside:
+                inside = [r for r in rows if t0 - 0.25 <= r[0] <= t1 + 0.25]
+                where = "within 0.25 s of the timed region"
+            rows = inside
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sms.sort()
-        return {"sm_mhz": sms[len(sms) // 2], "sm_max_mhz": max(maxs), "reasons": sorted(reasons),
-                "samples": len(sms)}
+        sms = sorted(r[1] for r in rows)
+        reasons = set().union(*(r[3] for r in rows))
+        return {"sm_mhz": sms[len(sms) // 2], "sm_max_mhz": max(r[2] for r in rows), "reasons": sorted(reasons),
+                "samples": len(rows), "sampled": where, "interval_ms": 20}
 
 
 def _json_default(o):
@@ -463,6 +476,8 @@ def run_gpu(args):
         ras.forward(ds, cam, out)
         ras.backward(ds, cam, gout, grads)
 
+    clocks = ClockSampler(local)
+    clocks.start()                 # sampling under way before the timed region starts
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -474,22 +489,22 @@ def run_gpu(args):
     L.check(lib.qgs_set_profiling(ras._ctx, 1), ras._ctx)
     ras.set_pair_counters(False)
     step()
-    clocks = ClockSampler(local)
-    clocks.start()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    t_wall0 = time.time()
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
+    t_wall1 = time.time()
     if world > 1:
         dist.barrier()
-    clk = clocks.stop()
+    clk = clocks.stop((t_wall0, t_wall1))
     st_timed = ras.stats()  # stage times of the last timed step
     ms = e0.elapsed_time(e1) / args.steps
     # forward alone (the same frame, rendered K times)
@@ -635,6 +650,7 @@ def _variants(args, ds, cam, gout, grads, dev):
     for name, kw, extras in (("extra_channels", {}, True), ("euclid", {"density": "euclid"}, False),
                              ("stopthepop", {"order": "stp"}, False)):
         ras = Rasterizer(dev, **kw)
+        ras.set_pair_counters(False)   # timed steps as the headline's: counters compiled out
         g = gx if extras else gout
 
         def step():
@@ -654,11 +670,14 @@ def _variants(args, ds, cam, gout, grads, dev):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / args.variant_steps
         ras.lib.qgs_set_profiling(ras._ctx, 1)
-        step()
+        step()                         # stage times of a step like the timed ones
         st = ras.stats()
+        ras.set_pair_counters(True)
+        step()                         # blended-pair count from a step with the counters
+        pb = ras.stats()["pair_blended"]
         res[name] = {"mpix_per_s": H * W / (ms * 1e-3) / 1e6, "ms_per_step": ms,
                      "ms_raster_fwd": st["ms_raster_fwd"], "ms_raster_bwd": st["ms_raster_bwd"],
-                     "pair_blended": st["pair_blended"]}
+                     "pair_blended": pb}
         ras.close()
     return res
 

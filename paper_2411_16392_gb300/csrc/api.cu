@@ -876,7 +876,8 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   if (stp)
     QGS_CU(launch_raster_fwd_stp(ctx->cfg.density == 1, extra, (unsigned)ntiles, st, ctx->ranges.p, ctx->ids,
                                  ctx->raster_state, rp, out->rgb, out->alpha, out->depth, out->normal,
-                                 ctx->T_final.p, ctx->n_contrib.p, ctx->xres.p, ex, ctx->stats.p, ctx->tile_order),
+                                 ctx->T_final.p, ctx->n_contrib.p, ctx->xres.p, ex,
+                                 ctx->pair_counters ? ctx->stats.p : nullptr, ctx->tile_order),
            "k_raster_fwd_stp");
   else
     QGS_CU(launch_raster_fwd(ctx->cfg.density == 1, extra, (unsigned)ntiles, st, ctx->ranges.p, ctx->ids,
@@ -884,7 +885,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
                              ctx->T_final.p, ctx->n_contrib.p, ex, ctx->pair_counters ? ctx->stats.p : nullptr,
                              ctx->tile_order, ctx->inst_used.p),
            "k_raster_fwd");
-  ctx->counted_fwd = stp || ctx->pair_counters;
+  ctx->counted_fwd = ctx->pair_counters;
   ctx->counted_bwd = false;
   ctx->stp = stp;
   ++launch_counter();
@@ -1185,7 +1186,8 @@ qgs_status render_backward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camer
   if (ctx->stp)
     QGS_CU(launch_raster_bwd_stp(euclid, extra, (unsigned)ntiles, st, ctx->ranges.p, ctx->ids, ctx->raster_state,
                                  rp, grad_out->rgb, grad_out->alpha, grad_out->depth, grad_out->normal,
-                                 ctx->T_final.p, ctx->xres.p, eg, ctx->pgrad.p, ctx->stats.p, ctx->tile_order),
+                                 ctx->T_final.p, ctx->xres.p, eg, ctx->pgrad.p,
+                                 ctx->pair_counters ? ctx->stats.p : nullptr, ctx->tile_order),
            "k_raster_bwd_stp");
   else
     QGS_CU(launch_raster_bwd(euclid, extra, (unsigned)ntiles, st, ctx->ranges.p, ctx->ids, ctx->id_stride,
@@ -1193,7 +1195,7 @@ qgs_status render_backward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camer
                              grad_out->normal, ctx->T_final.p, ctx->n_contrib.p, eg, ctx->pgrad.p,
                              ctx->pair_counters ? ctx->stats.p : nullptr, ctx->tile_order, ctx->inst_used.p),
            "k_raster_bwd");
-  ctx->counted_bwd = ctx->stp || ctx->pair_counters;
+  ctx->counted_bwd = ctx->pair_counters;
   ++launch_counter();
   mark(ctx, 8, st);
   SceneView sv{scene->mean, scene->quat, scene->scale, scene->curv, scene->opacity, scene->sh};

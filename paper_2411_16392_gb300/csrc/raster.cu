@@ -605,11 +605,15 @@ __device__ __forceinline__ float warp_reduce_scatter20(const float v[32], int& k
 // sized for more CTAs per SM).
 template <int PPT>
 constexpr int kBwdBatch = PPT == 1 ? BLOCK : BLOCK / 2;
-// Two pixels per thread: measured 2 % faster than one at 3M / 1297x840 (the staging, loop
-// and reduction halve per pixel; 95 registers, 5 CTAs of 4 warps per SM instead of 3 of 8).
+// Two pixels per thread when the frame has at least this many tiles per SM: measured 2 %
+// faster than one at 3M / 1297x840 (4346 tiles; the staging, loop and reduction halve per
+// pixel; 95 registers, 5 CTAs of 4 warps per SM instead of 3 of 8), while small frames keep
+// one pixel per thread for the warps it gives them (64 tiles: 0.16 ms against 0.10).
 // Adding the records of pairs with at most two contributing lanes by shared atomics instead
-// of the reduce-scatter measured 3 % slower.
-constexpr int kBwdPixelsPerThread = 2;
+// of the reduce-scatter measured 3 % slower. Two-pixel CTAs take 6 per SM (80 registers, a
+// few spilled stores: 0.5 % faster than 5) except with the extra channels, whose larger
+// state spills more at 6 (5 % slower) and keeps 5.
+constexpr int kBwdTwoPixelTilesPerSM = 8;
 template <int PPT>
 constexpr size_t raster_bwd_smem() {
   return (sizeof(PrimState) + sizeof(float) * NGRAD + sizeof(int)) * (size_t)kBwdBatch<PPT>;
@@ -629,7 +633,7 @@ __device__ __forceinline__ void pixel_of_bwd(int tile, int tiles_x, int p, int& 
 // g_D A2 joins the alpha gradient, and tau = t - c and tau^2 act as two more blended
 // channels with upstream gradients -2 g_D A1 and g_D A0.
 template <bool EUCLID, bool EXTRA, bool STATS, int PPT>
-__global__ void __launch_bounds__(BLOCK / PPT, PPT == 1 ? 3 : 5)
+__global__ void __launch_bounds__(BLOCK / PPT, PPT == 1 ? 3 : (EXTRA ? 5 : 6))
     k_raster_bwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids, int id_stride,
                  const PrimState* __restrict__ state, RasterParams rp, const float* __restrict__ g_rgb,
                  const float* __restrict__ g_alpha, const float* __restrict__ g_depth,
@@ -791,24 +795,41 @@ struct ResortBuf {
   }
 };
 
-__device__ __forceinline__ PrimState load_state(const PrimState* __restrict__ state, uint32_t pid) {
-  PrimState P;
-  const float4* src = reinterpret_cast<const float4*>(state + pid);
-#pragma unroll
-  for (int c = 0; c < 8; ++c) P.f[c] = __ldg(src + c);
-  return P;
-}
 
 }  // namespace
 
-template <bool EUCLID, bool EXTRA>
+// Shared memory of the StopThePop kernels: the staged batch, then one record slot per thread
+// (a blended entry outside the current batch is copied there from global memory, so that
+// its evaluation reads the record from shared memory like a staged one instead of holding
+// all 32 floats in registers).
+constexpr size_t RASTER_STP_SMEM = sizeof(PrimState) * 2 * BLOCK;
+
+namespace {
+// The state record of list position pos: the staged copy when it is in the current batch
+// [cur0, cur1), else the thread's slot filled from global memory.
+__device__ __forceinline__ const PrimState* stp_record(const PrimState* sm, PrimState* slot,
+                                                      const PrimState* __restrict__ state,
+                                                      const uint32_t* __restrict__ ids, uint32_t id_mask,
+                                                      uint32_t pos, uint32_t cur0, uint32_t cur1) {
+  if (pos >= cur0 && pos < cur1) return sm + (pos - cur0);
+  const float4* src = reinterpret_cast<const float4*>(state + (__ldg(ids + pos) & id_mask));
+  float4* dst = reinterpret_cast<float4*>(slot);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) dst[c] = __ldg(src + c);
+  return slot;
+}
+}  // namespace
+
+template <bool EUCLID, bool EXTRA, bool STATS>
 __global__ void __launch_bounds__(BLOCK, 3)
     k_raster_fwd_stp(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids,
                      const PrimState* __restrict__ state, RasterParams rp, float* __restrict__ out_rgb,
                      float* __restrict__ out_alpha, float* __restrict__ out_depth, float* __restrict__ out_normal,
                      float* __restrict__ T_final, uint32_t* __restrict__ n_blended, float* __restrict__ xres,
                      ExtraPlanes ex, RasterStats* __restrict__ stats, const uint32_t* __restrict__ tile_order) {
-  __shared__ PrimState sm[BLOCK];
+  extern __shared__ float4 dyn_smem[];
+  PrimState* sm = reinterpret_cast<PrimState*>(dyn_smem);
+  PrimState* slot = sm + BLOCK + threadIdx.x;
   const int tile = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;
   int px, py;
   pixel_of(tile, rp.tiles_x, px, py);
@@ -826,7 +847,7 @@ __global__ void __launch_bounds__(BLOCK, 3)
   // copy when it is in the current batch, else global memory)
   uint32_t cur0 = 0, cur1 = 0;  // list positions [cur0, cur1) staged in sm
   auto blend = [&](uint32_t pos) {
-    const PrimState P = (pos >= cur0 && pos < cur1) ? sm[pos - cur0] : load_state(state, __ldg(ids + pos) & rp.id_mask);
+    const PrimState& P = *stp_record(sm, slot, state, ids, rp.id_mask, pos, cur0, cur1);
     Hit h;
     bool gz = false;
     if (!eval_pair<EUCLID>(P, X, Y, rp, h, gz, dummy)) return;  // deterministic: it hit when buffered
@@ -923,7 +944,7 @@ __global__ void __launch_bounds__(BLOCK, 3)
       }
     }
   }
-  if (stats) {
+  if (STATS && stats) {
     const unsigned ev = __reduce_add_sync(FULL, evals), is = __reduce_add_sync(FULL, isect);
     const unsigned hi = __reduce_add_sync(FULL, hits), bl = __reduce_add_sync(FULL, blended);
     const unsigned gzz = __reduce_add_sync(FULL, grazes);
@@ -941,7 +962,7 @@ __global__ void __launch_bounds__(BLOCK, 3)
 // atomics, 16 bytes each): the pixels of a tile pop different pairs at the same step, so
 // the warp reduction of the list-order backward does not apply, and per-tile shared
 // accumulators serialise on the many pixels that blend the same near primitive.
-template <bool EUCLID, bool EXTRA>
+template <bool EUCLID, bool EXTRA, bool STATS>
 __global__ void __launch_bounds__(BLOCK, 2)
     k_raster_bwd_stp(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids,
                      const PrimState* __restrict__ state, RasterParams rp, const float* __restrict__ g_rgb,
@@ -949,7 +970,9 @@ __global__ void __launch_bounds__(BLOCK, 2)
                      const float* __restrict__ g_normal, const float* __restrict__ T_final,
                      const float* __restrict__ xres, ExtraGrads eg, float* __restrict__ pgrad,
                      RasterStats* __restrict__ stats, const uint32_t* __restrict__ tile_order) {
-  __shared__ PrimState sm[BLOCK];
+  extern __shared__ float4 dyn_smem[];
+  PrimState* sm = reinterpret_cast<PrimState*>(dyn_smem);
+  PrimState* slot = sm + BLOCK + threadIdx.x;
   const int tile = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;
   int px, py;
   pixel_of(tile, rp.tiles_x, px, py);
@@ -978,7 +1001,7 @@ __global__ void __launch_bounds__(BLOCK, 2)
   uint32_t cur0 = 0, cur1 = 0;  // list positions [cur0, cur1) staged in sm
   auto blend = [&](uint32_t pos) {
     const uint32_t pid = __ldg(ids + pos) & rp.id_mask;
-    const PrimState Ps = (pos >= cur0 && pos < cur1) ? sm[pos - cur0] : load_state(state, pid);
+    const PrimState& Ps = *stp_record(sm, slot, state, ids, rp.id_mask, pos, cur0, cur1);
     Hit h;
     bool gz = false;
     if (!eval_pair<EUCLID>(Ps, X, Y, rp, h, gz, dummy)) return;
@@ -1024,7 +1047,7 @@ __global__ void __launch_bounds__(BLOCK, 2)
     }
   }
   while (!done && buf.n > 0) blend(buf.pop());
-  if (stats) {
+  if (STATS && stats) {
     const unsigned np = __reduce_add_sync(FULL, n_pairs), nc = __reduce_add_sync(FULL, n_contrib_pairs);
     if ((threadIdx.x & 31) == 0) {
       atomicAdd(&stats->bwd_pairs, (unsigned long long)np);
@@ -1082,16 +1105,22 @@ cudaError_t launch_raster_bwd(bool euclid, bool extra, unsigned grid, cudaStream
                               const float* T_final, const uint32_t* n_contrib, const ExtraGrads& eg, float* pgrad,
                               RasterStats* stats, const uint32_t* tile_order, const uint8_t* inst_used) {
   cudaError_t e = cudaSuccess;
-  constexpr int PPT = kBwdPixelsPerThread;
-  constexpr size_t smem = raster_bwd_smem<PPT>();
-  QGS_RASTER_DISPATCH_S(euclid, extra, stats != nullptr, {
+  int dev = 0, n_sm = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  auto go = [&](auto kern, int nt, size_t smem) {
     // the records, accumulators and flags exceed the 48 KB static limit (one pixel per
     // thread); set for every instantiation alike
-    e = cudaFuncSetAttribute(k_raster_bwd<E_, X_, S_, PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-      k_raster_bwd<E_, X_, S_, PPT><<<grid, BLOCK / PPT, smem, st>>>(ranges, ids, id_stride, state, rp, g_rgb,
-                                                                    g_alpha, g_depth, g_normal, T_final, n_contrib,
-                                                                    eg, pgrad, stats, tile_order, inst_used);
+      kern<<<grid, nt, smem, st>>>(ranges, ids, id_stride, state, rp, g_rgb, g_alpha, g_depth, g_normal, T_final,
+                                   n_contrib, eg, pgrad, stats, tile_order, inst_used);
+  };
+  const bool two = (int64_t)grid >= (int64_t)kBwdTwoPixelTilesPerSM * n_sm;
+  QGS_RASTER_DISPATCH_S(euclid, extra, stats != nullptr, {
+    if (two) go(k_raster_bwd<E_, X_, S_, 2>, BLOCK / 2, raster_bwd_smem<2>());
+    else go(k_raster_bwd<E_, X_, S_, 1>, BLOCK, raster_bwd_smem<1>());
   });
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
@@ -1101,10 +1130,16 @@ cudaError_t launch_raster_fwd_stp(bool euclid, bool extra, unsigned grid, cudaSt
                                   float* out_rgb, float* out_alpha, float* out_depth, float* out_normal,
                                   float* T_final, uint32_t* n_blended, float* xres, const ExtraPlanes& ex,
                                   RasterStats* stats, const uint32_t* tile_order) {
-  QGS_RASTER_DISPATCH(euclid, extra,
-                      k_raster_fwd_stp<E_, X_><<<grid, BLOCK, 0, st>>>(ranges, ids, state, rp, out_rgb, out_alpha,
-                                                                       out_depth, out_normal, T_final, n_blended,
-                                                                       xres, ex, stats, tile_order));
+  cudaError_t e = cudaSuccess;
+  QGS_RASTER_DISPATCH_S(euclid, extra, stats != nullptr, {
+    e = cudaFuncSetAttribute(k_raster_fwd_stp<E_, X_, S_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)RASTER_STP_SMEM);
+    if (e == cudaSuccess)
+      k_raster_fwd_stp<E_, X_, S_><<<grid, BLOCK, RASTER_STP_SMEM, st>>>(ranges, ids, state, rp, out_rgb, out_alpha,
+                                                                        out_depth, out_normal, T_final, n_blended,
+                                                                        xres, ex, stats, tile_order);
+  });
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -1114,10 +1149,16 @@ cudaError_t launch_raster_bwd_stp(bool euclid, bool extra, unsigned grid, cudaSt
                                   const float* g_normal, const float* T_final, const float* xres,
                                   const ExtraGrads& eg, float* pgrad, RasterStats* stats,
                                   const uint32_t* tile_order) {
-  QGS_RASTER_DISPATCH(euclid, extra,
-                      k_raster_bwd_stp<E_, X_><<<grid, BLOCK, 0, st>>>(ranges, ids, state, rp, g_rgb, g_alpha,
-                                                                       g_depth, g_normal, T_final, xres, eg, pgrad,
-                                                                       stats, tile_order));
+  cudaError_t e = cudaSuccess;
+  QGS_RASTER_DISPATCH_S(euclid, extra, stats != nullptr, {
+    e = cudaFuncSetAttribute(k_raster_bwd_stp<E_, X_, S_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)RASTER_STP_SMEM);
+    if (e == cudaSuccess)
+      k_raster_bwd_stp<E_, X_, S_><<<grid, BLOCK, RASTER_STP_SMEM, st>>>(ranges, ids, state, rp, g_rgb, g_alpha,
+                                                                        g_depth, g_normal, T_final, xres, eg,
+                                                                        pgrad, stats, tile_order);
+  });
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 #undef QGS_RASTER_DISPATCH_S
