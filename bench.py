@@ -58,11 +58,12 @@ FLOP_GRAD = 200
 # scan (4 B). Preprocess backward per visible primitive: the 80-byte gradient record,
 # the parameters (144 B) and a read-modify-write of the float32 gradients (240 B x 2).
 B_PRE_PRIM, B_PRE_VIS = 164, 128 + 2 * 80
-# DRAM bytes (read + write) per launch of the compositing kernels at 3M / 1297x840, from
-# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, summary under profiles/),
-# valid only while the kernels' sources hash to the recorded value.
+# DRAM bytes (read + write) per launch of the compositing kernels at 3M / 1297x840 (mean over
+# the launches of one ncu launch list, dram__bytes_read.sum + dram__bytes_write.sum; summary
+# in profiles/launches_unbounded_3m_1297x840.md), valid only while the kernels' sources hash
+# to the recorded value.
 TRAFFIC_SRC = ("paper_2411_16392_gb300/csrc/raster.cu", "paper_2411_16392_gb300/csrc/qgs_common.cuh")
-TRAFFIC = {"hash": "aebe601613de2e39", "k_raster_fwd": 13452032 + 1142272, "k_raster_bwd": 56476416 + 27392}
+TRAFFIC = {"hash": "790f88b63115895d", "k_raster_fwd": 13476571 + 513133, "k_raster_bwd": 56407552 + 23244}
 B_BIN_VIS, B_BIN_INST = 4 * 20 + 256, 4 + 2 * 12 + 4
 B_PREBWD_VIS = 80 + 144 + 480
 

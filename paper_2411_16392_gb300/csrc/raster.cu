@@ -755,9 +755,10 @@ __global__ void __launch_bounds__(BLOCK / PPT, PPT == 1 ? 3 : (EXTRA ? 5 : 6))
 // Resorting"): the tile lists are sorted by each primitive's hit depth on the tile's
 // representative ray; each pixel keeps its contributing pairs in a buffer of 8 (hit depth,
 // list position) entries and blends the nearest one whenever the buffer is full, the rest
-// nearest first at the end of the list. An entry is re-evaluated when it is blended (its
-// state record is read again from global memory), so a buffered entry costs two
-// registers. The backward replays the same sequence front to back with the
+// nearest first at the end of the list. An entry is re-evaluated when it is blended (from
+// its state record in shared memory: the staged batch, or a per-thread slot filled from
+// global memory when the entry was staged in an earlier batch), so a buffered entry costs
+// two registers. The backward replays the same sequence front to back with the
 // supplementary's front-to-back dX/d(alpha) and adds each pair's gradient record to
 // global memory per pixel.
 namespace {
@@ -801,17 +802,39 @@ struct ResortBuf {
 // Shared memory of the StopThePop kernels: the staged batch, then one record slot per thread
 // (a blended entry outside the current batch is copied there from global memory, so that
 // its evaluation reads the record from shared memory like a staged one instead of holding
-// all 32 floats in registers).
-constexpr size_t RASTER_STP_SMEM = sizeof(PrimState) * 2 * BLOCK;
+// all 32 floats in registers). Records sit at a 144-byte stride (the 128-byte record and 16
+// bytes of padding): the lanes of a warp blend different entries, and at 128 bytes their
+// 16-byte reads of one field would all fall in the same four banks.
+constexpr int kStpStride = 9;  // float4 per shared record
+constexpr size_t RASTER_STP_SMEM = sizeof(float4) * kStpStride * 2 * BLOCK;
 
 namespace {
+struct StpRecs {
+  float4* base;
+  __device__ __forceinline__ const PrimState& operator[](int r) const {
+    return *reinterpret_cast<const PrimState*>(base + (size_t)r * kStpStride);
+  }
+  __device__ __forceinline__ PrimState* ptr(int r) const {
+    return reinterpret_cast<PrimState*>(base + (size_t)r * kStpStride);
+  }
+};
+
+__device__ __forceinline__ void stage_batch_stp(StpRecs sm, const uint32_t* ids, uint32_t id_mask,
+                                                const PrimState* state, uint32_t first, int cnt) {
+  for (int e = threadIdx.x; e < cnt * 8; e += BLOCK) {
+    const int r = e >> 3, c = e & 7;
+    const uint32_t pid = __ldg(ids + first + r) & id_mask;
+    sm.base[r * kStpStride + c] = __ldg(reinterpret_cast<const float4*>(state + pid) + c);
+  }
+}
+
 // The state record of list position pos: the staged copy when it is in the current batch
 // [cur0, cur1), else the thread's slot filled from global memory.
-__device__ __forceinline__ const PrimState* stp_record(const PrimState* sm, PrimState* slot,
+__device__ __forceinline__ const PrimState* stp_record(StpRecs sm, PrimState* slot,
                                                       const PrimState* __restrict__ state,
                                                       const uint32_t* __restrict__ ids, uint32_t id_mask,
                                                       uint32_t pos, uint32_t cur0, uint32_t cur1) {
-  if (pos >= cur0 && pos < cur1) return sm + (pos - cur0);
+  if (pos >= cur0 && pos < cur1) return &sm[(int)(pos - cur0)];
   const float4* src = reinterpret_cast<const float4*>(state + (__ldg(ids + pos) & id_mask));
   float4* dst = reinterpret_cast<float4*>(slot);
 #pragma unroll
@@ -828,8 +851,8 @@ __global__ void __launch_bounds__(BLOCK, 3)
                      float* __restrict__ T_final, uint32_t* __restrict__ n_blended, float* __restrict__ xres,
                      ExtraPlanes ex, RasterStats* __restrict__ stats, const uint32_t* __restrict__ tile_order) {
   extern __shared__ float4 dyn_smem[];
-  PrimState* sm = reinterpret_cast<PrimState*>(dyn_smem);
-  PrimState* slot = sm + BLOCK + threadIdx.x;
+  const StpRecs sm{dyn_smem};
+  PrimState* slot = sm.ptr(BLOCK + threadIdx.x);
   const int tile = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;
   int px, py;
   pixel_of(tile, rp.tiles_x, px, py);
@@ -888,7 +911,7 @@ __global__ void __launch_bounds__(BLOCK, 3)
   for (int b0 = 0; b0 < n; b0 += BLOCK) {
     if (__syncthreads_count(done) == BLOCK) break;
     const int cnt = min(BLOCK, n - b0);
-    stage_batch(sm, ids, 1, rp.id_mask, state, rg.x + b0, cnt);
+    stage_batch_stp(sm, ids, rp.id_mask, state, rg.x + b0, cnt);
     cur0 = rg.x + (uint32_t)b0;
     cur1 = cur0 + (uint32_t)cnt;
     __syncthreads();
@@ -958,10 +981,12 @@ __global__ void __launch_bounds__(BLOCK, 3)
   }
 }
 
-// Each pixel adds the gradient record of each blended pair to global memory (vector
-// atomics, 16 bytes each): the pixels of a tile pop different pairs at the same step, so
-// the warp reduction of the list-order backward does not apply, and per-tile shared
-// accumulators serialise on the many pixels that blend the same near primitive.
+// Each pixel adds the gradient record of each blended pair to global memory: the pixels of
+// a tile pop their own sequences, so in general the lanes of a warp blend different pairs
+// at the same step and each adds its record with 16-byte vector atomics (per-tile shared
+// accumulators would serialise on the many pixels that blend the same near primitive).
+// A warp that is converged at the blend and blends one primitive in every lane sums the
+// records with the list-order backward's reduce-scatter instead.
 template <bool EUCLID, bool EXTRA, bool STATS>
 __global__ void __launch_bounds__(BLOCK, 2)
     k_raster_bwd_stp(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids,
@@ -971,8 +996,8 @@ __global__ void __launch_bounds__(BLOCK, 2)
                      const float* __restrict__ xres, ExtraGrads eg, float* __restrict__ pgrad,
                      RasterStats* __restrict__ stats, const uint32_t* __restrict__ tile_order) {
   extern __shared__ float4 dyn_smem[];
-  PrimState* sm = reinterpret_cast<PrimState*>(dyn_smem);
-  PrimState* slot = sm + BLOCK + threadIdx.x;
+  const StpRecs sm{dyn_smem};
+  PrimState* slot = sm.ptr(BLOCK + threadIdx.x);
   const int tile = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;
   int px, py;
   pixel_of(tile, rp.tiles_x, px, py);
@@ -1015,18 +1040,32 @@ __global__ void __launch_bounds__(BLOCK, 2)
     float v[32];
     S_prefix += pair_grad<EUCLID, EXTRA, true>(Ps, h, oG, al, T, xn, yn, rp, pg, S_total, S_prefix, v);
     ++n_contrib_pairs;
-    float4* dst = reinterpret_cast<float4*>(pgrad + (size_t)pid * NGRAD_PAD);  // 80-byte records
+    // a whole warp that blends the same primitive at this point (pixels with the same hit
+    // order so far) sums its records with the reduce-scatter; otherwise each lane adds its
+    // record with vector atomics
+    bool reduced = false;
+    if (__activemask() == FULL && __all_sync(FULL, pid == __shfl_sync(FULL, pid, 0))) {
 #pragma unroll
-    for (int k = 0; k < NGRAD / 4; ++k) {
-      const float4 q = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
-      if (q.x != 0.f || q.y != 0.f || q.z != 0.f || q.w != 0.f) atomicAdd(dst + k, q);
+      for (int k = NGRAD; k < 32; ++k) v[k] = 0.f;
+      int kc;
+      const float r = warp_reduce_scatter20(v, kc);
+      if (kc >= 0 && r != 0.f) atomicAdd(pgrad + (size_t)pid * NGRAD_PAD + kc, r);
+      reduced = true;
+    }
+    if (!reduced) {
+      float4* dst = reinterpret_cast<float4*>(pgrad + (size_t)pid * NGRAD_PAD);  // 80-byte records
+#pragma unroll
+      for (int k = 0; k < NGRAD / 4; ++k) {
+        const float4 q = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+        if (q.x != 0.f || q.y != 0.f || q.z != 0.f || q.w != 0.f) atomicAdd(dst + k, q);
+      }
     }
     T = Tn;
   };
   for (int b0 = 0; b0 < n; b0 += BLOCK) {
     if (__syncthreads_count(done) == BLOCK) break;
     const int cnt = min(BLOCK, n - b0);
-    stage_batch(sm, ids, 1, rp.id_mask, state, rg.x + b0, cnt);
+    stage_batch_stp(sm, ids, rp.id_mask, state, rg.x + b0, cnt);
     cur0 = rg.x + (uint32_t)b0;
     cur1 = cur0 + (uint32_t)cnt;
     __syncthreads();

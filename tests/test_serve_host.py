@@ -171,6 +171,30 @@ def test_queued_views_of_one_scene_are_batched(lib):
     s.close()
 
 
+def test_only_single_slot_servers_batch(lib):
+    """Batching saves a view its launches and host round trip, which the other slots already
+    hide: with two slots the queued views run as single renders in both slots; frames
+    larger than 512x384 never batch, not even on one slot."""
+    s = _server(budget_bytes=1 << 40, slots=2, batch=4, fake_us_per_mpix=1_000_000.0)
+    a = s.load_scene(n=10)
+    ts = [s.submit(a, CAM) for _ in range(8)]
+    for t in ts:
+        s.wait(t)
+    st = s.stats()
+    assert st["completed"] == 8 and st["max_batch"] == 1 and st["batches"] == 8
+    assert st["max_in_flight"] == 2
+    s.close()
+    big = Camera(640, 480, 500.0, 500.0, 320.0, 240.0)
+    s = _server(budget_bytes=1 << 40, slots=1, batch=4, fake_us_per_mpix=100_000.0)
+    a = s.load_scene(n=10)
+    ts = [s.submit(a, big) for _ in range(5)]
+    for t in ts:
+        s.wait(t)
+    st = s.stats()
+    assert st["completed"] == 5 and st["max_batch"] == 1
+    s.close()
+
+
 def test_batch_size_is_bounded_by_the_budget(lib):
     per = (10 * 168 + 64 * 65536 * 16 + 64 * 65536 / 16 + 65536 * 40) + (1 << 20)
     s = _server(budget_bytes=int(2.5 * per), slots=1, batch=8, fake_us_per_mpix=500_000.0)
