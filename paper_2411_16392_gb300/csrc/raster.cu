@@ -61,20 +61,20 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 // by rho, (asinh(u)/u + sqrt(1 + u^2)) / 2. For |u| < 0.25 its Taylor series
 // 1 + u^2/6 - u^4/40 + u^6/112 - 5u^8/1152 + 7u^10/2816 (truncation < 1e-10 there; for
 // |u| < 1e-3 only the first three terms matter in FP32); above, the closed form with
-// asinh(|u|) = log(|u| + sqrt(1 + u^2)), well conditioned for |u| >= 0.25.
+// asinh(|u|) = log(|u| + sqrt(1 + u^2)), well conditioned for |u| >= 0.25. Both are
+// formed and one selected (no divergent branch where a warp's lanes fall on both sides).
 __device__ __forceinline__ float arc_ratio(float u) {
   const float au = fabsf(u);
-  if (au < 0.25f) {
-    const float u2 = __fmul_rn(u, u);
-    float p = 7.f / 2816.f;
-    p = __fmaf_rn(p, u2, -5.f / 1152.f);
-    p = __fmaf_rn(p, u2, 1.f / 112.f);
-    p = __fmaf_rn(p, u2, -0.025f);
-    p = __fmaf_rn(p, u2, 1.f / 6.f);
-    return __fmaf_rn(p, u2, 1.f);
-  }
+  const float u2 = __fmul_rn(u, u);
+  float p = 7.f / 2816.f;
+  p = __fmaf_rn(p, u2, -5.f / 1152.f);
+  p = __fmaf_rn(p, u2, 1.f / 112.f);
+  p = __fmaf_rn(p, u2, -0.025f);
+  p = __fmaf_rn(p, u2, 1.f / 6.f);
+  const float ft = __fmaf_rn(p, u2, 1.f);
   const float r = sqrt_approx(__fmaf_rn(au, au, 1.f));
-  return __fmul_rn(0.5f, __fadd_rn(__fdividef(__logf(__fadd_rn(au, r)), au), r));
+  const float fl = __fmul_rn(0.5f, __fadd_rn(__fdividef(__logf(__fadd_rn(au, r)), au), r));
+  return au < 0.25f ? ft : fl;
 }
 
 // dF/du. Series u (1/3 - u^2/10 + 3u^4/56 - 5u^6/144 + 35u^8/1408 - 63u^10/3328) for
@@ -602,17 +602,27 @@ __device__ __forceinline__ float warp_reduce_scatter20(const float v[32], int& k
 // each of its pixels, and the thread's pixels add their gradient records before the warp
 // reduces them, so the staging, the loop and the reduction are paid once per PPT pixels.
 // Records are staged kBwdBatch<PPT> at a time (the shared memory of the smaller CTAs is
-// sized for more CTAs per SM).
+// sized for more CTAs per SM). Each pixel's upstream gradients and residue constants sit
+// in shared memory ([field][thread]), read by the pairs that produce a gradient: the
+// registers they would hold let the two-pixel CTAs fit 7 per SM without spilling
+// (measured 2 % faster than 6 per SM with them in registers and batches of 128).
+#ifndef QGS_BWD_BATCH2
+#define QGS_BWD_BATCH2 64
+#endif
+#ifndef QGS_BWD_CTAS2
+#define QGS_BWD_CTAS2 7
+#endif
 template <int PPT>
-constexpr int kBwdBatch = PPT == 1 ? BLOCK : BLOCK / 2;
+constexpr int kBwdBatch = PPT == 1 ? BLOCK : QGS_BWD_BATCH2;
+template <bool EXTRA>
+constexpr int kPixFields = EXTRA ? 13 : 9;
 // Two pixels per thread when the frame has at least this many tiles per SM: measured 2 %
 // faster than one at 3M / 1297x840 (4346 tiles; the staging, loop and reduction halve per
 // pixel; 95 registers, 5 CTAs of 4 warps per SM instead of 3 of 8), while small frames keep
 // one pixel per thread for the warps it gives them (64 tiles: 0.16 ms against 0.10).
 // Adding the records of pairs with at most two contributing lanes by shared atomics instead
-// of the reduce-scatter measured 3 % slower. Two-pixel CTAs take 6 per SM (80 registers, a
-// few spilled stores: 0.5 % faster than 5) except with the extra channels, whose larger
-// state spills more at 6 (5 % slower) and keeps 5.
+// of the reduce-scatter measured 3 % slower. Two-pixel CTAs take QGS_BWD_CTAS2 per SM except
+// with the extra channels, whose larger state keeps 5.
 constexpr int kBwdTwoPixelTilesPerSM = 8;
 template <int PPT>
 constexpr size_t raster_bwd_smem() {
@@ -626,6 +636,29 @@ __device__ __forceinline__ void pixel_of_bwd(int tile, int tiles_x, int p, int& 
   px = (tile % tiles_x) * TILE + (warp & 1) * 8 + (lane & 7);
   py = (tile / tiles_x) * TILE + (warp >> 1) * (4 * PPT) + (lane >> 3) + 4 * p;
 }
+
+// A pixel's PixGrads in shared memory: field f of this thread's pixel p at
+// s[(p * kPixFields + f) * NT + threadIdx.x] (consecutive threads in consecutive banks).
+template <bool EXTRA, int NT>
+__device__ __forceinline__ void store_pix(float* s, int p, const PixGrads& g) {
+  float* b = s + (size_t)p * kPixFields<EXTRA> * NT + threadIdx.x;
+  b[0 * NT] = g.gR; b[1 * NT] = g.gG; b[2 * NT] = g.gB; b[3 * NT] = g.gA;
+  b[4 * NT] = g.gD; b[5 * NT] = g.gNx; b[6 * NT] = g.gNy; b[7 * NT] = g.gNz; b[8 * NT] = g.Tfin;
+  if constexpr (EXTRA) {
+    b[9 * NT] = g.gK; b[10 * NT] = g.tref; b[11 * NT] = g.g_tau; b[12 * NT] = g.g_tau2;
+  }
+}
+template <bool EXTRA, int NT>
+__device__ __forceinline__ PixGrads load_pix(const float* s, int p) {
+  const float* b = s + (size_t)p * kPixFields<EXTRA> * NT + threadIdx.x;
+  PixGrads g{};
+  g.gR = b[0 * NT]; g.gG = b[1 * NT]; g.gB = b[2 * NT]; g.gA = b[3 * NT];
+  g.gD = b[4 * NT]; g.gNx = b[5 * NT]; g.gNy = b[6 * NT]; g.gNz = b[7 * NT]; g.Tfin = b[8 * NT];
+  if constexpr (EXTRA) {
+    g.gK = b[9 * NT]; g.tref = b[10 * NT]; g.g_tau = b[11 * NT]; g.g_tau2 = b[12 * NT];
+  }
+  return g;
+}
 }  // namespace
 
 // EXTRA: also the gradients of the curvature map and of the depth distortion. With
@@ -633,7 +666,7 @@ __device__ __forceinline__ void pixel_of_bwd(int tile, int tiles_x, int p, int& 
 // g_D A2 joins the alpha gradient, and tau = t - c and tau^2 act as two more blended
 // channels with upstream gradients -2 g_D A1 and g_D A0.
 template <bool EUCLID, bool EXTRA, bool STATS, int PPT>
-__global__ void __launch_bounds__(BLOCK / PPT, PPT == 1 ? 3 : (EXTRA ? 5 : 6))
+__global__ void __launch_bounds__(BLOCK / PPT, PPT == 1 ? 3 : (EXTRA ? 5 : QGS_BWD_CTAS2))
     k_raster_bwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids, int id_stride,
                  const PrimState* __restrict__ state, RasterParams rp, const float* __restrict__ g_rgb,
                  const float* __restrict__ g_alpha, const float* __restrict__ g_depth,
@@ -654,7 +687,7 @@ __global__ void __launch_bounds__(BLOCK / PPT, PPT == 1 ? 3 : (EXTRA ? 5 : 6))
   const size_t P = (size_t)rp.W * rp.H;
   float X[PPT], Y[PPT], xn[PPT], yn[PPT], T[PPT], Sdot[PPT];  // Sdot: sum over later pairs of w (g . X)
   uint32_t last[PPT], mlast = 0;
-  PixGrads pg[PPT];
+  __shared__ float spg[PPT * kPixFields<EXTRA> * NT];
 #pragma unroll
   for (int p = 0; p < PPT; ++p) {
     int px, py;
@@ -667,7 +700,7 @@ __global__ void __launch_bounds__(BLOCK / PPT, PPT == 1 ? 3 : (EXTRA ? 5 : 6))
     const size_t pix = inside ? (size_t)py * rp.W + px : 0;
     T[p] = inside ? T_final[pix] : 1.f;
     last[p] = inside ? n_contrib[pix] : 0u;
-    pg[p] = load_pix_grads<EXTRA>(inside, pix, P, T[p], g_rgb, g_alpha, g_depth, g_normal, eg);
+    store_pix<EXTRA, NT>(spg, p, load_pix_grads<EXTRA>(inside, pix, P, T[p], g_rgb, g_alpha, g_depth, g_normal, eg));
     Sdot[p] = 0.f;
     mlast = max(mlast, last[p]);
   }
@@ -712,8 +745,9 @@ __global__ void __launch_bounds__(BLOCK / PPT, PPT == 1 ? 3 : (EXTRA ? 5 : 6))
               contrib = true;
               ++n_contrib_pairs;
               T[p] = __fdividef(T[p], 1.f - al);  // T_i from T_{i+1}
+              const PixGrads pgp = load_pix<EXTRA, NT>(spg, p);
               Sdot[p] += pair_grad<EUCLID, EXTRA, false, (PPT > 1)>(sm[j], h, oG, al, T[p], xn[p], yn[p], rp,
-                                                                    pg[p], Sdot[p], 0.f, v);
+                                                                    pgp, Sdot[p], 0.f, v);
             }
           }
         }
