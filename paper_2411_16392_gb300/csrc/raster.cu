@@ -789,12 +789,14 @@ __global__ void __launch_bounds__(BLOCK / PPT, PPT == 1 ? 3 : (EXTRA ? 5 : QGS_B
 // Resorting"): the tile lists are sorted by each primitive's hit depth on the tile's
 // representative ray; each pixel keeps its contributing pairs in a buffer of 8 (hit depth,
 // list position) entries and blends the nearest one whenever the buffer is full, the rest
-// nearest first at the end of the list. An entry is re-evaluated when it is blended (from
-// its state record in shared memory: the staged batch, or a per-thread slot filled from
-// global memory when the entry was staged in an earlier batch), so a buffered entry costs
-// two registers. The backward replays the same sequence front to back with the
-// supplementary's front-to-back dX/d(alpha) and adds each pair's gradient record to
-// global memory per pixel.
+// nearest first at the end of the list. The forward keeps each buffered entry's blend data
+// (alpha and the normal, formed at its push) in shared memory, so blending it needs only
+// its colour. The backward replays the same sequence front to back with the
+// supplementary's front-to-back dX/d(alpha), re-evaluating an entry when it is blended
+// (from its state record in shared memory: the staged batch, or a per-thread slot filled
+// from global memory when the entry was staged in an earlier batch; the gradient needs the
+// whole hit, too much to buffer), and adds each pair's gradient record to global memory
+// per pixel.
 namespace {
 
 constexpr int RESORT = 8;
@@ -833,14 +835,13 @@ struct ResortBuf {
 
 }  // namespace
 
-// Shared memory of the StopThePop kernels: the staged batch, then one record slot per thread
-// (a blended entry outside the current batch is copied there from global memory, so that
-// its evaluation reads the record from shared memory like a staged one instead of holding
-// all 32 floats in registers). Records sit at a 144-byte stride (the 128-byte record and 16
-// bytes of padding): the lanes of a warp blend different entries, and at 128 bytes their
-// 16-byte reads of one field would all fall in the same four banks.
+// Shared memory of the StopThePop backward: the staged batch, then one record slot per
+// thread (a blended entry outside the current batch is copied there from global memory, so
+// that its evaluation reads the record from shared memory like a staged one instead of
+// holding all 32 floats in registers). Records sit at a 144-byte stride (the 128-byte
+// record and 16 bytes of padding): the lanes of a warp blend different entries, and at 128
+// bytes their 16-byte reads of one field would all fall in the same four banks.
 constexpr int kStpStride = 9;  // float4 per shared record
-constexpr size_t RASTER_STP_SMEM = sizeof(float4) * kStpStride * 2 * BLOCK;
 // The backward stages 128 records per batch and keeps each pixel's upstream gradients in
 // shared memory: with the registers and shared memory that frees, 3 CTAs fit per SM
 // instead of 2 (measured 5.28 -> 4.65 ms at 3M / 1297x840).
@@ -880,7 +881,67 @@ __device__ __forceinline__ const PrimState* stp_record(StpRecs sm, PrimState* sl
   for (int c = 0; c < 8; ++c) dst[c] = __ldg(src + c);
   return slot;
 }
+
+// The forward's resort buffer with the blend data of each buffered entry: (hit depth, list
+// position) in registers for the selection, and what blending the entry needs, formed
+// when it is pushed (alpha, the normal's signed 1/|n_c| and n_c, with the extra channels
+// the Gaussian curvature), in shared memory: field f of entry k at
+// ent[(k * NF + f) * BLOCK + threadIdx.x]. Popping moves the last entry into the freed one.
+template <int NF>
+struct StpEntries {
+  float t[RESORT];
+  uint32_t pos[RESORT];
+  int n = 0;
+  float* ent;
+  __device__ __forceinline__ void push(float tt, uint32_t p, const float (&d)[NF]) {
+#pragma unroll
+    for (int k = 0; k < RESORT; ++k)
+      if (k == n) { t[k] = tt; pos[k] = p; }
+    float* b = ent + (size_t)n * NF * BLOCK + threadIdx.x;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) b[f * BLOCK] = d[f];
+    ++n;
+  }
+  // remove the entry with the smallest (depth, list position): its depth in tt, its data in d
+  __device__ __forceinline__ uint32_t pop(float& tt, float (&d)[NF]) {
+    float bt = INFINITY;
+    uint32_t bp = 0xFFFFFFFFu;
+    int bk = 0;
+#pragma unroll
+    for (int k = 0; k < RESORT; ++k)
+      if (k < n && (t[k] < bt || (t[k] == bt && pos[k] < bp))) { bt = t[k]; bp = pos[k]; bk = k; }
+    float* b = ent + (size_t)bk * NF * BLOCK + threadIdx.x;
+    const float* l = ent + (size_t)(n - 1) * NF * BLOCK + threadIdx.x;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      d[f] = b[f * BLOCK];
+      b[f * BLOCK] = l[f * BLOCK];
+    }
+    float lt = 0.f;
+    uint32_t lp = 0;
+#pragma unroll
+    for (int k = 0; k < RESORT; ++k)
+      if (k == n - 1) { lt = t[k]; lp = pos[k]; }
+#pragma unroll
+    for (int k = 0; k < RESORT; ++k)
+      if (k == bk) { t[k] = lt; pos[k] = lp; }
+    --n;
+    tt = bt;
+    return bp;
+  }
+};
+template <bool EXTRA>
+constexpr int kStpEntFields = EXTRA ? 6 : 5;
 }  // namespace
+
+// The forward stages kStpFwdBatch records per batch, then holds the entries' blend data
+// (measured 3.28 -> 2.67 ms at 3M / 1297x840 against re-evaluating each blended entry;
+// 96 records at 4 CTAs per SM spill and take 2.83 ms).
+constexpr int kStpFwdBatch = 128;
+template <bool EXTRA>
+constexpr size_t raster_stp_fwd_smem() {
+  return sizeof(float4) * kStpStride * kStpFwdBatch + sizeof(float) * RESORT * kStpEntFields<EXTRA> * BLOCK;
+}
 
 template <bool EUCLID, bool EXTRA, bool STATS>
 __global__ void __launch_bounds__(BLOCK, 3)
@@ -889,9 +950,9 @@ __global__ void __launch_bounds__(BLOCK, 3)
                      float* __restrict__ out_alpha, float* __restrict__ out_depth, float* __restrict__ out_normal,
                      float* __restrict__ T_final, uint32_t* __restrict__ n_blended, float* __restrict__ xres,
                      ExtraPlanes ex, RasterStats* __restrict__ stats, const uint32_t* __restrict__ tile_order) {
+  constexpr int NF = kStpEntFields<EXTRA>;
   extern __shared__ float4 dyn_smem[];
   const StpRecs sm{dyn_smem};
-  PrimState* slot = sm.ptr(BLOCK + threadIdx.x);
   const int tile = tile_order ? (int)tile_order[blockIdx.x] : (int)blockIdx.x;
   int px, py;
   pixel_of(tile, rp.tiles_x, px, py);
@@ -902,42 +963,37 @@ __global__ void __launch_bounds__(BLOCK, 3)
   const float xn = (X - rp.cx) * rp.inv_fx, yn = (Y - rp.cy) * rp.inv_fy;
   float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, dep = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
   float kc = 0.f, tref = 0.f, A1 = 0.f, A2 = 0.f, med = 0.f;
-  uint32_t evals = 0, grazes = 0, isect = 0, hits = 0, blended = 0, dummy = 0;
+  uint32_t evals = 0, grazes = 0, isect = 0, hits = 0, blended = 0;
   bool done = !inside;
-  ResortBuf buf;
-  // blend the entry at list position pos (re-evaluated from its state record: the staged
-  // copy when it is in the current batch, else global memory)
+  StpEntries<NF> buf;
+  buf.ent = reinterpret_cast<float*>(dyn_smem + (size_t)kStpStride * kStpFwdBatch);
   uint32_t cur0 = 0, cur1 = 0;  // list positions [cur0, cur1) staged in sm
-  auto blend = [&](uint32_t pos) {
-    const PrimState& P = *stp_record(sm, slot, state, ids, rp.id_mask, pos, cur0, cur1);
-    Hit h;
-    bool gz = false;
-    if (!eval_pair<EUCLID>(P, X, Y, rp, h, gz, dummy)) return;  // deterministic: it hit when buffered
-    const float4 f2 = P.f[2], f3 = P.f[3], f4 = P.f[4], f5 = P.f[5], f6 = P.f[6], f7 = P.f[7];
-    const float al = fminf(rp.alpha_max, __fmul_rn(f5.w, h.G));
+  // blend the buffered entry with the smallest hit depth, from the data kept at its push
+  // (its colour from the staged record when it is in the current batch, else global memory)
+  auto blend = [&]() {
+    float t;
+    float d[NF];
+    const uint32_t pos = buf.pop(t, d);
+    const float al = d[0];
     const float Tn = __fmul_rn(T, __fsub_rn(1.f, al));
     if (Tn < rp.T_min) {
       done = true;
       return;
     }
+    const float4 f7 = (pos >= cur0 && pos < cur1)
+                          ? sm[(int)(pos - cur0)].f[7]
+                          : __ldg(reinterpret_cast<const float4*>(state + (__ldg(ids + pos) & rp.id_mask)) + 7);
     const float w = al * T;
     cr = fmaf(w, f7.y, cr);
     cg = fmaf(w, f7.z, cg);
     cb = fmaf(w, f7.w, cb);
-    const float t = f2.w + h.s;
     dep = fmaf(w, t, dep);
-    const float nlx = 2.f * f5.y * h.x, nly = 2.f * f5.z * h.y;
-    const float ncx = fmaf(f3.x, nlx, fmaf(f3.z, nly, -f4.x));
-    const float ncy = fmaf(f3.y, nlx, fmaf(f3.w, nly, -f4.y));
-    const float ncz = fmaf(f6.z, nlx, fmaf(f6.w, nly, -f7.x));
-    float inn = rsqrtf(fmaf(ncx, ncx, fmaf(ncy, ncy, ncz * ncz)));
-    if (fmaf(ncx, xn, fmaf(ncy, yn, ncz)) > 0.f) inn = -inn;
-    const float wn = w * inn;
-    nx = fmaf(wn, ncx, nx);
-    ny = fmaf(wn, ncy, ny);
-    nz = fmaf(wn, ncz, nz);
+    const float wn = w * d[1];
+    nx = fmaf(wn, d[2], nx);
+    ny = fmaf(wn, d[3], ny);
+    nz = fmaf(wn, d[4], nz);
     if constexpr (EXTRA) {
-      kc = fmaf(w, curvature(f5.y, f5.z, h.x, h.y), kc);
+      kc = fmaf(w, d[5], kc);
       if (blended == 0) tref = t;
       const float tau = t - tref;
       A1 = fmaf(w, tau, A1);
@@ -947,9 +1003,9 @@ __global__ void __launch_bounds__(BLOCK, 3)
     T = Tn;
     ++blended;
   };
-  for (int b0 = 0; b0 < n; b0 += BLOCK) {
+  for (int b0 = 0; b0 < n; b0 += kStpFwdBatch) {
     if (__syncthreads_count(done) == BLOCK) break;
-    const int cnt = min(BLOCK, n - b0);
+    const int cnt = min(kStpFwdBatch, n - b0);
     stage_batch_stp(sm, ids, rp.id_mask, state, rg.x + b0, cnt);
     cur0 = rg.x + (uint32_t)b0;
     cur1 = cur0 + (uint32_t)cnt;
@@ -959,21 +1015,38 @@ __global__ void __launch_bounds__(BLOCK, 3)
         ++evals;
         Hit h;
         bool gz = false;
-        const bool hit = eval_pair<EUCLID>(sm[j], X, Y, rp, h, gz, isect);
+        const PrimState& P = sm[j];
+        const bool hit = eval_pair<EUCLID>(P, X, Y, rp, h, gz, isect);
         grazes += gz;
         if (!hit) continue;
         ++hits;
-        const float al = fminf(rp.alpha_max, __fmul_rn(sm[j].f[5].w, h.G));
+        const float4 f5 = P.f[5];
+        const float al = fminf(rp.alpha_max, __fmul_rn(f5.w, h.G));
         if (al < rp.alpha_min) continue;
-        buf.push(sm[j].f[2].w + h.s, rg.x + (uint32_t)(b0 + j));
+        // the blend data: alpha and the camera-space normal n_c = W n_l, facing the camera
+        const float4 f3 = P.f[3], f4 = P.f[4], f6 = P.f[6], f7 = P.f[7];
+        const float nlx = 2.f * f5.y * h.x, nly = 2.f * f5.z * h.y;
+        const float ncx = fmaf(f3.x, nlx, fmaf(f3.z, nly, -f4.x));
+        const float ncy = fmaf(f3.y, nlx, fmaf(f3.w, nly, -f4.y));
+        const float ncz = fmaf(f6.z, nlx, fmaf(f6.w, nly, -f7.x));
+        float inn = rsqrtf(fmaf(ncx, ncx, fmaf(ncy, ncy, ncz * ncz)));
+        if (fmaf(ncx, xn, fmaf(ncy, yn, ncz)) > 0.f) inn = -inn;
+        float d[NF];
+        d[0] = al;
+        d[1] = inn;
+        d[2] = ncx;
+        d[3] = ncy;
+        d[4] = ncz;
+        if constexpr (EXTRA) d[NF - 1] = curvature(f5.y, f5.z, h.x, h.y);
+        buf.push(P.f[2].w + h.s, rg.x + (uint32_t)(b0 + j), d);
         if (buf.n == RESORT) {
-          blend(buf.pop());
+          blend();
           if (done) break;
         }
       }
     }
   }
-  while (!done && buf.n > 0) blend(buf.pop());
+  while (!done && buf.n > 0) blend();
   if (inside) {
     const size_t P = (size_t)rp.W * rp.H, pix = (size_t)py * rp.W + px;
     out_rgb[pix] = cr;
@@ -1214,9 +1287,9 @@ cudaError_t launch_raster_fwd_stp(bool euclid, bool extra, unsigned grid, cudaSt
   cudaError_t e = cudaSuccess;
   QGS_RASTER_DISPATCH_S(euclid, extra, stats != nullptr, {
     e = cudaFuncSetAttribute(k_raster_fwd_stp<E_, X_, S_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)RASTER_STP_SMEM);
+                             (int)raster_stp_fwd_smem<X_>());
     if (e == cudaSuccess)
-      k_raster_fwd_stp<E_, X_, S_><<<grid, BLOCK, RASTER_STP_SMEM, st>>>(ranges, ids, state, rp, out_rgb, out_alpha,
+      k_raster_fwd_stp<E_, X_, S_><<<grid, BLOCK, raster_stp_fwd_smem<X_>(), st>>>(ranges, ids, state, rp, out_rgb, out_alpha,
                                                                         out_depth, out_normal, T_final, n_blended,
                                                                         xres, ex, stats, tile_order);
   });
