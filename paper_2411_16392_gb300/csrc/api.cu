@@ -683,7 +683,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   QGS_CU(ctx->cnt_sorted.reserve(n1), "alloc cnt");
   QGS_CU(ctx->offs.reserve(n1 + 1), "alloc offs");
   QGS_CU(ctx->rect.reserve(n1), "alloc rect");
-  if (sm == 0) QGS_CU(ctx->vpos.reserve(n1 + 1), "alloc visibility scan");
+  QGS_CU(ctx->vpos.reserve(n1 + 1), "alloc visibility scan");
   QGS_CU(ctx->tslab.reserve(n1), "alloc tile slabs");
   QGS_CU(ctx->tbits_off.reserve(n1), "alloc tile mask offsets");
   if (ctx->tbits_want) QGS_CU(ctx->tbits.reserve(ctx->tbits_want), "alloc tile masks");
@@ -716,7 +716,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
     QGS_CU(cudaGetLastError(), "k_preprocess");
     // keep the rectangle's tiles that meet the parallelogram and the conic; totals and visibility
     k_count_tiles<<<(unsigned)((N + kCountBlock - 1) / kCountBlock), kCountBlock, 0, st>>>(N, ctx->tslab.p, cam->W, cam->H, ctx->count.p, ctx->rect.p,
-                                           ctx->zkey.p, sm == 0 ? ctx->vpos.p : nullptr, ctx->dcount.p,
+                                           ctx->zkey.p, ctx->vpos.p, ctx->dcount.p,
                                            tb_on ? ctx->tbits.p : nullptr, ctx->tbits_off.p, cap_words);
     ++launch_counter();
     QGS_CU(cudaGetLastError(), "k_count_tiles");
@@ -728,7 +728,8 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   QGS_CU(cudaMemcpyAsync(ctx->h_total, ctx->dcount.p, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "totals");
   if (!ctx->totals_ready) QGS_CU(cudaEventCreateWithFlags(&ctx->totals_ready, cudaEventDisableTiming), "event");
   QGS_CU(cudaEventRecord(ctx->totals_ready, st), "event");
-  if (sm == 0 && N > 0) {
+  // (both key modes: the list also drives the preprocessing backward)
+  if (N > 0) {
     QGS_CU(scan_exclusive_u32(ctx->vpos.p, ctx->vpos.p, N, ctx->scan_tmp.p, ctx->scan_tmp.cap, st), "scan");
     k_compact<<<nblk(N), 256, 0, st>>>(N, ctx->count.p, ctx->zkey.p, ctx->vpos.p, ctx->zkey2.p, ctx->idx2.p);
     ++launch_counter();
@@ -849,7 +850,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
     rp.id_mask = 0xFFFFFFFFu;
     ctx->raster_state = ctx->state.p;
     ctx->pgrad_by_pos = false;
-    ctx->vis_list = nullptr;
+    ctx->vis_list = ctx->idx2.p;  // visible primitives in index order (gradient records by index)
   }
   ctx->sorted_keys = sorted;
   QGS_CU(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(uint2) * (size_t)ntiles, st), "memset ranges");

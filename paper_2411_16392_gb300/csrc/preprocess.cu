@@ -794,7 +794,7 @@ __device__ __forceinline__ uint32_t hit_key_bits(const float muc[3], const float
 
 }  // namespace
 
-__global__ void __launch_bounds__(256) k_emit_hit(int64_t n, SceneView sc, CamParams cp,
+__global__ void __launch_bounds__(256, 4) k_emit_hit(int64_t n, SceneView sc, CamParams cp,
                                                   const uint32_t* __restrict__ count,
                                                   const short4* __restrict__ rect,
                                                   const TileSlab* __restrict__ tslab,
