@@ -63,7 +63,7 @@ B_PRE_PRIM, B_PRE_VIS = 164, 128 + 2 * 80
 # in profiles/launches_unbounded_3m_1297x840.md), valid only while the kernels' sources hash
 # to the recorded value.
 TRAFFIC_SRC = ("paper_2411_16392_gb300/csrc/raster.cu", "paper_2411_16392_gb300/csrc/qgs_common.cuh")
-TRAFFIC = {"hash": "4c553090f699c973", "k_raster_fwd": 13474889 + 814190, "k_raster_bwd": 56434790 + 10138}
+TRAFFIC = {"hash": "cab7d0c979ceeed0", "k_raster_fwd": 13474889 + 814190, "k_raster_bwd": 56434790 + 10138}
 B_BIN_VIS, B_BIN_INST = 4 * 20 + 256, 4 + 2 * 12 + 4
 B_PREBWD_VIS = 80 + 144 + 480
 

@@ -2,9 +2,9 @@
 //
 // One CTA per 16x16 tile; the forward takes one thread per pixel (warps cover 8x4 pixel
 // blocks), the backward two (warps cover 8x8 blocks, see k_raster_bwd). The
-// tile's sorted primitive list is walked in batches of 256 projected-state records
-// staged in shared memory (one 128-byte line per primitive, gathered by 8 threads per
-// record). Per (pixel, primitive) pair:
+// tile's sorted primitive list is walked in batches of projected-state records staged in
+// shared memory (256 in the forward, 64 in the two-pixel backward; one 128-byte line per
+// primitive, gathered by 8 threads per record). Per (pixel, primitive) pair:
 //   - the pixel's offset from the projected centre (double-float) is tested against the
 //     screen conic of the chord ellipsoid x^2/s_u^2 + y^2/s_v^2 + z^2/m^2 <= 9 that holds
 //     the support (arc >= chord): a pixel whose ray line misses it cannot have a hit;
