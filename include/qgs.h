@@ -253,6 +253,19 @@ qgs_status qgs_check_frame(qgs_ctx* ctx);
  * the next forward. spins <= 0 clears it. Errors: EINVAL. */
 qgs_status qgs_debug_withhold_sort_chunk(qgs_ctx* ctx, int32_t spins);
 
+/* Debug bounds checks (the paper has no counterpart). A library built with
+ * -DQGS_DEBUG_CHECKS (paper_2411_16392_gb300.build.build(debug_checks=True), which writes
+ * libqgs_check.so beside libqgs.so) checks the computed indices of its binning kernels: the
+ * slot of every emitted tile instance against the frame's instance count (bit 1), every
+ * tile id of the range pass against the tile grid (bit 2), and every scatter position of the
+ * radix sort against its chunk and its key count (bit 4). A failed check sets its bit and
+ * skips the access (nothing traps). This call waits for the device `device`, then reports
+ * whether the checks are compiled in (*compiled_in, 0 or 1) and the bits set since the last
+ * call on that device (*word, cleared by the read). In the normal build *compiled_in and
+ * *word are 0 and the device is not touched. Errors: EINVAL (NULL pointer, bad device),
+ * ECUDA. */
+qgs_status qgs_debug_check_word(int32_t device, int32_t* compiled_in, uint32_t* word);
+
 /* Copy the last forward's tile binning to HOST memory, for inspection and tests:
  * keys[i] = (tile << 32) | float bits of the primitive's view depth, vals[i] = primitive
  * index, in sorted order (cap entries at most); ranges[2*t], ranges[2*t+1] = [start, end)

@@ -79,6 +79,7 @@ EXPORTS = [
     ("qgs_copy_residue", C.c_int, [_P, _P, _P]),
     ("qgs_check_frame", C.c_int, [_P]),
     ("qgs_debug_withhold_sort_chunk", C.c_int, [_P, C.c_int32]),
+    ("qgs_debug_check_word", C.c_int, [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_uint32)]),
     ("qgs_set_profiling", C.c_int, [_P, C.c_int32]),
     ("qgs_set_tile_mask_capacity", C.c_int, [_P, C.c_int64]),
     ("qgs_set_pair_counters", C.c_int, [_P, C.c_int32]),
@@ -100,7 +101,9 @@ _lib = None
 
 
 def load():
-    """Load libqgs.so and declare its entry points. Raises if it is missing."""
+    """Load libqgs.so (or the library at LIB_PATH, e.g. the bounds-checked build
+    libqgs_check.so when a process sets it before the first load) and declare its entry
+    points. Raises if it is missing."""
     global _lib
     if _lib is not None:
         return _lib

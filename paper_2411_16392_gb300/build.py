@@ -1,7 +1,9 @@
 """Build libqgs.so (the CUDA kernels and the C ABI) in-tree for sm_103a.
 
 Each .cu file under csrc/ is compiled to an object in parallel, then linked into
-paper_2411_16392_gb300/libqgs.so. Run as `python -m paper_2411_16392_gb300.build`.
+paper_2411_16392_gb300/libqgs.so. Run as `python -m paper_2411_16392_gb300.build`
+(`--debug-checks`: the variant with the binning kernels' bounds checks compiled in,
+libqgs_check.so, see qgs_debug_check_word in include/qgs.h).
 """
 from __future__ import annotations
 
@@ -15,6 +17,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "libqgs.so")
+OUT_CHECK = os.path.join(PKG, "libqgs_check.so")
 BUILD_DIR = os.path.join(ROOT, "_build", "qgs")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
@@ -32,8 +35,8 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def _compile(nvcc, src, extra):
-    obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
+def _compile(nvcc, src, extra, build_dir=BUILD_DIR):
+    obj = os.path.join(build_dir, os.path.basename(src) + ".o")
     cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -41,26 +44,31 @@ def _compile(nvcc, src, extra):
     return obj, r.stderr
 
 
-def build(verbose: bool = False, ptxas_info: bool = False) -> str:
+def build(verbose: bool = False, ptxas_info: bool = False, debug_checks: bool = False) -> str:
+    """Compile and link the library; returns its path (libqgs_check.so with debug_checks)."""
     nvcc = _nvcc()
-    os.makedirs(BUILD_DIR, exist_ok=True)
+    build_dir = BUILD_DIR + ("_check" if debug_checks else "")
+    out = OUT_CHECK if debug_checks else OUT
+    os.makedirs(build_dir, exist_ok=True)
     extra = ["-Xptxas", "-v"] if ptxas_info else []
+    if debug_checks:
+        extra += ["-DQGS_DEBUG_CHECKS"]
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        results = list(ex.map(lambda s: _compile(nvcc, s, extra), srcs))
+        results = list(ex.map(lambda s: _compile(nvcc, s, extra, build_dir), srcs))
     if verbose or ptxas_info:
         for (obj, err) in results:
             if err.strip():
                 print(err, file=sys.stderr)
     objs = [o for o, _ in results]
-    tmp = OUT + ".tmp"
+    tmp = out + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, OUT)
-    return OUT
+    os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":
-    print(build(verbose=True, ptxas_info="--ptxas" in sys.argv))
+    print(build(verbose=True, ptxas_info="--ptxas" in sys.argv, debug_checks="--debug-checks" in sys.argv))

@@ -63,6 +63,10 @@ struct DevBuf {
 // are not a permutation, and using them could read or write out of range.
 __device__ __forceinline__ bool sort_failed(const uint32_t* err) { return err && *(volatile const uint32_t*)err; }
 
+#ifdef QGS_DEBUG_CHECKS
+__device__ uint32_t g_check_api;  // QGS_CHECK bits of this file's kernels
+#endif
+
 __global__ void k_gather_u32(int64_t n, const uint32_t* __restrict__ idx, const uint32_t* __restrict__ src,
                              uint32_t* __restrict__ dst, const uint32_t* err) {
   if (sort_failed(err)) return;
@@ -149,7 +153,7 @@ __global__ void k_emit_packed(int64_t V, const uint32_t* __restrict__ sidx, cons
                               const short4* __restrict__ rect, const TileSlab* __restrict__ tslab, int W, int H,
                               const uint32_t* __restrict__ offs, int tiles_x, int rb, K* __restrict__ keys,
                               const uint32_t* __restrict__ tbits, const uint32_t* __restrict__ tbits_off,
-                              const uint32_t* err) {
+                              const uint32_t* err, int64_t n_inst) {
   if (sort_failed(err)) return;
   const int lane = threadIdx.x & 31;
   const int64_t r0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kEmitPerWarp;
@@ -176,7 +180,7 @@ __global__ void k_emit_packed(int64_t V, const uint32_t* __restrict__ sidx, cons
     const short4 rk = make_short4((short)(a & 0xFFFF), (short)(a >> 16), (short)(b & 0xFFFF), (short)(b >> 16));
     warp_tiles(rk, tslab ? tslab + pp : nullptr, W, H, [&](uint32_t e, int tx, int ty) {
       const uint32_t tile = (uint32_t)ty * (uint32_t)tiles_x + (uint32_t)tx;
-      keys[(size_t)oo + e] = ((K)tile << rb) | (K)rr;
+      if (QGS_CHECK(g_check_api, (int64_t)oo + e < n_inst, kChkInstance)) keys[(size_t)oo + e] = ((K)tile << rb) | (K)rr;
     }, nullptr, wk != kNoTileBits ? tbits + wk : nullptr);
   }
 }
@@ -230,7 +234,7 @@ __global__ void k_emit_packed_views(int64_t V, const uint32_t* __restrict__ sidx
 // The same for u32 keys, four per thread (one vector load; the neighbours of the four
 // are the thread's own keys except at its ends).
 __global__ void k_tile_ranges_x4(int64_t n, const uint32_t* __restrict__ keys, int shift, uint2* __restrict__ ranges,
-                                 const uint32_t* err) {
+                                 const uint32_t* err, uint32_t ntiles) {
   if (sort_failed(err)) return;
   const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
   if (i0 >= n) return;
@@ -249,6 +253,7 @@ __global__ void k_tile_ranges_x4(int64_t n, const uint32_t* __restrict__ keys, i
     const int64_t i = i0 + q;
     if (i >= n) break;
     const uint32_t t = k[1 + q] >> shift;
+    if (!QGS_CHECK(g_check_api, t < ntiles, kChkTile)) continue;
     if (i == 0 || (k[q] >> shift) != t) ranges[t].x = (uint32_t)i;
     if (i == n - 1 || (k[2 + q] >> shift) != t) ranges[t].y = (uint32_t)(i + 1);
   }
@@ -792,7 +797,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
         uint32_t* k1 = reinterpret_cast<uint32_t*>(ctx->inst2.p);
         k_emit_packed<uint32_t><<<emit_blocks(V), 256, 0, st>>>(V, sidx, ctx->cnt_sorted.p, ctx->rect.p, ctx->tslab.p,
                                                          cam->W, cam->H, ctx->offs.p, cp.tiles_x, rb, k0,
-                                                         tb_on ? ctx->tbits.p : nullptr, ctx->tbits_off.p, tmp.err);
+                                                         tb_on ? ctx->tbits.p : nullptr, ctx->tbits_off.p, tmp.err, I);
         ++launch_counter();
         QGS_CU(cudaGetLastError(), "emit");
         mark(ctx, 4, st);
@@ -802,7 +807,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
       } else {
         k_emit_packed<uint64_t><<<emit_blocks(V), 256, 0, st>>>(V, sidx, ctx->cnt_sorted.p, ctx->rect.p, ctx->tslab.p,
                                                          cam->W, cam->H, ctx->offs.p, cp.tiles_x, 32, ctx->inst.p,
-                                                         tb_on ? ctx->tbits.p : nullptr, ctx->tbits_off.p, tmp.err);
+                                                         tb_on ? ctx->tbits.p : nullptr, ctx->tbits_off.p, tmp.err, I);
         ++launch_counter();
         QGS_CU(cudaGetLastError(), "emit");
         mark(ctx, 4, st);
@@ -857,7 +862,7 @@ qgs_status render_forward(qgs_ctx* ctx, const qgs_scene* scene, const qgs_camera
   if (I > 0) {
     if (ctx->packed32)
       k_tile_ranges_x4<<<nblk((I + 3) / 4), 256, 0, st>>>(I, reinterpret_cast<const uint32_t*>(sorted), shift,
-                                                           ctx->ranges.p, tmp.err);
+                                                           ctx->ranges.p, tmp.err, (uint32_t)ntiles);
     else
       k_tile_ranges_t<uint64_t><<<nblk(I), 256, 0, st>>>(I, reinterpret_cast<const uint64_t*>(sorted), shift,
                                                          ctx->ranges.p, tmp.err);
@@ -1115,7 +1120,7 @@ qgs_status render_forward_batch(qgs_ctx* ctx, const qgs_scene* scene, int32_t n_
   QGS_CU(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(uint2) * (size_t)T_all, st), "memset ranges");
   if (I > 0) {
     if (packed)
-      k_tile_ranges_x4<<<nblk((I + 3) / 4), 256, 0, st>>>(I, ids, rb, ctx->ranges.p, tmp.err);
+      k_tile_ranges_x4<<<nblk((I + 3) / 4), 256, 0, st>>>(I, ids, rb, ctx->ranges.p, tmp.err, (uint32_t)T_all);
     else
       k_tile_ranges_t<uint64_t><<<nblk(I), 256, 0, st>>>(I, reinterpret_cast<const uint64_t*>(sorted), 32,
                                                          ctx->ranges.p, tmp.err);
@@ -1290,6 +1295,24 @@ qgs_status qgs_debug_withhold_sort_chunk(qgs_ctx* ctx, int32_t spins) {
   }
   ctx->test_withhold = 1;
   ctx->test_spins = spins;
+  return QGS_OK;
+}
+
+qgs_status qgs_debug_check_word(int32_t device, int32_t* compiled_in, uint32_t* word) {
+  if (!compiled_in || !word) return QGS_EINVAL;
+  *compiled_in = kDebugChecks ? 1 : 0;
+  *word = 0;
+  if (!kDebugChecks) return QGS_OK;
+#ifdef QGS_DEBUG_CHECKS
+  if (cudaSetDevice(device) != cudaSuccess) return QGS_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return QGS_ECUDA;
+  uint32_t w = 0, ws = 0;
+  const uint32_t zero = 0;
+  if (cudaMemcpyFromSymbol(&w, g_check_api, sizeof(uint32_t)) != cudaSuccess ||
+      cudaMemcpyToSymbol(g_check_api, &zero, sizeof(uint32_t)) != cudaSuccess || sort_check_word(&ws) != cudaSuccess)
+    return QGS_ECUDA;
+  *word = w | ws;
+#endif
   return QGS_OK;
 }
 

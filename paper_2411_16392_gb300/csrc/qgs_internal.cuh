@@ -321,6 +321,25 @@ __global__ void k_emit_hit(int64_t n, SceneView sc, CamParams cp, const uint32_t
 __global__ void k_preprocess_bwd(int64_t n, const uint32_t* list, SceneView sc, CamParams cp, const uint32_t* count,
                                  const float* pgrad, bool pgrad_by_pos, GradView gd);
 
+// ---------------------------------------------------------------- debug bounds checks
+// Checks of computed indices in the binning kernels: the emission's instance slots, the
+// range pass's tile ids, the radix sort's scatter positions. Built with -DQGS_DEBUG_CHECKS,
+// a failed check sets its bit in its translation unit's check word (a static __device__
+// word per .cu file) and the guarded access is skipped: the kernel never traps and never
+// writes out of range. Without the flag QGS_CHECK is the constant true and compiles away.
+#ifdef QGS_DEBUG_CHECKS
+#define QGS_CHECK(word, cond, bit) ((cond) || (atomicOr(&(word), (uint32_t)(bit)), false))
+constexpr bool kDebugChecks = true;
+#else
+#define QGS_CHECK(word, cond, bit) true
+constexpr bool kDebugChecks = false;
+#endif
+constexpr uint32_t kChkInstance = 1u;  // an emitted instance's slot beyond the instance count
+constexpr uint32_t kChkTile = 2u;      // a tile id beyond the tile grid
+constexpr uint32_t kChkScatter = 4u;   // a radix-sort scatter position beyond the chunk or the keys
+// Reads and clears sort.cu's check word on the current device (0 without the checks).
+cudaError_t sort_check_word(uint32_t* word);
+
 // ---------------------------------------------------------------- sorting / scan
 // Keys per CTA of the radix sort (histogram sizes depend on it).
 constexpr int kRadixChunk = 2048;

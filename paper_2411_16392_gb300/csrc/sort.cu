@@ -32,6 +32,9 @@ constexpr int RS_ITEMS = 8;                     // keys per lane
 constexpr int RS_CHUNK = RS_WARPS * 32 * RS_ITEMS;  // 2048 keys per CTA
 static_assert(RS_CHUNK == kRadixChunk, "histogram sizing assumes kRadixChunk keys per CTA");
 constexpr unsigned FULL = 0xffffffffu;
+#ifdef QGS_DEBUG_CHECKS
+__device__ uint32_t g_check_sort;  // QGS_CHECK bits of this file's kernels
+#endif
 
 // Load / store 16 consecutive u32 of a chunk (vectorised when the addresses allow it).
 __device__ __forceinline__ void load16(const uint32_t* in, int64_t i0, int64_t n, bool vec,
@@ -371,6 +374,7 @@ __global__ void __launch_bounds__(BLOCK) k_radix_downsweep(const K* __restrict__
     if (rk[it] == 0xFFFFFFFFu) continue;
     const uint32_t d = digit_of(kk[it], shift, mask);
     const uint32_t lp = lstart[d] + wh[warp][d] + rk[it];
+    if (!QGS_CHECK(g_check_sort, lp < (uint32_t)RS_CHUNK, kChkScatter)) continue;
     skeys[lp] = kk[it];
     if (HAS_VAL) svals[lp] = vv[it];
   }
@@ -380,6 +384,7 @@ __global__ void __launch_bounds__(BLOCK) k_radix_downsweep(const K* __restrict__
     const K key = skeys[i];
     const uint32_t d = digit_of(key, shift, mask);
     const uint32_t pos = boff[d] + (uint32_t)i - lstart[d];
+    if (!QGS_CHECK(g_check_sort, (int64_t)pos < n, kChkScatter)) continue;
     kout[pos] = key;
     if (HAS_VAL) vout[pos] = svals[i];
   }
@@ -559,6 +564,18 @@ cudaError_t scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, uin
   k_scan_down_off<<<nb, BLOCK, 0, st>>>(in, n, sums_scan, out, vec);
   ++launch_counter();
   return cudaGetLastError();
+}
+
+cudaError_t sort_check_word(uint32_t* word) {
+  *word = 0;
+#ifdef QGS_DEBUG_CHECKS
+  cudaError_t e = cudaMemcpyFromSymbol(word, g_check_sort, sizeof(uint32_t));
+  const uint32_t zero = 0;
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_check_sort, &zero, sizeof(uint32_t));
+  return e;
+#else
+  return cudaSuccess;
+#endif
 }
 
 bool radix_sort_u32_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t n, int begin_bit,

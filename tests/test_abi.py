@@ -66,3 +66,23 @@ def test_no_oracle_import_on_product_path():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 txt = open(os.path.join(dp, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_debug_checks_compiled_out_of_the_normal_build(lib):
+    """The normal build reports the bounds checks as absent and touches no device."""
+    ci, w = ctypes.c_int32(7), ctypes.c_uint32(9)
+    assert lib.qgs_debug_check_word(0, ctypes.byref(ci), ctypes.byref(w)) == 0
+    assert ci.value == 0 and w.value == 0
+    assert lib.qgs_debug_check_word(0, None, ctypes.byref(w)) == 1   # QGS_EINVAL
+
+
+def test_debug_check_build_compiles_and_exports():
+    """The bounds-checked variant (-DQGS_DEBUG_CHECKS) builds for sm_103a and exports the
+    same entry points."""
+    from paper_2411_16392_gb300 import _lib as L
+    from paper_2411_16392_gb300 import build as B
+    path = B.build(debug_checks=True)
+    assert path.endswith("libqgs_check.so") and os.path.exists(path)
+    chk = ctypes.CDLL(path)
+    missing = [n for n in L.declared_symbols() if not hasattr(chk, n)]
+    assert not missing, missing
