@@ -66,3 +66,29 @@ def test_json_line_takes_numpy_values():
                        "unmatched": [(1, 2, np.float64(0.5), np.int64(6), True)]}}
     assert json.loads(bench._dumps(line)) == {"parity": {"bracketed_pixels": 7, "err": 0.25, "tiles": [0, 1, 2],
                                                          "unmatched": [[1, 2, 0.5, 6, True]]}}
+
+
+def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):
+    """The reference arm (the FP64 oracle on the host cores, one stratified tile per step at
+    a small primitive count) prints one JSON line with the bench contract's keys, its own
+    e2e (no copies) and a cpu_baseline describing the run."""
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+
+    class Args:
+        steps, warmup, gpus, prims, ref_tiles = 1, 0, 1, 20000, 1
+
+    assert bench.run_reference(Args()) == 0
+    out = capsys.readouterr().out.strip().splitlines()
+    assert len(out) == 1
+    line = json.loads(out[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "impl", "e2e", "cpu_baseline"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["value"] > 0 and line["higher_is_better"] is True and line["n_gpus"] == 1
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]
