@@ -59,9 +59,8 @@ FLOP_GRAD = 200
 # the parameters (144 B) and a read-modify-write of the float32 gradients (240 B x 2).
 B_PRE_PRIM, B_PRE_VIS = 164, 128 + 2 * 80
 # DRAM bytes (read + write) per launch of the compositing kernels at 3M / 1297x840 (mean over
-# the launches of one ncu launch list, dram__bytes_read.sum + dram__bytes_write.sum; summary
-# in profiles/launches_unbounded_3m_1297x840.md), valid only while the kernels' sources hash
-# to the recorded value.
+# the launches of one ncu launch list of this benchmark, dram__bytes_read.sum +
+# dram__bytes_write.sum), valid only while the kernels' sources hash to the recorded value.
 TRAFFIC_SRC = ("paper_2411_16392_gb300/csrc/raster.cu", "paper_2411_16392_gb300/csrc/qgs_common.cuh")
 TRAFFIC = {"hash": "cab7d0c979ceeed0", "k_raster_fwd": 13474889 + 814190, "k_raster_bwd": 56434790 + 10138}
 B_BIN_VIS, B_BIN_INST = 4 * 20 + 256, 4 + 2 * 12 + 4
